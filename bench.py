@@ -1,0 +1,301 @@
+#!/usr/bin/env python3
+"""Benchmark: primary rays/s of the single-view 1920x1080 render of the
+4096^3 city world (8^3 chunks of 512^3, 4 LODs, LOD threshold 1 px), one
+step = Eq. 1 selection + visibility + per-pixel first-hit cast of one frame.
+
+Prints one JSON line.  `value` is device time (CUDA events on the launch
+stream, L2 flushed between steps, scene resident in HBM); `e2e` is the same
+metric through aok_render_host (camera in, frame copied to pinned host memory
+every step); `roofline` divides the cast kernel's algorithmic bytes (visit
+counts from the counting kernel, whose counts equal the oracle's) by its
+event time and by the measured HBM copy bandwidth; `cpu_baseline` is the CPU
+oracle timed on a bounded pixel sample on this host.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank renders its own replica (no collective in the path).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import scenegen as sg  # noqa: E402
+
+METRIC = "primary rays/s + % memory roofline; batched/served vs plain aggregate, p50/p99"
+UNIT = "rays/s"
+TAU = 1.0
+CAM_SEED = 102
+W, H = 1920, 1080
+WORKLOAD = "city4096: 4096^3 world, 8x8x8 chunks of 512^3, 4 LODs, crust terrain + 4000 hollow blocks; " \
+           "one 1920x1080 view, LOD threshold 1 px, camera seed 102"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler (clocks + throttle reasons) around the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if not self.p:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def cpu_oracle_sample(world, cam, budget_s=20.0, max_pixels=400_000):
+    """Oracle rays/s on a stratified pixel sample of the same frame (all host cores)."""
+    import oracle as orc
+    S = orc.OracleScene(world)
+    sel = S.select(cam, TAU)
+    t0 = time.perf_counter()
+    S.prepare(sel)
+    prep = time.perf_counter() - t0
+    n = W * H
+    # calibrate on a small sample, then size the timed one to ~budget_s
+    step = 97
+    idx = np.arange(0, n, step)
+    pix = np.stack([idx % W, idx // W], 1)
+    t0 = time.perf_counter()
+    S.cast(cam, sel, pix)
+    rate = len(idx) / max(time.perf_counter() - t0, 1e-6)
+    m = int(min(max_pixels, max(20_000, rate * budget_s)))
+    step = max(1, n // m)
+    idx = np.arange(0, n, step)
+    pix = np.stack([idx % W, idx // W], 1)
+    t0 = time.perf_counter()
+    S.cast(cam, sel, pix)
+    dt = time.perf_counter() - t0
+    cores = orc.default_threads()
+    return {"value": len(idx) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"every {step}th pixel of the frame ({len(idx)} rays), FP64 oracle on {cores} threads; "
+                      f"oracle DAG build for the frame's LOD selection took {prep:.1f} s and is not timed"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle as it stands, same workload/metric, bounded sample per step."""
+    rank, world_size, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle as orc
+    world = sg.World(sg.CITY_4096)
+    cam = sg.ground_camera(world, CAM_SEED, W, H)
+    S = orc.OracleScene(world)
+    sel = S.select(cam, TAU)
+    S.prepare(sel)
+    n = W * H
+    per_step = 4096
+    rng = np.random.default_rng(0)
+    for _ in range(args.warmup):
+        idx = rng.integers(0, n, per_step)
+        S.cast(cam, sel, np.stack([idx % W, idx // W], 1))
+    t0 = time.perf_counter()
+    rays = 0
+    for _ in range(args.steps):
+        idx = rng.integers(0, n, per_step)
+        S.cast(cam, sel, np.stack([idx % W, idx // W], 1))
+        rays += per_step
+    dt = time.perf_counter() - t0
+    v = rays / dt
+    cores = orc.default_threads()
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "step": f"{per_step} random pixels of the frame per step"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} random pixels per step, {args.steps} steps"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--threads", type=int, default=0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2505_02017_gb300 as aok
+
+    rank, world_size, local_rank = dist_env()
+    dist = None
+    if world_size > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = local_rank if world_size > 1 else 0
+    torch.cuda.set_device(dev)
+    threads = args.threads or os.cpu_count() or 1
+
+    # ---- scene: build every chunk x LOD on the host, upload (untimed) ----
+    t0 = time.perf_counter()
+    world = sg.World(sg.CITY_4096)
+    built = aok.BuiltWorld(world, threads)
+    t_build = time.perf_counter() - t0
+    ctx = aok.Context(dev)
+    t0 = time.perf_counter()
+    scene = aok.Scene.from_world(ctx, world, built=built)
+    t_upload = time.perf_counter() - t0
+    cam = sg.ground_camera(world, CAM_SEED, W, H)
+    stream = torch.cuda.current_stream()
+    hit, t = aok.alloc_frame(W, H, device=f"cuda:{dev}")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=f"cuda:{dev}")  # > 129 MB L2
+
+    # ---- algorithmic bytes of this frame (counting kernel, untimed) ----
+    counts = torch.zeros((H, W, 3), dtype=torch.int32, device=f"cuda:{dev}")
+    aok.render_counted(ctx, scene, cam, TAU, hit, t, counts)
+    torch.cuda.synchronize()
+    c = counts.view(-1, 3).to(torch.int64).sum(0).tolist()
+    algo_bytes = 8 * c[0] + 8 * c[1] + c[2] + 20 * W * H  # node visits, leaf visits, resolve, output
+    del counts
+
+    # ---- warmup ----
+    for _ in range(args.warmup):
+        aok.render(ctx, scene, cam, TAU, hit, t)
+    torch.cuda.synchronize()
+
+    # ---- timed: K steps, L2 flushed between steps, events around select and cast ----
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clocks = Clocks(dev)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        aok.select_chunks(ctx, scene, cam, TAU, stream=stream)
+        ev[k][1].record(stream)
+        aok.cast_selected(ctx, scene, cam, hit, t, stream=stream)
+        ev[k][2].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    time.sleep(0.3)
+    clk = clocks.stop()
+    step_ms = [e[0].elapsed_time(e[2]) for e in ev]
+    cast_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        tt = torch.tensor([total_ms], device=f"cuda:{dev}")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    rays = W * H
+    value = world_size * rays * args.steps / (total_ms / 1000.0)
+    cast_avg = sum(cast_ms) / len(cast_ms)
+    hbm, peak_kind = peaks()
+    achieved = algo_bytes / (cast_avg / 1000.0) / 1e9
+
+    # ---- e2e: public API with host buffers (camera in, frame copied out every step) ----
+    hh = torch.empty((H, W, 4), dtype=torch.int32, pin_memory=True)
+    th = torch.empty((H, W), dtype=torch.float32, pin_memory=True)
+    for _ in range(3):
+        aok.render_host(ctx, scene, cam, TAU, hh, th)
+    e2e_steps = max(3, min(args.steps, 50))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        aok.render_host(ctx, scene, cam, TAU, hh, th)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = world_size * rays / e2e_s
+    if dist:
+        tt = torch.tensor([e2e_s], device=f"cuda:{dev}")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e = world_size * rays / float(tt.item())
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world_size, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "i64/f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "rays_per_step": rays, "parallelism": f"replicas x{world_size}",
+                   "l2": "flushed between steps (512 MB write)", "scene_build_s": round(t_build, 2),
+                   "scene_upload_s": round(t_upload, 2),
+                   "scene_bytes": {"nodes": built.node_words * 4, "leaves": built.leaves * 8,
+                                   "mats": built.mat_bytes}},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": None, "kernel": "cast_kernel", "peak_kind": f"{peak_kind} hbm_gbs",
+                     "algo_bytes_per_launch": algo_bytes, "algo_bytes_per_ray": algo_bytes / rays,
+                     "cast_ms": cast_avg},
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 52, "d2h_bytes_per_step": rays * 20},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+        "wall_s_timed": wall,
+    }
+    if rank == 0 and world_size == 1 and not args.no_cpu_baseline:
+        try:
+            out["cpu_baseline"] = cpu_oracle_sample(world, cam)
+        except Exception as ex:  # pragma: no cover
+            out["cpu_baseline"] = {"error": str(ex)}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    scene.destroy()
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

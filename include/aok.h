@@ -1,0 +1,281 @@
+/*
+ * aok.h -- C ABI of the GB300 primary-ray library for chunked multi-LOD
+ * sparse voxel DAG scenes (after "Aokana: A GPU-Driven Voxel Rendering
+ * Framework for Open World Games", Fang, Wang, Wang, PACMCGIT 8(1), 2025).
+ *
+ * A scene is a grid of chunk regions, each M^3 LOD-0 voxels (Sec. 3.1), each
+ * stored at n_lods levels of detail (Sec. 3.4) as one sparse voxel DAG per
+ * (chunk, LOD) (Sec. 3.2) with a depth-first material array (Sec. 3.3).  A
+ * frame selects one LOD per chunk region with Eq. 1, culls chunks to the
+ * view, and casts one primary ray per pixel to its first solid voxel,
+ * returning voxel coordinate, LOD, material and hit distance (the ray
+ * marching and colour-resolve passes of Sec. 3.5).
+ *
+ * Conventions common to every call:
+ *  - Every call returns an aok_status (int); no C++ exception or abort
+ *    crosses this boundary.  AOK_E_CUDA means a CUDA error was observed; a
+ *    sticky device error leaves the context unusable.
+ *  - Host pointers are read during the call only; the caller keeps ownership.
+ *  - "device" pointers are CUDA global-memory addresses on the context's
+ *    device, owned by the caller unless stated otherwise.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls taking a stream only enqueue work; they return before
+ *    the GPU finishes.
+ *  - Coordinates are LOD-0 voxel units, up axis z; voxel k covers [k, k+1).
+ *  - A context is used by one host thread at a time, except the serving
+ *    calls (aok_serve_*), which are thread-safe.
+ */
+#ifndef AOK_H
+#define AOK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum aok_status {
+    AOK_OK = 0,
+    AOK_PENDING = 1,          /* serving: request not finished yet */
+    AOK_E_INVALID = -1,       /* bad argument (null, out of range, misaligned) */
+    AOK_E_OOM = -2,           /* HBM budget or pool capacity exceeded */
+    AOK_E_NOT_RESIDENT = -3,  /* chunk/LOD or scene not present */
+    AOK_E_TIMEOUT = -4,       /* a bounded wait ran out */
+    AOK_E_CUDA = -5,          /* CUDA runtime error */
+    AOK_E_BUSY = -6,          /* serving: no free slot, retry later */
+    AOK_E_CORRUPT = -7        /* chunk blob failed validation */
+} aok_status;
+
+typedef struct aok_ctx aok_ctx;
+
+/* ------------------------------------------------------------------ */
+/* Context                                                            */
+/* ------------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`.  All device memory the library
+ * allocates (scene pools, per-frame tables, serving slots) is charged
+ * against `hbm_budget_bytes` (0 = 90% of the device's free memory at
+ * creation).  Returns AOK_E_INVALID for a bad device, AOK_E_CUDA on
+ * initialisation failure. */
+int aok_create(aok_ctx** out, int device, size_t hbm_budget_bytes);
+/* Wait for the context's work, free every allocation, stop serving. */
+void aok_destroy(aok_ctx* ctx);
+/* Bytes currently charged against the budget / the budget itself. */
+int aok_memory(aok_ctx* ctx, size_t* used_bytes, size_t* budget_bytes);
+const char* aok_status_str(int status);
+
+/* ------------------------------------------------------------------ */
+/* Scenes and chunk residency (Sec. 3.1-3.4)                          */
+/* ------------------------------------------------------------------ */
+
+typedef struct aok_scene_desc {
+    int32_t grid[3];          /* chunk regions per axis (>= 1); grid*chunk_res <= 131072 per axis */
+    int32_t chunk_res;        /* M: LOD-0 voxels per chunk side, power of two in [8, 512] */
+    int32_t n_lods;           /* LODs per chunk, 1 <= n_lods and (chunk_res >> (n_lods-1)) >= 8 */
+    float view_dist;          /* > 0: hits farther than this (LOD-0 units) are misses; 0 = none */
+    uint64_t node_words;      /* device pool capacities: DAG node words (uint32) ... */
+    uint64_t leaf_count;      /* ... 4x4x4 leaf masks (uint64) ... */
+    uint64_t mat_bytes;       /* ... material bytes */
+} aok_scene_desc;
+
+/* Allocate a scene's device pools (charged to the budget; AOK_E_OOM if they
+ * do not fit).  *scene_id receives a handle. */
+int aok_scene_create(aok_ctx* ctx, const aok_scene_desc* desc, uint32_t* scene_id);
+/* Free a scene (waits for the context's streams first). */
+int aok_scene_destroy(aok_ctx* ctx, uint32_t scene);
+
+/* One (chunk, LOD) as produced offline (Sec. 3.2, Sec. 3.3, Fig. 2).
+ *  nodes  : uint32 words.  A node is [header, leaf_count, child_0 .. child_{k-1}]:
+ *           header bits 0..7 = child mask (bit o set <=> octant o non-empty;
+ *           octant o = x | y<<1 | z<<2), bits 8..31 zero; leaf_count = solid
+ *           voxels in the subtree; k = popcount(mask) child pointers in octant
+ *           order.  A node covering 8x8x8 voxels of its LOD points into
+ *           `leaves`; every other node points to node word indices.  Pointers
+ *           are relative to this blob.
+ *  leaves : uint64 masks of 4x4x4 voxel blocks, bit x + 4y + 16z.
+ *  mats   : one uint8 per solid voxel in depth-first order (ascending octant,
+ *           then ascending leaf bit); n_mats = leaf_count of the root.
+ *  root   : word index of the root node (covers the whole chunk region at
+ *           resolution chunk_res >> lod).  n_node_words == 0 => empty chunk.
+ *  aabb   : bounding box of the solid voxels, chunk-local LOD-0 units, [lo, hi). */
+typedef struct aok_chunk_blob {
+    const uint32_t* nodes;
+    uint64_t n_node_words;
+    const uint64_t* leaves;
+    uint64_t n_leaves;
+    const uint8_t* mats;
+    uint64_t n_mats;
+    uint32_t root;
+    int32_t aabb_lo[3];
+    int32_t aabb_hi[3];
+} aok_chunk_blob;
+
+/* Validate a host blob, rebase its pointers and copy it into the scene's
+ * device pools (synchronously on the context's copy stream).  Replaces a
+ * previous upload of the same (chunk, lod).  The validator walks every node
+ * reachable from the root and returns AOK_E_CORRUPT (uploading nothing) for
+ * an out-of-range pointer, a zero or reserved-bit header, a node reached at
+ * two depths, a leaf count that is not the sum of its children's, a root
+ * count different from n_mats, or an AABB outside the chunk.
+ * AOK_E_OOM if a pool is full; AOK_E_INVALID for a bad chunk/lod. */
+int aok_scene_upload_chunk(aok_ctx* ctx, uint32_t scene, int32_t cx, int32_t cy, int32_t cz,
+                           uint32_t lod, const aok_chunk_blob* blob);
+/* Host-only check of a blob against the rules aok_scene_upload_chunk applies
+ * (no device work, no context needed): AOK_OK, AOK_E_CORRUPT, or
+ * AOK_E_INVALID for a bad chunk_res / lod. */
+int aok_validate_chunk(const aok_chunk_blob* blob, int32_t chunk_res, uint32_t lod);
+/* Make a (chunk, lod) non-resident (it renders as empty).  Pool space of the
+ * evicted chunk is reused by later uploads of at most the same size. */
+int aok_scene_evict_chunk(aok_ctx* ctx, uint32_t scene, int32_t cx, int32_t cy, int32_t cz, uint32_t lod);
+
+/* ------------------------------------------------------------------ */
+/* Cameras and frames                                                 */
+/* ------------------------------------------------------------------ */
+
+/* Pinhole camera.  origin components must be multiples of 2^-12 with
+ * |origin| < 2^17 (exact fixed-point traversal; AOK_E_INVALID otherwise).
+ * R is row-major 3x3 whose columns are right, up and back (= -forward).
+ * The ray of pixel (px, py) is origin + t d with d computed in IEEE binary32,
+ * one rounding per operation, no contraction:
+ *   u = (((2px+1)/W) - 1) * tan_half_fovy * (W/H),  v = (1 - (2py+1)/H) * tan_half_fovy,
+ *   d_i = ((R_i0 u) + (R_i1 v)) - R_i2. */
+typedef struct aok_camera {
+    float origin[3];
+    float R[9];
+    float tan_half_fovy;
+    int32_t width, height;
+} aok_camera;
+
+/* Per-pixel output, caller-owned device buffers, row-major (py*W + px):
+ *  hit  : 4 x uint32 per pixel, 16-byte aligned: x, y, z = min corner of the
+ *         first-hit voxel (LOD-0 units, multiples of 2^lod) and meta =
+ *         lod (bits 0..7) | material << 8 | normal << 16 (3 bits:
+ *         2*axis + (d_axis < 0), 7 = origin inside a voxel) | 1 << 19 (hit).
+ *         A miss writes x = y = z = 0, meta = 0xFF | 7 << 16.
+ *  t    : float per pixel, 4-byte aligned: hit distance |t* d| in LOD-0
+ *         units (+inf on a miss). */
+typedef struct aok_frame {
+    void* hit;
+    float* t;
+} aok_frame;
+
+/* ------------------------------------------------------------------ */
+/* Per-frame LOD selection and visibility (Sec. 3.4 Eq. 1, Sec. 3.5)  */
+/* ------------------------------------------------------------------ */
+
+/* Select one LOD per chunk region with Eq. 1,
+ *   LODError = ChunkSize * StreamingFactor - |ChunkCenter - CameraPos|,
+ * over the implicit chunk octree (level n block = (2^n)^3 chunk regions,
+ * ChunkSize = 2^n M, centre = the block's centre): a chunk takes the first
+ * level n from n_lods-1 down to 0 whose LODError <= 0, else 0.  The pixel
+ * threshold tau maps to StreamingFactor = (H / (2 tan_half_fovy)) / (tau M),
+ * i.e. an LOD-n voxel at the cut-off distance covers tau pixels.  Evaluated
+ * in IEEE FP64 with a fixed operation order.  Then culls chunks whose
+ * selected DAG is empty or not resident, whose AABB lies outside the view
+ * pyramid, or (view_dist > 0) beyond the view distance.
+ *  lod_per_chunk_dev : optional device int8[grid x*y*z] (x fastest) receiving
+ *                      every chunk region's Eq. 1 LOD.
+ *  visible_dev       : optional device uint8[grid x*y*z]: 1 if the chunk is
+ *                      kept for casting, 0 if empty, not resident or culled.
+ *  n_visible_out     : optional host pointer; if given the call synchronises
+ *                      the stream and returns the number of visible chunks.
+ * Enqueued on `stream`; writes the scene's per-frame chunk table used by the
+ * next aok_render of this scene on the same stream. */
+int aok_select_chunks(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double lod_threshold_px,
+                      int8_t* lod_per_chunk_dev, uint8_t* visible_dev, uint32_t* n_visible_out, void* stream);
+
+/* Select (as aok_select_chunks) and cast every pixel's primary ray through
+ * the chunk grid and the selected DAGs; writes `frame` on `stream`.  The
+ * scene's per-frame chunk table is shared: aok_render calls on one scene that
+ * overlap on the GPU (different streams) race; use aok_render_batch for
+ * concurrent views. */
+int aok_render(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double lod_threshold_px,
+               const aok_frame* frame, void* stream);
+
+/* Cast with the chunk table written by the last aok_select_chunks of this
+ * scene (same camera), so that the two passes can be enqueued and timed
+ * separately.  Same output contract as aok_render. */
+int aok_cast_selected(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, const aok_frame* frame, void* stream);
+
+/* aok_render into host memory: renders into library-owned device buffers,
+ * then copies the frame into the caller's host buffers (hit_host: 16 bytes
+ * per pixel, t_host: 4 bytes per pixel; pinned memory gives asynchronous
+ * copies) and synchronises `stream` before returning.  The device buffers
+ * are kept for the next call (grown on demand, charged to the budget). */
+int aok_render_host(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double lod_threshold_px,
+                    void* hit_host, float* t_host, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* Batched multi-view rendering                                       */
+/* ------------------------------------------------------------------ */
+
+typedef struct aok_view {
+    uint32_t scene;
+    aok_camera cam;
+    double lod_threshold_px;
+    aok_frame frame;
+} aok_view;
+
+/* Render n views (any scenes, uneven resolutions) with one selection launch
+ * and one persistent casting launch that pulls ray packets from a global
+ * queue across all views.  The same list shape (n and every width/height)
+ * replays a CUDA graph captured on first use.  Results equal n separate
+ * aok_render calls.  AOK_E_INVALID if n is 0 or above 4096. */
+int aok_render_batch(aok_ctx* ctx, const aok_view* views, uint32_t n, void* stream);
+
+/* Launch shape of the persistent casting kernel (0 = keep current):
+ * CTAs per SM, threads per CTA (multiple of 32), rays per packet (multiple
+ * of 32).  aok_autotune times candidate shapes on the given views and keeps
+ * the fastest; *best_ms receives its time per batch. */
+int aok_set_launch(aok_ctx* ctx, uint32_t ctas_per_sm, uint32_t threads_per_cta, uint32_t packet_rays);
+int aok_get_launch(aok_ctx* ctx, uint32_t* ctas_per_sm, uint32_t* threads_per_cta, uint32_t* packet_rays);
+int aok_autotune(aok_ctx* ctx, const aok_view* views, uint32_t n, void* stream, float* best_ms);
+
+/* ------------------------------------------------------------------ */
+/* Continuous-batching serving                                        */
+/* ------------------------------------------------------------------ */
+
+typedef struct aok_request {
+    uint32_t scene;
+    aok_camera cam;
+    double lod_threshold_px;
+} aok_request;
+
+/* Start the serving loop: a host thread admits submitted requests into at
+ * most `max_slots` in-flight slots when their framebuffers fit in the HBM
+ * budget, groups the admitted ones into batches of at most `max_batch`
+ * views, and launches each batch on one of `n_streams` streams, so that new
+ * arrivals overlap with batches already on the GPU. */
+int aok_serve_start(aok_ctx* ctx, uint32_t max_slots, uint32_t max_batch, uint32_t n_streams);
+/* Stop admitting, finish in-flight work, join the loop. */
+int aok_serve_stop(aok_ctx* ctx);
+/* Queue a request; *ticket identifies it.  AOK_E_BUSY when the submit queue
+ * is full, AOK_E_NOT_RESIDENT for an unknown scene. */
+int aok_serve_submit(aok_ctx* ctx, const aok_request* req, uint64_t* ticket);
+/* AOK_PENDING while queued or running; AOK_OK when done, with out_view
+ * pointing at library-owned device buffers valid until aok_serve_release. */
+int aok_serve_poll(aok_ctx* ctx, uint64_t ticket, aok_frame* out_view);
+/* Block until done or `timeout_ms` passes (AOK_E_TIMEOUT). */
+int aok_serve_wait(aok_ctx* ctx, uint64_t ticket, uint32_t timeout_ms, aok_frame* out_view);
+/* Return the ticket's buffers to the pool (cancels it if not started). */
+int aok_serve_release(aok_ctx* ctx, uint64_t ticket);
+
+/* ------------------------------------------------------------------ */
+/* Diagnostics                                                        */
+/* ------------------------------------------------------------------ */
+
+/* Like aok_render, but also writes per-pixel traversal counts to the device
+ * buffer counts (3 x uint32 per pixel: interior-node visits including chunk
+ * roots, leaf-block visits, material-resolve bytes).  Slower; used to derive
+ * the algorithmic bytes of a frame. */
+int aok_render_counted(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double lod_threshold_px,
+                       const aok_frame* frame, uint32_t* counts, void* stream);
+/* Write every pixel's FP32 ray direction (3 floats per pixel) to the device
+ * buffer dirs, as the casting kernel computes it. */
+int aok_ray_dirs(aok_ctx* ctx, const aok_camera* cam, float* dirs, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AOK_H */

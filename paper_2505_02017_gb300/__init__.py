@@ -1,0 +1,340 @@
+"""GB300 primary-ray casting through chunked multi-LOD sparse voxel DAGs.
+
+Thin ctypes binding of the C ABI in include/aok.h (argument marshalling only:
+every step of the path runs in the native library's CUDA kernels).  PyTorch
+supplies device memory and streams.  There is no CPU fallback: importing the
+binding raises if libaok.so cannot be built or loaded.
+
+Method: "Aokana: A GPU-Driven Voxel Rendering Framework for Open World Games"
+(Fang, Wang, Wang, PACMCGIT 8(1), 2025), Sec. 3.1-3.5 and Eq. 1.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _native
+
+AOK_OK, AOK_PENDING = 0, 1
+AOK_E_INVALID, AOK_E_OOM, AOK_E_NOT_RESIDENT, AOK_E_TIMEOUT = -1, -2, -3, -4
+AOK_E_CUDA, AOK_E_BUSY, AOK_E_CORRUPT = -5, -6, -7
+
+
+class AokError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {lib().aok_status_str(status).decode()} ({status})")
+
+
+# ---------------------------------------------------------------------------
+# ctypes mirrors of include/aok.h
+# ---------------------------------------------------------------------------
+class SceneDesc(ctypes.Structure):
+    _fields_ = [("grid", ctypes.c_int32 * 3), ("chunk_res", ctypes.c_int32), ("n_lods", ctypes.c_int32),
+                ("view_dist", ctypes.c_float), ("node_words", ctypes.c_uint64), ("leaf_count", ctypes.c_uint64),
+                ("mat_bytes", ctypes.c_uint64)]
+
+
+class ChunkBlob(ctypes.Structure):
+    _fields_ = [("nodes", ctypes.c_void_p), ("n_node_words", ctypes.c_uint64), ("leaves", ctypes.c_void_p),
+                ("n_leaves", ctypes.c_uint64), ("mats", ctypes.c_void_p), ("n_mats", ctypes.c_uint64),
+                ("root", ctypes.c_uint32), ("aabb_lo", ctypes.c_int32 * 3), ("aabb_hi", ctypes.c_int32 * 3)]
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_float * 3), ("R", ctypes.c_float * 9), ("tan_half_fovy", ctypes.c_float),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+
+
+class Frame(ctypes.Structure):
+    _fields_ = [("hit", ctypes.c_void_p), ("t", ctypes.c_void_p)]
+
+
+class View(ctypes.Structure):
+    _fields_ = [("scene", ctypes.c_uint32), ("cam", Camera), ("lod_threshold_px", ctypes.c_double),
+                ("frame", Frame)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("scene", ctypes.c_uint32), ("cam", Camera), ("lod_threshold_px", ctypes.c_double)]
+
+
+_lib = None
+_blib = None
+
+
+def lib() -> ctypes.CDLL:
+    """libaok.so with typed signatures (built in-tree on first use)."""
+    global _lib
+    if _lib is None:
+        _native.build()
+        L = ctypes.CDLL(_native.LIBAOK)
+        vp, u32, i32, u64, dbl = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_double
+        P = ctypes.POINTER
+        sig = {
+            "aok_create": [P(vp), ctypes.c_int, ctypes.c_size_t],
+            "aok_memory": [vp, P(ctypes.c_size_t), P(ctypes.c_size_t)],
+            "aok_scene_create": [vp, P(SceneDesc), P(u32)],
+            "aok_scene_destroy": [vp, u32],
+            "aok_scene_upload_chunk": [vp, u32, i32, i32, i32, u32, P(ChunkBlob)],
+            "aok_scene_evict_chunk": [vp, u32, i32, i32, i32, u32],
+            "aok_select_chunks": [vp, u32, P(Camera), dbl, vp, vp, P(u32), vp],
+            "aok_render": [vp, u32, P(Camera), dbl, P(Frame), vp],
+            "aok_render_counted": [vp, u32, P(Camera), dbl, P(Frame), vp, vp],
+            "aok_ray_dirs": [vp, P(Camera), vp, vp],
+            "aok_cast_selected": [vp, u32, P(Camera), P(Frame), vp],
+            "aok_render_host": [vp, u32, P(Camera), dbl, vp, vp, vp],
+            "aok_validate_chunk": [P(ChunkBlob), i32, u32],
+            "aok_render_batch": [vp, P(View), u32, vp],
+            "aok_set_launch": [vp, u32, u32, u32],
+            "aok_get_launch": [vp, P(u32), P(u32), P(u32)],
+            "aok_autotune": [vp, P(View), u32, vp, P(ctypes.c_float)],
+            "aok_serve_start": [vp, u32, u32, u32],
+            "aok_serve_stop": [vp],
+            "aok_serve_submit": [vp, P(Request), P(u64)],
+            "aok_serve_poll": [vp, u64, P(Frame)],
+            "aok_serve_wait": [vp, u64, u32, P(Frame)],
+            "aok_serve_release": [vp, u64],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.aok_destroy.argtypes = [vp]
+        L.aok_destroy.restype = None
+        L.aok_status_str.argtypes = [ctypes.c_int]
+        L.aok_status_str.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def blib() -> ctypes.CDLL:
+    """libaokbuild.so: offline chunk preparation over scenegen worlds."""
+    global _blib
+    if _blib is None:
+        _native.build()
+        L = ctypes.CDLL(_native.LIBBUILD)
+        vp = ctypes.c_void_p
+        L.aokb_build.restype = vp
+        L.aokb_build.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, vp, ctypes.c_int64, ctypes.c_int32]
+        L.aokb_free.argtypes = [vp]
+        L.aokb_count.restype = ctypes.c_int64
+        L.aokb_count.argtypes = [vp]
+        L.aokb_get.restype = ctypes.c_int
+        L.aokb_get.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+                               ctypes.POINTER(ChunkBlob)]
+        L.aokb_totals.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64 * 4)]
+        _blib = L
+    return _blib
+
+
+def validate_chunk(blob: ChunkBlob, chunk_res: int, lod: int) -> int:
+    """Host-only blob validation (no device needed); returns the status code."""
+    return int(lib().aok_validate_chunk(ctypes.byref(blob), chunk_res, lod))
+
+
+def check(status: int, what: str = "aok") -> int:
+    if status < 0:
+        raise AokError(status, what)
+    return status
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def to_camera(cam) -> Camera:
+    """From a scenegen.Camera (origin, R, tan_half_fovy, W, H)."""
+    c = Camera()
+    for i in range(3):
+        c.origin[i] = float(cam.origin[i])
+    R = np.asarray(cam.R, np.float32)
+    for i in range(3):
+        for j in range(3):
+            c.R[3 * i + j] = float(R[i, j])
+    c.tan_half_fovy = float(cam.tan_half_fovy)
+    c.width, c.height = int(cam.W), int(cam.H)
+    return c
+
+
+# ---------------------------------------------------------------------------
+# context / scene / frames
+# ---------------------------------------------------------------------------
+class Context:
+    """One aok_ctx on a CUDA device (owns all library device memory)."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 0):
+        h = ctypes.c_void_p()
+        check(lib().aok_create(ctypes.byref(h), device, budget_bytes), "aok_create")
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if self.h:
+            lib().aok_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def memory(self):
+        u, b = ctypes.c_size_t(), ctypes.c_size_t()
+        check(lib().aok_memory(self.h, ctypes.byref(u), ctypes.byref(b)))
+        return u.value, b.value
+
+
+class BuiltWorld:
+    """Chunk blobs (all LODs) of a scenegen world, built by libaokbuild."""
+
+    def __init__(self, world, threads: int | None = None, chunks=None):
+        spec = world.spec
+        self.spec = spec
+        arr = None
+        n = 0
+        if chunks is not None:
+            arr = np.ascontiguousarray(chunks, np.int64)
+            n = len(arr)
+        self.h = blib().aokb_build(world.handle, spec.chunk, spec.n_lods,
+                                   arr.ctypes.data if arr is not None else None, n,
+                                   threads or os.cpu_count() or 1)
+        if not self.h:
+            raise ValueError("bad chunking for the builder")
+        t = (ctypes.c_uint64 * 4)()
+        blib().aokb_totals(self.h, ctypes.byref(t))
+        self.node_words, self.leaves, self.mat_bytes, self.nonempty = (int(v) for v in t)
+
+    def __len__(self):
+        return int(blib().aokb_count(self.h))
+
+    def blob(self, i: int, lod: int):
+        b = ChunkBlob()
+        c = ctypes.c_int64()
+        if blib().aokb_get(self.h, i, lod, ctypes.byref(c), ctypes.byref(b)) != 0:
+            raise IndexError(i)
+        return int(c.value), b
+
+    def close(self):
+        if self.h:
+            blib().aokb_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Scene:
+    """A scene on a Context: pools sized for `built`, every blob uploaded."""
+
+    def __init__(self, ctx: Context, spec, node_words: int, leaves: int, mat_bytes: int):
+        self.ctx = ctx
+        self.spec = spec
+        self.grid = (spec.wx // spec.chunk, spec.wy // spec.chunk, spec.wz // spec.chunk)
+        d = SceneDesc()
+        for a in range(3):
+            d.grid[a] = self.grid[a]
+        d.chunk_res, d.n_lods, d.view_dist = spec.chunk, spec.n_lods, float(spec.view_dist)
+        d.node_words, d.leaf_count, d.mat_bytes = max(1, node_words), max(1, leaves), max(1, mat_bytes)
+        sid = ctypes.c_uint32()
+        check(lib().aok_scene_create(ctx.h, ctypes.byref(d), ctypes.byref(sid)), "aok_scene_create")
+        self.id = sid.value
+
+    @classmethod
+    def from_world(cls, ctx: Context, world, threads: int | None = None, built: BuiltWorld | None = None):
+        bw = built or BuiltWorld(world, threads)
+        sc = cls(ctx, world.spec, bw.node_words, bw.leaves, bw.mat_bytes)
+        sc.upload_built(bw)
+        return sc
+
+    def upload_built(self, bw: BuiltWorld):
+        gx, gy, _ = self.grid
+        for i in range(len(bw)):
+            for lod in range(self.spec.n_lods):
+                c, b = bw.blob(i, lod)
+                self.upload(c % gx, (c // gx) % gy, c // (gx * gy), lod, b)
+
+    def upload(self, cx, cy, cz, lod, blob: ChunkBlob):
+        return check(lib().aok_scene_upload_chunk(self.ctx.h, self.id, cx, cy, cz, lod, ctypes.byref(blob)),
+                     "aok_scene_upload_chunk")
+
+    def evict(self, cx, cy, cz, lod):
+        return check(lib().aok_scene_evict_chunk(self.ctx.h, self.id, cx, cy, cz, lod), "aok_scene_evict_chunk")
+
+    def destroy(self):
+        if self.id:
+            lib().aok_scene_destroy(self.ctx.h, self.id)
+            self.id = 0
+
+
+def alloc_frame(W: int, H: int, device="cuda"):
+    """Caller-owned device output buffers: hit int32[H, W, 4], t float32[H, W]."""
+    import torch
+    hit = torch.empty((H, W, 4), dtype=torch.int32, device=device)
+    t = torch.empty((H, W), dtype=torch.float32, device=device)
+    return hit, t
+
+
+def frame_of(hit, t) -> Frame:
+    f = Frame()
+    f.hit = hit.data_ptr()
+    f.t = t.data_ptr()
+    return f
+
+
+def render(ctx: Context, scene: Scene, cam, tau: float, hit, t, stream=None):
+    f = frame_of(hit, t)
+    c = to_camera(cam)
+    return check(lib().aok_render(ctx.h, scene.id, ctypes.byref(c), float(tau), ctypes.byref(f),
+                                  _stream_handle(stream)), "aok_render")
+
+
+def cast_selected(ctx: Context, scene: Scene, cam, hit, t, stream=None):
+    """Cast with the table of the last select_chunks on this scene."""
+    f = frame_of(hit, t)
+    c = to_camera(cam)
+    return check(lib().aok_cast_selected(ctx.h, scene.id, ctypes.byref(c), ctypes.byref(f), _stream_handle(stream)),
+                 "aok_cast_selected")
+
+
+def render_host(ctx: Context, scene: Scene, cam, tau: float, hit_host, t_host, stream=None):
+    """Render into host tensors (pinned for asynchronous copies); returns after the copies."""
+    c = to_camera(cam)
+    return check(lib().aok_render_host(ctx.h, scene.id, ctypes.byref(c), float(tau), hit_host.data_ptr(),
+                                       t_host.data_ptr(), _stream_handle(stream)), "aok_render_host")
+
+
+def render_counted(ctx: Context, scene: Scene, cam, tau: float, hit, t, counts, stream=None):
+    f = frame_of(hit, t)
+    c = to_camera(cam)
+    return check(lib().aok_render_counted(ctx.h, scene.id, ctypes.byref(c), float(tau), ctypes.byref(f),
+                                          counts.data_ptr(), _stream_handle(stream)), "aok_render_counted")
+
+
+def select_chunks(ctx: Context, scene: Scene, cam, tau: float, lod_out=None, vis_out=None, stream=None,
+                  count: bool = False):
+    c = to_camera(cam)
+    nvis = ctypes.c_uint32()
+    check(lib().aok_select_chunks(ctx.h, scene.id, ctypes.byref(c), float(tau),
+                                  lod_out.data_ptr() if lod_out is not None else None,
+                                  vis_out.data_ptr() if vis_out is not None else None,
+                                  ctypes.byref(nvis) if count else None, _stream_handle(stream)),
+          "aok_select_chunks")
+    return nvis.value if count else None
+
+
+def ray_dirs(ctx: Context, cam, dirs, stream=None):
+    c = to_camera(cam)
+    return check(lib().aok_ray_dirs(ctx.h, ctypes.byref(c), dirs.data_ptr(), _stream_handle(stream)),
+                 "aok_ray_dirs")

@@ -1,0 +1,70 @@
+// Internal structures shared by the host runtime and the CUDA kernels.
+#pragma once
+#include <cstdint>
+
+#include "../../include/aok.h"
+
+namespace aok {
+
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+constexpr int kFix = 12;            // camera origin fixed point: multiples of 2^-12
+constexpr int kMaxLevels = 10;      // log2(512) + 1
+
+// One (chunk, LOD) as resident on the device, and (per frame) the selected
+// LOD of a chunk region.  32 bytes: one sector per lookup.
+struct ChunkRef {
+    uint32_t root;       // global node word index, kNone = empty / not resident / culled
+    uint32_t lod;        // LOD of this DAG
+    uint64_t mat_base;   // offset of its materials in the scene's material pool
+    uint16_t aabb[6];    // chunk-local LOD-0 units: lo x,y,z, hi x,y,z ([lo, hi))
+    uint32_t pad;
+};
+static_assert(sizeof(ChunkRef) == 32, "ChunkRef is one 32-byte sector");
+
+struct SceneDev {
+    const uint32_t* nodes;
+    const uint64_t* leaves;
+    const uint8_t* mats;
+    const ChunkRef* desc;   // [chunk * n_lods + lod]
+    int32_t grid[3];
+    int32_t mlog;           // log2(chunk_res)
+    int32_t n_lods;
+    float view_dist;
+};
+
+// Camera as the kernels consume it.
+struct CamDev {
+    float R[9];
+    float tan_half;
+    int32_t W, H;
+    int32_t O[3];           // origin * 2^kFix (exact)
+    float of[3];            // origin as float
+    float planes[4][4];     // view-pyramid side planes: n . (p - o) <= 0 inside (n, unused)
+    double sf;              // StreamingFactor for Eq. 1
+};
+
+// A view of a batch: which scene, which camera, where the pixels go.
+struct ViewDev {
+    SceneDev scene;
+    CamDev cam;
+    ChunkRef* frame;        // per-view selected chunk table [chunk]
+    uint4* hit;
+    float* t;
+    uint64_t pix_begin;     // first global pixel index of this view in the batch
+};
+
+}  // namespace aok
+
+// Kernel launchers (aok_kernels.cu), called by the runtime.
+extern "C" {
+int aokk_select(const aok::SceneDev* s, const aok::CamDev* c, aok::ChunkRef* frame, int8_t* lod_out,
+                uint8_t* vis_out, uint32_t* n_visible, void* stream);
+int aokk_cast(const aok::SceneDev* s, const aok::CamDev* c, const aok::ChunkRef* frame, uint4* hit, float* t,
+              uint32_t* counts, void* stream);
+int aokk_ray_dirs(const aok::CamDev* c, float* dirs, void* stream);
+// Batched: views[] on the device, n views, total pixels, queue counter (zeroed by the kernel chain).
+int aokk_select_batch(const aok::ViewDev* views_dev, uint32_t n_views, uint32_t max_chunks, void* stream);
+int aokk_cast_batch(const aok::ViewDev* views_dev, uint32_t n_views, uint64_t total_pixels,
+                    unsigned long long* queue, uint32_t ctas, uint32_t threads, uint32_t packet, void* stream);
+int aokk_sm_count(int device);
+}

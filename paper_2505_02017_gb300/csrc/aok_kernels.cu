@@ -1,0 +1,485 @@
+// CUDA kernels (sm_103a): per-frame chunk LOD selection and visibility, and
+// per-pixel primary-ray first-hit casting through the chunk grid and the
+// selected sparse voxel DAGs (Aokana Sec. 3.4-3.5).
+//
+// Exactness.  The ray is origin + t d with the origin on a 2^-12 grid and d
+// an FP32 vector.  Every ordering decision of the traversal (which face a
+// cell is left through, which child octant holds the entry point) compares
+// two plane-crossing parameters t_a = (P_a - o_a) / d_a.  The traversal works
+// in a frame mirrored so that every d_a >= 0, writes N_a = (P_a - o_a) 2^12 as
+// an int32 and |d_a| = m_a 2^E_a (24-bit mantissa), and decides
+// t_a < t_b  <=>  N_a m_b 2^(E_b - E_a) < N_b m_a  with 64-bit products and an
+// exact shift comparison.  No decision is approximated, so the hit voxel,
+// LOD, material and normal equal those of the exact real ray; only the
+// reported distance is rounded (FP32, relative error ~1e-7).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "aok_internal.h"
+
+using namespace aok;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// exact comparison of plane-crossing parameters
+// ---------------------------------------------------------------------------
+// N1 / (m1 2^E1) < N2 / (m2 2^E2), s = E2 - E1, m1, m2 > 0, |N| < 2^31, m < 2^24.
+__device__ __forceinline__ bool tlt(int32_t N1, int32_t m1, int32_t N2, int32_t m2, int32_t s) {
+    const long long P = (long long)N1 * m2;
+    const long long Q = (long long)N2 * m1;
+    if (s >= 0) {
+        // P 2^s < Q  <=>  P <= floor((Q - 1) / 2^s)
+        return P <= ((Q - 1) >> min(s, 63));
+    }
+    // P 2^s < Q  <=>  floor(P / 2^-s) < Q
+    return (P >> min(-s, 63)) < Q;
+}
+
+// |d| = m 2^E; a zero component becomes m = 1, E = -400 (crossings at +-infinity).
+__device__ __forceinline__ void decompose(float d, int32_t& m, int32_t& E) {
+    const uint32_t b = __float_as_uint(d) & 0x7FFFFFFFu;
+    const uint32_t ex = b >> 23, man = b & 0x7FFFFFu;
+    if (b == 0) { m = 1; E = -400; }
+    else if (ex == 0) { m = (int32_t)man; E = -149; }
+    else { m = (int32_t)(man | 0x800000u); E = (int32_t)ex - 150; }
+}
+
+// Ray direction of pixel (px, py): IEEE binary32, one rounding per operation.
+__device__ __forceinline__ void ray_dir(const CamDev& c, int px, int py, float d[3]) {
+    const float fW = __int2float_rn(c.W), fH = __int2float_rn(c.H);
+    const float a = __int2float_rn(2 * px + 1);
+    const float b = __fdiv_rn(a, fW);
+    const float cc = __fsub_rn(b, 1.0f);
+    const float e = __fmul_rn(cc, c.tan_half);
+    const float aspect = __fdiv_rn(fW, fH);
+    const float u = __fmul_rn(e, aspect);
+    const float a2 = __int2float_rn(2 * py + 1);
+    const float b2 = __fdiv_rn(a2, fH);
+    const float c2 = __fsub_rn(1.0f, b2);
+    const float v = __fmul_rn(c2, c.tan_half);
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        const float p = __fmul_rn(c.R[3 * i + 0], u);
+        const float q = __fmul_rn(c.R[3 * i + 1], v);
+        const float s = __fadd_rn(p, q);
+        d[i] = __fsub_rn(s, c.R[3 * i + 2]);
+    }
+}
+
+// Mirror a 4x4x4 mask (bit x + 4y + 16z) along the axes set in `mir`.
+__device__ __forceinline__ uint64_t mirror_leaf(uint64_t m, uint32_t mir) {
+    if (mir & 1u)
+        m = ((m & 0x1111111111111111ull) << 3) | ((m & 0x2222222222222222ull) << 1) |
+            ((m >> 1) & 0x2222222222222222ull) | ((m >> 3) & 0x1111111111111111ull);
+    if (mir & 2u)
+        m = ((m & 0x000F000F000F000Full) << 12) | ((m & 0x00F000F000F000F0ull) << 4) |
+            ((m >> 4) & 0x00F000F000F000F0ull) | ((m >> 12) & 0x000F000F000F000Full);
+    if (mir & 4u)
+        m = ((m & 0xFFFFull) << 48) | ((m & 0xFFFF0000ull) << 16) | ((m >> 16) & 0xFFFF0000ull) | (m >> 48);
+    return m;
+}
+
+// Eq. 1 for the octree block b at level n: LODError <= 0 (load), squared, FP64, fixed order.
+__device__ __forceinline__ bool lod_loads(int n, int bx, int by, int bz, int mlog, const float o[3], double sf) {
+    const double S = (double)(1ll << (mlog + n));
+    const int b[3] = {bx, by, bz};
+    double e2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const double c = __dadd_rn(__dmul_rn((double)b[a], S), __dmul_rn(0.5, S));
+        const double dd = __dsub_rn(c, (double)o[a]);
+        e2 = __dadd_rn(e2, __dmul_rn(dd, dd));
+    }
+    const double thr = __dmul_rn(S, sf);
+    return e2 >= __dmul_rn(thr, thr);
+}
+
+// ---------------------------------------------------------------------------
+// selection + visibility: one thread per chunk region
+// ---------------------------------------------------------------------------
+__global__ void select_kernel(SceneDev S, CamDev C, ChunkRef* __restrict__ frame, int8_t* __restrict__ lod_out,
+                              uint8_t* __restrict__ vis_out, uint32_t* __restrict__ n_visible) {
+    const int nch = S.grid[0] * S.grid[1] * S.grid[2];
+    const int chunk = blockIdx.x * blockDim.x + threadIdx.x;
+    if (chunk >= nch) return;
+    const int cx = chunk % S.grid[0], cy = (chunk / S.grid[0]) % S.grid[1], cz = chunk / (S.grid[0] * S.grid[1]);
+    int sel = 0;
+    for (int n = S.n_lods - 1; n >= 1; n--)
+        if (lod_loads(n, cx >> n, cy >> n, cz >> n, S.mlog, C.of, C.sf)) { sel = n; break; }
+    ChunkRef ref = S.desc[(size_t)chunk * S.n_lods + sel];
+    bool vis = ref.root != kNone;
+    if (vis) {
+        // AABB grown by one voxel: culling stays conservative under FP32 rounding
+        const int org[3] = {cx << S.mlog, cy << S.mlog, cz << S.mlog};
+        float lo[3], hi[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            lo[a] = (float)(org[a] + ref.aabb[a]) - 1.0f - C.of[a];
+            hi[a] = (float)(org[a] + ref.aabb[3 + a]) + 1.0f - C.of[a];
+        }
+#pragma unroll
+        for (int p = 0; p < 4; p++) {
+            const float* n = C.planes[p];
+            const float dmin = n[0] * (n[0] > 0 ? lo[0] : hi[0]) + n[1] * (n[1] > 0 ? lo[1] : hi[1]) +
+                               n[2] * (n[2] > 0 ? lo[2] : hi[2]);
+            if (dmin > 0.0f) vis = false;
+        }
+        if (S.view_dist > 0.0f) {
+            float d2 = 0.0f;
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                const float q = fminf(fmaxf(0.0f, lo[a]), hi[a]);
+                d2 += q * q;
+            }
+            if (d2 > S.view_dist * S.view_dist * 1.0001f + 4.0f) vis = false;
+        }
+    }
+    if (!vis) ref.root = kNone;
+    ref.lod = (uint32_t)sel;
+    frame[chunk] = ref;
+    if (lod_out) lod_out[chunk] = (int8_t)sel;
+    if (vis_out) vis_out[chunk] = vis ? 1 : 0;
+    if (vis && n_visible) atomicAdd(n_visible, 1u);
+}
+
+// ---------------------------------------------------------------------------
+// per-chunk DAG traversal in the chunk's mirrored local frame
+// ---------------------------------------------------------------------------
+struct RayState {
+    float d[3];
+    int32_t m[3], E[3];
+    uint32_t mir;
+};
+
+struct HitRec {
+    int32_t c[3];       // voxel index (mirrored, chunk-local, voxel units of the LOD)
+    int e;              // entry axis (3 = origin inside)
+    int32_t Ne;         // entry plane numerator
+    uint32_t mat;
+};
+
+struct Counters {
+    uint32_t v_int, v_leaf, rbytes;
+};
+
+// Returns true on a hit inside this chunk.  (e, Ne): entry plane into the chunk
+// (e = 3: the origin lies inside the chunk).  Oloc: mirrored local origin numerators.
+template <bool COUNT>
+__device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& ref, const RayState& r,
+                                            const int32_t Oloc[3], int e, int32_t Ne, HitRec& hit, Counters& cnt) {
+    const uint32_t* __restrict__ nodes = S.nodes;
+    const int R = S.mlog;
+    const int n = (int)ref.lod;
+    uint32_t sidx[kMaxLevels];
+    uint32_t smask[kMaxLevels];
+    int k = R;
+    int32_t c0 = 0, c1 = 0, c2 = 0;
+    int32_t me = 1, Ee = 0;
+    if (e < 3) { me = r.m[e]; Ee = r.E[e]; }
+    uint64_t lm = 0, lmu = 0;
+    bool occ = true;
+    for (;;) {
+        if (occ) {
+            if (k == n) {
+                hit.c[0] = c0; hit.c[1] = c1; hit.c[2] = c2;
+                hit.e = e;
+                hit.Ne = Ne;
+                // material through the depth-first index (Sec. 3.3)
+                const uint32_t mirv = r.mir;
+                const int32_t side = (1 << (R - n)) - 1;
+                const int32_t u0 = (mirv & 1u) ? side - c0 : c0;
+                const int32_t u1 = (mirv & 2u) ? side - c1 : c1;
+                const int32_t u2 = (mirv & 4u) ? side - c2 : c2;
+                uint32_t idx = 0;
+                for (int j = R; j >= n + 3; j--) {
+                    const uint32_t node = sidx[j], mk = smask[j];
+                    const int sh = j - 1 - n;
+                    const int oct = ((u0 >> sh) & 1) | (((u1 >> sh) & 1) << 1) | (((u2 >> sh) & 1) << 2);
+                    const int rk = __popc(mk & ((1u << oct) - 1u));
+                    const bool leafkids = (j - 1 == n + 2);
+                    for (int q = 0; q < rk; q++) {
+                        const uint32_t ch = nodes[node + 2 + q];
+                        idx += leafkids ? (uint32_t)__popcll(S.leaves[ch]) : nodes[ch + 1];
+                    }
+                    if (COUNT) cnt.rbytes += rk * (leafkids ? 8u : 4u);
+                }
+                const int bit = (u0 & 3) + 4 * (u1 & 3) + 16 * (u2 & 3);
+                idx += (uint32_t)__popcll(lmu & ((1ull << bit) - 1ull));
+                hit.mat = S.mats[ref.mat_base + idx];
+                if (COUNT) cnt.rbytes += 1;
+                return true;
+            }
+            if (k >= n + 2) {
+                uint32_t idx;
+                if (k == R) {
+                    idx = ref.root;
+                } else {
+                    const uint32_t oct = ((uint32_t)(c0 & 1) | ((uint32_t)(c1 & 1) << 1) | ((uint32_t)(c2 & 1) << 2)) ^ r.mir;
+                    idx = nodes[sidx[k + 1] + 2 + __popc(smask[k + 1] & ((1u << oct) - 1u))];
+                }
+                if (k >= n + 3) {
+                    sidx[k] = idx;
+                    smask[k] = nodes[idx] & 0xFFu;
+                    if (COUNT) cnt.v_int++;
+                } else {
+                    lmu = S.leaves[idx];
+                    lm = mirror_leaf(lmu, r.mir);
+                    if (COUNT) cnt.v_leaf++;
+                }
+            }
+            // child of cell (k, c) holding the entry point: compare t_entry with the mid planes
+            const int kk = k - 1;
+            const int32_t mid0 = ((2 * c0 + 1) << (kk + kFix)) - Oloc[0];
+            const int32_t mid1 = ((2 * c1 + 1) << (kk + kFix)) - Oloc[1];
+            const int32_t mid2 = ((2 * c2 + 1) << (kk + kFix)) - Oloc[2];
+            const int32_t b0 = (e != 0) && !tlt(Ne, me, mid0, r.m[0], r.E[0] - Ee);
+            const int32_t b1 = (e != 1) && !tlt(Ne, me, mid1, r.m[1], r.E[1] - Ee);
+            const int32_t b2 = (e != 2) && !tlt(Ne, me, mid2, r.m[2], r.E[2] - Ee);
+            c0 = 2 * c0 + b0;
+            c1 = 2 * c1 + b1;
+            c2 = 2 * c2 + b2;
+            k = kk;
+        } else {
+            // leave cell (k, c) through its nearest exit face
+            const int32_t N0 = ((c0 + 1) << (k + kFix)) - Oloc[0];
+            const int32_t N1 = ((c1 + 1) << (k + kFix)) - Oloc[1];
+            const int32_t N2 = ((c2 + 1) << (k + kFix)) - Oloc[2];
+            const bool xy = tlt(N0, r.m[0], N1, r.m[1], r.E[1] - r.E[0]);
+            const int32_t Na = xy ? N0 : N1, ma = xy ? r.m[0] : r.m[1], Ea = xy ? r.E[0] : r.E[1];
+            const bool az = tlt(Na, ma, N2, r.m[2], r.E[2] - Ea);
+            int ax;
+            if (az) { ax = xy ? 0 : 1; Ne = Na; me = ma; Ee = Ea; }
+            else { ax = 2; Ne = N2; me = r.m[2]; Ee = r.E[2]; }
+            e = ax;
+            int32_t cax;
+            if (ax == 0) cax = ++c0;
+            else if (ax == 1) cax = ++c1;
+            else cax = ++c2;
+            if ((cax << k) >= (1 << R)) return false;  // left the chunk
+            while (k < R && (cax & 1) == 0) {
+                c0 >>= 1; c1 >>= 1; c2 >>= 1;
+                cax >>= 1;
+                k++;
+            }
+        }
+        // occupancy of cell (k, c)
+        if (k >= n + 2) {
+            const uint32_t oct = ((uint32_t)(c0 & 1) | ((uint32_t)(c1 & 1) << 1) | ((uint32_t)(c2 & 1) << 2)) ^ r.mir;
+            occ = (smask[k + 1] >> oct) & 1u;
+        } else if (k == n + 1) {
+            occ = (lm & (0x330033ull << ((c0 & 1) * 2 + (c1 & 1) * 8 + (c2 & 1) * 32))) != 0ull;
+        } else {
+            occ = (lm >> ((c0 & 3) + 4 * (c1 & 3) + 16 * (c2 & 3))) & 1ull;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// one pixel: world-grid chunk march + per-chunk DAG traversal
+// ---------------------------------------------------------------------------
+template <bool COUNT>
+__device__ __forceinline__ void trace_pixel(const SceneDev& S, const CamDev& C, const ChunkRef* __restrict__ frame,
+                                            int px, int py, uint4* __restrict__ out_hit, float* __restrict__ out_t,
+                                            uint32_t* __restrict__ counts, size_t pix) {
+    RayState r;
+    ray_dir(C, px, py, r.d);
+    r.mir = 0;
+    int32_t Ow[3], Wfix[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        decompose(r.d[a], r.m[a], r.E[a]);
+        if (r.d[a] < 0.0f) r.mir |= 1u << a;
+        Wfix[a] = S.grid[a] << (S.mlog + kFix);
+        Ow[a] = ((r.mir >> a) & 1u) ? Wfix[a] - C.O[a] : C.O[a];
+    }
+    Counters cnt = {0, 0, 0};
+    HitRec hit;
+    bool found = false;
+    const int cs = S.mlog + kFix;  // chunk side as a shift of numerator units
+    int e = 3;
+    int32_t Ne = 0, me = 1, Ee = 0;
+    int32_t cc[3];
+    bool alive = true;
+    if (Ow[0] >= 0 && Ow[1] >= 0 && Ow[2] >= 0 && Ow[0] < Wfix[0] && Ow[1] < Wfix[1] && Ow[2] < Wfix[2]) {
+#pragma unroll
+        for (int a = 0; a < 3; a++) cc[a] = Ow[a] >> cs;
+    } else {
+        // enter the world box: latest entry plane vs earliest exit plane
+        e = -1;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            if (Ow[a] >= Wfix[a] || (r.d[a] == 0.0f && Ow[a] < 0)) alive = false;
+            if (Ow[a] < 0) {
+                const int32_t Na = -Ow[a];
+                if (e < 0 || tlt(Ne, me, Na, r.m[a], r.E[a] - Ee)) { e = a; Ne = Na; me = r.m[a]; Ee = r.E[a]; }
+            }
+        }
+        int32_t Nx = Wfix[0] - Ow[0], mx = r.m[0], Ex = r.E[0];
+#pragma unroll
+        for (int a = 1; a < 3; a++) {
+            const int32_t Na = Wfix[a] - Ow[a];
+            if (tlt(Na, r.m[a], Nx, mx, Ex - r.E[a])) { Nx = Na; mx = r.m[a]; Ex = r.E[a]; }
+        }
+        if (alive && e >= 0 && tlt(Ne, me, Nx, mx, Ex - Ee)) {
+            const float te_num = (float)Ne / fabsf(r.d[e]);
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                if (a == e) { cc[a] = 0; continue; }
+                const float pa = (float)Ow[a] + te_num * fabsf(r.d[a]);
+                int32_t cell = (int32_t)floorf(pa * (1.0f / (float)(1 << cs)));
+                cell = max(0, min(cell, S.grid[a] - 1));
+                // exact correction: cell*M <= x_a(t_entry) < (cell+1)*M
+                while (cell + 1 < S.grid[a] && !tlt(Ne, me, ((cell + 1) << cs) - Ow[a], r.m[a], r.E[a] - Ee)) cell++;
+                while (cell > 0 && tlt(Ne, me, (cell << cs) - Ow[a], r.m[a], r.E[a] - Ee)) cell--;
+                cc[a] = cell;
+            }
+        } else {
+            alive = false;
+        }
+    }
+    const float dn = sqrtf(__fadd_rn(__fadd_rn(__fmul_rn(r.d[0], r.d[0]), __fmul_rn(r.d[1], r.d[1])), __fmul_rn(r.d[2], r.d[2])));
+    float inv[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) inv[a] = 1.0f / r.d[a];
+    while (alive) {
+        int32_t u[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) u[a] = ((r.mir >> a) & 1u) ? S.grid[a] - 1 - cc[a] : cc[a];
+        const ChunkRef ref = frame[(size_t)u[0] + (size_t)S.grid[0] * ((size_t)u[1] + (size_t)S.grid[1] * u[2])];
+        if (S.view_dist > 0.0f && e < 3) {
+            const float tent = (float)Ne / (4096.0f * fabsf(r.d[e]));
+            if (tent * dn > S.view_dist * 1.00001f + 1.0f) break;
+        }
+        if (ref.root != kNone) {
+            // skip chunks whose solid-voxel AABB (grown by 1/16 voxel) the ray misses
+            float tn = 0.0f, tf = 3.0e38f;
+            bool pass = true;
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                const float lo = (float)((u[a] << S.mlog) + ref.aabb[a]) - 0.0625f;
+                const float hi = (float)((u[a] << S.mlog) + ref.aabb[3 + a]) + 0.0625f;
+                if (r.d[a] == 0.0f) {
+                    if (C.of[a] < lo || C.of[a] > hi) pass = false;
+                } else {
+                    float t1 = (lo - C.of[a]) * inv[a], t2 = (hi - C.of[a]) * inv[a];
+                    tn = fmaxf(tn, fminf(t1, t2));
+                    tf = fminf(tf, fmaxf(t1, t2));
+                }
+            }
+            if (pass && tn <= tf) {
+                int32_t Oloc[3];
+#pragma unroll
+                for (int a = 0; a < 3; a++) Oloc[a] = Ow[a] - (cc[a] << cs);
+                if (trace_chunk<COUNT>(S, ref, r, Oloc, e, Ne, hit, cnt)) {
+                    found = true;
+                    // un-mirror the voxel index to world LOD-0 units
+                    const int n = (int)ref.lod;
+                    const int32_t side = (1 << (S.mlog - n)) - 1;
+                    int32_t wxyz[3];
+#pragma unroll
+                    for (int a = 0; a < 3; a++) {
+                        const int32_t uv = ((r.mir >> a) & 1u) ? side - hit.c[a] : hit.c[a];
+                        wxyz[a] = (u[a] << S.mlog) + (uv << n);
+                    }
+                    float dist = 0.0f;
+                    if (hit.e < 3) dist = __fdiv_rn((float)hit.Ne * (1.0f / 4096.0f), fabsf(r.d[hit.e])) * dn;
+                    if (S.view_dist > 0.0f) {
+                        double dd = 0.0;
+                        if (hit.e < 3) {
+                            const double d0 = r.d[0], d1 = r.d[1], d2 = r.d[2];
+                            dd = (double)hit.Ne / (4096.0 * fabs((double)r.d[hit.e])) * sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+                        }
+                        if (dd > (double)S.view_dist) { found = false; break; }
+                    }
+                    const uint32_t normal = hit.e == 3 ? 7u : (uint32_t)(2 * hit.e) + ((r.mir >> hit.e) & 1u);
+                    out_hit[pix] = make_uint4((uint32_t)wxyz[0], (uint32_t)wxyz[1], (uint32_t)wxyz[2],
+                                              (uint32_t)n | (hit.mat << 8) | (normal << 16) | (1u << 19));
+                    out_t[pix] = dist;
+                    break;
+                }
+            }
+        }
+        // next chunk cell
+        const int32_t N0 = ((cc[0] + 1) << cs) - Ow[0];
+        const int32_t N1 = ((cc[1] + 1) << cs) - Ow[1];
+        const int32_t N2 = ((cc[2] + 1) << cs) - Ow[2];
+        const bool xy = tlt(N0, r.m[0], N1, r.m[1], r.E[1] - r.E[0]);
+        const int32_t Na = xy ? N0 : N1, ma = xy ? r.m[0] : r.m[1], Ea = xy ? r.E[0] : r.E[1];
+        const bool az = tlt(Na, ma, N2, r.m[2], r.E[2] - Ea);
+        int ax;
+        if (az) { ax = xy ? 0 : 1; Ne = Na; me = ma; Ee = Ea; }
+        else { ax = 2; Ne = N2; me = r.m[2]; Ee = r.E[2]; }
+        e = ax;
+        if (++cc[ax] >= S.grid[ax]) break;
+    }
+    if (!found) {
+        out_hit[pix] = make_uint4(0u, 0u, 0u, 0xFFu | (7u << 16));
+        out_t[pix] = __int_as_float(0x7F800000);
+    }
+    if (COUNT) {
+        counts[3 * pix + 0] = cnt.v_int;
+        counts[3 * pix + 1] = cnt.v_leaf;
+        counts[3 * pix + 2] = cnt.rbytes;
+    }
+}
+
+// 16 x 8 pixel tiles, warps of 8 x 4 pixels
+template <bool COUNT>
+__global__ void __launch_bounds__(128) cast_kernel(SceneDev S, CamDev C, const ChunkRef* __restrict__ frame,
+                                                   uint4* __restrict__ out_hit, float* __restrict__ out_t,
+                                                   uint32_t* __restrict__ counts) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int px = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
+    const int py = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
+    if (px >= C.W || py >= C.H) return;
+    trace_pixel<COUNT>(S, C, frame, px, py, out_hit, out_t, counts, (size_t)py * C.W + px);
+}
+
+__global__ void ray_dirs_kernel(CamDev C, float* __restrict__ dirs) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= C.W * C.H) return;
+    float d[3];
+    ray_dir(C, i % C.W, i / C.W, d);
+    dirs[3 * i] = d[0];
+    dirs[3 * i + 1] = d[1];
+    dirs[3 * i + 2] = d[2];
+}
+
+int status_of(cudaError_t e) { return e == cudaSuccess ? AOK_OK : AOK_E_CUDA; }
+
+}  // namespace
+
+extern "C" {
+
+int aokk_select(const SceneDev* s, const CamDev* c, ChunkRef* frame, int8_t* lod_out, uint8_t* vis_out,
+                uint32_t* n_visible, void* stream) {
+    const int nch = s->grid[0] * s->grid[1] * s->grid[2];
+    select_kernel<<<(nch + 127) / 128, 128, 0, (cudaStream_t)stream>>>(*s, *c, frame, lod_out, vis_out, n_visible);
+    return status_of(cudaGetLastError());
+}
+
+int aokk_cast(const SceneDev* s, const CamDev* c, const ChunkRef* frame, uint4* hit, float* t, uint32_t* counts,
+              void* stream) {
+    dim3 grid((c->W + 15) / 16, (c->H + 7) / 8);
+    if (counts)
+        cast_kernel<true><<<grid, 128, 0, (cudaStream_t)stream>>>(*s, *c, frame, hit, t, counts);
+    else
+        cast_kernel<false><<<grid, 128, 0, (cudaStream_t)stream>>>(*s, *c, frame, hit, t, nullptr);
+    return status_of(cudaGetLastError());
+}
+
+int aokk_ray_dirs(const CamDev* c, float* dirs, void* stream) {
+    const int n = c->W * c->H;
+    ray_dirs_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(*c, dirs);
+    return status_of(cudaGetLastError());
+}
+
+int aokk_sm_count(int device) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device);
+    return n;
+}
+
+}  // extern "C"

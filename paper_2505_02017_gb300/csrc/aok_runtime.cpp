@@ -1,0 +1,598 @@
+// Host runtime of the C ABI (include/aok.h): context and HBM budget, scene
+// pools, validating chunk upload with pointer rebasing, camera setup, and the
+// per-frame select / render entry points.  Batched rendering and the serving
+// loop live in aok_serve.cpp.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "aok_runtime.h"
+
+using namespace aok;
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+namespace aok {
+
+int cuda_status(aok_ctx* ctx, cudaError_t e) {
+    if (e == cudaSuccess) return AOK_OK;
+    ctx->last_cuda = e;
+    return AOK_E_CUDA;
+}
+
+int charge(aok_ctx* ctx, size_t bytes) {
+    std::lock_guard<std::mutex> g(ctx->mem_mu);
+    if (ctx->used + bytes > ctx->budget) return AOK_E_OOM;
+    ctx->used += bytes;
+    return AOK_OK;
+}
+
+void uncharge(aok_ctx* ctx, size_t bytes) {
+    std::lock_guard<std::mutex> g(ctx->mem_mu);
+    ctx->used -= std::min(ctx->used, bytes);
+}
+
+int dev_alloc(aok_ctx* ctx, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return AOK_OK;
+    int st = charge(ctx, bytes);
+    if (st) return st;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        uncharge(ctx, bytes);
+        cudaGetLastError();
+        *p = nullptr;
+        return e == cudaErrorMemoryAllocation ? AOK_E_OOM : cuda_status(ctx, e);
+    }
+    return AOK_OK;
+}
+
+void dev_free(aok_ctx* ctx, void* p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    uncharge(ctx, bytes);
+}
+
+Scene* find_scene(aok_ctx* ctx, uint32_t id) {
+    std::lock_guard<std::mutex> g(ctx->scene_mu);
+    auto it = ctx->scenes.find(id);
+    return it == ctx->scenes.end() ? nullptr : it->second;
+}
+
+static int ilog2i(int v) {
+    int l = 0;
+    while ((1 << l) < v) l++;
+    return l;
+}
+
+// First-fit range allocator over a pool of `cap` units.
+uint64_t Pool::alloc(uint64_t n) {
+    if (n == 0) return 0;
+    for (size_t i = 0; i < free_list.size(); i++) {
+        if (free_list[i].second >= n) {
+            uint64_t off = free_list[i].first;
+            free_list[i].first += n;
+            free_list[i].second -= n;
+            if (!free_list[i].second) free_list.erase(free_list.begin() + (long)i);
+            return off;
+        }
+    }
+    if (used + n > cap) return kNoRange;
+    uint64_t off = used;
+    used += n;
+    return off;
+}
+
+void Pool::release(uint64_t off, uint64_t n) {
+    if (n) free_list.emplace_back(off, n);
+}
+
+int make_cam(aok_ctx* ctx, const Scene* sc, const aok_camera* cam, double tau, CamDev* out) {
+    (void)ctx;
+    if (!cam || cam->width <= 0 || cam->height <= 0 || (int64_t)cam->width * cam->height > (1ll << 31)) return AOK_E_INVALID;
+    if (!(tau > 0.0) || !std::isfinite(tau)) return AOK_E_INVALID;
+    if (!(cam->tan_half_fovy > 0.0f) || !std::isfinite(cam->tan_half_fovy)) return AOK_E_INVALID;
+    std::memset(out, 0, sizeof(*out));
+    for (int i = 0; i < 9; i++) {
+        if (!std::isfinite(cam->R[i])) return AOK_E_INVALID;
+        out->R[i] = cam->R[i];
+    }
+    out->tan_half = cam->tan_half_fovy;
+    out->W = cam->width;
+    out->H = cam->height;
+    for (int a = 0; a < 3; a++) {
+        const double o = cam->origin[a];
+        if (!std::isfinite(o) || std::fabs(o) >= 131072.0) return AOK_E_INVALID;
+        const double f = o * (double)(1 << kFix);
+        if (f != std::floor(f)) return AOK_E_INVALID;  // not on the 2^-12 grid
+        out->O[a] = (int32_t)f;
+        out->of[a] = cam->origin[a];
+    }
+    // view-pyramid side planes (conservative): every pixel direction
+    // d = u c0 + v c1 - c2 has |u| < U = t W/H and |v| < V = t
+    double c[3][3];
+    for (int j = 0; j < 3; j++)
+        for (int i = 0; i < 3; i++) c[j][i] = cam->R[3 * i + j];
+    const double t = cam->tan_half_fovy, asp = (double)cam->width / (double)cam->height;
+    const double U = t * asp * (1.0 + 1e-5), V = t * (1.0 + 1e-5);
+    auto cross = [](const double* a, const double* b, double* r) {
+        r[0] = a[1] * b[2] - a[2] * b[1];
+        r[1] = a[2] * b[0] - a[0] * b[2];
+        r[2] = a[0] * b[1] - a[1] * b[0];
+    };
+    for (int p = 0; p < 4; p++) {
+        // p = 0: u = +U, 1: u = -U, 2: v = +V, 3: v = -V
+        const int along = p < 2 ? 0 : 1, other = p < 2 ? 1 : 0;
+        const double s = (p % 2 == 0) ? 1.0 : -1.0;
+        const double lim = p < 2 ? U : V;
+        double edge[3], n[3];
+        for (int i = 0; i < 3; i++) edge[i] = s * lim * c[along][i] - c[2][i];
+        cross(c[other], edge, n);
+        double dot = n[0] * c[along][0] + n[1] * c[along][1] + n[2] * c[along][2];
+        if (s * dot < 0) for (int i = 0; i < 3; i++) n[i] = -n[i];
+        double len = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        for (int i = 0; i < 3; i++) out->planes[p][i] = len > 0 ? (float)(n[i] / len) : 0.0f;
+        out->planes[p][3] = 0.0f;
+    }
+    // StreamingFactor from the pixel threshold (fixed FP64 operation order)
+    const double fpx = (double)cam->height / (2.0 * (double)cam->tan_half_fovy);
+    out->sf = fpx / (tau * (double)sc->desc.chunk_res);
+    return AOK_OK;
+}
+
+SceneDev scene_dev(const Scene* sc) {
+    SceneDev s;
+    s.nodes = sc->d_nodes;
+    s.leaves = sc->d_leaves;
+    s.mats = sc->d_mats;
+    s.desc = sc->d_desc;
+    for (int a = 0; a < 3; a++) s.grid[a] = sc->desc.grid[a];
+    s.mlog = sc->mlog;
+    s.n_lods = sc->desc.n_lods;
+    s.view_dist = sc->desc.view_dist;
+    return s;
+}
+
+}  // namespace aok
+
+// ---------------------------------------------------------------------------
+// blob validation + rebasing (host)
+// ---------------------------------------------------------------------------
+static int validate_blob(const aok_chunk_blob* b, int res, int M, uint32_t node_base, uint32_t leaf_base,
+                         uint32_t* out) {
+    const uint64_t nw = b->n_node_words;
+    if (nw == 0) return (b->n_leaves == 0 && b->n_mats == 0) ? AOK_OK : AOK_E_CORRUPT;
+    if (!b->nodes || b->root >= nw || (b->n_leaves && !b->leaves) || (b->n_mats && !b->mats)) return AOK_E_CORRUPT;
+    if (nw > 0xFFFFFFFFull || b->n_leaves > 0xFFFFFFFFull) return AOK_E_CORRUPT;
+    const int n_int = ilog2i(res) - 2;
+    std::memcpy(out, b->nodes, nw * sizeof(uint32_t));
+    std::vector<int8_t> depth(nw, -1);
+    std::vector<std::pair<uint32_t, int>> st;
+    st.emplace_back(b->root, 0);
+    while (!st.empty()) {
+        auto [node, d] = st.back();
+        st.pop_back();
+        if (depth[node] >= 0) {
+            if (depth[node] != d) return AOK_E_CORRUPT;
+            continue;
+        }
+        depth[node] = (int8_t)d;
+        if ((uint64_t)node + 2 > nw) return AOK_E_CORRUPT;
+        const uint32_t hdr = b->nodes[node];
+        if ((hdr >> 8) != 0 || (hdr & 0xFFu) == 0) return AOK_E_CORRUPT;
+        const int k = __builtin_popcount(hdr);
+        if ((uint64_t)node + 2 + k > nw) return AOK_E_CORRUPT;
+        const bool leafkids = d == n_int - 1;
+        uint64_t sum = 0;
+        for (int i = 0; i < k; i++) {
+            const uint32_t ch = b->nodes[node + 2 + i];
+            if (leafkids) {
+                if (ch >= b->n_leaves || b->leaves[ch] == 0) return AOK_E_CORRUPT;
+                sum += (uint64_t)__builtin_popcountll(b->leaves[ch]);
+                out[node + 2 + i] = ch + leaf_base;
+            } else {
+                if ((uint64_t)ch + 2 > nw) return AOK_E_CORRUPT;
+                sum += b->nodes[ch + 1];
+                st.emplace_back(ch, d + 1);
+                out[node + 2 + i] = ch + node_base;
+            }
+        }
+        if (sum != b->nodes[node + 1]) return AOK_E_CORRUPT;
+    }
+    if ((uint64_t)b->nodes[b->root + 1] != b->n_mats) return AOK_E_CORRUPT;
+    for (int a = 0; a < 3; a++)
+        if (b->aabb_lo[a] < 0 || b->aabb_hi[a] > M || b->aabb_lo[a] >= b->aabb_hi[a]) return AOK_E_CORRUPT;
+    return AOK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* aok_status_str(int s) {
+    switch (s) {
+        case AOK_OK: return "ok";
+        case AOK_PENDING: return "pending";
+        case AOK_E_INVALID: return "invalid argument";
+        case AOK_E_OOM: return "out of device memory budget";
+        case AOK_E_NOT_RESIDENT: return "not resident";
+        case AOK_E_TIMEOUT: return "timeout";
+        case AOK_E_CUDA: return "CUDA error";
+        case AOK_E_BUSY: return "busy";
+        case AOK_E_CORRUPT: return "corrupt chunk blob";
+        default: return "unknown status";
+    }
+}
+
+int aok_create(aok_ctx** out, int device, size_t budget) {
+    if (!out) return AOK_E_INVALID;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return AOK_E_INVALID;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return AOK_E_CUDA;
+    aok_ctx* ctx = new (std::nothrow) aok_ctx();
+    if (!ctx) return AOK_E_OOM;
+    ctx->device = device;
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    ctx->budget = budget ? budget : (size_t)((double)fr * 0.9);
+    if (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMallocHost(&ctx->pinned_word, sizeof(uint32_t)) != cudaSuccess) {
+        delete ctx;
+        return AOK_E_CUDA;
+    }
+    if (dev_alloc(ctx, (void**)&ctx->d_counter, sizeof(uint32_t) * 16) != AOK_OK) {
+        delete ctx;
+        return AOK_E_CUDA;
+    }
+    ctx->sm_count = aokk_sm_count(device);
+    *out = ctx;
+    return AOK_OK;
+}
+
+void aok_destroy(aok_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    aok_serve_stop(ctx);
+    cudaDeviceSynchronize();
+    std::vector<uint32_t> ids;
+    for (auto& kv : ctx->scenes) ids.push_back(kv.first);
+    for (uint32_t id : ids) aok_scene_destroy(ctx, id);
+    batch_release(ctx);
+    dev_free(ctx, ctx->host_hit_dev, ctx->host_frame_px * 16);
+    dev_free(ctx, ctx->host_t_dev, ctx->host_frame_px * 4);
+    dev_free(ctx, ctx->d_counter, sizeof(uint32_t) * 16);
+    if (ctx->staging) cudaFreeHost(ctx->staging);
+    if (ctx->pinned_word) cudaFreeHost(ctx->pinned_word);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    delete ctx;
+}
+
+int aok_memory(aok_ctx* ctx, size_t* used, size_t* budget) {
+    if (!ctx) return AOK_E_INVALID;
+    std::lock_guard<std::mutex> g(ctx->mem_mu);
+    if (used) *used = ctx->used;
+    if (budget) *budget = ctx->budget;
+    return AOK_OK;
+}
+
+int aok_scene_create(aok_ctx* ctx, const aok_scene_desc* d, uint32_t* scene_id) {
+    if (!ctx || !d || !scene_id) return AOK_E_INVALID;
+    const int M = d->chunk_res;
+    if (M < 8 || M > 512 || (M & (M - 1)) || d->n_lods < 1 || (M >> (d->n_lods - 1)) < 8) return AOK_E_INVALID;
+    for (int a = 0; a < 3; a++)
+        if (d->grid[a] < 1 || (int64_t)d->grid[a] * M > 131072) return AOK_E_INVALID;
+    if (d->node_words > 0xFFFFFFFFull || d->leaf_count > 0xFFFFFFFFull || !(d->view_dist >= 0.0f)) return AOK_E_INVALID;
+    cudaSetDevice(ctx->device);
+    Scene* sc = new Scene();
+    sc->desc = *d;
+    sc->mlog = ilog2i(M);
+    sc->n_chunks = (int64_t)d->grid[0] * d->grid[1] * d->grid[2];
+    sc->nodes.cap = std::max<uint64_t>(d->node_words, 1);
+    sc->leaves.cap = std::max<uint64_t>(d->leaf_count, 1);
+    sc->mats.cap = std::max<uint64_t>(d->mat_bytes, 1);
+    const size_t ndesc = (size_t)sc->n_chunks * d->n_lods;
+    int st = dev_alloc(ctx, (void**)&sc->d_nodes, sc->nodes.cap * 4);
+    if (!st) st = dev_alloc(ctx, (void**)&sc->d_leaves, sc->leaves.cap * 8);
+    if (!st) st = dev_alloc(ctx, (void**)&sc->d_mats, sc->mats.cap);
+    if (!st) st = dev_alloc(ctx, (void**)&sc->d_desc, ndesc * sizeof(ChunkRef));
+    if (!st) st = dev_alloc(ctx, (void**)&sc->d_frame, (size_t)sc->n_chunks * sizeof(ChunkRef));
+    if (st) {
+        dev_free(ctx, sc->d_nodes, sc->nodes.cap * 4);
+        dev_free(ctx, sc->d_leaves, sc->leaves.cap * 8);
+        dev_free(ctx, sc->d_mats, sc->mats.cap);
+        dev_free(ctx, sc->d_desc, ndesc * sizeof(ChunkRef));
+        delete sc;
+        return st;
+    }
+    ChunkRef empty;
+    std::memset(&empty, 0, sizeof(empty));
+    empty.root = kNone;
+    sc->h_desc.assign(ndesc, empty);
+    sc->alloc.assign(ndesc, ChunkAlloc());
+    for (size_t i = 0; i < ndesc; i++) sc->h_desc[i].lod = (uint32_t)(i % d->n_lods);
+    cudaError_t e = cudaMemcpy(sc->d_desc, sc->h_desc.data(), ndesc * sizeof(ChunkRef), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        int r = cuda_status(ctx, e);
+        delete sc;
+        return r;
+    }
+    std::lock_guard<std::mutex> g(ctx->scene_mu);
+    uint32_t id = ++ctx->next_scene;
+    ctx->scenes[id] = sc;
+    *scene_id = id;
+    return AOK_OK;
+}
+
+int aok_scene_destroy(aok_ctx* ctx, uint32_t id) {
+    if (!ctx) return AOK_E_INVALID;
+    Scene* sc;
+    {
+        std::lock_guard<std::mutex> g(ctx->scene_mu);
+        auto it = ctx->scenes.find(id);
+        if (it == ctx->scenes.end()) return AOK_E_NOT_RESIDENT;
+        sc = it->second;
+        ctx->scenes.erase(it);
+    }
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    const size_t ndesc = (size_t)sc->n_chunks * sc->desc.n_lods;
+    dev_free(ctx, sc->d_nodes, sc->nodes.cap * 4);
+    dev_free(ctx, sc->d_leaves, sc->leaves.cap * 8);
+    dev_free(ctx, sc->d_mats, sc->mats.cap);
+    dev_free(ctx, sc->d_desc, ndesc * sizeof(ChunkRef));
+    dev_free(ctx, sc->d_frame, (size_t)sc->n_chunks * sizeof(ChunkRef));
+    delete sc;
+    return AOK_OK;
+}
+
+static int chunk_index(const Scene* sc, int32_t cx, int32_t cy, int32_t cz, uint32_t lod, int64_t* out) {
+    if (cx < 0 || cy < 0 || cz < 0 || cx >= sc->desc.grid[0] || cy >= sc->desc.grid[1] || cz >= sc->desc.grid[2] ||
+        lod >= (uint32_t)sc->desc.n_lods)
+        return AOK_E_INVALID;
+    *out = ((int64_t)cx + (int64_t)sc->desc.grid[0] * ((int64_t)cy + (int64_t)sc->desc.grid[1] * cz)) * sc->desc.n_lods + lod;
+    return AOK_OK;
+}
+
+static void free_alloc(Scene* sc, ChunkAlloc& a) {
+    sc->nodes.release(a.node_off, a.node_n);
+    sc->leaves.release(a.leaf_off, a.leaf_n);
+    sc->mats.release(a.mat_off, a.mat_n);
+    a = ChunkAlloc();
+}
+
+int aok_scene_upload_chunk(aok_ctx* ctx, uint32_t scene, int32_t cx, int32_t cy, int32_t cz, uint32_t lod,
+                           const aok_chunk_blob* blob) {
+    if (!ctx || !blob) return AOK_E_INVALID;
+    Scene* sc = find_scene(ctx, scene);
+    if (!sc) return AOK_E_NOT_RESIDENT;
+    int64_t di;
+    int st = chunk_index(sc, cx, cy, cz, lod, &di);
+    if (st) return st;
+    cudaSetDevice(ctx->device);
+    std::lock_guard<std::mutex> g(sc->mu);
+    const int M = sc->desc.chunk_res, res = M >> lod;
+    const uint64_t nw = blob->n_node_words;
+    // staging: rebased node words + leaves + mats, 16-byte aligned segments
+    const size_t nb = (nw * 4 + 15) & ~(size_t)15, lb = (blob->n_leaves * 8 + 15) & ~(size_t)15;
+    const size_t need = nb + lb + blob->n_mats + 16;
+    if (need > ctx->staging_cap) {
+        if (ctx->staging) cudaFreeHost(ctx->staging);
+        ctx->staging = nullptr;
+        ctx->staging_cap = 0;
+        size_t cap = std::max<size_t>(need, 64u << 20);
+        if (cudaMallocHost(&ctx->staging, cap) != cudaSuccess) {
+            cudaGetLastError();
+            return AOK_E_OOM;
+        }
+        ctx->staging_cap = cap;
+    }
+    // free the previous upload of this (chunk, lod) once the pools are idle
+    ChunkAlloc& old = sc->alloc[di];
+    if (old.node_n || old.leaf_n || old.mat_n) {
+        cudaDeviceSynchronize();
+        free_alloc(sc, old);
+        sc->h_desc[di].root = kNone;
+    }
+    ChunkAlloc a;
+    if (nw) {
+        a.node_off = sc->nodes.alloc(nw);
+        a.leaf_off = sc->leaves.alloc(blob->n_leaves);
+        a.mat_off = sc->mats.alloc(blob->n_mats);
+        a.node_n = nw;
+        a.leaf_n = blob->n_leaves;
+        a.mat_n = blob->n_mats;
+        if (a.node_off == kNoRange || a.leaf_off == kNoRange || a.mat_off == kNoRange ||
+            a.node_off + nw > 0xFFFFFFFFull || a.leaf_off + blob->n_leaves > 0xFFFFFFFFull) {
+            if (a.node_off != kNoRange) sc->nodes.release(a.node_off, nw);
+            if (a.leaf_off != kNoRange) sc->leaves.release(a.leaf_off, blob->n_leaves);
+            if (a.mat_off != kNoRange) sc->mats.release(a.mat_off, blob->n_mats);
+            return AOK_E_OOM;
+        }
+    }
+    uint8_t* stg = (uint8_t*)ctx->staging;
+    st = validate_blob(blob, res, M, (uint32_t)a.node_off, (uint32_t)a.leaf_off, (uint32_t*)stg);
+    if (st) {
+        free_alloc(sc, a);
+        return st;
+    }
+    ChunkRef ref;
+    std::memset(&ref, 0, sizeof(ref));
+    ref.root = kNone;
+    ref.lod = lod;
+    if (nw) {
+        std::memcpy(stg + nb, blob->leaves, blob->n_leaves * 8);
+        std::memcpy(stg + nb + lb, blob->mats, blob->n_mats);
+        cudaError_t e = cudaMemcpyAsync(sc->d_nodes + a.node_off, stg, nw * 4, cudaMemcpyHostToDevice, ctx->copy_stream);
+        if (e == cudaSuccess && blob->n_leaves)
+            e = cudaMemcpyAsync(sc->d_leaves + a.leaf_off, stg + nb, blob->n_leaves * 8, cudaMemcpyHostToDevice,
+                                ctx->copy_stream);
+        if (e == cudaSuccess && blob->n_mats)
+            e = cudaMemcpyAsync(sc->d_mats + a.mat_off, stg + nb + lb, blob->n_mats, cudaMemcpyHostToDevice,
+                                ctx->copy_stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->copy_stream);
+        if (e != cudaSuccess) {
+            free_alloc(sc, a);
+            return cuda_status(ctx, e);
+        }
+        ref.root = (uint32_t)a.node_off + blob->root;
+        ref.mat_base = a.mat_off;
+        for (int i = 0; i < 3; i++) {
+            ref.aabb[i] = (uint16_t)blob->aabb_lo[i];
+            ref.aabb[3 + i] = (uint16_t)blob->aabb_hi[i];
+        }
+    }
+    sc->alloc[di] = a;
+    sc->h_desc[di] = ref;
+    cudaError_t e = cudaMemcpy(sc->d_desc + di, &ref, sizeof(ref), cudaMemcpyHostToDevice);
+    return cuda_status(ctx, e);
+}
+
+int aok_validate_chunk(const aok_chunk_blob* blob, int32_t M, uint32_t lod) {
+    if (!blob || M < 8 || M > 512 || (M & (M - 1)) || lod > 6 || (M >> lod) < 8) return AOK_E_INVALID;
+    std::vector<uint32_t> tmp(std::max<uint64_t>(blob->n_node_words, 1));
+    if (blob->n_node_words > (1ull << 32)) return AOK_E_CORRUPT;
+    return validate_blob(blob, M >> lod, M, 0, 0, tmp.data());
+}
+
+int aok_scene_evict_chunk(aok_ctx* ctx, uint32_t scene, int32_t cx, int32_t cy, int32_t cz, uint32_t lod) {
+    if (!ctx) return AOK_E_INVALID;
+    Scene* sc = find_scene(ctx, scene);
+    if (!sc) return AOK_E_NOT_RESIDENT;
+    int64_t di;
+    int st = chunk_index(sc, cx, cy, cz, lod, &di);
+    if (st) return st;
+    cudaSetDevice(ctx->device);
+    std::lock_guard<std::mutex> g(sc->mu);
+    ChunkRef ref;
+    std::memset(&ref, 0, sizeof(ref));
+    ref.root = kNone;
+    ref.lod = lod;
+    cudaDeviceSynchronize();
+    free_alloc(sc, sc->alloc[di]);
+    sc->h_desc[di] = ref;
+    return cuda_status(ctx, cudaMemcpy(sc->d_desc + di, &ref, sizeof(ref), cudaMemcpyHostToDevice));
+}
+
+int aok_select_chunks(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double tau, int8_t* lod_out,
+                      uint8_t* vis_out, uint32_t* n_visible_out, void* stream) {
+    if (!ctx) return AOK_E_INVALID;
+    Scene* sc = find_scene(ctx, scene);
+    if (!sc) return AOK_E_NOT_RESIDENT;
+    CamDev cd;
+    int st = make_cam(ctx, sc, cam, tau, &cd);
+    if (st) return st;
+    cudaSetDevice(ctx->device);
+    SceneDev sd = scene_dev(sc);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n_visible_out) {
+        st = cuda_status(ctx, cudaMemsetAsync(ctx->d_counter, 0, sizeof(uint32_t), s));
+        if (st) return st;
+    }
+    st = aokk_select(&sd, &cd, sc->d_frame, lod_out, vis_out, n_visible_out ? ctx->d_counter : nullptr, stream);
+    if (st) return cuda_status(ctx, cudaGetLastError());
+    if (n_visible_out) {
+        cudaError_t e = cudaMemcpyAsync(ctx->pinned_word, ctx->d_counter, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_status(ctx, e);
+        *n_visible_out = *ctx->pinned_word;
+    }
+    return AOK_OK;
+}
+
+static int render_impl(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double tau, const aok_frame* frame,
+                       uint32_t* counts, void* stream) {
+    if (!ctx || !frame || !frame->hit || !frame->t) return AOK_E_INVALID;
+    if (((uintptr_t)frame->hit & 15) || ((uintptr_t)frame->t & 3) || ((uintptr_t)counts & 3)) return AOK_E_INVALID;
+    Scene* sc = find_scene(ctx, scene);
+    if (!sc) return AOK_E_NOT_RESIDENT;
+    CamDev cd;
+    int st = make_cam(ctx, sc, cam, tau, &cd);
+    if (st) return st;
+    cudaSetDevice(ctx->device);
+    SceneDev sd = scene_dev(sc);
+    st = aokk_select(&sd, &cd, sc->d_frame, nullptr, nullptr, nullptr, stream);
+    if (!st) st = aokk_cast(&sd, &cd, sc->d_frame, (uint4*)frame->hit, frame->t, counts, stream);
+    if (st) return cuda_status(ctx, cudaGetLastError());
+    return AOK_OK;
+}
+
+int aok_render(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double tau, const aok_frame* frame, void* stream) {
+    return render_impl(ctx, scene, cam, tau, frame, nullptr, stream);
+}
+
+int aok_render_counted(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double tau, const aok_frame* frame,
+                       uint32_t* counts, void* stream) {
+    if (!counts) return AOK_E_INVALID;
+    return render_impl(ctx, scene, cam, tau, frame, counts, stream);
+}
+
+int aok_cast_selected(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, const aok_frame* frame, void* stream) {
+    if (!ctx || !frame || !frame->hit || !frame->t) return AOK_E_INVALID;
+    if (((uintptr_t)frame->hit & 15) || ((uintptr_t)frame->t & 3)) return AOK_E_INVALID;
+    Scene* sc = find_scene(ctx, scene);
+    if (!sc) return AOK_E_NOT_RESIDENT;
+    CamDev cd;
+    int st = make_cam(ctx, sc, cam, 1.0, &cd);
+    if (st) return st;
+    cudaSetDevice(ctx->device);
+    SceneDev sd = scene_dev(sc);
+    st = aokk_cast(&sd, &cd, sc->d_frame, (uint4*)frame->hit, frame->t, nullptr, stream);
+    return st ? cuda_status(ctx, cudaGetLastError()) : AOK_OK;
+}
+
+int aok_render_host(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double tau, void* hit_host, float* t_host,
+                    void* stream) {
+    if (!ctx || !cam || !hit_host || !t_host || cam->width <= 0 || cam->height <= 0) return AOK_E_INVALID;
+    const size_t px = (size_t)cam->width * cam->height;
+    cudaSetDevice(ctx->device);
+    if (px > ctx->host_frame_px) {
+        cudaDeviceSynchronize();
+        dev_free(ctx, ctx->host_hit_dev, ctx->host_frame_px * 16);
+        dev_free(ctx, ctx->host_t_dev, ctx->host_frame_px * 4);
+        ctx->host_hit_dev = nullptr;
+        ctx->host_t_dev = nullptr;
+        ctx->host_frame_px = 0;
+        int st = dev_alloc(ctx, &ctx->host_hit_dev, px * 16);
+        if (!st) st = dev_alloc(ctx, (void**)&ctx->host_t_dev, px * 4);
+        if (st) {
+            dev_free(ctx, ctx->host_hit_dev, px * 16);
+            ctx->host_hit_dev = nullptr;
+            return st;
+        }
+        ctx->host_frame_px = px;
+    }
+    aok_frame f{ctx->host_hit_dev, ctx->host_t_dev};
+    int st = aok_render(ctx, scene, cam, tau, &f, stream);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(hit_host, ctx->host_hit_dev, px * 16, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t_host, ctx->host_t_dev, px * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return cuda_status(ctx, e);
+}
+
+int aok_ray_dirs(aok_ctx* ctx, const aok_camera* cam, float* dirs, void* stream) {
+    if (!ctx || !cam || !dirs || ((uintptr_t)dirs & 3)) return AOK_E_INVALID;
+    CamDev cd;
+    Scene dummy;
+    dummy.desc.chunk_res = 512;
+    int st = make_cam(ctx, &dummy, cam, 1.0, &cd);
+    if (st) return st;
+    cudaSetDevice(ctx->device);
+    st = aokk_ray_dirs(&cd, dirs, stream);
+    return st ? cuda_status(ctx, cudaGetLastError()) : AOK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,101 @@
+// Host-side state of the runtime (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <condition_variable>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <utility>
+#include <vector>
+
+#include "aok_internal.h"
+
+namespace aok {
+
+constexpr uint64_t kNoRange = ~0ull;
+
+struct Pool {  // units of the pool's element type
+    uint64_t cap = 0, used = 0;
+    std::vector<std::pair<uint64_t, uint64_t>> free_list;  // (offset, count)
+    uint64_t alloc(uint64_t n);
+    void release(uint64_t off, uint64_t n);
+};
+
+struct ChunkAlloc {
+    uint64_t node_off = 0, node_n = 0, leaf_off = 0, leaf_n = 0, mat_off = 0, mat_n = 0;
+};
+
+struct Scene {
+    aok_scene_desc desc{};
+    int mlog = 0;
+    int64_t n_chunks = 0;
+    uint32_t* d_nodes = nullptr;
+    uint64_t* d_leaves = nullptr;
+    uint8_t* d_mats = nullptr;
+    ChunkRef* d_desc = nullptr;   // [chunk * n_lods + lod]
+    ChunkRef* d_frame = nullptr;  // per-frame selection of aok_render
+    Pool nodes, leaves, mats;
+    std::vector<ChunkRef> h_desc;
+    std::vector<ChunkAlloc> alloc;
+    std::mutex mu;
+};
+
+// Device arena of one batch shape (views, frame tables, queue), reused across calls.
+struct BatchArena {
+    ViewDev* d_views = nullptr;
+    ChunkRef* d_frames = nullptr;
+    unsigned long long* d_queue = nullptr;
+    size_t views_cap = 0, frames_cap = 0;
+    ViewDev* h_views = nullptr;  // pinned
+    // captured graph for one list shape
+    cudaGraphExec_t exec = nullptr;
+    std::vector<uint64_t> shape;
+    cudaStream_t cap_stream = nullptr;
+};
+
+struct ServeState;
+
+struct aok_ctx_impl;
+
+}  // namespace aok
+
+struct aok_ctx {
+    int device = 0;
+    int sm_count = 0;
+    size_t budget = 0, used = 0;
+    std::mutex mem_mu;
+    cudaError_t last_cuda = cudaSuccess;
+    cudaStream_t copy_stream = nullptr;
+    std::mutex scene_mu;
+    std::map<uint32_t, aok::Scene*> scenes;
+    uint32_t next_scene = 0;
+    void* staging = nullptr;
+    size_t staging_cap = 0;
+    uint32_t* pinned_word = nullptr;
+    uint32_t* d_counter = nullptr;
+    // persistent casting launch shape (0 = defaults)
+    uint32_t ctas_per_sm = 0, threads_per_cta = 0, packet_rays = 0;
+    aok::BatchArena batch;
+    // device frame of aok_render_host
+    void* host_hit_dev = nullptr;
+    float* host_t_dev = nullptr;
+    size_t host_frame_px = 0;
+    aok::ServeState* serve = nullptr;
+};
+
+namespace aok {
+int cuda_status(aok_ctx* ctx, cudaError_t e);
+int charge(aok_ctx* ctx, size_t bytes);
+void uncharge(aok_ctx* ctx, size_t bytes);
+int dev_alloc(aok_ctx* ctx, void** p, size_t bytes);
+void dev_free(aok_ctx* ctx, void* p, size_t bytes);
+Scene* find_scene(aok_ctx* ctx, uint32_t id);
+int make_cam(aok_ctx* ctx, const Scene* sc, const aok_camera* cam, double tau, CamDev* out);
+SceneDev scene_dev(const Scene* sc);
+void batch_release(aok_ctx* ctx);
+}  // namespace aok

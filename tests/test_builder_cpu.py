@@ -1,0 +1,166 @@
+"""CPU checks of the product side that need no GPU: the native chunk builder
+against the oracle's dense LOD grids and DAG node counts, the blob validator,
+and the C ABI's exported symbols."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as orc
+import paper_2505_02017_gb300 as aok
+import scenegen as sg
+from worlds import MED64, MULTI16, MULTI32
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def blob_arrays(b):
+    nodes = np.ctypeslib.as_array(ctypes.cast(b.nodes, ctypes.POINTER(ctypes.c_uint32)), (b.n_node_words,)).copy() \
+        if b.n_node_words else np.zeros(0, np.uint32)
+    leaves = np.ctypeslib.as_array(ctypes.cast(b.leaves, ctypes.POINTER(ctypes.c_uint64)), (b.n_leaves,)).copy() \
+        if b.n_leaves else np.zeros(0, np.uint64)
+    mats = np.ctypeslib.as_array(ctypes.cast(b.mats, ctypes.POINTER(ctypes.c_uint8)), (b.n_mats,)).copy() \
+        if b.n_mats else np.zeros(0, np.uint8)
+    return nodes, leaves, mats
+
+
+def decode_blob(b, res):
+    """Expand a blob to dense occupancy/materials (test-side decoder)."""
+    nodes, leaves, mats = blob_arrays(b)
+    occ = np.zeros((res, res, res), np.uint8)
+    mat = np.zeros((res, res, res), np.uint8)
+    if b.n_node_words == 0:
+        return occ, mat, {}
+    counter = [0]
+    per_level = {}
+
+    def rec(node, x0, y0, z0, size, depth):
+        per_level.setdefault(depth, set()).add(node)
+        mask = int(nodes[node]) & 0xFF
+        p = node + 2
+        h = size // 2
+        for o in range(8):
+            if not (mask >> o) & 1:
+                continue
+            ch = int(nodes[p])
+            p += 1
+            cx, cy, cz = x0 + (o & 1) * h, y0 + ((o >> 1) & 1) * h, z0 + (o >> 2) * h
+            if h == 4:
+                per_level.setdefault("leaf", set()).add(ch)
+                m = int(leaves[ch])
+                for bit in range(64):
+                    if (m >> bit) & 1:
+                        x, y, z = cx + (bit & 3), cy + ((bit >> 2) & 3), cz + (bit >> 4)
+                        occ[z, y, x] = 1
+                        mat[z, y, x] = mats[counter[0]]
+                        counter[0] += 1
+            else:
+                rec(ch, cx, cy, cz, h, depth + 1)
+
+    rec(b.root, 0, 0, 0, res, 0)
+    assert counter[0] == b.n_mats
+    return occ, mat, {k: len(v) for k, v in per_level.items()}
+
+
+@pytest.mark.parametrize("spec", [MULTI16, MULTI32, MED64], ids=lambda s: s.name)
+def test_builder_matches_oracle_dense_and_node_counts(spec):
+    w = sg.World(spec)
+    bw = aok.BuiltWorld(w, threads=4)
+    gx, gy, gz = spec.grid
+    assert len(bw) == gx * gy * gz
+    rng = np.random.default_rng(1)
+    picks = rng.choice(len(bw), size=min(6, len(bw)), replace=False)
+    nonempty = 0
+    for i in picks:
+        for lod in range(spec.n_lods):
+            c, b = bw.blob(int(i), lod)
+            cx, cy, cz = c % gx, (c // gx) % gy, c // (gx * gy)
+            res = spec.chunk >> lod
+            occ, mat = orc.chunk_dense(w, spec.chunk, cx, cy, cz, lod)
+            docc, dmat, levels = decode_blob(b, res)
+            assert (docc == occ).all(), (c, lod)
+            assert (dmat == mat * occ).all(), (c, lod)
+            if occ.any():
+                nonempty += 1
+                assert aok.validate_chunk(b, spec.chunk, lod) == aok.AOK_OK
+                # same dedup as the oracle: unique nodes per level and unique leaves
+                od = orc.OracleDag(occ, mat)
+                lv = od.level_nodes()
+                assert [levels[d] for d in range(od.n_int)] == lv[:-1]
+                assert levels["leaf"] == lv[-1] == b.n_leaves
+                # AABB of the solid voxels, chunk-local LOD-0 units
+                zs, ys, xs = np.nonzero(occ)
+                assert list(b.aabb_lo) == [int(xs.min()) << lod, int(ys.min()) << lod, int(zs.min()) << lod]
+                assert list(b.aabb_hi) == [(int(xs.max()) + 1) << lod, (int(ys.max()) + 1) << lod,
+                                           (int(zs.max()) + 1) << lod]
+                # breadth-first layout: the root is the first node
+                assert b.root == 0
+            else:
+                assert b.n_node_words == 0 and b.n_mats == 0
+    assert nonempty > 0
+
+
+def corrupt_variants(b, spec_chunk, lod):
+    nodes, leaves, mats = blob_arrays(b)
+    out = []
+
+    def mk(n, l, m, root=b.root, lo=None, hi=None):
+        c = aok.ChunkBlob()
+        n = np.ascontiguousarray(n, np.uint32)
+        l = np.ascontiguousarray(l, np.uint64)
+        m = np.ascontiguousarray(m, np.uint8)
+        c.nodes, c.n_node_words = n.ctypes.data, len(n)
+        c.leaves, c.n_leaves = l.ctypes.data, len(l)
+        c.mats, c.n_mats = m.ctypes.data, len(m)
+        c.root = root
+        for a in range(3):
+            c.aabb_lo[a] = (lo or list(b.aabb_lo))[a]
+            c.aabb_hi[a] = (hi or list(b.aabb_hi))[a]
+        out.append((c, (n, l, m)))
+
+    k = bin(int(nodes[b.root]) & 0xFF).count("1")
+    n1 = nodes.copy(); n1[b.root + 2] = len(nodes) + 5; mk(n1, leaves, mats)           # pointer out of range
+    n2 = nodes.copy(); n2[b.root] |= 0x100; mk(n2, leaves, mats)                        # reserved header bit
+    n3 = nodes.copy(); n3[b.root + 1] += 1; mk(n3, leaves, mats)                        # wrong leaf count
+    mk(nodes, leaves, mats[:-1])                                                         # material array too short
+    mk(nodes, leaves, mats, root=len(nodes) + 1)                                        # root out of range
+    mk(nodes, leaves, mats, hi=[spec_chunk + 1, 1, 1])                                  # AABB outside the chunk
+    n4 = nodes.copy(); n4[b.root] = 0; mk(n4, leaves, mats)                             # empty mask
+    return out, k
+
+
+def test_validator_rejects_corrupt_blobs():
+    spec = MULTI32
+    w = sg.World(spec)
+    bw = aok.BuiltWorld(w, threads=4)
+    tested = 0
+    for i in range(len(bw)):
+        _, b = bw.blob(i, 0)
+        if b.n_node_words == 0:
+            continue
+        assert aok.validate_chunk(b, spec.chunk, 0) == aok.AOK_OK
+        variants, _ = corrupt_variants(b, spec.chunk, 0)
+        for c, keep in variants:
+            assert aok.validate_chunk(c, spec.chunk, 0) == aok.AOK_E_CORRUPT
+        tested += 1
+        if tested == 3:
+            break
+    assert tested == 3
+    # wrong LOD for the blob's depth: node levels no longer line up
+    _, b1 = bw.blob(0, 1)
+    if b1.n_node_words:
+        assert aok.validate_chunk(b1, spec.chunk, 0) != aok.AOK_OK
+    # bad arguments
+    assert aok.validate_chunk(b, 48, 0) == aok.AOK_E_INVALID
+
+
+def test_abi_exports_every_declared_symbol():
+    with open(os.path.join(ROOT, "include", "aok.h")) as f:
+        text = f.read()
+    names = set(re.findall(r"^\s*(?:int|void|const char\*)\s+(aok_\w+)\s*\(", text, re.M))
+    assert len(names) >= 20
+    L = aok.lib()
+    for n in sorted(names):
+        assert hasattr(L, n), n

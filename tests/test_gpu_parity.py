@@ -1,0 +1,240 @@
+"""GPU path vs oracle, element by element, through the C ABI (libaok.so).
+
+Small worlds (several tiles per ray, ragged image sizes, cameras inside and
+outside the world, mixed LODs, a view distance) on every pixel; the 128^3
+single-chunk workload on every pixel; the 4096^3 world at 1920x1080 (the
+benchmark's launch) on sampled pixels the oracle computes one by one."""
+import numpy as np
+import pytest
+
+import oracle as orc
+import scenegen as sg
+from gpu_util import compare, decode
+from worlds import MED64, MULTI16, MULTI32, TINY32
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # GPU tests are collected everywhere, run only with a device
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2505_02017_gb300 as aok  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = aok.Context(0)
+    yield c
+    c.close()
+
+
+_scenes = {}
+
+
+def scene_for(ctx, spec):
+    key = (id(ctx), spec.name)
+    if key not in _scenes:
+        w = sg.World(spec)
+        _scenes[key] = (w, aok.Scene.from_world(ctx, w, threads=16), orc.OracleScene(w))
+    return _scenes[key]
+
+
+def run(ctx, spec, cam, tau, view_dist=None, idx=None):
+    w, sc, S = scene_for(ctx, spec)
+    hit, t = aok.alloc_frame(cam.W, cam.H)
+    aok.render(ctx, sc, cam, tau, hit, t)
+    torch.cuda.synchronize()
+    g = decode(hit, t)
+    sel = S.select(cam, tau)
+    if idx is None:
+        ref = S.cast(cam, sel, view_dist=spec.view_dist)
+    else:
+        pix = np.stack([idx % cam.W, idx // cam.W], 1)
+        ref = S.cast(cam, sel, pixels=pix, view_dist=spec.view_dist)
+    return g, ref, sel
+
+
+CASES = [
+    (TINY32, lambda w: sg.orbit_camera(TINY32, 5, 40, 30), 1.0),
+    (TINY32, lambda w: sg.orbit_camera(TINY32, 6, 37, 23), 4.0),
+    (MULTI16, lambda w: sg.ground_camera(w, 3, 40, 24, lo_frac=0.3, hi_frac=0.7, z_lo=3, z_hi=8), 2.0),
+    (MULTI16, lambda w: sg.orbit_camera(MULTI16, 1, 61, 47, radius=80), 2.0),
+    (MULTI32, lambda w: sg.ground_camera(w, 4, 64, 40, z_lo=4, z_hi=20), 1.0),
+    (MED64, lambda w: sg.ground_camera(w, 4, 160, 90, z_lo=4, z_hi=40), 4.0),
+    (MED64, lambda w: sg.ground_camera(w, 9, 203, 117, z_lo=4, z_hi=40), 1.5),
+    (MED64, lambda w: sg.orbit_camera(MED64, 3, 128, 96, radius=300), 2.0),
+]
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_small_worlds_every_pixel(ctx, case):
+    spec, camf, tau = CASES[case]
+    w, _, _ = scene_for(ctx, spec)
+    cam = camf(w)
+    g, ref, _ = run(ctx, spec, cam, tau)
+    checked, amb = compare(g, ref, max_amb_frac=2e-3)
+    assert checked > 0.99 * cam.W * cam.H
+
+
+def test_single_chunk_128_every_pixel(ctx):
+    spec = sg.SINGLE_128
+    cam = sg.orbit_camera(spec, 101, 256, 256, radius=160, center=(64, 64, 48))
+    g, ref, _ = run(ctx, spec, cam, 1.0)
+    checked, amb = compare(g, ref)
+    assert (ref["hit"] == 1).mean() > 0.3
+
+
+def test_view_distance(ctx):
+    from dataclasses import replace
+    spec = replace(MULTI32, name="multi32vd", view_dist=45.0)
+    w, _, _ = scene_for(ctx, spec)
+    cam = sg.ground_camera(w, 4, 64, 40, z_lo=4, z_hi=20)
+    g, ref, _ = run(ctx, spec, cam, 1.0)
+    compare(g, ref, max_amb_frac=2e-3)
+    assert (ref["hit"] == 0).sum() > 0
+
+
+def test_degenerate_images_and_axis_aligned_rays(ctx):
+    spec = MED64
+    w, _, _ = scene_for(ctx, spec)
+    # 1x1 image: u = v = 0, the ray is -R[:,2]; straight down is axis-aligned (d_x = d_y = 0)
+    for fwd in [(0.0, 0.0, -1.0), (1.0, 0.0, 0.0), (0.0, -1.0, 0.0), (1.0, 1.0, -1.0)]:
+        cam = sg.make_camera((100.25, 130.5, 120.0), fwd, 1, 1)
+        g, ref, _ = run(ctx, spec, cam, 1.0)
+        compare(g, ref)
+    cam = sg.make_camera((100.25, 130.5, 120.0), (0.3, 0.2, -1.0), 7, 1)
+    g, ref, _ = run(ctx, spec, cam, 1.0)
+    compare(g, ref)
+
+
+def test_ray_directions_bitwise(ctx):
+    w, _, _ = scene_for(ctx, MED64)
+    cam = sg.ground_camera(w, 4, 97, 61, z_lo=4, z_hi=40)
+    dirs = torch.empty((cam.H, cam.W, 3), dtype=torch.float32, device="cuda")
+    aok.ray_dirs(ctx, cam, dirs)
+    torch.cuda.synchronize()
+    ref = orc.ray_dirs(cam)
+    assert (dirs.cpu().numpy().view(np.uint32) == ref.view(np.uint32)).all()
+
+
+def test_selection_matches_eq1(ctx):
+    for spec, camf, tau in [(MED64, lambda w: sg.ground_camera(w, 4, 160, 90, z_lo=4, z_hi=40), 4.0),
+                            (MULTI32, lambda w: sg.ground_camera(w, 4, 64, 40, z_lo=4, z_hi=20), 1.0)]:
+        w, sc, S = scene_for(ctx, spec)
+        cam = camf(w)
+        n = int(np.prod(sc.grid))
+        lod = torch.full((n,), -7, dtype=torch.int8, device="cuda")
+        vis = torch.zeros((n,), dtype=torch.uint8, device="cuda")
+        nvis = aok.select_chunks(ctx, sc, cam, tau, lod, vis, count=True)
+        ref = S.select(cam, tau)
+        assert (lod.cpu().numpy() == ref).all()
+        v = vis.cpu().numpy()
+        assert nvis == int(v.sum())
+        # visible chunks are non-empty at their LOD; hit chunks are never culled
+        S.prepare(ref)
+        for c in np.nonzero(v)[0]:
+            d, _ = S.dag(int(c), int(ref[c]))
+            assert d is not None and d.n_words > 0
+
+
+def test_traversal_counts_match_oracle(ctx):
+    spec = MED64
+    w, sc, S = scene_for(ctx, spec)
+    cam = sg.ground_camera(w, 4, 120, 70, z_lo=4, z_hi=40)
+    hit, t = aok.alloc_frame(cam.W, cam.H)
+    counts = torch.zeros((cam.H, cam.W, 3), dtype=torch.int32, device="cuda")
+    aok.render_counted(ctx, sc, cam, 2.0, hit, t, counts)
+    torch.cuda.synchronize()
+    c = counts.cpu().numpy().reshape(-1, 3)
+    sel = S.select(cam, 2.0)
+    ref = S.cast(cam, sel)
+    ok = ref["amb"] == 0
+    for j, k in enumerate(("v_int", "v_leaf", "resolve_bytes")):
+        same = (c[ok, j] == ref[k][ok])
+        assert same.mean() > 0.995, (k, same.mean())
+    # the counted frame equals the plain one
+    g = decode(hit, t)
+    compare(g, ref, max_amb_frac=2e-3)
+
+
+def test_city4096_1080p_sampled(ctx):
+    """The benchmark's launch: 4096^3 world (8^3 chunks of 512^3, 4 LODs), 1920x1080, tau = 1."""
+    spec = sg.CITY_4096
+    w, _, _ = scene_for(ctx, spec)
+    cam = sg.ground_camera(w, 102, 1920, 1080)
+    rng = np.random.default_rng(7)
+    n = cam.W * cam.H
+    idx = np.unique(np.concatenate([rng.integers(0, n, 6000), np.arange(0, n, 997),
+                                    np.arange(cam.W * 540, cam.W * 541)]))  # a full middle row
+    g, ref, sel = run(ctx, spec, cam, 1.0, idx=idx)
+    checked, amb = compare(g, ref, idx=idx)
+    assert checked > 0.999 * len(idx)
+    assert len(set(sel.tolist())) >= 2
+
+
+def test_city4096_far_view_mixed_lods(ctx):
+    """High camera looking across the world: many LOD-1/2 hits."""
+    spec = sg.CITY_4096
+    w, _, _ = scene_for(ctx, spec)
+    cam = sg.ground_camera(w, 7, 640, 360, z_lo=600, z_hi=900, pitch=(-20.0, -8.0))
+    g, ref, sel = run(ctx, spec, cam, 1.0)
+    compare(g, ref)
+    lods = ref["lod"][ref["hit"] == 1]
+    assert len(np.unique(lods)) >= 2
+
+
+def test_abi_errors(ctx):
+    w, sc, _ = scene_for(ctx, TINY32)
+    cam = sg.orbit_camera(TINY32, 5, 8, 8)
+    hit, t = aok.alloc_frame(8, 8)
+    c = aok.to_camera(cam)
+    c.origin[0] = 1.0 / 3.0  # not on the 2^-12 grid
+    f = aok.frame_of(hit, t)
+    import ctypes
+    L = aok.lib()
+    s = torch.cuda.current_stream().cuda_stream
+    assert L.aok_render(ctx.h, sc.id, ctypes.byref(c), 1.0, ctypes.byref(f), s) == aok.AOK_E_INVALID
+    c = aok.to_camera(cam)
+    assert L.aok_render(ctx.h, 999999, ctypes.byref(c), 1.0, ctypes.byref(f), s) == aok.AOK_E_NOT_RESIDENT
+    assert L.aok_render(ctx.h, sc.id, ctypes.byref(c), -1.0, ctypes.byref(f), s) == aok.AOK_E_INVALID
+    f2 = aok.Frame()
+    f2.hit = hit.data_ptr() + 4  # misaligned
+    f2.t = t.data_ptr()
+    assert L.aok_render(ctx.h, sc.id, ctypes.byref(c), 1.0, ctypes.byref(f2), s) == aok.AOK_E_INVALID
+    # a corrupt blob is rejected by the upload and nothing changes
+    bw = aok.BuiltWorld(w, threads=2)
+    _, b = bw.blob(0, 0)
+    bad = aok.ChunkBlob.from_buffer_copy(b)
+    bad.n_mats = b.n_mats + 1
+    assert L.aok_scene_upload_chunk(ctx.h, sc.id, 0, 0, 0, 0, ctypes.byref(bad)) == aok.AOK_E_CORRUPT
+    g1 = decode(hit, t)
+    aok.render(ctx, sc, cam, 1.0, hit, t)
+    torch.cuda.synchronize()
+    # a scene larger than the budget is refused
+    small = aok.Context(0, budget_bytes=1 << 20)
+    d = aok.SceneDesc()
+    d.grid[0] = d.grid[1] = d.grid[2] = 1
+    d.chunk_res, d.n_lods = 64, 1
+    d.node_words, d.leaf_count, d.mat_bytes = 1 << 20, 1 << 20, 1 << 20
+    sid = ctypes.c_uint32()
+    assert L.aok_scene_create(small.h, ctypes.byref(d), ctypes.byref(sid)) == aok.AOK_E_OOM
+    small.close()
+    del g1
+
+
+def test_evict_renders_as_empty(ctx):
+    from dataclasses import replace
+    spec = replace(TINY32, name="tiny32evict")
+    w = sg.World(spec)
+    sc = aok.Scene.from_world(ctx, w, threads=2)
+    cam = sg.orbit_camera(spec, 5, 32, 32)
+    hit, t = aok.alloc_frame(32, 32)
+    aok.render(ctx, sc, cam, 1.0, hit, t)
+    torch.cuda.synchronize()
+    assert decode(hit, t)["hit"].sum() > 0
+    for lod in range(spec.n_lods):
+        sc.evict(0, 0, 0, lod)
+    aok.render(ctx, sc, cam, 1.0, hit, t)
+    torch.cuda.synchronize()
+    assert decode(hit, t)["hit"].sum() == 0
+    sc.destroy()
