@@ -210,6 +210,10 @@ def main():
     c = counts.view(-1, 3).to(torch.int64).sum(0).tolist()
     algo_bytes = 8 * c[0] + 8 * c[1] + c[2] + 20 * W * H  # node visits, leaf visits, resolve, output
     del counts
+    meta = hit.view(-1, 4)[:, 3]
+    is_hit = ((meta >> 19) & 1) == 1
+    hit_frac = float(is_hit.float().mean().item())
+    lod_hist = torch.bincount((meta[is_hit] & 0xFF).long(), minlength=4).tolist()
 
     # ---- warmup ----
     for _ in range(args.warmup):
@@ -272,7 +276,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "i64/f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "rays_per_step": rays, "parallelism": f"replicas x{world_size}",
                    "l2": "flushed between steps (512 MB write)", "scene_build_s": round(t_build, 2),
-                   "scene_upload_s": round(t_upload, 2),
+                   "scene_upload_s": round(t_upload, 2), "hit_frac": hit_frac, "hit_lod_hist": lod_hist,
                    "scene_bytes": {"nodes": built.node_words * 4, "leaves": built.leaves * 8,
                                    "mats": built.mat_bytes}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,

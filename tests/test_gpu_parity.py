@@ -157,18 +157,15 @@ def test_traversal_counts_match_oracle(ctx):
     compare(g, ref, max_amb_frac=2e-3)
 
 
-def test_city4096_1080p_sampled(ctx):
-    """The benchmark's launch: 4096^3 world (8^3 chunks of 512^3, 4 LODs), 1920x1080, tau = 1."""
+def test_city4096_1080p_every_pixel(ctx):
+    """The benchmark's launch: 4096^3 world (8^3 chunks of 512^3, 4 LODs), 1920x1080,
+    tau = 1, every pixel against the oracle; ambiguous pixels <= 0.01% of the frame."""
     spec = sg.CITY_4096
     w, _, _ = scene_for(ctx, spec)
     cam = sg.ground_camera(w, 102, 1920, 1080)
-    rng = np.random.default_rng(7)
-    n = cam.W * cam.H
-    idx = np.unique(np.concatenate([rng.integers(0, n, 6000), np.arange(0, n, 997),
-                                    np.arange(cam.W * 540, cam.W * 541)]))  # a full middle row
-    g, ref, sel = run(ctx, spec, cam, 1.0, idx=idx)
-    checked, amb = compare(g, ref, idx=idx)
-    assert checked > 0.999 * len(idx)
+    g, ref, sel = run(ctx, spec, cam, 1.0)
+    checked, amb = compare(g, ref, max_amb_frac=1e-4)
+    assert checked >= 0.9999 * cam.W * cam.H
     assert len(set(sel.tolist())) >= 2
 
 
@@ -176,11 +173,11 @@ def test_city4096_far_view_mixed_lods(ctx):
     """High camera looking across the world: many LOD-1/2 hits."""
     spec = sg.CITY_4096
     w, _, _ = scene_for(ctx, spec)
-    cam = sg.ground_camera(w, 7, 640, 360, z_lo=600, z_hi=900, pitch=(-20.0, -8.0))
-    g, ref, sel = run(ctx, spec, cam, 1.0)
-    compare(g, ref)
+    cam = sg.ground_camera(w, 8, 320, 180, z_lo=600, z_hi=900, pitch=(-20.0, -8.0))
+    g, ref, sel = run(ctx, spec, cam, 1.0 / 3.0)
+    compare(g, ref, max_amb_frac=2e-4)
     lods = ref["lod"][ref["hit"] == 1]
-    assert len(np.unique(lods)) >= 2
+    assert len(np.unique(lods)) >= 3  # LOD 0, 1 and 2 surfaces in one frame
 
 
 def test_abi_errors(ctx):
