@@ -117,8 +117,11 @@ typedef struct aok_chunk_blob {
  * reachable from the root and returns AOK_E_CORRUPT (uploading nothing) for
  * an out-of-range pointer, a zero or reserved-bit header, a node reached at
  * two depths, a leaf count that is not the sum of its children's, a root
- * count different from n_mats, or an AABB outside the chunk.
- * AOK_E_OOM if a pool is full; AOK_E_INVALID for a bad chunk/lod. */
+ * count different from n_mats, or an AABB outside the chunk; a rejected
+ * blob changes nothing.  When the pools cannot hold the new blob next to the
+ * previous upload of the same (chunk, lod), the previous one is evicted
+ * first; AOK_E_OOM if the blob still does not fit (the chunk is then
+ * non-resident).  AOK_E_INVALID for a bad chunk/lod. */
 int aok_scene_upload_chunk(aok_ctx* ctx, uint32_t scene, int32_t cx, int32_t cy, int32_t cz,
                            uint32_t lod, const aok_chunk_blob* blob);
 /* Host-only check of a blob against the rules aok_scene_upload_chunk applies

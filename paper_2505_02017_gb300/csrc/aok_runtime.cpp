@@ -398,15 +398,27 @@ int aok_scene_upload_chunk(aok_ctx* ctx, uint32_t scene, int32_t cx, int32_t cy,
         }
         ctx->staging_cap = cap;
     }
-    // free the previous upload of this (chunk, lod) once the pools are idle
+    uint8_t* stg = (uint8_t*)ctx->staging;
+    // 1. validate before touching anything: a rejected blob changes nothing
+    st = validate_blob(blob, res, M, 0, 0, (uint32_t*)stg);
+    if (st) return st;
+    // 2. allocate; if the pools are too full, evict the previous upload of this
+    //    (chunk, lod) first (after the GPU is idle) and retry
     ChunkAlloc& old = sc->alloc[di];
-    if (old.node_n || old.leaf_n || old.mat_n) {
+    auto evict_old = [&]() {
+        if (!(old.node_n || old.leaf_n || old.mat_n)) return;
         cudaDeviceSynchronize();
         free_alloc(sc, old);
-        sc->h_desc[di].root = kNone;
-    }
-    ChunkAlloc a;
-    if (nw) {
+        ChunkRef none;
+        std::memset(&none, 0, sizeof(none));
+        none.root = kNone;
+        none.lod = lod;
+        sc->h_desc[di] = none;
+        cudaMemcpy(sc->d_desc + di, &none, sizeof(none), cudaMemcpyHostToDevice);
+    };
+    auto try_alloc = [&](ChunkAlloc& a) -> bool {
+        a = ChunkAlloc();
+        if (!nw) return true;
         a.node_off = sc->nodes.alloc(nw);
         a.leaf_off = sc->leaves.alloc(blob->n_leaves);
         a.mat_off = sc->mats.alloc(blob->n_mats);
@@ -418,15 +430,18 @@ int aok_scene_upload_chunk(aok_ctx* ctx, uint32_t scene, int32_t cx, int32_t cy,
             if (a.node_off != kNoRange) sc->nodes.release(a.node_off, nw);
             if (a.leaf_off != kNoRange) sc->leaves.release(a.leaf_off, blob->n_leaves);
             if (a.mat_off != kNoRange) sc->mats.release(a.mat_off, blob->n_mats);
-            return AOK_E_OOM;
+            a = ChunkAlloc();
+            return false;
         }
+        return true;
+    };
+    ChunkAlloc a;
+    if (!try_alloc(a)) {
+        evict_old();
+        if (!try_alloc(a)) return AOK_E_OOM;
     }
-    uint8_t* stg = (uint8_t*)ctx->staging;
-    st = validate_blob(blob, res, M, (uint32_t)a.node_off, (uint32_t)a.leaf_off, (uint32_t*)stg);
-    if (st) {
-        free_alloc(sc, a);
-        return st;
-    }
+    // 3. rebase the (valid) blob onto its pool offsets
+    validate_blob(blob, res, M, (uint32_t)a.node_off, (uint32_t)a.leaf_off, (uint32_t*)stg);
     ChunkRef ref;
     std::memset(&ref, 0, sizeof(ref));
     ref.root = kNone;
@@ -452,6 +467,10 @@ int aok_scene_upload_chunk(aok_ctx* ctx, uint32_t scene, int32_t cx, int32_t cy,
             ref.aabb[i] = (uint16_t)blob->aabb_lo[i];
             ref.aabb[3 + i] = (uint16_t)blob->aabb_hi[i];
         }
+    }
+    if (old.node_n || old.leaf_n || old.mat_n) {
+        cudaDeviceSynchronize();
+        free_alloc(sc, old);
     }
     sc->alloc[di] = a;
     sc->h_desc[di] = ref;

@@ -199,14 +199,24 @@ def test_abi_errors(ctx):
     f2.t = t.data_ptr()
     assert L.aok_render(ctx.h, sc.id, ctypes.byref(c), 1.0, ctypes.byref(f2), s) == aok.AOK_E_INVALID
     # a corrupt blob is rejected by the upload and nothing changes
+    aok.render(ctx, sc, cam, 1.0, hit, t)
+    torch.cuda.synchronize()
+    g1 = decode(hit, t)
     bw = aok.BuiltWorld(w, threads=2)
     _, b = bw.blob(0, 0)
     bad = aok.ChunkBlob.from_buffer_copy(b)
     bad.n_mats = b.n_mats + 1
     assert L.aok_scene_upload_chunk(ctx.h, sc.id, 0, 0, 0, 0, ctypes.byref(bad)) == aok.AOK_E_CORRUPT
-    g1 = decode(hit, t)
     aok.render(ctx, sc, cam, 1.0, hit, t)
     torch.cuda.synchronize()
+    g2 = decode(hit, t)
+    assert all((g1[k] == g2[k]).all() for k in ("hit", "x", "y", "z", "lod", "mat"))
+    # a valid re-upload into the exactly sized pools replaces the chunk in place
+    assert L.aok_scene_upload_chunk(ctx.h, sc.id, 0, 0, 0, 0, ctypes.byref(b)) == aok.AOK_OK
+    aok.render(ctx, sc, cam, 1.0, hit, t)
+    torch.cuda.synchronize()
+    g3 = decode(hit, t)
+    assert all((g1[k] == g3[k]).all() for k in ("hit", "x", "y", "z", "lod", "mat"))
     # a scene larger than the budget is refused
     small = aok.Context(0, budget_bytes=1 << 20)
     d = aok.SceneDesc()
@@ -216,7 +226,6 @@ def test_abi_errors(ctx):
     sid = ctypes.c_uint32()
     assert L.aok_scene_create(small.h, ctypes.byref(d), ctypes.byref(sid)) == aok.AOK_E_OOM
     small.close()
-    del g1
 
 
 def test_evict_renders_as_empty(ctx):
