@@ -265,6 +265,35 @@ int aok_serve_wait(aok_ctx* ctx, uint64_t ticket, uint32_t timeout_ms, aok_frame
 int aok_serve_release(aok_ctx* ctx, uint64_t ticket);
 
 /* ------------------------------------------------------------------ */
+/* Rendering without device allocation                                */
+/* ------------------------------------------------------------------ */
+
+/* Largest chunk grid (x*y*z chunk regions) aok_render_noalloc accepts. */
+#define AOK_NOALLOC_MAX_CHUNKS 65536
+
+/* aok_render for callers that must not allocate device memory while they
+ * render -- for example an engine frame loop that reserved all of its device
+ * memory up front, or code running under an allocator that forbids
+ * cudaMalloc/cudaFree at that point.  (The paper has no counterpart: its
+ * renderer is a set of engine passes.)  The result equals aok_render's.
+ * The call allocates nothing and calls no cudaMalloc or cudaFree: the
+ * per-frame chunk table that aok_render keeps in scene memory lives instead
+ * in one static device array of AOK_NOALLOC_MAX_CHUNKS entries (2 MiB) that
+ * every GPU loading this library holds until the process exits.
+ *  - Scenes with more than AOK_NOALLOC_MAX_CHUNKS chunk regions are rejected
+ *    with AOK_E_INVALID before any work is enqueued.
+ *  - The first call on a device looks up the array's device address (with
+ *    that device current) and caches it; make that first call before any
+ *    CUDA stream capture.
+ *  - All calls share the one array and each call overwrites the entries it
+ *    uses, so calls whose GPU work overlaps (different streams, or no
+ *    ordering between them) race and may return wrong pixels; order them on
+ *    one stream or synchronise between them.
+ * The scene, camera and frame are passed as for aok_render. */
+int aok_render_noalloc(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double lod_threshold_px,
+                       const aok_frame* frame, void* stream);
+
+/* ------------------------------------------------------------------ */
 /* Diagnostics                                                        */
 /* ------------------------------------------------------------------ */
 

@@ -83,6 +83,7 @@ def lib() -> ctypes.CDLL:
             "aok_select_chunks": [vp, u32, P(Camera), dbl, vp, vp, P(u32), vp],
             "aok_render": [vp, u32, P(Camera), dbl, P(Frame), vp],
             "aok_render_counted": [vp, u32, P(Camera), dbl, P(Frame), vp, vp],
+            "aok_render_noalloc": [vp, u32, P(Camera), dbl, P(Frame), vp],
             "aok_ray_dirs": [vp, P(Camera), vp, vp],
             "aok_cast_selected": [vp, u32, P(Camera), P(Frame), vp],
             "aok_render_host": [vp, u32, P(Camera), dbl, vp, vp, vp],

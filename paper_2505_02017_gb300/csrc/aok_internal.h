@@ -67,4 +67,6 @@ int aokk_select_batch(const aok::ViewDev* views_dev, uint32_t n_views, uint32_t 
 int aokk_cast_batch(const aok::ViewDev* views_dev, uint32_t n_views, uint64_t total_pixels,
                     unsigned long long* queue, uint32_t ctas, uint32_t threads, uint32_t packet, void* stream);
 int aokk_sm_count(int device);
+// aok_render_noalloc's launcher: chunk table in static device memory.
+int aokk_render_noalloc(const aok::SceneDev* s, const aok::CamDev* c, uint4* hit, float* t, void* stream);
 }

@@ -14,7 +14,9 @@
 // reported distance is rounded (FP32, relative error ~1e-7).
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
+#include <mutex>
 
 #include "aok_internal.h"
 
@@ -473,6 +475,46 @@ int aokk_cast(const SceneDev* s, const CamDev* c, const ChunkRef* frame, uint4* 
 int aokk_ray_dirs(const CamDev* c, float* dirs, void* stream) {
     const int n = c->W * c->H;
     ray_dirs_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(*c, dirs);
+    return status_of(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// Render without allocating: the per-frame chunk table lives in a file-scope
+// device array instead of scene-owned memory.  The array is created when the
+// module loads on a device and stays until the process exits.  Its device
+// address is looked up once per device (with that device current) and
+// cached; every call then reuses the same array, so calls that overlap on the
+// GPU race on it.  select_kernel overwrites every entry of the scene's grid
+// before cast_kernel reads it, so nothing needs clearing between calls.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) ChunkRef g_noalloc_frame[AOK_NOALLOC_MAX_CHUNKS];
+
+static constexpr int kMaxNoallocDevices = 128;
+static std::atomic<ChunkRef*> g_noalloc_ptr[kMaxNoallocDevices];
+static std::mutex g_noalloc_mu;
+
+int aokk_render_noalloc(const SceneDev* s, const CamDev* c, uint4* hit, float* t, void* stream) {
+    const long long nch = (long long)s->grid[0] * s->grid[1] * s->grid[2];
+    if (nch > AOK_NOALLOC_MAX_CHUNKS) return AOK_E_INVALID;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return AOK_E_CUDA;
+    if (dev < 0 || dev >= kMaxNoallocDevices) return AOK_E_INVALID;
+    ChunkRef* frame = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+    if (!frame) {
+        std::lock_guard<std::mutex> g(g_noalloc_mu);
+        frame = g_noalloc_ptr[dev].load(std::memory_order_relaxed);
+        if (!frame) {
+            void* p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_frame);
+            if (e != cudaSuccess || !p) return AOK_E_CUDA;
+            frame = (ChunkRef*)p;
+            g_noalloc_ptr[dev].store(frame, std::memory_order_release);
+        }
+    }
+    const cudaStream_t st = (cudaStream_t)stream;
+    select_kernel<<<(unsigned)((nch + 127) / 128), 128, 0, st>>>(*s, *c, frame, nullptr, nullptr, nullptr);
+    dim3 grid((c->W + 15) / 16, (c->H + 7) / 8);
+    cast_kernel<false><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, nullptr);
     return status_of(cudaGetLastError());
 }
 

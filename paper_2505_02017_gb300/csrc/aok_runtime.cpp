@@ -551,6 +551,23 @@ int aok_render(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double tau, 
     return render_impl(ctx, scene, cam, tau, frame, nullptr, stream);
 }
 
+int aok_render_noalloc(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double tau, const aok_frame* frame,
+                       void* stream) {
+    if (!ctx || !frame || !frame->hit || !frame->t) return AOK_E_INVALID;
+    if (((uintptr_t)frame->hit & 15) || ((uintptr_t)frame->t & 3)) return AOK_E_INVALID;
+    Scene* sc = find_scene(ctx, scene);
+    if (!sc) return AOK_E_NOT_RESIDENT;
+    if (sc->n_chunks > AOK_NOALLOC_MAX_CHUNKS) return AOK_E_INVALID;
+    CamDev cd;
+    int st = make_cam(ctx, sc, cam, tau, &cd);
+    if (st) return st;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_status(ctx, cudaGetLastError());
+    SceneDev sd = scene_dev(sc);
+    st = aokk_render_noalloc(&sd, &cd, (uint4*)frame->hit, frame->t, stream);
+    if (st == AOK_E_CUDA) return cuda_status(ctx, cudaGetLastError());
+    return st;
+}
+
 int aok_render_counted(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double tau, const aok_frame* frame,
                        uint32_t* counts, void* stream) {
     if (!counts) return AOK_E_INVALID;
