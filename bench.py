@@ -127,6 +127,151 @@ def cpu_oracle_sample(world, cam, budget_s=20.0, max_pixels=400_000):
                       f"oracle DAG build for the frame's LOD selection took {prep:.1f} s and is not timed"}
 
 
+def time_events(fn, reps, flush, stream):
+    """Median and best ms of fn() over reps, L2 flushed before each rep."""
+    import torch
+    ms = []
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return statistics.median(ms), min(ms)
+
+
+def bench_batched(aok, ctx, scene, world, flush, reps=5):
+    """64 walker views of the city world at resolutions drawn from five sizes:
+    one aok_render_batch (autotuned persistent launch, CUDA graph) vs 64
+    separate aok_render launches on one stream.  Outputs must be identical."""
+    import torch
+    cams = sg.batch_cameras(world, 104, 64)
+    rays = sum(c.W * c.H for c in cams)
+    stream = torch.cuda.current_stream()
+    plain = [aok.alloc_frame(c.W, c.H) for c in cams]
+    batch = [aok.alloc_frame(c.W, c.H) for c in cams]
+    views = [aok.make_view(scene, c, TAU, h, t) for c, (h, t) in zip(cams, batch)]
+
+    def run_plain():
+        for c, (h, t) in zip(cams, plain):
+            aok.render(ctx, scene, c, TAU, h, t)
+
+    def run_batch():
+        aok.render_batch(ctx, views)
+
+    run_plain()
+    t0 = time.perf_counter()
+    tune_ms = aok.autotune(ctx, views)
+    tune_s = time.perf_counter() - t0
+    run_batch()
+    torch.cuda.synchronize()
+    equal = all(torch.equal(a[0], b[0]) and torch.equal(a[1].view(torch.int32), b[1].view(torch.int32))
+                for a, b in zip(plain, batch))
+    p_med, p_best = time_events(run_plain, reps, flush, stream)
+    b_med, b_best = time_events(run_batch, reps, flush, stream)
+    ctas, threads, packet = aok.get_launch(ctx)
+    return {"workload": "city4096, 64 views (seed 104), resolutions uniform over "
+                        "{320x180, 640x360, 1280x720, 1920x1080, 2560x1440}, tau = 1 px",
+            "rays": rays, "plain_rays_per_s": rays / (p_med / 1e3), "batched_rays_per_s": rays / (b_med / 1e3),
+            "plain_ms": p_med, "batched_ms": b_med, "plain_best_ms": p_best, "batched_best_ms": b_best,
+            "speedup": p_med / b_med, "identical_outputs": bool(equal), "plain_launches": 128,
+            "batched_launches": 2, "autotuned": {"ctas_per_sm": ctas, "threads": threads, "packet_rays": packet,
+                                                 "best_ms": tune_ms, "tune_s": round(tune_s, 2)}}
+
+
+def bench_served(aok, ctx, base_scene, threads, rates=(200, 500, 1000, 2000), n_req=1000, n_warm=100):
+    """Poisson arrivals over 4 resident worlds (two 4096^3 cities, two 2048^3),
+    each request a random walker pose, a resolution from the five sizes and a
+    threshold U[0.5, 2] px: continuous-batching server vs serial FIFO renders."""
+    import threading
+    import torch
+    worlds = [sg.World(s) for s in sg.SERVE_WORLDS]
+    scenes = [base_scene] + [aok.Scene.from_world(ctx, w, threads) for w in worlds[1:]]
+    rng = sg.Rng(105)
+    pools = []
+    for wi, w in enumerate(worlds):
+        pools.append([sg.ground_camera(w, rng.next(), 64, 64) for _ in range(96)])
+    out = {"workload": "4 resident worlds (city4096 seeds 2, 5; city2048 seeds 6, 7), Poisson arrivals, "
+                       "poses by the walker rule, resolutions from the five sizes, tau ~ U[0.5, 2] px",
+           "requests_per_rate": n_req, "warmup_per_rate": n_warm, "rates": []}
+    stream = torch.cuda.current_stream()
+    for rate in rates:
+        reqs = []
+        t = 0.0
+        for i in range(n_req + n_warm):
+            t += -math.log(1.0 - (rng.next() >> 11) * (1.0 / 9007199254740992.0)) / rate
+            wi = rng.randint(0, 3)
+            W, H = sg.RESOLUTIONS[rng.randint(0, len(sg.RESOLUTIONS) - 1)]
+            cam = pools[wi][rng.randint(0, len(pools[wi]) - 1)]
+            cam = sg.Camera(cam.origin, cam.R, cam.tan_half_fovy, W, H)
+            tau = 0.5 + 1.5 * ((rng.next() >> 11) * (1.0 / 9007199254740992.0))
+            reqs.append((t, wi, cam, tau))
+        rays = sum(r[2].W * r[2].H for r in reqs[n_warm:])
+        # --- served ---
+        srv = aok.Server(ctx, max_slots=64, max_batch=16, n_streams=3)
+        tickets = [None] * len(reqs)
+        lat = [None] * len(reqs)
+        done_ns = [0] * len(reqs)
+
+        def submitter(t0):
+            for i, (ta, wi, cam, tau) in enumerate(reqs):
+                d = t0 + ta - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                tickets[i] = srv.submit(scenes[wi], cam, tau)
+
+        def releaser():
+            for i in range(len(reqs)):
+                while tickets[i] is None:
+                    time.sleep(0.0001)
+                st, f = srv.wait(tickets[i], 120000)
+                s_ns, d_ns = srv.times(tickets[i])
+                lat[i] = (d_ns - s_ns) / 1e6
+                done_ns[i] = d_ns
+                srv.release(tickets[i])
+
+        t0 = time.perf_counter()
+        th1 = threading.Thread(target=submitter, args=(t0,))
+        th2 = threading.Thread(target=releaser)
+        th1.start(); th2.start(); th1.join(); th2.join()
+        srv.stop()
+        span = (max(done_ns[n_warm:]) - min(done_ns[n_warm:])) / 1e9
+        ls = sorted(lat[n_warm:])
+        served = {"p50_ms": ls[len(ls) // 2], "p99_ms": ls[int(len(ls) * 0.99)],
+                  "req_per_s": (n_req - 1) / max(span, 1e-9), "rays_per_s": rays / max(span, 1e-9)}
+        # --- serial FIFO plain renders of the same trace ---
+        frames = {}
+        lat2 = []
+        t0 = time.perf_counter()
+        t_first = t_last = None
+        for i, (ta, wi, cam, tau) in enumerate(reqs):
+            d = t0 + ta - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            key = (cam.W, cam.H)
+            if key not in frames:
+                frames[key] = aok.alloc_frame(cam.W, cam.H)
+            h, tt = frames[key]
+            aok.render(ctx, scenes[wi], cam, tau, h, tt)
+            stream.synchronize()
+            now = time.perf_counter()
+            if i >= n_warm:
+                lat2.append((now - (t0 + ta)) * 1e3)
+                t_first = now if t_first is None else t_first
+                t_last = now
+        ls2 = sorted(lat2)
+        span2 = t_last - t_first
+        serial = {"p50_ms": ls2[len(ls2) // 2], "p99_ms": ls2[int(len(ls2) * 0.99)],
+                  "req_per_s": (n_req - 1) / max(span2, 1e-9), "rays_per_s": rays / max(span2, 1e-9)}
+        out["rates"].append({"arrival_req_per_s": rate, "served": served, "serial_plain": serial})
+    for sc in scenes[1:]:
+        sc.destroy()
+    return out
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle as it stands, same workload/metric, bounded sample per step."""
     rank, world_size, _ = dist_env()
@@ -171,6 +316,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--threads", type=int, default=0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -288,6 +435,10 @@ def main():
         "clocks": clk,
         "wall_s_timed": wall,
     }
+    if not args.no_batch:
+        out["batched"] = bench_batched(aok, ctx, scene, world, flush)
+    if not args.no_serve:
+        out["served"] = bench_served(aok, ctx, scene, threads)
     if rank == 0 and world_size == 1 and not args.no_cpu_baseline:
         try:
             out["cpu_baseline"] = cpu_oracle_sample(world, cam)

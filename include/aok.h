@@ -234,6 +234,13 @@ int aok_render_batch(aok_ctx* ctx, const aok_view* views, uint32_t n, void* stre
 int aok_set_launch(aok_ctx* ctx, uint32_t ctas_per_sm, uint32_t threads_per_cta, uint32_t packet_rays);
 int aok_get_launch(aok_ctx* ctx, uint32_t* ctas_per_sm, uint32_t* threads_per_cta, uint32_t* packet_rays);
 int aok_autotune(aok_ctx* ctx, const aok_view* views, uint32_t n, void* stream, float* best_ms);
+/* Warp tile of the persistent kernel: tile_w x (32 / tile_w) pixels, tile_w in
+ * {4, 8, 16, 32} (default 8).  aok_autotune also picks it. */
+int aok_set_tile(aok_ctx* ctx, uint32_t tile_w);
+/* Kernel used by aok_render / aok_cast_selected for one view: 0 = one thread
+ * per pixel over a grid of 16x8 tiles (default), 1 = the persistent kernel of
+ * aok_render_batch with this context's launch shape.  Results are identical. */
+int aok_set_single_view_kernel(aok_ctx* ctx, int persistent);
 
 /* ------------------------------------------------------------------ */
 /* Continuous-batching serving                                        */
@@ -261,8 +268,12 @@ int aok_serve_submit(aok_ctx* ctx, const aok_request* req, uint64_t* ticket);
 int aok_serve_poll(aok_ctx* ctx, uint64_t ticket, aok_frame* out_view);
 /* Block until done or `timeout_ms` passes (AOK_E_TIMEOUT). */
 int aok_serve_wait(aok_ctx* ctx, uint64_t ticket, uint32_t timeout_ms, aok_frame* out_view);
-/* Return the ticket's buffers to the pool (cancels it if not started). */
+/* Return the ticket's buffers to the pool (cancels it if not started);
+ * AOK_E_BUSY while its batch is on the GPU. */
 int aok_serve_release(aok_ctx* ctx, uint64_t ticket);
+/* Host steady-clock times (ns) at which the ticket was submitted and at which
+ * the serving loop saw its batch complete (0 while not complete). */
+int aok_serve_times(aok_ctx* ctx, uint64_t ticket, uint64_t* submit_ns, uint64_t* done_ns);
 
 /* ------------------------------------------------------------------ */
 /* Rendering without device allocation                                */

@@ -92,12 +92,15 @@ def lib() -> ctypes.CDLL:
             "aok_set_launch": [vp, u32, u32, u32],
             "aok_get_launch": [vp, P(u32), P(u32), P(u32)],
             "aok_autotune": [vp, P(View), u32, vp, P(ctypes.c_float)],
+            "aok_set_tile": [vp, u32],
+            "aok_set_single_view_kernel": [vp, ctypes.c_int],
             "aok_serve_start": [vp, u32, u32, u32],
             "aok_serve_stop": [vp],
             "aok_serve_submit": [vp, P(Request), P(u64)],
             "aok_serve_poll": [vp, u64, P(Frame)],
             "aok_serve_wait": [vp, u64, u32, P(Frame)],
             "aok_serve_release": [vp, u64],
+            "aok_serve_times": [vp, u64, P(u64), P(u64)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -339,3 +342,113 @@ def ray_dirs(ctx: Context, cam, dirs, stream=None):
     c = to_camera(cam)
     return check(lib().aok_ray_dirs(ctx.h, ctypes.byref(c), dirs.data_ptr(), _stream_handle(stream)),
                  "aok_ray_dirs")
+
+
+# ---------------------------------------------------------------------------
+# batched rendering, launch shape, serving
+# ---------------------------------------------------------------------------
+def make_view(scene: Scene, cam, tau: float, hit, t) -> View:
+    v = View()
+    v.scene = scene.id
+    v.cam = to_camera(cam)
+    v.lod_threshold_px = float(tau)
+    v.frame.hit = hit.data_ptr()
+    v.frame.t = t.data_ptr()
+    return v
+
+
+def _view_array(views):
+    arr = (View * len(views))()
+    for i, v in enumerate(views):
+        arr[i] = v
+    return arr
+
+
+def render_batch(ctx: Context, views, stream=None):
+    arr = _view_array(views)
+    return check(lib().aok_render_batch(ctx.h, arr, len(views), _stream_handle(stream)), "aok_render_batch")
+
+
+def autotune(ctx: Context, views, stream=None) -> float:
+    arr = _view_array(views)
+    ms = ctypes.c_float()
+    check(lib().aok_autotune(ctx.h, arr, len(views), _stream_handle(stream), ctypes.byref(ms)), "aok_autotune")
+    return ms.value
+
+
+def set_launch(ctx: Context, ctas_per_sm: int = 0, threads: int = 0, packet_rays: int = 0):
+    return check(lib().aok_set_launch(ctx.h, ctas_per_sm, threads, packet_rays), "aok_set_launch")
+
+
+def get_launch(ctx: Context):
+    a, b, c = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    check(lib().aok_get_launch(ctx.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "aok_get_launch")
+    return a.value, b.value, c.value
+
+
+def set_tile(ctx: Context, tile_w: int):
+    return check(lib().aok_set_tile(ctx.h, tile_w), "aok_set_tile")
+
+
+def set_single_view_kernel(ctx: Context, persistent: bool):
+    return check(lib().aok_set_single_view_kernel(ctx.h, int(persistent)), "aok_set_single_view_kernel")
+
+
+class _DevArray:
+    """Zero-copy view of library-owned device memory for torch.as_tensor."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 2, "strides": None}
+
+
+class Server:
+    """Continuous-batching render server on a Context (aok_serve_*)."""
+
+    def __init__(self, ctx: Context, max_slots: int = 64, max_batch: int = 32, n_streams: int = 2):
+        self.ctx = ctx
+        check(lib().aok_serve_start(ctx.h, max_slots, max_batch, n_streams), "aok_serve_start")
+        self.shapes = {}
+
+    def submit(self, scene: Scene, cam, tau: float) -> int:
+        r = Request()
+        r.scene = scene.id
+        r.cam = to_camera(cam)
+        r.lod_threshold_px = float(tau)
+        tk = ctypes.c_uint64()
+        check(lib().aok_serve_submit(self.ctx.h, ctypes.byref(r), ctypes.byref(tk)), "aok_serve_submit")
+        self.shapes[tk.value] = (int(cam.H), int(cam.W))
+        return tk.value
+
+    def poll(self, ticket: int):
+        f = Frame()
+        return int(lib().aok_serve_poll(self.ctx.h, ticket, ctypes.byref(f))), f
+
+    def wait(self, ticket: int, timeout_ms: int = 60000):
+        f = Frame()
+        st = int(lib().aok_serve_wait(self.ctx.h, ticket, timeout_ms, ctypes.byref(f)))
+        return st, f
+
+    def result(self, ticket: int, f: Frame):
+        """torch views (hit int32[H, W, 4], t float32[H, W]) of a finished ticket's buffers."""
+        import torch
+        H, W = self.shapes[ticket]
+        hit = torch.as_tensor(_DevArray(f.hit, (H, W, 4), "<i4"), device="cuda")
+        t = torch.as_tensor(_DevArray(f.t, (H, W), "<f4"), device="cuda")
+        return hit, t
+
+    def times(self, ticket: int):
+        a, b = ctypes.c_uint64(), ctypes.c_uint64()
+        check(lib().aok_serve_times(self.ctx.h, ticket, ctypes.byref(a), ctypes.byref(b)), "aok_serve_times")
+        return a.value, b.value
+
+    def release(self, ticket: int) -> int:
+        st = int(lib().aok_serve_release(self.ctx.h, ticket))
+        if st == AOK_OK:
+            self.shapes.pop(ticket, None)
+        return st
+
+    def stop(self):
+        if self.ctx is not None and self.ctx.h:
+            lib().aok_serve_stop(self.ctx.h)
+        self.ctx = None

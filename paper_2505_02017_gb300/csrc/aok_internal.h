@@ -1,6 +1,9 @@
 // Internal structures shared by the host runtime and the CUDA kernels.
 #pragma once
+#include <cuda_runtime.h>
+
 #include <cstdint>
+#include <vector>
 
 #include "../../include/aok.h"
 
@@ -50,7 +53,28 @@ struct ViewDev {
     ChunkRef* frame;        // per-view selected chunk table [chunk]
     uint4* hit;
     float* t;
-    uint64_t pix_begin;     // first global pixel index of this view in the batch
+    uint64_t tile_begin;    // first global warp-tile index of this view in the batch
+};
+
+// Parameter block of one batched launch (kernel parameters: up to 32 KB).
+constexpr int kBatchViews = 128;
+struct BatchParams {
+    uint32_t n_views;
+    uint32_t per_fetch;        // warp tiles taken per queue fetch
+    uint32_t tile_w_log;       // warp tile = 2^tile_w_log x 32 / 2^tile_w_log pixels
+    uint32_t max_chunks;       // largest chunk grid among the views
+    uint64_t total_tiles;      // warp tiles of all views
+    unsigned long long* queue; // [0] next warp tile, [1] finished CTAs; zero at launch, re-armed by the last CTA
+    ViewDev v[kBatchViews];
+};
+static_assert(sizeof(BatchParams) < 32000, "batched launch parameters must fit the kernel parameter space");
+
+// CUDA graph of one batch shape, rebuilt when the shape changes.
+struct GraphCache {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaGraphNode_t> nodes;  // select, cast per group
+    std::vector<uint64_t> key;
 };
 
 }  // namespace aok
@@ -62,10 +86,14 @@ int aokk_select(const aok::SceneDev* s, const aok::CamDev* c, aok::ChunkRef* fra
 int aokk_cast(const aok::SceneDev* s, const aok::CamDev* c, const aok::ChunkRef* frame, uint4* hit, float* t,
               uint32_t* counts, void* stream);
 int aokk_ray_dirs(const aok::CamDev* c, float* dirs, void* stream);
-// Batched: views[] on the device, n views, total pixels, queue counter (zeroed by the kernel chain).
-int aokk_select_batch(const aok::ViewDev* views_dev, uint32_t n_views, uint32_t max_chunks, void* stream);
-int aokk_cast_batch(const aok::ViewDev* views_dev, uint32_t n_views, uint64_t total_pixels,
-                    unsigned long long* queue, uint32_t ctas, uint32_t threads, uint32_t packet, void* stream);
+// Batched: one selection launch over (view, chunk), then one persistent
+// casting launch over all views' warp tiles.
+int aokk_select_batch(const aok::BatchParams* p, void* stream);
+int aokk_cast_batch(const aok::BatchParams* p, uint32_t ctas, uint32_t threads, void* stream);
+int aokk_batch_run(const aok::BatchParams* groups, uint32_t n_groups, uint32_t ctas, uint32_t threads, void* stream,
+                   aok::GraphCache* gc);
+void aokk_graph_destroy(aok::GraphCache* gc);
+int aokk_max_ctas_per_sm(uint32_t threads);
 int aokk_sm_count(int device);
 // aok_render_noalloc's launcher: chunk table in static device memory.
 int aokk_render_noalloc(const aok::SceneDev* s, const aok::CamDev* c, uint4* hit, float* t, void* stream);

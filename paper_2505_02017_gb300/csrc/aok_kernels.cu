@@ -17,6 +17,7 @@
 #include <atomic>
 #include <cstdint>
 #include <mutex>
+#include <vector>
 
 #include "aok_internal.h"
 
@@ -101,11 +102,9 @@ __device__ __forceinline__ bool lod_loads(int n, int bx, int by, int bz, int mlo
 // ---------------------------------------------------------------------------
 // selection + visibility: one thread per chunk region
 // ---------------------------------------------------------------------------
-__global__ void select_kernel(SceneDev S, CamDev C, ChunkRef* __restrict__ frame, int8_t* __restrict__ lod_out,
-                              uint8_t* __restrict__ vis_out, uint32_t* __restrict__ n_visible) {
-    const int nch = S.grid[0] * S.grid[1] * S.grid[2];
-    const int chunk = blockIdx.x * blockDim.x + threadIdx.x;
-    if (chunk >= nch) return;
+__device__ __forceinline__ void select_one(const SceneDev& S, const CamDev& C, ChunkRef* __restrict__ frame,
+                                           int8_t* __restrict__ lod_out, uint8_t* __restrict__ vis_out,
+                                           uint32_t* __restrict__ n_visible, int chunk) {
     const int cx = chunk % S.grid[0], cy = (chunk / S.grid[0]) % S.grid[1], cz = chunk / (S.grid[0] * S.grid[1]);
     int sel = 0;
     for (int n = S.n_lods - 1; n >= 1; n--)
@@ -146,19 +145,73 @@ __global__ void select_kernel(SceneDev S, CamDev C, ChunkRef* __restrict__ frame
     if (vis && n_visible) atomicAdd(n_visible, 1u);
 }
 
+__global__ void select_kernel(SceneDev S, CamDev C, ChunkRef* __restrict__ frame, int8_t* __restrict__ lod_out,
+                              uint8_t* __restrict__ vis_out, uint32_t* __restrict__ n_visible) {
+    const int nch = S.grid[0] * S.grid[1] * S.grid[2];
+    const int chunk = blockIdx.x * blockDim.x + threadIdx.x;
+    if (chunk < nch) select_one(S, C, frame, lod_out, vis_out, n_visible, chunk);
+}
+
+// one launch for all views of a batch: blockIdx.y = view
+__global__ void select_batch_kernel(const __grid_constant__ BatchParams P) {
+    const ViewDev& v = P.v[blockIdx.y];
+    const int nch = v.scene.grid[0] * v.scene.grid[1] * v.scene.grid[2];
+    const int chunk = blockIdx.x * blockDim.x + threadIdx.x;
+    if (chunk < nch) select_one(v.scene, v.cam, v.frame, nullptr, nullptr, nullptr, chunk);
+}
+
 // ---------------------------------------------------------------------------
-// per-chunk DAG traversal in the chunk's mirrored local frame
+// ray representation for exact comparisons
 // ---------------------------------------------------------------------------
-struct RayState {
+// FAST rays: the exponents of the non-zero |d| components span <= 6, so the
+// mantissas are shifted to a common exponent (M_a < 2^30) and
+// t_a < t_b  <=>  N_a M_b < N_b M_a  (two 32x32->64 products); a zero
+// component has M = 0, i.e. its crossings lie at +-infinity.
+// Other rays keep (m, E) per axis and use tlt().
+struct Ray {
     float d[3];
-    int32_t m[3], E[3];
+    float inv[3];
     uint32_t mir;
+    int32_t m0, m1, m2;
+    int32_t E0, E1, E2;
 };
 
+template <bool FAST>
+__device__ __forceinline__ bool tless(int32_t N1, int32_t m1, int32_t E1, int32_t N2, int32_t m2, int32_t E2) {
+    if (FAST) return (long long)N1 * m2 < (long long)N2 * m1;
+    return tlt(N1, m1, N2, m2, E2 - E1);
+}
+
+// Returns true if the ray qualifies for the FAST representation.
+__device__ __forceinline__ bool make_ray(const CamDev& C, int px, int py, Ray& r) {
+    ray_dir(C, px, py, r.d);
+    int32_t m[3], E[3];
+    r.mir = 0;
+    int emin = 1 << 20, emax = -(1 << 20);
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        decompose(r.d[a], m[a], E[a]);
+        if (r.d[a] < 0.0f) r.mir |= 1u << a;
+        r.inv[a] = 1.0f / r.d[a];
+        if (r.d[a] != 0.0f) { emin = min(emin, E[a]); emax = max(emax, E[a]); }
+    }
+    const bool fast = emax - emin <= 6;
+    if (fast) {
+        r.m0 = r.d[0] != 0.0f ? m[0] << (E[0] - emin) : 0;
+        r.m1 = r.d[1] != 0.0f ? m[1] << (E[1] - emin) : 0;
+        r.m2 = r.d[2] != 0.0f ? m[2] << (E[2] - emin) : 0;
+        r.E0 = r.E1 = r.E2 = 0;
+    } else {
+        r.m0 = m[0]; r.m1 = m[1]; r.m2 = m[2];
+        r.E0 = E[0]; r.E1 = E[1]; r.E2 = E[2];
+    }
+    return fast;
+}
+
 struct HitRec {
-    int32_t c[3];       // voxel index (mirrored, chunk-local, voxel units of the LOD)
-    int e;              // entry axis (3 = origin inside)
-    int32_t Ne;         // entry plane numerator
+    int32_t c0, c1, c2;  // voxel index (mirrored, chunk-local, voxel units of the LOD)
+    int e;               // entry axis (3 = origin inside)
+    int32_t Ne;          // entry plane numerator
     uint32_t mat;
 };
 
@@ -166,44 +219,68 @@ struct Counters {
     uint32_t v_int, v_leaf, rbytes;
 };
 
-// Returns true on a hit inside this chunk.  (e, Ne): entry plane into the chunk
-// (e = 3: the origin lies inside the chunk).  Oloc: mirrored local origin numerators.
-template <bool COUNT>
-__device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& ref, const RayState& r,
-                                            const int32_t Oloc[3], int e, int32_t Ne, HitRec& hit, Counters& cnt) {
+// axis with the smallest crossing among (N0, N1, N2); updates the entry (Ne, me, Ee)
+template <bool FAST>
+__device__ __forceinline__ int argmin3(const Ray& r, int32_t N0, int32_t N1, int32_t N2, int32_t& Ne, int32_t& me,
+                                       int32_t& Ee) {
+    const bool xy = tless<FAST>(N0, r.m0, r.E0, N1, r.m1, r.E1);
+    const int32_t Na = xy ? N0 : N1, ma = xy ? r.m0 : r.m1, Ea = xy ? r.E0 : r.E1;
+    if (tless<FAST>(Na, ma, Ea, N2, r.m2, r.E2)) {
+        Ne = Na; me = ma; Ee = Ea;
+        return xy ? 0 : 1;
+    }
+    Ne = N2; me = r.m2; Ee = r.E2;
+    return 2;
+}
+
+// ---------------------------------------------------------------------------
+// per-chunk DAG traversal in the chunk's mirrored local frame
+// ---------------------------------------------------------------------------
+// Cells are addressed by level k (cell side 2^k LOD-0 units) and mirrored
+// integer coordinates c.  Levels R = log2(M) (root) .. n+3 are interior nodes,
+// n+2 is a 4x4x4 leaf block, n+1 a 2x2x2 group inside it, n a voxel (LOD n).
+// (e, Ne): the plane through which the current cell was entered (e = 3: the
+// origin lies inside).  Returns true on a hit inside this chunk.
+template <bool FAST, bool COUNT>
+__device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& ref, const Ray& r, int32_t O0,
+                                            int32_t O1, int32_t O2, int e, int32_t Ne, HitRec& hit, Counters& cnt) {
     const uint32_t* __restrict__ nodes = S.nodes;
     const int R = S.mlog;
     const int n = (int)ref.lod;
-    uint32_t sidx[kMaxLevels];
-    uint32_t smask[kMaxLevels];
+    uint2 stk[kMaxLevels];  // (node word index, child mask) of the interior node at each level
     int k = R;
     int32_t c0 = 0, c1 = 0, c2 = 0;
     int32_t me = 1, Ee = 0;
-    if (e < 3) { me = r.m[e]; Ee = r.E[e]; }
-    uint64_t lm = 0, lmu = 0;
+    if (e == 0) { me = r.m0; Ee = r.E0; }
+    else if (e == 1) { me = r.m1; Ee = r.E1; }
+    else if (e == 2) { me = r.m2; Ee = r.E2; }
+    uint32_t pidx = 0, pmask = 0;  // interior node at level k + 1 (parent of the current cell)
+    uint64_t lm = 0, lmu = 0;      // current leaf block: mirrored / as stored
     bool occ = true;
     for (;;) {
         if (occ) {
             if (k == n) {
-                hit.c[0] = c0; hit.c[1] = c1; hit.c[2] = c2;
+                hit.c0 = c0; hit.c1 = c1; hit.c2 = c2;
                 hit.e = e;
                 hit.Ne = Ne;
                 // material through the depth-first index (Sec. 3.3)
-                const uint32_t mirv = r.mir;
                 const int32_t side = (1 << (R - n)) - 1;
-                const int32_t u0 = (mirv & 1u) ? side - c0 : c0;
-                const int32_t u1 = (mirv & 2u) ? side - c1 : c1;
-                const int32_t u2 = (mirv & 4u) ? side - c2 : c2;
+                const int32_t u0 = (r.mir & 1u) ? side - c0 : c0;
+                const int32_t u1 = (r.mir & 2u) ? side - c1 : c1;
+                const int32_t u2 = (r.mir & 4u) ? side - c2 : c2;
                 uint32_t idx = 0;
                 for (int j = R; j >= n + 3; j--) {
-                    const uint32_t node = sidx[j], mk = smask[j];
+                    const uint2 sj = stk[j];
                     const int sh = j - 1 - n;
                     const int oct = ((u0 >> sh) & 1) | (((u1 >> sh) & 1) << 1) | (((u2 >> sh) & 1) << 2);
-                    const int rk = __popc(mk & ((1u << oct) - 1u));
+                    const int rk = __popc(sj.y & ((1u << oct) - 1u));
                     const bool leafkids = (j - 1 == n + 2);
-                    for (int q = 0; q < rk; q++) {
-                        const uint32_t ch = nodes[node + 2 + q];
-                        idx += leafkids ? (uint32_t)__popcll(S.leaves[ch]) : nodes[ch + 1];
+                    uint32_t ch[7];
+#pragma unroll
+                    for (int q = 0; q < 7; q++) ch[q] = q < rk ? nodes[sj.x + 2 + q] : 0u;
+#pragma unroll
+                    for (int q = 0; q < 7; q++) {
+                        if (q < rk) idx += leafkids ? (uint32_t)__popcll(S.leaves[ch[q]]) : nodes[ch[q] + 1];
                     }
                     if (COUNT) cnt.rbytes += rk * (leafkids ? 8u : 4u);
                 }
@@ -219,11 +296,12 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
                     idx = ref.root;
                 } else {
                     const uint32_t oct = ((uint32_t)(c0 & 1) | ((uint32_t)(c1 & 1) << 1) | ((uint32_t)(c2 & 1) << 2)) ^ r.mir;
-                    idx = nodes[sidx[k + 1] + 2 + __popc(smask[k + 1] & ((1u << oct) - 1u))];
+                    idx = nodes[pidx + 2 + __popc(pmask & ((1u << oct) - 1u))];
                 }
                 if (k >= n + 3) {
-                    sidx[k] = idx;
-                    smask[k] = nodes[idx] & 0xFFu;
+                    pidx = idx;
+                    pmask = nodes[idx] & 0xFFu;
+                    stk[k] = make_uint2(pidx, pmask);
                     if (COUNT) cnt.v_int++;
                 } else {
                     lmu = S.leaves[idx];
@@ -233,43 +311,44 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
             }
             // child of cell (k, c) holding the entry point: compare t_entry with the mid planes
             const int kk = k - 1;
-            const int32_t mid0 = ((2 * c0 + 1) << (kk + kFix)) - Oloc[0];
-            const int32_t mid1 = ((2 * c1 + 1) << (kk + kFix)) - Oloc[1];
-            const int32_t mid2 = ((2 * c2 + 1) << (kk + kFix)) - Oloc[2];
-            const int32_t b0 = (e != 0) && !tlt(Ne, me, mid0, r.m[0], r.E[0] - Ee);
-            const int32_t b1 = (e != 1) && !tlt(Ne, me, mid1, r.m[1], r.E[1] - Ee);
-            const int32_t b2 = (e != 2) && !tlt(Ne, me, mid2, r.m[2], r.E[2] - Ee);
+            const int32_t mid0 = ((2 * c0 + 1) << (kk + kFix)) - O0;
+            const int32_t mid1 = ((2 * c1 + 1) << (kk + kFix)) - O1;
+            const int32_t mid2 = ((2 * c2 + 1) << (kk + kFix)) - O2;
+            const int32_t b0 = (e != 0) && !tless<FAST>(Ne, me, Ee, mid0, r.m0, r.E0);
+            const int32_t b1 = (e != 1) && !tless<FAST>(Ne, me, Ee, mid1, r.m1, r.E1);
+            const int32_t b2 = (e != 2) && !tless<FAST>(Ne, me, Ee, mid2, r.m2, r.E2);
             c0 = 2 * c0 + b0;
             c1 = 2 * c1 + b1;
             c2 = 2 * c2 + b2;
             k = kk;
         } else {
             // leave cell (k, c) through its nearest exit face
-            const int32_t N0 = ((c0 + 1) << (k + kFix)) - Oloc[0];
-            const int32_t N1 = ((c1 + 1) << (k + kFix)) - Oloc[1];
-            const int32_t N2 = ((c2 + 1) << (k + kFix)) - Oloc[2];
-            const bool xy = tlt(N0, r.m[0], N1, r.m[1], r.E[1] - r.E[0]);
-            const int32_t Na = xy ? N0 : N1, ma = xy ? r.m[0] : r.m[1], Ea = xy ? r.E[0] : r.E[1];
-            const bool az = tlt(Na, ma, N2, r.m[2], r.E[2] - Ea);
-            int ax;
-            if (az) { ax = xy ? 0 : 1; Ne = Na; me = ma; Ee = Ea; }
-            else { ax = 2; Ne = N2; me = r.m[2]; Ee = r.E[2]; }
-            e = ax;
+            const int32_t N0 = ((c0 + 1) << (k + kFix)) - O0;
+            const int32_t N1 = ((c1 + 1) << (k + kFix)) - O1;
+            const int32_t N2 = ((c2 + 1) << (k + kFix)) - O2;
+            e = argmin3<FAST>(r, N0, N1, N2, Ne, me, Ee);
             int32_t cax;
-            if (ax == 0) cax = ++c0;
-            else if (ax == 1) cax = ++c1;
+            if (e == 0) cax = ++c0;
+            else if (e == 1) cax = ++c1;
             else cax = ++c2;
             if ((cax << k) >= (1 << R)) return false;  // left the chunk
-            while (k < R && (cax & 1) == 0) {
-                c0 >>= 1; c1 >>= 1; c2 >>= 1;
-                cax >>= 1;
-                k++;
+            if ((cax & 1) == 0) {
+                do {
+                    c0 >>= 1; c1 >>= 1; c2 >>= 1;
+                    cax >>= 1;
+                    k++;
+                } while (k < R && (cax & 1) == 0);
+                if (k >= n + 2) {
+                    const uint2 p = stk[k + 1];
+                    pidx = p.x;
+                    pmask = p.y;
+                }
             }
         }
         // occupancy of cell (k, c)
         if (k >= n + 2) {
             const uint32_t oct = ((uint32_t)(c0 & 1) | ((uint32_t)(c1 & 1) << 1) | ((uint32_t)(c2 & 1) << 2)) ^ r.mir;
-            occ = (smask[k + 1] >> oct) & 1u;
+            occ = (pmask >> oct) & 1u;
         } else if (k == n + 1) {
             occ = (lm & (0x330033ull << ((c0 & 1) * 2 + (c1 & 1) * 8 + (c2 & 1) * 32))) != 0ull;
         } else {
@@ -281,122 +360,110 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
 // ---------------------------------------------------------------------------
 // one pixel: world-grid chunk march + per-chunk DAG traversal
 // ---------------------------------------------------------------------------
-template <bool COUNT>
-__device__ __forceinline__ void trace_pixel(const SceneDev& S, const CamDev& C, const ChunkRef* __restrict__ frame,
-                                            int px, int py, uint4* __restrict__ out_hit, float* __restrict__ out_t,
-                                            uint32_t* __restrict__ counts, size_t pix) {
-    RayState r;
-    ray_dir(C, px, py, r.d);
-    r.mir = 0;
-    int32_t Ow[3], Wfix[3];
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-        decompose(r.d[a], r.m[a], r.E[a]);
-        if (r.d[a] < 0.0f) r.mir |= 1u << a;
-        Wfix[a] = S.grid[a] << (S.mlog + kFix);
-        Ow[a] = ((r.mir >> a) & 1u) ? Wfix[a] - C.O[a] : C.O[a];
-    }
+template <bool FAST, bool COUNT>
+__device__ __forceinline__ void trace_ray(const SceneDev& S, const CamDev& C, const ChunkRef* __restrict__ frame,
+                                          const Ray& r, uint4* __restrict__ out_hit, float* __restrict__ out_t,
+                                          uint32_t* __restrict__ counts, size_t pix) {
+    const int cs = S.mlog + kFix;  // chunk side as a shift of numerator units
+    const int32_t G0 = S.grid[0], G1 = S.grid[1], G2 = S.grid[2];
+    const int32_t W0 = G0 << cs, W1 = G1 << cs, W2 = G2 << cs;
+    const int32_t Ow0 = (r.mir & 1u) ? W0 - C.O[0] : C.O[0];
+    const int32_t Ow1 = (r.mir & 2u) ? W1 - C.O[1] : C.O[1];
+    const int32_t Ow2 = (r.mir & 4u) ? W2 - C.O[2] : C.O[2];
     Counters cnt = {0, 0, 0};
     HitRec hit;
     bool found = false;
-    const int cs = S.mlog + kFix;  // chunk side as a shift of numerator units
     int e = 3;
     int32_t Ne = 0, me = 1, Ee = 0;
-    int32_t cc[3];
+    int32_t cc0, cc1, cc2;
     bool alive = true;
-    if (Ow[0] >= 0 && Ow[1] >= 0 && Ow[2] >= 0 && Ow[0] < Wfix[0] && Ow[1] < Wfix[1] && Ow[2] < Wfix[2]) {
-#pragma unroll
-        for (int a = 0; a < 3; a++) cc[a] = Ow[a] >> cs;
+    if (Ow0 >= 0 && Ow1 >= 0 && Ow2 >= 0 && Ow0 < W0 && Ow1 < W1 && Ow2 < W2) {
+        cc0 = Ow0 >> cs; cc1 = Ow1 >> cs; cc2 = Ow2 >> cs;
     } else {
         // enter the world box: latest entry plane vs earliest exit plane
+        if (Ow0 >= W0 || Ow1 >= W1 || Ow2 >= W2 || (r.d[0] == 0.0f && Ow0 < 0) || (r.d[1] == 0.0f && Ow1 < 0) ||
+            (r.d[2] == 0.0f && Ow2 < 0))
+            alive = false;
         e = -1;
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            if (Ow[a] >= Wfix[a] || (r.d[a] == 0.0f && Ow[a] < 0)) alive = false;
-            if (Ow[a] < 0) {
-                const int32_t Na = -Ow[a];
-                if (e < 0 || tlt(Ne, me, Na, r.m[a], r.E[a] - Ee)) { e = a; Ne = Na; me = r.m[a]; Ee = r.E[a]; }
-            }
-        }
-        int32_t Nx = Wfix[0] - Ow[0], mx = r.m[0], Ex = r.E[0];
-#pragma unroll
-        for (int a = 1; a < 3; a++) {
-            const int32_t Na = Wfix[a] - Ow[a];
-            if (tlt(Na, r.m[a], Nx, mx, Ex - r.E[a])) { Nx = Na; mx = r.m[a]; Ex = r.E[a]; }
-        }
-        if (alive && e >= 0 && tlt(Ne, me, Nx, mx, Ex - Ee)) {
-            const float te_num = (float)Ne / fabsf(r.d[e]);
+        if (Ow0 < 0) { e = 0; Ne = -Ow0; me = r.m0; Ee = r.E0; }
+        if (Ow1 < 0 && (e < 0 || tless<FAST>(Ne, me, Ee, -Ow1, r.m1, r.E1))) { e = 1; Ne = -Ow1; me = r.m1; Ee = r.E1; }
+        if (Ow2 < 0 && (e < 0 || tless<FAST>(Ne, me, Ee, -Ow2, r.m2, r.E2))) { e = 2; Ne = -Ow2; me = r.m2; Ee = r.E2; }
+        int32_t Nx, mx, Ex;
+        argmin3<FAST>(r, W0 - Ow0, W1 - Ow1, W2 - Ow2, Nx, mx, Ex);
+        if (alive && e >= 0 && tless<FAST>(Ne, me, Ee, Nx, mx, Ex)) {
+            const float te = (float)Ne / fabsf(r.d[e]);
+            const int32_t Ows[3] = {Ow0, Ow1, Ow2};
+            const int32_t Gs[3] = {G0, G1, G2};
+            const int32_t ms[3] = {r.m0, r.m1, r.m2}, Es[3] = {r.E0, r.E1, r.E2};
+            int32_t cc[3];
 #pragma unroll
             for (int a = 0; a < 3; a++) {
                 if (a == e) { cc[a] = 0; continue; }
-                const float pa = (float)Ow[a] + te_num * fabsf(r.d[a]);
+                const float pa = (float)Ows[a] + te * fabsf(r.d[a]);
                 int32_t cell = (int32_t)floorf(pa * (1.0f / (float)(1 << cs)));
-                cell = max(0, min(cell, S.grid[a] - 1));
+                cell = max(0, min(cell, Gs[a] - 1));
                 // exact correction: cell*M <= x_a(t_entry) < (cell+1)*M
-                while (cell + 1 < S.grid[a] && !tlt(Ne, me, ((cell + 1) << cs) - Ow[a], r.m[a], r.E[a] - Ee)) cell++;
-                while (cell > 0 && tlt(Ne, me, (cell << cs) - Ow[a], r.m[a], r.E[a] - Ee)) cell--;
+                while (cell + 1 < Gs[a] && !tless<FAST>(Ne, me, Ee, ((cell + 1) << cs) - Ows[a], ms[a], Es[a])) cell++;
+                while (cell > 0 && tless<FAST>(Ne, me, Ee, (cell << cs) - Ows[a], ms[a], Es[a])) cell--;
                 cc[a] = cell;
             }
+            cc0 = cc[0]; cc1 = cc[1]; cc2 = cc[2];
         } else {
             alive = false;
+            cc0 = cc1 = cc2 = 0;
         }
     }
-    const float dn = sqrtf(__fadd_rn(__fadd_rn(__fmul_rn(r.d[0], r.d[0]), __fmul_rn(r.d[1], r.d[1])), __fmul_rn(r.d[2], r.d[2])));
-    float inv[3];
-#pragma unroll
-    for (int a = 0; a < 3; a++) inv[a] = 1.0f / r.d[a];
+    const float dn = sqrtf(__fadd_rn(__fadd_rn(__fmul_rn(r.d[0], r.d[0]), __fmul_rn(r.d[1], r.d[1])),
+                                     __fmul_rn(r.d[2], r.d[2])));
     while (alive) {
-        int32_t u[3];
-#pragma unroll
-        for (int a = 0; a < 3; a++) u[a] = ((r.mir >> a) & 1u) ? S.grid[a] - 1 - cc[a] : cc[a];
-        const ChunkRef ref = frame[(size_t)u[0] + (size_t)S.grid[0] * ((size_t)u[1] + (size_t)S.grid[1] * u[2])];
+        const int32_t u0 = (r.mir & 1u) ? G0 - 1 - cc0 : cc0;
+        const int32_t u1 = (r.mir & 2u) ? G1 - 1 - cc1 : cc1;
+        const int32_t u2 = (r.mir & 4u) ? G2 - 1 - cc2 : cc2;
+        const ChunkRef ref = frame[(size_t)u0 + (size_t)G0 * ((size_t)u1 + (size_t)G1 * u2)];
         if (S.view_dist > 0.0f && e < 3) {
-            const float tent = (float)Ne / (4096.0f * fabsf(r.d[e]));
+            const float de = e == 0 ? r.d[0] : (e == 1 ? r.d[1] : r.d[2]);
+            const float tent = (float)Ne / (4096.0f * fabsf(de));
             if (tent * dn > S.view_dist * 1.00001f + 1.0f) break;
         }
         if (ref.root != kNone) {
             // skip chunks whose solid-voxel AABB (grown by 1/16 voxel) the ray misses
             float tn = 0.0f, tf = 3.0e38f;
             bool pass = true;
+            const int32_t us[3] = {u0, u1, u2};
 #pragma unroll
             for (int a = 0; a < 3; a++) {
-                const float lo = (float)((u[a] << S.mlog) + ref.aabb[a]) - 0.0625f;
-                const float hi = (float)((u[a] << S.mlog) + ref.aabb[3 + a]) + 0.0625f;
+                const float lo = (float)((us[a] << S.mlog) + ref.aabb[a]) - 0.0625f;
+                const float hi = (float)((us[a] << S.mlog) + ref.aabb[3 + a]) + 0.0625f;
                 if (r.d[a] == 0.0f) {
                     if (C.of[a] < lo || C.of[a] > hi) pass = false;
                 } else {
-                    float t1 = (lo - C.of[a]) * inv[a], t2 = (hi - C.of[a]) * inv[a];
+                    const float t1 = (lo - C.of[a]) * r.inv[a], t2 = (hi - C.of[a]) * r.inv[a];
                     tn = fmaxf(tn, fminf(t1, t2));
                     tf = fminf(tf, fmaxf(t1, t2));
                 }
             }
             if (pass && tn <= tf) {
-                int32_t Oloc[3];
-#pragma unroll
-                for (int a = 0; a < 3; a++) Oloc[a] = Ow[a] - (cc[a] << cs);
-                if (trace_chunk<COUNT>(S, ref, r, Oloc, e, Ne, hit, cnt)) {
+                if (trace_chunk<FAST, COUNT>(S, ref, r, Ow0 - (cc0 << cs), Ow1 - (cc1 << cs), Ow2 - (cc2 << cs), e, Ne,
+                                             hit, cnt)) {
                     found = true;
                     // un-mirror the voxel index to world LOD-0 units
                     const int n = (int)ref.lod;
                     const int32_t side = (1 << (S.mlog - n)) - 1;
-                    int32_t wxyz[3];
-#pragma unroll
-                    for (int a = 0; a < 3; a++) {
-                        const int32_t uv = ((r.mir >> a) & 1u) ? side - hit.c[a] : hit.c[a];
-                        wxyz[a] = (u[a] << S.mlog) + (uv << n);
-                    }
+                    const int32_t w0 = (u0 << S.mlog) + (((r.mir & 1u) ? side - hit.c0 : hit.c0) << n);
+                    const int32_t w1 = (u1 << S.mlog) + (((r.mir & 2u) ? side - hit.c1 : hit.c1) << n);
+                    const int32_t w2 = (u2 << S.mlog) + (((r.mir & 4u) ? side - hit.c2 : hit.c2) << n);
                     float dist = 0.0f;
-                    if (hit.e < 3) dist = __fdiv_rn((float)hit.Ne * (1.0f / 4096.0f), fabsf(r.d[hit.e])) * dn;
-                    if (S.view_dist > 0.0f) {
-                        double dd = 0.0;
-                        if (hit.e < 3) {
+                    if (hit.e < 3) {
+                        const float de = hit.e == 0 ? r.d[0] : (hit.e == 1 ? r.d[1] : r.d[2]);
+                        dist = __fdiv_rn((float)hit.Ne * (1.0f / 4096.0f), fabsf(de)) * dn;
+                        if (S.view_dist > 0.0f) {
                             const double d0 = r.d[0], d1 = r.d[1], d2 = r.d[2];
-                            dd = (double)hit.Ne / (4096.0 * fabs((double)r.d[hit.e])) * sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+                            const double dd = (double)hit.Ne / (4096.0 * fabs((double)de)) * sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+                            if (dd > (double)S.view_dist) { found = false; break; }
                         }
-                        if (dd > (double)S.view_dist) { found = false; break; }
                     }
                     const uint32_t normal = hit.e == 3 ? 7u : (uint32_t)(2 * hit.e) + ((r.mir >> hit.e) & 1u);
-                    out_hit[pix] = make_uint4((uint32_t)wxyz[0], (uint32_t)wxyz[1], (uint32_t)wxyz[2],
+                    out_hit[pix] = make_uint4((uint32_t)w0, (uint32_t)w1, (uint32_t)w2,
                                               (uint32_t)n | (hit.mat << 8) | (normal << 16) | (1u << 19));
                     out_t[pix] = dist;
                     break;
@@ -404,17 +471,10 @@ __device__ __forceinline__ void trace_pixel(const SceneDev& S, const CamDev& C, 
             }
         }
         // next chunk cell
-        const int32_t N0 = ((cc[0] + 1) << cs) - Ow[0];
-        const int32_t N1 = ((cc[1] + 1) << cs) - Ow[1];
-        const int32_t N2 = ((cc[2] + 1) << cs) - Ow[2];
-        const bool xy = tlt(N0, r.m[0], N1, r.m[1], r.E[1] - r.E[0]);
-        const int32_t Na = xy ? N0 : N1, ma = xy ? r.m[0] : r.m[1], Ea = xy ? r.E[0] : r.E[1];
-        const bool az = tlt(Na, ma, N2, r.m[2], r.E[2] - Ea);
-        int ax;
-        if (az) { ax = xy ? 0 : 1; Ne = Na; me = ma; Ee = Ea; }
-        else { ax = 2; Ne = N2; me = r.m[2]; Ee = r.E[2]; }
-        e = ax;
-        if (++cc[ax] >= S.grid[ax]) break;
+        e = argmin3<FAST>(r, ((cc0 + 1) << cs) - Ow0, ((cc1 + 1) << cs) - Ow1, ((cc2 + 1) << cs) - Ow2, Ne, me, Ee);
+        if (e == 0) { if (++cc0 >= G0) break; }
+        else if (e == 1) { if (++cc1 >= G1) break; }
+        else { if (++cc2 >= G2) break; }
     }
     if (!found) {
         out_hit[pix] = make_uint4(0u, 0u, 0u, 0xFFu | (7u << 16));
@@ -427,6 +487,15 @@ __device__ __forceinline__ void trace_pixel(const SceneDev& S, const CamDev& C, 
     }
 }
 
+template <bool COUNT>
+__device__ __forceinline__ void trace_pixel(const SceneDev& S, const CamDev& C, const ChunkRef* __restrict__ frame,
+                                            int px, int py, uint4* __restrict__ out_hit, float* __restrict__ out_t,
+                                            uint32_t* __restrict__ counts, size_t pix) {
+    Ray r;
+    if (make_ray(C, px, py, r)) trace_ray<true, COUNT>(S, C, frame, r, out_hit, out_t, counts, pix);
+    else trace_ray<false, COUNT>(S, C, frame, r, out_hit, out_t, counts, pix);
+}
+
 // 16 x 8 pixel tiles, warps of 8 x 4 pixels
 template <bool COUNT>
 __global__ void __launch_bounds__(128) cast_kernel(SceneDev S, CamDev C, const ChunkRef* __restrict__ frame,
@@ -437,6 +506,56 @@ __global__ void __launch_bounds__(128) cast_kernel(SceneDev S, CamDev C, const C
     const int py = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
     if (px >= C.W || py >= C.H) return;
     trace_pixel<COUNT>(S, C, frame, px, py, out_hit, out_t, counts, (size_t)py * C.W + px);
+}
+
+// Persistent casting over a list of views (P.queue[0] = next tile, P.queue[1]
+// = finished CTAs; both zero at launch).  Each warp pulls `per_fetch`
+// consecutive warp tiles (2^tile_w_log x 32/2^tile_w_log pixels of one view)
+// from a global counter until every tile of every view is done.
+// P.v[v].tile_begin is the exclusive prefix sum of the views' tile counts.
+__global__ void __launch_bounds__(256) cast_persistent(const __grid_constant__ BatchParams P) {
+    const int lane = threadIdx.x & 31;
+    const int tw = 1 << P.tile_w_log, th = 32 >> P.tile_w_log;
+    uint32_t cur = 0;
+    uint64_t vbeg = 0, vend = 0;
+    int tiles_x = 1;
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(P.queue, (unsigned long long)P.per_fetch);
+        base = __shfl_sync(0xFFFFFFFFu, base, 0);
+        if (base >= P.total_tiles) break;
+        const uint64_t stop = min((uint64_t)base + P.per_fetch, P.total_tiles);
+        for (uint64_t tile = base; tile < stop; tile++) {
+            if (tile < vbeg || tile >= vend) {
+                uint32_t lo = 0, hi = P.n_views - 1;  // last view with tile_begin <= tile
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi + 1) >> 1;
+                    if (P.v[mid].tile_begin <= tile) lo = mid;
+                    else hi = mid - 1;
+                }
+                cur = lo;
+                vbeg = P.v[cur].tile_begin;
+                vend = cur + 1 < P.n_views ? P.v[cur + 1].tile_begin : P.total_tiles;
+                tiles_x = (P.v[cur].cam.W + tw - 1) >> P.tile_w_log;
+            }
+            const ViewDev& v = P.v[cur];
+            const int32_t local = (int32_t)(tile - vbeg);
+            const int px = (local % tiles_x) * tw + (lane & (tw - 1));
+            const int py = (local / tiles_x) * th + (lane >> P.tile_w_log);
+            if (px < v.cam.W && py < v.cam.H)
+                trace_pixel<false>(v.scene, v.cam, v.frame, px, py, v.hit, v.t, nullptr, (size_t)py * v.cam.W + px);
+        }
+    }
+    // the last CTA to finish re-arms the counters for the next launch
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&P.queue[1], 1ull) == (unsigned long long)gridDim.x - 1ull) {
+            P.queue[0] = 0ull;
+            P.queue[1] = 0ull;
+            __threadfence();
+        }
+    }
 }
 
 __global__ void ray_dirs_kernel(CamDev C, float* __restrict__ dirs) {
@@ -470,6 +589,93 @@ int aokk_cast(const SceneDev* s, const CamDev* c, const ChunkRef* frame, uint4* 
     else
         cast_kernel<false><<<grid, 128, 0, (cudaStream_t)stream>>>(*s, *c, frame, hit, t, nullptr);
     return status_of(cudaGetLastError());
+}
+
+int aokk_select_batch(const BatchParams* p, void* stream) {
+    dim3 grid((p->max_chunks + 127) / 128, p->n_views);
+    select_batch_kernel<<<grid, 128, 0, (cudaStream_t)stream>>>(*p);
+    return status_of(cudaGetLastError());
+}
+
+int aokk_cast_batch(const BatchParams* p, uint32_t ctas, uint32_t threads, void* stream) {
+    cast_persistent<<<ctas, threads, 0, (cudaStream_t)stream>>>(*p);
+    return status_of(cudaGetLastError());
+}
+
+// Run n_groups (select, cast) launch pairs on `stream`.  With a cache, the pairs
+// form one CUDA graph built per shape (group sizes, launch dims) whose kernel
+// nodes are updated with the new parameters on every call.
+int aokk_batch_run(const BatchParams* groups, uint32_t n_groups, uint32_t ctas, uint32_t threads, void* stream,
+                   GraphCache* gc) {
+    const cudaStream_t st = (cudaStream_t)stream;
+    if (!gc) {
+        for (uint32_t g = 0; g < n_groups; g++) {
+            int r = aokk_select_batch(&groups[g], stream);
+            if (!r) r = aokk_cast_batch(&groups[g], ctas, threads, stream);
+            if (r) return r;
+        }
+        return AOK_OK;
+    }
+    std::vector<uint64_t> key{n_groups, ctas, threads};
+    for (uint32_t g = 0; g < n_groups; g++) { key.push_back(groups[g].n_views); key.push_back(groups[g].max_chunks); }
+    auto params = [&](uint32_t g, bool sel, void** argp, cudaKernelNodeParams& kp) {
+        argp[0] = (void*)&groups[g];
+        kp.func = sel ? (void*)select_batch_kernel : (void*)cast_persistent;
+        kp.gridDim = sel ? dim3((groups[g].max_chunks + 127) / 128, groups[g].n_views) : dim3(ctas);
+        kp.blockDim = sel ? dim3(128) : dim3(threads);
+        kp.sharedMemBytes = 0;
+        kp.kernelParams = argp;
+        kp.extra = nullptr;
+    };
+    cudaError_t e = cudaSuccess;
+    if (!gc->exec || gc->key != key) {
+        aokk_graph_destroy(gc);
+        e = cudaGraphCreate(&gc->graph, 0);
+        cudaGraphNode_t prev = nullptr;
+        for (uint32_t g = 0; g < n_groups && e == cudaSuccess; g++) {
+            for (int sel = 1; sel >= 0 && e == cudaSuccess; sel--) {
+                void* argp[1];
+                cudaKernelNodeParams kp;
+                params(g, sel != 0, argp, kp);
+                cudaGraphNode_t node;
+                e = cudaGraphAddKernelNode(&node, gc->graph, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
+                gc->nodes.push_back(node);
+                prev = node;
+            }
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&gc->exec, gc->graph, 0);
+        if (e != cudaSuccess) {
+            aokk_graph_destroy(gc);
+            return AOK_E_CUDA;
+        }
+        gc->key = key;
+    } else {
+        for (uint32_t g = 0; g < n_groups && e == cudaSuccess; g++) {
+            for (int sel = 1; sel >= 0 && e == cudaSuccess; sel--) {
+                void* argp[1];
+                cudaKernelNodeParams kp;
+                params(g, sel != 0, argp, kp);
+                e = cudaGraphExecKernelNodeSetParams(gc->exec, gc->nodes[2 * g + (sel ? 0 : 1)], &kp);
+            }
+        }
+        if (e != cudaSuccess) return AOK_E_CUDA;
+    }
+    return status_of(cudaGraphLaunch(gc->exec, st));
+}
+
+void aokk_graph_destroy(GraphCache* gc) {
+    if (gc->exec) cudaGraphExecDestroy(gc->exec);
+    if (gc->graph) cudaGraphDestroy(gc->graph);
+    gc->exec = nullptr;
+    gc->graph = nullptr;
+    gc->nodes.clear();
+    gc->key.clear();
+}
+
+int aokk_max_ctas_per_sm(uint32_t threads) {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cast_persistent, (int)threads, 0);
+    return n;
 }
 
 int aokk_ray_dirs(const CamDev* c, float* dirs, void* stream) {

@@ -252,7 +252,9 @@ int aok_create(aok_ctx** out, int device, size_t budget) {
         delete ctx;
         return AOK_E_CUDA;
     }
-    if (dev_alloc(ctx, (void**)&ctx->d_counter, sizeof(uint32_t) * 16) != AOK_OK) {
+    if (dev_alloc(ctx, (void**)&ctx->d_counter, sizeof(uint32_t) * 16) != AOK_OK ||
+        dev_alloc(ctx, (void**)&ctx->d_single_queue, 2 * sizeof(unsigned long long)) != AOK_OK ||
+        cudaMemset(ctx->d_single_queue, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) {
         delete ctx;
         return AOK_E_CUDA;
     }
@@ -273,6 +275,7 @@ void aok_destroy(aok_ctx* ctx) {
     dev_free(ctx, ctx->host_hit_dev, ctx->host_frame_px * 16);
     dev_free(ctx, ctx->host_t_dev, ctx->host_frame_px * 4);
     dev_free(ctx, ctx->d_counter, sizeof(uint32_t) * 16);
+    dev_free(ctx, ctx->d_single_queue, 2 * sizeof(unsigned long long));
     if (ctx->staging) cudaFreeHost(ctx->staging);
     if (ctx->pinned_word) cudaFreeHost(ctx->pinned_word);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
@@ -541,8 +544,12 @@ static int render_impl(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, doub
     if (st) return st;
     cudaSetDevice(ctx->device);
     SceneDev sd = scene_dev(sc);
-    st = aokk_select(&sd, &cd, sc->d_frame, nullptr, nullptr, nullptr, stream);
-    if (!st) st = aokk_cast(&sd, &cd, sc->d_frame, (uint4*)frame->hit, frame->t, counts, stream);
+    if (ctx->single_persistent && !counts) {
+        st = render_persistent(ctx, sc, cd, frame, stream, true);
+    } else {
+        st = aokk_select(&sd, &cd, sc->d_frame, nullptr, nullptr, nullptr, stream);
+        if (!st) st = aokk_cast(&sd, &cd, sc->d_frame, (uint4*)frame->hit, frame->t, counts, stream);
+    }
     if (st) return cuda_status(ctx, cudaGetLastError());
     return AOK_OK;
 }
@@ -584,8 +591,15 @@ int aok_cast_selected(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, const
     if (st) return st;
     cudaSetDevice(ctx->device);
     SceneDev sd = scene_dev(sc);
-    st = aokk_cast(&sd, &cd, sc->d_frame, (uint4*)frame->hit, frame->t, nullptr, stream);
+    if (ctx->single_persistent) st = render_persistent(ctx, sc, cd, frame, stream, false);
+    else st = aokk_cast(&sd, &cd, sc->d_frame, (uint4*)frame->hit, frame->t, nullptr, stream);
     return st ? cuda_status(ctx, cudaGetLastError()) : AOK_OK;
+}
+
+int aok_set_single_view_kernel(aok_ctx* ctx, int persistent) {
+    if (!ctx || persistent < 0 || persistent > 1) return AOK_E_INVALID;
+    ctx->single_persistent = persistent;
+    return AOK_OK;
 }
 
 int aok_render_host(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double tau, void* hit_host, float* t_host,

@@ -45,17 +45,14 @@ struct Scene {
     std::mutex mu;
 };
 
-// Device arena of one batch shape (views, frame tables, queue), reused across calls.
+// Device arena of aok_render_batch: per-view frame tables, work counters and
+// the CUDA graph of the last list shape.
 struct BatchArena {
-    ViewDev* d_views = nullptr;
     ChunkRef* d_frames = nullptr;
-    unsigned long long* d_queue = nullptr;
-    size_t views_cap = 0, frames_cap = 0;
-    ViewDev* h_views = nullptr;  // pinned
-    // captured graph for one list shape
-    cudaGraphExec_t exec = nullptr;
-    std::vector<uint64_t> shape;
-    cudaStream_t cap_stream = nullptr;
+    size_t frames_cap = 0;
+    unsigned long long* d_queue = nullptr;  // 2 per group, zero between launches
+    size_t queue_cap = 0;
+    GraphCache graph;
 };
 
 struct ServeState;
@@ -78,8 +75,11 @@ struct aok_ctx {
     size_t staging_cap = 0;
     uint32_t* pinned_word = nullptr;
     uint32_t* d_counter = nullptr;
-    // persistent casting launch shape (0 = defaults)
-    uint32_t ctas_per_sm = 0, threads_per_cta = 0, packet_rays = 0;
+    // persistent casting launch shape (0 = defaults) and single-view kernel choice
+    uint32_t ctas_per_sm = 0, threads_per_cta = 0, packet_rays = 0, tile_w_log = 0;
+    int single_persistent = 0;
+    unsigned long long* d_single_queue = nullptr;  // counters of single-view persistent launches
+    aok::BatchParams single_params;
     aok::BatchArena batch;
     // device frame of aok_render_host
     void* host_hit_dev = nullptr;
@@ -98,4 +98,5 @@ Scene* find_scene(aok_ctx* ctx, uint32_t id);
 int make_cam(aok_ctx* ctx, const Scene* sc, const aok_camera* cam, double tau, CamDev* out);
 SceneDev scene_dev(const Scene* sc);
 void batch_release(aok_ctx* ctx);
+int render_persistent(aok_ctx* ctx, Scene* sc, const CamDev& cd, const aok_frame* frame, void* stream, bool select);
 }  // namespace aok
