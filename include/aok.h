@@ -74,7 +74,9 @@ typedef struct aok_scene_desc {
     int32_t chunk_res;        /* M: LOD-0 voxels per chunk side, power of two in [8, 512] */
     int32_t n_lods;           /* LODs per chunk, 1 <= n_lods and (chunk_res >> (n_lods-1)) >= 8 */
     float view_dist;          /* > 0: hits farther than this (LOD-0 units) are misses; 0 = none */
-    uint64_t node_words;      /* device pool capacities: DAG node words (uint32) ... */
+    uint64_t node_words;      /* pool capacities: DAG node words (uint32, blob format; the device
+                                 layout stores a prefix count beside every child pointer and
+                                 reserves twice this many words) ... */
     uint64_t leaf_count;      /* ... 4x4x4 leaf masks (uint64) ... */
     uint64_t mat_bytes;       /* ... material bytes */
 } aok_scene_desc;

@@ -71,19 +71,6 @@ __device__ __forceinline__ void ray_dir(const CamDev& c, int px, int py, float d
     }
 }
 
-// Mirror a 4x4x4 mask (bit x + 4y + 16z) along the axes set in `mir`.
-__device__ __forceinline__ uint64_t mirror_leaf(uint64_t m, uint32_t mir) {
-    if (mir & 1u)
-        m = ((m & 0x1111111111111111ull) << 3) | ((m & 0x2222222222222222ull) << 1) |
-            ((m >> 1) & 0x2222222222222222ull) | ((m >> 3) & 0x1111111111111111ull);
-    if (mir & 2u)
-        m = ((m & 0x000F000F000F000Full) << 12) | ((m & 0x00F000F000F000F0ull) << 4) |
-            ((m >> 4) & 0x00F000F000F000F0ull) | ((m >> 12) & 0x000F000F000F000Full);
-    if (mir & 4u)
-        m = ((m & 0xFFFFull) << 48) | ((m & 0xFFFF0000ull) << 16) | ((m >> 16) & 0xFFFF0000ull) | (m >> 48);
-    return m;
-}
-
 // Eq. 1 for the octree block b at level n: LODError <= 0 (load), squared, FP64, fixed order.
 __device__ __forceinline__ bool lod_loads(int n, int bx, int by, int bz, int mlog, const float o[3], double sf) {
     const double S = (double)(1ll << (mlog + n));
@@ -161,57 +148,33 @@ __global__ void select_batch_kernel(const __grid_constant__ BatchParams P) {
 }
 
 // ---------------------------------------------------------------------------
-// ray representation for exact comparisons
+// per-chunk DAG traversal in the chunk's mirrored local frame
 // ---------------------------------------------------------------------------
 // FAST rays: the exponents of the non-zero |d| components span <= 6, so the
-// mantissas are shifted to a common exponent (M_a < 2^30) and
-// t_a < t_b  <=>  N_a M_b < N_b M_a  (two 32x32->64 products); a zero
-// component has M = 0, i.e. its crossings lie at +-infinity.
-// Other rays keep (m, E) per axis and use tlt().
-struct Ray {
+// mantissas are shifted to a common exponent (m < 2^30, zero components get
+// m = 0, i.e. crossings at +-infinity) and t_a < t_b <=> N_a m_b < N_b m_a;
+// other rays keep (m, E) per axis and use tlt().
+template <bool FAST>
+__device__ __forceinline__ bool tltf(int32_t N1, int32_t m1, int32_t N2, int32_t m2, int32_t s) {
+    if (FAST) return (long long)N1 * m2 < (long long)N2 * m1;
+    return tlt(N1, m1, N2, m2, s);
+}
+
+// Cells are addressed by level k (side 2^k LOD-0 units) and mirrored integer
+// coordinates c.  Levels R = log2(M) (root) .. n+3 are interior nodes, n+2 a
+// 4x4x4 leaf block, n+1 a 2x2x2 group in it, n a voxel of LOD n.  Leaf bits
+// are addressed in stored (unmirrored) order: along a mirrored axis the index
+// inside a block is c ^ 3 (group: c ^ 1).
+struct RayState {
     float d[3];
-    float inv[3];
+    int32_t m[3], E[3];
     uint32_t mir;
-    int32_t m0, m1, m2;
-    int32_t E0, E1, E2;
 };
 
-template <bool FAST>
-__device__ __forceinline__ bool tless(int32_t N1, int32_t m1, int32_t E1, int32_t N2, int32_t m2, int32_t E2) {
-    if (FAST) return (long long)N1 * m2 < (long long)N2 * m1;
-    return tlt(N1, m1, N2, m2, E2 - E1);
-}
-
-// Returns true if the ray qualifies for the FAST representation.
-__device__ __forceinline__ bool make_ray(const CamDev& C, int px, int py, Ray& r) {
-    ray_dir(C, px, py, r.d);
-    int32_t m[3], E[3];
-    r.mir = 0;
-    int emin = 1 << 20, emax = -(1 << 20);
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-        decompose(r.d[a], m[a], E[a]);
-        if (r.d[a] < 0.0f) r.mir |= 1u << a;
-        r.inv[a] = 1.0f / r.d[a];
-        if (r.d[a] != 0.0f) { emin = min(emin, E[a]); emax = max(emax, E[a]); }
-    }
-    const bool fast = emax - emin <= 6;
-    if (fast) {
-        r.m0 = r.d[0] != 0.0f ? m[0] << (E[0] - emin) : 0;
-        r.m1 = r.d[1] != 0.0f ? m[1] << (E[1] - emin) : 0;
-        r.m2 = r.d[2] != 0.0f ? m[2] << (E[2] - emin) : 0;
-        r.E0 = r.E1 = r.E2 = 0;
-    } else {
-        r.m0 = m[0]; r.m1 = m[1]; r.m2 = m[2];
-        r.E0 = E[0]; r.E1 = E[1]; r.E2 = E[2];
-    }
-    return fast;
-}
-
 struct HitRec {
-    int32_t c0, c1, c2;  // voxel index (mirrored, chunk-local, voxel units of the LOD)
-    int e;               // entry axis (3 = origin inside)
-    int32_t Ne;          // entry plane numerator
+    int32_t c[3];       // voxel index (mirrored, chunk-local, voxel units of the LOD)
+    int e;              // entry axis (3 = origin inside)
+    int32_t Ne;         // entry plane numerator
     uint32_t mat;
 };
 
@@ -219,70 +182,44 @@ struct Counters {
     uint32_t v_int, v_leaf, rbytes;
 };
 
-// axis with the smallest crossing among (N0, N1, N2); updates the entry (Ne, me, Ee)
-template <bool FAST>
-__device__ __forceinline__ int argmin3(const Ray& r, int32_t N0, int32_t N1, int32_t N2, int32_t& Ne, int32_t& me,
-                                       int32_t& Ee) {
-    const bool xy = tless<FAST>(N0, r.m0, r.E0, N1, r.m1, r.E1);
-    const int32_t Na = xy ? N0 : N1, ma = xy ? r.m0 : r.m1, Ea = xy ? r.E0 : r.E1;
-    if (tless<FAST>(Na, ma, Ea, N2, r.m2, r.E2)) {
-        Ne = Na; me = ma; Ee = Ea;
-        return xy ? 0 : 1;
-    }
-    Ne = N2; me = r.m2; Ee = r.E2;
-    return 2;
-}
-
-// ---------------------------------------------------------------------------
-// per-chunk DAG traversal in the chunk's mirrored local frame
-// ---------------------------------------------------------------------------
-// Cells are addressed by level k (cell side 2^k LOD-0 units) and mirrored
-// integer coordinates c.  Levels R = log2(M) (root) .. n+3 are interior nodes,
-// n+2 is a 4x4x4 leaf block, n+1 a 2x2x2 group inside it, n a voxel (LOD n).
-// (e, Ne): the plane through which the current cell was entered (e = 3: the
-// origin lies inside).  Returns true on a hit inside this chunk.
+// Returns true on a hit inside this chunk.  (e, Ne): entry plane into the chunk
+// (e = 3: the origin lies inside the chunk).  Oloc: mirrored local origin numerators.
 template <bool FAST, bool COUNT>
-__device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& ref, const Ray& r, int32_t O0,
-                                            int32_t O1, int32_t O2, int e, int32_t Ne, HitRec& hit, Counters& cnt) {
+__device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& ref, const RayState& r,
+                                            const int32_t Oloc[3], int e, int32_t Ne, HitRec& hit, Counters& cnt) {
     const uint32_t* __restrict__ nodes = S.nodes;
     const int R = S.mlog;
     const int n = (int)ref.lod;
-    uint2 stk[kMaxLevels];  // (node word index, child mask) of the interior node at each level
+    uint32_t sidx[kMaxLevels];
+    uint32_t smask[kMaxLevels];
     int k = R;
     int32_t c0 = 0, c1 = 0, c2 = 0;
     int32_t me = 1, Ee = 0;
-    if (e == 0) { me = r.m0; Ee = r.E0; }
-    else if (e == 1) { me = r.m1; Ee = r.E1; }
-    else if (e == 2) { me = r.m2; Ee = r.E2; }
-    uint32_t pidx = 0, pmask = 0;  // interior node at level k + 1 (parent of the current cell)
-    uint64_t lm = 0, lmu = 0;      // current leaf block: mirrored / as stored
+    if (e < 3) { me = r.m[e]; Ee = r.E[e]; }
+    uint64_t lmu = 0;
+    const int f1 = (r.mir & 1u) ? 1 : 0, f2 = (r.mir & 2u) ? 1 : 0, f4 = (r.mir & 4u) ? 1 : 0;
+    const int g1 = 3 * f1, g2 = 3 * f2, g4 = 3 * f4;
     bool occ = true;
     for (;;) {
         if (occ) {
             if (k == n) {
-                hit.c0 = c0; hit.c1 = c1; hit.c2 = c2;
+                hit.c[0] = c0; hit.c[1] = c1; hit.c[2] = c2;
                 hit.e = e;
                 hit.Ne = Ne;
                 // material through the depth-first index (Sec. 3.3)
+                const uint32_t mirv = r.mir;
                 const int32_t side = (1 << (R - n)) - 1;
-                const int32_t u0 = (r.mir & 1u) ? side - c0 : c0;
-                const int32_t u1 = (r.mir & 2u) ? side - c1 : c1;
-                const int32_t u2 = (r.mir & 4u) ? side - c2 : c2;
+                const int32_t u0 = (mirv & 1u) ? side - c0 : c0;
+                const int32_t u1 = (mirv & 2u) ? side - c1 : c1;
+                const int32_t u2 = (mirv & 4u) ? side - c2 : c2;
+                // node = [hdr, count, (child, earlier siblings' count) x k]: one word per level
                 uint32_t idx = 0;
                 for (int j = R; j >= n + 3; j--) {
-                    const uint2 sj = stk[j];
                     const int sh = j - 1 - n;
                     const int oct = ((u0 >> sh) & 1) | (((u1 >> sh) & 1) << 1) | (((u2 >> sh) & 1) << 2);
-                    const int rk = __popc(sj.y & ((1u << oct) - 1u));
-                    const bool leafkids = (j - 1 == n + 2);
-                    uint32_t ch[7];
-#pragma unroll
-                    for (int q = 0; q < 7; q++) ch[q] = q < rk ? nodes[sj.x + 2 + q] : 0u;
-#pragma unroll
-                    for (int q = 0; q < 7; q++) {
-                        if (q < rk) idx += leafkids ? (uint32_t)__popcll(S.leaves[ch[q]]) : nodes[ch[q] + 1];
-                    }
-                    if (COUNT) cnt.rbytes += rk * (leafkids ? 8u : 4u);
+                    const int rk = __popc(smask[j] & ((1u << oct) - 1u));
+                    idx += nodes[sidx[j] + 3 + 2 * rk];
+                    if (COUNT) cnt.rbytes += rk * ((j - 1 == n + 2) ? 8u : 4u);
                 }
                 const int bit = (u0 & 3) + 4 * (u1 & 3) + 16 * (u2 & 3);
                 idx += (uint32_t)__popcll(lmu & ((1ull << bit) - 1ull));
@@ -296,63 +233,60 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
                     idx = ref.root;
                 } else {
                     const uint32_t oct = ((uint32_t)(c0 & 1) | ((uint32_t)(c1 & 1) << 1) | ((uint32_t)(c2 & 1) << 2)) ^ r.mir;
-                    idx = nodes[pidx + 2 + __popc(pmask & ((1u << oct) - 1u))];
+                    idx = nodes[sidx[k + 1] + 2 + 2 * __popc(smask[k + 1] & ((1u << oct) - 1u))];
                 }
                 if (k >= n + 3) {
-                    pidx = idx;
-                    pmask = nodes[idx] & 0xFFu;
-                    stk[k] = make_uint2(pidx, pmask);
+                    sidx[k] = idx;
+                    smask[k] = nodes[idx] & 0xFFu;
                     if (COUNT) cnt.v_int++;
                 } else {
                     lmu = S.leaves[idx];
-                    lm = mirror_leaf(lmu, r.mir);
                     if (COUNT) cnt.v_leaf++;
                 }
             }
             // child of cell (k, c) holding the entry point: compare t_entry with the mid planes
             const int kk = k - 1;
-            const int32_t mid0 = ((2 * c0 + 1) << (kk + kFix)) - O0;
-            const int32_t mid1 = ((2 * c1 + 1) << (kk + kFix)) - O1;
-            const int32_t mid2 = ((2 * c2 + 1) << (kk + kFix)) - O2;
-            const int32_t b0 = (e != 0) && !tless<FAST>(Ne, me, Ee, mid0, r.m0, r.E0);
-            const int32_t b1 = (e != 1) && !tless<FAST>(Ne, me, Ee, mid1, r.m1, r.E1);
-            const int32_t b2 = (e != 2) && !tless<FAST>(Ne, me, Ee, mid2, r.m2, r.E2);
+            const int32_t mid0 = ((2 * c0 + 1) << (kk + kFix)) - Oloc[0];
+            const int32_t mid1 = ((2 * c1 + 1) << (kk + kFix)) - Oloc[1];
+            const int32_t mid2 = ((2 * c2 + 1) << (kk + kFix)) - Oloc[2];
+            const int32_t b0 = (e != 0) && !tltf<FAST>(Ne, me, mid0, r.m[0], r.E[0] - Ee);
+            const int32_t b1 = (e != 1) && !tltf<FAST>(Ne, me, mid1, r.m[1], r.E[1] - Ee);
+            const int32_t b2 = (e != 2) && !tltf<FAST>(Ne, me, mid2, r.m[2], r.E[2] - Ee);
             c0 = 2 * c0 + b0;
             c1 = 2 * c1 + b1;
             c2 = 2 * c2 + b2;
             k = kk;
         } else {
             // leave cell (k, c) through its nearest exit face
-            const int32_t N0 = ((c0 + 1) << (k + kFix)) - O0;
-            const int32_t N1 = ((c1 + 1) << (k + kFix)) - O1;
-            const int32_t N2 = ((c2 + 1) << (k + kFix)) - O2;
-            e = argmin3<FAST>(r, N0, N1, N2, Ne, me, Ee);
+            const int32_t N0 = ((c0 + 1) << (k + kFix)) - Oloc[0];
+            const int32_t N1 = ((c1 + 1) << (k + kFix)) - Oloc[1];
+            const int32_t N2 = ((c2 + 1) << (k + kFix)) - Oloc[2];
+            const bool xy = tltf<FAST>(N0, r.m[0], N1, r.m[1], r.E[1] - r.E[0]);
+            const int32_t Na = xy ? N0 : N1, ma = xy ? r.m[0] : r.m[1], Ea = xy ? r.E[0] : r.E[1];
+            const bool az = tltf<FAST>(Na, ma, N2, r.m[2], r.E[2] - Ea);
+            int ax;
+            if (az) { ax = xy ? 0 : 1; Ne = Na; me = ma; Ee = Ea; }
+            else { ax = 2; Ne = N2; me = r.m[2]; Ee = r.E[2]; }
+            e = ax;
             int32_t cax;
-            if (e == 0) cax = ++c0;
-            else if (e == 1) cax = ++c1;
+            if (ax == 0) cax = ++c0;
+            else if (ax == 1) cax = ++c1;
             else cax = ++c2;
             if ((cax << k) >= (1 << R)) return false;  // left the chunk
-            if ((cax & 1) == 0) {
-                do {
-                    c0 >>= 1; c1 >>= 1; c2 >>= 1;
-                    cax >>= 1;
-                    k++;
-                } while (k < R && (cax & 1) == 0);
-                if (k >= n + 2) {
-                    const uint2 p = stk[k + 1];
-                    pidx = p.x;
-                    pmask = p.y;
-                }
+            while (k < R && (cax & 1) == 0) {
+                c0 >>= 1; c1 >>= 1; c2 >>= 1;
+                cax >>= 1;
+                k++;
             }
         }
         // occupancy of cell (k, c)
         if (k >= n + 2) {
             const uint32_t oct = ((uint32_t)(c0 & 1) | ((uint32_t)(c1 & 1) << 1) | ((uint32_t)(c2 & 1) << 2)) ^ r.mir;
-            occ = (pmask >> oct) & 1u;
+            occ = (smask[k + 1] >> oct) & 1u;
         } else if (k == n + 1) {
-            occ = (lm & (0x330033ull << ((c0 & 1) * 2 + (c1 & 1) * 8 + (c2 & 1) * 32))) != 0ull;
+            occ = (lmu & (0x330033ull << (((c0 & 1) ^ f1) * 2 + ((c1 & 1) ^ f2) * 8 + ((c2 & 1) ^ f4) * 32))) != 0ull;
         } else {
-            occ = (lm >> ((c0 & 3) + 4 * (c1 & 3) + 16 * (c2 & 3))) & 1ull;
+            occ = (lmu >> (((c0 & 3) ^ g1) + 4 * ((c1 & 3) ^ g2) + 16 * ((c2 & 3) ^ g4))) & 1ull;
         }
     }
 }
@@ -361,109 +295,116 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
 // one pixel: world-grid chunk march + per-chunk DAG traversal
 // ---------------------------------------------------------------------------
 template <bool FAST, bool COUNT>
-__device__ __forceinline__ void trace_ray(const SceneDev& S, const CamDev& C, const ChunkRef* __restrict__ frame,
-                                          const Ray& r, uint4* __restrict__ out_hit, float* __restrict__ out_t,
-                                          uint32_t* __restrict__ counts, size_t pix) {
-    const int cs = S.mlog + kFix;  // chunk side as a shift of numerator units
-    const int32_t G0 = S.grid[0], G1 = S.grid[1], G2 = S.grid[2];
-    const int32_t W0 = G0 << cs, W1 = G1 << cs, W2 = G2 << cs;
-    const int32_t Ow0 = (r.mir & 1u) ? W0 - C.O[0] : C.O[0];
-    const int32_t Ow1 = (r.mir & 2u) ? W1 - C.O[1] : C.O[1];
-    const int32_t Ow2 = (r.mir & 4u) ? W2 - C.O[2] : C.O[2];
+__device__ __forceinline__ void trace_pixel_t(const SceneDev& S, const CamDev& C, const ChunkRef* __restrict__ frame,
+                                            const RayState& r, uint4* __restrict__ out_hit, float* __restrict__ out_t,
+                                            uint32_t* __restrict__ counts, size_t pix) {
+    int32_t Ow[3], Wfix[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        Wfix[a] = S.grid[a] << (S.mlog + kFix);
+        Ow[a] = ((r.mir >> a) & 1u) ? Wfix[a] - C.O[a] : C.O[a];
+    }
     Counters cnt = {0, 0, 0};
     HitRec hit;
     bool found = false;
+    const int cs = S.mlog + kFix;  // chunk side as a shift of numerator units
     int e = 3;
     int32_t Ne = 0, me = 1, Ee = 0;
-    int32_t cc0, cc1, cc2;
+    int32_t cc[3];
     bool alive = true;
-    if (Ow0 >= 0 && Ow1 >= 0 && Ow2 >= 0 && Ow0 < W0 && Ow1 < W1 && Ow2 < W2) {
-        cc0 = Ow0 >> cs; cc1 = Ow1 >> cs; cc2 = Ow2 >> cs;
+    if (Ow[0] >= 0 && Ow[1] >= 0 && Ow[2] >= 0 && Ow[0] < Wfix[0] && Ow[1] < Wfix[1] && Ow[2] < Wfix[2]) {
+#pragma unroll
+        for (int a = 0; a < 3; a++) cc[a] = Ow[a] >> cs;
     } else {
         // enter the world box: latest entry plane vs earliest exit plane
-        if (Ow0 >= W0 || Ow1 >= W1 || Ow2 >= W2 || (r.d[0] == 0.0f && Ow0 < 0) || (r.d[1] == 0.0f && Ow1 < 0) ||
-            (r.d[2] == 0.0f && Ow2 < 0))
-            alive = false;
         e = -1;
-        if (Ow0 < 0) { e = 0; Ne = -Ow0; me = r.m0; Ee = r.E0; }
-        if (Ow1 < 0 && (e < 0 || tless<FAST>(Ne, me, Ee, -Ow1, r.m1, r.E1))) { e = 1; Ne = -Ow1; me = r.m1; Ee = r.E1; }
-        if (Ow2 < 0 && (e < 0 || tless<FAST>(Ne, me, Ee, -Ow2, r.m2, r.E2))) { e = 2; Ne = -Ow2; me = r.m2; Ee = r.E2; }
-        int32_t Nx, mx, Ex;
-        argmin3<FAST>(r, W0 - Ow0, W1 - Ow1, W2 - Ow2, Nx, mx, Ex);
-        if (alive && e >= 0 && tless<FAST>(Ne, me, Ee, Nx, mx, Ex)) {
-            const float te = (float)Ne / fabsf(r.d[e]);
-            const int32_t Ows[3] = {Ow0, Ow1, Ow2};
-            const int32_t Gs[3] = {G0, G1, G2};
-            const int32_t ms[3] = {r.m0, r.m1, r.m2}, Es[3] = {r.E0, r.E1, r.E2};
-            int32_t cc[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            if (Ow[a] >= Wfix[a] || (r.d[a] == 0.0f && Ow[a] < 0)) alive = false;
+            if (Ow[a] < 0) {
+                const int32_t Na = -Ow[a];
+                if (e < 0 || tltf<FAST>(Ne, me, Na, r.m[a], r.E[a] - Ee)) { e = a; Ne = Na; me = r.m[a]; Ee = r.E[a]; }
+            }
+        }
+        int32_t Nx = Wfix[0] - Ow[0], mx = r.m[0], Ex = r.E[0];
+#pragma unroll
+        for (int a = 1; a < 3; a++) {
+            const int32_t Na = Wfix[a] - Ow[a];
+            if (tltf<FAST>(Na, r.m[a], Nx, mx, Ex - r.E[a])) { Nx = Na; mx = r.m[a]; Ex = r.E[a]; }
+        }
+        if (alive && e >= 0 && tltf<FAST>(Ne, me, Nx, mx, Ex - Ee)) {
+            const float te_num = (float)Ne / fabsf(r.d[e]);
 #pragma unroll
             for (int a = 0; a < 3; a++) {
                 if (a == e) { cc[a] = 0; continue; }
-                const float pa = (float)Ows[a] + te * fabsf(r.d[a]);
+                const float pa = (float)Ow[a] + te_num * fabsf(r.d[a]);
                 int32_t cell = (int32_t)floorf(pa * (1.0f / (float)(1 << cs)));
-                cell = max(0, min(cell, Gs[a] - 1));
+                cell = max(0, min(cell, S.grid[a] - 1));
                 // exact correction: cell*M <= x_a(t_entry) < (cell+1)*M
-                while (cell + 1 < Gs[a] && !tless<FAST>(Ne, me, Ee, ((cell + 1) << cs) - Ows[a], ms[a], Es[a])) cell++;
-                while (cell > 0 && tless<FAST>(Ne, me, Ee, (cell << cs) - Ows[a], ms[a], Es[a])) cell--;
+                while (cell + 1 < S.grid[a] && !tltf<FAST>(Ne, me, ((cell + 1) << cs) - Ow[a], r.m[a], r.E[a] - Ee)) cell++;
+                while (cell > 0 && tltf<FAST>(Ne, me, (cell << cs) - Ow[a], r.m[a], r.E[a] - Ee)) cell--;
                 cc[a] = cell;
             }
-            cc0 = cc[0]; cc1 = cc[1]; cc2 = cc[2];
         } else {
             alive = false;
-            cc0 = cc1 = cc2 = 0;
         }
     }
-    const float dn = sqrtf(__fadd_rn(__fadd_rn(__fmul_rn(r.d[0], r.d[0]), __fmul_rn(r.d[1], r.d[1])),
-                                     __fmul_rn(r.d[2], r.d[2])));
+    const float dn = sqrtf(__fadd_rn(__fadd_rn(__fmul_rn(r.d[0], r.d[0]), __fmul_rn(r.d[1], r.d[1])), __fmul_rn(r.d[2], r.d[2])));
+    float inv[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) inv[a] = 1.0f / r.d[a];
     while (alive) {
-        const int32_t u0 = (r.mir & 1u) ? G0 - 1 - cc0 : cc0;
-        const int32_t u1 = (r.mir & 2u) ? G1 - 1 - cc1 : cc1;
-        const int32_t u2 = (r.mir & 4u) ? G2 - 1 - cc2 : cc2;
-        const ChunkRef ref = frame[(size_t)u0 + (size_t)G0 * ((size_t)u1 + (size_t)G1 * u2)];
+        int32_t u[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) u[a] = ((r.mir >> a) & 1u) ? S.grid[a] - 1 - cc[a] : cc[a];
+        const ChunkRef ref = frame[(size_t)u[0] + (size_t)S.grid[0] * ((size_t)u[1] + (size_t)S.grid[1] * u[2])];
         if (S.view_dist > 0.0f && e < 3) {
-            const float de = e == 0 ? r.d[0] : (e == 1 ? r.d[1] : r.d[2]);
-            const float tent = (float)Ne / (4096.0f * fabsf(de));
+            const float tent = (float)Ne / (4096.0f * fabsf(r.d[e]));
             if (tent * dn > S.view_dist * 1.00001f + 1.0f) break;
         }
         if (ref.root != kNone) {
             // skip chunks whose solid-voxel AABB (grown by 1/16 voxel) the ray misses
             float tn = 0.0f, tf = 3.0e38f;
             bool pass = true;
-            const int32_t us[3] = {u0, u1, u2};
 #pragma unroll
             for (int a = 0; a < 3; a++) {
-                const float lo = (float)((us[a] << S.mlog) + ref.aabb[a]) - 0.0625f;
-                const float hi = (float)((us[a] << S.mlog) + ref.aabb[3 + a]) + 0.0625f;
+                const float lo = (float)((u[a] << S.mlog) + ref.aabb[a]) - 0.0625f;
+                const float hi = (float)((u[a] << S.mlog) + ref.aabb[3 + a]) + 0.0625f;
                 if (r.d[a] == 0.0f) {
                     if (C.of[a] < lo || C.of[a] > hi) pass = false;
                 } else {
-                    const float t1 = (lo - C.of[a]) * r.inv[a], t2 = (hi - C.of[a]) * r.inv[a];
+                    float t1 = (lo - C.of[a]) * inv[a], t2 = (hi - C.of[a]) * inv[a];
                     tn = fmaxf(tn, fminf(t1, t2));
                     tf = fminf(tf, fmaxf(t1, t2));
                 }
             }
             if (pass && tn <= tf) {
-                if (trace_chunk<FAST, COUNT>(S, ref, r, Ow0 - (cc0 << cs), Ow1 - (cc1 << cs), Ow2 - (cc2 << cs), e, Ne,
-                                             hit, cnt)) {
+                int32_t Oloc[3];
+#pragma unroll
+                for (int a = 0; a < 3; a++) Oloc[a] = Ow[a] - (cc[a] << cs);
+                if (trace_chunk<FAST, COUNT>(S, ref, r, Oloc, e, Ne, hit, cnt)) {
                     found = true;
                     // un-mirror the voxel index to world LOD-0 units
                     const int n = (int)ref.lod;
                     const int32_t side = (1 << (S.mlog - n)) - 1;
-                    const int32_t w0 = (u0 << S.mlog) + (((r.mir & 1u) ? side - hit.c0 : hit.c0) << n);
-                    const int32_t w1 = (u1 << S.mlog) + (((r.mir & 2u) ? side - hit.c1 : hit.c1) << n);
-                    const int32_t w2 = (u2 << S.mlog) + (((r.mir & 4u) ? side - hit.c2 : hit.c2) << n);
+                    int32_t wxyz[3];
+#pragma unroll
+                    for (int a = 0; a < 3; a++) {
+                        const int32_t uv = ((r.mir >> a) & 1u) ? side - hit.c[a] : hit.c[a];
+                        wxyz[a] = (u[a] << S.mlog) + (uv << n);
+                    }
                     float dist = 0.0f;
-                    if (hit.e < 3) {
-                        const float de = hit.e == 0 ? r.d[0] : (hit.e == 1 ? r.d[1] : r.d[2]);
-                        dist = __fdiv_rn((float)hit.Ne * (1.0f / 4096.0f), fabsf(de)) * dn;
-                        if (S.view_dist > 0.0f) {
+                    if (hit.e < 3) dist = __fdiv_rn((float)hit.Ne * (1.0f / 4096.0f), fabsf(r.d[hit.e])) * dn;
+                    if (S.view_dist > 0.0f) {
+                        double dd = 0.0;
+                        if (hit.e < 3) {
                             const double d0 = r.d[0], d1 = r.d[1], d2 = r.d[2];
-                            const double dd = (double)hit.Ne / (4096.0 * fabs((double)de)) * sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-                            if (dd > (double)S.view_dist) { found = false; break; }
+                            dd = (double)hit.Ne / (4096.0 * fabs((double)r.d[hit.e])) * sqrt(d0 * d0 + d1 * d1 + d2 * d2);
                         }
+                        if (dd > (double)S.view_dist) { found = false; break; }
                     }
                     const uint32_t normal = hit.e == 3 ? 7u : (uint32_t)(2 * hit.e) + ((r.mir >> hit.e) & 1u);
-                    out_hit[pix] = make_uint4((uint32_t)w0, (uint32_t)w1, (uint32_t)w2,
+                    out_hit[pix] = make_uint4((uint32_t)wxyz[0], (uint32_t)wxyz[1], (uint32_t)wxyz[2],
                                               (uint32_t)n | (hit.mat << 8) | (normal << 16) | (1u << 19));
                     out_t[pix] = dist;
                     break;
@@ -471,10 +412,17 @@ __device__ __forceinline__ void trace_ray(const SceneDev& S, const CamDev& C, co
             }
         }
         // next chunk cell
-        e = argmin3<FAST>(r, ((cc0 + 1) << cs) - Ow0, ((cc1 + 1) << cs) - Ow1, ((cc2 + 1) << cs) - Ow2, Ne, me, Ee);
-        if (e == 0) { if (++cc0 >= G0) break; }
-        else if (e == 1) { if (++cc1 >= G1) break; }
-        else { if (++cc2 >= G2) break; }
+        const int32_t N0 = ((cc[0] + 1) << cs) - Ow[0];
+        const int32_t N1 = ((cc[1] + 1) << cs) - Ow[1];
+        const int32_t N2 = ((cc[2] + 1) << cs) - Ow[2];
+        const bool xy = tltf<FAST>(N0, r.m[0], N1, r.m[1], r.E[1] - r.E[0]);
+        const int32_t Na = xy ? N0 : N1, ma = xy ? r.m[0] : r.m[1], Ea = xy ? r.E[0] : r.E[1];
+        const bool az = tltf<FAST>(Na, ma, N2, r.m[2], r.E[2] - Ea);
+        int ax;
+        if (az) { ax = xy ? 0 : 1; Ne = Na; me = ma; Ee = Ea; }
+        else { ax = 2; Ne = N2; me = r.m[2]; Ee = r.E[2]; }
+        e = ax;
+        if (++cc[ax] >= S.grid[ax]) break;
     }
     if (!found) {
         out_hit[pix] = make_uint4(0u, 0u, 0u, 0xFFu | (7u << 16));
@@ -491,10 +439,25 @@ template <bool COUNT>
 __device__ __forceinline__ void trace_pixel(const SceneDev& S, const CamDev& C, const ChunkRef* __restrict__ frame,
                                             int px, int py, uint4* __restrict__ out_hit, float* __restrict__ out_t,
                                             uint32_t* __restrict__ counts, size_t pix) {
-    Ray r;
-    if (make_ray(C, px, py, r)) trace_ray<true, COUNT>(S, C, frame, r, out_hit, out_t, counts, pix);
-    else trace_ray<false, COUNT>(S, C, frame, r, out_hit, out_t, counts, pix);
+    RayState r;
+    ray_dir(C, px, py, r.d);
+    r.mir = 0;
+    int emin = 1 << 20, emax = -(1 << 20);
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        decompose(r.d[a], r.m[a], r.E[a]);
+        if (r.d[a] < 0.0f) r.mir |= 1u << a;
+        if (r.d[a] != 0.0f) { emin = min(emin, r.E[a]); emax = max(emax, r.E[a]); }
+    }
+    if (emax - emin <= 6) {
+#pragma unroll
+        for (int a = 0; a < 3; a++) { r.m[a] = r.d[a] != 0.0f ? r.m[a] << (r.E[a] - emin) : 0; r.E[a] = 0; }
+        trace_pixel_t<true, COUNT>(S, C, frame, r, out_hit, out_t, counts, pix);
+    } else {
+        trace_pixel_t<false, COUNT>(S, C, frame, r, out_hit, out_t, counts, pix);
+    }
 }
+
 
 // 16 x 8 pixel tiles, warps of 8 x 4 pixels
 template <bool COUNT>

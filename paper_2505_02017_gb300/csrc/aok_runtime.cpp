@@ -165,14 +165,12 @@ SceneDev scene_dev(const Scene* sc) {
 // ---------------------------------------------------------------------------
 // blob validation + rebasing (host)
 // ---------------------------------------------------------------------------
-static int validate_blob(const aok_chunk_blob* b, int res, int M, uint32_t node_base, uint32_t leaf_base,
-                         uint32_t* out) {
+static int validate_blob(const aok_chunk_blob* b, int res, int M) {
     const uint64_t nw = b->n_node_words;
     if (nw == 0) return (b->n_leaves == 0 && b->n_mats == 0) ? AOK_OK : AOK_E_CORRUPT;
     if (!b->nodes || b->root >= nw || (b->n_leaves && !b->leaves) || (b->n_mats && !b->mats)) return AOK_E_CORRUPT;
     if (nw > 0xFFFFFFFFull || b->n_leaves > 0xFFFFFFFFull) return AOK_E_CORRUPT;
     const int n_int = ilog2i(res) - 2;
-    std::memcpy(out, b->nodes, nw * sizeof(uint32_t));
     std::vector<int8_t> depth(nw, -1);
     std::vector<std::pair<uint32_t, int>> st;
     st.emplace_back(b->root, 0);
@@ -196,12 +194,10 @@ static int validate_blob(const aok_chunk_blob* b, int res, int M, uint32_t node_
             if (leafkids) {
                 if (ch >= b->n_leaves || b->leaves[ch] == 0) return AOK_E_CORRUPT;
                 sum += (uint64_t)__builtin_popcountll(b->leaves[ch]);
-                out[node + 2 + i] = ch + leaf_base;
             } else {
                 if ((uint64_t)ch + 2 > nw) return AOK_E_CORRUPT;
                 sum += b->nodes[ch + 1];
                 st.emplace_back(ch, d + 1);
-                out[node + 2 + i] = ch + node_base;
             }
         }
         if (sum != b->nodes[node + 1]) return AOK_E_CORRUPT;
@@ -210,6 +206,61 @@ static int validate_blob(const aok_chunk_blob* b, int res, int M, uint32_t node_
     for (int a = 0; a < 3; a++)
         if (b->aabb_lo[a] < 0 || b->aabb_hi[a] > M || b->aabb_lo[a] >= b->aabb_hi[a]) return AOK_E_CORRUPT;
     return AOK_OK;
+}
+
+// Device layout of a validated blob: every node reachable from the root,
+// in ascending blob order, as [header, count, (child, prefix) x k] where
+// prefix = summed counts of the earlier children, so that the depth-first
+// index of a voxel needs one word per level instead of every earlier
+// sibling's count.  Child pointers are rebased (node_base: device word
+// offset of this chunk's nodes, leaf_base: of its leaves).  Returns the
+// word count; with out == nullptr only sizes are computed.
+static uint64_t layout_blob(const aok_chunk_blob* b, int res, uint32_t node_base, uint32_t leaf_base, uint32_t* out,
+                            uint32_t* root_out) {
+    const uint64_t nw = b->n_node_words;
+    if (!nw) return 0;
+    const int n_int = ilog2i(res) - 2;
+    std::vector<int8_t> depth(nw, -1);
+    std::vector<uint32_t> st{b->root};
+    depth[b->root] = 0;
+    while (!st.empty()) {
+        const uint32_t node = st.back();
+        st.pop_back();
+        if (depth[node] == n_int - 1) continue;
+        const int k = __builtin_popcount(b->nodes[node]);
+        for (int i = 0; i < k; i++) {
+            const uint32_t ch = b->nodes[node + 2 + i];
+            if (depth[ch] < 0) {
+                depth[ch] = (int8_t)(depth[node] + 1);
+                st.push_back(ch);
+            }
+        }
+    }
+    std::vector<uint32_t> off(out ? nw : 0, 0);
+    uint64_t w = 0;
+    for (uint64_t i = 0; i < nw; i++) {
+        if (depth[i] < 0) continue;
+        if (out) off[i] = (uint32_t)w;
+        w += 2 + 2 * (uint64_t)__builtin_popcount(b->nodes[i]);
+    }
+    if (!out) return w;
+    for (uint64_t i = 0; i < nw; i++) {
+        if (depth[i] < 0) continue;
+        const uint32_t hdr = b->nodes[i], o = off[i];
+        const int k = __builtin_popcount(hdr);
+        const bool leafkids = depth[i] == n_int - 1;
+        out[o] = hdr;
+        out[o + 1] = b->nodes[i + 1];
+        uint32_t pre = 0;
+        for (int c = 0; c < k; c++) {
+            const uint32_t ch = b->nodes[i + 2 + c];
+            out[o + 2 + 2 * c] = leafkids ? ch + leaf_base : off[ch] + node_base;
+            out[o + 3 + 2 * c] = pre;
+            pre += leafkids ? (uint32_t)__builtin_popcountll(b->leaves[ch]) : b->nodes[ch + 1];
+        }
+    }
+    *root_out = off[b->root] + node_base;
+    return w;
 }
 
 // ---------------------------------------------------------------------------
@@ -296,13 +347,13 @@ int aok_scene_create(aok_ctx* ctx, const aok_scene_desc* d, uint32_t* scene_id) 
     if (M < 8 || M > 512 || (M & (M - 1)) || d->n_lods < 1 || (M >> (d->n_lods - 1)) < 8) return AOK_E_INVALID;
     for (int a = 0; a < 3; a++)
         if (d->grid[a] < 1 || (int64_t)d->grid[a] * M > 131072) return AOK_E_INVALID;
-    if (d->node_words > 0xFFFFFFFFull || d->leaf_count > 0xFFFFFFFFull || !(d->view_dist >= 0.0f)) return AOK_E_INVALID;
+    if (d->node_words > 0x7FFFFFFFull || d->leaf_count > 0xFFFFFFFFull || !(d->view_dist >= 0.0f)) return AOK_E_INVALID;
     cudaSetDevice(ctx->device);
     Scene* sc = new Scene();
     sc->desc = *d;
     sc->mlog = ilog2i(M);
     sc->n_chunks = (int64_t)d->grid[0] * d->grid[1] * d->grid[2];
-    sc->nodes.cap = std::max<uint64_t>(d->node_words, 1);
+    sc->nodes.cap = std::max<uint64_t>(2 * d->node_words, 2);  // device layout: (child, prefix) pairs
     sc->leaves.cap = std::max<uint64_t>(d->leaf_count, 1);
     sc->mats.cap = std::max<uint64_t>(d->mat_bytes, 1);
     const size_t ndesc = (size_t)sc->n_chunks * d->n_lods;
@@ -386,8 +437,13 @@ int aok_scene_upload_chunk(aok_ctx* ctx, uint32_t scene, int32_t cx, int32_t cy,
     cudaSetDevice(ctx->device);
     std::lock_guard<std::mutex> g(sc->mu);
     const int M = sc->desc.chunk_res, res = M >> lod;
-    const uint64_t nw = blob->n_node_words;
-    // staging: rebased node words + leaves + mats, 16-byte aligned segments
+    const uint64_t nw_blob = blob->n_node_words;
+    // 1. validate before touching anything: a rejected blob changes nothing
+    st = validate_blob(blob, res, M);
+    if (st) return st;
+    uint32_t droot = 0;
+    const uint64_t nw = layout_blob(blob, res, 0, 0, nullptr, &droot);  // device words (even)
+    // staging: laid-out node words + leaves + mats, 16-byte aligned segments
     const size_t nb = (nw * 4 + 15) & ~(size_t)15, lb = (blob->n_leaves * 8 + 15) & ~(size_t)15;
     const size_t need = nb + lb + blob->n_mats + 16;
     if (need > ctx->staging_cap) {
@@ -402,9 +458,7 @@ int aok_scene_upload_chunk(aok_ctx* ctx, uint32_t scene, int32_t cx, int32_t cy,
         ctx->staging_cap = cap;
     }
     uint8_t* stg = (uint8_t*)ctx->staging;
-    // 1. validate before touching anything: a rejected blob changes nothing
-    st = validate_blob(blob, res, M, 0, 0, (uint32_t*)stg);
-    if (st) return st;
+    (void)nw_blob;
     // 2. allocate; if the pools are too full, evict the previous upload of this
     //    (chunk, lod) first (after the GPU is idle) and retry
     ChunkAlloc& old = sc->alloc[di];
@@ -443,8 +497,8 @@ int aok_scene_upload_chunk(aok_ctx* ctx, uint32_t scene, int32_t cx, int32_t cy,
         evict_old();
         if (!try_alloc(a)) return AOK_E_OOM;
     }
-    // 3. rebase the (valid) blob onto its pool offsets
-    validate_blob(blob, res, M, (uint32_t)a.node_off, (uint32_t)a.leaf_off, (uint32_t*)stg);
+    // 3. lay the (valid) blob out at its pool offsets
+    layout_blob(blob, res, (uint32_t)a.node_off, (uint32_t)a.leaf_off, (uint32_t*)stg, &droot);
     ChunkRef ref;
     std::memset(&ref, 0, sizeof(ref));
     ref.root = kNone;
@@ -464,7 +518,7 @@ int aok_scene_upload_chunk(aok_ctx* ctx, uint32_t scene, int32_t cx, int32_t cy,
             free_alloc(sc, a);
             return cuda_status(ctx, e);
         }
-        ref.root = (uint32_t)a.node_off + blob->root;
+        ref.root = droot;
         ref.mat_base = a.mat_off;
         for (int i = 0; i < 3; i++) {
             ref.aabb[i] = (uint16_t)blob->aabb_lo[i];
@@ -483,9 +537,8 @@ int aok_scene_upload_chunk(aok_ctx* ctx, uint32_t scene, int32_t cx, int32_t cy,
 
 int aok_validate_chunk(const aok_chunk_blob* blob, int32_t M, uint32_t lod) {
     if (!blob || M < 8 || M > 512 || (M & (M - 1)) || lod > 6 || (M >> lod) < 8) return AOK_E_INVALID;
-    std::vector<uint32_t> tmp(std::max<uint64_t>(blob->n_node_words, 1));
     if (blob->n_node_words > (1ull << 32)) return AOK_E_CORRUPT;
-    return validate_blob(blob, M >> lod, M, 0, 0, tmp.data());
+    return validate_blob(blob, M >> lod, M);
 }
 
 int aok_scene_evict_chunk(aok_ctx* ctx, uint32_t scene, int32_t cx, int32_t cy, int32_t cz, uint32_t lod) {
