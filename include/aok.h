@@ -223,16 +223,24 @@ typedef struct aok_view {
 } aok_view;
 
 /* Render n views (any scenes, uneven resolutions) with one selection launch
- * and one persistent casting launch that pulls ray packets from a global
- * queue across all views.  The same list shape (n and every width/height)
- * replays a CUDA graph captured on first use.  Results equal n separate
- * aok_render calls.  AOK_E_INVALID if n is 0 or above 4096. */
+ * and one casting launch per group of up to 128 views: by default a grid
+ * over the block tiles (2x2 warp tiles) of all views, scheduled by the
+ * hardware; optionally (aok_set_batch_kernel) a persistent kernel whose warps
+ * pull warp tiles from a global counter.  The launches of one list shape (n,
+ * scenes, sizes) form a CUDA graph built on first use and updated in place.
+ * Results equal n separate aok_render calls.  Calls on one context are
+ * serialised by the caller (one stream).  AOK_E_INVALID if n is 0 or above
+ * 4096. */
 int aok_render_batch(aok_ctx* ctx, const aok_view* views, uint32_t n, void* stream);
 
+/* 0: batches use the grid launch (default); 1: the persistent kernel. */
+int aok_set_batch_kernel(aok_ctx* ctx, int persistent);
 /* Launch shape of the persistent casting kernel (0 = keep current):
  * CTAs per SM, threads per CTA (multiple of 32), rays per packet (multiple
- * of 32).  aok_autotune times candidate shapes on the given views and keeps
- * the fastest; *best_ms receives its time per batch. */
+ * of 32).  aok_autotune times grid launches (three warp tiles) and
+ * persistent shapes on the given views and keeps the fastest; *best_ms
+ * receives its time per batch.  aok_get_launch reports 0 CTAs per SM while
+ * the grid launch is selected. */
 int aok_set_launch(aok_ctx* ctx, uint32_t ctas_per_sm, uint32_t threads_per_cta, uint32_t packet_rays);
 int aok_get_launch(aok_ctx* ctx, uint32_t* ctas_per_sm, uint32_t* threads_per_cta, uint32_t* packet_rays);
 int aok_autotune(aok_ctx* ctx, const aok_view* views, uint32_t n, void* stream, float* best_ms);

@@ -93,6 +93,7 @@ def lib() -> ctypes.CDLL:
             "aok_get_launch": [vp, P(u32), P(u32), P(u32)],
             "aok_autotune": [vp, P(View), u32, vp, P(ctypes.c_float)],
             "aok_set_tile": [vp, u32],
+            "aok_set_batch_kernel": [vp, ctypes.c_int],
             "aok_set_single_view_kernel": [vp, ctypes.c_int],
             "aok_serve_start": [vp, u32, u32, u32],
             "aok_serve_stop": [vp],
@@ -388,6 +389,10 @@ def get_launch(ctx: Context):
 
 def set_tile(ctx: Context, tile_w: int):
     return check(lib().aok_set_tile(ctx.h, tile_w), "aok_set_tile")
+
+
+def set_batch_kernel(ctx: Context, persistent: bool):
+    return check(lib().aok_set_batch_kernel(ctx.h, int(persistent)), "aok_set_batch_kernel")
 
 
 def set_single_view_kernel(ctx: Context, persistent: bool):

@@ -521,6 +521,30 @@ __global__ void __launch_bounds__(256) cast_persistent(const __grid_constant__ B
     }
 }
 
+// One launch over all views of a batch, scheduled by the hardware: block b
+// covers block tile b of the concatenated views, a block tile being 2x2 warp
+// tiles (2^tile_w_log x 32/2^tile_w_log pixels each); P.v[v].tile_begin is the
+// exclusive prefix sum of the views' block-tile counts.  The view index derives
+// from blockIdx only, so every per-view parameter load is block-uniform.
+__global__ void __launch_bounds__(128) cast_grid(const __grid_constant__ BatchParams P) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t blk = blockIdx.x;
+    uint32_t lo = 0, hi = P.n_views - 1;  // last view with tile_begin <= blk
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (P.v[mid].tile_begin <= blk) lo = mid;
+        else hi = mid - 1;
+    }
+    const ViewDev& v = P.v[lo];
+    const int twl = P.tile_w_log, tw = 1 << twl, th = 32 >> twl;
+    const int bw = (v.cam.W + 2 * tw - 1) / (2 * tw);
+    const int32_t local = (int32_t)(blk - v.tile_begin);
+    const int px = (local % bw) * 2 * tw + (warp & 1) * tw + (lane & (tw - 1));
+    const int py = (local / bw) * 2 * th + (warp >> 1) * th + (lane >> twl);
+    if (px < v.cam.W && py < v.cam.H)
+        trace_pixel<false>(v.scene, v.cam, v.frame, px, py, v.hit, v.t, nullptr, (size_t)py * v.cam.W + px);
+}
+
 __global__ void ray_dirs_kernel(CamDev C, float* __restrict__ dirs) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= C.W * C.H) return;
@@ -561,7 +585,10 @@ int aokk_select_batch(const BatchParams* p, void* stream) {
 }
 
 int aokk_cast_batch(const BatchParams* p, uint32_t ctas, uint32_t threads, void* stream) {
-    cast_persistent<<<ctas, threads, 0, (cudaStream_t)stream>>>(*p);
+    if (ctas == 0)  // grid launch: one 128-thread block per block tile
+        cast_grid<<<(unsigned)p->total_tiles, 128, 0, (cudaStream_t)stream>>>(*p);
+    else
+        cast_persistent<<<ctas, threads, 0, (cudaStream_t)stream>>>(*p);
     return status_of(cudaGetLastError());
 }
 
@@ -580,12 +607,17 @@ int aokk_batch_run(const BatchParams* groups, uint32_t n_groups, uint32_t ctas, 
         return AOK_OK;
     }
     std::vector<uint64_t> key{n_groups, ctas, threads};
-    for (uint32_t g = 0; g < n_groups; g++) { key.push_back(groups[g].n_views); key.push_back(groups[g].max_chunks); }
+    for (uint32_t g = 0; g < n_groups; g++) {
+        key.push_back(groups[g].n_views);
+        key.push_back(groups[g].max_chunks);
+        if (!ctas) key.push_back(groups[g].total_tiles);  // grid size of the casting node
+    }
     auto params = [&](uint32_t g, bool sel, void** argp, cudaKernelNodeParams& kp) {
         argp[0] = (void*)&groups[g];
-        kp.func = sel ? (void*)select_batch_kernel : (void*)cast_persistent;
-        kp.gridDim = sel ? dim3((groups[g].max_chunks + 127) / 128, groups[g].n_views) : dim3(ctas);
-        kp.blockDim = sel ? dim3(128) : dim3(threads);
+        kp.func = sel ? (void*)select_batch_kernel : (ctas ? (void*)cast_persistent : (void*)cast_grid);
+        kp.gridDim = sel ? dim3((groups[g].max_chunks + 127) / 128, groups[g].n_views)
+                         : dim3(ctas ? ctas : (unsigned)groups[g].total_tiles);
+        kp.blockDim = sel ? dim3(128) : dim3(ctas ? threads : 128);
         kp.sharedMemBytes = 0;
         kp.kernelParams = argp;
         kp.extra = nullptr;

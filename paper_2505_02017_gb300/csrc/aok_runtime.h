@@ -78,6 +78,7 @@ struct aok_ctx {
     // persistent casting launch shape (0 = defaults) and single-view kernel choice
     uint32_t ctas_per_sm = 0, threads_per_cta = 0, packet_rays = 0, tile_w_log = 0;
     int single_persistent = 0;
+    int batch_persistent = 0;  // 0: batches cast with one grid launch over block tiles
     unsigned long long* d_single_queue = nullptr;  // counters of single-view persistent launches
     aok::BatchParams single_params;
     aok::BatchArena batch;

@@ -17,11 +17,18 @@ namespace aok {
 // launch shape
 // ---------------------------------------------------------------------------
 struct LaunchShape {
-    uint32_t ctas, threads, per_fetch, tile_w_log;
+    uint32_t ctas, threads, per_fetch, tile_w_log;  // ctas == 0: grid launch over block tiles
 };
 
 static LaunchShape launch_shape(aok_ctx* ctx) {
     LaunchShape L;
+    if (!ctx->batch_persistent) {
+        L.ctas = 0;
+        L.threads = 128;
+        L.per_fetch = 1;
+        L.tile_w_log = ctx->tile_w_log ? ctx->tile_w_log : 3;
+        return L;
+    }
     L.threads = ctx->threads_per_cta ? ctx->threads_per_cta : 256;
     int occ = aokk_max_ctas_per_sm(L.threads);
     if (occ < 1) occ = 1;
@@ -30,6 +37,14 @@ static LaunchShape launch_shape(aok_ctx* ctx) {
     L.per_fetch = ctx->packet_rays ? std::max<uint32_t>(1, ctx->packet_rays / 32) : 1;
     L.tile_w_log = ctx->tile_w_log ? ctx->tile_w_log : 3;
     return L;
+}
+
+// Work units of one view: warp tiles (persistent kernel) or block tiles of
+// 2x2 warp tiles (grid launch).
+static uint64_t view_tiles(const LaunchShape& L, int W, int H) {
+    uint32_t tw = 1u << L.tile_w_log, th = 32u >> L.tile_w_log;
+    if (!L.ctas) { tw *= 2; th *= 2; }
+    return (uint64_t)((W + tw - 1) / tw) * (uint64_t)((H + th - 1) / th);
 }
 
 // ---------------------------------------------------------------------------
@@ -49,7 +64,6 @@ static int prepare_batch(aok_ctx* ctx, const aok_view* views, uint32_t n, ChunkR
     const uint32_t ngroups = (n + kBatchViews - 1) / kBatchViews;
     out.groups.resize(ngroups);
     size_t foff = 0;
-    const uint32_t tw = 1u << L.tile_w_log, th = 32u >> L.tile_w_log;
     for (uint32_t g = 0; g < ngroups; g++) {
         BatchParams& P = out.groups[g];
         std::memset(&P, 0, sizeof(P));
@@ -77,7 +91,7 @@ static int prepare_batch(aok_ctx* ctx, const aok_view* views, uint32_t n, ChunkR
             d.hit = (uint4*)v.frame.hit;
             d.t = v.frame.t;
             d.tile_begin = tiles;
-            tiles += (uint64_t)((v.cam.width + tw - 1) / tw) * (uint64_t)((v.cam.height + th - 1) / th);
+            tiles += view_tiles(L, v.cam.width, v.cam.height);
             P.max_chunks = std::max<uint32_t>(P.max_chunks, (uint32_t)sc->n_chunks);
         }
         P.total_tiles = tiles;
@@ -155,8 +169,7 @@ int render_persistent(aok_ctx* ctx, Scene* sc, const CamDev& cd, const aok_frame
     d.hit = (uint4*)frame->hit;
     d.t = frame->t;
     d.tile_begin = 0;
-    const uint32_t tw = 1u << L.tile_w_log, th = 32u >> L.tile_w_log;
-    P->total_tiles = (uint64_t)((cd.W + tw - 1) / tw) * (uint64_t)((cd.H + th - 1) / th);
+    P->total_tiles = view_tiles(L, cd.W, cd.H);
     if (select) {
         st = aokk_select_batch(P, stream);
         if (st) return st;
@@ -310,7 +323,6 @@ static void serve_loop(aok_ctx* ctx) {
         int rc = AOK_OK;
         {
             std::lock_guard<std::mutex> g(S.mu);
-            const uint32_t tw = 1u << L.tile_w_log, th = 32u >> L.tile_w_log;
             for (uint32_t gi = 0; gi < ngroups && rc == AOK_OK; gi++) {
                 BatchParams& P = S.params[gi];
                 std::memset(&P, 0, sizeof(P));
@@ -331,7 +343,7 @@ static void serve_loop(aok_ctx* ctx) {
                     d.hit = (uint4*)t.hit;
                     d.t = t.t;
                     d.tile_begin = tiles;
-                    tiles += (uint64_t)((t.req.cam.width + tw - 1) / tw) * (uint64_t)((t.req.cam.height + th - 1) / th);
+                    tiles += view_tiles(L, t.req.cam.width, t.req.cam.height);
                     P.max_chunks = std::max<uint32_t>(P.max_chunks, (uint32_t)sc->n_chunks);
                 }
                 P.total_tiles = tiles;
@@ -387,7 +399,7 @@ int aok_set_launch(aok_ctx* ctx, uint32_t ctas_per_sm, uint32_t threads_per_cta,
 int aok_get_launch(aok_ctx* ctx, uint32_t* ctas_per_sm, uint32_t* threads_per_cta, uint32_t* packet_rays) {
     if (!ctx) return AOK_E_INVALID;
     const LaunchShape L = launch_shape(ctx);
-    if (ctas_per_sm) *ctas_per_sm = L.ctas / (uint32_t)std::max(1, ctx->sm_count);
+    if (ctas_per_sm) *ctas_per_sm = L.ctas / (uint32_t)std::max(1, ctx->sm_count);  // 0: grid launch
     if (threads_per_cta) *threads_per_cta = L.threads;
     if (packet_rays) *packet_rays = 32 * L.per_fetch;
     return AOK_OK;
@@ -401,55 +413,64 @@ int aok_set_tile(aok_ctx* ctx, uint32_t tile_w) {
     return AOK_OK;
 }
 
+int aok_set_batch_kernel(aok_ctx* ctx, int persistent) {
+    if (!ctx || persistent < 0 || persistent > 1) return AOK_E_INVALID;
+    ctx->batch_persistent = persistent;
+    return AOK_OK;
+}
+
 int aok_autotune(aok_ctx* ctx, const aok_view* views, uint32_t n, void* stream, float* best_ms) {
     if (!ctx || !views || !n) return AOK_E_INVALID;
     cudaSetDevice(ctx->device);
+    struct Cand { int persistent; uint32_t per_sm, threads, packet, twl; };
+    std::vector<Cand> cands;
+    for (uint32_t twl : {2u, 3u, 4u}) cands.push_back({0, 0, 128, 32, twl});  // grid launches
+    for (uint32_t threads : {128u, 256u}) {
+        const int occ = std::max(1, aokk_max_ctas_per_sm(threads));
+        for (int per_sm : {occ, std::max(1, occ / 2)})
+            for (uint32_t packet : {32u, 128u})
+                for (uint32_t twl : {3u}) cands.push_back({1, (uint32_t)per_sm, threads, packet, twl});
+    }
+    const int keep_p = ctx->batch_persistent;
     const uint32_t keep[4] = {ctx->ctas_per_sm, ctx->threads_per_cta, ctx->packet_rays, ctx->tile_w_log};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const cudaStream_t st = (cudaStream_t)stream;
     float best = 1e30f;
-    uint32_t bc[4] = {keep[0], keep[1], keep[2], keep[3]};
+    Cand bc = {keep_p, keep[0], keep[1], keep[2], keep[3]};
     int rc = AOK_OK;
-    for (uint32_t threads : {128u, 256u}) {
-        const int occ = std::max(1, aokk_max_ctas_per_sm(threads));
-        for (int per_sm : {occ, std::max(1, occ / 2)}) {
-            for (uint32_t packet : {32u, 64u, 128u}) {
-                for (uint32_t twl : {2u, 3u, 4u}) {
-                    ctx->threads_per_cta = threads;
-                    ctx->ctas_per_sm = (uint32_t)per_sm;
-                    ctx->packet_rays = packet;
-                    ctx->tile_w_log = twl;
-                    float ms = 1e30f;
-                    for (int rep = 0; rep < 3 && rc == AOK_OK; rep++) {
-                        cudaEventRecord(e0, st);
-                        rc = render_batch_impl(ctx, views, n, stream, false);
-                        cudaEventRecord(e1, st);
-                        cudaEventSynchronize(e1);
-                        float t = 0;
-                        cudaEventElapsedTime(&t, e0, e1);
-                        if (rep > 0) ms = std::min(ms, t);  // first run warms caches
-                    }
-                    if (rc) break;
-                    if (ms < best) {
-                        best = ms;
-                        bc[0] = (uint32_t)per_sm; bc[1] = threads; bc[2] = packet; bc[3] = twl;
-                    }
-                }
-            }
+    for (const Cand& c : cands) {
+        ctx->batch_persistent = c.persistent;
+        ctx->ctas_per_sm = c.per_sm;
+        ctx->threads_per_cta = c.threads;
+        ctx->packet_rays = c.packet;
+        ctx->tile_w_log = c.twl;
+        float ms = 1e30f;
+        for (int rep = 0; rep < 3 && rc == AOK_OK; rep++) {
+            cudaEventRecord(e0, st);
+            rc = render_batch_impl(ctx, views, n, stream, false);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float t = 0;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep > 0) ms = std::min(ms, t);  // the first run warms caches
+        }
+        if (rc) break;
+        if (ms < best) {
+            best = ms;
+            bc = c;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    ctx->ctas_per_sm = bc[0];
-    ctx->threads_per_cta = bc[1];
-    ctx->packet_rays = bc[2];
-    ctx->tile_w_log = bc[3];
-    if (rc) {
-        ctx->ctas_per_sm = keep[0]; ctx->threads_per_cta = keep[1]; ctx->packet_rays = keep[2]; ctx->tile_w_log = keep[3];
-        return rc;
-    }
+    if (rc) bc = {keep_p, keep[0], keep[1], keep[2], keep[3]};
+    ctx->batch_persistent = bc.persistent;
+    ctx->ctas_per_sm = bc.per_sm;
+    ctx->threads_per_cta = bc.threads;
+    ctx->packet_rays = bc.packet;
+    ctx->tile_w_log = bc.twl;
+    if (rc) return rc;
     if (best_ms) *best_ms = best;
     return AOK_OK;
 }
