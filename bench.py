@@ -182,7 +182,7 @@ def bench_batched(aok, ctx, scene, world, flush, reps=5):
                                                  "best_ms": tune_ms, "tune_s": round(tune_s, 2)}}
 
 
-def bench_served(aok, ctx, base_scene, threads, rates=(200, 500, 1000, 2000), n_req=1000, n_warm=100):
+def bench_served(aok, ctx, base_scene, threads, rates=(200, 500, 1000, 2000, 4000), n_req=1000, n_warm=100):
     """Poisson arrivals over 4 resident worlds (two 4096^3 cities, two 2048^3),
     each request a random walker pose, a resolution from the five sizes and a
     threshold U[0.5, 2] px: continuous-batching server vs serial FIFO renders."""
@@ -272,6 +272,50 @@ def bench_served(aok, ctx, base_scene, threads, rates=(200, 500, 1000, 2000), n_
     return out
 
 
+def bench_open(aok, ctx, threads, n_poses=300):
+    """Open world 65536x65536x1024 (128x128x2 chunks of 512^3, 4 LODs), view
+    distance 16384: along a 300-pose path at 2560x1440, only the (chunk, LOD)
+    pairs within the view distance are resident (streamed between frames);
+    per frame the selection (a1+a2) and the cast (a4-a7) are timed."""
+    import torch
+    from paper_2505_02017_gb300.stream import Streamer
+    spec = sg.OPEN_65536
+    world = sg.World(spec)
+    cams = sg.path_cameras(world, 103, n_poses, 2560, 1440)
+    scene = aok.Scene(ctx, spec, node_words=512 << 20, leaves=256 << 20, mat_bytes=16 << 30)
+    st = Streamer(ctx, world, scene, threads)
+    hit, t = aok.alloc_frame(2560, 1440)
+    stream = torch.cuda.current_stream()
+    sel_ms, cast_ms, host = [], [], []
+    max_bytes = 0
+    for i, cam in enumerate(cams):
+        host.append(st.update(cam, TAU))
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        aok.select_chunks(ctx, scene, cam, TAU, stream=stream)
+        e[1].record(stream)
+        aok.cast_selected(ctx, scene, cam, hit, t, stream=stream)
+        e[2].record(stream)
+        e[2].synchronize()
+        sel_ms.append(e[0].elapsed_time(e[1]))
+        cast_ms.append(e[1].elapsed_time(e[2]))
+    frame = [a + b for a, b in zip(sel_ms, cast_ms)]
+    rays = 2560 * 1440
+    srt = sorted(frame)
+    out = {"workload": "open65536: 65536x65536x1024, 128x128x2 chunks of 512^3, 4 LODs, view distance 16384; "
+                       f"{n_poses}-pose path (seed 103), 2560x1440, tau = 1 px",
+           "rays_per_s": rays * len(frame) / (sum(frame) / 1e3),
+           "frame_ms_median": srt[len(srt) // 2], "frame_ms_p99": srt[int(len(srt) * 0.99) - 1],
+           "select_ms_mean": sum(sel_ms) / len(sel_ms), "cast_ms_mean": sum(cast_ms) / len(cast_ms),
+           "max_resident_chunks": st.max_resident, "max_resident_mb": round(st.max_bytes / 1e6, 1),
+           "first_frame_built": host[0]["built"], "first_frame_build_s": round(host[0]["build_s"], 2),
+           "later_frames_built_total": sum(h["built"] for h in host[1:]),
+           "later_frames_evicted_total": sum(h["evicted"] for h in host[1:]),
+           "streaming_host_s_total": round(sum(h["plan_s"] + h["build_s"] + h["upload_s"] for h in host), 2)}
+    scene.destroy()
+    return out
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle as it stands, same workload/metric, bounded sample per step."""
     rank, world_size, _ = dist_env()
@@ -318,6 +362,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-open", action="store_true")
     ap.add_argument("--threads", type=int, default=0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -439,6 +484,8 @@ def main():
         out["batched"] = bench_batched(aok, ctx, scene, world, flush)
     if not args.no_serve:
         out["served"] = bench_served(aok, ctx, scene, threads)
+    if not args.no_open:
+        out["open_world"] = bench_open(aok, ctx, threads)
     if rank == 0 and world_size == 1 and not args.no_cpu_baseline:
         try:
             out["cpu_baseline"] = cpu_oracle_sample(world, cam)

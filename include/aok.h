@@ -190,6 +190,16 @@ typedef struct aok_frame {
 int aok_select_chunks(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double lod_threshold_px,
                       int8_t* lod_per_chunk_dev, uint8_t* visible_dev, uint32_t* n_visible_out, void* stream);
 
+/* Residency plan for one camera, on the host (the streaming side of
+ * Sec. 3.4): for every chunk region, the LOD that Eq. 1 selects -- the same
+ * FP64 arithmetic as aok_select_chunks, so the GPU selection finds exactly
+ * these (chunk, LOD) -- if the region's cell lies within the scene's view
+ * distance of the camera (all regions when view_dist is 0), else 0xFF.
+ * lod_out: host uint8[grid x*y*z] (x fastest).  Returns the number of
+ * regions kept in *n_kept (optional). */
+int aok_plan_residency(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double lod_threshold_px,
+                       uint8_t* lod_out, uint32_t* n_kept);
+
 /* Select (as aok_select_chunks) and cast every pixel's primary ray through
  * the chunk grid and the selected DAGs; writes `frame` on `stream`.  The
  * scene's per-frame chunk table is shared: aok_render calls on one scene that

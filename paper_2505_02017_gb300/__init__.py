@@ -86,6 +86,7 @@ def lib() -> ctypes.CDLL:
             "aok_render_noalloc": [vp, u32, P(Camera), dbl, P(Frame), vp],
             "aok_ray_dirs": [vp, P(Camera), vp, vp],
             "aok_cast_selected": [vp, u32, P(Camera), P(Frame), vp],
+            "aok_plan_residency": [vp, u32, P(Camera), dbl, vp, P(u32)],
             "aok_render_host": [vp, u32, P(Camera), dbl, vp, vp, vp],
             "aok_validate_chunk": [P(ChunkBlob), i32, u32],
             "aok_render_batch": [vp, P(View), u32, vp],
@@ -124,6 +125,8 @@ def blib() -> ctypes.CDLL:
         vp = ctypes.c_void_p
         L.aokb_build.restype = vp
         L.aokb_build.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, vp, ctypes.c_int64, ctypes.c_int32]
+        L.aokb_build_masked.restype = vp
+        L.aokb_build_masked.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, vp, vp, ctypes.c_int64, ctypes.c_int32]
         L.aokb_free.argtypes = [vp]
         L.aokb_count.restype = ctypes.c_int64
         L.aokb_count.argtypes = [vp]
@@ -201,17 +204,21 @@ class Context:
 class BuiltWorld:
     """Chunk blobs (all LODs) of a scenegen world, built by libaokbuild."""
 
-    def __init__(self, world, threads: int | None = None, chunks=None):
+    def __init__(self, world, threads: int | None = None, chunks=None, lod_masks=None):
         spec = world.spec
         self.spec = spec
         arr = None
+        msk = None
         n = 0
         if chunks is not None:
             arr = np.ascontiguousarray(chunks, np.int64)
             n = len(arr)
-        self.h = blib().aokb_build(world.handle, spec.chunk, spec.n_lods,
-                                   arr.ctypes.data if arr is not None else None, n,
-                                   threads or os.cpu_count() or 1)
+            if lod_masks is not None:
+                msk = np.ascontiguousarray(lod_masks, np.uint32)
+        self.h = blib().aokb_build_masked(world.handle, spec.chunk, spec.n_lods,
+                                          arr.ctypes.data if arr is not None else None,
+                                          msk.ctypes.data if msk is not None else None, n,
+                                          threads or os.cpu_count() or 1)
         if not self.h:
             raise ValueError("bad chunking for the builder")
         t = (ctypes.c_uint64 * 4)()

@@ -59,7 +59,9 @@ def build(force: bool = False, verbose: bool = False) -> None:
             o = os.path.join(_BUILD, os.path.basename(s) + ".o")
             objs.append(o)
             if force or _newer(o, [s] + hdrs):
-                flags = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-lineinfo", "-I", os.path.join(_ROOT, "include")]
+                # host code: no floating-point contraction (Eq. 1 must round exactly as on the GPU)
+                flags = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-lineinfo",
+                         "-I", os.path.join(_ROOT, "include")]
                 if s.endswith(".cu"):
                     flags += ["-gencode", GENCODE, "--fmad=false", "-Xptxas", "-v"] if verbose else \
                              ["-gencode", GENCODE, "--fmad=false"]

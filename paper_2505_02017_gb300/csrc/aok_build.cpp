@@ -141,8 +141,10 @@ struct Blob {
 
 constexpr uint32_t NONE = 0xFFFFFFFFu;
 
-// Build the DAG of one dense LOD grid (bits + materials, side r).
-void build_dag(const BitGrid& g, const std::vector<uint8_t>& mat, Blob& out) {
+// Build the DAG of one dense LOD grid (bits, side r); mat(x, y, z) gives the
+// material of a solid voxel (LOD-local coordinates).
+template <class MatFn>
+void build_dag(const BitGrid& g, MatFn mat, Blob& out) {
     const int r = g.r, nb = r / 4;
     const size_t nblk = (size_t)nb * nb * nb;
     // 4x4x4 leaf masks, bit x + 4y + 16z, block index bx + nb*(by + nb*bz)
@@ -276,7 +278,7 @@ void build_dag(const BitGrid& g, const std::vector<uint8_t>& mat, Blob& out) {
                 int bit = __builtin_ctzll(m);
                 m &= m - 1;
                 int vx = 4 * cx + (bit & 3), vy = 4 * cy + ((bit >> 2) & 3), vz = 4 * cz + (bit >> 4);
-                out.mats.push_back(mat[(size_t)vx + (size_t)r * ((size_t)vy + (size_t)r * vz)]);
+                out.mats.push_back(mat(vx, vy, vz));
                 lo[0] = std::min(lo[0], vx); lo[1] = std::min(lo[1], vy); lo[2] = std::min(lo[2], vz);
                 hi[0] = std::max(hi[0], vx); hi[1] = std::max(hi[1], vy); hi[2] = std::max(hi[2], vz);
             }
@@ -286,8 +288,10 @@ void build_dag(const BitGrid& g, const std::vector<uint8_t>& mat, Blob& out) {
 }
 
 // One LOD step (Sec. 3.4): a voxel exists iff >= 2 of its 8 children exist; its
-// material is the rounded mean of the existing children's.
-void aggregate(const BitGrid& g, const std::vector<uint8_t>& mat, BitGrid& g2, std::vector<uint8_t>& mat2) {
+// material is the rounded mean of the existing children's (mat(x, y, z) of
+// the finer grid).
+template <class MatFn>
+void aggregate(const BitGrid& g, MatFn mat, BitGrid& g2, std::vector<uint8_t>& mat2) {
     const int r = g.r, h = r / 2;
     g2.init(h);
     mat2.resize((size_t)h * h * h);
@@ -301,6 +305,7 @@ void aggregate(const BitGrid& g, const std::vector<uint8_t>& mat, BitGrid& g2, s
                     int xb = 2 * x0;  // 64 source bits
                     rows[k] = g.w[(size_t)(xb >> 6) + (size_t)g.w64 * ((size_t)yy + (size_t)r * zz)] >> (xb & 63);
                 }
+                if ((rows[0] | rows[1] | rows[2] | rows[3]) == 0) continue;  // nothing below these 32 voxels
                 for (int i = 0; i < xn; i++) {
                     int c = 0;
                     for (int k = 0; k < 4; k++) c += __builtin_popcountll((rows[k] >> (2 * i)) & 3);
@@ -310,8 +315,7 @@ void aggregate(const BitGrid& g, const std::vector<uint8_t>& mat, BitGrid& g2, s
                     for (int k = 0; k < 4; k++) {
                         int yy = 2 * y + (k & 1), zz = 2 * z + (k >> 1);
                         for (int dx = 0; dx < 2; dx++)
-                            if ((rows[k] >> (2 * i + dx)) & 1)
-                                sum += mat[(size_t)(2 * x + dx) + (size_t)r * ((size_t)yy + (size_t)r * zz)];
+                            if ((rows[k] >> (2 * i + dx)) & 1) sum += mat(2 * x + dx, yy, zz);
                     }
                     g2.w[(size_t)(x >> 6) + (size_t)g2.w64 * ((size_t)y + (size_t)h * z)] |= 1ull << (x & 63);
                     mat2[(size_t)x + (size_t)h * ((size_t)y + (size_t)h * z)] = (uint8_t)((sum + c / 2) / c);
@@ -319,7 +323,8 @@ void aggregate(const BitGrid& g, const std::vector<uint8_t>& mat, BitGrid& g2, s
             }
 }
 
-void build_chunk(const sg_scene* w, int M, int L, int cx, int cy, int cz, Blob* out /* [L] */) {
+void build_chunk(const sg_scene* w, int M, int L, int cx, int cy, int cz, Blob* out /* [L] */,
+                 uint32_t lod_mask = 0xFFFFFFFFu) {
     BitGrid g;
     g.init(M);
     uint64_t solid;
@@ -338,32 +343,38 @@ void build_chunk(const sg_scene* w, int M, int L, int cx, int cy, int cz, Blob* 
         for (int l = 0; l < L; l++) out[l] = Blob();
         return;
     }
-    std::vector<uint8_t> mat((size_t)M * M * M);
-    for (int z = 0; z < M; z++)
-        for (int y = 0; y < M; y++)
-            for (int xw = 0; xw < g.w64; xw++) {
-                uint64_t bits = g.w[(size_t)xw + (size_t)g.w64 * ((size_t)y + (size_t)M * z)];
-                while (bits) {
-                    int x = 64 * xw + __builtin_ctzll(bits);
-                    bits &= bits - 1;
-                    mat[(size_t)x + (size_t)M * ((size_t)y + (size_t)M * z)] =
-                        sg_material(w, cx * M + x, cy * M + y, cz * M + z);
-                }
+    // LOD 0 materials straight from the generator; coarser LODs in dense grids
+    const int ox = cx * M, oy = cy * M, oz = cz * M;
+    auto mat0 = [&](int x, int y, int z) -> uint8_t { return sg_material(w, ox + x, oy + y, oz + z); };
+    std::vector<uint8_t> mat;
+    int last = -1;
+    for (int l = 0; l < L; l++)
+        if ((lod_mask >> l) & 1u) last = l;
+    for (int l = 0; l <= last; l++) {
+        const int rl = g.r;
+        auto matl = [&](int x, int y, int z) -> uint8_t {
+            return mat[(size_t)x + (size_t)rl * ((size_t)y + (size_t)rl * z)];
+        };
+        if ((lod_mask >> l) & 1u) {
+            if (l == 0) build_dag(g, mat0, out[l]);
+            else build_dag(g, matl, out[l]);
+            for (int a = 0; a < 3; a++) {  // AABB to chunk-local LOD-0 units
+                out[l].lo[a] <<= l;
+                out[l].hi[a] <<= l;
             }
-    for (int l = 0; l < L; l++) {
-        build_dag(g, mat, out[l]);
-        for (int a = 0; a < 3; a++) {  // AABB to chunk-local LOD-0 units
-            out[l].lo[a] <<= l;
-            out[l].hi[a] <<= l;
+        } else {
+            out[l] = Blob();
         }
-        if (l + 1 < L) {
+        if (l + 1 <= last) {
             BitGrid g2;
             std::vector<uint8_t> m2;
-            aggregate(g, mat, g2, m2);
+            if (l == 0) aggregate(g, mat0, g2, m2);
+            else aggregate(g, matl, g2, m2);
             g = std::move(g2);
             mat = std::move(m2);
         }
     }
+    for (int l = last + 1; l < L; l++) out[l] = Blob();
 }
 
 }  // namespace
@@ -377,9 +388,11 @@ typedef struct aokb_world {
     std::vector<Blob> blobs;      // [entry * L + lod]
 } aokb_world;
 
-// Build all LODs of the listed chunk regions (chunk index = cx + gx*(cy + gy*cz)),
-// or of every chunk region when chunks == NULL.
-aokb_world* aokb_build(const sg_scene* w, int32_t M, int32_t L, const int64_t* chunks, int64_t n, int32_t n_threads) {
+// Build the LODs of the listed chunk regions (chunk index = cx + gx*(cy + gy*cz)),
+// or of every chunk region when chunks == NULL.  lod_masks (optional, one per
+// listed chunk): bit l set = emit LOD l (other LODs come back empty).
+aokb_world* aokb_build_masked(const sg_scene* w, int32_t M, int32_t L, const int64_t* chunks, const uint32_t* lod_masks,
+                              int64_t n, int32_t n_threads) {
     const sg_params* p = sg_get_params(w);
     if (M < 8 || (M & (M - 1)) || L < 1 || (M >> (L - 1)) < 8 || p->wx % M || p->wy % M || p->wz % M) return nullptr;
     auto* out = new aokb_world();
@@ -399,11 +412,16 @@ aokb_world* aokb_build(const sg_scene* w, int32_t M, int32_t L, const int64_t* c
                 int64_t i = next.fetch_add(1);
                 if (i >= (int64_t)out->chunks.size()) break;
                 int64_t c = out->chunks[i];
-                build_chunk(w, M, L, (int)(c % gx), (int)((c / gx) % gy), (int)(c / (gx * gy)), &out->blobs[i * L]);
+                build_chunk(w, M, L, (int)(c % gx), (int)((c / gx) % gy), (int)(c / (gx * gy)), &out->blobs[i * L],
+                            (chunks && lod_masks) ? lod_masks[i] : 0xFFFFFFFFu);
             }
         });
     for (auto& t : th) t.join();
     return out;
+}
+
+aokb_world* aokb_build(const sg_scene* w, int32_t M, int32_t L, const int64_t* chunks, int64_t n, int32_t n_threads) {
+    return aokb_build_masked(w, M, L, chunks, nullptr, n, n_threads);
 }
 
 void aokb_free(aokb_world* b) { delete b; }

@@ -90,8 +90,24 @@ uint64_t Pool::alloc(uint64_t n) {
     return off;
 }
 
+// Free ranges stay sorted by offset and merge with their neighbours; a range
+// that ends at the bump pointer gives the space back to it.
 void Pool::release(uint64_t off, uint64_t n) {
-    if (n) free_list.emplace_back(off, n);
+    if (!n) return;
+    auto it = std::lower_bound(free_list.begin(), free_list.end(), std::make_pair(off, (uint64_t)0));
+    it = free_list.insert(it, std::make_pair(off, n));
+    if (it + 1 != free_list.end() && it->first + it->second == (it + 1)->first) {
+        it->second += (it + 1)->second;
+        free_list.erase(it + 1);
+    }
+    if (it != free_list.begin() && (it - 1)->first + (it - 1)->second == it->first) {
+        (it - 1)->second += it->second;
+        it = free_list.erase(it) - 1;
+    }
+    if (it->first + it->second == used) {
+        used = it->first;
+        free_list.erase(it);
+    }
 }
 
 int make_cam(aok_ctx* ctx, const Scene* sc, const aok_camera* cam, double tau, CamDev* out) {
@@ -583,6 +599,57 @@ int aok_select_chunks(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, doubl
         if (e != cudaSuccess) return cuda_status(ctx, e);
         *n_visible_out = *ctx->pinned_word;
     }
+    return AOK_OK;
+}
+
+// Eq. 1 on the host with the kernel's operation order (compiled without
+// floating-point contraction, so the results are bit-identical).
+static bool host_lod_loads(int n, const int b[3], int mlog, const float o[3], double sf) {
+    const double S = (double)(1ll << (mlog + n));
+    double e2 = 0.0;
+    for (int a = 0; a < 3; a++) {
+        const double c = (double)b[a] * S + 0.5 * S;
+        const double dd = c - (double)o[a];
+        e2 = e2 + dd * dd;
+    }
+    const double thr = S * sf;
+    return e2 >= thr * thr;
+}
+
+int aok_plan_residency(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double tau, uint8_t* lod_out,
+                       uint32_t* n_kept) {
+    if (!ctx || !lod_out) return AOK_E_INVALID;
+    Scene* sc = find_scene(ctx, scene);
+    if (!sc) return AOK_E_NOT_RESIDENT;
+    CamDev cd;
+    int st = make_cam(ctx, sc, cam, tau, &cd);
+    if (st) return st;
+    const int G0 = sc->desc.grid[0], G1 = sc->desc.grid[1], G2 = sc->desc.grid[2], M = sc->desc.chunk_res;
+    const double vd = sc->desc.view_dist;
+    uint32_t kept = 0;
+    for (int cz = 0; cz < G2; cz++)
+        for (int cy = 0; cy < G1; cy++)
+            for (int cx = 0; cx < G0; cx++) {
+                const size_t i = (size_t)cx + (size_t)G0 * ((size_t)cy + (size_t)G1 * cz);
+                if (vd > 0) {  // distance from the camera to the region's cell
+                    const int c[3] = {cx, cy, cz};
+                    double d2 = 0;
+                    for (int a = 0; a < 3; a++) {
+                        const double lo = (double)c[a] * M, hi = lo + M, o = cd.of[a];
+                        const double q = o < lo ? lo - o : (o > hi ? o - hi : 0.0);
+                        d2 += q * q;
+                    }
+                    if (d2 > (vd + 2.0) * (vd + 2.0)) { lod_out[i] = 0xFF; continue; }
+                }
+                int sel = 0;
+                for (int n = sc->desc.n_lods - 1; n >= 1; n--) {
+                    const int b[3] = {cx >> n, cy >> n, cz >> n};
+                    if (host_lod_loads(n, b, sc->mlog, cd.of, cd.sf)) { sel = n; break; }
+                }
+                lod_out[i] = (uint8_t)sel;
+                kept++;
+            }
+    if (n_kept) *n_kept = kept;
     return AOK_OK;
 }
 

@@ -198,14 +198,29 @@ struct Ticket {
     int status = AOK_OK;
 };
 
+struct ServeState;
+
+// Completion record of one launched batch; the stream's host callback marks it
+// done and wakes the serving loop (no CUDA calls inside the callback).
+struct BatchDone {
+    ServeState* S = nullptr;
+    std::atomic<int> done{0};
+    std::atomic<uint64_t> t_ns{0};
+};
+
 struct InFlight {
     cudaEvent_t done;
+    BatchDone* flag;
     std::vector<uint64_t> tickets;
     uint32_t stream_slot;
 };
 
 struct ServeState {
     uint32_t max_slots = 0, max_batch = 0;
+    // wake-ups of the loop: own mutex, never held across a CUDA call
+    std::mutex wake_mu;
+    std::condition_variable wake_cv;
+    int wake = 0;
     std::vector<cudaStream_t> streams;
     std::vector<unsigned long long*> counters;  // 2 * kBatchViews-group pairs per stream
     std::vector<uint32_t> stream_busy;
@@ -221,6 +236,21 @@ struct ServeState {
     std::thread loop;
     std::vector<BatchParams> params;  // staging
 };
+
+static void wake_loop(ServeState* S) {
+    {
+        std::lock_guard<std::mutex> g(S->wake_mu);
+        S->wake = 1;
+    }
+    S->wake_cv.notify_all();
+}
+
+static void CUDART_CB on_batch_done(void* p) {
+    BatchDone* b = (BatchDone*)p;
+    b->t_ns.store(now_ns());
+    b->done.store(1);
+    wake_loop(b->S);
+}
 
 static size_t request_bytes(const Scene* sc, const aok_camera& cam) {
     const size_t px = (size_t)cam.width * cam.height;
@@ -251,17 +281,18 @@ static void serve_loop(aok_ctx* ctx) {
             {
                 std::lock_guard<std::mutex> g(S.mu);
                 for (auto& f : S.inflight) {
-                    if (cudaEventQuery(f.done) == cudaSuccess) finished.push_back(f);
+                    if (f.flag->done.load() && cudaEventQuery(f.done) == cudaSuccess) finished.push_back(f);
                     else still.push_back(f);
                 }
                 S.inflight.swap(still);
-                const uint64_t tnow = now_ns();
                 for (auto& f : finished) {
+                    const uint64_t tdone = f.flag->t_ns.load();
+                    delete f.flag;
                     for (uint64_t id : f.tickets) {
                         auto it = S.tickets.find(id);
                         if (it != S.tickets.end() && it->second.state == kRunning) {
                             it->second.state = kDone;
-                            it->second.t_done = tnow;
+                            it->second.t_done = tdone;
                         }
                         S.running--;
                     }
@@ -311,10 +342,13 @@ static void serve_loop(aok_ctx* ctx) {
                 S.pending.pop_front();
                 batch.push_back(id);
             }
-            if (batch.empty()) {
-                S.cv.wait_for(g, std::chrono::microseconds(200));
-                continue;
-            }
+        }
+        if (batch.empty()) {
+            // sleep until a submission, a release or a batch completion wakes us
+            std::unique_lock<std::mutex> w(S.wake_mu);
+            if (!S.wake) S.wake_cv.wait_for(w, std::chrono::milliseconds(2));
+            S.wake = 0;
+            continue;
         }
         // launch the batch on its stream: groups of up to 128 views
         const cudaStream_t st = S.streams[slot];
@@ -369,8 +403,12 @@ static void serve_loop(aok_ctx* ctx) {
             cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
         }
         cudaEventRecord(ev, st);
+        BatchDone* flag = new BatchDone();
+        flag->S = &S;
+        cudaLaunchHostFunc(st, on_batch_done, flag);
         InFlight f;
         f.done = ev;
+        f.flag = flag;
         f.tickets = batch;
         f.stream_slot = slot;
         S.stream_busy[slot]++;
@@ -515,7 +553,7 @@ int aok_serve_stop(aok_ctx* ctx) {
         }
         S->pending.clear();
     }
-    S->cv.notify_all();
+    wake_loop(S);
     if (S->loop.joinable()) S->loop.join();
     cudaSetDevice(ctx->device);
     for (auto& kv : S->tickets) free_ticket_memory(ctx, kv.second, S->streams[0]);
@@ -525,7 +563,10 @@ int aok_serve_stop(aok_ctx* ctx) {
         cudaStreamDestroy(S->streams[i]);
     }
     for (cudaEvent_t e : S->free_events) cudaEventDestroy(e);
-    for (auto& f : S->inflight) cudaEventDestroy(f.done);
+    for (auto& f : S->inflight) {
+        cudaEventDestroy(f.done);
+        delete f.flag;
+    }
     // counters were charged: give the bytes back
     const uint32_t ngroups = (S->max_batch + kBatchViews - 1) / kBatchViews;
     uncharge(ctx, S->streams.size() * 2 * ngroups * sizeof(unsigned long long));
@@ -556,7 +597,7 @@ int aok_serve_submit(aok_ctx* ctx, const aok_request* req, uint64_t* ticket) {
         S->pending.push_back(id);
         *ticket = id;
     }
-    S->cv.notify_one();
+    wake_loop(S);
     return AOK_OK;
 }
 
@@ -619,7 +660,7 @@ int aok_serve_release(aok_ctx* ctx, uint64_t ticket) {
     cudaSetDevice(ctx->device);
     free_ticket_memory(ctx, t, S->streams[0]);
     S->tickets.erase(it);
-    S->cv.notify_one();
+    wake_loop(S);
     return AOK_OK;
 }
 

@@ -311,3 +311,38 @@ def batch_cameras(world: World, seed: int, n: int):
         W, H = RESOLUTIONS[rng.randint(0, len(RESOLUTIONS) - 1)]
         cams.append(ground_camera(world, rng.next(), W, H))
     return cams
+
+
+def path_cameras(world: World, seed: int, n_poses: int, W: int, H: int, n_waypoints: int = 10,
+                 span: float = 6000.0, z_lo: float = 32.0, z_hi: float = 512.0, pitch=(-20.0, 0.0)):
+    """A flight path: n_waypoints seeded waypoints (x, y inside a span x span square
+    around a seeded centre, z = terrain + U[z_lo, z_hi]), linearly interpolated to
+    n_poses poses looking along the direction of travel with a seeded pitch."""
+    spec = world.spec
+    rng = Rng(seed)
+    cx = rng.uniform(0.25 * spec.wx, 0.75 * spec.wx)
+    cy = rng.uniform(0.25 * spec.wy, 0.75 * spec.wy)
+    wps = []
+    for _ in range(n_waypoints):
+        x = min(max(cx + rng.uniform(-span / 2, span / 2), 1.0), spec.wx - 1.0)
+        y = min(max(cy + rng.uniform(-span / 2, span / 2), 1.0), spec.wy - 1.0)
+        z = min(world.height(int(x), int(y)) + rng.uniform(z_lo, z_hi), spec.wz - 4.0)
+        wps.append(np.array([x, y, z]))
+    pit = [math.radians(rng.uniform(*pitch)) for _ in range(n_waypoints)]
+    cams = []
+    for i in range(n_poses):
+        s = i * (n_waypoints - 1) / max(1, n_poses - 1)
+        k = min(int(s), n_waypoints - 2)
+        f = s - k
+        p = wps[k] * (1 - f) + wps[k + 1] * f
+        g = max(p[2], world.height(int(p[0]), int(p[1])) + 8.0)  # stay above the ground
+        d = wps[k + 1] - wps[k]
+        yaw = math.atan2(d[1], d[0])
+        pt = pit[k] * (1 - f) + pit[k + 1] * f
+        fwd = (math.cos(pt) * math.cos(yaw), math.cos(pt) * math.sin(yaw), math.sin(pt))
+        cams.append(make_camera((p[0], p[1], g), fwd, W, H))
+    return cams
+
+
+OPEN_8192 = replace(OPEN_65536, name="open8192", seed=31, wx=8192, wy=8192, wz=1024, period0=2048,
+                    n_boxes=16000, view_dist=3000.0)

@@ -66,9 +66,61 @@ int32_t sg_height(const sg_scene* s, int32_t x, int32_t y) {
     return p->h_min + (int32_t)(((int64_t)(p->h_max - p->h_min) * nq) >> 16);
 }
 
+/* Same values as sg_height over a rectangle, with the per-octave lattice values
+ * and interpolation weights computed once per cell / column / row. */
 void sg_heights(const sg_scene* s, int32_t x0, int32_t y0, int32_t nx, int32_t ny, int32_t* out) {
-    for (int32_t y = 0; y < ny; y++)
-        for (int32_t x = 0; x < nx; x++) out[(size_t)y * nx + x] = sg_height(s, x0 + x, y0 + y);
+    const sg_params* p = &s->p;
+    const int32_t K = p->octaves - 1;
+    int64_t* acc = (int64_t*)calloc((size_t)nx * ny, sizeof(int64_t));
+    int32_t* ix = (int32_t*)malloc((size_t)nx * sizeof(int32_t));
+    int32_t* iy = (int32_t*)malloc((size_t)ny * sizeof(int32_t));
+    int64_t* sx = (int64_t*)malloc((size_t)nx * sizeof(int64_t));
+    int64_t* sy = (int64_t*)malloc((size_t)ny * sizeof(int64_t));
+    int64_t wsum = 0;
+    for (int32_t o = 0; o < p->octaves; o++) {
+        int32_t P = p->period0 >> o;
+        if (P < 1) P = 1;
+        for (int32_t x = 0; x < nx; x++) {
+            const int32_t i = floor_div(x0 + x, P);
+            ix[x] = i;
+            sx[x] = smooth_q16(((int64_t)(x0 + x - i * P) << 16) / P);
+        }
+        for (int32_t y = 0; y < ny; y++) {
+            const int32_t j = floor_div(y0 + y, P);
+            iy[y] = j;
+            sy[y] = smooth_q16(((int64_t)(y0 + y - j * P) << 16) / P);
+        }
+        const int32_t i0 = ix[0], j0 = iy[0];
+        const int32_t ci = ix[nx - 1] - i0 + 2, cj = iy[ny - 1] - j0 + 2;
+        int64_t* lat = (int64_t*)malloc((size_t)ci * cj * sizeof(int64_t));
+        for (int32_t j = 0; j < cj; j++)
+            for (int32_t i = 0; i < ci; i++) lat[(size_t)j * ci + i] = lattice(s, i0 + i, j0 + j, o);
+        for (int32_t y = 0; y < ny; y++) {
+            const int64_t* r0 = lat + (size_t)(iy[y] - j0) * ci;
+            const int64_t* r1 = r0 + ci;
+            const int64_t wy = sy[y];
+            int64_t* a = acc + (size_t)y * nx;
+            for (int32_t x = 0; x < nx; x++) {
+                const int32_t c = ix[x] - i0;
+                const int64_t wx = sx[x];
+                const int64_t ta = (r0[c] * (65536 - wx) + r0[c + 1] * wx) >> 16;
+                const int64_t tb = (r1[c] * (65536 - wx) + r1[c + 1] * wx) >> 16;
+                const int64_t n = (ta * (65536 - wy) + tb * wy) >> 16;
+                a[x] += n << (K - o);
+            }
+        }
+        free(lat);
+        wsum += (int64_t)1 << (K - o);
+    }
+    for (size_t k = 0; k < (size_t)nx * ny; k++) {
+        const int64_t nq = acc[k] / wsum;
+        out[k] = p->h_min + (int32_t)(((int64_t)(p->h_max - p->h_min) * nq) >> 16);
+    }
+    free(acc);
+    free(ix);
+    free(iy);
+    free(sx);
+    free(sy);
 }
 
 const sg_params* sg_get_params(const sg_scene* s) { return &s->p; }

@@ -23,3 +23,17 @@ def test_generator_fingerprints():
 
 def test_oracle_fingerprints():
     assert make_golden.oracle_fingerprints() == load("oracle_small.json")
+
+
+def test_rectangle_heights_equal_point_heights():
+    import numpy as np
+    import scenegen as sg
+    rng = np.random.default_rng(4)
+    for spec in (sg.SINGLE_128, sg.CITY_4096, sg.OPEN_65536):
+        w = sg.World(spec)
+        for _ in range(4):
+            x0, y0 = (int(v) for v in rng.integers(-300, spec.wx, 2))
+            nx, ny = (int(v) for v in rng.integers(1, 90, 2))
+            h = w.heights(x0, y0, nx, ny)
+            ref = np.array([[w.height(x0 + x, y0 + y) for x in range(nx)] for y in range(ny)], np.int32)
+            assert (h == ref).all()
