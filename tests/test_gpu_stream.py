@@ -46,3 +46,56 @@ def test_streaming_path_matches_oracle():
     assert stats[0]["built"] > 0 and any(s["evicted"] > 0 or s["built"] > 0 for s in stats[1:])
     sc.destroy()
     ctx.close()
+
+
+def ray_chunks(spec, cam, pix, tmax):
+    """Chunk regions whose cell meets the segment [0, tmax[i]] of each sampled ray."""
+    M = spec.chunk
+    gx, gy, gz = spec.grid
+    cz, cy, cx = np.meshgrid(np.arange(gz), np.arange(gy), np.arange(gx), indexing="ij")
+    lo = np.stack([cx.ravel(), cy.ravel(), cz.ravel()], 1).astype(np.float64) * M
+    hi = lo + M
+    o = cam.origin.astype(np.float64)
+    keep = np.zeros(len(lo), bool)
+    for i, (px, py) in enumerate(pix):
+        d = orc.ray_dir(cam, int(px), int(py)).astype(np.float64)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t1 = (lo - o) / d
+            t2 = (hi - o) / d
+        tn = np.nanmax(np.where(d == 0, np.where((o >= lo) & (o <= hi), -np.inf, np.inf), np.minimum(t1, t2)), 1)
+        tf = np.nanmin(np.where(d == 0, np.where((o >= lo) & (o <= hi), np.inf, -np.inf), np.maximum(t1, t2)), 1)
+        keep |= (tn <= tf) & (tf >= 0) & (tn <= tmax[i])
+    return keep
+
+
+def test_open65536_path_pose_sampled():
+    """The benchmark's open world (65536x65536x1024, view distance 16384) at
+    2560x1440 for one pose of its path, on sampled pixels."""
+    spec = sg.OPEN_65536
+    w = sg.World(spec)
+    ctx = aok.Context(0)
+    sc = aok.Scene(ctx, spec, node_words=512 << 20, leaves=256 << 20, mat_bytes=16 << 30)
+    st = Streamer(ctx, w, sc, threads=16)
+    cam = sg.path_cameras(w, 103, 300, 2560, 1440)[150]
+    tau = 1.0
+    st.update(cam, tau)
+    hit, t = aok.alloc_frame(cam.W, cam.H)
+    aok.render(ctx, sc, cam, tau, hit, t)
+    torch.cuda.synchronize()
+    g = decode(hit, t)
+    rng = np.random.default_rng(3)
+    n = cam.W * cam.H
+    idx = np.unique(np.concatenate([rng.integers(0, n, 300), np.arange(cam.W * 700, cam.W * 700 + cam.W, 16)]))
+    pix = np.stack([idx % cam.W, idx // cam.W], 1)
+    dn = np.array([np.linalg.norm(orc.ray_dir(cam, int(x), int(y)).astype(np.float64)) for x, y in pix])
+    dist = np.where(g["hit"][idx] == 1, g["dist"][idx], spec.view_dist)
+    keep = ray_chunks(spec, cam, pix, dist / dn + 2.0)
+    plan = st.plan(cam, tau)
+    sel = np.where(keep & (plan != 0xFF), plan.astype(np.int32), -1).astype(np.int8)
+    S = orc.OracleScene(w)
+    ref = S.cast(cam, sel, pixels=pix, view_dist=spec.view_dist)
+    checked, amb = compare(g, ref, idx=idx, max_amb_frac=5e-3)
+    assert checked >= len(idx) - 2
+    assert (g["hit"][idx] == 1).mean() > 0.3
+    sc.destroy()
+    ctx.close()
