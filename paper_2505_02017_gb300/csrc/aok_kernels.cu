@@ -198,7 +198,8 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
     if (e < 3) { me = r.m[e]; Ee = r.E[e]; }
     uint64_t lmu = 0;
     const int f1 = (r.mir & 1u) ? 1 : 0, f2 = (r.mir & 2u) ? 1 : 0, f4 = (r.mir & 4u) ? 1 : 0;
-    const int g1 = 3 * f1, g2 = 3 * f2, g4 = 3 * f4;
+    uint32_t pm8 = 0;   // parent's child mask, stored octant order (node mask / leaf groups / group voxels)
+    uint32_t g8 = 0;    // group occupancy of the current leaf block
     bool occ = true;
     for (;;) {
         if (occ) {
@@ -236,13 +237,24 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
                     idx = nodes[sidx[k + 1] + 2 + 2 * __popc(smask[k + 1] & ((1u << oct) - 1u))];
                 }
                 if (k >= n + 3) {
+                    pm8 = nodes[idx] & 0xFFu;
                     sidx[k] = idx;
-                    smask[k] = nodes[idx] & 0xFFu;
+                    smask[k] = pm8;
                     if (COUNT) cnt.v_int++;
                 } else {
                     lmu = S.leaves[idx];
+                    uint64_t t = lmu | (lmu >> 1);
+                    t |= t >> 4;
+                    t |= t >> 16;
+                    g8 = (uint32_t)((t & 1) | ((t >> 1) & 2) | ((t >> 6) & 4) | ((t >> 7) & 8) | ((t >> 28) & 16) |
+                                    ((t >> 29) & 32) | ((t >> 34) & 64) | ((t >> 35) & 128));
+                    pm8 = g8;
                     if (COUNT) cnt.v_leaf++;
                 }
+            } else {
+                // entering a 2x2x2 group of the leaf: its 8 voxel bits in octant order
+                const uint64_t v = lmu >> (((c0 & 1) ^ f1) * 2 + ((c1 & 1) ^ f2) * 8 + ((c2 & 1) ^ f4) * 32);
+                pm8 = (uint32_t)((v & 3) | ((v >> 2) & 0xC) | ((v >> 12) & 0x30) | ((v >> 14) & 0xC0));
             }
             // child of cell (k, c) holding the entry point: compare t_entry with the mid planes
             const int kk = k - 1;
@@ -273,21 +285,17 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
             else if (ax == 1) cax = ++c1;
             else cax = ++c2;
             if ((cax << k) >= (1 << R)) return false;  // left the chunk
-            while (k < R && (cax & 1) == 0) {
-                c0 >>= 1; c1 >>= 1; c2 >>= 1;
-                cax >>= 1;
-                k++;
+            if ((cax & 1) == 0) {
+                do {
+                    c0 >>= 1; c1 >>= 1; c2 >>= 1;
+                    cax >>= 1;
+                    k++;
+                } while (k < R && (cax & 1) == 0);
+                pm8 = k >= n + 2 ? smask[k + 1] : g8;  // popped into a new parent (a node or the leaf)
             }
         }
-        // occupancy of cell (k, c)
-        if (k >= n + 2) {
-            const uint32_t oct = ((uint32_t)(c0 & 1) | ((uint32_t)(c1 & 1) << 1) | ((uint32_t)(c2 & 1) << 2)) ^ r.mir;
-            occ = (smask[k + 1] >> oct) & 1u;
-        } else if (k == n + 1) {
-            occ = (lmu & (0x330033ull << (((c0 & 1) ^ f1) * 2 + ((c1 & 1) ^ f2) * 8 + ((c2 & 1) ^ f4) * 32))) != 0ull;
-        } else {
-            occ = (lmu >> (((c0 & 3) ^ g1) + 4 * ((c1 & 3) ^ g2) + 16 * ((c2 & 3) ^ g4))) & 1ull;
-        }
+        // occupancy of cell (k, c) in its parent
+        occ = (pm8 >> (((uint32_t)(c0 & 1) | ((uint32_t)(c1 & 1) << 1) | ((uint32_t)(c2 & 1) << 2)) ^ r.mir)) & 1u;
     }
 }
 
