@@ -48,6 +48,26 @@ def peaks():
         return 6800.0, "fallback"
 
 
+PROFILE = os.path.join(ROOT, "profiles", "cast_kernel_city4096_1080p.md")
+KERNEL_SRC = os.path.join(ROOT, "paper_2505_02017_gb300", "csrc", "aok_kernels.cu")
+
+
+def profiled_traffic():
+    """DRAM bytes (read + write) of one cast_kernel launch on this workload from
+    the committed ncu summary, if it was taken on the current kernel source;
+    else None (the counters no longer describe the kernel)."""
+    import hashlib
+    import re
+    try:
+        with open(KERNEL_SRC, "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()[:16]
+        with open(PROFILE) as f:
+            m = re.search(r"^traffic: (\d+) bytes per launch, aok_kernels\.cu sha256 ([0-9a-f]{16})", f.read(), re.M)
+    except OSError:
+        return None
+    return int(m.group(1)) if m and m.group(2) == h else None
+
+
 class Clocks:
     """nvidia-smi sampler (clocks + throttle reasons) around the timed region."""
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
@@ -316,6 +336,84 @@ def bench_open(aok, ctx, threads, n_poses=300):
     return out
 
 
+def _chunks_met(spec, cam, pix, tmax):
+    """Chunk regions whose cell meets the segment [0, tmax[i]] of each sampled ray."""
+    import oracle as orc
+    M = spec.chunk
+    gx, gy, gz = spec.grid
+    cz, cy, cx = np.meshgrid(np.arange(gz), np.arange(gy), np.arange(gx), indexing="ij")
+    lo = np.stack([cx.ravel(), cy.ravel(), cz.ravel()], 1).astype(np.float64) * M
+    hi = lo + M
+    o = cam.origin.astype(np.float64)
+    keep = np.zeros(len(lo), bool)
+    for i, (px, py) in enumerate(pix):
+        d = orc.ray_dir(cam, int(px), int(py)).astype(np.float64)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t1, t2 = (lo - o) / d, (hi - o) / d
+        tn = np.nanmax(np.where(d == 0, np.where((o >= lo) & (o <= hi), -np.inf, np.inf), np.minimum(t1, t2)), 1)
+        tf = np.nanmin(np.where(d == 0, np.where((o >= lo) & (o <= hi), np.inf, -np.inf), np.maximum(t1, t2)), 1)
+        keep |= (tn <= tf) & (tf >= 0) & (tn <= tmax[i])
+    return keep
+
+
+def cpu_scaling(threads):
+    """Oracle rays/s at 1 thread and at all host threads for a single128 frame
+    (256x256, camera seed 101), the city4096 1080p frame and one open65536
+    2560x1440 frame (pose 150 of the path; the oracle is given the chunks the
+    sampled rays meet up to the GPU's hit distance).  DAG builds are not timed."""
+    import torch
+    import oracle as orc
+    import paper_2505_02017_gb300 as aok
+    from paper_2505_02017_gb300.stream import Streamer
+    res = {}
+
+    def rate(S, cam, sel, pix, nthr, view_dist=0.0):
+        S.cast(cam, sel, pix[: max(1, len(pix) // 20)], view_dist=view_dist, threads=nthr)  # warm
+        t0 = time.perf_counter()
+        S.cast(cam, sel, pix, view_dist=view_dist, threads=nthr)
+        return len(pix) / (time.perf_counter() - t0)
+
+    def stride_pix(cam, n):
+        step = max(1, cam.W * cam.H // n)
+        idx = np.arange(0, cam.W * cam.H, step)
+        return np.stack([idx % cam.W, idx // cam.W], 1)
+
+    for name, spec, cam_fn, n1 in (("single128_256x256", sg.SINGLE_128, lambda w: sg.orbit_camera(w.spec, 101, 256, 256), 20000),
+                                   ("city4096_1080p", sg.CITY_4096, lambda w: sg.ground_camera(w, CAM_SEED, W, H), 4000)):
+        w = sg.World(spec)
+        cam = cam_fn(w)
+        S = orc.OracleScene(w)
+        sel = S.select(cam, TAU)
+        S.prepare(sel)
+        res[name] = {"threads_1": rate(S, cam, sel, stride_pix(cam, n1), 1),
+                     f"threads_{threads}": rate(S, cam, sel, stride_pix(cam, n1 * threads), threads)}
+    spec = sg.OPEN_65536
+    w = sg.World(spec)
+    ctx = aok.Context(0)
+    sc = aok.Scene(ctx, spec, node_words=512 << 20, leaves=256 << 20, mat_bytes=16 << 30)
+    st = Streamer(ctx, w, sc, threads)
+    cam = sg.path_cameras(w, 103, 300, 2560, 1440)[150]
+    st.update(cam, TAU)
+    hit, t = aok.alloc_frame(cam.W, cam.H)
+    aok.render(ctx, sc, cam, TAU, hit, t)
+    torch.cuda.synchronize()
+    pix = stride_pix(cam, 400)
+    idx = pix[:, 1] * cam.W + pix[:, 0]
+    meta = hit.view(-1, 4)[:, 3].cpu().numpy()[idx]
+    dist = np.where((meta >> 19) & 1, t.view(-1).cpu().numpy()[idx], spec.view_dist)
+    dn = np.array([np.linalg.norm(orc.ray_dir(cam, int(x), int(y)).astype(np.float64)) for x, y in pix])
+    plan = st.plan(cam, TAU)
+    sel = np.where(_chunks_met(spec, cam, pix, dist / dn + 2.0) & (plan != 0xFF), plan.astype(np.int32), -1)
+    sel = sel.astype(np.int8)
+    S = orc.OracleScene(w)
+    S.prepare(sel)
+    res["open65536_1440p_pose150"] = {"threads_1": rate(S, cam, sel, pix, 1, spec.view_dist),
+                                      f"threads_{threads}": rate(S, cam, sel, pix, threads, spec.view_dist)}
+    sc.destroy()
+    ctx.close()
+    print(json.dumps({"oracle_rays_per_s": res, "host_threads": threads}), flush=True)
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle as it stands, same workload/metric, bounded sample per step."""
     rank, world_size, _ = dist_env()
@@ -364,10 +462,14 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-open", action="store_true")
     ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--cpu-scaling", action="store_true",
+                    help="print the oracle's 1-thread / all-thread rays/s for three workloads and exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.cpu_scaling:
+        return cpu_scaling(args.threads or os.cpu_count() or 1)
 
     import torch
     import paper_2505_02017_gb300 as aok
@@ -444,6 +546,9 @@ def main():
     cast_avg = sum(cast_ms) / len(cast_ms)
     hbm, peak_kind = peaks()
     achieved = algo_bytes / (cast_avg / 1000.0) / 1e9
+    # the library's own read microbenchmark: L2-resident (64 MB) and HBM (4 GB) buffers
+    l2_gbs = aok.read_bandwidth(ctx, 64 << 20, 200)
+    hbm_read_gbs = aok.read_bandwidth(ctx, 4 << 30, 5)
 
     # ---- e2e: public API with host buffers (camera in, frame copied out every step) ----
     hh = torch.empty((H, W, 4), dtype=torch.int32, pin_memory=True)
@@ -472,9 +577,12 @@ def main():
                    "scene_bytes": {"nodes": built.node_words * 4, "leaves": built.leaves * 8,
                                    "mats": built.mat_bytes}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": None, "kernel": "cast_kernel", "peak_kind": f"{peak_kind} hbm_gbs",
+                     "traffic": profiled_traffic(), "kernel": "cast_kernel", "peak_kind": f"{peak_kind} hbm_gbs",
                      "algo_bytes_per_launch": algo_bytes, "algo_bytes_per_ray": algo_bytes / rays,
-                     "cast_ms": cast_avg},
+                     "cast_ms": cast_avg, "cast_ms_median": statistics.median(cast_ms),
+                     "cast_ms_best": min(cast_ms),
+                     "l2_read_gbs": l2_gbs, "frac_of_l2_read": achieved / l2_gbs,
+                     "hbm_read_gbs": hbm_read_gbs},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 52, "d2h_bytes_per_step": rays * 20},
         "gpu_launches": 2 * args.steps,
         "clocks": clk,

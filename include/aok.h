@@ -337,6 +337,15 @@ int aok_render_counted(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, doub
 /* Write every pixel's FP32 ray direction (3 floats per pixel) to the device
  * buffer dirs, as the casting kernel computes it. */
 int aok_ray_dirs(aok_ctx* ctx, const aok_camera* cam, float* dirs, void* stream);
+/* Read-bandwidth microbenchmark (no counterpart in the paper; the yardstick
+ * for traversal kernels whose working set sits in L2).  Allocates a device
+ * buffer of `bytes` (rounded down to 16; charged to the budget while the call
+ * runs), reads it `reps` times with 16-byte L2 loads in one launch of one
+ * resident grid after a warm-up launch of two passes, and writes the achieved
+ * GB/s (1e9 B/s) of the timed launch to *gbs.
+ * bytes below the L2 size measure L2, larger ones HBM.  Synchronous.
+ * AOK_E_INVALID for bytes < 16 or reps < 1, AOK_E_OOM if the buffer does not fit. */
+int aok_read_bandwidth(aok_ctx* ctx, uint64_t bytes, int reps, double* gbs);
 
 #ifdef __cplusplus
 }

@@ -85,6 +85,7 @@ def lib() -> ctypes.CDLL:
             "aok_render_counted": [vp, u32, P(Camera), dbl, P(Frame), vp, vp],
             "aok_render_noalloc": [vp, u32, P(Camera), dbl, P(Frame), vp],
             "aok_ray_dirs": [vp, P(Camera), vp, vp],
+            "aok_read_bandwidth": [vp, ctypes.c_uint64, ctypes.c_int, P(dbl)],
             "aok_cast_selected": [vp, u32, P(Camera), P(Frame), vp],
             "aok_plan_residency": [vp, u32, P(Camera), dbl, vp, P(u32)],
             "aok_render_host": [vp, u32, P(Camera), dbl, vp, vp, vp],
@@ -344,6 +345,13 @@ def select_chunks(ctx: Context, scene: Scene, cam, tau: float, lod_out=None, vis
                                   ctypes.byref(nvis) if count else None, _stream_handle(stream)),
           "aok_select_chunks")
     return nvis.value if count else None
+
+
+def read_bandwidth(ctx: Context, nbytes: int, reps: int = 20) -> float:
+    """GB/s of 16-byte L2 reads over a device buffer of nbytes (aok_read_bandwidth)."""
+    g = ctypes.c_double()
+    check(lib().aok_read_bandwidth(ctx.h, int(nbytes), int(reps), ctypes.byref(g)), "aok_read_bandwidth")
+    return g.value
 
 
 def ray_dirs(ctx: Context, cam, dirs, stream=None):

@@ -86,6 +86,7 @@ int aokk_select(const aok::SceneDev* s, const aok::CamDev* c, aok::ChunkRef* fra
 int aokk_cast(const aok::SceneDev* s, const aok::CamDev* c, const aok::ChunkRef* frame, uint4* hit, float* t,
               uint32_t* counts, void* stream);
 int aokk_ray_dirs(const aok::CamDev* c, float* dirs, void* stream);
+int aokk_read_bw(const void* buf, size_t n16, int passes, uint32_t* sink, int sms, void* stream);
 // Batched: one selection launch over (view, chunk), then one persistent
 // casting launch over all views' warp tiles.
 int aokk_select_batch(const aok::BatchParams* p, void* stream);

@@ -688,6 +688,40 @@ int aokk_ray_dirs(const CamDev* c, float* dirs, void* stream) {
 }
 
 // ---------------------------------------------------------------------------
+// Read bandwidth microbenchmark: one resident grid streams the buffer `passes`
+// times in 16-byte words through L2 (ld.global.cg, L1 bypassed; volatile so
+// that no pass is merged with another), four independent loads in flight per
+// thread.  A buffer smaller than L2 measures L2 read bandwidth, a larger one
+// HBM read bandwidth.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t ld_cg_xor(const uint4* p) {
+    uint32_t a, b, c, d;
+    asm volatile("ld.global.cg.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(a), "=r"(b), "=r"(c), "=r"(d) : "l"(p));
+    return a ^ b ^ c ^ d;
+}
+
+__global__ void __launch_bounds__(512) read_bw_kernel(const uint4* __restrict__ p, size_t n, int passes,
+                                                      uint32_t* __restrict__ sink) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    uint32_t acc = 0;
+    for (int r = 0; r < passes; r++) {
+        size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+        for (; i + 3 * stride < n; i += 4 * stride)
+            acc ^= ld_cg_xor(p + i) ^ ld_cg_xor(p + i + stride) ^ ld_cg_xor(p + i + 2 * stride) ^
+                   ld_cg_xor(p + i + 3 * stride);
+        for (; i < n; i += stride) acc ^= ld_cg_xor(p + i);
+    }
+    if (acc == 0x9E3779B9u) sink[0] = acc;  // data-dependent store keeps the loads
+}
+
+int aokk_read_bw(const void* buf, size_t n16, int passes, uint32_t* sink, int sms, void* stream) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, read_bw_kernel, 512, 0);
+    read_bw_kernel<<<sms * std::max(per_sm, 1), 512, 0, (cudaStream_t)stream>>>((const uint4*)buf, n16, passes, sink);
+    return status_of(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
 // Render without allocating: the per-frame chunk table lives in a file-scope
 // device array instead of scene-owned memory.  The array is created when the
 // module loads on a device and stays until the process exits.  Its device

@@ -765,4 +765,36 @@ int aok_ray_dirs(aok_ctx* ctx, const aok_camera* cam, float* dirs, void* stream)
     return st ? cuda_status(ctx, cudaGetLastError()) : AOK_OK;
 }
 
+int aok_read_bandwidth(aok_ctx* ctx, uint64_t bytes, int reps, double* gbs) {
+    if (!ctx || !gbs || bytes < 16 || reps < 1) return AOK_E_INVALID;
+    cudaSetDevice(ctx->device);
+    bytes &= ~(uint64_t)15;
+    void* buf = nullptr;
+    int st = dev_alloc(ctx, &buf, bytes + 16);
+    if (st) return st;
+    uint32_t* sink = (uint32_t*)((char*)buf + bytes);
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(buf, 0x5A, bytes + 16, s);
+    const int sms = aokk_sm_count(ctx->device);
+    // warm-up passes (below the L2 size they also make the buffer resident), then one timed launch
+    if (e == cudaSuccess && aokk_read_bw(buf, bytes / 16, 2, sink, sms, s)) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess && aokk_read_bw(buf, bytes / 16, reps, sink, sms, s)) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+    dev_free(ctx, buf, bytes + 16);
+    if (e != cudaSuccess) return cuda_status(ctx, e);
+    *gbs = ms > 0.0f ? (double)bytes * reps / (ms * 1e-3) / 1e9 : 0.0;
+    return AOK_OK;
+}
+
 }  // extern "C"

@@ -244,3 +244,17 @@ def test_evict_renders_as_empty(ctx):
     torch.cuda.synchronize()
     assert decode(hit, t)["hit"].sum() == 0
     sc.destroy()
+
+
+def test_read_bandwidth_microbenchmark(ctx):
+    l2 = aok.read_bandwidth(ctx, 32 << 20, 200)
+    hbm = aok.read_bandwidth(ctx, 1 << 30, 3)
+    assert 100.0 < hbm < l2 < 1e6, (hbm, l2)
+    for nbytes, reps in ((8, 1), (1 << 20, 0)):
+        with pytest.raises(aok.AokError) as ex:
+            aok.read_bandwidth(ctx, nbytes, reps)
+        assert ex.value.status == aok.AOK_E_INVALID
+    used, budget = ctx.memory()
+    with pytest.raises(aok.AokError) as ex:
+        aok.read_bandwidth(ctx, budget - used + (1 << 20), 1)
+    assert ex.value.status == aok.AOK_E_OOM
