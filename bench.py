@@ -49,20 +49,29 @@ def peaks():
 
 
 PROFILE = os.path.join(ROOT, "profiles", "cast_kernel_city4096_1080p.md")
-KERNEL_SRC = os.path.join(ROOT, "paper_2505_02017_gb300", "csrc", "aok_kernels.cu")
+KERNEL_SRCS = [os.path.join(ROOT, "paper_2505_02017_gb300", "csrc", f)
+               for f in ("aok_kernels.cu", "aok_trace.cuh", "aok_internal.h")]
+
+
+def kernel_sources_hash():
+    """sha256 (16 hex digits) of the sources cast_kernel is compiled from."""
+    import hashlib
+    h = hashlib.sha256()
+    for p in KERNEL_SRCS:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def profiled_traffic():
     """DRAM bytes (read + write) of one cast_kernel launch on this workload from
-    the committed ncu summary, if it was taken on the current kernel source;
+    the committed ncu summary, if it was taken on the current kernel sources;
     else None (the counters no longer describe the kernel)."""
-    import hashlib
     import re
     try:
-        with open(KERNEL_SRC, "rb") as f:
-            h = hashlib.sha256(f.read()).hexdigest()[:16]
+        h = kernel_sources_hash()
         with open(PROFILE) as f:
-            m = re.search(r"^traffic: (\d+) bytes per launch, aok_kernels\.cu sha256 ([0-9a-f]{16})", f.read(), re.M)
+            m = re.search(r"^traffic: (\d+) bytes per launch, kernel sources sha256 ([0-9a-f]{16})", f.read(), re.M)
     except OSError:
         return None
     return int(m.group(1)) if m and m.group(2) == h else None
@@ -292,6 +301,32 @@ def bench_served(aok, ctx, base_scene, threads, rates=(200, 500, 1000, 2000, 400
     return out
 
 
+def bench_tiles(aok, ctx, scene, world, flush, reps=20):
+    """The paper's tile-chunk pipeline (aok_render_tiles) against the per-ray
+    march (aok_render) on the benchmark frame: first frame (no Hi-Z history)
+    and steady state (the previous frame's Hi-Z), same outputs required."""
+    import torch
+    cam = sg.ground_camera(world, CAM_SEED, W, H)
+    hit, t = aok.alloc_frame(W, H)
+    hit2, t2 = aok.alloc_frame(W, H)
+    stream = torch.cuda.current_stream()
+
+    def first():
+        aok.tiles_forget(ctx)
+        aok.render_tiles(ctx, scene, cam, TAU, hit2, t2)
+
+    out = {"workload": WORKLOAD}
+    for name, fn in (("march", lambda: aok.render(ctx, scene, cam, TAU, hit, t)), ("tiles_first_frame", first),
+                     ("tiles_steady", lambda: aok.render_tiles(ctx, scene, cam, TAU, hit2, t2))):
+        for _ in range(3):
+            fn()
+        out[name + "_ms_median"], out[name + "_ms_best"] = time_events(fn, reps, flush, stream)
+        if name != "march":
+            out[name + "_stats"] = aok.tiles_stats(ctx)
+    out["identical_outputs"] = bool(torch.equal(hit, hit2) and torch.equal(t.view(torch.int32), t2.view(torch.int32)))
+    return out
+
+
 def bench_open(aok, ctx, threads, n_poses=300):
     """Open world 65536x65536x1024 (128x128x2 chunks of 512^3, 4 LODs), view
     distance 16384: along a 300-pose path at 2560x1440, only the (chunk, LOD)
@@ -305,20 +340,27 @@ def bench_open(aok, ctx, threads, n_poses=300):
     scene = aok.Scene(ctx, spec, node_words=512 << 20, leaves=256 << 20, mat_bytes=16 << 30)
     st = Streamer(ctx, world, scene, threads)
     hit, t = aok.alloc_frame(2560, 1440)
+    hit2, t2 = aok.alloc_frame(2560, 1440)
     stream = torch.cuda.current_stream()
-    sel_ms, cast_ms, host = [], [], []
-    max_bytes = 0
+    sel_ms, cast_ms, tiles_ms, host = [], [], [], []
+    tiles_same = True
+    aok.tiles_forget(ctx)
     for i, cam in enumerate(cams):
         host.append(st.update(cam, TAU))
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         e[0].record(stream)
         aok.select_chunks(ctx, scene, cam, TAU, stream=stream)
         e[1].record(stream)
         aok.cast_selected(ctx, scene, cam, hit, t, stream=stream)
         e[2].record(stream)
-        e[2].synchronize()
+        # the paper's tile-chunk pipeline on the same frame (Hi-Z history: the previous pose)
+        aok.render_tiles(ctx, scene, cam, TAU, hit2, t2, stream=stream)
+        e[3].record(stream)
+        e[3].synchronize()
         sel_ms.append(e[0].elapsed_time(e[1]))
         cast_ms.append(e[1].elapsed_time(e[2]))
+        tiles_ms.append(e[2].elapsed_time(e[3]))
+        tiles_same &= torch.equal(hit, hit2) and torch.equal(t.view(torch.int32), t2.view(torch.int32))
     frame = [a + b for a, b in zip(sel_ms, cast_ms)]
     rays = 2560 * 1440
     srt = sorted(frame)
@@ -331,7 +373,10 @@ def bench_open(aok, ctx, threads, n_poses=300):
            "first_frame_built": host[0]["built"], "first_frame_build_s": round(host[0]["build_s"], 2),
            "later_frames_built_total": sum(h["built"] for h in host[1:]),
            "later_frames_evicted_total": sum(h["evicted"] for h in host[1:]),
-           "streaming_host_s_total": round(sum(h["plan_s"] + h["build_s"] + h["upload_s"] for h in host), 2)}
+           "streaming_host_s_total": round(sum(h["plan_s"] + h["build_s"] + h["upload_s"] for h in host), 2),
+           "tile_pipeline": {"frame_ms_median": sorted(tiles_ms)[len(tiles_ms) // 2],
+                             "march_frame_ms_median": srt[len(srt) // 2],
+                             "identical_outputs_all_poses": bool(tiles_same)}}
     scene.destroy()
     return out
 
@@ -461,6 +506,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-open", action="store_true")
+    ap.add_argument("--no-tiles", action="store_true")
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--cpu-scaling", action="store_true",
                     help="print the oracle's 1-thread / all-thread rays/s for three workloads and exit")
@@ -588,6 +634,8 @@ def main():
         "clocks": clk,
         "wall_s_timed": wall,
     }
+    if not args.no_tiles:
+        out["tile_pipeline"] = bench_tiles(aok, ctx, scene, world, flush)
     if not args.no_batch:
         out["batched"] = bench_batched(aok, ctx, scene, world, flush)
     if not args.no_serve:

@@ -84,6 +84,9 @@ def lib() -> ctypes.CDLL:
             "aok_render": [vp, u32, P(Camera), dbl, P(Frame), vp],
             "aok_render_counted": [vp, u32, P(Camera), dbl, P(Frame), vp, vp],
             "aok_render_noalloc": [vp, u32, P(Camera), dbl, P(Frame), vp],
+            "aok_render_tiles": [vp, u32, P(Camera), dbl, P(Frame), vp],
+            "aok_tiles_stats": [vp, P(u64)],
+            "aok_tiles_forget": [vp],
             "aok_ray_dirs": [vp, P(Camera), vp, vp],
             "aok_read_bandwidth": [vp, ctypes.c_uint64, ctypes.c_int, P(dbl)],
             "aok_cast_selected": [vp, u32, P(Camera), P(Frame), vp],
@@ -311,6 +314,29 @@ def render(ctx: Context, scene: Scene, cam, tau: float, hit, t, stream=None):
     c = to_camera(cam)
     return check(lib().aok_render(ctx.h, scene.id, ctypes.byref(c), float(tau), ctypes.byref(f),
                                   _stream_handle(stream)), "aok_render")
+
+
+def render_tiles(ctx: Context, scene: Scene, cam, tau: float, hit, t, stream=None):
+    """The frame of render() through the tile-chunk pipeline (aok_render_tiles)."""
+    f = frame_of(hit, t)
+    c = to_camera(cam)
+    return check(lib().aok_render_tiles(ctx.h, scene.id, ctypes.byref(c), float(tau), ctypes.byref(f),
+                                        _stream_handle(stream)), "aok_render_tiles")
+
+
+TILE_STATS = ("regions_with_pairs", "items_marched_1", "items_culled_1", "items_marched_2", "items_culled_2",
+              "pixel_traces", "pixel_skips", "resolve_failures")
+
+
+def tiles_stats(ctx: Context) -> dict:
+    """Counters of the last render_tiles frame (aok_tiles_stats; synchronises)."""
+    a = (ctypes.c_uint64 * 8)()
+    check(lib().aok_tiles_stats(ctx.h, a), "aok_tiles_stats")
+    return dict(zip(TILE_STATS, (int(v) for v in a)))
+
+
+def tiles_forget(ctx: Context):
+    return check(lib().aok_tiles_forget(ctx.h), "aok_tiles_forget")
 
 
 def cast_selected(ctx: Context, scene: Scene, cam, hit, t, stream=None):

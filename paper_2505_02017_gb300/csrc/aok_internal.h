@@ -46,6 +46,22 @@ struct CamDev {
     double sf;              // StreamingFactor for Eq. 1
 };
 
+// Device buffers of the tile-chunk pipeline (Sec. 3.5) for one resolution.
+constexpr int kTileStats = 8;
+struct TileDev {
+    unsigned long long* vis;   // [W*H] visibility keys (distance | march order | chunk), ~0 = none
+    float* hiz_prev;           // [tiles] previous frame's per-tile max hit distance (no culling: huge)
+    float* hiz;                // [tiles] per-tile max distance after pass 1 of this frame
+    float* hiz_next;           // [tiles] this frame's final per-tile max distance
+    int4* rect;                // [chunks] tile rectangle [x0, x1) x [y0, y1) of the chunk's AABB
+    float* dmin;               // [chunks] lower bound of the distance from the camera to the AABB
+    uint32_t* area;            // [chunks] tiles in the rectangle (0: no pairs)
+    uint32_t* list;            // [chunks] chunks with pairs, ascending
+    unsigned long long* offs;  // [chunks + 1] exclusive prefix of their areas; offs[n_list] = pairs
+    unsigned long long* stats; // [kTileStats] n_list, items traced / culled per pass, pixel traces ...
+    int32_t tiles_x, tiles_y;
+};
+
 // A view of a batch: which scene, which camera, where the pixels go.
 struct ViewDev {
     SceneDev scene;
@@ -86,6 +102,8 @@ int aokk_select(const aok::SceneDev* s, const aok::CamDev* c, aok::ChunkRef* fra
 int aokk_cast(const aok::SceneDev* s, const aok::CamDev* c, const aok::ChunkRef* frame, uint4* hit, float* t,
               uint32_t* counts, void* stream);
 int aokk_ray_dirs(const aok::CamDev* c, float* dirs, void* stream);
+int aokk_tiles_frame(const aok::SceneDev* S, const aok::CamDev* C, const aok::ChunkRef* frame, const aok::TileDev* T,
+                     uint4* hit, float* t, int sms, void* stream);
 int aokk_read_bw(const void* buf, size_t n16, int passes, uint32_t* sink, int sms, void* stream);
 // Batched: one selection launch over (view, chunk), then one persistent
 // casting launch over all views' warp tiles.

@@ -1,17 +1,7 @@
 // CUDA kernels (sm_103a): per-frame chunk LOD selection and visibility, and
 // per-pixel primary-ray first-hit casting through the chunk grid and the
-// selected sparse voxel DAGs (Aokana Sec. 3.4-3.5).
-//
-// Exactness.  The ray is origin + t d with the origin on a 2^-12 grid and d
-// an FP32 vector.  Every ordering decision of the traversal (which face a
-// cell is left through, which child octant holds the entry point) compares
-// two plane-crossing parameters t_a = (P_a - o_a) / d_a.  The traversal works
-// in a frame mirrored so that every d_a >= 0, writes N_a = (P_a - o_a) 2^12 as
-// an int32 and |d_a| = m_a 2^E_a (24-bit mantissa), and decides
-// t_a < t_b  <=>  N_a m_b 2^(E_b - E_a) < N_b m_a  with 64-bit products and an
-// exact shift comparison.  No decision is approximated, so the hit voxel,
-// LOD, material and normal equal those of the exact real ray; only the
-// reported distance is rounded (FP32, relative error ~1e-7).
+// selected sparse voxel DAGs (Aokana Sec. 3.4-3.5).  The exact traversal
+// itself is in aok_trace.cuh.
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -20,56 +10,11 @@
 #include <vector>
 
 #include "aok_internal.h"
+#include "aok_trace.cuh"
 
 using namespace aok;
 
 namespace {
-
-// ---------------------------------------------------------------------------
-// exact comparison of plane-crossing parameters
-// ---------------------------------------------------------------------------
-// N1 / (m1 2^E1) < N2 / (m2 2^E2), s = E2 - E1, m1, m2 > 0, |N| < 2^31, m < 2^24.
-__device__ __forceinline__ bool tlt(int32_t N1, int32_t m1, int32_t N2, int32_t m2, int32_t s) {
-    const long long P = (long long)N1 * m2;
-    const long long Q = (long long)N2 * m1;
-    if (s >= 0) {
-        // P 2^s < Q  <=>  P <= floor((Q - 1) / 2^s)
-        return P <= ((Q - 1) >> min(s, 63));
-    }
-    // P 2^s < Q  <=>  floor(P / 2^-s) < Q
-    return (P >> min(-s, 63)) < Q;
-}
-
-// |d| = m 2^E; a zero component becomes m = 1, E = -400 (crossings at +-infinity).
-__device__ __forceinline__ void decompose(float d, int32_t& m, int32_t& E) {
-    const uint32_t b = __float_as_uint(d) & 0x7FFFFFFFu;
-    const uint32_t ex = b >> 23, man = b & 0x7FFFFFu;
-    if (b == 0) { m = 1; E = -400; }
-    else if (ex == 0) { m = (int32_t)man; E = -149; }
-    else { m = (int32_t)(man | 0x800000u); E = (int32_t)ex - 150; }
-}
-
-// Ray direction of pixel (px, py): IEEE binary32, one rounding per operation.
-__device__ __forceinline__ void ray_dir(const CamDev& c, int px, int py, float d[3]) {
-    const float fW = __int2float_rn(c.W), fH = __int2float_rn(c.H);
-    const float a = __int2float_rn(2 * px + 1);
-    const float b = __fdiv_rn(a, fW);
-    const float cc = __fsub_rn(b, 1.0f);
-    const float e = __fmul_rn(cc, c.tan_half);
-    const float aspect = __fdiv_rn(fW, fH);
-    const float u = __fmul_rn(e, aspect);
-    const float a2 = __int2float_rn(2 * py + 1);
-    const float b2 = __fdiv_rn(a2, fH);
-    const float c2 = __fsub_rn(1.0f, b2);
-    const float v = __fmul_rn(c2, c.tan_half);
-#pragma unroll
-    for (int i = 0; i < 3; i++) {
-        const float p = __fmul_rn(c.R[3 * i + 0], u);
-        const float q = __fmul_rn(c.R[3 * i + 1], v);
-        const float s = __fadd_rn(p, q);
-        d[i] = __fsub_rn(s, c.R[3 * i + 2]);
-    }
-}
 
 // Eq. 1 for the octree block b at level n: LODError <= 0 (load), squared, FP64, fixed order.
 __device__ __forceinline__ bool lod_loads(int n, int bx, int by, int bz, int mlog, const float o[3], double sf) {
@@ -146,326 +91,6 @@ __global__ void select_batch_kernel(const __grid_constant__ BatchParams P) {
     const int chunk = blockIdx.x * blockDim.x + threadIdx.x;
     if (chunk < nch) select_one(v.scene, v.cam, v.frame, nullptr, nullptr, nullptr, chunk);
 }
-
-// ---------------------------------------------------------------------------
-// per-chunk DAG traversal in the chunk's mirrored local frame
-// ---------------------------------------------------------------------------
-// FAST rays: the exponents of the non-zero |d| components span <= 6, so the
-// mantissas are shifted to a common exponent (m < 2^30, zero components get
-// m = 0, i.e. crossings at +-infinity) and t_a < t_b <=> N_a m_b < N_b m_a;
-// other rays keep (m, E) per axis and use tlt().
-template <bool FAST>
-__device__ __forceinline__ bool tltf(int32_t N1, int32_t m1, int32_t N2, int32_t m2, int32_t s) {
-    if (FAST) return (long long)N1 * m2 < (long long)N2 * m1;
-    return tlt(N1, m1, N2, m2, s);
-}
-
-// Cells are addressed by level k (side 2^k LOD-0 units) and mirrored integer
-// coordinates c.  Levels R = log2(M) (root) .. n+3 are interior nodes, n+2 a
-// 4x4x4 leaf block, n+1 a 2x2x2 group in it, n a voxel of LOD n.  Leaf bits
-// are addressed in stored (unmirrored) order: along a mirrored axis the index
-// inside a block is c ^ 3 (group: c ^ 1).
-struct RayState {
-    float d[3];
-    int32_t m[3], E[3];
-    uint32_t mir;
-};
-
-struct HitRec {
-    int32_t c[3];       // voxel index (mirrored, chunk-local, voxel units of the LOD)
-    int e;              // entry axis (3 = origin inside)
-    int32_t Ne;         // entry plane numerator
-    uint32_t mat;
-};
-
-struct Counters {
-    uint32_t v_int, v_leaf, rbytes;
-};
-
-// Returns true on a hit inside this chunk.  (e, Ne): entry plane into the chunk
-// (e = 3: the origin lies inside the chunk).  Oloc: mirrored local origin numerators.
-template <bool FAST, bool COUNT>
-__device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& ref, const RayState& r,
-                                            const int32_t Oloc[3], int e, int32_t Ne, HitRec& hit, Counters& cnt) {
-    const uint32_t* __restrict__ nodes = S.nodes;
-    const int R = S.mlog;
-    const int n = (int)ref.lod;
-    uint32_t sidx[kMaxLevels];
-    uint32_t smask[kMaxLevels];
-    int k = R;
-    int32_t c0 = 0, c1 = 0, c2 = 0;
-    int32_t me = 1, Ee = 0;
-    if (e < 3) { me = r.m[e]; Ee = r.E[e]; }
-    uint64_t lmu = 0;
-    const int f1 = (r.mir & 1u) ? 1 : 0, f2 = (r.mir & 2u) ? 1 : 0, f4 = (r.mir & 4u) ? 1 : 0;
-    uint32_t pm8 = 0;   // parent's child mask, stored octant order (node mask / leaf groups / group voxels)
-    uint32_t g8 = 0;    // group occupancy of the current leaf block
-    bool occ = true;
-    for (;;) {
-        if (occ) {
-            if (k == n) {
-                hit.c[0] = c0; hit.c[1] = c1; hit.c[2] = c2;
-                hit.e = e;
-                hit.Ne = Ne;
-                // material through the depth-first index (Sec. 3.3)
-                const uint32_t mirv = r.mir;
-                const int32_t side = (1 << (R - n)) - 1;
-                const int32_t u0 = (mirv & 1u) ? side - c0 : c0;
-                const int32_t u1 = (mirv & 2u) ? side - c1 : c1;
-                const int32_t u2 = (mirv & 4u) ? side - c2 : c2;
-                // node = [hdr, count, (child, earlier siblings' count) x k]: one word per level
-                uint32_t idx = 0;
-                for (int j = R; j >= n + 3; j--) {
-                    const int sh = j - 1 - n;
-                    const int oct = ((u0 >> sh) & 1) | (((u1 >> sh) & 1) << 1) | (((u2 >> sh) & 1) << 2);
-                    const int rk = __popc(smask[j] & ((1u << oct) - 1u));
-                    idx += nodes[sidx[j] + 3 + 2 * rk];
-                    if (COUNT) cnt.rbytes += rk * ((j - 1 == n + 2) ? 8u : 4u);
-                }
-                const int bit = (u0 & 3) + 4 * (u1 & 3) + 16 * (u2 & 3);
-                idx += (uint32_t)__popcll(lmu & ((1ull << bit) - 1ull));
-                hit.mat = S.mats[ref.mat_base + idx];
-                if (COUNT) cnt.rbytes += 1;
-                return true;
-            }
-            if (k >= n + 2) {
-                uint32_t idx;
-                if (k == R) {
-                    idx = ref.root;
-                } else {
-                    const uint32_t oct = ((uint32_t)(c0 & 1) | ((uint32_t)(c1 & 1) << 1) | ((uint32_t)(c2 & 1) << 2)) ^ r.mir;
-                    idx = nodes[sidx[k + 1] + 2 + 2 * __popc(smask[k + 1] & ((1u << oct) - 1u))];
-                }
-                if (k >= n + 3) {
-                    pm8 = nodes[idx] & 0xFFu;
-                    sidx[k] = idx;
-                    smask[k] = pm8;
-                    if (COUNT) cnt.v_int++;
-                } else {
-                    lmu = S.leaves[idx];
-                    uint64_t t = lmu | (lmu >> 1);
-                    t |= t >> 4;
-                    t |= t >> 16;
-                    g8 = (uint32_t)((t & 1) | ((t >> 1) & 2) | ((t >> 6) & 4) | ((t >> 7) & 8) | ((t >> 28) & 16) |
-                                    ((t >> 29) & 32) | ((t >> 34) & 64) | ((t >> 35) & 128));
-                    pm8 = g8;
-                    if (COUNT) cnt.v_leaf++;
-                }
-            } else {
-                // entering a 2x2x2 group of the leaf: its 8 voxel bits in octant order
-                const uint64_t v = lmu >> (((c0 & 1) ^ f1) * 2 + ((c1 & 1) ^ f2) * 8 + ((c2 & 1) ^ f4) * 32);
-                pm8 = (uint32_t)((v & 3) | ((v >> 2) & 0xC) | ((v >> 12) & 0x30) | ((v >> 14) & 0xC0));
-            }
-            // child of cell (k, c) holding the entry point: compare t_entry with the mid planes
-            const int kk = k - 1;
-            const int32_t mid0 = ((2 * c0 + 1) << (kk + kFix)) - Oloc[0];
-            const int32_t mid1 = ((2 * c1 + 1) << (kk + kFix)) - Oloc[1];
-            const int32_t mid2 = ((2 * c2 + 1) << (kk + kFix)) - Oloc[2];
-            const int32_t b0 = (e != 0) && !tltf<FAST>(Ne, me, mid0, r.m[0], r.E[0] - Ee);
-            const int32_t b1 = (e != 1) && !tltf<FAST>(Ne, me, mid1, r.m[1], r.E[1] - Ee);
-            const int32_t b2 = (e != 2) && !tltf<FAST>(Ne, me, mid2, r.m[2], r.E[2] - Ee);
-            c0 = 2 * c0 + b0;
-            c1 = 2 * c1 + b1;
-            c2 = 2 * c2 + b2;
-            k = kk;
-        } else {
-            // leave cell (k, c) through its nearest exit face
-            const int32_t N0 = ((c0 + 1) << (k + kFix)) - Oloc[0];
-            const int32_t N1 = ((c1 + 1) << (k + kFix)) - Oloc[1];
-            const int32_t N2 = ((c2 + 1) << (k + kFix)) - Oloc[2];
-            const bool xy = tltf<FAST>(N0, r.m[0], N1, r.m[1], r.E[1] - r.E[0]);
-            const int32_t Na = xy ? N0 : N1, ma = xy ? r.m[0] : r.m[1], Ea = xy ? r.E[0] : r.E[1];
-            const bool az = tltf<FAST>(Na, ma, N2, r.m[2], r.E[2] - Ea);
-            int ax;
-            if (az) { ax = xy ? 0 : 1; Ne = Na; me = ma; Ee = Ea; }
-            else { ax = 2; Ne = N2; me = r.m[2]; Ee = r.E[2]; }
-            e = ax;
-            int32_t cax;
-            if (ax == 0) cax = ++c0;
-            else if (ax == 1) cax = ++c1;
-            else cax = ++c2;
-            if ((cax << k) >= (1 << R)) return false;  // left the chunk
-            if ((cax & 1) == 0) {
-                do {
-                    c0 >>= 1; c1 >>= 1; c2 >>= 1;
-                    cax >>= 1;
-                    k++;
-                } while (k < R && (cax & 1) == 0);
-                pm8 = k >= n + 2 ? smask[k + 1] : g8;  // popped into a new parent (a node or the leaf)
-            }
-        }
-        // occupancy of cell (k, c) in its parent
-        occ = (pm8 >> (((uint32_t)(c0 & 1) | ((uint32_t)(c1 & 1) << 1) | ((uint32_t)(c2 & 1) << 2)) ^ r.mir)) & 1u;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// one pixel: world-grid chunk march + per-chunk DAG traversal
-// ---------------------------------------------------------------------------
-template <bool FAST, bool COUNT>
-__device__ __forceinline__ void trace_pixel_t(const SceneDev& S, const CamDev& C, const ChunkRef* __restrict__ frame,
-                                            const RayState& r, uint4* __restrict__ out_hit, float* __restrict__ out_t,
-                                            uint32_t* __restrict__ counts, size_t pix) {
-    int32_t Ow[3], Wfix[3];
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-        Wfix[a] = S.grid[a] << (S.mlog + kFix);
-        Ow[a] = ((r.mir >> a) & 1u) ? Wfix[a] - C.O[a] : C.O[a];
-    }
-    Counters cnt = {0, 0, 0};
-    HitRec hit;
-    bool found = false;
-    const int cs = S.mlog + kFix;  // chunk side as a shift of numerator units
-    int e = 3;
-    int32_t Ne = 0, me = 1, Ee = 0;
-    int32_t cc[3];
-    bool alive = true;
-    if (Ow[0] >= 0 && Ow[1] >= 0 && Ow[2] >= 0 && Ow[0] < Wfix[0] && Ow[1] < Wfix[1] && Ow[2] < Wfix[2]) {
-#pragma unroll
-        for (int a = 0; a < 3; a++) cc[a] = Ow[a] >> cs;
-    } else {
-        // enter the world box: latest entry plane vs earliest exit plane
-        e = -1;
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            if (Ow[a] >= Wfix[a] || (r.d[a] == 0.0f && Ow[a] < 0)) alive = false;
-            if (Ow[a] < 0) {
-                const int32_t Na = -Ow[a];
-                if (e < 0 || tltf<FAST>(Ne, me, Na, r.m[a], r.E[a] - Ee)) { e = a; Ne = Na; me = r.m[a]; Ee = r.E[a]; }
-            }
-        }
-        int32_t Nx = Wfix[0] - Ow[0], mx = r.m[0], Ex = r.E[0];
-#pragma unroll
-        for (int a = 1; a < 3; a++) {
-            const int32_t Na = Wfix[a] - Ow[a];
-            if (tltf<FAST>(Na, r.m[a], Nx, mx, Ex - r.E[a])) { Nx = Na; mx = r.m[a]; Ex = r.E[a]; }
-        }
-        if (alive && e >= 0 && tltf<FAST>(Ne, me, Nx, mx, Ex - Ee)) {
-            const float te_num = (float)Ne / fabsf(r.d[e]);
-#pragma unroll
-            for (int a = 0; a < 3; a++) {
-                if (a == e) { cc[a] = 0; continue; }
-                const float pa = (float)Ow[a] + te_num * fabsf(r.d[a]);
-                int32_t cell = (int32_t)floorf(pa * (1.0f / (float)(1 << cs)));
-                cell = max(0, min(cell, S.grid[a] - 1));
-                // exact correction: cell*M <= x_a(t_entry) < (cell+1)*M
-                while (cell + 1 < S.grid[a] && !tltf<FAST>(Ne, me, ((cell + 1) << cs) - Ow[a], r.m[a], r.E[a] - Ee)) cell++;
-                while (cell > 0 && tltf<FAST>(Ne, me, (cell << cs) - Ow[a], r.m[a], r.E[a] - Ee)) cell--;
-                cc[a] = cell;
-            }
-        } else {
-            alive = false;
-        }
-    }
-    const float dn = sqrtf(__fadd_rn(__fadd_rn(__fmul_rn(r.d[0], r.d[0]), __fmul_rn(r.d[1], r.d[1])), __fmul_rn(r.d[2], r.d[2])));
-    float inv[3];
-#pragma unroll
-    for (int a = 0; a < 3; a++) inv[a] = 1.0f / r.d[a];
-    while (alive) {
-        int32_t u[3];
-#pragma unroll
-        for (int a = 0; a < 3; a++) u[a] = ((r.mir >> a) & 1u) ? S.grid[a] - 1 - cc[a] : cc[a];
-        const ChunkRef ref = frame[(size_t)u[0] + (size_t)S.grid[0] * ((size_t)u[1] + (size_t)S.grid[1] * u[2])];
-        if (S.view_dist > 0.0f && e < 3) {
-            const float tent = (float)Ne / (4096.0f * fabsf(r.d[e]));
-            if (tent * dn > S.view_dist * 1.00001f + 1.0f) break;
-        }
-        if (ref.root != kNone) {
-            // skip chunks whose solid-voxel AABB (grown by 1/16 voxel) the ray misses
-            float tn = 0.0f, tf = 3.0e38f;
-            bool pass = true;
-#pragma unroll
-            for (int a = 0; a < 3; a++) {
-                const float lo = (float)((u[a] << S.mlog) + ref.aabb[a]) - 0.0625f;
-                const float hi = (float)((u[a] << S.mlog) + ref.aabb[3 + a]) + 0.0625f;
-                if (r.d[a] == 0.0f) {
-                    if (C.of[a] < lo || C.of[a] > hi) pass = false;
-                } else {
-                    float t1 = (lo - C.of[a]) * inv[a], t2 = (hi - C.of[a]) * inv[a];
-                    tn = fmaxf(tn, fminf(t1, t2));
-                    tf = fminf(tf, fmaxf(t1, t2));
-                }
-            }
-            if (pass && tn <= tf) {
-                int32_t Oloc[3];
-#pragma unroll
-                for (int a = 0; a < 3; a++) Oloc[a] = Ow[a] - (cc[a] << cs);
-                if (trace_chunk<FAST, COUNT>(S, ref, r, Oloc, e, Ne, hit, cnt)) {
-                    found = true;
-                    // un-mirror the voxel index to world LOD-0 units
-                    const int n = (int)ref.lod;
-                    const int32_t side = (1 << (S.mlog - n)) - 1;
-                    int32_t wxyz[3];
-#pragma unroll
-                    for (int a = 0; a < 3; a++) {
-                        const int32_t uv = ((r.mir >> a) & 1u) ? side - hit.c[a] : hit.c[a];
-                        wxyz[a] = (u[a] << S.mlog) + (uv << n);
-                    }
-                    float dist = 0.0f;
-                    if (hit.e < 3) dist = __fdiv_rn((float)hit.Ne * (1.0f / 4096.0f), fabsf(r.d[hit.e])) * dn;
-                    if (S.view_dist > 0.0f) {
-                        double dd = 0.0;
-                        if (hit.e < 3) {
-                            const double d0 = r.d[0], d1 = r.d[1], d2 = r.d[2];
-                            dd = (double)hit.Ne / (4096.0 * fabs((double)r.d[hit.e])) * sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-                        }
-                        if (dd > (double)S.view_dist) { found = false; break; }
-                    }
-                    const uint32_t normal = hit.e == 3 ? 7u : (uint32_t)(2 * hit.e) + ((r.mir >> hit.e) & 1u);
-                    out_hit[pix] = make_uint4((uint32_t)wxyz[0], (uint32_t)wxyz[1], (uint32_t)wxyz[2],
-                                              (uint32_t)n | (hit.mat << 8) | (normal << 16) | (1u << 19));
-                    out_t[pix] = dist;
-                    break;
-                }
-            }
-        }
-        // next chunk cell
-        const int32_t N0 = ((cc[0] + 1) << cs) - Ow[0];
-        const int32_t N1 = ((cc[1] + 1) << cs) - Ow[1];
-        const int32_t N2 = ((cc[2] + 1) << cs) - Ow[2];
-        const bool xy = tltf<FAST>(N0, r.m[0], N1, r.m[1], r.E[1] - r.E[0]);
-        const int32_t Na = xy ? N0 : N1, ma = xy ? r.m[0] : r.m[1], Ea = xy ? r.E[0] : r.E[1];
-        const bool az = tltf<FAST>(Na, ma, N2, r.m[2], r.E[2] - Ea);
-        int ax;
-        if (az) { ax = xy ? 0 : 1; Ne = Na; me = ma; Ee = Ea; }
-        else { ax = 2; Ne = N2; me = r.m[2]; Ee = r.E[2]; }
-        e = ax;
-        if (++cc[ax] >= S.grid[ax]) break;
-    }
-    if (!found) {
-        out_hit[pix] = make_uint4(0u, 0u, 0u, 0xFFu | (7u << 16));
-        out_t[pix] = __int_as_float(0x7F800000);
-    }
-    if (COUNT) {
-        counts[3 * pix + 0] = cnt.v_int;
-        counts[3 * pix + 1] = cnt.v_leaf;
-        counts[3 * pix + 2] = cnt.rbytes;
-    }
-}
-
-template <bool COUNT>
-__device__ __forceinline__ void trace_pixel(const SceneDev& S, const CamDev& C, const ChunkRef* __restrict__ frame,
-                                            int px, int py, uint4* __restrict__ out_hit, float* __restrict__ out_t,
-                                            uint32_t* __restrict__ counts, size_t pix) {
-    RayState r;
-    ray_dir(C, px, py, r.d);
-    r.mir = 0;
-    int emin = 1 << 20, emax = -(1 << 20);
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-        decompose(r.d[a], r.m[a], r.E[a]);
-        if (r.d[a] < 0.0f) r.mir |= 1u << a;
-        if (r.d[a] != 0.0f) { emin = min(emin, r.E[a]); emax = max(emax, r.E[a]); }
-    }
-    if (emax - emin <= 6) {
-#pragma unroll
-        for (int a = 0; a < 3; a++) { r.m[a] = r.d[a] != 0.0f ? r.m[a] << (r.E[a] - emin) : 0; r.E[a] = 0; }
-        trace_pixel_t<true, COUNT>(S, C, frame, r, out_hit, out_t, counts, pix);
-    } else {
-        trace_pixel_t<false, COUNT>(S, C, frame, r, out_hit, out_t, counts, pix);
-    }
-}
-
 
 // 16 x 8 pixel tiles, warps of 8 x 4 pixels
 template <bool COUNT>

@@ -343,6 +343,7 @@ void aok_destroy(aok_ctx* ctx) {
     dev_free(ctx, ctx->host_t_dev, ctx->host_frame_px * 4);
     dev_free(ctx, ctx->d_counter, sizeof(uint32_t) * 16);
     dev_free(ctx, ctx->d_single_queue, 2 * sizeof(unsigned long long));
+    dev_free(ctx, ctx->tiles.block, ctx->tiles.bytes);
     if (ctx->staging) cudaFreeHost(ctx->staging);
     if (ctx->pinned_word) cudaFreeHost(ctx->pinned_word);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
@@ -714,6 +715,110 @@ int aok_cast_selected(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, const
     if (ctx->single_persistent) st = render_persistent(ctx, sc, cd, frame, stream, false);
     else st = aokk_cast(&sd, &cd, sc->d_frame, (uint4*)frame->hit, frame->t, nullptr, stream);
     return st ? cuda_status(ctx, cudaGetLastError()) : AOK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// tile-chunk pipeline (Sec. 3.5)
+// ---------------------------------------------------------------------------
+static constexpr uint32_t kFarBits = 0x7F7F7F7Fu;  // 3.4e38 as float: "no Hi-Z history"
+
+// (Re)allocate the pipeline's buffers for W x H and n_chunks regions; a new
+// scene or size starts without Hi-Z history.
+static int ensure_tiles(aok_ctx* ctx, uint32_t scene, int32_t W, int32_t H, int64_t nch, cudaStream_t s) {
+    TileState& ts = ctx->tiles;
+    if (ts.block && ts.W == W && ts.H == H && ts.n_chunks == nch) {
+        if (ts.scene != scene) {
+            const size_t tiles = (size_t)ts.dev.tiles_x * ts.dev.tiles_y;
+            if (cudaMemsetAsync(ts.dev.hiz_prev, 0x7F, tiles * sizeof(float), s) != cudaSuccess)
+                return cuda_status(ctx, cudaGetLastError());
+            ts.scene = scene;
+        }
+        return AOK_OK;
+    }
+    if (ts.block) {
+        cudaDeviceSynchronize();
+        dev_free(ctx, ts.block, ts.bytes);
+        ts = TileState{};
+    }
+    const int32_t tx = (W + 7) / 8, ty = (H + 7) / 8;
+    const size_t tiles = (size_t)tx * ty, px = (size_t)W * H, n = (size_t)nch;
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t sz[] = {px * 8, tiles * 4, tiles * 4, tiles * 4, n * 16, n * 4, n * 4, n * 4, (n + 1) * 8,
+                         kTileStats * 8};
+    size_t total = 0;
+    for (size_t b : sz) total += al(b);
+    void* block = nullptr;
+    int st = dev_alloc(ctx, &block, total);
+    if (st) return st;
+    char* p = (char*)block;
+    char* q[10];
+    for (int i = 0; i < 10; i++) { q[i] = p; p += al(sz[i]); }
+    TileDev& d = ts.dev;
+    d.vis = (unsigned long long*)q[0];
+    d.hiz_prev = (float*)q[1];
+    d.hiz = (float*)q[2];
+    d.hiz_next = (float*)q[3];
+    d.rect = (int4*)q[4];
+    d.dmin = (float*)q[5];
+    d.area = (uint32_t*)q[6];
+    d.list = (uint32_t*)q[7];
+    d.offs = (unsigned long long*)q[8];
+    d.stats = (unsigned long long*)q[9];
+    d.tiles_x = tx;
+    d.tiles_y = ty;
+    cudaError_t e = cudaMemsetAsync(d.vis, 0xFF, px * 8, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.hiz_prev, 0x7F, tiles * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.stats, 0, kTileStats * 8, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        dev_free(ctx, block, total);
+        ts = TileState{};
+        return cuda_status(ctx, e);
+    }
+    ts.block = block;
+    ts.bytes = total;
+    ts.W = W;
+    ts.H = H;
+    ts.n_chunks = nch;
+    ts.scene = scene;
+    return AOK_OK;
+}
+
+int aok_render_tiles(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double tau, const aok_frame* frame,
+                     void* stream) {
+    if (!ctx || !frame || !frame->hit || !frame->t) return AOK_E_INVALID;
+    if (((uintptr_t)frame->hit & 15) || ((uintptr_t)frame->t & 3)) return AOK_E_INVALID;
+    Scene* sc = find_scene(ctx, scene);
+    if (!sc) return AOK_E_NOT_RESIDENT;
+    if (sc->n_chunks > AOK_TILES_MAX_CHUNKS) return AOK_E_INVALID;
+    CamDev cd;
+    int st = make_cam(ctx, sc, cam, tau, &cd);
+    if (st) return st;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_status(ctx, cudaGetLastError());
+    st = ensure_tiles(ctx, scene, cd.W, cd.H, sc->n_chunks, (cudaStream_t)stream);
+    if (st) return st;
+    SceneDev sd = scene_dev(sc);
+    st = aokk_select(&sd, &cd, sc->d_frame, nullptr, nullptr, nullptr, stream);
+    if (!st) st = aokk_tiles_frame(&sd, &cd, sc->d_frame, &ctx->tiles.dev, (uint4*)frame->hit, frame->t,
+                                   ctx->sm_count, stream);
+    if (st) return cuda_status(ctx, cudaGetLastError());
+    std::swap(ctx->tiles.dev.hiz_prev, ctx->tiles.dev.hiz_next);  // this frame's depth culls the next one
+    return AOK_OK;
+}
+
+int aok_tiles_stats(aok_ctx* ctx, uint64_t* stats) {
+    if (!ctx || !stats) return AOK_E_INVALID;
+    if (!ctx->tiles.block) return AOK_E_INVALID;
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(stats, ctx->tiles.dev.stats, kTileStats * 8, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? AOK_OK : cuda_status(ctx, e);
+}
+
+int aok_tiles_forget(aok_ctx* ctx) {
+    if (!ctx) return AOK_E_INVALID;
+    ctx->tiles.scene = 0xFFFFFFFFu;
+    return AOK_OK;
 }
 
 int aok_set_single_view_kernel(aok_ctx* ctx, int persistent) {

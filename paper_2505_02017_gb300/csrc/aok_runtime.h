@@ -57,6 +57,18 @@ struct BatchArena {
 
 struct ServeState;
 
+// Buffers of the tile-chunk pipeline for one resolution and grid size (one
+// device allocation carved into the TileDev arrays), and the scene whose
+// Hi-Z history hiz_prev holds.
+struct TileState {
+    TileDev dev{};
+    void* block = nullptr;
+    size_t bytes = 0;
+    int32_t W = 0, H = 0;
+    int64_t n_chunks = 0;
+    uint32_t scene = 0xFFFFFFFFu;
+};
+
 struct aok_ctx_impl;
 
 }  // namespace aok
@@ -87,6 +99,7 @@ struct aok_ctx {
     float* host_t_dev = nullptr;
     size_t host_frame_px = 0;
     aok::ServeState* serve = nullptr;
+    aok::TileState tiles;
 };
 
 namespace aok {
