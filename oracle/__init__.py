@@ -7,13 +7,16 @@ their input worlds from ``scenegen``.
 
 The C source (``oracle.c``) is a plain restatement of the paper's definitions:
 LOD aggregation (Sec. 3.4), SVDAG geometry compression (Sec. 3.2), depth-first
-material indexing (Sec. 3.3), Eq. 1 LOD selection (Sec. 3.4) and the first-hit
+material indexing and colour-block compression (Sec. 3.3), Eq. 1 LOD
+selection (Sec. 3.4) and the first-hit
 query of the ray-marching and colour-resolve passes (Sec. 3.5), traced in FP64.
 
 Parity pins (see tests/test_oracle_*.py): DAG decompression equals the dense
 grid; per-level node counts equal brute-force distinct-block counts; leaf
 counts add up; the DFS order equals a sort by (octree path, leaf bit); the LOD
-rule on hand-made blocks; Eq. 1 recursive == closed form plus exact tie cases;
+rule on hand-made blocks; colour blocks == runs of equal values at e_c = 0,
+one block with the rounded mean for e_c >= 1, hand-worked merges and the
+greedy rule's invariants; Eq. 1 recursive == closed form plus exact tie cases;
 the FP64 caster equals a brute-force every-voxel caster on small worlds and
 analytic single-voxel cases.
 """
@@ -104,6 +107,11 @@ def lib() -> ctypes.CDLL:
         L.or_chunk_dense.argtypes = [vp, i32, i32, i32, i32, i32, vp, vp]
         L.or_cast.restype = ctypes.c_int
         L.or_cast.argtypes = [vp, vp, ctypes.POINTER(Cam), f64, vp, i64, vp, ctypes.c_int]
+        L.or_color_blocks.restype = ctypes.c_uint64
+        L.or_color_blocks.argtypes = [vp, ctypes.c_uint64, f64, vp, vp]
+        L.or_color_lookup.restype = ctypes.c_uint8
+        L.or_color_lookup.argtypes = [vp, vp, ctypes.c_uint64, ctypes.c_uint64]
+        L.or_scene_set_color_tol.argtypes = [vp, f64]
         L.or_cast_brute.restype = ctypes.c_int
         L.or_cast_brute.argtypes = [vp, i32, i32, vp, ctypes.POINTER(Cam), f64, vp, i64, vp, ctypes.c_int]
         _lib = L
@@ -237,13 +245,34 @@ def ray_dirs(cam: scenegen.Camera) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
+# Colour blocks (Sec. 3.3)
+# ---------------------------------------------------------------------------
+
+def color_blocks(values: np.ndarray, e_c: float):
+    """Block starts (uint64) and colours (uint8) of a uint8 colour array."""
+    v = np.ascontiguousarray(values, np.uint8)
+    start = np.zeros(max(1, len(v)), np.uint64)
+    color = np.zeros(max(1, len(v)), np.uint8)
+    nb = int(lib().or_color_blocks(v.ctypes.data, len(v), float(e_c), start.ctypes.data, color.ctypes.data))
+    return start[:nb].copy(), color[:nb].copy()
+
+
+def color_lookup(start: np.ndarray, color: np.ndarray, idx: int) -> int:
+    s = np.ascontiguousarray(start, np.uint64)
+    c = np.ascontiguousarray(color, np.uint8)
+    return int(lib().or_color_lookup(s.ctypes.data, c.ctypes.data, len(s), int(idx)))
+
+
+# ---------------------------------------------------------------------------
 # Scene + casting
 # ---------------------------------------------------------------------------
 
 class OracleScene:
     """Per-(chunk, LOD) oracle DAGs of a scenegen world, built on demand."""
 
-    def __init__(self, world: scenegen.World, M: int | None = None, L: int | None = None):
+    def __init__(self, world: scenegen.World, M: int | None = None, L: int | None = None,
+                 color_tol: float | None = None):
+        """color_tol: colour-block tolerance e_c of the scene's colour arrays (None: exact)."""
         self.world = world
         self.M = M or world.spec.chunk
         self.L = L or world.spec.n_lods
@@ -251,6 +280,8 @@ class OracleScene:
         self._h = lib().or_scene_create(world.handle, self.M, self.L)
         if not self._h:
             raise ValueError("bad chunking")
+        if color_tol is not None:
+            lib().or_scene_set_color_tol(self._h, float(color_tol))
 
     def __del__(self):
         try:

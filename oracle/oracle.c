@@ -245,6 +245,45 @@ int64_t or_dag_dfs_index(const or_dag* g, int32_t x, int32_t y, int32_t z) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Colour blocks, Sec. 3.3                                                  */
+/* ------------------------------------------------------------------------ */
+uint64_t or_color_blocks(const uint8_t* v, uint64_t n, double e_c, uint64_t* start, uint8_t* color) {
+    if (n == 0) return 0;
+    const double tol = e_c * 255.0;
+    uint64_t nb = 0, sum = 0, cnt = 0;
+    uint8_t cur = 0;
+    for (uint64_t i = 0; i < n; i++) {
+        const double dist = fabs((double)v[i] - (double)cur);
+        if (cnt > 0 && dist <= tol) {
+            /* merge: the block's colour becomes the average of its entries */
+            sum += v[i];
+            cnt++;
+            cur = (uint8_t)((sum + cnt / 2) / cnt);
+        } else {
+            /* close the current block (if any) and open one at i */
+            if (cnt > 0) color[nb - 1] = cur;
+            start[nb++] = i;
+            sum = v[i];
+            cnt = 1;
+            cur = v[i];
+        }
+    }
+    color[nb - 1] = cur;
+    return nb;
+}
+
+uint8_t or_color_lookup(const uint64_t* start, const uint8_t* color, uint64_t n_blocks, uint64_t idx) {
+    /* largest j with start[j] <= idx */
+    uint64_t lo = 0, hi = n_blocks;
+    while (hi - lo > 1) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        if (start[mid] <= idx) lo = mid;
+        else hi = mid;
+    }
+    return color[lo];
+}
+
+/* ------------------------------------------------------------------------ */
 /* LOD selection, Sec. 3.4, Eq. 1                                           */
 /* ------------------------------------------------------------------------ */
 double or_streaming_factor(int32_t H, float tan_half_fovy, double tau, int32_t M) {
@@ -337,6 +376,7 @@ void or_ray_dir(const or_cam* cam, int32_t px, int32_t py, float d[3]) {
 struct or_scene {
     const sg_scene* w;
     int32_t M, L, gx, gy, gz;
+    double color_tol;   /* < 0: exact colour arrays */
     or_dag* dags;       /* [chunk * L + lod] */
     uint8_t* built;
     int32_t* aabb;      /* [chunk * L + lod][6] */
@@ -357,7 +397,22 @@ or_scene* or_scene_create(const sg_scene* world, int32_t M, int32_t L) {
     s->dags = (or_dag*)calloc(n, sizeof(or_dag));
     s->built = (uint8_t*)calloc(n, 1);
     s->aabb = (int32_t*)calloc(n * 6, sizeof(int32_t));
+    s->color_tol = -1.0;
     return s;
+}
+
+void or_scene_set_color_tol(or_scene* s, double e_c) { s->color_tol = e_c; }
+
+/* Replace a DAG's colour array by what the colour-block resolve returns for
+ * every DFS index. */
+static void apply_color_blocks(or_dag* g, double e_c) {
+    if (!g->n_mats) return;
+    uint64_t* start = (uint64_t*)malloc(g->n_mats * sizeof(uint64_t));
+    uint8_t* color = (uint8_t*)malloc(g->n_mats);
+    uint64_t nb = or_color_blocks(g->mats, g->n_mats, e_c, start, color);
+    for (uint64_t i = 0; i < g->n_mats; i++) g->mats[i] = or_color_lookup(start, color, nb, i);
+    free(start);
+    free(color);
 }
 
 void or_scene_destroy(or_scene* s) {
@@ -418,6 +473,7 @@ static void build_one(or_scene* s, int64_t key) {
     uint8_t* mat = (uint8_t*)malloc(nv);
     or_chunk_dense(s->w, M, cx, cy, cz, lod, occ, mat);
     or_dag_build(occ, mat, r, &s->dags[key]);
+    if (s->color_tol >= 0.0) apply_color_blocks(&s->dags[key], s->color_tol);
     int32_t lo[3] = { r, r, r }, hi[3] = { -1, -1, -1 };
     for (int32_t z = 0; z < r; z++)
         for (int32_t y = 0; y < r; y++)

@@ -72,6 +72,19 @@ void or_dag_decode(const or_dag* g, uint8_t* occ, uint8_t* mat);
 /* DFS index of voxel (x,y,z) (chunk-local voxel units at the DAG's LOD); -1 if empty. */
 int64_t or_dag_dfs_index(const or_dag* g, int32_t x, int32_t y, int32_t z);
 
+/* ---- colour blocks (Sec. 3.3, colour compression) ---------------------- */
+/* The DFS colour array v[0..n) cut into blocks of consecutive entries, left
+ * to right: an entry joins the current block when its distance to the
+ * block's colour is within e_c (on the 0..1 scale of v / 255), and the
+ * block's colour becomes the average of its entries (rounded mean of the
+ * uint8 values, (sum + count/2) / count); otherwise it opens a new block.
+ * Writes each block's first index and colour; returns the block count.
+ * e_c = 0 gives the runs of equal values. */
+uint64_t or_color_blocks(const uint8_t* v, uint64_t n, double e_c, uint64_t* start, uint8_t* color);
+/* Colour of entry idx: the block with the largest start <= idx (Sec. 3.5,
+ * colour resolve by binary search over the block array). */
+uint8_t or_color_lookup(const uint64_t* start, const uint8_t* color, uint64_t n_blocks, uint64_t idx);
+
 /* ---- LOD selection (Sec. 3.4, Eq. 1) ------------------------------------ */
 /* StreamingFactor equivalent to a pixel threshold tau: a voxel of LOD n at
  * distance d covers 2^n H / (2 tan(fovy/2) d) pixels, so Eq. 1's cut-off
@@ -105,6 +118,10 @@ void or_ray_dir(const or_cam* cam, int32_t px, int32_t py, float d[3]);
 typedef struct or_scene or_scene;
 or_scene* or_scene_create(const sg_scene* world, int32_t M, int32_t L);
 void or_scene_destroy(or_scene* s);
+/* Colour-block tolerance e_c of the scene's DAGs (< 0: exact colour arrays,
+ * the default).  With e_c >= 0 every DAG built afterwards resolves colours
+ * through or_color_blocks / or_color_lookup of its DFS colour array. */
+void or_scene_set_color_tol(or_scene* s, double e_c);
 /* Build the DAGs for every (chunk, lod_sel[chunk]) not yet built (threads > 0). */
 int or_scene_prepare(or_scene* s, const int8_t* lod_sel, int n_threads);
 /* Access a built DAG (NULL if not built). aabb: lo[3], hi[3] world LOD-0 units, [lo, hi). */
