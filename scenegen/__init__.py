@@ -49,7 +49,7 @@ class _Params(ctypes.Structure):
                 ("wz", ctypes.c_int32), ("octaves", ctypes.c_int32), ("period0", ctypes.c_int32),
                 ("h_min", ctypes.c_int32), ("h_max", ctypes.c_int32), ("crust", ctypes.c_int32),
                 ("n_boxes", ctypes.c_int32), ("box_min", ctypes.c_int32), ("box_max", ctypes.c_int32),
-                ("box_hollow", ctypes.c_int32)]
+                ("box_hollow", ctypes.c_int32), ("mat_mode", ctypes.c_int32)]
 
 
 class _Box(ctypes.Structure):
@@ -107,6 +107,7 @@ class WorldSpec:
     box_max: int
     box_hollow: int
     view_dist: float = 0.0  # 0 = unlimited
+    mat_mode: int = 0       # 0: hashed material per voxel; 1: layered, coherent materials
 
     @property
     def grid(self):
@@ -119,7 +120,8 @@ class World:
     def __init__(self, spec: WorldSpec):
         self.spec = spec
         p = _Params(spec.seed, spec.wx, spec.wy, spec.wz, spec.octaves, spec.period0, spec.h_min,
-                    spec.h_max, spec.crust, spec.n_boxes, spec.box_min, spec.box_max, spec.box_hollow)
+                    spec.h_max, spec.crust, spec.n_boxes, spec.box_min, spec.box_max, spec.box_hollow,
+                    spec.mat_mode)
         self._h = lib().sg_create(ctypes.byref(p))
         if not self._h:
             raise ValueError(f"bad world spec {spec}")
@@ -187,6 +189,9 @@ SINGLE_128 = WorldSpec("single128", seed=1, wx=128, wy=128, wz=128, chunk=128, n
 CITY_4096 = WorldSpec("city4096", seed=2, wx=4096, wy=4096, wz=4096, chunk=512, n_lods=4,
                       octaves=6, period0=1024, h_min=256, h_max=1536, crust=8,
                       n_boxes=4000, box_min=4, box_max=64, box_hollow=1)
+
+# the city world with layered (coherent) materials: the colour-block workload
+CITY_4096_LAYERED = replace(CITY_4096, name="city4096_layered", mat_mode=1)
 
 OPEN_65536 = WorldSpec("open65536", seed=3, wx=65536, wy=65536, wz=1024, chunk=512, n_lods=4,
                        octaves=6, period0=4096, h_min=64, h_max=896, crust=8,

@@ -129,7 +129,8 @@ void sg_get_box(const sg_scene* s, int32_t i, sg_box* out) { *out = s->boxes[i];
 
 sg_scene* sg_create(const sg_params* p) {
     if (!p || p->wx <= 0 || p->wy <= 0 || p->wz <= 0 || p->octaves < 1 || p->octaves > 16 ||
-        p->period0 < 1 || p->h_max < p->h_min || p->n_boxes < 0 || p->crust < 0)
+        p->period0 < 1 || p->h_max < p->h_min || p->n_boxes < 0 || p->crust < 0 || p->mat_mode < 0 ||
+        p->mat_mode > 1)
         return NULL;
     sg_scene* s = (sg_scene*)calloc(1, sizeof(sg_scene));
     s->p = *p;
@@ -230,7 +231,12 @@ int sg_solid(const sg_scene* s, int32_t x, int32_t y, int32_t z) {
 uint8_t sg_material(const sg_scene* s, int32_t x, int32_t y, int32_t z) {
     uint64_t key = ((uint64_t)(uint32_t)x & 0x1FFFFFULL) | (((uint64_t)(uint32_t)y & 0x1FFFFFULL) << 21) |
                    (((uint64_t)(uint32_t)z & 0x1FFFFFULL) << 42);
-    return (uint8_t)(sg_mix64(key ^ s->mat_seed) & 0xFFu);
+    const uint64_t h = sg_mix64(key ^ s->mat_seed);
+    if (s->p.mat_mode == 0) return (uint8_t)(h & 0xFFu);
+    if ((h & 15u) == 0) return (uint8_t)((h >> 8) & 0xFFu);
+    const uint32_t stratum = (uint32_t)z >> 3;
+    const uint32_t cell = (((uint32_t)x >> 6) * 7u + ((uint32_t)y >> 6) * 13u) & 31u;
+    return (uint8_t)((stratum * 5u + cell * 3u + (uint32_t)(s->mat_seed & 63u)) & 0xFFu);
 }
 
 void sg_materials(const sg_scene* s, const int32_t* xyz, size_t n, uint8_t* out) {

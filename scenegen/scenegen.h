@@ -24,7 +24,11 @@
  *           lo = max(0, min(h(x,y), h(x+-1,y), h(x,y+-1)) - crust); every
  *           exposed side face of a column is therefore backed by solid voxels.
  *   boxes   axis-aligned boxes, either solid or hollow (1-voxel shell).
- *   solid   = terrain OR any box; material(x,y,z) = hash(x,y,z,seed) & 0xFF.
+ *   solid   = terrain OR any box; material(x,y,z) = hash(x,y,z,seed) & 0xFF
+ *   (mat_mode 0), or (mat_mode 1) spatially coherent: a stratum of 8 voxels
+ *   in z combined with a 64x64 column cell, plus a hashed value on 1 voxel
+ *   in 16 -- long runs of equal values in depth-first order, as colours of
+ *   real scenes have.
  */
 #ifndef SCENEGEN_H
 #define SCENEGEN_H
@@ -51,6 +55,7 @@ typedef struct sg_params {
     int32_t n_boxes;           /* number of seeded boxes */
     int32_t box_min, box_max;  /* box side range (inclusive) */
     int32_t box_hollow;        /* 1: hollow city boxes on the terrain; 0: solid floating boxes */
+    int32_t mat_mode;          /* 0: material = hash per voxel; 1: layered (coherent) materials */
 } sg_params;
 
 typedef struct sg_scene sg_scene;

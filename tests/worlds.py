@@ -18,3 +18,6 @@ MULTI32 = replace(sg.CITY_4096, name="multi32", seed=13, wx=96, wy=96, wz=64, ch
 # 4x4x2 chunks of 64^3 (256x256x128), 4 LODs: several tiles per ray, ragged image sizes
 MED64 = replace(sg.CITY_4096, name="med64", seed=14, wx=256, wy=256, wz=128, chunk=64, n_lods=4,
                 period0=128, h_min=20, h_max=90, crust=6, n_boxes=60, box_min=4, box_max=24)
+
+# MED64 with layered (coherent) materials: the colour-block workload
+MED64_LAYERED = replace(MED64, name="med64_layered", mat_mode=1)
