@@ -327,6 +327,34 @@ def bench_tiles(aok, ctx, scene, world, flush, reps=20):
     return out
 
 
+def bench_color(aok, ctx, threads, flush, reps=20):
+    """Colour-block compression (Sec. 3.3) on the city world with layered
+    (coherent) colours: colour bytes resident and the benchmark frame's time
+    with raw arrays, lossless blocks (e_c = 0) and the paper's e_c = 0.05."""
+    import torch
+    world = sg.World(sg.CITY_4096_LAYERED)
+    bw = aok.BuiltWorld(world, threads)
+    cam = sg.ground_camera(world, CAM_SEED, W, H)
+    stream = torch.cuda.current_stream()
+    out = {"workload": "city4096 with layered colours (8-voxel strata x 64-voxel column cells, 1/64 hashed), "
+                       "1920x1080, camera seed 102, tau = 1 px"}
+    frames = {}
+    for name, tol in (("raw", None), ("lossless_e0", 0.0), ("lossy_e0.05", 0.05)):
+        sc = aok.Scene.from_world(ctx, world, built=bw, color_tol=tol)
+        hit, t = aok.alloc_frame(W, H)
+        for _ in range(3):
+            aok.render(ctx, sc, cam, TAU, hit, t)
+        med, best = time_events(lambda: aok.render(ctx, sc, cam, TAU, hit, t), reps, flush, stream)
+        out[name] = {"color_bytes": sc.usage()["color_bytes"], "frame_ms_median": med, "frame_ms_best": best}
+        frames[name] = (hit, t)
+        sc.destroy()
+    r, l0, l5 = frames["raw"], frames["lossless_e0"], frames["lossy_e0.05"]
+    out["lossless_identical"] = bool(torch.equal(r[0], l0[0]) and torch.equal(r[1], l0[1]))
+    meta_r, meta_5 = r[0].view(-1, 4)[:, 3], l5[0].view(-1, 4)[:, 3]
+    out["lossy_pixels_with_other_colour"] = float(((meta_r >> 8) & 0xFF).ne((meta_5 >> 8) & 0xFF).float().mean())
+    return out
+
+
 def bench_open(aok, ctx, threads, n_poses=300):
     """Open world 65536x65536x1024 (128x128x2 chunks of 512^3, 4 LODs), view
     distance 16384: along a 300-pose path at 2560x1440, only the (chunk, LOD)
@@ -507,6 +535,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-open", action="store_true")
     ap.add_argument("--no-tiles", action="store_true")
+    ap.add_argument("--no-color", action="store_true")
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--cpu-scaling", action="store_true",
                     help="print the oracle's 1-thread / all-thread rays/s for three workloads and exit")
@@ -636,6 +665,8 @@ def main():
     }
     if not args.no_tiles:
         out["tile_pipeline"] = bench_tiles(aok, ctx, scene, world, flush)
+    if not args.no_color:
+        out["color_blocks"] = bench_color(aok, ctx, threads, flush)
     if not args.no_batch:
         out["batched"] = bench_batched(aok, ctx, scene, world, flush)
     if not args.no_serve:

@@ -133,6 +133,24 @@ int aok_validate_chunk(const aok_chunk_blob* blob, int32_t chunk_res, uint32_t l
 /* Make a (chunk, lod) non-resident (it renders as empty).  Pool space of the
  * evicted chunk is reused by later uploads of at most the same size. */
 int aok_scene_evict_chunk(aok_ctx* ctx, uint32_t scene, int32_t cx, int32_t cy, int32_t cz, uint32_t lod);
+/* Colour-block compression of the scene's colour (material) arrays (Sec. 3.3):
+ * chunks uploaded after this call store their DFS colour array as blocks of
+ * consecutive entries -- an entry within e_c (on the 0..1 scale of value/255)
+ * of the current block's colour joins it and the block's colour becomes the
+ * rounded mean (sum + count/2) / count of its entries; any other entry opens a
+ * new block -- and the casting kernels resolve a hit's colour by binary search
+ * for the last block whose first index is <= the DFS index (Sec. 3.5).
+ * e_c = 0 is lossless (runs of equal values); e_c > 0 is lossy; e_c < 0
+ * (the default) stores raw arrays.  Blocks take 5 bytes each plus a 4-byte
+ * search hint per 128 entries; a chunk whose blocks would not be smaller than
+ * its array stores one byte per entry instead,
+ * holding the colour its block gives (the same rendered colours).
+ * AOK_E_INVALID for e_c > 1 or NaN. */
+int aok_scene_set_color_blocks(aok_ctx* ctx, uint32_t scene, double e_c);
+/* Device pool usage of the scene's resident (chunk, LOD)s: usage[0] node
+ * bytes, [1] leaf bytes, [2] colour bytes (blocks or raw arrays), [3] resident
+ * (chunk, LOD) count. */
+int aok_scene_usage(aok_ctx* ctx, uint32_t scene, uint64_t* usage);
 
 /* ------------------------------------------------------------------ */
 /* Cameras and frames                                                 */

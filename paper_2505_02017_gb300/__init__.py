@@ -80,6 +80,8 @@ def lib() -> ctypes.CDLL:
             "aok_scene_destroy": [vp, u32],
             "aok_scene_upload_chunk": [vp, u32, i32, i32, i32, u32, P(ChunkBlob)],
             "aok_scene_evict_chunk": [vp, u32, i32, i32, i32, u32],
+            "aok_scene_set_color_blocks": [vp, u32, dbl],
+            "aok_scene_usage": [vp, u32, P(u64)],
             "aok_select_chunks": [vp, u32, P(Camera), dbl, vp, vp, P(u32), vp],
             "aok_render": [vp, u32, P(Camera), dbl, P(Frame), vp],
             "aok_render_counted": [vp, u32, P(Camera), dbl, P(Frame), vp, vp],
@@ -268,9 +270,12 @@ class Scene:
         self.id = sid.value
 
     @classmethod
-    def from_world(cls, ctx: Context, world, threads: int | None = None, built: BuiltWorld | None = None):
+    def from_world(cls, ctx: Context, world, threads: int | None = None, built: BuiltWorld | None = None,
+                   color_tol: float | None = None):
         bw = built or BuiltWorld(world, threads)
         sc = cls(ctx, world.spec, bw.node_words, bw.leaves, bw.mat_bytes)
+        if color_tol is not None:
+            sc.set_color_blocks(color_tol)
         sc.upload_built(bw)
         return sc
 
@@ -287,6 +292,16 @@ class Scene:
 
     def evict(self, cx, cy, cz, lod):
         return check(lib().aok_scene_evict_chunk(self.ctx.h, self.id, cx, cy, cz, lod), "aok_scene_evict_chunk")
+
+    def set_color_blocks(self, e_c: float):
+        """Colour-block tolerance of later uploads (aok_scene_set_color_blocks; < 0: raw arrays)."""
+        return check(lib().aok_scene_set_color_blocks(self.ctx.h, self.id, float(e_c)), "aok_scene_set_color_blocks")
+
+    def usage(self) -> dict:
+        """Resident bytes per device pool (aok_scene_usage)."""
+        a = (ctypes.c_uint64 * 4)()
+        check(lib().aok_scene_usage(self.ctx.h, self.id, a), "aok_scene_usage")
+        return {"node_bytes": int(a[0]), "leaf_bytes": int(a[1]), "color_bytes": int(a[2]), "resident": int(a[3])}
 
     def destroy(self):
         if self.id:

@@ -20,7 +20,9 @@ struct ChunkRef {
     uint32_t lod;        // LOD of this DAG
     uint64_t mat_base;   // offset of its materials in the scene's material pool
     uint16_t aabb[6];    // chunk-local LOD-0 units: lo x,y,z, hi x,y,z ([lo, hi))
-    uint32_t pad;
+    uint32_t nblocks;    // 0: materials[DFS index] at mat_base; else colour blocks at mat_base:
+                         // nt, nt uint32 block-of-entry-128j, nblocks uint32 first indices,
+                         // nblocks uint8 colours (Sec. 3.3)
 };
 static_assert(sizeof(ChunkRef) == 32, "ChunkRef is one 32-byte sector");
 

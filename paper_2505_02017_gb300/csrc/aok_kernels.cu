@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(256) cast_persistent(const __grid_constant__ B
 // tiles (2^tile_w_log x 32/2^tile_w_log pixels each); P.v[v].tile_begin is the
 // exclusive prefix sum of the views' block-tile counts.  The view index derives
 // from blockIdx only, so every per-view parameter load is block-uniform.
-__global__ void __launch_bounds__(128) cast_grid(const __grid_constant__ BatchParams P) {
+__global__ void __launch_bounds__(128, 7) cast_grid(const __grid_constant__ BatchParams P) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t blk = blockIdx.x;
     uint32_t lo = 0, hi = P.n_views - 1;  // last view with tile_begin <= blk

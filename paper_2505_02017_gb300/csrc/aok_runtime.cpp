@@ -443,6 +443,30 @@ static void free_alloc(Scene* sc, ChunkAlloc& a) {
     a = ChunkAlloc();
 }
 
+// Colour blocks of a DFS colour array (Sec. 3.3): entries are taken left to
+// right; one within tol = e_c * 255 of the current block's colour joins it and
+// the colour becomes the rounded mean of the block's entries, any other opens
+// a new block.
+static void color_blocks(const uint8_t* v, uint64_t n, double e_c, std::vector<uint32_t>& first,
+                         std::vector<uint8_t>& colour) {
+    first.clear();
+    colour.clear();
+    const double tol = e_c * 255.0;
+    uint64_t sum = 0, cnt = 0;
+    for (uint64_t i = 0; i < n; i++) {
+        if (cnt && std::fabs((double)v[i] - (double)colour.back()) <= tol) {
+            sum += v[i];
+            cnt++;
+            colour.back() = (uint8_t)((sum + cnt / 2) / cnt);
+        } else {
+            first.push_back((uint32_t)i);
+            colour.push_back(v[i]);
+            sum = v[i];
+            cnt = 1;
+        }
+    }
+}
+
 int aok_scene_upload_chunk(aok_ctx* ctx, uint32_t scene, int32_t cx, int32_t cy, int32_t cz, uint32_t lod,
                            const aok_chunk_blob* blob) {
     if (!ctx || !blob) return AOK_E_INVALID;
@@ -460,9 +484,31 @@ int aok_scene_upload_chunk(aok_ctx* ctx, uint32_t scene, int32_t cx, int32_t cy,
     if (st) return st;
     uint32_t droot = 0;
     const uint64_t nw = layout_blob(blob, res, 0, 0, nullptr, &droot);  // device words (even)
+    // material storage: colour blocks when the scene asks for them and they are
+    // smaller than the raw array (3 bytes of slack align the uint32 indices)
+    std::vector<uint32_t> bfirst;
+    std::vector<uint8_t> bcol, decoded;
+    uint64_t mat_n = blob->n_mats;
+    const uint8_t* raw_mats = blob->mats;
+    if (sc->color_tol >= 0.0 && blob->n_mats) {
+        color_blocks(blob->mats, blob->n_mats, sc->color_tol, bfirst, bcol);
+        const uint64_t cb = 4ull * (1 + (blob->n_mats + 127) / 128) + 5ull * bfirst.size() + 3;
+        if (cb < blob->n_mats) {
+            mat_n = cb;
+        } else {
+            // not smaller: one byte per entry, holding the colour its block gives
+            decoded.resize(blob->n_mats);
+            for (size_t b = 0; b < bfirst.size(); b++) {
+                const uint64_t end = b + 1 < bfirst.size() ? bfirst[b + 1] : blob->n_mats;
+                std::memset(decoded.data() + bfirst[b], bcol[b], end - bfirst[b]);
+            }
+            raw_mats = decoded.data();
+            bfirst.clear();
+        }
+    }
     // staging: laid-out node words + leaves + mats, 16-byte aligned segments
     const size_t nb = (nw * 4 + 15) & ~(size_t)15, lb = (blob->n_leaves * 8 + 15) & ~(size_t)15;
-    const size_t need = nb + lb + blob->n_mats + 16;
+    const size_t need = nb + lb + mat_n + 16;
     if (need > ctx->staging_cap) {
         if (ctx->staging) cudaFreeHost(ctx->staging);
         ctx->staging = nullptr;
@@ -495,15 +541,15 @@ int aok_scene_upload_chunk(aok_ctx* ctx, uint32_t scene, int32_t cx, int32_t cy,
         if (!nw) return true;
         a.node_off = sc->nodes.alloc(nw);
         a.leaf_off = sc->leaves.alloc(blob->n_leaves);
-        a.mat_off = sc->mats.alloc(blob->n_mats);
+        a.mat_off = sc->mats.alloc(mat_n);
         a.node_n = nw;
         a.leaf_n = blob->n_leaves;
-        a.mat_n = blob->n_mats;
+        a.mat_n = mat_n;
         if (a.node_off == kNoRange || a.leaf_off == kNoRange || a.mat_off == kNoRange ||
             a.node_off + nw > 0xFFFFFFFFull || a.leaf_off + blob->n_leaves > 0xFFFFFFFFull) {
             if (a.node_off != kNoRange) sc->nodes.release(a.node_off, nw);
             if (a.leaf_off != kNoRange) sc->leaves.release(a.leaf_off, blob->n_leaves);
-            if (a.mat_off != kNoRange) sc->mats.release(a.mat_off, blob->n_mats);
+            if (a.mat_off != kNoRange) sc->mats.release(a.mat_off, mat_n);
             a = ChunkAlloc();
             return false;
         }
@@ -520,15 +566,35 @@ int aok_scene_upload_chunk(aok_ctx* ctx, uint32_t scene, int32_t cx, int32_t cy,
     std::memset(&ref, 0, sizeof(ref));
     ref.root = kNone;
     ref.lod = lod;
+    uint64_t mat_base = a.mat_off;
     if (nw) {
         std::memcpy(stg + nb, blob->leaves, blob->n_leaves * 8);
-        std::memcpy(stg + nb + lb, blob->mats, blob->n_mats);
+        if (bfirst.empty()) {
+            std::memcpy(stg + nb + lb, raw_mats, blob->n_mats);
+        } else {
+            // [pad to 4][nt][nt x uint32: block holding entry 128 j]
+            // [nblocks x uint32 first index][nblocks x uint8 colour]
+            mat_base = (a.mat_off + 3) & ~(uint64_t)3;
+            const size_t nt = (blob->n_mats + 127) / 128;
+            std::vector<uint32_t> head(1 + nt);
+            head[0] = (uint32_t)nt;
+            for (size_t j = 0, b = 0; j < nt; j++) {
+                while (b + 1 < bfirst.size() && bfirst[b + 1] <= 128 * j) b++;
+                head[1 + j] = (uint32_t)b;
+            }
+            uint8_t* seg = stg + nb + lb;
+            std::memset(seg, 0, mat_n);
+            uint8_t* q = seg + (mat_base - a.mat_off);
+            std::memcpy(q, head.data(), head.size() * 4);
+            std::memcpy(q + head.size() * 4, bfirst.data(), bfirst.size() * 4);
+            std::memcpy(q + head.size() * 4 + bfirst.size() * 4, bcol.data(), bcol.size());
+        }
         cudaError_t e = cudaMemcpyAsync(sc->d_nodes + a.node_off, stg, nw * 4, cudaMemcpyHostToDevice, ctx->copy_stream);
         if (e == cudaSuccess && blob->n_leaves)
             e = cudaMemcpyAsync(sc->d_leaves + a.leaf_off, stg + nb, blob->n_leaves * 8, cudaMemcpyHostToDevice,
                                 ctx->copy_stream);
-        if (e == cudaSuccess && blob->n_mats)
-            e = cudaMemcpyAsync(sc->d_mats + a.mat_off, stg + nb + lb, blob->n_mats, cudaMemcpyHostToDevice,
+        if (e == cudaSuccess && mat_n)
+            e = cudaMemcpyAsync(sc->d_mats + a.mat_off, stg + nb + lb, mat_n, cudaMemcpyHostToDevice,
                                 ctx->copy_stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->copy_stream);
         if (e != cudaSuccess) {
@@ -536,7 +602,8 @@ int aok_scene_upload_chunk(aok_ctx* ctx, uint32_t scene, int32_t cx, int32_t cy,
             return cuda_status(ctx, e);
         }
         ref.root = droot;
-        ref.mat_base = a.mat_off;
+        ref.mat_base = mat_base;
+        ref.nblocks = (uint32_t)bfirst.size();
         for (int i = 0; i < 3; i++) {
             ref.aabb[i] = (uint16_t)blob->aabb_lo[i];
             ref.aabb[3 + i] = (uint16_t)blob->aabb_hi[i];
@@ -550,6 +617,33 @@ int aok_scene_upload_chunk(aok_ctx* ctx, uint32_t scene, int32_t cx, int32_t cy,
     sc->h_desc[di] = ref;
     cudaError_t e = cudaMemcpy(sc->d_desc + di, &ref, sizeof(ref), cudaMemcpyHostToDevice);
     return cuda_status(ctx, e);
+}
+
+int aok_scene_set_color_blocks(aok_ctx* ctx, uint32_t scene, double e_c) {
+    if (!ctx || !(e_c == e_c) || e_c > 1.0) return AOK_E_INVALID;
+    Scene* sc = find_scene(ctx, scene);
+    if (!sc) return AOK_E_NOT_RESIDENT;
+    std::lock_guard<std::mutex> g(sc->mu);
+    sc->color_tol = e_c < 0.0 ? -1.0 : e_c;
+    return AOK_OK;
+}
+
+int aok_scene_usage(aok_ctx* ctx, uint32_t scene, uint64_t* usage) {
+    if (!ctx || !usage) return AOK_E_INVALID;
+    Scene* sc = find_scene(ctx, scene);
+    if (!sc) return AOK_E_NOT_RESIDENT;
+    std::lock_guard<std::mutex> g(sc->mu);
+    uint64_t u[4] = {0, 0, 0, 0};
+    for (const ChunkAlloc& a : sc->alloc) {
+        u[0] += a.node_n;
+        u[1] += a.leaf_n;
+        u[2] += a.mat_n;
+        u[3] += (a.node_n || a.leaf_n || a.mat_n) ? 1 : 0;
+    }
+    u[0] *= 4;
+    u[1] *= 8;
+    std::memcpy(usage, u, sizeof(u));
+    return AOK_OK;
 }
 
 int aok_validate_chunk(const aok_chunk_blob* blob, int32_t M, uint32_t lod) {

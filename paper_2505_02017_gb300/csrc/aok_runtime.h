@@ -32,6 +32,7 @@ struct ChunkAlloc {
 
 struct Scene {
     aok_scene_desc desc{};
+    double color_tol = -1.0;  // colour-block tolerance of later uploads (< 0: raw arrays)
     int mlog = 0;
     int64_t n_chunks = 0;
     uint32_t* d_nodes = nullptr;

@@ -86,6 +86,27 @@ __device__ __forceinline__ bool tltf(int32_t N1, int32_t m1, int32_t N2, int32_t
 // 4x4x4 leaf block, n+1 a 2x2x2 group in it, n a voxel of LOD n.  Leaf bits
 // are addressed in stored (unmirrored) order: along a mirrored axis the index
 // inside a block is c ^ 3 (group: c ^ 1).
+// Colour of DFS index idx in a colour-block array (Sec. 3.3) at base:
+// [nt][nt x uint32: block holding entry 128 j][nblocks x uint32 first index]
+// [nblocks x uint8 colour].  The block is the last one whose first index is
+// <= idx (Sec. 3.5: a binary search), searched between the blocks holding
+// entries 128 (idx / 128) and 128 (idx / 128 + 1), so that a hit costs a few
+// dependent loads instead of log2(nblocks).
+static __device__ __forceinline__ uint32_t block_colour(const uint8_t* __restrict__ base, uint32_t nblocks,
+                                                        uint32_t idx) {
+    const uint32_t* __restrict__ w = reinterpret_cast<const uint32_t*>(base);
+    const uint32_t nt = w[0], j = idx >> 7;
+    uint32_t lo = w[1 + j];
+    uint32_t hi = j + 1 < nt ? w[2 + j] : nblocks - 1;
+    const uint32_t* __restrict__ first = w + 1 + nt;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (first[mid] <= idx) lo = mid;
+        else hi = mid - 1;
+    }
+    return base[4ull * (1 + nt + nblocks) + lo];
+}
+
 struct RayState {
     float d[3];
     int32_t m[3], E[3];
@@ -145,7 +166,8 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
                 }
                 const int bit = (u0 & 3) + 4 * (u1 & 3) + 16 * (u2 & 3);
                 idx += (uint32_t)__popcll(lmu & ((1ull << bit) - 1ull));
-                hit.mat = S.mats[ref.mat_base + idx];
+                hit.mat = ref.nblocks == 0 ? S.mats[ref.mat_base + idx]
+                                           : block_colour(S.mats + ref.mat_base, ref.nblocks, idx);
                 if (COUNT) cnt.rbytes += 1;
                 return true;
             }

@@ -233,7 +233,7 @@ uint8_t sg_material(const sg_scene* s, int32_t x, int32_t y, int32_t z) {
                    (((uint64_t)(uint32_t)z & 0x1FFFFFULL) << 42);
     const uint64_t h = sg_mix64(key ^ s->mat_seed);
     if (s->p.mat_mode == 0) return (uint8_t)(h & 0xFFu);
-    if ((h & 15u) == 0) return (uint8_t)((h >> 8) & 0xFFu);
+    if ((h & 63u) == 0) return (uint8_t)((h >> 8) & 0xFFu);
     const uint32_t stratum = (uint32_t)z >> 3;
     const uint32_t cell = (((uint32_t)x >> 6) * 7u + ((uint32_t)y >> 6) * 13u) & 31u;
     return (uint8_t)((stratum * 5u + cell * 3u + (uint32_t)(s->mat_seed & 63u)) & 0xFFu);

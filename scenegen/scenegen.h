@@ -27,7 +27,7 @@
  *   solid   = terrain OR any box; material(x,y,z) = hash(x,y,z,seed) & 0xFF
  *   (mat_mode 0), or (mat_mode 1) spatially coherent: a stratum of 8 voxels
  *   in z combined with a 64x64 column cell, plus a hashed value on 1 voxel
- *   in 16 -- long runs of equal values in depth-first order, as colours of
+ *   in 64 -- long runs of equal values in depth-first order, as colours of
  *   real scenes have.
  */
 #ifndef SCENEGEN_H
