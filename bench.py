@@ -487,6 +487,59 @@ def cpu_scaling(threads):
     print(json.dumps({"oracle_rays_per_s": res, "host_threads": threads}), flush=True)
 
 
+def bench_open_async(aok, ctx, threads, n_poses=300, fps=60.0):
+    """The open-world path with asynchronous residency (aok_stream): frames
+    are paced at `fps`; each frame installs what the background workers
+    loaded since the previous one (coarser LODs first, then nearest), renders
+    with stand-in LODs where a load is still missing, and never waits for a
+    build.  The first pose is loaded completely before the path starts."""
+    import torch
+    from paper_2505_02017_gb300.stream import AsyncStreamer
+    spec = sg.OPEN_65536
+    world = sg.World(spec)
+    cams = sg.path_cameras(world, 103, n_poses, 2560, 1440)
+    scene = aok.Scene(ctx, spec, node_words=512 << 20, leaves=256 << 20, mat_bytes=16 << 30)
+    st = AsyncStreamer(ctx, world, scene, threads)
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    st.update(cams[0], TAU, stream=stream)
+    st.wait()
+    st.update(cams[0], TAU, stream=stream)
+    warm_s = time.perf_counter() - t0
+    hit, t = aok.alloc_frame(2560, 1440)
+    render_ms, update_ms, missing = [], [], []
+    period = 1.0 / fps
+    for cam in cams:
+        f0 = time.perf_counter()
+        st.update(cam, TAU, stream=stream)
+        update_ms.append(1e3 * (time.perf_counter() - f0))
+        missing.append(st.stats()["missing"])
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        aok.render(ctx, scene, cam, TAU, hit, t, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        render_ms.append(e0.elapsed_time(e1))
+        rest = period - (time.perf_counter() - f0)
+        if rest > 0:
+            time.sleep(rest)
+    s = st.stats()
+    st.close()
+    scene.destroy()
+    rs, us = sorted(render_ms), sorted(update_ms)
+    return {"workload": f"open65536 path (seed 103), {n_poses} poses at 2560x1440 paced at {fps:g} frames/s, "
+                        f"tau = 1 px; {threads} loader threads",
+            "first_pose_load_s": round(warm_s, 2),
+            "render_ms_median": rs[len(rs) // 2], "render_ms_p99": rs[int(len(rs) * 0.99) - 1],
+            "update_ms_median": us[len(us) // 2], "update_ms_p99": us[int(len(us) * 0.99) - 1],
+            "frames_with_every_planned_lod": sum(m == 0 for m in missing) / len(missing),
+            "max_regions_missing": max(missing), "max_resident_chunks": s["max_resident"],
+            "max_resident_mb": round(s["max_resident_bytes"] / 1e6, 1), "installed_total": s["installed_total"],
+            "evicted_total": s["evicted_total"], "cancelled_total": s["cancelled_total"],
+            "failed_total": s["failed_total"], "deferred_total": s["deferred_total"]}
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle as it stands, same workload/metric, bounded sample per step."""
     rank, world_size, _ = dist_env()
@@ -673,6 +726,7 @@ def main():
         out["served"] = bench_served(aok, ctx, scene, threads)
     if not args.no_open:
         out["open_world"] = bench_open(aok, ctx, threads)
+        out["open_world_async"] = bench_open_async(aok, ctx, threads)
     if rank == 0 and world_size == 1 and not args.no_cpu_baseline:
         try:
             out["cpu_baseline"] = cpu_oracle_sample(world, cam)

@@ -194,11 +194,15 @@ typedef struct aok_frame {
  * level n from n_lods-1 down to 0 whose LODError <= 0, else 0.  The pixel
  * threshold tau maps to StreamingFactor = (H / (2 tan_half_fovy)) / (tau M),
  * i.e. an LOD-n voxel at the cut-off distance covers tau pixels.  Evaluated
- * in IEEE FP64 with a fixed operation order.  Then culls chunks whose
- * selected DAG is empty or not resident, whose AABB lies outside the view
- * pyramid, or (view_dist > 0) beyond the view distance.
+ * in IEEE FP64 with a fixed operation order.  When the selected (chunk, LOD)
+ * has not been uploaded (it may still be streaming in) but another LOD of
+ * the region has, that LOD stands in: the nearest coarser one, else the
+ * nearest finer one.  Then culls chunks whose DAG is empty or not resident,
+ * whose AABB lies outside the view pyramid, or (view_dist > 0) beyond the
+ * view distance.
  *  lod_per_chunk_dev : optional device int8[grid x*y*z] (x fastest) receiving
- *                      every chunk region's Eq. 1 LOD.
+ *                      every chunk region's LOD: Eq. 1's, or the stand-in
+ *                      actually used.
  *  visible_dev       : optional device uint8[grid x*y*z]: 1 if the chunk is
  *                      kept for casting, 0 if empty, not resident or culled.
  *  n_visible_out     : optional host pointer; if given the call synchronises
@@ -207,6 +211,63 @@ typedef struct aok_frame {
  * next aok_render of this scene on the same stream. */
 int aok_select_chunks(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double lod_threshold_px,
                       int8_t* lod_per_chunk_dev, uint8_t* visible_dev, uint32_t* n_visible_out, void* stream);
+
+/* ------------------------------------------------------------------ */
+/* Asynchronous streaming (Sec. 3.4)                                  */
+/* ------------------------------------------------------------------ */
+
+/* Produces the blob of one (chunk, LOD) on the calling (worker) thread:
+ * returns 0 and fills *out (pointers valid until release(user, *handle)),
+ * non-zero on failure. */
+typedef int (*aok_chunk_source_fn)(void* user, int32_t cx, int32_t cy, int32_t cz, uint32_t lod,
+                                   aok_chunk_blob* out, void** handle);
+typedef void (*aok_chunk_release_fn)(void* user, void* handle);
+
+typedef struct aok_stream aok_stream;
+
+/* Background loader that keeps the (chunk, LOD)s a camera needs resident in
+ * a scene's device pools (Sec. 3.4).  n_threads worker threads take load
+ * requests in the paper's order -- coarser LODs first, then the regions
+ * nearest the camera -- build each blob with `source`, validate it and copy
+ * it into free pool space (copy stream), while frames keep rendering.  A
+ * loaded (chunk, LOD) becomes visible to rendering only at the next
+ * aok_stream_update, which installs every change with one small kernel on
+ * the rendering stream, so a frame sees a consistent descriptor table.  Pool
+ * space of an evicted (chunk, LOD) is reused only after the rendering work
+ * enqueued before its eviction has finished.  While a region's selected LOD
+ * is not resident yet, frames render the nearest resident LOD of the region
+ * (coarser first; see aok_select_chunks' lod output).  The scene's pools
+ * (aok_scene_desc capacities) are the HBM budget: a load that does not fit
+ * waits for evictions and is retried.  The streamer owns the residency of
+ * its scene: do not upload or evict its chunks by other calls meanwhile, and
+ * destroy it before the scene. */
+int aok_stream_create(aok_ctx* ctx, uint32_t scene, aok_chunk_source_fn source, aok_chunk_release_fn release,
+                      void* user, int32_t n_threads, aok_stream** out);
+/* Between frames, on the rendering thread: plan the camera's residency (as
+ * aok_plan_residency), install the loads finished since the last update and
+ * the evictions of LODs no longer needed (a region keeps its old LOD until
+ * the new one is installed) on `stream`, cancel queued requests the new plan
+ * no longer wants, queue the missing ones, free quarantined pool space whose
+ * frames are done.  Does not wait for loads.  Frames must render on `stream`
+ * (or streams ordered after it). */
+int aok_stream_update(aok_stream* s, const aok_camera* cam, double lod_threshold_px, void* stream);
+/* Block until no load is queued or running (AOK_E_TIMEOUT after timeout_ms;
+ * < 0 waits without limit).  The finished loads are installed by the next
+ * aok_stream_update. */
+int aok_stream_wait(aok_stream* s, int32_t timeout_ms);
+/* stats[0] installed (chunk, LOD)s, [1] their device bytes, [2] / [3] the
+ * maxima of both so far, [4] queued requests, [5] loads running, [6] loads
+ * finished but not installed, [7] installed in total, [8] evicted in total,
+ * [9] requests cancelled, [10] loads that failed (source or validation),
+ * [11] loads deferred for lack of pool space, [12] planned regions whose
+ * planned LOD was not installed at the last update (0: the frame after it
+ * renders exactly the Eq. 1 selection). */
+int aok_stream_stats(aok_stream* s, uint64_t* stats);
+/* Per chunk region (x fastest) the bitmask of installed LODs (bit l = LOD l). */
+int aok_stream_resident(aok_stream* s, uint8_t* lod_masks);
+/* Stop the workers (running loads finish), free loads not installed and
+ * quarantined pool space (waits for their frames).  Installed chunks stay. */
+int aok_stream_destroy(aok_stream* s);
 
 /* Residency plan for one camera, on the host (the streaming side of
  * Sec. 3.4): for every chunk region, the LOD that Eq. 1 selects -- the same

@@ -81,6 +81,12 @@ def lib() -> ctypes.CDLL:
             "aok_scene_upload_chunk": [vp, u32, i32, i32, i32, u32, P(ChunkBlob)],
             "aok_scene_evict_chunk": [vp, u32, i32, i32, i32, u32],
             "aok_scene_set_color_blocks": [vp, u32, dbl],
+            "aok_stream_create": [vp, u32, vp, vp, vp, i32, P(vp)],
+            "aok_stream_update": [vp, P(Camera), dbl, vp],
+            "aok_stream_wait": [vp, i32],
+            "aok_stream_stats": [vp, P(u64)],
+            "aok_stream_resident": [vp, vp],
+            "aok_stream_destroy": [vp],
             "aok_scene_usage": [vp, u32, P(u64)],
             "aok_select_chunks": [vp, u32, P(Camera), dbl, vp, vp, P(u32), vp],
             "aok_render": [vp, u32, P(Camera), dbl, P(Frame), vp],
@@ -140,6 +146,9 @@ def blib() -> ctypes.CDLL:
         L.aokb_get.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
                                ctypes.POINTER(ChunkBlob)]
         L.aokb_totals.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64 * 4)]
+        L.aokb_source_create.restype = vp
+        L.aokb_source_create.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
+        L.aokb_source_destroy.argtypes = [vp]
         _blib = L
     return _blib
 

@@ -444,6 +444,50 @@ int aokb_get(const aokb_world* b, int64_t i, int32_t lod, int64_t* chunk, aok_ch
     return 0;
 }
 
+// Chunk source for aok_stream (the callback types of include/aok.h): builds
+// one (chunk, LOD) of a world on the calling thread.  The blob points into a
+// builder-owned allocation returned through *handle and freed by
+// aokb_source_release.
+typedef struct aokb_source {
+    const sg_scene* w;
+    int M, L;
+    int64_t gx, gy, gz;
+} aokb_source;
+
+aokb_source* aokb_source_create(const sg_scene* w, int32_t M, int32_t L) {
+    const sg_params* p = sg_get_params(w);
+    if (M < 8 || (M & (M - 1)) || L < 1 || (M >> (L - 1)) < 8 || p->wx % M || p->wy % M || p->wz % M) return nullptr;
+    return new aokb_source{w, M, L, p->wx / M, p->wy / M, p->wz / M};
+}
+
+void aokb_source_destroy(aokb_source* s) { delete s; }
+
+int aokb_source_build(void* user, int32_t cx, int32_t cy, int32_t cz, uint32_t lod, aok_chunk_blob* out,
+                      void** handle) {
+    const aokb_source* s = (const aokb_source*)user;
+    if (!s || !out || !handle || cx < 0 || cy < 0 || cz < 0 || cx >= s->gx || cy >= s->gy || cz >= s->gz ||
+        (int)lod >= s->L)
+        return -1;
+    std::vector<Blob>* blobs = new std::vector<Blob>(s->L);
+    build_chunk(s->w, s->M, s->L, cx, cy, cz, blobs->data(), 1u << lod);
+    const Blob& b = (*blobs)[lod];
+    out->nodes = b.nodes.data();
+    out->n_node_words = b.nodes.size();
+    out->leaves = b.leaves.data();
+    out->n_leaves = b.leaves.size();
+    out->mats = b.mats.data();
+    out->n_mats = b.mats.size();
+    out->root = b.root;
+    for (int a = 0; a < 3; a++) { out->aabb_lo[a] = b.lo[a]; out->aabb_hi[a] = b.hi[a]; }
+    *handle = blobs;
+    return 0;
+}
+
+void aokb_source_release(void* user, void* handle) {
+    (void)user;
+    delete (std::vector<Blob>*)handle;
+}
+
 // Totals over all entries: [0] node words, [1] leaves, [2] material bytes, [3] non-empty blobs.
 void aokb_totals(const aokb_world* b, uint64_t out[4]) {
     out[0] = out[1] = out[2] = out[3] = 0;

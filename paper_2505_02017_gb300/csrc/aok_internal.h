@@ -10,6 +10,10 @@
 namespace aok {
 
 constexpr uint32_t kNone = 0xFFFFFFFFu;
+// In a descriptor (not a frame entry): lod | kResidentBit marks an uploaded
+// (chunk, LOD) whose DAG is empty (root == kNone), as opposed to one that is
+// not resident.
+constexpr uint32_t kResidentBit = 0x80000000u;
 constexpr int kFix = 12;            // camera origin fixed point: multiples of 2^-12
 constexpr int kMaxLevels = 10;      // log2(512) + 1
 
@@ -64,6 +68,19 @@ struct TileDev {
     int32_t tiles_x, tiles_y;
 };
 
+// Descriptor updates applied by a kernel on the rendering stream, so that a
+// frame sees every (chunk, LOD) change published before it and none after.
+struct DescPatch {
+    uint64_t index;  // descriptor index chunk * n_lods + lod
+    ChunkRef ref;
+};
+constexpr int kPatchMax = 96;
+struct DescPatches {
+    uint32_t n;
+    uint32_t pad;
+    DescPatch p[kPatchMax];
+};
+
 // A view of a batch: which scene, which camera, where the pixels go.
 struct ViewDev {
     SceneDev scene;
@@ -106,6 +123,7 @@ int aokk_cast(const aok::SceneDev* s, const aok::CamDev* c, const aok::ChunkRef*
 int aokk_ray_dirs(const aok::CamDev* c, float* dirs, void* stream);
 int aokk_tiles_frame(const aok::SceneDev* S, const aok::CamDev* C, const aok::ChunkRef* frame, const aok::TileDev* T,
                      uint4* hit, float* t, int sms, void* stream);
+int aokk_patch_desc(aok::ChunkRef* desc, const aok::DescPatches* p, void* stream);
 int aokk_read_bw(const void* buf, size_t n16, int passes, uint32_t* sink, int sms, void* stream);
 // Batched: one selection launch over (view, chunk), then one persistent
 // casting launch over all views' warp tiles.

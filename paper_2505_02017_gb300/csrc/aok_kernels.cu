@@ -41,7 +41,18 @@ __device__ __forceinline__ void select_one(const SceneDev& S, const CamDev& C, C
     int sel = 0;
     for (int n = S.n_lods - 1; n >= 1; n--)
         if (lod_loads(n, cx >> n, cy >> n, cz >> n, S.mlog, C.of, C.sf)) { sel = n; break; }
-    ChunkRef ref = S.desc[(size_t)chunk * S.n_lods + sel];
+    const ChunkRef* d = S.desc + (size_t)chunk * S.n_lods;
+    ChunkRef ref = d[sel];
+    if (ref.root == kNone && !(ref.lod & kResidentBit)) {
+        // the selected LOD is not resident (still streaming in): show the
+        // nearest resident LOD of the region, coarser ones first (Sec. 3.4
+        // loads coarser LODs first)
+        for (int n = sel + 1; n < S.n_lods; n++)
+            if (d[n].root != kNone) { ref = d[n]; break; }
+        for (int n = sel - 1; n >= 0 && ref.root == kNone; n--)
+            if (d[n].root != kNone) ref = d[n];
+    }
+    const int used = ref.root != kNone ? (int)(ref.lod & 0xFFu) : sel;
     bool vis = ref.root != kNone;
     if (vis) {
         // AABB grown by one voxel: culling stays conservative under FP32 rounding
@@ -70,9 +81,9 @@ __device__ __forceinline__ void select_one(const SceneDev& S, const CamDev& C, C
         }
     }
     if (!vis) ref.root = kNone;
-    ref.lod = (uint32_t)sel;
+    ref.lod = (uint32_t)used;
     frame[chunk] = ref;
-    if (lod_out) lod_out[chunk] = (int8_t)sel;
+    if (lod_out) lod_out[chunk] = (int8_t)used;
     if (vis_out) vis_out[chunk] = vis ? 1 : 0;
     if (vis && n_visible) atomicAdd(n_visible, 1u);
 }
@@ -176,6 +187,11 @@ __global__ void __launch_bounds__(128, 7) cast_grid(const __grid_constant__ Batc
     const int py = (local / bw) * 2 * th + (warp >> 1) * th + (lane >> twl);
     if (px < v.cam.W && py < v.cam.H)
         trace_pixel<false>(v.scene, v.cam, v.frame, px, py, v.hit, v.t, nullptr, (size_t)py * v.cam.W + px);
+}
+
+__global__ void patch_desc_kernel(ChunkRef* __restrict__ desc, const __grid_constant__ DescPatches P) {
+    const uint32_t i = threadIdx.x;
+    if (i < P.n) desc[P.p[i].index] = P.p[i].ref;
 }
 
 __global__ void ray_dirs_kernel(CamDev C, float* __restrict__ dirs) {
@@ -304,6 +320,12 @@ int aokk_max_ctas_per_sm(uint32_t threads) {
     int n = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, cast_persistent, (int)threads, 0);
     return n;
+}
+
+int aokk_patch_desc(ChunkRef* desc, const DescPatches* p, void* stream) {
+    if (p->n == 0) return AOK_OK;
+    patch_desc_kernel<<<1, kPatchMax, 0, (cudaStream_t)stream>>>(desc, *p);
+    return status_of(cudaGetLastError());
 }
 
 int aokk_ray_dirs(const CamDev* c, float* dirs, void* stream) {

@@ -436,7 +436,9 @@ static int chunk_index(const Scene* sc, int32_t cx, int32_t cy, int32_t cz, uint
     return AOK_OK;
 }
 
-static void free_alloc(Scene* sc, ChunkAlloc& a) {
+}  // extern "C"
+
+void aok::free_alloc(Scene* sc, ChunkAlloc& a) {
     sc->nodes.release(a.node_off, a.node_n);
     sc->leaves.release(a.leaf_off, a.leaf_n);
     sc->mats.release(a.mat_off, a.mat_n);
@@ -467,20 +469,19 @@ static void color_blocks(const uint8_t* v, uint64_t n, double e_c, std::vector<u
     }
 }
 
-int aok_scene_upload_chunk(aok_ctx* ctx, uint32_t scene, int32_t cx, int32_t cy, int32_t cz, uint32_t lod,
-                           const aok_chunk_blob* blob) {
-    if (!ctx || !blob) return AOK_E_INVALID;
-    Scene* sc = find_scene(ctx, scene);
-    if (!sc) return AOK_E_NOT_RESIDENT;
-    int64_t di;
-    int st = chunk_index(sc, cx, cy, cz, lod, &di);
-    if (st) return st;
-    cudaSetDevice(ctx->device);
-    std::lock_guard<std::mutex> g(sc->mu);
+// Validate a blob, allocate pool space for it and copy its device image
+// (node layout, leaves, colour array or blocks) through the staging memory
+// `sg` on its stream, waiting for the copies.  Nothing is published: *a and
+// *ref describe the staged (chunk, lod) for the caller to install in the
+// descriptor table.  When the pools are full and evict_old_first is set, the
+// previous upload of descriptor di is evicted first (after the device is
+// idle).  The pools are touched under *pool_mu, or under the caller's hold of
+// sc->mu when pool_mu is null.
+int aok::stage_chunk(aok_ctx* ctx, Scene* sc, int64_t di, uint32_t lod, const aok_chunk_blob* blob,
+                     bool evict_old_first, Staging* sg, std::mutex* pool_mu, ChunkAlloc* out_a, ChunkRef* out_ref) {
     const int M = sc->desc.chunk_res, res = M >> lod;
-    const uint64_t nw_blob = blob->n_node_words;
     // 1. validate before touching anything: a rejected blob changes nothing
-    st = validate_blob(blob, res, M);
+    int st = validate_blob(blob, res, M);
     if (st) return st;
     uint32_t droot = 0;
     const uint64_t nw = layout_blob(blob, res, 0, 0, nullptr, &droot);  // device words (even)
@@ -509,23 +510,22 @@ int aok_scene_upload_chunk(aok_ctx* ctx, uint32_t scene, int32_t cx, int32_t cy,
     // staging: laid-out node words + leaves + mats, 16-byte aligned segments
     const size_t nb = (nw * 4 + 15) & ~(size_t)15, lb = (blob->n_leaves * 8 + 15) & ~(size_t)15;
     const size_t need = nb + lb + mat_n + 16;
-    if (need > ctx->staging_cap) {
-        if (ctx->staging) cudaFreeHost(ctx->staging);
-        ctx->staging = nullptr;
-        ctx->staging_cap = 0;
-        size_t cap = std::max<size_t>(need, 64u << 20);
-        if (cudaMallocHost(&ctx->staging, cap) != cudaSuccess) {
+    if (need > sg->cap) {
+        if (sg->buf) cudaFreeHost(sg->buf);
+        sg->buf = nullptr;
+        sg->cap = 0;
+        size_t cap = std::max<size_t>(need, sg->min_cap);
+        if (cudaMallocHost(&sg->buf, cap) != cudaSuccess) {
             cudaGetLastError();
             return AOK_E_OOM;
         }
-        ctx->staging_cap = cap;
+        sg->cap = cap;
     }
-    uint8_t* stg = (uint8_t*)ctx->staging;
-    (void)nw_blob;
+    uint8_t* stg = (uint8_t*)sg->buf;
     // 2. allocate; if the pools are too full, evict the previous upload of this
     //    (chunk, lod) first (after the GPU is idle) and retry
-    ChunkAlloc& old = sc->alloc[di];
     auto evict_old = [&]() {
+        ChunkAlloc& old = sc->alloc[di];
         if (!(old.node_n || old.leaf_n || old.mat_n)) return;
         cudaDeviceSynchronize();
         free_alloc(sc, old);
@@ -556,16 +556,21 @@ int aok_scene_upload_chunk(aok_ctx* ctx, uint32_t scene, int32_t cx, int32_t cy,
         return true;
     };
     ChunkAlloc a;
-    if (!try_alloc(a)) {
-        evict_old();
-        if (!try_alloc(a)) return AOK_E_OOM;
+    {
+        std::unique_lock<std::mutex> pl;
+        if (pool_mu) pl = std::unique_lock<std::mutex>(*pool_mu);
+        if (!try_alloc(a)) {
+            if (!evict_old_first) return AOK_E_OOM;
+            evict_old();
+            if (!try_alloc(a)) return AOK_E_OOM;
+        }
     }
-    // 3. lay the (valid) blob out at its pool offsets
+    // 3. lay the (valid) blob out at its pool offsets and copy it
     layout_blob(blob, res, (uint32_t)a.node_off, (uint32_t)a.leaf_off, (uint32_t*)stg, &droot);
     ChunkRef ref;
     std::memset(&ref, 0, sizeof(ref));
     ref.root = kNone;
-    ref.lod = lod;
+    ref.lod = lod | kResidentBit;  // an uploaded, empty DAG until the root is set below
     uint64_t mat_base = a.mat_off;
     if (nw) {
         std::memcpy(stg + nb, blob->leaves, blob->n_leaves * 8);
@@ -589,19 +594,21 @@ int aok_scene_upload_chunk(aok_ctx* ctx, uint32_t scene, int32_t cx, int32_t cy,
             std::memcpy(q + head.size() * 4, bfirst.data(), bfirst.size() * 4);
             std::memcpy(q + head.size() * 4 + bfirst.size() * 4, bcol.data(), bcol.size());
         }
-        cudaError_t e = cudaMemcpyAsync(sc->d_nodes + a.node_off, stg, nw * 4, cudaMemcpyHostToDevice, ctx->copy_stream);
+        cudaError_t e = cudaMemcpyAsync(sc->d_nodes + a.node_off, stg, nw * 4, cudaMemcpyHostToDevice, sg->stream);
         if (e == cudaSuccess && blob->n_leaves)
             e = cudaMemcpyAsync(sc->d_leaves + a.leaf_off, stg + nb, blob->n_leaves * 8, cudaMemcpyHostToDevice,
-                                ctx->copy_stream);
+                                sg->stream);
         if (e == cudaSuccess && mat_n)
-            e = cudaMemcpyAsync(sc->d_mats + a.mat_off, stg + nb + lb, mat_n, cudaMemcpyHostToDevice,
-                                ctx->copy_stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->copy_stream);
+            e = cudaMemcpyAsync(sc->d_mats + a.mat_off, stg + nb + lb, mat_n, cudaMemcpyHostToDevice, sg->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(sg->stream);
         if (e != cudaSuccess) {
+            std::unique_lock<std::mutex> pl;
+            if (pool_mu) pl = std::unique_lock<std::mutex>(*pool_mu);
             free_alloc(sc, a);
             return cuda_status(ctx, e);
         }
         ref.root = droot;
+        ref.lod = lod;
         ref.mat_base = mat_base;
         ref.nblocks = (uint32_t)bfirst.size();
         for (int i = 0; i < 3; i++) {
@@ -609,6 +616,34 @@ int aok_scene_upload_chunk(aok_ctx* ctx, uint32_t scene, int32_t cx, int32_t cy,
             ref.aabb[3 + i] = (uint16_t)blob->aabb_hi[i];
         }
     }
+    *out_a = a;
+    *out_ref = ref;
+    return AOK_OK;
+}
+
+extern "C" {
+
+int aok_scene_upload_chunk(aok_ctx* ctx, uint32_t scene, int32_t cx, int32_t cy, int32_t cz, uint32_t lod,
+                           const aok_chunk_blob* blob) {
+    if (!ctx || !blob) return AOK_E_INVALID;
+    Scene* sc = find_scene(ctx, scene);
+    if (!sc) return AOK_E_NOT_RESIDENT;
+    int64_t di;
+    int st = chunk_index(sc, cx, cy, cz, lod, &di);
+    if (st) return st;
+    cudaSetDevice(ctx->device);
+    std::lock_guard<std::mutex> g(sc->mu);
+    ChunkAlloc a;
+    ChunkRef ref;
+    {
+        std::lock_guard<std::mutex> up(ctx->upload_mu);
+        Staging sg{ctx->staging, ctx->staging_cap, ctx->copy_stream};
+        st = stage_chunk(ctx, sc, di, lod, blob, true, &sg, nullptr, &a, &ref);
+        ctx->staging = sg.buf;
+        ctx->staging_cap = sg.cap;
+    }
+    if (st) return st;
+    ChunkAlloc& old = sc->alloc[di];
     if (old.node_n || old.leaf_n || old.mat_n) {
         cudaDeviceSynchronize();
         free_alloc(sc, old);

@@ -101,6 +101,7 @@ struct aok_ctx {
     size_t host_frame_px = 0;
     aok::ServeState* serve = nullptr;
     aok::TileState tiles;
+    std::mutex upload_mu;  // the staging buffer and the copy stream: one upload at a time
 };
 
 namespace aok {
@@ -113,5 +114,15 @@ Scene* find_scene(aok_ctx* ctx, uint32_t id);
 int make_cam(aok_ctx* ctx, const Scene* sc, const aok_camera* cam, double tau, CamDev* out);
 SceneDev scene_dev(const Scene* sc);
 void batch_release(aok_ctx* ctx);
+void free_alloc(Scene* sc, ChunkAlloc& a);
+// Pinned staging memory and the stream its copies go on.
+struct Staging {
+    void* buf = nullptr;
+    size_t cap = 0;
+    cudaStream_t stream = nullptr;
+    size_t min_cap = (size_t)64 << 20;  // smallest buffer allocated when it grows
+};
+int stage_chunk(aok_ctx* ctx, Scene* sc, int64_t di, uint32_t lod, const aok_chunk_blob* blob, bool evict_old_first,
+                Staging* stg, std::mutex* pool_mu, ChunkAlloc* out_a, ChunkRef* out_ref);
 int render_persistent(aok_ctx* ctx, Scene* sc, const CamDev& cd, const aok_frame* frame, void* stream, bool select);
 }  // namespace aok

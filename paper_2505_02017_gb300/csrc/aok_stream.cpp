@@ -1,0 +1,368 @@
+// Asynchronous chunk streaming (Aokana Sec. 3.4): worker threads load the
+// (chunk, LOD)s a camera needs while frames render; loads and evictions are
+// installed in the descriptor table at frame boundaries, by a kernel on the
+// rendering stream; evicted pool space is reused only after the frames that
+// could still read it have finished.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "aok_runtime.h"
+
+using namespace aok;
+
+namespace {
+
+struct Request {
+    uint32_t lod;
+    double dist2;  // squared distance from the camera to the region's centre
+    int64_t chunk;
+};
+
+// Heap order: the paper loads coarser LODs first, then the regions nearest
+// the camera.  std::push_heap keeps the "largest" on top, so "less" means
+// "loaded later".
+struct LoadsLater {
+    bool operator()(const Request& a, const Request& b) const {
+        if (a.lod != b.lod) return a.lod < b.lod;
+        if (a.dist2 != b.dist2) return a.dist2 > b.dist2;
+        return a.chunk > b.chunk;
+    }
+};
+
+struct Loaded {
+    int64_t chunk;
+    uint32_t lod;
+    ChunkAlloc alloc;
+    ChunkRef ref;
+};
+
+struct Quarantined {
+    cudaEvent_t done;
+    std::vector<ChunkAlloc> allocs;
+};
+
+uint64_t alloc_bytes(const ChunkAlloc& a) { return a.node_n * 4 + a.leaf_n * 8 + a.mat_n; }
+
+}  // namespace
+
+struct aok_stream {
+    aok_ctx* ctx = nullptr;
+    uint32_t scene_id = 0;
+    Scene* sc = nullptr;
+    aok_chunk_source_fn source = nullptr;
+    aok_chunk_release_fn release = nullptr;
+    void* user = nullptr;
+    int L = 0;
+    int64_t n = 0;
+    int gx = 0, gy = 0;
+
+    std::mutex mu;
+    std::condition_variable work_cv, idle_cv;
+    bool stop = false;
+    std::vector<uint8_t> want;      // planned LOD per region (0xFF: none)
+    std::vector<uint8_t> resident;  // installed LODs per region (bitmask)
+    std::vector<uint8_t> pending;   // LODs queued, loading or loaded-not-installed (bitmask)
+    std::vector<Request> heap;
+    std::vector<Request> deferred;  // loads that did not fit in the pools
+    std::vector<Loaded> loaded;
+    std::deque<Quarantined> quarantine;
+    int running = 0;
+    std::vector<std::thread> workers;
+
+    uint64_t res_count = 0, res_bytes = 0, max_count = 0, max_bytes = 0;
+    uint64_t n_installed = 0, n_evicted = 0, n_cancelled = 0, n_failed = 0, n_deferred = 0;
+    uint64_t n_missing = 0;  // planned regions whose planned LOD was not installed at the last update
+
+    void worker();
+};
+
+void aok_stream::worker() {
+    cudaSetDevice(ctx->device);
+    // each worker stages and copies on its own pinned buffer and stream
+    Staging sg;
+    sg.min_cap = (size_t)8 << 20;
+    if (cudaStreamCreateWithFlags(&sg.stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        sg.stream = nullptr;
+    }
+    for (;;) {
+        Request r;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            work_cv.wait(lk, [&] { return stop || !heap.empty(); });
+            if (stop) break;
+            std::pop_heap(heap.begin(), heap.end(), LoadsLater());
+            r = heap.back();
+            heap.pop_back();
+            if (want[r.chunk] != r.lod) {  // the plan moved on: cancel
+                pending[r.chunk] &= (uint8_t)~(1u << r.lod);
+                n_cancelled++;
+                if (heap.empty() && running == 0) idle_cv.notify_all();
+                continue;
+            }
+            running++;
+        }
+        const int cx = (int)(r.chunk % gx), cy = (int)((r.chunk / gx) % gy), cz = (int)(r.chunk / ((int64_t)gx * gy));
+        aok_chunk_blob blob;
+        std::memset(&blob, 0, sizeof(blob));
+        void* handle = nullptr;
+        int st = source(user, cx, cy, cz, r.lod, &blob, &handle) == 0 ? AOK_OK : AOK_E_INVALID;
+        ChunkAlloc a;
+        ChunkRef ref;
+        if (st == AOK_OK) st = sg.stream ? stage_chunk(ctx, sc, r.chunk * L + r.lod, r.lod, &blob, false, &sg, &sc->mu,
+                                                       &a, &ref)
+                                         : AOK_E_CUDA;
+        if (handle) release(user, handle);
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            running--;
+            if (st == AOK_OK) {
+                loaded.push_back({r.chunk, r.lod, a, ref});
+            } else if (st == AOK_E_OOM) {
+                deferred.push_back(r);  // retried after the next evictions
+                n_deferred++;
+            } else {
+                pending[r.chunk] &= (uint8_t)~(1u << r.lod);
+                n_failed++;
+            }
+            if (heap.empty() && running == 0) idle_cv.notify_all();
+        }
+    }
+    if (sg.buf) cudaFreeHost(sg.buf);
+    if (sg.stream) cudaStreamDestroy(sg.stream);
+}
+
+extern "C" {
+
+int aok_stream_create(aok_ctx* ctx, uint32_t scene, aok_chunk_source_fn source, aok_chunk_release_fn release,
+                      void* user, int32_t n_threads, aok_stream** out) {
+    if (!ctx || !source || !release || !out || n_threads < 1 || n_threads > 256) return AOK_E_INVALID;
+    Scene* sc = find_scene(ctx, scene);
+    if (!sc) return AOK_E_NOT_RESIDENT;
+    aok_stream* s = new (std::nothrow) aok_stream();
+    if (!s) return AOK_E_OOM;
+    s->ctx = ctx;
+    s->scene_id = scene;
+    s->sc = sc;
+    s->source = source;
+    s->release = release;
+    s->user = user;
+    s->L = sc->desc.n_lods;
+    s->n = sc->n_chunks;
+    s->gx = sc->desc.grid[0];
+    s->gy = sc->desc.grid[1];
+    s->want.assign((size_t)s->n, 0xFF);
+    s->resident.assign((size_t)s->n, 0);
+    s->pending.assign((size_t)s->n, 0);
+    {
+        // adopt what is already installed
+        std::lock_guard<std::mutex> g(sc->mu);
+        for (int64_t c = 0; c < s->n; c++)
+            for (int l = 0; l < s->L; l++) {
+                const ChunkAlloc& a = sc->alloc[(size_t)(c * s->L + l)];
+                const ChunkRef& d = sc->h_desc[(size_t)(c * s->L + l)];
+                if (d.root != kNone || (d.lod & kResidentBit)) {
+                    s->resident[c] |= (uint8_t)(1u << l);
+                    s->res_count++;
+                    s->res_bytes += alloc_bytes(a);
+                }
+            }
+        s->max_count = s->res_count;
+        s->max_bytes = s->res_bytes;
+    }
+    for (int i = 0; i < n_threads; i++) s->workers.emplace_back([s] { s->worker(); });
+    *out = s;
+    return AOK_OK;
+}
+
+int aok_stream_update(aok_stream* s, const aok_camera* cam, double tau, void* stream) {
+    if (!s || !cam) return AOK_E_INVALID;
+    aok_ctx* ctx = s->ctx;
+    Scene* sc = s->sc;
+    std::vector<uint8_t> plan((size_t)s->n);
+    int st = aok_plan_residency(ctx, s->scene_id, cam, tau, plan.data(), nullptr);
+    if (st) return st;
+    CamDev cd;
+    st = make_cam(ctx, sc, cam, tau, &cd);
+    if (st) return st;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_status(ctx, cudaGetLastError());
+    const double M = sc->desc.chunk_res;
+    std::vector<DescPatch> patches;
+    std::vector<ChunkAlloc> dead;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        std::lock_guard<std::mutex> g(sc->mu);
+        s->want.swap(plan);
+        auto none_ref = [](uint32_t lod) {
+            ChunkRef r;
+            std::memset(&r, 0, sizeof(r));
+            r.root = kNone;
+            r.lod = lod;
+            return r;
+        };
+        // 1. install finished loads (a region no longer planned frees its load at once: never visible)
+        for (Loaded& ld : s->loaded) {
+            const size_t di = (size_t)(ld.chunk * s->L + ld.lod);
+            s->pending[ld.chunk] &= (uint8_t)~(1u << ld.lod);
+            if (s->want[ld.chunk] == 0xFF) {
+                free_alloc(sc, ld.alloc);
+                s->n_cancelled++;
+                continue;
+            }
+            patches.push_back({(uint64_t)di, ld.ref});
+            sc->alloc[di] = ld.alloc;
+            sc->h_desc[di] = ld.ref;
+            s->resident[ld.chunk] |= (uint8_t)(1u << ld.lod);
+            s->res_count++;
+            s->res_bytes += alloc_bytes(ld.alloc);
+            s->n_installed++;
+        }
+        s->loaded.clear();
+        // 2. evictions: a region's other LODs go once its planned LOD is installed,
+        //    all of them once it is no longer planned
+        for (int64_t c = 0; c < s->n; c++) {
+            const uint8_t res = s->resident[c];
+            if (!res) continue;
+            const uint8_t w = s->want[c];
+            const bool settled = w == 0xFF || (res >> w) & 1u;
+            if (!settled) continue;
+            for (int l = 0; l < s->L; l++) {
+                if (!((res >> l) & 1u) || l == (int)w) continue;
+                const size_t di = (size_t)(c * s->L + l);
+                patches.push_back({(uint64_t)di, none_ref((uint32_t)l)});
+                s->res_bytes -= std::min(s->res_bytes, alloc_bytes(sc->alloc[di]));
+                dead.push_back(sc->alloc[di]);
+                sc->alloc[di] = ChunkAlloc();
+                sc->h_desc[di] = none_ref((uint32_t)l);
+                s->resident[c] &= (uint8_t)~(1u << l);
+                s->res_count--;
+                s->n_evicted++;
+            }
+        }
+        s->max_count = std::max(s->max_count, s->res_count);
+        s->max_bytes = std::max(s->max_bytes, s->res_bytes);
+        // 3. requests for planned LODs neither installed nor on their way; deferred loads retry
+        for (Request& r : s->deferred) {
+            if (s->want[r.chunk] == r.lod) {
+                s->heap.push_back(r);
+                std::push_heap(s->heap.begin(), s->heap.end(), LoadsLater());
+            } else {
+                s->pending[r.chunk] &= (uint8_t)~(1u << r.lod);
+                s->n_cancelled++;
+            }
+        }
+        s->deferred.clear();
+        s->n_missing = 0;
+        for (int64_t c = 0; c < s->n; c++) {
+            const uint8_t w = s->want[c];
+            if (w != 0xFF && !((s->resident[c] >> w) & 1u)) s->n_missing++;
+            if (w == 0xFF || ((s->resident[c] | s->pending[c]) >> w) & 1u) continue;
+            const int cx = (int)(c % s->gx), cy = (int)((c / s->gx) % s->gy), cz = (int)(c / ((int64_t)s->gx * s->gy));
+            const double q[3] = {(cx + 0.5) * M - cd.of[0], (cy + 0.5) * M - cd.of[1], (cz + 0.5) * M - cd.of[2]};
+            s->heap.push_back({(uint32_t)w, q[0] * q[0] + q[1] * q[1] + q[2] * q[2], c});
+            std::push_heap(s->heap.begin(), s->heap.end(), LoadsLater());
+            s->pending[c] |= (uint8_t)(1u << w);
+        }
+    }
+    s->work_cv.notify_all();
+    // 4. the descriptor changes, ordered before every later frame on `stream`
+    for (size_t i = 0; i < patches.size(); i += kPatchMax) {
+        DescPatches P;
+        P.n = (uint32_t)std::min<size_t>(kPatchMax, patches.size() - i);
+        P.pad = 0;
+        std::memcpy(P.p, patches.data() + i, P.n * sizeof(DescPatch));
+        if (aokk_patch_desc(sc->d_desc, &P, stream)) return cuda_status(ctx, cudaGetLastError());
+    }
+    // 5. evicted space waits for the frames enqueued before the eviction
+    if (!dead.empty()) {
+        Quarantined q;
+        if (cudaEventCreateWithFlags(&q.done, cudaEventDisableTiming) != cudaSuccess)
+            return cuda_status(ctx, cudaGetLastError());
+        if (cudaEventRecord(q.done, (cudaStream_t)stream) != cudaSuccess) {
+            cudaEventDestroy(q.done);
+            return cuda_status(ctx, cudaGetLastError());
+        }
+        q.allocs.swap(dead);
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->quarantine.push_back(std::move(q));
+    }
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        bool freed = false;
+        while (!s->quarantine.empty() && cudaEventQuery(s->quarantine.front().done) == cudaSuccess) {
+            std::lock_guard<std::mutex> g(sc->mu);
+            for (ChunkAlloc& a : s->quarantine.front().allocs) free_alloc(sc, a);
+            cudaEventDestroy(s->quarantine.front().done);
+            s->quarantine.pop_front();
+            freed = true;
+        }
+        cudaGetLastError();  // cudaErrorNotReady from the query is not an error
+        if (freed && !s->deferred.empty()) {
+            for (Request& r : s->deferred) {
+                s->heap.push_back(r);
+                std::push_heap(s->heap.begin(), s->heap.end(), LoadsLater());
+            }
+            s->deferred.clear();
+            s->work_cv.notify_all();
+        }
+    }
+    return AOK_OK;
+}
+
+int aok_stream_wait(aok_stream* s, int32_t timeout_ms) {
+    if (!s) return AOK_E_INVALID;
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto idle = [&] { return s->heap.empty() && s->running == 0; };
+    if (timeout_ms < 0) {
+        s->idle_cv.wait(lk, idle);
+        return AOK_OK;
+    }
+    return s->idle_cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), idle) ? AOK_OK : AOK_E_TIMEOUT;
+}
+
+int aok_stream_stats(aok_stream* s, uint64_t* st) {
+    if (!s || !st) return AOK_E_INVALID;
+    std::lock_guard<std::mutex> lk(s->mu);
+    const uint64_t v[13] = {s->res_count, s->res_bytes, s->max_count, s->max_bytes, (uint64_t)s->heap.size(),
+                            (uint64_t)s->running, (uint64_t)s->loaded.size(), s->n_installed, s->n_evicted,
+                            s->n_cancelled, s->n_failed, s->n_deferred, s->n_missing};
+    std::memcpy(st, v, sizeof(v));
+    return AOK_OK;
+}
+
+int aok_stream_resident(aok_stream* s, uint8_t* masks) {
+    if (!s || !masks) return AOK_E_INVALID;
+    std::lock_guard<std::mutex> lk(s->mu);
+    std::memcpy(masks, s->resident.data(), s->resident.size());
+    return AOK_OK;
+}
+
+int aok_stream_destroy(aok_stream* s) {
+    if (!s) return AOK_E_INVALID;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->work_cv.notify_all();
+    for (std::thread& t : s->workers) t.join();
+    cudaSetDevice(s->ctx->device);
+    std::lock_guard<std::mutex> g(s->sc->mu);
+    for (Loaded& ld : s->loaded) free_alloc(s->sc, ld.alloc);
+    for (Quarantined& q : s->quarantine) {
+        cudaEventSynchronize(q.done);
+        for (ChunkAlloc& a : q.allocs) free_alloc(s->sc, a);
+        cudaEventDestroy(q.done);
+    }
+    delete s;
+    return AOK_OK;
+}
+
+}  // extern "C"

@@ -1,9 +1,16 @@
 """Chunk residency for large worlds (the streaming side of Sec. 3.4).
 
-For each camera, aok_plan_residency gives the LOD Eq. 1 selects for every
-chunk region within the view distance (bit-identical to the GPU selection);
-regions whose resident LOD differs are evicted, missing (chunk, LOD) pairs are
-built by the native builder (only the needed LOD of each region) and uploaded.
+Streamer (synchronous): for each camera, aok_plan_residency gives the LOD
+Eq. 1 selects for every chunk region within the view distance (bit-identical
+to the GPU selection); regions whose resident LOD differs are evicted, missing
+(chunk, LOD) pairs are built by the native builder (only the needed LOD of
+each region) and uploaded before the frame renders.
+
+AsyncStreamer: the native background loader of aok_stream_* -- worker threads
+build and upload in the paper's load order (coarser LODs first, then nearest)
+while frames render; changes are installed between frames.  The builder's C
+functions are handed to it directly as the chunk source.
+
 Every step runs in the native libraries; this module only moves lists.
 """
 from __future__ import annotations
@@ -14,7 +21,7 @@ import time
 
 import numpy as np
 
-from . import BuiltWorld, Scene, check, lib, to_camera
+from . import BuiltWorld, Scene, _stream_handle, blib, check, lib, to_camera
 
 
 class Streamer:
@@ -71,3 +78,59 @@ class Streamer:
         self.max_bytes = max(self.max_bytes, nbytes)
         return {"evicted": int(len(stale)), "built": int(len(missing)), "resident": nres, "resident_bytes": nbytes,
                 "plan_s": t1 - t0, "build_s": t2 - t1, "upload_s": t3 - t2}
+
+
+STREAM_STATS = ("resident", "resident_bytes", "max_resident", "max_resident_bytes", "queued", "running",
+                "loaded_not_installed", "installed_total", "evicted_total", "cancelled_total", "failed_total",
+                "deferred_total", "missing")
+
+
+class AsyncStreamer:
+    """Background residency for `scene` (aok_stream_*), loading from the native builder."""
+
+    def __init__(self, ctx, world, scene: Scene, threads: int | None = None):
+        self.ctx, self.world, self.scene = ctx, world, scene
+        spec = world.spec
+        self._src = blib().aokb_source_create(world.handle, spec.chunk, spec.n_lods)
+        if not self._src:
+            raise ValueError("bad chunking for the builder")
+        build = ctypes.cast(blib().aokb_source_build, ctypes.c_void_p)
+        release = ctypes.cast(blib().aokb_source_release, ctypes.c_void_p)
+        h = ctypes.c_void_p()
+        check(lib().aok_stream_create(ctx.h, scene.id, build, release, self._src, int(threads or os.cpu_count() or 1),
+                                      ctypes.byref(h)), "aok_stream_create")
+        self.h = h
+        gx, gy, gz = scene.grid
+        self.n = gx * gy * gz
+
+    def update(self, cam, tau: float, stream=None):
+        c = to_camera(cam)
+        return check(lib().aok_stream_update(self.h, ctypes.byref(c), float(tau), _stream_handle(stream)),
+                     "aok_stream_update")
+
+    def wait(self, timeout_ms: int = -1) -> int:
+        return int(lib().aok_stream_wait(self.h, int(timeout_ms)))
+
+    def stats(self) -> dict:
+        a = (ctypes.c_uint64 * 13)()
+        check(lib().aok_stream_stats(self.h, a), "aok_stream_stats")
+        return dict(zip(STREAM_STATS, (int(v) for v in a)))
+
+    def resident(self) -> np.ndarray:
+        out = np.zeros(self.n, np.uint8)
+        check(lib().aok_stream_resident(self.h, out.ctypes.data), "aok_stream_resident")
+        return out
+
+    def close(self):
+        if self.h:
+            lib().aok_stream_destroy(self.h)
+            self.h = None
+        if self._src:
+            blib().aokb_source_destroy(self._src)
+            self._src = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

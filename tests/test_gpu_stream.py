@@ -99,3 +99,55 @@ def test_open65536_path_pose_sampled():
     assert (g["hit"][idx] == 1).mean() > 0.3
     sc.destroy()
     ctx.close()
+
+
+def test_async_streaming_frames_match_oracle_and_settle():
+    """Asynchronous residency (Sec. 3.4): frames render while loads run in the
+    background; every frame equals the oracle for the LODs it actually used
+    (the selected one where installed, else the stand-in the selection chose);
+    once the loads finish, the frame equals the synchronous streamer's."""
+    from paper_2505_02017_gb300.stream import AsyncStreamer
+    spec = sg.OPEN_8192
+    w = sg.World(spec)
+    ctx = aok.Context(0)
+    sc_a = aok.Scene(ctx, spec, node_words=64 << 20, leaves=16 << 20, mat_bytes=1 << 30)
+    sc_s = aok.Scene(ctx, spec, node_words=64 << 20, leaves=16 << 20, mat_bytes=1 << 30)
+    ast = AsyncStreamer(ctx, w, sc_a, threads=8)
+    sst = Streamer(ctx, w, sc_s, threads=8)
+    S = orc.OracleScene(w)
+    cams = sg.path_cameras(w, 77, 6, 160, 90, n_waypoints=3, span=3000.0)
+    tau = 1.0 / 3.0
+    n = sc_a.grid[0] * sc_a.grid[1] * sc_a.grid[2]
+    partial = 0
+    for i, cam in enumerate(cams):
+        ast.update(cam, tau)
+        if i == 2:
+            ast.wait()  # one frame in the middle with every load of the previous plan finished
+        lod = torch.empty(n, dtype=torch.int8, device="cuda")
+        hit, t = aok.alloc_frame(cam.W, cam.H)
+        aok.select_chunks(ctx, sc_a, cam, tau, lod_out=lod)
+        aok.cast_selected(ctx, sc_a, cam, hit, t)
+        torch.cuda.synchronize()
+        used = lod.cpu().numpy().astype(np.int64)
+        res = ast.resident().astype(np.int64)
+        sel = np.where((res >> used) & 1, used, -1).astype(np.int8)
+        partial += int(ast.stats()["missing"] > 0)
+        ref = S.cast(cam, sel, view_dist=spec.view_dist)
+        compare(decode(hit, t), ref, max_amb_frac=2e-3)
+    assert partial > 0  # some frames rendered before their loads finished
+    # settle on the last pose and compare with the synchronous streamer
+    assert ast.wait(120000) == aok.AOK_OK
+    ast.update(cams[-1], tau)
+    st = ast.stats()
+    assert st["missing"] == 0 and st["failed_total"] == 0 and st["installed_total"] > 0
+    assert st["max_resident"] >= st["resident"] > 0
+    sst.update(cams[-1], tau)
+    fa, fs = aok.alloc_frame(160, 90), aok.alloc_frame(160, 90)
+    aok.render(ctx, sc_a, cams[-1], tau, *fa)
+    aok.render(ctx, sc_s, cams[-1], tau, *fs)
+    torch.cuda.synchronize()
+    assert torch.equal(fa[0], fs[0]) and torch.equal(fa[1].view(torch.int32), fs[1].view(torch.int32))
+    ast.close()
+    sc_a.destroy()
+    sc_s.destroy()
+    ctx.close()
