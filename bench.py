@@ -122,6 +122,21 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over all ranks (the job takes as long as its slowest rank)."""
+    if dist is None:
+        return x
+    import torch
+    tt = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_rate(units_per_rank: float, world_size: int, seconds: float) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return world_size * units_per_rank / seconds
+
+
 def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
         int(os.environ.get("LOCAL_RANK", "0"))
@@ -666,11 +681,9 @@ def main():
     cast_ms = [e[1].elapsed_time(e[2]) for e in ev]
     total_ms = sum(step_ms)
     if dist:
-        tt = torch.tensor([total_ms], device=f"cuda:{dev}")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+        total_ms = max_over_ranks(total_ms, dist, f"cuda:{dev}")
     rays = W * H
-    value = world_size * rays * args.steps / (total_ms / 1000.0)
+    value = job_rate(rays * args.steps, world_size, total_ms / 1000.0)
     cast_avg = sum(cast_ms) / len(cast_ms)
     hbm, peak_kind = peaks()
     achieved = algo_bytes / (cast_avg / 1000.0) / 1e9
@@ -691,9 +704,7 @@ def main():
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e = world_size * rays / e2e_s
     if dist:
-        tt = torch.tensor([e2e_s], device=f"cuda:{dev}")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e = world_size * rays / float(tt.item())
+        e2e = job_rate(rays, world_size, max_over_ranks(e2e_s, dist, f"cuda:{dev}"))
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world_size, "steps": args.steps,
