@@ -330,6 +330,20 @@ int aok_cast_selected(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, const
  * are kept for the next call (grown on demand, charged to the budget). */
 int aok_render_host(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double lod_threshold_px,
                     void* hit_host, float* t_host, void* stream);
+/* Pipelined aok_render_host for frame loops: enqueues the render into one of
+ * three library-owned device frames on a context stream and the copy into
+ * the caller's host buffers (pinned) on a second stream, and returns at once
+ * with a ticket, so that a frame's render overlaps the previous frame's copy.
+ * The host buffers must stay valid and untouched until
+ * aok_host_frame_wait(ticket) returns.  With three frames in flight, a new
+ * call first waits for the oldest one's copy.  Frames of one context are
+ * rendered in call order on the context's own stream: other renders of the
+ * same scene must not overlap them (aok_render's rule). */
+int aok_render_host_async(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double lod_threshold_px,
+                          void* hit_host, float* t_host, uint64_t* ticket);
+/* Block until the frame `ticket` is complete in host memory (AOK_E_INVALID
+ * for a ticket never issued). */
+int aok_host_frame_wait(aok_ctx* ctx, uint64_t ticket);
 
 /* ------------------------------------------------------------------ */
 /* Batched multi-view rendering                                       */

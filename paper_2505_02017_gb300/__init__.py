@@ -93,6 +93,8 @@ def lib() -> ctypes.CDLL:
             "aok_render_counted": [vp, u32, P(Camera), dbl, P(Frame), vp, vp],
             "aok_render_noalloc": [vp, u32, P(Camera), dbl, P(Frame), vp],
             "aok_render_tiles": [vp, u32, P(Camera), dbl, P(Frame), vp],
+            "aok_render_host_async": [vp, u32, P(Camera), dbl, vp, vp, P(u64)],
+            "aok_host_frame_wait": [vp, u64],
             "aok_tiles_stats": [vp, P(u64)],
             "aok_tiles_forget": [vp],
             "aok_ray_dirs": [vp, P(Camera), vp, vp],
@@ -376,6 +378,19 @@ def render_host(ctx: Context, scene: Scene, cam, tau: float, hit_host, t_host, s
     c = to_camera(cam)
     return check(lib().aok_render_host(ctx.h, scene.id, ctypes.byref(c), float(tau), hit_host.data_ptr(),
                                        t_host.data_ptr(), _stream_handle(stream)), "aok_render_host")
+
+
+def render_host_async(ctx: Context, scene: Scene, cam, tau: float, hit_host, t_host) -> int:
+    """Enqueue a frame into host tensors (pinned); returns its ticket (aok_render_host_async)."""
+    c = to_camera(cam)
+    tk = ctypes.c_uint64()
+    check(lib().aok_render_host_async(ctx.h, scene.id, ctypes.byref(c), float(tau), hit_host.data_ptr(),
+                                      t_host.data_ptr(), ctypes.byref(tk)), "aok_render_host_async")
+    return tk.value
+
+
+def host_frame_wait(ctx: Context, ticket: int):
+    return check(lib().aok_host_frame_wait(ctx.h, int(ticket)), "aok_host_frame_wait")
 
 
 def render_counted(ctx: Context, scene: Scene, cam, tau: float, hit, t, counts, stream=None):

@@ -279,6 +279,8 @@ static uint64_t layout_blob(const aok_chunk_blob* b, int res, uint32_t node_base
     return w;
 }
 
+static void pipe_release(aok_ctx* ctx);
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -344,6 +346,9 @@ void aok_destroy(aok_ctx* ctx) {
     dev_free(ctx, ctx->d_counter, sizeof(uint32_t) * 16);
     dev_free(ctx, ctx->d_single_queue, 2 * sizeof(unsigned long long));
     dev_free(ctx, ctx->tiles.block, ctx->tiles.bytes);
+    pipe_release(ctx);
+    if (ctx->pipe.render) cudaStreamDestroy(ctx->pipe.render);
+    if (ctx->pipe.copy) cudaStreamDestroy(ctx->pipe.copy);
     if (ctx->staging) cudaFreeHost(ctx->staging);
     if (ctx->pinned_word) cudaFreeHost(ctx->pinned_word);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
@@ -985,6 +990,81 @@ int aok_render_host(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double 
     if (e == cudaSuccess) e = cudaMemcpyAsync(t_host, ctx->host_t_dev, px * 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     return cuda_status(ctx, e);
+}
+
+// ---------------------------------------------------------------------------
+// pipelined rendering into host memory
+// ---------------------------------------------------------------------------
+extern "C++" {
+static void pipe_release(aok_ctx* ctx) {
+    HostPipe& p = ctx->pipe;
+    for (HostSlot& sl : p.slot) {
+        if (sl.copied) cudaEventSynchronize(sl.copied);
+        dev_free(ctx, sl.hit, p.px * 16);
+        dev_free(ctx, sl.t, p.px * 4);
+        if (sl.rendered) cudaEventDestroy(sl.rendered);
+        if (sl.copied) cudaEventDestroy(sl.copied);
+        sl = HostSlot();
+    }
+    p.px = 0;
+}
+
+static int pipe_ensure(aok_ctx* ctx, size_t px) {
+    HostPipe& p = ctx->pipe;
+    if (!p.render) {
+        if (cudaStreamCreateWithFlags(&p.render, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&p.copy, cudaStreamNonBlocking) != cudaSuccess)
+            return cuda_status(ctx, cudaGetLastError());
+    }
+    if (px <= p.px) return AOK_OK;
+    pipe_release(ctx);
+    for (HostSlot& sl : p.slot) {
+        int st = dev_alloc(ctx, &sl.hit, px * 16);
+        if (!st) st = dev_alloc(ctx, (void**)&sl.t, px * 4);
+        if (!st && (cudaEventCreateWithFlags(&sl.rendered, cudaEventDisableTiming) != cudaSuccess ||
+                    cudaEventCreateWithFlags(&sl.copied, cudaEventDisableTiming) != cudaSuccess))
+            st = cuda_status(ctx, cudaGetLastError());
+        if (st) {
+            p.px = px;
+            pipe_release(ctx);
+            return st;
+        }
+    }
+    p.px = px;
+    return AOK_OK;
+}
+}  // extern "C++"
+
+int aok_render_host_async(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double tau, void* hit_host,
+                          float* t_host, uint64_t* ticket) {
+    if (!ctx || !cam || !hit_host || !t_host || !ticket || cam->width <= 0 || cam->height <= 0) return AOK_E_INVALID;
+    const size_t px = (size_t)cam->width * cam->height;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_status(ctx, cudaGetLastError());
+    int st = pipe_ensure(ctx, px);
+    if (st) return st;
+    HostPipe& p = ctx->pipe;
+    HostSlot& sl = p.slot[p.next % kHostSlots];
+    // the slot's previous frame must have left the device buffers
+    if (sl.ticket && cudaEventSynchronize(sl.copied) != cudaSuccess) return cuda_status(ctx, cudaGetLastError());
+    aok_frame f{sl.hit, sl.t};
+    st = aok_render(ctx, scene, cam, tau, &f, p.render);
+    if (st) return st;
+    cudaError_t e = cudaEventRecord(sl.rendered, p.render);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p.copy, sl.rendered, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hit_host, sl.hit, px * 16, cudaMemcpyDeviceToHost, p.copy);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t_host, sl.t, px * 4, cudaMemcpyDeviceToHost, p.copy);
+    if (e == cudaSuccess) e = cudaEventRecord(sl.copied, p.copy);
+    if (e != cudaSuccess) return cuda_status(ctx, e);
+    sl.ticket = ++p.next;
+    *ticket = sl.ticket;
+    return AOK_OK;
+}
+
+int aok_host_frame_wait(aok_ctx* ctx, uint64_t ticket) {
+    if (!ctx || ticket == 0 || ticket > ctx->pipe.next) return AOK_E_INVALID;
+    for (HostSlot& sl : ctx->pipe.slot)
+        if (sl.ticket == ticket) return cuda_status(ctx, cudaEventSynchronize(sl.copied));
+    return AOK_OK;  // its slot was reused, which waited for it
 }
 
 int aok_ray_dirs(aok_ctx* ctx, const aok_camera* cam, float* dirs, void* stream) {

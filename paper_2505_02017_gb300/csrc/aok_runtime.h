@@ -58,6 +58,22 @@ struct BatchArena {
 
 struct ServeState;
 
+// Frames rendered into host memory through a pipeline: slot k's render (on
+// `render`) overlaps slot k-1's device-to-host copy (on `copy`).
+constexpr int kHostSlots = 3;
+struct HostSlot {
+    void* hit = nullptr;
+    float* t = nullptr;
+    cudaEvent_t rendered = nullptr, copied = nullptr;
+    uint64_t ticket = 0;  // frame in this slot (0: none yet)
+};
+struct HostPipe {
+    cudaStream_t render = nullptr, copy = nullptr;
+    HostSlot slot[kHostSlots];
+    size_t px = 0;        // pixels each slot holds
+    uint64_t next = 0;    // last ticket issued
+};
+
 // Buffers of the tile-chunk pipeline for one resolution and grid size (one
 // device allocation carved into the TileDev arrays), and the scene whose
 // Hi-Z history hiz_prev holds.
@@ -101,6 +117,7 @@ struct aok_ctx {
     size_t host_frame_px = 0;
     aok::ServeState* serve = nullptr;
     aok::TileState tiles;
+    aok::HostPipe pipe;
     std::mutex upload_mu;  // the staging buffer and the copy stream: one upload at a time
 };
 

@@ -199,3 +199,23 @@ def test_serving_admission_by_budget_and_cancel(env):
         srv.stop()
         sc.destroy()
         ctx.close()
+
+
+def test_pipelined_host_frames_equal_device_frames(env):
+    """aok_render_host_async: frames in flight overlap; each host frame equals
+    the device render of its camera."""
+    ctx, worlds, scenes = env
+    ps = poses(worlds, 7, 23)
+    refs = [solo(ctx, scenes[n], c, tau) for (n, c, tau) in ps]
+    torch.cuda.synchronize()  # the pipeline renders on its own stream
+    bufs = [(torch.empty((c.H, c.W, 4), dtype=torch.int32, pin_memory=True),
+             torch.empty((c.H, c.W), dtype=torch.float32, pin_memory=True)) for (_, c, _) in ps]
+    tickets = [aok.render_host_async(ctx, scenes[n], c, tau, *b) for (n, c, tau), b in zip(ps, bufs)]
+    assert tickets == sorted(tickets) and len(set(tickets)) == len(tickets)
+    for tk in tickets:
+        aok.host_frame_wait(ctx, tk)
+    for (hr, tr), (hh, th) in zip(refs, bufs):
+        assert torch.equal(hr.cpu(), hh) and torch.equal(tr.cpu().view(torch.int32), th.view(torch.int32))
+    with pytest.raises(aok.AokError) as ex:
+        aok.host_frame_wait(ctx, tickets[-1] + 100)
+    assert ex.value.status == aok.AOK_E_INVALID
