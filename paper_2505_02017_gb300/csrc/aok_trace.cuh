@@ -212,29 +212,35 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
             c2 = 2 * c2 + b2;
             k = kk;
         } else {
-            // leave cell (k, c) through its nearest exit face
-            const int32_t N0 = ((c0 + 1) << (k + kFix)) - Oloc[0];
-            const int32_t N1 = ((c1 + 1) << (k + kFix)) - Oloc[1];
-            const int32_t N2 = ((c2 + 1) << (k + kFix)) - Oloc[2];
-            const bool xy = tltf<FAST>(N0, r.m[0], N1, r.m[1], r.E[1] - r.E[0]);
-            const int32_t Na = xy ? N0 : N1, ma = xy ? r.m[0] : r.m[1], Ea = xy ? r.E[0] : r.E[1];
-            const bool az = tltf<FAST>(Na, ma, N2, r.m[2], r.E[2] - Ea);
-            int ax;
-            if (az) { ax = xy ? 0 : 1; Ne = Na; me = ma; Ee = Ea; }
-            else { ax = 2; Ne = N2; me = r.m[2]; Ee = r.E[2]; }
-            e = ax;
-            int32_t cax;
-            if (ax == 0) cax = ++c0;
-            else if (ax == 1) cax = ++c1;
-            else cax = ++c2;
-            if ((cax << k) >= (1 << R)) return false;  // left the chunk
-            if ((cax & 1) == 0) {
-                do {
-                    c0 >>= 1; c1 >>= 1; c2 >>= 1;
-                    cax >>= 1;
-                    k++;
-                } while (k < R && (cax & 1) == 0);
-                pm8 = k >= n + 2 ? smask[k + 1] : g8;  // popped into a new parent (a node or the leaf)
+            // leave cell (k, c) through its nearest exit face; while the
+            // neighbour is an empty sibling in the same parent, keep going
+            for (;;) {
+                const int32_t N0 = ((c0 + 1) << (k + kFix)) - Oloc[0];
+                const int32_t N1 = ((c1 + 1) << (k + kFix)) - Oloc[1];
+                const int32_t N2 = ((c2 + 1) << (k + kFix)) - Oloc[2];
+                const bool xy = tltf<FAST>(N0, r.m[0], N1, r.m[1], r.E[1] - r.E[0]);
+                const int32_t Na = xy ? N0 : N1, ma = xy ? r.m[0] : r.m[1], Ea = xy ? r.E[0] : r.E[1];
+                const bool az = tltf<FAST>(Na, ma, N2, r.m[2], r.E[2] - Ea);
+                int ax;
+                if (az) { ax = xy ? 0 : 1; Ne = Na; me = ma; Ee = Ea; }
+                else { ax = 2; Ne = N2; me = r.m[2]; Ee = r.E[2]; }
+                e = ax;
+                int32_t cax;
+                if (ax == 0) cax = ++c0;
+                else if (ax == 1) cax = ++c1;
+                else cax = ++c2;
+                if ((cax << k) >= (1 << R)) return false;  // left the chunk
+                if ((cax & 1) == 0) {
+                    do {
+                        c0 >>= 1; c1 >>= 1; c2 >>= 1;
+                        cax >>= 1;
+                        k++;
+                    } while (k < R && (cax & 1) == 0);
+                    pm8 = k >= n + 2 ? smask[k + 1] : g8;  // popped into a new parent (a node or the leaf)
+                    break;
+                }
+                if ((pm8 >> (((uint32_t)(c0 & 1) | ((uint32_t)(c1 & 1) << 1) | ((uint32_t)(c2 & 1) << 2)) ^ r.mir)) & 1u)
+                    break;  // an occupied sibling
             }
         }
         // occupancy of cell (k, c) in its parent
