@@ -151,3 +151,40 @@ def test_async_streaming_frames_match_oracle_and_settle():
     sc_a.destroy()
     sc_s.destroy()
     ctx.close()
+
+
+def test_async_streaming_under_pool_pressure():
+    """Pools too small for a whole plan: loads that do not fit are deferred and
+    retried after evictions free space; nothing fails, and every frame still
+    equals the oracle for the LODs it used."""
+    from paper_2505_02017_gb300.stream import AsyncStreamer
+    spec = sg.OPEN_8192
+    w = sg.World(spec)
+    ctx = aok.Context(0)
+    sc = aok.Scene(ctx, spec, node_words=512 << 10, leaves=128 << 10, mat_bytes=6 << 20)
+    ast = AsyncStreamer(ctx, w, sc, threads=8)
+    S = orc.OracleScene(w)
+    cams = sg.path_cameras(w, 91, 8, 96, 54, n_waypoints=4, span=6000.0)
+    tau = 1.0 / 30.0  # fine LODs far out: a plan larger than the pools
+    n = sc.grid[0] * sc.grid[1] * sc.grid[2]
+    for i, cam in enumerate(cams):
+        ast.update(cam, tau)
+        ast.wait(60000)
+        ast.update(cam, tau)  # install what finished
+        lod = torch.empty(n, dtype=torch.int8, device="cuda")
+        hit, t = aok.alloc_frame(cam.W, cam.H)
+        aok.select_chunks(ctx, sc, cam, tau, lod_out=lod)
+        aok.cast_selected(ctx, sc, cam, hit, t)
+        torch.cuda.synchronize()
+        used = lod.cpu().numpy().astype(np.int64)
+        res = ast.resident().astype(np.int64)
+        sel = np.where((res >> used) & 1, used, -1).astype(np.int8)
+        if i % 3 == 0:
+            compare(decode(hit, t), S.cast(cam, sel, view_dist=spec.view_dist), max_amb_frac=2e-3)
+    st = ast.stats()
+    assert st["deferred_total"] > 0 and st["failed_total"] == 0 and st["evicted_total"] > 0
+    u = sc.usage()
+    assert u["node_bytes"] <= 2 * 4 * (512 << 10) and u["color_bytes"] <= 6 << 20
+    ast.close()
+    sc.destroy()
+    ctx.close()
