@@ -235,6 +235,10 @@ struct ServeState {
     bool stop = false;
     std::thread loop;
     std::vector<BatchParams> params;  // staging
+    // request frames come from a memory pool of their own that keeps freed
+    // memory mapped (release threshold = the budget), so a burst of arrivals
+    // never waits for the driver to map memory again
+    cudaMemPool_t pool = nullptr;
 };
 
 static void wake_loop(ServeState* S) {
@@ -327,7 +331,7 @@ static void serve_loop(aok_ctx* ctx) {
                 const size_t bytes = request_bytes(sc, t.req.cam);
                 if (charge(ctx, bytes) != AOK_OK) break;  // wait for memory to free up
                 void* mem = nullptr;
-                if (cudaMallocAsync(&mem, bytes, S.streams[slot]) != cudaSuccess) {
+                if (cudaMallocFromPoolAsync(&mem, bytes, S.pool, S.streams[slot]) != cudaSuccess) {
                     cudaGetLastError();
                     uncharge(ctx, bytes);
                     break;
@@ -531,6 +535,17 @@ int aok_serve_start(aok_ctx* ctx, uint32_t max_slots, uint32_t max_batch, uint32
         S->counters.push_back(c);
         S->stream_busy.push_back(0);
     }
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = ctx->device;
+    if (cudaMemPoolCreate(&S->pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        return AOK_E_CUDA;
+    }
+    uint64_t keep = (uint64_t)ctx->budget;
+    cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     cudaDeviceSynchronize();
     ctx->serve = S;
     S->loop = std::thread(serve_loop, ctx);
@@ -566,6 +581,11 @@ int aok_serve_stop(aok_ctx* ctx) {
     for (auto& f : S->inflight) {
         cudaEventDestroy(f.done);
         delete f.flag;
+    }
+    if (S->pool) {
+        cudaDeviceSynchronize();  // frees of the pool's frames are complete
+        cudaMemPoolDestroy(S->pool);
+        S->pool = nullptr;
     }
     // counters were charged: give the bytes back
     const uint32_t ngroups = (S->max_batch + kBatchViews - 1) / kBatchViews;
