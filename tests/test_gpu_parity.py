@@ -258,3 +258,25 @@ def test_read_bandwidth_microbenchmark(ctx):
     with pytest.raises(aok.AokError) as ex:
         aok.read_bandwidth(ctx, budget - used + (1 << 20), 1)
     assert ex.value.status == aok.AOK_E_OOM
+
+
+def test_maximum_world_extent(ctx):
+    """A world 131072 voxels long, the largest extent the 2^-12 fixed-point
+    origin allows (|o| < 2^17): cameras near its far end looking back along it
+    (rays crossing 256 chunk regions) and toward its boundary, every pixel
+    against the oracle; the tile-chunk pipeline renders the same frames."""
+    spec = sg.WorldSpec("long131072", seed=41, wx=131072, wy=1024, wz=1024, chunk=512, n_lods=4, octaves=6,
+                        period0=4096, h_min=32, h_max=300, crust=8, n_boxes=4000, box_min=4, box_max=64,
+                        box_hollow=1)
+    w, sc, S = scene_for(ctx, spec)
+    x, y, z = 130990.25, 500.5, 900.0
+    for fwd in [(-1.0, 0.05, -0.3), (1.0, -0.1, -0.4), (-1.0, 0.0, -0.035)]:
+        cam = sg.make_camera((x, y, z), fwd, 160, 90)
+        g, ref, sel = run(ctx, spec, cam, 1.0)
+        compare(g, ref, max_amb_frac=2e-3)
+        hit, t = aok.alloc_frame(cam.W, cam.H)
+        aok.render_tiles(ctx, sc, cam, 1.0, hit, t)
+        torch.cuda.synchronize()
+        gt = decode(hit, t)
+        assert all((gt[k] == g[k]).all() for k in ("hit", "x", "y", "z", "lod", "mat", "normal"))
+    assert (g["hit"] == 1).sum() > 500 and (g["x"][g["hit"] == 1] < 131072 - 16 * 512).any()
