@@ -502,19 +502,50 @@ def cpu_scaling(threads):
     print(json.dumps({"oracle_rays_per_s": res, "host_threads": threads}), flush=True)
 
 
-def bench_open_async(aok, ctx, threads, n_poses=300, fps=60.0):
+def scene_grid(spec):
+    return (spec.wx // spec.chunk, spec.wy // spec.chunk, spec.wz // spec.chunk)
+
+
+def bench_open_async(aok, ctx, threads, n_poses=300, fps=60.0, from_file=False):
     """The open-world path with asynchronous residency (aok_stream): frames
     are paced at `fps`; each frame installs what the background workers
     loaded since the previous one (coarser LODs first, then nearest), renders
     with stand-in LODs where a load is still missing, and never waits for a
-    build.  The first pose is loaded completely before the path starts."""
+    load.  The first pose is loaded completely before the path starts.  The
+    loaders build chunks from the procedural world, or (from_file) read them
+    from a chunk-blob file holding every (chunk, LOD) the path plans, as the
+    paper streams preprocessed chunks from disk."""
     import torch
-    from paper_2505_02017_gb300.stream import AsyncStreamer
+    from paper_2505_02017_gb300.stream import AsyncStreamer, Streamer
     spec = sg.OPEN_65536
     world = sg.World(spec)
     cams = sg.path_cameras(world, 103, n_poses, 2560, 1440)
+    file_info = {}
+    blobs = None
+    path = None
+    if from_file:
+        t0 = time.perf_counter()
+        plan_scene = aok.Scene(ctx, spec, node_words=1 << 16, leaves=1 << 16, mat_bytes=1 << 16)
+        planner = Streamer(ctx, world, plan_scene, threads)
+        masks = {}
+        for cam in cams:
+            plan = planner.plan(cam, TAU)
+            for c in np.nonzero(plan != 0xFF)[0]:
+                masks[int(c)] = masks.get(int(c), 0) | (1 << int(plan[c]))
+        plan_scene.destroy()
+        chunks = np.array(sorted(masks), np.int64)
+        built = aok.BuiltWorld(world, threads, chunks=chunks,
+                               lod_masks=np.array([masks[int(c)] for c in chunks], np.uint32))
+        t1 = time.perf_counter()
+        path = os.path.join(os.environ.get("TMPDIR", "/tmp"), f"aok_open65536_path_{os.getpid()}.aokb")
+        n = aok.BlobFile.write(path, built, scene_grid(spec), spec.chunk, spec.n_lods)
+        built.close()
+        t2 = time.perf_counter()
+        file_info = {"file_entries": n, "file_mb": round(os.path.getsize(path) / 1e6, 1),
+                     "file_build_s": round(t1 - t0, 2), "file_write_s": round(t2 - t1, 2)}
+        blobs = aok.BlobFile(path)
     scene = aok.Scene(ctx, spec, node_words=512 << 20, leaves=256 << 20, mat_bytes=16 << 30)
-    st = AsyncStreamer(ctx, world, scene, threads)
+    st = AsyncStreamer(ctx, world, scene, threads, blobs=blobs)
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
     st.update(cams[0], TAU, stream=stream)
@@ -522,13 +553,15 @@ def bench_open_async(aok, ctx, threads, n_poses=300, fps=60.0):
     st.update(cams[0], TAU, stream=stream)
     warm_s = time.perf_counter() - t0
     hit, t = aok.alloc_frame(2560, 1440)
-    render_ms, update_ms, missing = [], [], []
+    render_ms, update_ms, missing, shown = [], [], [], []
     period = 1.0 / fps
     for cam in cams:
         f0 = time.perf_counter()
         st.update(cam, TAU, stream=stream)
         update_ms.append(1e3 * (time.perf_counter() - f0))
-        missing.append(st.stats()["missing"])
+        sst = st.stats()
+        missing.append(sst["missing"])
+        shown.append(1.0 - sst["missing"] / max(1, sst["planned"]))
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -542,14 +575,21 @@ def bench_open_async(aok, ctx, threads, n_poses=300, fps=60.0):
     s = st.stats()
     st.close()
     scene.destroy()
+    if blobs is not None:
+        blobs.close()
+        os.remove(path)
     rs, us = sorted(render_ms), sorted(update_ms)
     return {"workload": f"open65536 path (seed 103), {n_poses} poses at 2560x1440 paced at {fps:g} frames/s, "
-                        f"tau = 1 px; {threads} loader threads",
+                        f"tau = 1 px; {threads} loader threads "
+                        + ("reading a chunk-blob file" if from_file else "building chunks procedurally"),
+            **file_info,
             "first_pose_load_s": round(warm_s, 2),
             "render_ms_median": rs[len(rs) // 2], "render_ms_p99": rs[int(len(rs) * 0.99) - 1],
             "update_ms_median": us[len(us) // 2], "update_ms_p99": us[int(len(us) * 0.99) - 1],
             "frames_with_every_planned_lod": sum(m == 0 for m in missing) / len(missing),
-            "max_regions_missing": max(missing), "max_resident_chunks": s["max_resident"],
+            "planned_lods_installed_frac_median": sorted(shown)[len(shown) // 2],
+            "planned_lods_installed_frac_min": min(shown),
+            "regions_missing_median": sorted(missing)[len(missing) // 2], "max_regions_missing": max(missing), "max_resident_chunks": s["max_resident"],
             "max_resident_mb": round(s["max_resident_bytes"] / 1e6, 1), "installed_total": s["installed_total"],
             "evicted_total": s["evicted_total"], "cancelled_total": s["cancelled_total"],
             "failed_total": s["failed_total"], "deferred_total": s["deferred_total"]}
@@ -756,6 +796,7 @@ def main():
     if not args.no_open:
         out["open_world"] = bench_open(aok, ctx, threads)
         out["open_world_async"] = bench_open_async(aok, ctx, threads)
+        out["open_world_async_file"] = bench_open_async(aok, ctx, threads, from_file=True)
     if rank == 0 and world_size == 1 and not args.no_cpu_baseline:
         try:
             out["cpu_baseline"] = cpu_oracle_sample(world, cam)

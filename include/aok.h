@@ -261,13 +261,45 @@ int aok_stream_wait(aok_stream* s, int32_t timeout_ms);
  * [9] requests cancelled, [10] loads that failed (source or validation),
  * [11] loads deferred for lack of pool space, [12] planned regions whose
  * planned LOD was not installed at the last update (0: the frame after it
- * renders exactly the Eq. 1 selection). */
+ * renders exactly the Eq. 1 selection), [13] regions that update planned. */
 int aok_stream_stats(aok_stream* s, uint64_t* stats);
 /* Per chunk region (x fastest) the bitmask of installed LODs (bit l = LOD l). */
 int aok_stream_resident(aok_stream* s, uint8_t* lod_masks);
 /* Stop the workers (running loads finish), free loads not installed and
  * quarantined pool space (waits for their frames).  Installed chunks stay. */
 int aok_stream_destroy(aok_stream* s);
+
+/* ------------------------------------------------------------------ */
+/* Chunk-blob files (the on-disk chunks the paper streams from)       */
+/* ------------------------------------------------------------------ */
+
+/* A file of (chunk, LOD) blobs of one chunking (chunk_res, n_lods, grid),
+ * versioned and checksummed (64-bit FNV-1a over header, index and every
+ * entry).  Written once -- create, add each blob (pointers read during the
+ * call; one blob per (chunk, LOD), AOK_E_INVALID for a duplicate or an
+ * out-of-range chunk), finish (writes index and header, syncs, frees the
+ * handle) -- then opened for reading by any number of threads.  Host only. */
+typedef struct aok_blobfile aok_blobfile;
+int aok_blobfile_create(const char* path, int32_t chunk_res, int32_t n_lods, const int32_t grid[3],
+                        aok_blobfile** out);
+int aok_blobfile_add(aok_blobfile* f, int64_t chunk, uint32_t lod, const aok_chunk_blob* blob);
+int aok_blobfile_finish(aok_blobfile* f);
+/* Open for reading: AOK_E_CORRUPT for a wrong magic or version, a header or
+ * index checksum mismatch, or sizes that do not match the file. */
+int aok_blobfile_open(const char* path, aok_blobfile** out);
+int aok_blobfile_info(const aok_blobfile* f, int32_t* chunk_res, int32_t* n_lods, int32_t grid[3],
+                      uint64_t* n_entries);
+/* Read one blob (chunk index x fastest): *out points into a buffer owned by
+ * *handle until aok_blobfile_release(NULL, *handle).  AOK_E_NOT_RESIDENT if
+ * the file holds no such entry, AOK_E_CORRUPT on a checksum mismatch. */
+int aok_blobfile_read(aok_blobfile* f, int64_t chunk, uint32_t lod, aok_chunk_blob* out, void** handle);
+void aok_blobfile_release(void* user, void* handle);
+/* aok_chunk_source_fn over an open file (user = the aok_blobfile*): a
+ * (chunk, LOD) the file does not hold is an empty chunk; a corrupt entry
+ * fails the load.  Pair with aok_blobfile_release. */
+int aok_blobfile_source(void* user, int32_t cx, int32_t cy, int32_t cz, uint32_t lod, aok_chunk_blob* out,
+                        void** handle);
+int aok_blobfile_close(aok_blobfile* f);
 
 /* Residency plan for one camera, on the host (the streaming side of
  * Sec. 3.4): for every chunk region, the LOD that Eq. 1 selects -- the same

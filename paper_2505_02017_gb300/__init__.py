@@ -87,6 +87,15 @@ def lib() -> ctypes.CDLL:
             "aok_stream_stats": [vp, P(u64)],
             "aok_stream_resident": [vp, vp],
             "aok_stream_destroy": [vp],
+            "aok_blobfile_create": [ctypes.c_char_p, i32, i32, P(i32), P(vp)],
+            "aok_blobfile_add": [vp, ctypes.c_int64, u32, P(ChunkBlob)],
+            "aok_blobfile_finish": [vp],
+            "aok_blobfile_open": [ctypes.c_char_p, P(vp)],
+            "aok_blobfile_info": [vp, P(i32), P(i32), P(i32), P(u64)],
+            "aok_blobfile_read": [vp, ctypes.c_int64, u32, P(ChunkBlob), P(vp)],
+            "aok_blobfile_close": [vp],
+            "aok_blobfile_release": [vp, vp],
+            "aok_blobfile_source": [vp, i32, i32, i32, u32, P(ChunkBlob), P(vp)],
             "aok_scene_usage": [vp, u32, P(u64)],
             "aok_select_chunks": [vp, u32, P(Camera), dbl, vp, vp, P(u32), vp],
             "aok_render": [vp, u32, P(Camera), dbl, P(Frame), vp],
@@ -255,6 +264,69 @@ class BuiltWorld:
     def close(self):
         if self.h:
             blib().aokb_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BlobFile:
+    """A chunk-blob file (aok_blobfile_*): write() stores a BuiltWorld's
+    non-empty (chunk, LOD) blobs; BlobFile(path) opens one for reading."""
+
+    @staticmethod
+    def write(path: str, built: "BuiltWorld", grid, chunk_res: int, n_lods: int) -> int:
+        g = (ctypes.c_int32 * 3)(*grid)
+        h = ctypes.c_void_p()
+        check(lib().aok_blobfile_create(os.fsencode(path), int(chunk_res), int(n_lods), g, ctypes.byref(h)),
+              "aok_blobfile_create")
+        n = 0
+        try:
+            for i in range(len(built)):
+                for lod in range(n_lods):
+                    c, b = built.blob(i, lod)
+                    if b.n_node_words:
+                        check(lib().aok_blobfile_add(h, int(c), int(lod), ctypes.byref(b)), "aok_blobfile_add")
+                        n += 1
+        finally:
+            check(lib().aok_blobfile_finish(h), "aok_blobfile_finish")
+        return n
+
+    def __init__(self, path: str):
+        h = ctypes.c_void_p()
+        check(lib().aok_blobfile_open(os.fsencode(path), ctypes.byref(h)), "aok_blobfile_open")
+        self.h = h
+
+    def info(self):
+        m, nl, n = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_uint64()
+        g = (ctypes.c_int32 * 3)()
+        check(lib().aok_blobfile_info(self.h, ctypes.byref(m), ctypes.byref(nl), g, ctypes.byref(n)),
+              "aok_blobfile_info")
+        return {"chunk_res": m.value, "n_lods": nl.value, "grid": tuple(g), "entries": n.value}
+
+    def read(self, chunk: int, lod: int) -> dict:
+        """One entry as numpy copies (nodes, leaves, mats, root, aabb)."""
+        b = ChunkBlob()
+        hd = ctypes.c_void_p()
+        check(lib().aok_blobfile_read(self.h, int(chunk), int(lod), ctypes.byref(b), ctypes.byref(hd)),
+              "aok_blobfile_read")
+        try:
+            def arr(ptr, n, dt):
+                return np.ctypeslib.as_array(ctypes.cast(ptr, ctypes.POINTER(dt)), (n,)).copy() if n else \
+                    np.zeros(0, np.dtype(dt))
+            return {"nodes": arr(b.nodes, b.n_node_words, ctypes.c_uint32),
+                    "leaves": arr(b.leaves, b.n_leaves, ctypes.c_uint64),
+                    "mats": arr(b.mats, b.n_mats, ctypes.c_uint8), "root": int(b.root),
+                    "aabb": (tuple(b.aabb_lo), tuple(b.aabb_hi))}
+        finally:
+            lib().aok_blobfile_release(None, hd)
+
+    def close(self):
+        if self.h:
+            lib().aok_blobfile_close(self.h)
             self.h = None
 
     def __del__(self):

@@ -80,6 +80,7 @@ struct aok_stream {
     uint64_t res_count = 0, res_bytes = 0, max_count = 0, max_bytes = 0;
     uint64_t n_installed = 0, n_evicted = 0, n_cancelled = 0, n_failed = 0, n_deferred = 0;
     uint64_t n_missing = 0;  // planned regions whose planned LOD was not installed at the last update
+    uint64_t n_planned = 0;  // regions the last update planned
 
     void worker();
 };
@@ -261,8 +262,10 @@ int aok_stream_update(aok_stream* s, const aok_camera* cam, double tau, void* st
         }
         s->deferred.clear();
         s->n_missing = 0;
+        s->n_planned = 0;
         for (int64_t c = 0; c < s->n; c++) {
             const uint8_t w = s->want[c];
+            if (w != 0xFF) s->n_planned++;
             if (w != 0xFF && !((s->resident[c] >> w) & 1u)) s->n_missing++;
             if (w == 0xFF || ((s->resident[c] | s->pending[c]) >> w) & 1u) continue;
             const int cx = (int)(c % s->gx), cy = (int)((c / s->gx) % s->gy), cz = (int)(c / ((int64_t)s->gx * s->gy));
@@ -331,9 +334,9 @@ int aok_stream_wait(aok_stream* s, int32_t timeout_ms) {
 int aok_stream_stats(aok_stream* s, uint64_t* st) {
     if (!s || !st) return AOK_E_INVALID;
     std::lock_guard<std::mutex> lk(s->mu);
-    const uint64_t v[13] = {s->res_count, s->res_bytes, s->max_count, s->max_bytes, (uint64_t)s->heap.size(),
+    const uint64_t v[14] = {s->res_count, s->res_bytes, s->max_count, s->max_bytes, (uint64_t)s->heap.size(),
                             (uint64_t)s->running, (uint64_t)s->loaded.size(), s->n_installed, s->n_evicted,
-                            s->n_cancelled, s->n_failed, s->n_deferred, s->n_missing};
+                            s->n_cancelled, s->n_failed, s->n_deferred, s->n_missing, s->n_planned};
     std::memcpy(st, v, sizeof(v));
     return AOK_OK;
 }

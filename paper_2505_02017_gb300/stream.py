@@ -82,22 +82,32 @@ class Streamer:
 
 STREAM_STATS = ("resident", "resident_bytes", "max_resident", "max_resident_bytes", "queued", "running",
                 "loaded_not_installed", "installed_total", "evicted_total", "cancelled_total", "failed_total",
-                "deferred_total", "missing")
+                "deferred_total", "missing", "planned")
 
 
 class AsyncStreamer:
-    """Background residency for `scene` (aok_stream_*), loading from the native builder."""
+    """Background residency for `scene` (aok_stream_*), loading from the
+    native builder over `world`, or from a chunk-blob file (`blobs`, an open
+    BlobFile) -- the paper's disk-resident chunks."""
 
-    def __init__(self, ctx, world, scene: Scene, threads: int | None = None):
+    def __init__(self, ctx, world, scene: Scene, threads: int | None = None, blobs=None):
         self.ctx, self.world, self.scene = ctx, world, scene
-        spec = world.spec
-        self._src = blib().aokb_source_create(world.handle, spec.chunk, spec.n_lods)
-        if not self._src:
-            raise ValueError("bad chunking for the builder")
-        build = ctypes.cast(blib().aokb_source_build, ctypes.c_void_p)
-        release = ctypes.cast(blib().aokb_source_release, ctypes.c_void_p)
+        self._src = None
+        self._blobs = blobs
+        if blobs is not None:
+            build = ctypes.cast(lib().aok_blobfile_source, ctypes.c_void_p)
+            release = ctypes.cast(lib().aok_blobfile_release, ctypes.c_void_p)
+            user = blobs.h
+        else:
+            spec = world.spec
+            self._src = blib().aokb_source_create(world.handle, spec.chunk, spec.n_lods)
+            if not self._src:
+                raise ValueError("bad chunking for the builder")
+            build = ctypes.cast(blib().aokb_source_build, ctypes.c_void_p)
+            release = ctypes.cast(blib().aokb_source_release, ctypes.c_void_p)
+            user = self._src
         h = ctypes.c_void_p()
-        check(lib().aok_stream_create(ctx.h, scene.id, build, release, self._src, int(threads or os.cpu_count() or 1),
+        check(lib().aok_stream_create(ctx.h, scene.id, build, release, user, int(threads or os.cpu_count() or 1),
                                       ctypes.byref(h)), "aok_stream_create")
         self.h = h
         gx, gy, gz = scene.grid
@@ -112,7 +122,7 @@ class AsyncStreamer:
         return int(lib().aok_stream_wait(self.h, int(timeout_ms)))
 
     def stats(self) -> dict:
-        a = (ctypes.c_uint64 * 13)()
+        a = (ctypes.c_uint64 * 14)()
         check(lib().aok_stream_stats(self.h, a), "aok_stream_stats")
         return dict(zip(STREAM_STATS, (int(v) for v in a)))
 

@@ -188,3 +188,50 @@ def test_async_streaming_under_pool_pressure():
     ast.close()
     sc.destroy()
     ctx.close()
+
+
+def test_async_streaming_from_blob_file(tmp_path):
+    """The paper's disk-resident chunks: the (chunk, LOD)s a path needs are
+    written to a chunk-blob file; the asynchronous loader reads them from it;
+    once settled, every pose renders exactly as with the synchronous,
+    procedurally built residency."""
+    from paper_2505_02017_gb300.stream import AsyncStreamer
+    spec = sg.OPEN_8192
+    w = sg.World(spec)
+    ctx = aok.Context(0)
+    sc_f = aok.Scene(ctx, spec, node_words=64 << 20, leaves=16 << 20, mat_bytes=1 << 30)
+    sc_s = aok.Scene(ctx, spec, node_words=64 << 20, leaves=16 << 20, mat_bytes=1 << 30)
+    sst = Streamer(ctx, w, sc_s, threads=8)
+    cams = sg.path_cameras(w, 77, 5, 160, 90, n_waypoints=3, span=3000.0)
+    tau = 1.0 / 3.0
+    masks = {}
+    for cam in cams:
+        plan = sst.plan(cam, tau)
+        for c in np.nonzero(plan != 0xFF)[0]:
+            masks[int(c)] = masks.get(int(c), 0) | (1 << int(plan[c]))
+    chunks = np.array(sorted(masks), np.int64)
+    bw = aok.BuiltWorld(w, threads=8, chunks=chunks, lod_masks=np.array([masks[c] for c in chunks], np.uint32))
+    path = str(tmp_path / "open8192_path.aokb")
+    n = aok.BlobFile.write(path, bw, sc_f.grid, spec.chunk, spec.n_lods)
+    bw.close()
+    assert n > 0
+    blobs = aok.BlobFile(path)
+    ast = AsyncStreamer(ctx, None, sc_f, threads=8, blobs=blobs)
+    for cam in cams:
+        ast.update(cam, tau)
+        assert ast.wait(60000) == aok.AOK_OK
+        ast.update(cam, tau)
+        assert ast.stats()["missing"] == 0
+        sst.update(cam, tau)
+        fa, fs = aok.alloc_frame(cam.W, cam.H), aok.alloc_frame(cam.W, cam.H)
+        aok.render(ctx, sc_f, cam, tau, *fa)
+        aok.render(ctx, sc_s, cam, tau, *fs)
+        torch.cuda.synchronize()
+        assert torch.equal(fa[0], fs[0]) and torch.equal(fa[1].view(torch.int32), fs[1].view(torch.int32))
+    st = ast.stats()
+    assert st["failed_total"] == 0 and st["installed_total"] > 0
+    ast.close()
+    blobs.close()
+    sc_f.destroy()
+    sc_s.destroy()
+    ctx.close()
