@@ -490,6 +490,17 @@ int aok_render_noalloc(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, doub
  * the algorithmic bytes of a frame. */
 int aok_render_counted(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double lod_threshold_px,
                        const aok_frame* frame, uint32_t* counts, void* stream);
+/* Checked casting (no counterpart in the paper; the stand-in for a device
+ * memory checker): with on = 1, aok_render / aok_cast_selected of this
+ * context test every node, leaf and colour index against the scene's pool
+ * sizes before loading it; an index out of range ends that chunk's traversal
+ * as a miss and ORs a code into the context's error word (1 node word, 2
+ * leaf, 4 colour).  Slower; batches, serving and the tile pipeline are not
+ * checked. */
+int aok_set_checked(aok_ctx* ctx, int on);
+/* Read and clear the error word (synchronises the device); 0 = no index was
+ * ever out of range. */
+int aok_checked_errors(aok_ctx* ctx, uint32_t* errors);
 /* Write every pixel's FP32 ray direction (3 floats per pixel) to the device
  * buffer dirs, as the casting kernel computes it. */
 int aok_ray_dirs(aok_ctx* ctx, const aok_camera* cam, float* dirs, void* stream);

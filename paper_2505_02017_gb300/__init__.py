@@ -119,6 +119,8 @@ def lib() -> ctypes.CDLL:
             "aok_set_tile": [vp, u32],
             "aok_set_batch_kernel": [vp, ctypes.c_int],
             "aok_set_single_view_kernel": [vp, ctypes.c_int],
+            "aok_set_checked": [vp, ctypes.c_int],
+            "aok_checked_errors": [vp, P(u32)],
             "aok_serve_start": [vp, u32, u32, u32],
             "aok_serve_stop": [vp],
             "aok_serve_submit": [vp, P(Request), P(u64)],
@@ -412,6 +414,18 @@ def render(ctx: Context, scene: Scene, cam, tau: float, hit, t, stream=None):
     c = to_camera(cam)
     return check(lib().aok_render(ctx.h, scene.id, ctypes.byref(c), float(tau), ctypes.byref(f),
                                   _stream_handle(stream)), "aok_render")
+
+
+def set_checked(ctx: Context, on: bool):
+    """Checked casting: every pool index tested before its load (aok_set_checked)."""
+    return check(lib().aok_set_checked(ctx.h, 1 if on else 0), "aok_set_checked")
+
+
+def checked_errors(ctx: Context) -> int:
+    """Read and clear the checked-casting error word (aok_checked_errors)."""
+    e = ctypes.c_uint32()
+    check(lib().aok_checked_errors(ctx.h, ctypes.byref(e)), "aok_checked_errors")
+    return e.value
 
 
 def render_tiles(ctx: Context, scene: Scene, cam, tau: float, hit, t, stream=None):

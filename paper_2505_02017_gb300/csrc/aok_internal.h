@@ -41,6 +41,15 @@ struct SceneDev {
     float view_dist;
 };
 
+// Checked traversal (no counterpart in the paper; the stand-in for a memory
+// checker): pool sizes every node, leaf and colour index is checked against,
+// and the word the kernels OR an error code into instead of reading out of
+// bounds (1: node word, 2: leaf, 4: colour byte).
+struct CheckDev {
+    uint64_t n_nodes, n_leaves, n_mats;
+    uint32_t* err;
+};
+
 // Camera as the kernels consume it.
 struct CamDev {
     float R[9];
@@ -119,7 +128,7 @@ extern "C" {
 int aokk_select(const aok::SceneDev* s, const aok::CamDev* c, aok::ChunkRef* frame, int8_t* lod_out,
                 uint8_t* vis_out, uint32_t* n_visible, void* stream);
 int aokk_cast(const aok::SceneDev* s, const aok::CamDev* c, const aok::ChunkRef* frame, uint4* hit, float* t,
-              uint32_t* counts, void* stream);
+              uint32_t* counts, void* stream, const aok::CheckDev* ck);
 int aokk_ray_dirs(const aok::CamDev* c, float* dirs, void* stream);
 int aokk_tiles_frame(const aok::SceneDev* S, const aok::CamDev* C, const aok::ChunkRef* frame, const aok::TileDev* T,
                      uint4* hit, float* t, int sms, void* stream);

@@ -115,6 +115,17 @@ __global__ void __launch_bounds__(128) cast_kernel(SceneDev S, CamDev C, const C
     trace_pixel<COUNT>(S, C, frame, px, py, out_hit, out_t, counts, (size_t)py * C.W + px);
 }
 
+// The same casting with every pool index checked (CheckDev).
+__global__ void __launch_bounds__(128) cast_kernel_checked(SceneDev S, CamDev C, const ChunkRef* __restrict__ frame,
+                                                           uint4* __restrict__ out_hit, float* __restrict__ out_t,
+                                                           CheckDev ck) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int px = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
+    const int py = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
+    if (px >= C.W || py >= C.H) return;
+    trace_pixel<false, true>(S, C, frame, px, py, out_hit, out_t, nullptr, (size_t)py * C.W + px, &ck);
+}
+
 // Persistent casting over a list of views (P.queue[0] = next tile, P.queue[1]
 // = finished CTAs; both zero at launch).  Each warp pulls `per_fetch`
 // consecutive warp tiles (2^tile_w_log x 32/2^tile_w_log pixels of one view)
@@ -218,9 +229,11 @@ int aokk_select(const SceneDev* s, const CamDev* c, ChunkRef* frame, int8_t* lod
 }
 
 int aokk_cast(const SceneDev* s, const CamDev* c, const ChunkRef* frame, uint4* hit, float* t, uint32_t* counts,
-              void* stream) {
+              void* stream, const CheckDev* ck) {
     dim3 grid((c->W + 15) / 16, (c->H + 7) / 8);
-    if (counts)
+    if (ck && !counts)
+        cast_kernel_checked<<<grid, 128, 0, (cudaStream_t)stream>>>(*s, *c, frame, hit, t, *ck);
+    else if (counts)
         cast_kernel<true><<<grid, 128, 0, (cudaStream_t)stream>>>(*s, *c, frame, hit, t, counts);
     else
         cast_kernel<false><<<grid, 128, 0, (cudaStream_t)stream>>>(*s, *c, frame, hit, t, nullptr);

@@ -323,6 +323,7 @@ int aok_create(aok_ctx** out, int device, size_t budget) {
     }
     if (dev_alloc(ctx, (void**)&ctx->d_counter, sizeof(uint32_t) * 16) != AOK_OK ||
         dev_alloc(ctx, (void**)&ctx->d_single_queue, 2 * sizeof(unsigned long long)) != AOK_OK ||
+        cudaMemset(ctx->d_counter, 0, sizeof(uint32_t) * 16) != cudaSuccess ||
         cudaMemset(ctx->d_single_queue, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) {
         delete ctx;
         return AOK_E_CUDA;
@@ -788,6 +789,16 @@ int aok_plan_residency(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, doub
     return AOK_OK;
 }
 
+// Pool sizes and the error word of a checked cast (null when checking is off).
+static const CheckDev* check_dev(aok_ctx* ctx, const Scene* sc, CheckDev* ck) {
+    if (!ctx->checked) return nullptr;
+    ck->n_nodes = sc->nodes.cap;
+    ck->n_leaves = sc->leaves.cap;
+    ck->n_mats = sc->mats.cap;
+    ck->err = ctx->d_counter + 8;
+    return ck;
+}
+
 static int render_impl(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double tau, const aok_frame* frame,
                        uint32_t* counts, void* stream) {
     if (!ctx || !frame || !frame->hit || !frame->t) return AOK_E_INVALID;
@@ -803,7 +814,9 @@ static int render_impl(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, doub
         st = render_persistent(ctx, sc, cd, frame, stream, true);
     } else {
         st = aokk_select(&sd, &cd, sc->d_frame, nullptr, nullptr, nullptr, stream);
-        if (!st) st = aokk_cast(&sd, &cd, sc->d_frame, (uint4*)frame->hit, frame->t, counts, stream);
+        CheckDev ck;
+        if (!st) st = aokk_cast(&sd, &cd, sc->d_frame, (uint4*)frame->hit, frame->t, counts, stream,
+                                check_dev(ctx, sc, &ck));
     }
     if (st) return cuda_status(ctx, cudaGetLastError());
     return AOK_OK;
@@ -847,7 +860,10 @@ int aok_cast_selected(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, const
     cudaSetDevice(ctx->device);
     SceneDev sd = scene_dev(sc);
     if (ctx->single_persistent) st = render_persistent(ctx, sc, cd, frame, stream, false);
-    else st = aokk_cast(&sd, &cd, sc->d_frame, (uint4*)frame->hit, frame->t, nullptr, stream);
+    else {
+        CheckDev ck;
+        st = aokk_cast(&sd, &cd, sc->d_frame, (uint4*)frame->hit, frame->t, nullptr, stream, check_dev(ctx, sc, &ck));
+    }
     return st ? cuda_status(ctx, cudaGetLastError()) : AOK_OK;
 }
 
@@ -953,6 +969,21 @@ int aok_tiles_forget(aok_ctx* ctx) {
     if (!ctx) return AOK_E_INVALID;
     ctx->tiles.scene = 0xFFFFFFFFu;
     return AOK_OK;
+}
+
+int aok_set_checked(aok_ctx* ctx, int on) {
+    if (!ctx || on < 0 || on > 1) return AOK_E_INVALID;
+    ctx->checked = on;
+    return AOK_OK;
+}
+
+int aok_checked_errors(aok_ctx* ctx, uint32_t* errors) {
+    if (!ctx || !errors) return AOK_E_INVALID;
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(errors, ctx->d_counter + 8, sizeof(uint32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_counter + 8, 0, sizeof(uint32_t));
+    return e == cudaSuccess ? AOK_OK : cuda_status(ctx, e);
 }
 
 int aok_set_single_view_kernel(aok_ctx* ctx, int persistent) {

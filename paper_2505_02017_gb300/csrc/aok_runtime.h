@@ -118,6 +118,7 @@ struct aok_ctx {
     aok::ServeState* serve = nullptr;
     aok::TileState tiles;
     aok::HostPipe pipe;
+    int checked = 0;  // single-view casts check every pool index (error word: d_counter[8])
     std::mutex upload_mu;  // the staging buffer and the copy stream: one upload at a time
 };
 

@@ -126,9 +126,22 @@ struct Counters {
 
 // Returns true on a hit inside this chunk.  (e, Ne): entry plane into the chunk
 // (e = 3: the origin lies inside the chunk).  Oloc: mirrored local origin numerators.
-template <bool FAST, bool COUNT>
+// In a checked build (CHECK) every pool index is tested before its load; an
+// index out of range ORs its code into *ck.err and ends the chunk's traversal
+// as a miss.
+template <bool CHECK>
+__device__ __forceinline__ bool out_of(uint64_t i, uint64_t n, const CheckDev* ck, uint32_t code) {
+    if (CHECK && i >= n) {
+        atomicOr(ck->err, code);
+        return true;
+    }
+    return false;
+}
+
+template <bool FAST, bool COUNT, bool CHECK = false>
 __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& ref, const RayState& r,
-                                            const int32_t Oloc[3], int e, int32_t Ne, HitRec& hit, Counters& cnt) {
+                                            const int32_t Oloc[3], int e, int32_t Ne, HitRec& hit, Counters& cnt,
+                                            const CheckDev* ck = nullptr) {
     const uint32_t* __restrict__ nodes = S.nodes;
     const int R = S.mlog;
     const int n = (int)ref.lod;
@@ -161,11 +174,26 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
                     const int sh = j - 1 - n;
                     const int oct = ((u0 >> sh) & 1) | (((u1 >> sh) & 1) << 1) | (((u2 >> sh) & 1) << 2);
                     const int rk = __popc(smask[j] & ((1u << oct) - 1u));
+                    if (out_of<CHECK>((uint64_t)sidx[j] + 3 + 2 * rk, ck ? ck->n_nodes : 0, ck, 1u)) return false;
                     idx += nodes[sidx[j] + 3 + 2 * rk];
                     if (COUNT) cnt.rbytes += rk * ((j - 1 == n + 2) ? 8u : 4u);
                 }
                 const int bit = (u0 & 3) + 4 * (u1 & 3) + 16 * (u2 & 3);
                 idx += (uint32_t)__popcll(lmu & ((1ull << bit) - 1ull));
+                if (CHECK) {
+                    // raw array: the entry; blocks: the whole block structure
+                    const uint64_t end = ref.nblocks == 0
+                                             ? ref.mat_base + idx
+                                             : ref.mat_base + 4ull * (1 + ((uint64_t)idx >> 7) + 1) - 1;
+                    if (out_of<CHECK>(end, ck->n_mats, ck, 4u)) return false;
+                    if (ref.nblocks) {
+                        const uint32_t nt = *reinterpret_cast<const uint32_t*>(S.mats + ref.mat_base);
+                        if (out_of<CHECK>(ref.mat_base + 4ull * (1 + nt + ref.nblocks) + ref.nblocks - 1, ck->n_mats,
+                                          ck, 4u) ||
+                            out_of<CHECK>(idx >> 7, nt, ck, 4u))
+                            return false;
+                    }
+                }
                 hit.mat = ref.nblocks == 0 ? S.mats[ref.mat_base + idx]
                                            : block_colour(S.mats + ref.mat_base, ref.nblocks, idx);
                 if (COUNT) cnt.rbytes += 1;
@@ -177,14 +205,18 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
                     idx = ref.root;
                 } else {
                     const uint32_t oct = ((uint32_t)(c0 & 1) | ((uint32_t)(c1 & 1) << 1) | ((uint32_t)(c2 & 1) << 2)) ^ r.mir;
-                    idx = nodes[sidx[k + 1] + 2 + 2 * __popc(smask[k + 1] & ((1u << oct) - 1u))];
+                    const uint64_t at = (uint64_t)sidx[k + 1] + 2 + 2 * __popc(smask[k + 1] & ((1u << oct) - 1u));
+                    if (out_of<CHECK>(at, ck ? ck->n_nodes : 0, ck, 1u)) return false;
+                    idx = nodes[at];
                 }
                 if (k >= n + 3) {
+                    if (out_of<CHECK>((uint64_t)idx + 1, ck ? ck->n_nodes : 0, ck, 1u)) return false;
                     pm8 = nodes[idx] & 0xFFu;
                     sidx[k] = idx;
                     smask[k] = pm8;
                     if (COUNT) cnt.v_int++;
                 } else {
+                    if (out_of<CHECK>(idx, ck ? ck->n_leaves : 0, ck, 2u)) return false;
                     lmu = S.leaves[idx];
                     uint64_t t = lmu | (lmu >> 1);
                     t |= t >> 4;
@@ -315,10 +347,10 @@ __device__ __forceinline__ bool make_ray(const CamDev& C, int px, int py, RaySta
 // ---------------------------------------------------------------------------
 // one pixel: world-grid chunk march + per-chunk DAG traversal
 // ---------------------------------------------------------------------------
-template <bool FAST, bool COUNT>
+template <bool FAST, bool COUNT, bool CHECK = false>
 __device__ __forceinline__ void trace_pixel_t(const SceneDev& S, const CamDev& C, const ChunkRef* __restrict__ frame,
                                             const RayState& r, uint4* __restrict__ out_hit, float* __restrict__ out_t,
-                                            uint32_t* __restrict__ counts, size_t pix) {
+                                            uint32_t* __restrict__ counts, size_t pix, const CheckDev* ck = nullptr) {
     int32_t Ow[3], Wfix[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
@@ -403,7 +435,7 @@ __device__ __forceinline__ void trace_pixel_t(const SceneDev& S, const CamDev& C
                 int32_t Oloc[3];
 #pragma unroll
                 for (int a = 0; a < 3; a++) Oloc[a] = Ow[a] - (cc[a] << cs);
-                if (trace_chunk<FAST, COUNT>(S, ref, r, Oloc, e, Ne, hit, cnt)) {
+                if (trace_chunk<FAST, COUNT, CHECK>(S, ref, r, Oloc, e, Ne, hit, cnt, ck)) {
                     found = emit_hit(S, r, ref, u, hit, dn, out_hit, out_t, pix);
                     break;
                 }
@@ -430,13 +462,13 @@ __device__ __forceinline__ void trace_pixel_t(const SceneDev& S, const CamDev& C
     }
 }
 
-template <bool COUNT>
+template <bool COUNT, bool CHECK = false>
 __device__ __forceinline__ void trace_pixel(const SceneDev& S, const CamDev& C, const ChunkRef* __restrict__ frame,
                                             int px, int py, uint4* __restrict__ out_hit, float* __restrict__ out_t,
-                                            uint32_t* __restrict__ counts, size_t pix) {
+                                            uint32_t* __restrict__ counts, size_t pix, const CheckDev* ck = nullptr) {
     RayState r;
-    if (make_ray(C, px, py, r)) trace_pixel_t<true, COUNT>(S, C, frame, r, out_hit, out_t, counts, pix);
-    else trace_pixel_t<false, COUNT>(S, C, frame, r, out_hit, out_t, counts, pix);
+    if (make_ray(C, px, py, r)) trace_pixel_t<true, COUNT, CHECK>(S, C, frame, r, out_hit, out_t, counts, pix, ck);
+    else trace_pixel_t<false, COUNT, CHECK>(S, C, frame, r, out_hit, out_t, counts, pix, ck);
 }
 
 }  // namespace aok

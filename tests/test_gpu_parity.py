@@ -280,3 +280,43 @@ def test_maximum_world_extent(ctx):
         gt = decode(hit, t)
         assert all((gt[k] == g[k]).all() for k in ("hit", "x", "y", "z", "lod", "mat", "normal"))
     assert (g["hit"] == 1).sum() > 500 and (g["x"][g["hit"] == 1] < 131072 - 16 * 512).any()
+
+
+def test_checked_casting_stays_in_bounds(ctx):
+    """Checked casting (every node, leaf and colour index tested against the
+    pool sizes before its load): on small worlds, the 4096^3 benchmark frame
+    and a colour-block scene, no index is ever out of range and the frames
+    equal the unchecked ones."""
+    cases = [(CASES[i][0], CASES[i][1], CASES[i][2]) for i in (0, 2, 4, 5)]
+    cases.append((sg.CITY_4096, lambda w: sg.ground_camera(w, 102, 640, 360), 1.0))
+    cases.append((sg.CITY_4096, lambda w: sg.ground_camera(w, 8, 320, 180, z_lo=600, z_hi=900,
+                                                           pitch=(-20.0, -8.0)), 1.0 / 3.0))
+    assert aok.checked_errors(ctx) == 0
+    for spec, camf, tau in cases:
+        w, sc, _ = scene_for(ctx, spec)
+        cam = camf(w)
+        ref = aok.alloc_frame(cam.W, cam.H)
+        aok.render(ctx, sc, cam, tau, *ref)
+        aok.set_checked(ctx, True)
+        try:
+            out = aok.alloc_frame(cam.W, cam.H)
+            aok.render(ctx, sc, cam, tau, *out)
+            torch.cuda.synchronize()
+        finally:
+            aok.set_checked(ctx, False)
+        assert aok.checked_errors(ctx) == 0, spec.name
+        assert torch.equal(ref[0], out[0]) and torch.equal(ref[1].view(torch.int32), out[1].view(torch.int32))
+    # colour blocks: the block structure's bounds are checked too
+    from worlds import MED64_LAYERED
+    wl = sg.World(MED64_LAYERED)
+    scb = aok.Scene.from_world(ctx, wl, threads=8, color_tol=0.0)
+    cam = sg.ground_camera(wl, 4, 160, 90, z_lo=4, z_hi=40)
+    ref = aok.alloc_frame(cam.W, cam.H)
+    aok.render(ctx, scb, cam, 2.0, *ref)
+    aok.set_checked(ctx, True)
+    out = aok.alloc_frame(cam.W, cam.H)
+    aok.render(ctx, scb, cam, 2.0, *out)
+    aok.set_checked(ctx, False)
+    assert aok.checked_errors(ctx) == 0
+    assert torch.equal(ref[0], out[0])
+    scb.destroy()
