@@ -142,8 +142,12 @@ def dist_env():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
-def cpu_oracle_sample(world, cam, budget_s=20.0, max_pixels=400_000):
-    """Oracle rays/s on a stratified pixel sample of the same frame (all host cores)."""
+def cpu_oracle_sample(world, cam, budget_s=20.0, max_pixels=400_000, gpu_frame=None):
+    """Oracle rays/s on a stratified pixel sample of the same frame (all host
+    cores).  With the GPU's frame (hit int32 [H, W, 4], t float32 [H, W] on
+    the host), also the parity of that sample: pixels the oracle flags
+    ambiguous, and non-ambiguous pixels whose voxel, LOD, material, normal or
+    hit flag differ or whose distance is off by more than 1e-5 relative."""
     import oracle as orc
     S = orc.OracleScene(world)
     sel = S.select(cam, TAU)
@@ -163,12 +167,28 @@ def cpu_oracle_sample(world, cam, budget_s=20.0, max_pixels=400_000):
     idx = np.arange(0, n, step)
     pix = np.stack([idx % W, idx // W], 1)
     t0 = time.perf_counter()
-    S.cast(cam, sel, pix)
+    ref = S.cast(cam, sel, pix)
     dt = time.perf_counter() - t0
     cores = orc.default_threads()
-    return {"value": len(idx) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"every {step}th pixel of the frame ({len(idx)} rays), FP64 oracle on {cores} threads; "
-                      f"oracle DAG build for the frame's LOD selection took {prep:.1f} s and is not timed"}
+    out = {"value": len(idx) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"every {step}th pixel of the frame ({len(idx)} rays), FP64 oracle on {cores} threads; "
+                     f"oracle DAG build for the frame's LOD selection took {prep:.1f} s and is not timed"}
+    if gpu_frame is not None:
+        h = np.asarray(gpu_frame[0]).reshape(-1, 4).view(np.uint32)[idx]
+        t = np.asarray(gpu_frame[1]).reshape(-1).astype(np.float64)[idx]
+        meta = h[:, 3]
+        ok = ref["amb"] == 0
+        bad = ((((meta >> 19) & 1).astype(np.int32) != ref["hit"]) |
+               (h[:, 0].view(np.int32) != ref["x"]) | (h[:, 1].view(np.int32) != ref["y"]) |
+               (h[:, 2].view(np.int32) != ref["z"]) | ((meta & 0xFF).astype(np.int32) != ref["lod"]) |
+               (((meta >> 8) & 0xFF).astype(np.int32) != ref["mat"]) |
+               (((meta >> 16) & 7).astype(np.int32) != ref["normal"]))
+        hit = ref["hit"] == 1
+        far = np.zeros(len(idx), bool)
+        far[hit] = np.abs(t[hit] - ref["dist"][hit]) > 1e-5 * np.maximum(ref["dist"][hit], 1e-30)
+        out["parity"] = {"pixels": int(len(idx)), "ambiguous": int((~ok).sum()),
+                         "mismatched_non_ambiguous": int(((bad | far) & ok).sum())}
+    return out
 
 
 def time_events(fn, reps, flush, stream):
@@ -687,6 +707,7 @@ def main():
     c = counts.view(-1, 3).to(torch.int64).sum(0).tolist()
     algo_bytes = 8 * c[0] + 8 * c[1] + c[2] + 20 * W * H  # node visits, leaf visits, resolve, output
     del counts
+    n_visible = aok.select_chunks(ctx, scene, cam, TAU, count=True)
     meta = hit.view(-1, 4)[:, 3]
     is_hit = ((meta >> 19) & 1) == 1
     hit_frac = float(is_hit.float().mean().item())
@@ -767,7 +788,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "i64/f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "rays_per_step": rays, "parallelism": f"replicas x{world_size}",
                    "l2": "flushed between steps (512 MB write)", "scene_build_s": round(t_build, 2),
-                   "scene_upload_s": round(t_upload, 2), "hit_frac": hit_frac, "hit_lod_hist": lod_hist,
+                   "scene_upload_s": round(t_upload, 2), "hit_frac": hit_frac, "hit_lod_hist": lod_hist, "visible_chunks": n_visible,
                    "scene_bytes": {"nodes": built.node_words * 4, "leaves": built.leaves * 8,
                                    "mats": built.mat_bytes}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
@@ -799,7 +820,9 @@ def main():
         out["open_world_async_file"] = bench_open_async(aok, ctx, threads, from_file=True)
     if rank == 0 and world_size == 1 and not args.no_cpu_baseline:
         try:
-            out["cpu_baseline"] = cpu_oracle_sample(world, cam)
+            aok.render(ctx, scene, cam, TAU, hit, t)
+            torch.cuda.synchronize()
+            out["cpu_baseline"] = cpu_oracle_sample(world, cam, gpu_frame=(hit.cpu().numpy(), t.cpu().numpy()))
         except Exception as ex:  # pragma: no cover
             out["cpu_baseline"] = {"error": str(ex)}
     if rank == 0:
