@@ -394,7 +394,8 @@ def bench_open(aok, ctx, threads, n_poses=300):
     """Open world 65536x65536x1024 (128x128x2 chunks of 512^3, 4 LODs), view
     distance 16384: along a 300-pose path at 2560x1440, only the (chunk, LOD)
     pairs within the view distance are resident (streamed between frames);
-    per frame the selection (a1+a2) and the cast (a4-a7) are timed."""
+    per frame the render (selection a1+a2 and cast a4-a7 in one call) is
+    timed, and the selection alone once more after it."""
     import torch
     from paper_2505_02017_gb300.stream import Streamer
     spec = sg.OPEN_65536
@@ -408,23 +409,30 @@ def bench_open(aok, ctx, threads, n_poses=300):
     sel_ms, cast_ms, tiles_ms, host = [], [], [], []
     tiles_same = True
     aok.tiles_forget(ctx)
+    # each timed region starts behind a short spin kernel, so that the host's
+    # launch latency after a synchronisation is not counted as frame time
+    gate = 200_000  # cycles, ~0.1 ms
+    frame = []
     for i, cam in enumerate(cams):
         host.append(st.update(cam, TAU))
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        torch.cuda._sleep(gate)
         e[0].record(stream)
-        aok.select_chunks(ctx, scene, cam, TAU, stream=stream)
+        aok.render(ctx, scene, cam, TAU, hit, t, stream=stream)  # selection + cast, one call
         e[1].record(stream)
-        aok.cast_selected(ctx, scene, cam, hit, t, stream=stream)
-        e[2].record(stream)
         # the paper's tile-chunk pipeline on the same frame (Hi-Z history: the previous pose)
         aok.render_tiles(ctx, scene, cam, TAU, hit2, t2, stream=stream)
+        e[2].record(stream)
+        torch.cuda._sleep(gate)
         e[3].record(stream)
-        e[3].synchronize()
-        sel_ms.append(e[0].elapsed_time(e[1]))
-        cast_ms.append(e[1].elapsed_time(e[2]))
-        tiles_ms.append(e[2].elapsed_time(e[3]))
+        aok.select_chunks(ctx, scene, cam, TAU, stream=stream)  # the selection alone
+        e[4].record(stream)
+        e[4].synchronize()
+        frame.append(e[0].elapsed_time(e[1]))
+        tiles_ms.append(e[1].elapsed_time(e[2]))
+        sel_ms.append(e[3].elapsed_time(e[4]))
         tiles_same &= torch.equal(hit, hit2) and torch.equal(t.view(torch.int32), t2.view(torch.int32))
-    frame = [a + b for a, b in zip(sel_ms, cast_ms)]
+    cast_ms = [f - s_ for f, s_ in zip(frame, sel_ms)]
     rays = 2560 * 1440
     srt = sorted(frame)
     out = {"workload": "open65536: 65536x65536x1024, 128x128x2 chunks of 512^3, 4 LODs, view distance 16384; "
@@ -584,6 +592,7 @@ def bench_open_async(aok, ctx, threads, n_poses=300, fps=60.0, from_file=False):
         shown.append(1.0 - sst["missing"] / max(1, sst["planned"]))
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda._sleep(200_000)  # the timed region starts after the launch below is queued
         e0.record(stream)
         aok.render(ctx, scene, cam, TAU, hit, t, stream=stream)
         e1.record(stream)
