@@ -324,14 +324,16 @@ int aok_render(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double lod_t
  * paired with the selected chunks whose AABB they may see (pair depth = the
  * distance from the camera to the AABB), Hi-Z occlusion culling of the pairs
  * against the previous frame's per-tile depth, ray marching of each pair
- * through its chunk's DAG into a 64-bit visibility buffer with an atomic
- * minimum, this frame's Hi-Z, a second culling + marching pass over the
- * pairs the first pass culled, and a resolve pass that writes the output.
+ * through its chunk's DAG into a visibility buffer (a 64-bit key and a
+ * 64-bit payload per pixel, installed by a 128-bit compare-and-swap when the
+ * key is the smallest), this frame's Hi-Z, a second culling + marching pass
+ * over the pairs the first pass culled, and a resolve pass that writes the
+ * output from the payloads.
  * The output equals aok_render's (see the one exception documented in the
  * implementation: rays entering the world box exactly on an interior chunk
  * plane).  The previous frame's Hi-Z only saves work; it is kept per context
  * for the last scene and resolution rendered.
- * Buffers (visibility keys 8 B per pixel, per-tile and per-region arrays)
+ * Buffers (visibility records 16 B per pixel, per-tile and per-region arrays)
  * are allocated on first use and when the resolution or grid changes,
  * charged to the budget.  Not for concurrent calls on one context.
  * AOK_E_INVALID for scenes of more than AOK_TILES_MAX_CHUNKS regions (the key
@@ -343,8 +345,9 @@ int aok_render_tiles(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double
  * stats[0] chunk regions with pairs, [1] / [2] half-tile items marched /
  * culled by Hi-Z in pass 1, [3] / [4] the same in pass 2, [5] pixel rays
  * traced through a chunk, [6] pixel rays skipped because the pixel already
- * held a nearer hit, [7] resolve failures (0 unless the implementation is
- * wrong).  AOK_E_INVALID before the first aok_render_tiles. */
+ * held a nearer hit, [7] records not installed because the compare-and-swap
+ * loop ran out of attempts (0 unless the implementation is wrong).
+ * AOK_E_INVALID before the first aok_render_tiles. */
 int aok_tiles_stats(aok_ctx* ctx, uint64_t* stats);
 /* Drop the Hi-Z history: the next aok_render_tiles runs its first pass
  * without occlusion culling (as on a scene's first frame). */

@@ -437,7 +437,7 @@ def render_tiles(ctx: Context, scene: Scene, cam, tau: float, hit, t, stream=Non
 
 
 TILE_STATS = ("regions_with_pairs", "items_marched_1", "items_culled_1", "items_marched_2", "items_culled_2",
-              "pixel_traces", "pixel_skips", "resolve_failures")
+              "pixel_traces", "pixel_skips", "cas_exhausted")
 
 
 def tiles_stats(ctx: Context) -> dict:

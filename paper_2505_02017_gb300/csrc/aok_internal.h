@@ -64,7 +64,8 @@ struct CamDev {
 // Device buffers of the tile-chunk pipeline (Sec. 3.5) for one resolution.
 constexpr int kTileStats = 8;
 struct TileDev {
-    unsigned long long* vis;   // [W*H] visibility keys (distance | march order | chunk), ~0 = none
+    unsigned long long* vis;   // [W*H][2] visibility records: key (distance | march order | chunk), ~0 = none;
+                               // payload (hit voxel, LOD, entry axis, material)
     float* hiz_prev;           // [tiles] previous frame's per-tile max hit distance (no culling: huge)
     float* hiz;                // [tiles] per-tile max distance after pass 1 of this frame
     float* hiz_next;           // [tiles] this frame's final per-tile max distance

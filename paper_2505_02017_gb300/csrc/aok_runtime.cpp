@@ -893,7 +893,7 @@ static int ensure_tiles(aok_ctx* ctx, uint32_t scene, int32_t W, int32_t H, int6
     const int32_t tx = (W + 7) / 8, ty = (H + 7) / 8;
     const size_t tiles = (size_t)tx * ty, px = (size_t)W * H, n = (size_t)nch;
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    const size_t sz[] = {px * 8, tiles * 4, tiles * 4, tiles * 4, n * 16, n * 4, n * 4, n * 4, (n + 1) * 8,
+    const size_t sz[] = {px * 16, tiles * 4, tiles * 4, tiles * 4, n * 16, n * 4, n * 4, n * 4, (n + 1) * 8,
                          kTileStats * 8};
     size_t total = 0;
     for (size_t b : sz) total += al(b);
@@ -916,7 +916,7 @@ static int ensure_tiles(aok_ctx* ctx, uint32_t scene, int32_t W, int32_t H, int6
     d.stats = (unsigned long long*)q[9];
     d.tiles_x = tx;
     d.tiles_y = ty;
-    cudaError_t e = cudaMemsetAsync(d.vis, 0xFF, px * 8, s);
+    cudaError_t e = cudaMemsetAsync(d.vis, 0xFF, px * 16, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.hiz_prev, 0x7F, tiles * 4, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(d.stats, 0, kTileStats * 8, s);
     if (e != cudaSuccess) {

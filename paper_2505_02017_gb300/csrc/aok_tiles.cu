@@ -16,9 +16,9 @@
 //      upper bound of each pixel's distance so far).
 //   4. ray marching, pass 2: the pairs pass 1 culled are tested again
 //      against this frame's Hi-Z and the survivors marched.
-//   5. resolve: each pixel re-traces its ray in the winning chunk and writes
-//      the same output record as the march; the per-tile maximum of the
-//      final distances becomes the next frame's Hi-Z.
+//   5. resolve: each pixel decodes its visibility record and writes the same
+//      output record as the march; the per-tile maximum of the final
+//      distances becomes the next frame's Hi-Z.
 //
 // Pass 2 makes the result independent of the previous frame: a pair it culls
 // lies beyond every pixel's current hit in that tile, so it cannot hold a
@@ -27,8 +27,13 @@
 // instead of an appended TileInfo buffer with indirect dispatch; the key is
 // widened; each marching warp takes half a tile (32 pixels).
 //
-// Visibility key (the paper's 24-bit depth | normal | 13-bit chunk ID | 24-bit
-// position cannot address 512^3 chunks):
+// Visibility record: 16 bytes per pixel, a key and a payload installed
+// together by a 128-bit compare-and-swap (the paper's 64-bit InterlockedMax
+// record of depth | normal | 13-bit chunk ID | 24-bit position cannot address
+// 512^3 chunks).  Payload: the hit voxel's world LOD-0 corner x, y, z (17 bits
+// each), its LOD (3 bits), the entry axis (2 bits; 3: origin inside) and the
+// material (8 bits) -- with the ray, everything the output record needs.
+// Key:
 //   bits 63..32  top 32 bits of the FP64 ray parameter t of the hit (t >= 0,
 //                so the IEEE bits order as integers; truncation keeps order)
 //   bits 31..16  place of the chunk region in the march order along the ray:
@@ -50,7 +55,23 @@ using namespace aok;
 namespace {
 
 constexpr unsigned long long kNoKey = ~0ull;
-enum { kStList = 0, kStTraced1, kStCulled1, kStTraced2, kStCulled2, kStPixelTraces, kStPixelSkips, kStResolveFail };
+constexpr int kCasLimit = 4096;  // attempts: each failure means another chunk's smaller key went in
+
+// 128-bit compare-and-swap on a 16-byte aligned record (sm_90+): returns the
+// previous record.
+__device__ __forceinline__ ulonglong2 cas128(unsigned long long* p, ulonglong2 cmp, ulonglong2 val) {
+    ulonglong2 old;
+    asm volatile("{\n\t.reg .b128 d, c, n;\n\t"
+                 "mov.b128 c, {%2, %3};\n\t"
+                 "mov.b128 n, {%4, %5};\n\t"
+                 "atom.global.cas.b128 d, [%6], c, n;\n\t"
+                 "mov.b128 {%0, %1}, d;\n\t}"
+                 : "=l"(old.x), "=l"(old.y)
+                 : "l"(cmp.x), "l"(cmp.y), "l"(val.x), "l"(val.y), "l"(p)
+                 : "memory");
+    return old;
+}
+enum { kStList = 0, kStTraced1, kStCulled1, kStTraced2, kStCulled2, kStPixelTraces, kStPixelSkips, kStCasExhausted };
 
 __device__ __forceinline__ void region_coords(const SceneDev& S, uint32_t chunk, int32_t u[3]) {
     u[0] = (int32_t)(chunk % (uint32_t)S.grid[0]);
@@ -155,30 +176,35 @@ __device__ __forceinline__ int pair_pixel(const SceneDev& S, const CamDev& C, co
     region_coords(S, chunk, u);
     Entry en;
     if (!enter_region<FAST>(S, C, r, u, en) || !aabb_pass(S, C, r, ref, u)) return 0;
-    const unsigned long long cur = __ldcg(vis + pix);
+    unsigned long long* rec = vis + 2 * pix;
+    const unsigned long long cur = __ldcg(rec);
     if (cur != kNoKey && en.e < 3 && t_key(en.Ne, r.d[en.e]) > (uint32_t)(cur >> 32)) return 2;
     HitRec hit;
     Counters cnt = {0, 0, 0};
     if (trace_chunk<FAST, false>(S, ref, r, en.Oloc, en.e, en.Ne, hit, cnt) && within_view(S, r, hit)) {
         const uint32_t tk = hit.e < 3 ? t_key(hit.Ne, r.d[hit.e]) : 0u;
-        atomicMin(vis + pix, ((unsigned long long)tk << 32) | ((unsigned long long)(en.order & 0xFFFFu) << 16) | chunk);
+        const int n = (int)ref.lod;
+        const int32_t side = (1 << (S.mlog - n)) - 1;
+        unsigned long long pay = 0;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const int32_t uv = ((r.mir >> a) & 1u) ? side - hit.c[a] : hit.c[a];
+            pay |= (unsigned long long)(uint32_t)((u[a] << S.mlog) + (uv << n)) << (17 * a);
+        }
+        pay |= (unsigned long long)n << 51 | (unsigned long long)hit.e << 54 | (unsigned long long)hit.mat << 56;
+        const ulonglong2 mine = make_ulonglong2(
+            ((unsigned long long)tk << 32) | ((unsigned long long)(en.order & 0xFFFFu) << 16) | chunk, pay);
+        // install the record if its key is the smallest so far
+        ulonglong2 seen = make_ulonglong2(cur, __ldcg(rec + 1));
+        int tries = 0;
+        while (seen.x > mine.x) {
+            if (++tries > kCasLimit) return 3;
+            const ulonglong2 old = cas128(rec, seen, mine);
+            if (old.x == seen.x && old.y == seen.y) break;
+            seen = old;
+        }
     }
     return 1;
-}
-
-template <bool FAST>
-__device__ __forceinline__ bool resolve_pixel(const SceneDev& S, const CamDev& C, const ChunkRef* __restrict__ frame,
-                                              uint32_t chunk, const RayState& r, size_t pix, uint4* __restrict__ out_hit,
-                                              float* __restrict__ out_t) {
-    int32_t u[3];
-    region_coords(S, chunk, u);
-    const ChunkRef ref = frame[chunk];
-    Entry en;
-    if (ref.root == kNone || !enter_region<FAST>(S, C, r, u, en)) return false;
-    HitRec hit;
-    Counters cnt = {0, 0, 0};
-    if (!trace_chunk<FAST, false>(S, ref, r, en.Oloc, en.e, en.Ne, hit, cnt)) return false;
-    return emit_hit(S, r, ref, u, hit, ray_norm(r), out_hit, out_t, pix);
 }
 
 // ---------------------------------------------------------------------------
@@ -329,6 +355,7 @@ __global__ void __launch_bounds__(128) tc_cast_kernel(SceneDev S, CamDev C, cons
                                                    : pair_pixel<false>(S, C, ref, chunk, r, pix, T.vis);
             pix_traced += res == 1;
             pix_skipped += res == 2;
+            if (res == 3) atomicAdd(&T.stats[kStCasExhausted], 1ull);
         }
     }
     pix_traced = __reduce_add_sync(0xFFFFFFFFu, pix_traced);
@@ -356,7 +383,7 @@ __global__ void __launch_bounds__(256) tc_hiz_kernel(CamDev C, TileDev T) {
     for (int k = 0; k < 2; k++) {
         const int px = tx * 8 + (lane & 7), py = ty * 8 + k * 4 + (lane >> 3);
         if (px < C.W && py < C.H) {
-            const unsigned long long key = __ldcg(T.vis + (size_t)py * C.W + px);
+            const unsigned long long key = __ldcg(T.vis + 2 * ((size_t)py * C.W + px));
             float dist = __int_as_float(0x7F800000);
             if (key != kNoKey) {
                 float d[3];
@@ -386,21 +413,35 @@ __global__ void __launch_bounds__(128) tc_resolve_kernel(SceneDev S, CamDev C, c
     float dist_up = 0.0f;
     if (px < C.W && py < C.H) {
         const size_t pix = (size_t)py * C.W + px;
-        const unsigned long long key = __ldcg(T.vis + pix);
-        T.vis[pix] = kNoKey;  // re-armed for the next frame
-        bool ok = false;
-        if (key != kNoKey) {
-            RayState r;
-            const uint32_t chunk = (uint32_t)(key & 0xFFFFu);
-            ok = make_ray(C, px, py, r) ? resolve_pixel<true>(S, C, frame, chunk, r, pix, out_hit, out_t)
-                                        : resolve_pixel<false>(S, C, frame, chunk, r, pix, out_hit, out_t);
-            if (!ok) atomicAdd(&T.stats[kStResolveFail], 1ull);
-        }
-        if (ok) {
-            dist_up = __fmul_ru(out_t[pix], 1.000001f);
-        } else {
+        const ulonglong2 rec = __ldcg(reinterpret_cast<const ulonglong2*>(T.vis) + pix);
+        reinterpret_cast<ulonglong2*>(T.vis)[pix] = make_ulonglong2(kNoKey, kNoKey);  // re-armed for the next frame
+        if (rec.x == kNoKey) {
             emit_miss(out_hit, out_t, pix);
             dist_up = __int_as_float(0x7F800000);
+        } else {
+            // the output record of emit_hit, rebuilt from the payload and the ray
+            RayState r;
+            make_ray(C, px, py, r);
+            const unsigned long long pay = rec.y;
+            const uint32_t x = (uint32_t)(pay & 0x1FFFFu), y = (uint32_t)((pay >> 17) & 0x1FFFFu),
+                           z = (uint32_t)((pay >> 34) & 0x1FFFFu);
+            const int n = (int)((pay >> 51) & 7u), e = (int)((pay >> 54) & 3u);
+            const uint32_t mat = (uint32_t)(pay >> 56);
+            float dist = 0.0f;
+            if (e < 3) {
+                // entry plane: the voxel's face the mirrored ray meets first, as a numerator
+                const uint32_t w[3] = {x, y, z};
+                const bool m = (r.mir >> e) & 1u;
+                const int32_t wext = S.grid[e] << S.mlog;
+                const int32_t face = m ? wext - (int32_t)w[e] - (1 << n) : (int32_t)w[e];
+                const int32_t Ow = m ? (S.grid[e] << (S.mlog + kFix)) - C.O[e] : C.O[e];
+                const int32_t Ne = (face << kFix) - Ow;
+                dist = __fdiv_rn((float)Ne * (1.0f / 4096.0f), fabsf(r.d[e])) * ray_norm(r);
+            }
+            const uint32_t normal = e == 3 ? 7u : (uint32_t)(2 * e) + ((r.mir >> e) & 1u);
+            out_hit[pix] = make_uint4(x, y, z, (uint32_t)n | (mat << 8) | (normal << 16) | (1u << 19));
+            out_t[pix] = dist;
+            dist_up = __fmul_ru(dist, 1.000001f);
         }
     }
 #pragma unroll

@@ -52,7 +52,7 @@ def tiles(ctx, sc, cam, tau):
     hit, t = aok.alloc_frame(cam.W, cam.H)
     aok.render_tiles(ctx, sc, cam, tau, hit, t)
     st = aok.tiles_stats(ctx)
-    assert st["resolve_failures"] == 0, st
+    assert st["cas_exhausted"] == 0, st
     return (hit, t), st
 
 
