@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(1024) tc_scan_kernel(int nch, TileDev T) {
 // frame's keeps.
 // ---------------------------------------------------------------------------
 template <int PASS>
-__global__ void __launch_bounds__(128) tc_cast_kernel(SceneDev S, CamDev C, const ChunkRef* __restrict__ frame,
+__global__ void __launch_bounds__(128, 7) tc_cast_kernel(SceneDev S, CamDev C, const ChunkRef* __restrict__ frame,
                                                       TileDev T) {
     const uint32_t n_list = (uint32_t)T.stats[kStList];
     if (n_list == 0) return;
