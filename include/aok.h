@@ -483,6 +483,41 @@ int aok_serve_times(aok_ctx* ctx, uint64_t ticket, uint64_t* submit_ns, uint64_t
 int aok_render_noalloc(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double lod_threshold_px,
                        const aok_frame* frame, void* stream);
 
+/* Beam pass (ESVO's beam optimisation, which the paper's traversal builds on,
+ * Sec. 2; here exact): with on = 1, aok_render, aok_render_counted,
+ * aok_render_host(_async) and aok_cast_selected of this context first compute,
+ * for every 8 x 4 pixel tile, a lower bound on the L-infinity distance from
+ * the camera origin of every solid voxel of the frame's LOD-cut scene that
+ * the tile's rays can meet (a level-by-level walk of the selected DAGs,
+ * refining a node while its screen rectangle spans more than R tiles and
+ * its side is above 2^L voxels, each node scattering its distance to the
+ * tiles of its rectangle with an atomic minimum; R and L: aok_beam_tune).  The casting kernel then
+ * restarts each ray's march at the last integer plane of its dominant axis
+ * that the ray crosses before that distance.  Output records are identical
+ * with the pass on or off.  Buffers
+ * (4 B per tile, 2 x 16 MiB node queues) are charged to the budget at the
+ * first render of each resolution.  Not used by checked casting, the
+ * persistent single-view kernel, aok_render_noalloc, batches, serving or the
+ * tile pipeline.  Default off (on = 0).  The pass's buffers belong to the context:
+ * with it on, renders of one context on different streams must be ordered
+ * (an event or a synchronisation between them). */
+int aok_set_beam(aok_ctx* ctx, int on);
+/* Refinement of the beam pass's walk: a node is refined while its rectangle
+ * spans more than refine_tiles tiles and its side is above 2^min_node_log2
+ * LOD-0 voxels (defaults 8 and 2: down to the 4^3 leaves).  Any setting
+ * gives the same output records; it trades the pass's time for how tight
+ * the bounds are.  AOK_E_INVALID for min_node_log2 outside [2, 16]. */
+int aok_beam_tune(aok_ctx* ctx, uint32_t refine_tiles, int32_t min_node_log2);
+/* The last beam pass of this context (synchronises the device): bounds
+ * (nullable, n_bounds >= tiles_x * tiles_y entries, row-major, numerator
+ * units of 2^-12 LOD-0 voxels, INT32_MAX = no solid voxel reachable),
+ * level_counts (nullable, 16 entries: level 0 the selected regions walked,
+ * level l > 0 the nodes queued for it; a
+ * count above 2^20 means that level's queue overflowed and the parents stood
+ * in for their children) and tiles_xy (nullable, 2 entries).
+ * AOK_E_INVALID before the first beam pass or if n_bounds is too small. */
+int aok_beam_info(aok_ctx* ctx, int32_t* bounds, uint64_t n_bounds, uint32_t* level_counts, int32_t* tiles_xy);
+
 /* ------------------------------------------------------------------ */
 /* Diagnostics                                                        */
 /* ------------------------------------------------------------------ */

@@ -120,6 +120,9 @@ def lib() -> ctypes.CDLL:
             "aok_set_batch_kernel": [vp, ctypes.c_int],
             "aok_set_single_view_kernel": [vp, ctypes.c_int],
             "aok_set_checked": [vp, ctypes.c_int],
+            "aok_set_beam": [vp, ctypes.c_int],
+            "aok_beam_tune": [vp, u32, ctypes.c_int32],
+            "aok_beam_info": [vp, P(ctypes.c_int32), u64, P(u32), P(ctypes.c_int32)],
             "aok_checked_errors": [vp, P(u32)],
             "aok_serve_start": [vp, u32, u32, u32],
             "aok_serve_stop": [vp],
@@ -419,6 +422,29 @@ def render(ctx: Context, scene: Scene, cam, tau: float, hit, t, stream=None):
 def set_checked(ctx: Context, on: bool):
     """Checked casting: every pool index tested before its load (aok_set_checked)."""
     return check(lib().aok_set_checked(ctx.h, 1 if on else 0), "aok_set_checked")
+
+
+def set_beam(ctx: Context, on: bool):
+    """Beam pass before single-view casting: per 8x4 tile a lower bound on the
+    distance of the solid voxels its rays can meet (aok_set_beam)."""
+    return check(lib().aok_set_beam(ctx.h, 1 if on else 0), "aok_set_beam")
+
+
+def beam_tune(ctx: Context, refine_tiles: int = 8, min_node_log2: int = 2):
+    """Refinement of the beam pass's walk (aok_beam_tune)."""
+    return check(lib().aok_beam_tune(ctx.h, refine_tiles, min_node_log2), "aok_beam_tune")
+
+
+def beam_info(ctx: Context):
+    """The last beam pass (aok_beam_info; synchronises): (bounds as an int32
+    array [tiles_y, tiles_x] in 2^-12 voxel units, nodes queued per level)."""
+    xy = (ctypes.c_int32 * 2)()
+    lv = (ctypes.c_uint32 * 16)()
+    check(lib().aok_beam_info(ctx.h, None, 0, lv, xy), "aok_beam_info")
+    b = np.zeros((xy[1], xy[0]), dtype=np.int32)
+    check(lib().aok_beam_info(ctx.h, b.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), b.size, None, None),
+          "aok_beam_info")
+    return b, [int(v) for v in lv]
 
 
 def checked_errors(ctx: Context) -> int:

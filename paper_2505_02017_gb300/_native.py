@@ -45,7 +45,7 @@ def build(force: bool = False, verbose: bool = False) -> None:
     libaokbuild.so (g++/gcc).  Translation units compile in parallel."""
     hdrs = [os.path.join(_ROOT, "include", "aok.h"), os.path.join(_CSRC, "aok_internal.h"),
             os.path.join(_CSRC, "aok_runtime.h"), os.path.join(_CSRC, "aok_trace.cuh")]
-    srcs_cu = [os.path.join(_CSRC, f) for f in ("aok_kernels.cu", "aok_tiles.cu")]
+    srcs_cu = [os.path.join(_CSRC, f) for f in ("aok_kernels.cu", "aok_tiles.cu", "aok_beam.cu")]
     srcs_cpp = [os.path.join(_CSRC, f) for f in ("aok_runtime.cpp", "aok_serve.cpp", "aok_stream.cpp", "aok_file.cpp")]
     bsrc = os.path.join(_CSRC, "aok_build.cpp")
     sg = os.path.join(_ROOT, "scenegen", "scenegen.c")

@@ -1,0 +1,398 @@
+// Beam pass: the beam optimisation of ESVO (Laine and Karras; Aokana Sec. 2
+// names ESVO as the traversal it builds on), recast so that it cannot change
+// a single output record.
+//
+// ESVO casts a coarse ray per pixel block first and starts the block's rays
+// near the surface the coarse ray found.  Here the coarse pass computes, for
+// every 8 x 4 pixel tile (one casting warp), a lower bound Dn on the
+// L-infinity distance from the camera origin of every solid voxel of the
+// frame's LOD-cut scene that the tile's rays can meet.  A ray's L-infinity
+// distance from the origin at parameter t is t |d|_max, so the casting
+// kernel restarts each ray's march at the last integer plane of its dominant
+// axis crossed before that distance: every cell the ray passes before it is
+// empty for this ray, the cell holding the restart point is empty, and every
+// hit is entered later through the planes the full march crosses -- the same
+// first hit, entry plane and distance, without the traversal in front of it.
+//
+// The bound is a minimum over nodes of the selected DAGs, scattered to the
+// tiles their screen rectangle covers:
+//   * level 0 takes every chunk region of the frame table with its DAG root,
+//     the box being the region's AABB of valid voxels;
+//   * a node is projected in FP32 to a rectangle of tiles (box_rect, with
+//     margins that cover its rounding); if the rectangle spans more tiles
+//     than the refinement threshold and the node is not a 4^3 leaf, its
+//     children (cell boxes clipped to the AABB) go to the next level's queue;
+//     otherwise atomicMin(Dn[tile], its L-inf distance) over the rectangle.
+//     A leaf uses the bounding box of its set voxels;
+//   * a box that comes closer to the origin than 2/16 of the largest |d|
+//     component covers every tile (rays reach it before camera depth 1/16);
+//     any other box is projected from its part at depth >= 1/16, and dropped
+//     if it has none or it lies beyond the view distance (a hit there is
+//     reported as a miss anyway);
+//   * a full queue makes the node scatter itself instead of its children.
+// Every solid voxel a pixel ray meets lies in one scattered node whose
+// rectangle holds that pixel's tile, so Dn[tile] is at most its distance.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cmath>
+#include <cstdint>
+
+#include <cooperative_groups.h>
+
+#include "aok_internal.h"
+
+namespace cg = cooperative_groups;
+using namespace aok;
+
+namespace {
+
+constexpr uint32_t kNullItem = 0xFFFFFFFFu;
+constexpr int kBeamThreads = 256;      // block size of the cooperative walk
+constexpr int kBeamBlocksPerSM = 2;    // at most this many blocks per SM (fewer blocks: cheaper barriers)
+constexpr double kNearS = 1.0 / 16.0;  // camera-depth plane the projection clips at
+
+// The camera as the beam pass projects with it (host-computed).
+struct BeamCam {
+    float Af[9];       // row-major inverse of A = [R col 0, R col 1, -R col 2] (d = A (u, v, 1)), rounded to FP32
+    float U, V;        // u and v at the screen edges: tan_half * W / H, tan_half
+    float near_dn;     // numerator units: boxes closer than this cover every tile
+    float view_num;    // > 0: boxes farther than this (Euclidean, numerator units) are dropped
+    uint32_t expand;   // refine nodes whose rectangle spans more tiles than this
+    int32_t smin;      // ... and whose side is above 2^smin LOD-0 voxels
+    int32_t W, H;
+    int32_t O[3];
+};
+
+// Screen rectangle [x, z) x [y, w) of tiles a box (relative to the origin)
+// can cover from its part at camera depth s >= kNearS; false if none.
+// q = Af p in FP32 errs by at most dl = 8 2^-24 max_i sum_j |Af_ij| |p_j|
+// (rounding of p, of Af and of the products and sums).  A box wholly in front
+// of the plane is bounded by its corners' projections (their hull holds the
+// box's), widened by the error that dl and the division carry; a box that
+// straddles it by u = q_x / q_s over q_x in [X0, X1] and q_s in [kNearS, S1],
+// each widened by dl.  Then a 0.5 pixel margin for the FP32 pixel rays.
+__device__ bool box_rect(const BeamCam& K, const BeamDev& B, const float lo[3], const float hi[3], int4& rc) {
+    float pm[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) pm[a] = fmaxf(fabsf(lo[a]), fabsf(hi[a]));
+    float M = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+        M = fmaxf(M, fabsf(K.Af[3 * i]) * pm[0] + fabsf(K.Af[3 * i + 1]) * pm[1] + fabsf(K.Af[3 * i + 2]) * pm[2]);
+    const float dl = M * 4.8e-7f + 1e-6f;
+    float X0 = 3e38f, X1 = -3e38f, Y0 = 3e38f, Y1 = -3e38f, S0 = 3e38f, S1 = -3e38f;
+    float u0 = 3e38f, u1 = -3e38f, v0 = 3e38f, v1 = -3e38f;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const float p0 = (k & 1) ? hi[0] : lo[0], p1 = (k & 2) ? hi[1] : lo[1], p2 = (k & 4) ? hi[2] : lo[2];
+        const float qx = K.Af[0] * p0 + K.Af[1] * p1 + K.Af[2] * p2;
+        const float qy = K.Af[3] * p0 + K.Af[4] * p1 + K.Af[5] * p2;
+        const float qs = K.Af[6] * p0 + K.Af[7] * p1 + K.Af[8] * p2;
+        X0 = fminf(X0, qx); X1 = fmaxf(X1, qx);
+        Y0 = fminf(Y0, qy); Y1 = fmaxf(Y1, qy);
+        S0 = fminf(S0, qs); S1 = fmaxf(S1, qs);
+        if (qs > 0.0f) {
+            const float r = 1.0f / qs;
+            u0 = fminf(u0, qx * r); u1 = fmaxf(u1, qx * r);
+            v0 = fminf(v0, qy * r); v1 = fmaxf(v1, qy * r);
+        }
+    }
+    const float near_s = (float)kNearS;
+    if (S1 + dl < near_s) return false;  // wholly behind the plane: only the near rule can reach it
+    float a0, a1, b0, b1;
+    if (S0 - dl >= near_s) {
+        const float um = fmaxf(fabsf(u0), fabsf(u1)) * 1.001f, vm = fmaxf(fabsf(v0), fabsf(v1)) * 1.001f;
+        const float mu = dl * (1.0f + um) / (S0 - dl) + um * 4.8e-7f;
+        const float mv = dl * (1.0f + vm) / (S0 - dl) + vm * 4.8e-7f;
+        a0 = u0 - mu; a1 = u1 + mu;
+        b0 = v0 - mv; b1 = v1 + mv;
+    } else {
+        const float Xl = X0 - dl, Xh = X1 + dl, Yl = Y0 - dl, Yh = Y1 + dl, Sh = S1 + dl;
+        a0 = fminf(Xl / near_s, Xl / Sh); a1 = fmaxf(Xh / near_s, Xh / Sh);
+        b0 = fminf(Yl / near_s, Yl / Sh); b1 = fmaxf(Yh / near_s, Yh / Sh);
+        a0 -= fabsf(a0) * 1e-6f; a1 += fabsf(a1) * 1e-6f;
+        b0 -= fabsf(b0) * 1e-6f; b1 += fabsf(b1) * 1e-6f;
+    }
+    // pixel-centre coordinates of the pixel rays (the inverse of ray_dir), 0.5 pixel margin
+    const float x0 = (a0 / K.U + 1.0f) * 0.5f * K.W - 1.0f, x1 = (a1 / K.U + 1.0f) * 0.5f * K.W;
+    const float y0 = (1.0f - b1 / K.V) * 0.5f * K.H - 1.0f, y1 = (1.0f - b0 / K.V) * 0.5f * K.H;
+    if (!(x1 >= 0.0f) || !(y1 >= 0.0f) || !(x0 < (float)K.W) || !(y0 < (float)K.H)) return false;
+    rc.x = (int)fmaxf(floorf(x0 * (1.0f / kBeamTileW)), 0.0f);
+    rc.y = (int)fmaxf(floorf(y0 * (1.0f / kBeamTileH)), 0.0f);
+    rc.z = (int)fminf(floorf(x1 * (1.0f / kBeamTileW)) + 1.0f, (float)B.tiles_x);
+    rc.w = (int)fminf(floorf(y1 * (1.0f / kBeamTileH)) + 1.0f, (float)B.tiles_y);
+    return rc.z > rc.x && rc.w > rc.y;
+}
+
+// Occupied extent [lo, hi) of a 4^3 leaf mask along each axis (bit = x + 4y + 16z).
+__device__ __forceinline__ void leaf_extent(uint64_t m, int lo[3], int hi[3]) {
+    uint64_t t = m | (m >> 32);
+    t |= t >> 16;
+    const uint64_t tz = t;  // z folded
+    t |= t >> 8;
+    t |= t >> 4;
+    const uint32_t xo = (uint32_t)(t & 0xFu);
+    uint64_t ty = tz | (tz >> 2);
+    ty |= ty >> 1;
+    const uint32_t yo = (uint32_t)((ty & 1u) | ((ty >> 3) & 2u) | ((ty >> 6) & 4u) | ((ty >> 9) & 8u));
+    uint64_t q = m | (m >> 8);
+    q |= q >> 4;
+    q |= q >> 2;
+    q |= q >> 1;
+    const uint32_t zo = (uint32_t)((q & 1u) | ((q >> 15) & 2u) | ((q >> 30) & 4u) | ((q >> 45) & 8u));
+    const uint32_t o[3] = {xo, yo, zo};
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        lo[a] = __ffs(o[a]) - 1;
+        hi[a] = 32 - __clz(o[a]);
+    }
+}
+
+// One level of the walk over n items.  level 0: the items are the frame
+// table's regions.  Every lane of a warp runs the same iterations (the queue
+// push and the scatter are warp-wide).
+__device__ void beam_level(const SceneDev& S, const BeamCam& K, const ChunkRef* __restrict__ frame, const BeamDev& B,
+                           int level, uint32_t n, uint32_t gtid, uint32_t stride) {
+    const uint4* __restrict__ qin = B.q[level & 1];
+    uint4* __restrict__ qout = B.q[(level + 1) & 1];
+    const int lane = (int)(gtid & 31u);
+    for (uint32_t base = gtid & ~31u; base < n; base += stride) {
+        const uint32_t i = base + (uint32_t)lane;
+        bool scatter = false;
+        int4 rc = make_int4(0, 0, 0, 0);
+        int32_t D = 0;
+        uint4 it = make_uint4(kNullItem, 0u, 0u, 0u);
+        uint32_t kids = 0;  // children to queue
+        if (i < n) {
+            ChunkRef ref;
+            if (level == 0) {
+                ref = frame[i];
+                if (ref.root != kNone) it = make_uint4(i, ref.root, 0u, (uint32_t)S.mlog);
+            } else {
+                it = qin[i];
+                if (it.x != kNullItem) ref = frame[it.x];
+            }
+            if (it.x != kNullItem) {
+                const int s = (int)it.w, lod = (int)ref.lod;
+                const bool leaf = s == lod + 2;
+                int32_t u[3];
+                u[0] = (int32_t)(it.x % (uint32_t)S.grid[0]);
+                u[1] = (int32_t)((it.x / (uint32_t)S.grid[0]) % (uint32_t)S.grid[1]);
+                u[2] = (int32_t)(it.x / ((uint32_t)S.grid[0] * (uint32_t)S.grid[1]));
+                const int32_t cell[3] = {(int32_t)(it.z & 1023u), (int32_t)((it.z >> 10) & 1023u),
+                                         (int32_t)((it.z >> 20) & 1023u)};
+                int32_t blo[3], bhi[3];
+                if (leaf) {
+                    int l[3], h[3];
+                    leaf_extent(S.leaves[it.y], l, h);
+#pragma unroll
+                    for (int a = 0; a < 3; a++) {
+                        blo[a] = cell[a] + (l[a] << lod);
+                        bhi[a] = cell[a] + (h[a] << lod);
+                    }
+                } else {
+#pragma unroll
+                    for (int a = 0; a < 3; a++) {
+                        blo[a] = max(cell[a], (int32_t)ref.aabb[a]);
+                        bhi[a] = min(cell[a] + (1 << s), (int32_t)ref.aabb[3 + a]);
+                    }
+                }
+                // L-inf distance from the origin (exact, numerator units: |values| < 2^30)
+                int32_t wl[3], wh[3];
+                int32_t dmax = 0;
+                float e2 = 0.0f;
+                bool empty = false;
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    empty = empty || blo[a] >= bhi[a];
+                    wl[a] = (((u[a] << S.mlog) + blo[a]) << kFix) - K.O[a];
+                    wh[a] = (((u[a] << S.mlog) + bhi[a]) << kFix) - K.O[a];
+                    const int32_t da = wl[a] > 0 ? wl[a] : (wh[a] < 0 ? -wh[a] : 0);
+                    dmax = max(dmax, da);
+                    e2 += (float)da * (float)da;
+                }
+                D = dmax;
+                if (!empty && !(K.view_num > 0.0f && sqrtf(e2) > K.view_num)) {
+                    bool cover;
+                    if ((float)D < K.near_dn) {
+                        rc = make_int4(0, 0, B.tiles_x, B.tiles_y);
+                        cover = true;
+                    } else {
+                        const float sc = 1.0f / (1 << kFix);
+                        const float lf[3] = {(float)wl[0] * sc, (float)wl[1] * sc, (float)wl[2] * sc};
+                        const float hf[3] = {(float)wh[0] * sc, (float)wh[1] * sc, (float)wh[2] * sc};
+                        cover = box_rect(K, B, lf, hf, rc);
+                    }
+                    if (cover) {
+                        const uint32_t area = (uint32_t)(rc.z - rc.x) * (uint32_t)(rc.w - rc.y);
+                        scatter = true;
+                        if (!leaf && area > K.expand && s > K.smin && level + 1 < kBeamLevels)
+                            kids = (uint32_t)__popc(S.nodes[it.y] & 0xFFu);
+                    }
+                }
+            }
+        }
+        // queue the children: one atomic per warp
+        uint32_t pre = kids;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, pre, o);
+            if (lane >= o) pre += v;
+        }
+        const uint32_t total = __shfl_sync(0xFFFFFFFFu, pre, 31);
+        uint32_t wbase = 0;
+        if (total) {
+            if (lane == 31) wbase = atomicAdd(&B.cnt[level + 1], total);
+            wbase = __shfl_sync(0xFFFFFFFFu, wbase, 31);
+        }
+        if (kids) {
+            const uint32_t at = wbase + pre - kids;
+            if (at + kids <= B.cap) {
+                // children: cell boxes of half the size, in stored octant order
+                // (their pointers loaded together before the queue writes)
+                const int s = (int)it.w;
+                const uint32_t h = 1u << (s - 1);
+                uint32_t m = S.nodes[it.y] & 0xFFu;
+                uint32_t ch[8];
+#pragma unroll
+                for (int j = 0; j < 8; j++) ch[j] = (uint32_t)j < kids ? __ldg(S.nodes + it.y + 2 + 2 * j) : 0u;
+                const uint32_t cx0 = it.z & 1023u, cy0 = (it.z >> 10) & 1023u, cz0 = (it.z >> 20) & 1023u;
+#pragma unroll
+                for (int j = 0; j < 8; j++) {
+                    if ((uint32_t)j >= kids) break;
+                    const int oct = __ffs(m) - 1;
+                    m &= m - 1;
+                    const uint32_t cx = cx0 + ((oct & 1) ? h : 0u);
+                    const uint32_t cy = cy0 + ((oct & 2) ? h : 0u);
+                    const uint32_t cz = cz0 + ((oct & 4) ? h : 0u);
+                    qout[at + j] = make_uint4(it.x, ch[j], cx | (cy << 10) | (cz << 20), (uint32_t)(s - 1));
+                }
+                scatter = false;
+            } else {
+                // queue full: this node stands for its children
+                for (uint32_t j = at; j < B.cap && j < at + kids; j++) qout[j] = make_uint4(kNullItem, 0u, 0u, 0u);
+            }
+        }
+        // scatter: into the finest level L of the bound pyramid (level 0: the
+        // tiles; level L: cells of 2^L x 2^L tiles) at which the rectangle
+        // spans at most 16 cells (or the coarsest); the pass ends with each
+        // tile taking the minimum over its cells
+        if (scatter) {
+            int L = 0;
+            int x0 = rc.x, y0 = rc.y, x1 = rc.z - 1, y1 = rc.w - 1;
+            while (L < kBeamPyr - 1 && (x1 - x0 + 1) * (y1 - y0 + 1) > 16) {
+                L++;
+                x0 >>= 1; y0 >>= 1; x1 >>= 1; y1 >>= 1;
+            }
+            int32_t* lv = L == 0 ? B.dn : B.pyr + B.poff[L];
+            const int wl = (B.tiles_x + (1 << L) - 1) >> L;
+            for (int y = y0; y <= y1; y++)
+                for (int x = x0; x <= x1; x++) atomicMin(&lv[(size_t)y * wl + x], D);
+        }
+        // level 0's count: the regions walked
+        if (level == 0) {
+            const unsigned walked = __ballot_sync(0xFFFFFFFFu, it.x != kNullItem);
+            if (lane == 0 && walked) atomicAdd(&B.cnt[0], (uint32_t)__popc(walked));
+        }
+    }
+}
+
+// The whole pass in one cooperative launch (every block resident): bounds and
+// counters reset, then the levels of the walk with a grid-wide barrier after
+// each, ending at the first level that queued nothing.
+__global__ void __launch_bounds__(kBeamThreads) beam_kernel(SceneDev S, BeamCam K, const ChunkRef* __restrict__ frame,
+                                                   BeamDev B, int levels, uint32_t n_regions, int32_t fill) {
+    cg::grid_group g = cg::this_grid();
+    const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    const uint32_t tiles = (uint32_t)B.tiles_x * (uint32_t)B.tiles_y;
+    for (uint32_t i = gtid; i < tiles; i += stride) B.dn[i] = fill;
+    for (uint32_t i = gtid; i < (uint32_t)B.poff[kBeamPyr]; i += stride) B.pyr[i] = fill;
+    if (gtid < kBeamLevels) B.cnt[gtid] = 0;
+    g.sync();
+    for (int level = 0; level < levels; level++) {
+        const uint32_t n = level == 0 ? n_regions : min(*(volatile uint32_t*)&B.cnt[level], B.cap);
+        if (n == 0) break;  // the same value in every thread after the barrier
+        beam_level(S, K, frame, B, level, n, gtid, stride);
+        g.sync();
+    }
+    for (uint32_t i = gtid; i < tiles; i += stride) {
+        const uint32_t ty = i / (uint32_t)B.tiles_x, tx = i - ty * (uint32_t)B.tiles_x;
+        int32_t m = B.dn[i];
+        for (int L = 1; L < kBeamPyr; L++) {
+            const uint32_t wl = ((uint32_t)B.tiles_x + (1u << L) - 1) >> L;
+            m = min(m, B.pyr[B.poff[L] + (ty >> L) * wl + (tx >> L)]);
+        }
+        B.dn[i] = m;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int aokk_beam(const SceneDev* S, const CamDev* C, const ChunkRef* frame, const BeamDev* B, uint32_t expand_tiles,
+              int min_log2, int sms, void* stream) {
+    const cudaStream_t st = (cudaStream_t)stream;
+    BeamCam K;
+    // A = [c0, c1, -c2] with d_i = R[3i] u + R[3i+1] v - R[3i+2]
+    double A[9];
+    for (int i = 0; i < 3; i++) {
+        A[3 * i + 0] = C->R[3 * i + 0];
+        A[3 * i + 1] = C->R[3 * i + 1];
+        A[3 * i + 2] = -(double)C->R[3 * i + 2];
+    }
+    const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                       A[2] * (A[3] * A[7] - A[4] * A[6]);
+    double nrm = 0.0;
+    for (int i = 0; i < 9; i++) nrm = fmax(nrm, fabs(A[i]));
+    const bool valid = std::isfinite(det) && fabs(det) > 1e-6 * nrm * nrm * nrm;
+    if (!valid) {
+        // an unusable camera matrix: bound 0 everywhere (nothing is skipped)
+        if (cudaMemsetAsync(B->dn, 0, (size_t)B->tiles_x * B->tiles_y * 4, st) != cudaSuccess ||
+            cudaMemsetAsync(B->cnt, 0, kBeamLevels * 4, st) != cudaSuccess)
+            return AOK_E_CUDA;
+        return AOK_OK;
+    }
+    const double id = 1.0 / det;
+    double Ai[9];
+    Ai[0] = (A[4] * A[8] - A[5] * A[7]) * id;
+    Ai[1] = (A[2] * A[7] - A[1] * A[8]) * id;
+    Ai[2] = (A[1] * A[5] - A[2] * A[4]) * id;
+    Ai[3] = (A[5] * A[6] - A[3] * A[8]) * id;
+    Ai[4] = (A[0] * A[8] - A[2] * A[6]) * id;
+    Ai[5] = (A[2] * A[3] - A[0] * A[5]) * id;
+    Ai[6] = (A[3] * A[7] - A[4] * A[6]) * id;
+    Ai[7] = (A[1] * A[6] - A[0] * A[7]) * id;
+    Ai[8] = (A[0] * A[4] - A[1] * A[3]) * id;
+    for (int i = 0; i < 9; i++) K.Af[i] = (float)Ai[i];
+    const double U = (double)C->tan_half * (double)C->W / (double)C->H, V = (double)C->tan_half;
+    K.U = (float)U;
+    K.V = (float)V;
+    K.expand = expand_tiles;
+    K.smin = min_log2;
+    // largest |d| component over the screen, with slack for the FP32 ray arithmetic
+    double dmax = 0.0;
+    for (int i = 0; i < 3; i++) dmax = fmax(dmax, fabs(A[3 * i]) * U + fabs(A[3 * i + 1]) * V + fabs(A[3 * i + 2]));
+    K.near_dn = (float)(2.0 * kNearS * dmax * 1.01 * (double)(1 << kFix));
+    K.view_num = S->view_dist > 0.0f ? (float)(((double)S->view_dist * 1.00001 + 1.0) * (double)(1 << kFix)) : 0.0f;
+    K.W = C->W;
+    K.H = C->H;
+    for (int a = 0; a < 3; a++) K.O[a] = C->O[a];
+    uint32_t nch = (uint32_t)(S->grid[0] * S->grid[1] * S->grid[2]);
+    int levels = S->mlog - 1;  // root size 2^mlog down to LOD-0 leaves of size 4
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, beam_kernel, kBeamThreads, 0) != cudaSuccess ||
+        per_sm < 1)
+        return AOK_E_CUDA;
+    const unsigned grid = (unsigned)(sms > 0 ? sms : 1) * (unsigned)(per_sm < kBeamBlocksPerSM ? per_sm : kBeamBlocksPerSM);
+    SceneDev s_ = *S;
+    BeamDev b_ = *B;
+    int32_t fill = INT_MAX;
+    void* args[] = {&s_, &K, (void*)&frame, &b_, &levels, &nch, &fill};
+    if (cudaLaunchCooperativeKernel((const void*)beam_kernel, grid, kBeamThreads, args, 0, st) != cudaSuccess)
+        return AOK_E_CUDA;
+    return cudaGetLastError() == cudaSuccess ? AOK_OK : AOK_E_CUDA;
+}
+
+}  // extern "C"

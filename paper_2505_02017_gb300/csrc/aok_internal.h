@@ -78,6 +78,24 @@ struct TileDev {
     int32_t tiles_x, tiles_y;
 };
 
+// Device buffers of the beam pass (ESVO's beam optimisation, Sec. 2): per
+// 8 x 4 pixel tile (one casting warp) a lower bound on the L-infinity distance
+// from the camera origin of every solid voxel the tile's rays can meet,
+// found by a level-by-level walk of the selected DAGs that refines a node
+// while its screen rectangle spans more than a few tiles.
+constexpr int kBeamTileW = 8, kBeamTileH = 4;
+constexpr int kBeamLevels = 16;  // queue counters (node levels of a 512^3 chunk: 8)
+constexpr int kBeamPyr = 7;      // bound pyramid levels (level 0: the tiles)
+struct BeamDev {
+    int32_t* dn;             // [tiles] bound in origin numerator units (2^-kFix); INT32_MAX: nothing solid
+    int32_t* pyr;            // levels 1 .. kBeamPyr-1 of the bound pyramid: cells of 2^L x 2^L tiles, folded into dn
+    int32_t poff[8];         // offset of level L in pyr (poff[kBeamPyr]: total)
+    uint4* q[2];             // node queues of alternate levels: {chunk, node, cell x | y << 10 | z << 20, log2 size}
+    uint32_t* cnt;           // [kBeamLevels] items pushed per level
+    uint32_t cap;            // queue capacity in items
+    int32_t tiles_x, tiles_y;
+};
+
 // Descriptor updates applied by a kernel on the rendering stream, so that a
 // frame sees every (chunk, LOD) change published before it and none after.
 struct DescPatch {
@@ -129,7 +147,10 @@ extern "C" {
 int aokk_select(const aok::SceneDev* s, const aok::CamDev* c, aok::ChunkRef* frame, int8_t* lod_out,
                 uint8_t* vis_out, uint32_t* n_visible, void* stream);
 int aokk_cast(const aok::SceneDev* s, const aok::CamDev* c, const aok::ChunkRef* frame, uint4* hit, float* t,
-              uint32_t* counts, void* stream, const aok::CheckDev* ck);
+              uint32_t* counts, void* stream, const aok::CheckDev* ck, const int32_t* beam = nullptr);
+// Beam pass (aok_beam.cu): fills B->dn for the frame table `frame`.
+int aokk_beam(const aok::SceneDev* S, const aok::CamDev* C, const aok::ChunkRef* frame, const aok::BeamDev* B,
+              uint32_t expand_tiles, int min_log2, int sms, void* stream);
 int aokk_ray_dirs(const aok::CamDev* c, float* dirs, void* stream);
 int aokk_tiles_frame(const aok::SceneDev* S, const aok::CamDev* C, const aok::ChunkRef* frame, const aok::TileDev* T,
                      uint4* hit, float* t, int sms, void* stream);

@@ -103,16 +103,20 @@ __global__ void select_batch_kernel(const __grid_constant__ BatchParams P) {
     if (chunk < nch) select_one(v.scene, v.cam, v.frame, nullptr, nullptr, nullptr, chunk);
 }
 
-// 16 x 8 pixel tiles, warps of 8 x 4 pixels
-template <bool COUNT>
+// 16 x 8 pixel tiles, warps of 8 x 4 pixels.  BEAM: the warp's 8 x 4 tile
+// bound from the beam pass (aok_beam.cu) restarts its rays' march past the
+// space in front of the nearest voxel they can meet.
+template <bool COUNT, bool BEAM = false>
 __global__ void __launch_bounds__(128) cast_kernel(SceneDev S, CamDev C, const ChunkRef* __restrict__ frame,
                                                    uint4* __restrict__ out_hit, float* __restrict__ out_t,
-                                                   uint32_t* __restrict__ counts) {
+                                                   uint32_t* __restrict__ counts, const int32_t* __restrict__ beam) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int px = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
     const int py = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
     if (px >= C.W || py >= C.H) return;
-    trace_pixel<COUNT>(S, C, frame, px, py, out_hit, out_t, counts, (size_t)py * C.W + px);
+    int32_t Dn = 0;
+    if (BEAM) Dn = __ldg(beam + (size_t)(py / kBeamTileH) * ((C.W + kBeamTileW - 1) / kBeamTileW) + px / kBeamTileW);
+    trace_pixel<COUNT, false, BEAM>(S, C, frame, px, py, out_hit, out_t, counts, (size_t)py * C.W + px, nullptr, Dn);
 }
 
 // The same casting with every pool index checked (CheckDev).
@@ -229,14 +233,19 @@ int aokk_select(const SceneDev* s, const CamDev* c, ChunkRef* frame, int8_t* lod
 }
 
 int aokk_cast(const SceneDev* s, const CamDev* c, const ChunkRef* frame, uint4* hit, float* t, uint32_t* counts,
-              void* stream, const CheckDev* ck) {
+              void* stream, const CheckDev* ck, const int32_t* beam) {
     dim3 grid((c->W + 15) / 16, (c->H + 7) / 8);
+    const cudaStream_t st = (cudaStream_t)stream;
     if (ck && !counts)
-        cast_kernel_checked<<<grid, 128, 0, (cudaStream_t)stream>>>(*s, *c, frame, hit, t, *ck);
+        cast_kernel_checked<<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, *ck);
+    else if (counts && beam)
+        cast_kernel<true, true><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, counts, beam);
     else if (counts)
-        cast_kernel<true><<<grid, 128, 0, (cudaStream_t)stream>>>(*s, *c, frame, hit, t, counts);
+        cast_kernel<true><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, counts, nullptr);
+    else if (beam)
+        cast_kernel<false, true><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, nullptr, beam);
     else
-        cast_kernel<false><<<grid, 128, 0, (cudaStream_t)stream>>>(*s, *c, frame, hit, t, nullptr);
+        cast_kernel<false><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, nullptr, nullptr);
     return status_of(cudaGetLastError());
 }
 
@@ -417,7 +426,7 @@ int aokk_render_noalloc(const SceneDev* s, const CamDev* c, uint4* hit, float* t
     const cudaStream_t st = (cudaStream_t)stream;
     select_kernel<<<(unsigned)((nch + 127) / 128), 128, 0, st>>>(*s, *c, frame, nullptr, nullptr, nullptr);
     dim3 grid((c->W + 15) / 16, (c->H + 7) / 8);
-    cast_kernel<false><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, nullptr);
+    cast_kernel<false><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, nullptr, nullptr);
     return status_of(cudaGetLastError());
 }
 

@@ -347,6 +347,7 @@ void aok_destroy(aok_ctx* ctx) {
     dev_free(ctx, ctx->d_counter, sizeof(uint32_t) * 16);
     dev_free(ctx, ctx->d_single_queue, 2 * sizeof(unsigned long long));
     dev_free(ctx, ctx->tiles.block, ctx->tiles.bytes);
+    dev_free(ctx, ctx->beam.block, ctx->beam.bytes);
     pipe_release(ctx);
     if (ctx->pipe.render) cudaStreamDestroy(ctx->pipe.render);
     if (ctx->pipe.copy) cudaStreamDestroy(ctx->pipe.copy);
@@ -799,6 +800,62 @@ static const CheckDev* check_dev(aok_ctx* ctx, const Scene* sc, CheckDev* ck) {
     return ck;
 }
 
+// Beam buffers for W x H (reallocated when the size changes).
+static constexpr uint32_t kBeamCap = 1u << 20;  // queued nodes per level
+static int ensure_beam(aok_ctx* ctx, int32_t W, int32_t H) {
+    BeamState& b = ctx->beam;
+    if (b.block && b.W == W && b.H == H) return AOK_OK;
+    if (b.block) {
+        cudaDeviceSynchronize();
+        dev_free(ctx, b.block, b.bytes);
+        b = BeamState{};
+    }
+    const int32_t tx = (W + kBeamTileW - 1) / kBeamTileW, ty = (H + kBeamTileH - 1) / kBeamTileH;
+    auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    int32_t poff[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int L = 1; L < kBeamPyr; L++)
+        poff[L + 1] = poff[L] + ((tx + (1 << L) - 1) >> L) * ((ty + (1 << L) - 1) >> L);
+    const size_t sd = al((size_t)tx * ty * 4), sdc = al((size_t)poff[kBeamPyr] * 4), sq = al((size_t)kBeamCap * 16),
+                 sc = al(kBeamLevels * 4);
+    void* block = nullptr;
+    const int st = dev_alloc(ctx, &block, sd + sdc + 2 * sq + sc);
+    if (st) return st;
+    char* p = (char*)block;
+    b.dev.dn = (int32_t*)p;
+    b.dev.pyr = (int32_t*)(p + sd);
+    for (int L = 0; L < 8; L++) b.dev.poff[L] = poff[L];
+    b.dev.q[0] = (uint4*)(p + sd + sdc);
+    b.dev.q[1] = (uint4*)(p + sd + sdc + sq);
+    b.dev.cnt = (uint32_t*)(p + sd + sdc + 2 * sq);
+    b.dev.cap = kBeamCap;
+    b.dev.tiles_x = tx;
+    b.dev.tiles_y = ty;
+    b.block = block;
+    b.bytes = sd + sdc + 2 * sq + sc;
+    b.W = W;
+    b.H = H;
+    return AOK_OK;
+}
+
+// The casting launch of a single view, after the frame table is selected:
+// with the beam pass on (and no checked casting), the pass runs first and the
+// casting kernel takes its per-tile bounds.
+static int cast_single(aok_ctx* ctx, Scene* sc, const SceneDev& sd, const CamDev& cd, const aok_frame* frame,
+                       uint32_t* counts, void* stream) {
+    CheckDev ck;
+    const CheckDev* ckp = check_dev(ctx, sc, &ck);
+    const int32_t* beam = nullptr;
+    if (ctx->beam_on && !ckp) {
+        int st = ensure_beam(ctx, cd.W, cd.H);
+        if (st) return st;
+        st = aokk_beam(&sd, &cd, sc->d_frame, &ctx->beam.dev, ctx->beam_refine, ctx->beam_min_log2, ctx->sm_count,
+                       stream);
+        if (st) return st;
+        beam = ctx->beam.dev.dn;
+    }
+    return aokk_cast(&sd, &cd, sc->d_frame, (uint4*)frame->hit, frame->t, counts, stream, ckp, beam);
+}
+
 static int render_impl(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double tau, const aok_frame* frame,
                        uint32_t* counts, void* stream) {
     if (!ctx || !frame || !frame->hit || !frame->t) return AOK_E_INVALID;
@@ -814,10 +871,9 @@ static int render_impl(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, doub
         st = render_persistent(ctx, sc, cd, frame, stream, true);
     } else {
         st = aokk_select(&sd, &cd, sc->d_frame, nullptr, nullptr, nullptr, stream);
-        CheckDev ck;
-        if (!st) st = aokk_cast(&sd, &cd, sc->d_frame, (uint4*)frame->hit, frame->t, counts, stream,
-                                check_dev(ctx, sc, &ck));
+        if (!st) st = cast_single(ctx, sc, sd, cd, frame, counts, stream);
     }
+    if (st == AOK_E_OOM) return st;
     if (st) return cuda_status(ctx, cudaGetLastError());
     return AOK_OK;
 }
@@ -860,10 +916,8 @@ int aok_cast_selected(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, const
     cudaSetDevice(ctx->device);
     SceneDev sd = scene_dev(sc);
     if (ctx->single_persistent) st = render_persistent(ctx, sc, cd, frame, stream, false);
-    else {
-        CheckDev ck;
-        st = aokk_cast(&sd, &cd, sc->d_frame, (uint4*)frame->hit, frame->t, nullptr, stream, check_dev(ctx, sc, &ck));
-    }
+    else st = cast_single(ctx, sc, sd, cd, frame, nullptr, stream);
+    if (st == AOK_E_OOM) return st;
     return st ? cuda_status(ctx, cudaGetLastError()) : AOK_OK;
 }
 
@@ -968,6 +1022,38 @@ int aok_tiles_stats(aok_ctx* ctx, uint64_t* stats) {
 int aok_tiles_forget(aok_ctx* ctx) {
     if (!ctx) return AOK_E_INVALID;
     ctx->tiles.scene = 0xFFFFFFFFu;
+    return AOK_OK;
+}
+
+int aok_set_beam(aok_ctx* ctx, int on) {
+    if (!ctx) return AOK_E_INVALID;
+    ctx->beam_on = on ? 1 : 0;
+    return AOK_OK;
+}
+
+int aok_beam_tune(aok_ctx* ctx, uint32_t refine_tiles, int32_t min_node_log2) {
+    if (!ctx || min_node_log2 < 2 || min_node_log2 > 16) return AOK_E_INVALID;
+    ctx->beam_refine = refine_tiles;
+    ctx->beam_min_log2 = min_node_log2;
+    return AOK_OK;
+}
+
+int aok_beam_info(aok_ctx* ctx, int32_t* bounds, uint64_t n_bounds, uint32_t* level_counts, int32_t* tiles_xy) {
+    if (!ctx) return AOK_E_INVALID;
+    const BeamState& b = ctx->beam;
+    if (!b.block) return AOK_E_INVALID;
+    const uint64_t n = (uint64_t)b.dev.tiles_x * b.dev.tiles_y;
+    if (bounds && n_bounds < n) return AOK_E_INVALID;
+    cudaSetDevice(ctx->device);
+    if (cudaDeviceSynchronize() != cudaSuccess) return cuda_status(ctx, cudaGetLastError());
+    if (bounds && cudaMemcpy(bounds, b.dev.dn, n * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return cuda_status(ctx, cudaGetLastError());
+    if (level_counts && cudaMemcpy(level_counts, b.dev.cnt, kBeamLevels * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return cuda_status(ctx, cudaGetLastError());
+    if (tiles_xy) {
+        tiles_xy[0] = b.dev.tiles_x;
+        tiles_xy[1] = b.dev.tiles_y;
+    }
     return AOK_OK;
 }
 

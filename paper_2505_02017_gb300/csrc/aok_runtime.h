@@ -86,6 +86,14 @@ struct TileState {
     uint32_t scene = 0xFFFFFFFFu;
 };
 
+// Buffers of the beam pass for one resolution.
+struct BeamState {
+    BeamDev dev{};
+    void* block = nullptr;
+    size_t bytes = 0;
+    int32_t W = 0, H = 0;
+};
+
 struct aok_ctx_impl;
 
 }  // namespace aok
@@ -117,6 +125,10 @@ struct aok_ctx {
     size_t host_frame_px = 0;
     aok::ServeState* serve = nullptr;
     aok::TileState tiles;
+    aok::BeamState beam;
+    int beam_on = 0;  // single-view renders run the beam pass before casting
+    uint32_t beam_refine = 8;  // refine nodes spanning more tiles than this ...
+    int beam_min_log2 = 2;     // ... whose side is above 2^this LOD-0 voxels
     aok::HostPipe pipe;
     int checked = 0;  // single-view casts check every pool index (error word: d_counter[8])
     std::mutex upload_mu;  // the staging buffer and the copy stream: one upload at a time

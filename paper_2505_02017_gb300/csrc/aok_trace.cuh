@@ -126,6 +126,9 @@ struct Counters {
 
 // Returns true on a hit inside this chunk.  (e, Ne): entry plane into the chunk
 // (e = 3: the origin lies inside the chunk).  Oloc: mirrored local origin numerators.
+// BEAM: the entry plane (e, Ne) may lie inside the chunk (a restart of the
+// march past the beam's bound, trace_pixel_t), so the descent compares it
+// with the entry axis' mid planes as well.
 // In a checked build (CHECK) every pool index is tested before its load; an
 // index out of range ORs its code into *ck.err and ends the chunk's traversal
 // as a miss.
@@ -138,7 +141,7 @@ __device__ __forceinline__ bool out_of(uint64_t i, uint64_t n, const CheckDev* c
     return false;
 }
 
-template <bool FAST, bool COUNT, bool CHECK = false>
+template <bool FAST, bool COUNT, bool CHECK = false, bool BEAM = false>
 __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& ref, const RayState& r,
                                             const int32_t Oloc[3], int e, int32_t Ne, HitRec& hit, Counters& cnt,
                                             const CheckDev* ck = nullptr) {
@@ -236,9 +239,9 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
             const int32_t mid0 = ((2 * c0 + 1) << (kk + kFix)) - Oloc[0];
             const int32_t mid1 = ((2 * c1 + 1) << (kk + kFix)) - Oloc[1];
             const int32_t mid2 = ((2 * c2 + 1) << (kk + kFix)) - Oloc[2];
-            const int32_t b0 = (e != 0) && !tltf<FAST>(Ne, me, mid0, r.m[0], r.E[0] - Ee);
-            const int32_t b1 = (e != 1) && !tltf<FAST>(Ne, me, mid1, r.m[1], r.E[1] - Ee);
-            const int32_t b2 = (e != 2) && !tltf<FAST>(Ne, me, mid2, r.m[2], r.E[2] - Ee);
+            const int32_t b0 = (e != 0) ? !tltf<FAST>(Ne, me, mid0, r.m[0], r.E[0] - Ee) : (BEAM && Ne >= mid0);
+            const int32_t b1 = (e != 1) ? !tltf<FAST>(Ne, me, mid1, r.m[1], r.E[1] - Ee) : (BEAM && Ne >= mid1);
+            const int32_t b2 = (e != 2) ? !tltf<FAST>(Ne, me, mid2, r.m[2], r.E[2] - Ee) : (BEAM && Ne >= mid2);
             c0 = 2 * c0 + b0;
             c1 = 2 * c1 + b1;
             c2 = 2 * c2 + b2;
@@ -347,10 +350,11 @@ __device__ __forceinline__ bool make_ray(const CamDev& C, int px, int py, RaySta
 // ---------------------------------------------------------------------------
 // one pixel: world-grid chunk march + per-chunk DAG traversal
 // ---------------------------------------------------------------------------
-template <bool FAST, bool COUNT, bool CHECK = false>
+template <bool FAST, bool COUNT, bool CHECK = false, bool BEAM = false>
 __device__ __forceinline__ void trace_pixel_t(const SceneDev& S, const CamDev& C, const ChunkRef* __restrict__ frame,
                                             const RayState& r, uint4* __restrict__ out_hit, float* __restrict__ out_t,
-                                            uint32_t* __restrict__ counts, size_t pix, const CheckDev* ck = nullptr) {
+                                            uint32_t* __restrict__ counts, size_t pix, const CheckDev* ck = nullptr,
+                                            int32_t Dn = 0) {
     int32_t Ow[3], Wfix[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
@@ -402,6 +406,44 @@ __device__ __forceinline__ void trace_pixel_t(const SceneDev& S, const CamDev& C
             alive = false;
         }
     }
+    if (BEAM && alive && Dn > 0) {
+        // Beam restart.  Dn bounds from below (numerator units) the L-inf
+        // distance from the origin of every solid voxel this ray can meet, and
+        // the ray's L-inf distance at t is t |d|_max: the march resumes at the
+        // last integer plane of the dominant axis crossed strictly before that
+        // distance.  The cell holding that point is empty, so every hit is
+        // entered later, through the planes the full march would cross.
+        int as = 0;
+        if (fabsf(r.d[1]) > fabsf(r.d[as])) as = 1;
+        if (fabsf(r.d[2]) > fabsf(r.d[as])) as = 2;
+        const long long kp = ((long long)Dn - 1 + Ow[as]) >> kFix;  // plane index (floor)
+        const long long Nl = (kp << kFix) - Ow[as];
+        if (Nl >= (long long)Wfix[as] - Ow[as]) {
+            alive = false;  // past the world: nothing to meet
+        } else if (Nl > 0 && (e == 3 || tltf<FAST>(Ne, me, (int32_t)Nl, r.m[as], r.E[as] - Ee))) {
+            const int32_t Ns = (int32_t)Nl;
+#pragma unroll
+            for (int a = 0; a < 3; a++)
+                if (a != as && r.d[a] != 0.0f && !tltf<FAST>(Ns, r.m[as], Wfix[a] - Ow[a], r.m[a], r.E[a] - r.E[as]))
+                    alive = false;  // left the world box before the restart point
+            if (alive) {
+                e = as; Ne = Ns; me = r.m[as]; Ee = r.E[as];
+                cc[as] = (int32_t)(kp >> S.mlog);
+                const float ts_num = (float)Ns / fabsf(r.d[as]);
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    if (a == as) continue;
+                    const float pa = (float)Ow[a] + ts_num * fabsf(r.d[a]);
+                    int32_t cell = (int32_t)floorf(pa * (1.0f / (float)(1 << cs)));
+                    cell = max(0, min(cell, S.grid[a] - 1));
+                    // exact: cell*M <= x_a(t_s) < (cell+1)*M
+                    while (cell + 1 < S.grid[a] && !tltf<FAST>(Ne, me, ((cell + 1) << cs) - Ow[a], r.m[a], r.E[a] - Ee)) cell++;
+                    while (cell > 0 && tltf<FAST>(Ne, me, (cell << cs) - Ow[a], r.m[a], r.E[a] - Ee)) cell--;
+                    cc[a] = cell;
+                }
+            }
+        }
+    }
     const float dn = ray_norm(r);
     float inv[3];
 #pragma unroll
@@ -435,7 +477,7 @@ __device__ __forceinline__ void trace_pixel_t(const SceneDev& S, const CamDev& C
                 int32_t Oloc[3];
 #pragma unroll
                 for (int a = 0; a < 3; a++) Oloc[a] = Ow[a] - (cc[a] << cs);
-                if (trace_chunk<FAST, COUNT, CHECK>(S, ref, r, Oloc, e, Ne, hit, cnt, ck)) {
+                if (trace_chunk<FAST, COUNT, CHECK, BEAM>(S, ref, r, Oloc, e, Ne, hit, cnt, ck)) {
                     found = emit_hit(S, r, ref, u, hit, dn, out_hit, out_t, pix);
                     break;
                 }
@@ -462,13 +504,16 @@ __device__ __forceinline__ void trace_pixel_t(const SceneDev& S, const CamDev& C
     }
 }
 
-template <bool COUNT, bool CHECK = false>
+template <bool COUNT, bool CHECK = false, bool BEAM = false>
 __device__ __forceinline__ void trace_pixel(const SceneDev& S, const CamDev& C, const ChunkRef* __restrict__ frame,
                                             int px, int py, uint4* __restrict__ out_hit, float* __restrict__ out_t,
-                                            uint32_t* __restrict__ counts, size_t pix, const CheckDev* ck = nullptr) {
+                                            uint32_t* __restrict__ counts, size_t pix, const CheckDev* ck = nullptr,
+                                            int32_t Dn = 0) {
     RayState r;
-    if (make_ray(C, px, py, r)) trace_pixel_t<true, COUNT, CHECK>(S, C, frame, r, out_hit, out_t, counts, pix, ck);
-    else trace_pixel_t<false, COUNT, CHECK>(S, C, frame, r, out_hit, out_t, counts, pix, ck);
+    if (make_ray(C, px, py, r))
+        trace_pixel_t<true, COUNT, CHECK, BEAM>(S, C, frame, r, out_hit, out_t, counts, pix, ck, Dn);
+    else
+        trace_pixel_t<false, COUNT, CHECK, BEAM>(S, C, frame, r, out_hit, out_t, counts, pix, ck, Dn);
 }
 
 }  // namespace aok

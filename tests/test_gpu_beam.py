@@ -1,0 +1,201 @@
+"""Beam pass (ESVO's beam optimisation, made exact) through aok_set_beam:
+every frame equals the frame without the pass bit for bit -- voxel, LOD,
+material, normal, hit flag and distance -- and the oracle on every
+non-ambiguous pixel; every tile's bound is at most the L-infinity distance
+from the camera of every voxel hit in it; a camera matrix the pass cannot
+invert turns it off (all bounds 0); on the benchmark's 4096^3 frame the pass
+removes node visits."""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+import oracle as orc
+import scenegen as sg
+from gpu_util import compare, decode
+from worlds import MED64, MULTI16, MULTI32, TINY32
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2505_02017_gb300 as aok  # noqa: E402
+
+INT32_MAX = 2**31 - 1
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = aok.Context(0)
+    yield c
+    aok.set_beam(c, False)
+    c.close()
+
+
+_scenes = {}
+
+
+def scene_for(ctx, spec):
+    key = (id(ctx), spec.name)
+    if key not in _scenes:
+        w = sg.World(spec)
+        _scenes[key] = (w, aok.Scene.from_world(ctx, w, threads=16), orc.OracleScene(w))
+    return _scenes[key]
+
+
+def render(ctx, sc, cam, tau, beam):
+    aok.set_beam(ctx, beam)
+    hit, t = aok.alloc_frame(cam.W, cam.H)
+    aok.render(ctx, sc, cam, tau, hit, t)
+    torch.cuda.synchronize()
+    return hit, t
+
+
+def same(a, b):
+    return torch.equal(a[0], b[0]) and torch.equal(a[1].view(torch.int32), b[1].view(torch.int32))
+
+
+def check_bounds(ctx, cam, frame):
+    """Every hit voxel's L-inf distance from the origin (2^-12 units) >= its tile's bound."""
+    b, levels = aok.beam_info(ctx)
+    assert b.shape == ((cam.H + 3) // 4, (cam.W + 7) // 8)
+    assert all(v <= 1 << 20 for v in levels)  # no queue overflowed on these frames
+    g = decode(*frame)
+    O = np.round(cam.origin.astype(np.float64) * 4096).astype(np.int64)
+    py, px = np.divmod(np.arange(cam.W * cam.H), cam.W)
+    h = g["hit"] == 1
+    lo = np.stack([g["x"], g["y"], g["z"]], 1).astype(np.int64) * 4096 - O
+    hi = lo + (np.int64(4096) << g["lod"].astype(np.int64))[:, None]
+    d = np.maximum(np.maximum(lo, -hi), 0).max(1)
+    tb = b[py // 4, px // 8].astype(np.int64)
+    assert (tb[h] <= d[h]).all(), int((tb[h] > d[h]).sum())
+    # tiles whose rays all miss may hold any bound; the pass found something to skip
+    return b, levels
+
+
+CASES = [
+    (TINY32, lambda w: sg.orbit_camera(TINY32, 5, 40, 30), 1.0),
+    (TINY32, lambda w: sg.orbit_camera(TINY32, 6, 37, 23), 4.0),
+    (MULTI16, lambda w: sg.ground_camera(w, 3, 40, 24, lo_frac=0.3, hi_frac=0.7, z_lo=3, z_hi=8), 2.0),
+    (MULTI16, lambda w: sg.orbit_camera(MULTI16, 1, 61, 47, radius=80), 2.0),
+    (MULTI32, lambda w: sg.ground_camera(w, 4, 64, 40, z_lo=4, z_hi=20), 1.0),
+    (MED64, lambda w: sg.ground_camera(w, 4, 160, 90, z_lo=4, z_hi=40), 4.0),
+    (MED64, lambda w: sg.ground_camera(w, 9, 203, 117, z_lo=4, z_hi=40), 1.5),
+    (MED64, lambda w: sg.orbit_camera(MED64, 3, 128, 96, radius=300), 2.0),
+]
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_small_worlds_equal_and_oracle(ctx, case):
+    spec, camf, tau = CASES[case]
+    w, sc, S = scene_for(ctx, spec)
+    cam = camf(w)
+    off = render(ctx, sc, cam, tau, False)
+    on = render(ctx, sc, cam, tau, True)
+    assert same(off, on)
+    b, _ = check_bounds(ctx, cam, on)
+    compare(decode(*on), S.cast(cam, S.select(cam, tau), view_dist=spec.view_dist), max_amb_frac=2e-3)
+
+
+def test_bounds_are_used(ctx):
+    """On a walker view most tiles get a positive bound (geometry is not at the camera)."""
+    w, sc, _ = scene_for(ctx, MED64)
+    cam = sg.ground_camera(w, 9, 203, 117, z_lo=4, z_hi=40)
+    render(ctx, sc, cam, 1.5, True)
+    b, levels = aok.beam_info(ctx)
+    assert (b > 0).mean() > 0.5
+    assert levels[0] > 0 and levels[1] > 0  # the walk refined nodes below the chunk roots
+
+
+def test_moving_camera_and_view_distance(ctx):
+    spec = replace(MULTI32, name="multi32vd_beam", view_dist=45.0)
+    w, sc, S = scene_for(ctx, spec)
+    for seed in (4, 5, 6):
+        cam = sg.ground_camera(w, seed, 64, 40, z_lo=4, z_hi=20)
+        off = render(ctx, sc, cam, 1.0, False)
+        on = render(ctx, sc, cam, 1.0, True)
+        assert same(off, on)
+        check_bounds(ctx, cam, on)
+    orc_ref = S.cast(cam, S.select(cam, 1.0), view_dist=spec.view_dist)
+    compare(decode(*on), orc_ref, max_amb_frac=2e-3)
+    w, sc, _ = scene_for(ctx, MED64)
+    for cam in sg.path_cameras(w, 31, 6, 150, 100, n_waypoints=3, span=150.0, z_lo=4.0, z_hi=40.0):
+        assert same(render(ctx, sc, cam, 1.0, False), render(ctx, sc, cam, 1.0, True))
+        check_bounds(ctx, cam, render(ctx, sc, cam, 1.0, True))
+
+
+def test_axis_aligned_and_degenerate_images(ctx):
+    """Rays with zero direction components, 1-pixel-wide images, an origin on
+    chunk planes and one next to the ground."""
+    spec = MED64
+    w, sc, S = scene_for(ctx, spec)
+    cams = [sg.make_camera((100.25, 130.5, 120.0), fwd, 1, 1)
+            for fwd in [(0.0, 0.0, -1.0), (1.0, 0.0, 0.0), (0.0, -1.0, 0.0), (1.0, 1.0, -1.0)]]
+    cams.append(sg.make_camera((100.25, 130.5, 120.0), (0.3, 0.2, -1.0), 7, 1))
+    cams.append(sg.make_camera((128.0, 64.0, 100.0), (0.0, 0.0, -1.0), 9, 9))
+    h = w.height(100, 130)
+    cams.append(sg.make_camera((100.25, 130.5, h + 0.5), (1.0, 0.3, -0.2), 33, 17))  # just above the ground
+    cams.append(sg.make_camera((100.25, 130.5, h - 2.5), (1.0, 0.3, 0.4), 16, 8))    # inside it
+    for cam in cams:
+        off = render(ctx, sc, cam, 1.0, False)
+        on = render(ctx, sc, cam, 1.0, True)
+        assert same(off, on)
+        check_bounds(ctx, cam, on)
+
+
+def test_camera_matrix_without_inverse(ctx):
+    """Back column equal to the right column: the pass cannot project, every
+    bound is 0 and nothing is skipped."""
+    w, sc, _ = scene_for(ctx, MED64)
+    cam = sg.ground_camera(w, 4, 48, 32, z_lo=4, z_hi=40)
+    R = cam.R.copy()
+    R[:, 2] = R[:, 0]
+    cam = replace(cam, R=R)
+    off = render(ctx, sc, cam, 1.0, False)
+    on = render(ctx, sc, cam, 1.0, True)
+    assert same(off, on)
+    b, _ = aok.beam_info(ctx)
+    assert (b == 0).all()
+
+
+def test_city4096_1080p_equal_and_fewer_visits(ctx):
+    """The benchmark's frame: equal output, fewer interior-node visits."""
+    w, sc, _ = scene_for(ctx, sg.CITY_4096)
+    cam = sg.ground_camera(w, 102, 1920, 1080)
+    off = render(ctx, sc, cam, 1.0, False)
+    on = render(ctx, sc, cam, 1.0, True)
+    assert same(off, on)
+    check_bounds(ctx, cam, on)
+    visits = []
+    for beam in (False, True):
+        aok.set_beam(ctx, beam)
+        hit, t = aok.alloc_frame(cam.W, cam.H)
+        counts = torch.zeros(cam.W * cam.H * 3, dtype=torch.int32, device="cuda")
+        aok.render_counted(ctx, sc, cam, 1.0, hit, t, counts)
+        torch.cuda.synchronize()
+        assert same(off, (hit, t))
+        visits.append(int(counts.view(-1, 3)[:, 0].sum()))
+    assert visits[1] < visits[0], visits
+    # a far view with LOD 1-3 surfaces
+    cam = sg.ground_camera(w, 8, 640, 360, z_lo=600, z_hi=900, pitch=(-20.0, -8.0))
+    on = render(ctx, sc, cam, 1.0 / 3.0, True)
+    assert same(render(ctx, sc, cam, 1.0 / 3.0, False), on)
+    check_bounds(ctx, cam, on)
+
+
+def test_streamed_open_world_path(ctx):
+    """View distance + residency streaming (resident-LOD stand-ins): every pose equal."""
+    from paper_2505_02017_gb300.stream import Streamer
+    spec = sg.OPEN_8192
+    w = sg.World(spec)
+    sc = aok.Scene(ctx, spec, node_words=64 << 20, leaves=16 << 20, mat_bytes=1 << 30)
+    st = Streamer(ctx, w, sc, threads=16)
+    for cam in sg.path_cameras(w, 77, 5, 320, 180, n_waypoints=3, span=3000.0):
+        st.update(cam, 1.0 / 3.0)
+        off = render(ctx, sc, cam, 1.0 / 3.0, False)
+        on = render(ctx, sc, cam, 1.0 / 3.0, True)
+        assert same(off, on)
+        check_bounds(ctx, cam, on)
+    sc.destroy()
