@@ -34,6 +34,7 @@ METRIC = "primary rays/s + % memory roofline; batched/served vs plain aggregate,
 UNIT = "rays/s"
 TAU = 1.0
 CAM_SEED = 102
+BEAM_DEFAULT = True  # the beam pass runs before casting in the timed step
 W, H = 1920, 1080
 WORKLOAD = "city4096: 4096^3 world, 8x8x8 chunks of 512^3, 4 LODs, crust terrain + 4000 hollow blocks; " \
            "one 1920x1080 view, LOD threshold 1 px, camera seed 102"
@@ -362,6 +363,39 @@ def bench_tiles(aok, ctx, scene, world, flush, reps=20):
     return out
 
 
+def bench_beam(aok, ctx, scene, world, flush, reps=20):
+    """The beam pass (aok_set_beam) on and off for the benchmark frame and four
+    more walker views of the same world, 1920x1080: render time (selection,
+    beam pass, cast) and interior-node visits per ray; outputs must match."""
+    import torch
+    stream = torch.cuda.current_stream()
+    out = {"workload": "city4096 walker views, 1920x1080, tau = 1 px"}
+    for seed in (CAM_SEED, 5, 7, 11, 23):
+        cam = sg.ground_camera(world, seed, W, H)
+        row = {}
+        frames = []
+        for on in (False, True):
+            aok.set_beam(ctx, on)
+            hit, t = aok.alloc_frame(W, H)
+            fn = lambda: aok.render(ctx, scene, cam, TAU, hit, t)  # noqa: E731
+            for _ in range(3):
+                fn()
+            med, _ = time_events(fn, reps, flush, stream)
+            counts = torch.zeros(W * H * 3, dtype=torch.int32, device="cuda")
+            hc, tc = aok.alloc_frame(W, H)
+            aok.render_counted(ctx, scene, cam, TAU, hc, tc, counts)
+            torch.cuda.synchronize()
+            key = "on" if on else "off"
+            row[key + "_ms_median"] = med
+            row[key + "_interior_visits_per_ray"] = round(float(counts.view(-1, 3)[:, 0].double().mean()), 2)
+            frames.append((hit, t))
+        row["identical_outputs"] = bool(torch.equal(frames[0][0], frames[1][0]) and
+                                        torch.equal(frames[0][1].view(torch.int32), frames[1][1].view(torch.int32)))
+        out[f"camera_seed_{seed}"] = row
+    aok.set_beam(ctx, BEAM_DEFAULT)
+    return out
+
+
 def bench_color(aok, ctx, threads, flush, reps=20):
     """Colour-block compression (Sec. 3.3) on the city world with layered
     (coherent) colours: colour bytes resident and the benchmark frame's time
@@ -405,9 +439,10 @@ def bench_open(aok, ctx, threads, n_poses=300):
     st = Streamer(ctx, world, scene, threads)
     hit, t = aok.alloc_frame(2560, 1440)
     hit2, t2 = aok.alloc_frame(2560, 1440)
+    hit3, t3 = aok.alloc_frame(2560, 1440)
     stream = torch.cuda.current_stream()
-    sel_ms, cast_ms, tiles_ms, host = [], [], [], []
-    tiles_same = True
+    sel_ms, cast_ms, tiles_ms, other_ms, host = [], [], [], [], []
+    tiles_same = other_same = True
     aok.tiles_forget(ctx)
     # each timed region starts behind a short spin kernel, so that the host's
     # launch latency after a synchronisation is not counted as frame time
@@ -415,11 +450,18 @@ def bench_open(aok, ctx, threads, n_poses=300):
     frame = []
     for i, cam in enumerate(cams):
         host.append(st.update(cam, TAU))
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
         torch.cuda._sleep(gate)
         e[0].record(stream)
         aok.render(ctx, scene, cam, TAU, hit, t, stream=stream)  # selection + cast, one call
         e[1].record(stream)
+        # the same frame with the beam pass the other way round
+        aok.set_beam(ctx, not BEAM_DEFAULT)
+        torch.cuda._sleep(gate)
+        e[5].record(stream)
+        aok.render(ctx, scene, cam, TAU, hit3, t3, stream=stream)
+        e[6].record(stream)
+        aok.set_beam(ctx, BEAM_DEFAULT)
         # the paper's tile-chunk pipeline on the same frame (Hi-Z history: the previous pose)
         aok.render_tiles(ctx, scene, cam, TAU, hit2, t2, stream=stream)
         e[2].record(stream)
@@ -429,7 +471,9 @@ def bench_open(aok, ctx, threads, n_poses=300):
         e[4].record(stream)
         e[4].synchronize()
         frame.append(e[0].elapsed_time(e[1]))
-        tiles_ms.append(e[1].elapsed_time(e[2]))
+        tiles_ms.append(e[6].elapsed_time(e[2]))
+        other_ms.append(e[5].elapsed_time(e[6]))
+        other_same &= torch.equal(hit, hit3) and torch.equal(t.view(torch.int32), t3.view(torch.int32))
         sel_ms.append(e[3].elapsed_time(e[4]))
         tiles_same &= torch.equal(hit, hit2) and torch.equal(t.view(torch.int32), t2.view(torch.int32))
     cast_ms = [f - s_ for f, s_ in zip(frame, sel_ms)]
@@ -447,7 +491,10 @@ def bench_open(aok, ctx, threads, n_poses=300):
            "streaming_host_s_total": round(sum(h["plan_s"] + h["build_s"] + h["upload_s"] for h in host), 2),
            "tile_pipeline": {"frame_ms_median": sorted(tiles_ms)[len(tiles_ms) // 2],
                              "march_frame_ms_median": srt[len(srt) // 2],
-                             "identical_outputs_all_poses": bool(tiles_same)}}
+                             "identical_outputs_all_poses": bool(tiles_same)},
+           ("march_without_beam" if BEAM_DEFAULT else "march_with_beam"): {
+               "frame_ms_median": sorted(other_ms)[len(other_ms) // 2],
+               "identical_outputs_all_poses": bool(other_same)}}
     scene.destroy()
     return out
 
@@ -673,6 +720,7 @@ def main():
     ap.add_argument("--no-open", action="store_true")
     ap.add_argument("--no-tiles", action="store_true")
     ap.add_argument("--no-color", action="store_true")
+    ap.add_argument("--no-beam-ab", action="store_true")
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--cpu-scaling", action="store_true",
                     help="print the oracle's 1-thread / all-thread rays/s for three workloads and exit")
@@ -701,6 +749,7 @@ def main():
     built = aok.BuiltWorld(world, threads)
     t_build = time.perf_counter() - t0
     ctx = aok.Context(dev)
+    aok.set_beam(ctx, BEAM_DEFAULT)
     t0 = time.perf_counter()
     scene = aok.Scene.from_world(ctx, world, built=built)
     t_upload = time.perf_counter() - t0
@@ -727,8 +776,8 @@ def main():
         aok.render(ctx, scene, cam, TAU, hit, t)
     torch.cuda.synchronize()
 
-    # ---- timed: K steps, L2 flushed between steps, events around select and cast ----
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    # ---- timed: K steps, L2 flushed between steps, events around select, beam pass and cast ----
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     clocks = Clocks(dev)
     if dist:
         dist.barrier()
@@ -741,14 +790,18 @@ def main():
         ev[k][0].record(stream)
         aok.select_chunks(ctx, scene, cam, TAU, stream=stream)
         ev[k][1].record(stream)
-        aok.cast_selected(ctx, scene, cam, hit, t, stream=stream)
+        if BEAM_DEFAULT:
+            aok.beam_selected(ctx, scene, cam, stream=stream)
         ev[k][2].record(stream)
+        aok.cast_selected(ctx, scene, cam, hit, t, stream=stream)
+        ev[k][3].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     time.sleep(0.3)
     clk = clocks.stop()
-    step_ms = [e[0].elapsed_time(e[2]) for e in ev]
-    cast_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    step_ms = [e[0].elapsed_time(e[3]) for e in ev]
+    beam_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    cast_ms = [e[2].elapsed_time(e[3]) for e in ev]
     total_ms = sum(step_ms)
     if dist:
         total_ms = max_over_ranks(total_ms, dist, f"cuda:{dev}")
@@ -811,10 +864,14 @@ def main():
                 "api": "aok_render_host_async (3 frames in flight) + aok_host_frame_wait",
                 "ms_per_step": 1e3 * e2e_s, "synchronous_value": e2e_sync,
                 "synchronous_api": "aok_render_host"},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": (3 if BEAM_DEFAULT else 2) * args.steps,
         "clocks": clk,
         "wall_s_timed": wall,
+        "beam_pass": {"on": BEAM_DEFAULT, "pass_ms_median": statistics.median(beam_ms) if BEAM_DEFAULT else 0.0,
+                      "select_ms_median": statistics.median([e[0].elapsed_time(e[1]) for e in ev])},
     }
+    if not args.no_beam_ab:
+        out["beam_pass"]["on_off"] = bench_beam(aok, ctx, scene, world, flush)
     if not args.no_tiles:
         out["tile_pipeline"] = bench_tiles(aok, ctx, scene, world, flush)
     if not args.no_color:

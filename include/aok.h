@@ -495,19 +495,29 @@ int aok_render_noalloc(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, doub
  * restarts each ray's march at the last integer plane of its dominant axis
  * that the ray crosses before that distance.  Output records are identical
  * with the pass on or off.  Buffers
- * (4 B per tile, 2 x 16 MiB node queues) are charged to the budget at the
+ * (about 5.4 B per 8 x 4 pixel tile and two 16 MiB node queues) are charged to the budget at the
  * first render of each resolution.  Not used by checked casting, the
  * persistent single-view kernel, aok_render_noalloc, batches, serving or the
- * tile pipeline.  Default off (on = 0).  The pass's buffers belong to the context:
+ * tile pipeline.  Default on (for frames of at least 1.5 M pixels,
+ * aok_beam_tune).  The pass's buffers belong to the context:
  * with it on, renders of one context on different streams must be ordered
  * (an event or a synchronisation between them). */
 int aok_set_beam(aok_ctx* ctx, int on);
 /* Refinement of the beam pass's walk: a node is refined while its rectangle
  * spans more than refine_tiles tiles and its side is above 2^min_node_log2
- * LOD-0 voxels (defaults 8 and 2: down to the 4^3 leaves).  Any setting
- * gives the same output records; it trades the pass's time for how tight
- * the bounds are.  AOK_E_INVALID for min_node_log2 outside [2, 16]. */
-int aok_beam_tune(aok_ctx* ctx, uint32_t refine_tiles, int32_t min_node_log2);
+ * LOD-0 voxels (defaults 8 and 2: down to the 4^3 leaves); frames of fewer
+ * than min_pixels pixels cast without the pass (default 1,500,000: below
+ * that the pass's fixed cost, some tens of microseconds, outweighs what it
+ * saves).  Any setting gives the same output records.  AOK_E_INVALID for
+ * min_node_log2 outside [2, 16]. */
+int aok_beam_tune(aok_ctx* ctx, uint32_t refine_tiles, int32_t min_node_log2, uint64_t min_pixels);
+/* The beam pass alone, for the frame table the last aok_select_chunks (or
+ * render) of this scene selected and this camera: the next
+ * aok_cast_selected of the same scene and camera then casts with these
+ * bounds instead of computing them again (so that the pass and the cast can
+ * be timed apart).  Runs whether or not aok_set_beam is on.  Stream rules as
+ * for aok_cast_selected. */
+int aok_beam_selected(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, void* stream);
 /* The last beam pass of this context (synchronises the device): bounds
  * (nullable, n_bounds >= tiles_x * tiles_y entries, row-major, numerator
  * units of 2^-12 LOD-0 voxels, INT32_MAX = no solid voxel reachable),

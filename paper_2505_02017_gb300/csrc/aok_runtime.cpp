@@ -728,6 +728,7 @@ int aok_select_chunks(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, doubl
         st = cuda_status(ctx, cudaMemsetAsync(ctx->d_counter, 0, sizeof(uint32_t), s));
         if (st) return st;
     }
+    sc->select_gen++;
     st = aokk_select(&sd, &cd, sc->d_frame, lod_out, vis_out, n_visible_out ? ctx->d_counter : nullptr, stream);
     if (st) return cuda_status(ctx, cudaGetLastError());
     if (n_visible_out) {
@@ -837,20 +838,45 @@ static int ensure_beam(aok_ctx* ctx, int32_t W, int32_t H) {
     return AOK_OK;
 }
 
+// The beam pass over the scene's current frame table, remembered with what
+// it was computed for.
+static int run_beam(aok_ctx* ctx, uint32_t scene, Scene* sc, const SceneDev& sd, const CamDev& cd, void* stream) {
+    int st = ensure_beam(ctx, cd.W, cd.H);
+    if (st) return st;
+    BeamState& b = ctx->beam;
+    b.valid = false;
+    st = aokk_beam(&sd, &cd, sc->d_frame, &b.dev, ctx->beam_refine, ctx->beam_min_log2, ctx->sm_count, stream);
+    if (st) return st;
+    b.valid = true;
+    b.scene = scene;
+    b.gen = sc->select_gen;
+    b.cam = cd;
+    b.cam.sf = 0.0;  // the LOD threshold does not enter the bounds
+    return AOK_OK;
+}
+
+static bool beam_fresh(const aok_ctx* ctx, uint32_t scene, const Scene* sc, const CamDev& cd) {
+    const BeamState& b = ctx->beam;
+    if (!b.valid || b.scene != scene || b.gen != sc->select_gen) return false;
+    CamDev k = cd;
+    k.sf = 0.0;
+    return std::memcmp(&k, &b.cam, sizeof(CamDev)) == 0;
+}
+
 // The casting launch of a single view, after the frame table is selected:
-// with the beam pass on (and no checked casting), the pass runs first and the
-// casting kernel takes its per-tile bounds.
-static int cast_single(aok_ctx* ctx, Scene* sc, const SceneDev& sd, const CamDev& cd, const aok_frame* frame,
-                       uint32_t* counts, void* stream) {
+// with the beam pass on (and no checked casting) the casting kernel takes the
+// pass's per-tile bounds, computed first unless aok_beam_selected already did
+// for this selection and camera.
+static int cast_single(aok_ctx* ctx, uint32_t scene, Scene* sc, const SceneDev& sd, const CamDev& cd,
+                       const aok_frame* frame, uint32_t* counts, void* stream) {
     CheckDev ck;
     const CheckDev* ckp = check_dev(ctx, sc, &ck);
     const int32_t* beam = nullptr;
-    if (ctx->beam_on && !ckp) {
-        int st = ensure_beam(ctx, cd.W, cd.H);
-        if (st) return st;
-        st = aokk_beam(&sd, &cd, sc->d_frame, &ctx->beam.dev, ctx->beam_refine, ctx->beam_min_log2, ctx->sm_count,
-                       stream);
-        if (st) return st;
+    if (ctx->beam_on && !ckp && (uint64_t)cd.W * (uint64_t)cd.H >= ctx->beam_min_pixels) {
+        if (!beam_fresh(ctx, scene, sc, cd)) {
+            const int st = run_beam(ctx, scene, sc, sd, cd, stream);
+            if (st) return st;
+        }
         beam = ctx->beam.dev.dn;
     }
     return aokk_cast(&sd, &cd, sc->d_frame, (uint4*)frame->hit, frame->t, counts, stream, ckp, beam);
@@ -867,11 +893,12 @@ static int render_impl(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, doub
     if (st) return st;
     cudaSetDevice(ctx->device);
     SceneDev sd = scene_dev(sc);
+    sc->select_gen++;
     if (ctx->single_persistent && !counts) {
         st = render_persistent(ctx, sc, cd, frame, stream, true);
     } else {
         st = aokk_select(&sd, &cd, sc->d_frame, nullptr, nullptr, nullptr, stream);
-        if (!st) st = cast_single(ctx, sc, sd, cd, frame, counts, stream);
+        if (!st) st = cast_single(ctx, scene, sc, sd, cd, frame, counts, stream);
     }
     if (st == AOK_E_OOM) return st;
     if (st) return cuda_status(ctx, cudaGetLastError());
@@ -916,7 +943,7 @@ int aok_cast_selected(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, const
     cudaSetDevice(ctx->device);
     SceneDev sd = scene_dev(sc);
     if (ctx->single_persistent) st = render_persistent(ctx, sc, cd, frame, stream, false);
-    else st = cast_single(ctx, sc, sd, cd, frame, nullptr, stream);
+    else st = cast_single(ctx, scene, sc, sd, cd, frame, nullptr, stream);
     if (st == AOK_E_OOM) return st;
     return st ? cuda_status(ctx, cudaGetLastError()) : AOK_OK;
 }
@@ -1002,6 +1029,7 @@ int aok_render_tiles(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double
     st = ensure_tiles(ctx, scene, cd.W, cd.H, sc->n_chunks, (cudaStream_t)stream);
     if (st) return st;
     SceneDev sd = scene_dev(sc);
+    sc->select_gen++;
     st = aokk_select(&sd, &cd, sc->d_frame, nullptr, nullptr, nullptr, stream);
     if (!st) st = aokk_tiles_frame(&sd, &cd, sc->d_frame, &ctx->tiles.dev, (uint4*)frame->hit, frame->t,
                                    ctx->sm_count, stream);
@@ -1031,11 +1059,26 @@ int aok_set_beam(aok_ctx* ctx, int on) {
     return AOK_OK;
 }
 
-int aok_beam_tune(aok_ctx* ctx, uint32_t refine_tiles, int32_t min_node_log2) {
+int aok_beam_tune(aok_ctx* ctx, uint32_t refine_tiles, int32_t min_node_log2, uint64_t min_pixels) {
     if (!ctx || min_node_log2 < 2 || min_node_log2 > 16) return AOK_E_INVALID;
     ctx->beam_refine = refine_tiles;
     ctx->beam_min_log2 = min_node_log2;
+    ctx->beam_min_pixels = min_pixels;
     return AOK_OK;
+}
+
+int aok_beam_selected(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, void* stream) {
+    if (!ctx) return AOK_E_INVALID;
+    Scene* sc = find_scene(ctx, scene);
+    if (!sc) return AOK_E_NOT_RESIDENT;
+    CamDev cd;
+    int st = make_cam(ctx, sc, cam, 1.0, &cd);
+    if (st) return st;
+    cudaSetDevice(ctx->device);
+    SceneDev sd = scene_dev(sc);
+    st = run_beam(ctx, scene, sc, sd, cd, stream);
+    if (st == AOK_E_CUDA) return cuda_status(ctx, cudaGetLastError());
+    return st;
 }
 
 int aok_beam_info(aok_ctx* ctx, int32_t* bounds, uint64_t n_bounds, uint32_t* level_counts, int32_t* tiles_xy) {

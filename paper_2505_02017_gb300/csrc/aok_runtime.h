@@ -40,6 +40,7 @@ struct Scene {
     uint8_t* d_mats = nullptr;
     ChunkRef* d_desc = nullptr;   // [chunk * n_lods + lod]
     ChunkRef* d_frame = nullptr;  // per-frame selection of aok_render
+    uint64_t select_gen = 0;      // selections written into d_frame so far
     Pool nodes, leaves, mats;
     std::vector<ChunkRef> h_desc;
     std::vector<ChunkAlloc> alloc;
@@ -92,6 +93,11 @@ struct BeamState {
     void* block = nullptr;
     size_t bytes = 0;
     int32_t W = 0, H = 0;
+    // what the bounds in dev were computed for: a scene, its selection, a camera
+    bool valid = false;
+    uint32_t scene = 0xFFFFFFFFu;
+    uint64_t gen = 0;
+    CamDev cam{};
 };
 
 struct aok_ctx_impl;
@@ -126,9 +132,10 @@ struct aok_ctx {
     aok::ServeState* serve = nullptr;
     aok::TileState tiles;
     aok::BeamState beam;
-    int beam_on = 0;  // single-view renders run the beam pass before casting
+    int beam_on = 1;  // single-view renders run the beam pass before casting
     uint32_t beam_refine = 8;  // refine nodes spanning more tiles than this ...
     int beam_min_log2 = 2;     // ... whose side is above 2^this LOD-0 voxels
+    uint64_t beam_min_pixels = 1500000;  // smaller frames cast without the pass
     aok::HostPipe pipe;
     int checked = 0;  // single-view casts check every pool index (error word: d_counter[8])
     std::mutex upload_mu;  // the staging buffer and the copy stream: one upload at a time

@@ -29,6 +29,7 @@ INT32_MAX = 2**31 - 1
 @pytest.fixture(scope="module")
 def ctx():
     c = aok.Context(0)
+    aok.beam_tune(c, 8, 2, 0)  # the pass on every frame size
     yield c
     aok.set_beam(c, False)
     c.close()
@@ -199,3 +200,57 @@ def test_streamed_open_world_path(ctx):
         assert same(off, on)
         check_bounds(ctx, cam, on)
     sc.destroy()
+
+
+def test_beam_selected_then_cast(ctx):
+    """aok_beam_selected + aok_cast_selected equal a render; a later selection
+    or another camera makes the cast compute its own bounds."""
+    w, sc, _ = scene_for(ctx, MED64)
+    cam_a = sg.ground_camera(w, 4, 160, 90, z_lo=4, z_hi=40)
+    cam_b = sg.ground_camera(w, 9, 160, 90, z_lo=4, z_hi=40)
+    ref_a = render(ctx, sc, cam_a, 1.0, False)
+    ref_b = render(ctx, sc, cam_b, 1.0, False)
+    aok.set_beam(ctx, True)
+    hit, t = aok.alloc_frame(cam_a.W, cam_a.H)
+    aok.select_chunks(ctx, sc, cam_a, 1.0)
+    aok.beam_selected(ctx, sc, cam_a)
+    aok.cast_selected(ctx, sc, cam_a, hit, t)
+    torch.cuda.synchronize()
+    assert same(ref_a, (hit, t))
+    # bounds of camera a, then a selection for camera b: recomputed
+    aok.beam_selected(ctx, sc, cam_a)
+    aok.select_chunks(ctx, sc, cam_b, 1.0)
+    aok.cast_selected(ctx, sc, cam_b, hit, t)
+    torch.cuda.synchronize()
+    assert same(ref_b, (hit, t))
+    # same selection, other camera: recomputed
+    aok.select_chunks(ctx, sc, cam_a, 1.0)
+    aok.beam_selected(ctx, sc, cam_a)
+    aok.select_chunks(ctx, sc, cam_b, 1.0)
+    aok.beam_selected(ctx, sc, cam_a)  # stale for cam_b
+    aok.cast_selected(ctx, sc, cam_b, hit, t)
+    torch.cuda.synchronize()
+    assert same(ref_b, (hit, t))
+
+
+def test_refinement_settings_same_output(ctx):
+    """Any refinement setting gives the frame of the plain march."""
+    w, sc, _ = scene_for(ctx, MED64)
+    cam = sg.ground_camera(w, 9, 203, 117, z_lo=4, z_hi=40)
+    ref = render(ctx, sc, cam, 1.5, False)
+    try:
+        for refine, lg in ((0, 2), (4, 2), (64, 3), (1 << 30, 9), (8, 16)):
+            aok.beam_tune(ctx, refine, lg, 0)
+            out = render(ctx, sc, cam, 1.5, True)
+            assert same(ref, out), (refine, lg)
+            check_bounds(ctx, cam, out)
+        # below the frame-size threshold the pass does not run: the last
+        # pass's bounds stay, the frame is the plain march's
+        b0, _ = aok.beam_info(ctx)
+        cam2 = sg.ground_camera(w, 4, 203, 117, z_lo=4, z_hi=40)
+        ref2 = render(ctx, sc, cam2, 1.5, False)
+        aok.beam_tune(ctx, 8, 2, cam2.W * cam2.H + 1)
+        assert same(ref2, render(ctx, sc, cam2, 1.5, True))
+        assert (aok.beam_info(ctx)[0] == b0).all()
+    finally:
+        aok.beam_tune(ctx, 8, 2, 0)
