@@ -495,7 +495,7 @@ int aok_render_noalloc(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, doub
  * restarts each ray's march at the last integer plane of its dominant axis
  * that the ray crosses before that distance.  Output records are identical
  * with the pass on or off.  Buffers
- * (about 5.4 B per 8 x 4 pixel tile and two 16 MiB node queues) are charged to the budget at the
+ * (about 11 B per 8 x 4 pixel tile and two 16 MiB node queues) are charged to the budget at the
  * first render of each resolution.  Not used by checked casting, the
  * persistent single-view kernel, aok_render_noalloc, batches, serving or the
  * tile pipeline.  Default on (for frames of at least 1.5 M pixels,
@@ -520,11 +520,11 @@ int aok_beam_tune(aok_ctx* ctx, uint32_t refine_tiles, int32_t min_node_log2, ui
 int aok_beam_selected(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, void* stream);
 /* The last beam pass of this context (synchronises the device): bounds
  * (nullable, n_bounds >= tiles_x * tiles_y entries, row-major, numerator
- * units of 2^-12 LOD-0 voxels, INT32_MAX = no solid voxel reachable),
- * level_counts (nullable, 16 entries: level 0 the selected regions walked,
- * level l > 0 the nodes queued for it; a
- * count above 2^20 means that level's queue overflowed and the parents stood
- * in for their children) and tiles_xy (nullable, 2 entries).
+ * units of 2^-12 LOD-0 voxels, INT32_MAX = no solid voxel reachable; 0
+ * everywhere if the camera matrix has no usable inverse), level_counts
+ * (nullable, 16 entries: nodes walked at each depth below the region roots,
+ * depth 0 the selected regions; a queue holds 2^20 nodes per level, past
+ * that parents stand in for their children) and tiles_xy (nullable, 2).
  * AOK_E_INVALID before the first beam pass or if n_bounds is too small. */
 int aok_beam_info(aok_ctx* ctx, int32_t* bounds, uint64_t n_bounds, uint32_t* level_counts, int32_t* tiles_xy);
 

@@ -32,6 +32,14 @@
 //   * a full queue makes the node scatter itself instead of its children.
 // Every solid voxel a pixel ray meets lies in one scattered node whose
 // rectangle holds that pixel's tile, so Dn[tile] is at most its distance.
+//
+// The bounds live in a pyramid (level 0: the tiles; level L: cells of
+// 2^L x 2^L tiles): a node writes the finest level at which its rectangle
+// spans at most 16 cells, and the casting kernel takes each tile's minimum
+// over its cells.  Entries are 64-bit, (pass tag << 32) | bound, written by a
+// non-returning atomic minimum; the tag counts down from pass to pass, so an
+// entry of this pass always beats one left by an earlier pass, and readers
+// take entries of another tag as "nothing solid": the pyramid is never reset.
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -47,10 +55,10 @@ using namespace aok;
 
 namespace {
 
-constexpr uint32_t kNullItem = 0xFFFFFFFFu;
 constexpr int kBeamThreads = 256;      // block size of the cooperative walk
 constexpr int kBeamBlocksPerSM = 2;    // at most this many blocks per SM (fewer blocks: cheaper barriers)
 constexpr double kNearS = 1.0 / 16.0;  // camera-depth plane the projection clips at
+constexpr uint32_t kNoItem = 0xFFFFFFFFu;  // an empty queue slot
 
 // The camera as the beam pass projects with it (host-computed).
 struct BeamCam {
@@ -149,182 +157,182 @@ __device__ __forceinline__ void leaf_extent(uint64_t m, int lo[3], int hi[3]) {
     }
 }
 
-// One level of the walk over n items.  level 0: the items are the frame
-// table's regions.  Every lane of a warp runs the same iterations (the queue
-// push and the scatter are warp-wide).
-__device__ void beam_level(const SceneDev& S, const BeamCam& K, const ChunkRef* __restrict__ frame, const BeamDev& B,
-                           int level, uint32_t n, uint32_t gtid, uint32_t stride) {
-    const uint4* __restrict__ qin = B.q[level & 1];
-    uint4* __restrict__ qout = B.q[(level + 1) & 1];
-    const int lane = (int)(gtid & 31u);
-    for (uint32_t base = gtid & ~31u; base < n; base += stride) {
-        const uint32_t i = base + (uint32_t)lane;
-        bool scatter = false;
-        int4 rc = make_int4(0, 0, 0, 0);
-        int32_t D = 0;
-        uint4 it = make_uint4(kNullItem, 0u, 0u, 0u);
-        uint32_t kids = 0;  // children to queue
-        if (i < n) {
-            ChunkRef ref;
-            if (level == 0) {
-                ref = frame[i];
-                if (ref.root != kNone) it = make_uint4(i, ref.root, 0u, (uint32_t)S.mlog);
-            } else {
-                it = qin[i];
-                if (it.x != kNullItem) ref = frame[it.x];
-            }
-            if (it.x != kNullItem) {
-                const int s = (int)it.w, lod = (int)ref.lod;
-                const bool leaf = s == lod + 2;
-                int32_t u[3];
-                u[0] = (int32_t)(it.x % (uint32_t)S.grid[0]);
-                u[1] = (int32_t)((it.x / (uint32_t)S.grid[0]) % (uint32_t)S.grid[1]);
-                u[2] = (int32_t)(it.x / ((uint32_t)S.grid[0] * (uint32_t)S.grid[1]));
-                const int32_t cell[3] = {(int32_t)(it.z & 1023u), (int32_t)((it.z >> 10) & 1023u),
-                                         (int32_t)((it.z >> 20) & 1023u)};
-                int32_t blo[3], bhi[3];
-                if (leaf) {
-                    int l[3], h[3];
-                    leaf_extent(S.leaves[it.y], l, h);
+// A node's box (chunk-local cell clipped to the region's AABB, or a leaf's
+// set voxels), its L-inf distance from the origin and screen rectangle.
+// Returns false if the node cannot meet any pixel ray.
+__device__ __forceinline__ bool node_bound(const SceneDev& S, const BeamCam& K, const BeamDev& B, const ChunkRef& ref,
+                                           uint32_t chunk, uint32_t node, uint32_t packed_cell, int s, int4& rc,
+                                           int32_t& D) {
+    const int lod = (int)ref.lod;
+    const bool leaf = s == lod + 2;
+    int32_t u[3];
+    u[0] = (int32_t)(chunk % (uint32_t)S.grid[0]);
+    u[1] = (int32_t)((chunk / (uint32_t)S.grid[0]) % (uint32_t)S.grid[1]);
+    u[2] = (int32_t)(chunk / ((uint32_t)S.grid[0] * (uint32_t)S.grid[1]));
+    const int32_t cell[3] = {(int32_t)(packed_cell & 1023u), (int32_t)((packed_cell >> 10) & 1023u),
+                             (int32_t)((packed_cell >> 20) & 1023u)};
+    int32_t blo[3], bhi[3];
+    if (leaf) {
+        int l[3], h[3];
+        leaf_extent(S.leaves[node], l, h);
 #pragma unroll
-                    for (int a = 0; a < 3; a++) {
-                        blo[a] = cell[a] + (l[a] << lod);
-                        bhi[a] = cell[a] + (h[a] << lod);
-                    }
-                } else {
-#pragma unroll
-                    for (int a = 0; a < 3; a++) {
-                        blo[a] = max(cell[a], (int32_t)ref.aabb[a]);
-                        bhi[a] = min(cell[a] + (1 << s), (int32_t)ref.aabb[3 + a]);
-                    }
-                }
-                // L-inf distance from the origin (exact, numerator units: |values| < 2^30)
-                int32_t wl[3], wh[3];
-                int32_t dmax = 0;
-                float e2 = 0.0f;
-                bool empty = false;
-#pragma unroll
-                for (int a = 0; a < 3; a++) {
-                    empty = empty || blo[a] >= bhi[a];
-                    wl[a] = (((u[a] << S.mlog) + blo[a]) << kFix) - K.O[a];
-                    wh[a] = (((u[a] << S.mlog) + bhi[a]) << kFix) - K.O[a];
-                    const int32_t da = wl[a] > 0 ? wl[a] : (wh[a] < 0 ? -wh[a] : 0);
-                    dmax = max(dmax, da);
-                    e2 += (float)da * (float)da;
-                }
-                D = dmax;
-                if (!empty && !(K.view_num > 0.0f && sqrtf(e2) > K.view_num)) {
-                    bool cover;
-                    if ((float)D < K.near_dn) {
-                        rc = make_int4(0, 0, B.tiles_x, B.tiles_y);
-                        cover = true;
-                    } else {
-                        const float sc = 1.0f / (1 << kFix);
-                        const float lf[3] = {(float)wl[0] * sc, (float)wl[1] * sc, (float)wl[2] * sc};
-                        const float hf[3] = {(float)wh[0] * sc, (float)wh[1] * sc, (float)wh[2] * sc};
-                        cover = box_rect(K, B, lf, hf, rc);
-                    }
-                    if (cover) {
-                        const uint32_t area = (uint32_t)(rc.z - rc.x) * (uint32_t)(rc.w - rc.y);
-                        scatter = true;
-                        if (!leaf && area > K.expand && s > K.smin && level + 1 < kBeamLevels)
-                            kids = (uint32_t)__popc(S.nodes[it.y] & 0xFFu);
-                    }
-                }
-            }
+        for (int a = 0; a < 3; a++) {
+            blo[a] = cell[a] + (l[a] << lod);
+            bhi[a] = cell[a] + (h[a] << lod);
         }
-        // queue the children: one atomic per warp
-        uint32_t pre = kids;
+    } else {
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, pre, o);
-            if (lane >= o) pre += v;
-        }
-        const uint32_t total = __shfl_sync(0xFFFFFFFFu, pre, 31);
-        uint32_t wbase = 0;
-        if (total) {
-            if (lane == 31) wbase = atomicAdd(&B.cnt[level + 1], total);
-            wbase = __shfl_sync(0xFFFFFFFFu, wbase, 31);
-        }
-        if (kids) {
-            const uint32_t at = wbase + pre - kids;
-            if (at + kids <= B.cap) {
-                // children: cell boxes of half the size, in stored octant order
-                // (their pointers loaded together before the queue writes)
-                const int s = (int)it.w;
-                const uint32_t h = 1u << (s - 1);
-                uint32_t m = S.nodes[it.y] & 0xFFu;
-                uint32_t ch[8];
-#pragma unroll
-                for (int j = 0; j < 8; j++) ch[j] = (uint32_t)j < kids ? __ldg(S.nodes + it.y + 2 + 2 * j) : 0u;
-                const uint32_t cx0 = it.z & 1023u, cy0 = (it.z >> 10) & 1023u, cz0 = (it.z >> 20) & 1023u;
-#pragma unroll
-                for (int j = 0; j < 8; j++) {
-                    if ((uint32_t)j >= kids) break;
-                    const int oct = __ffs(m) - 1;
-                    m &= m - 1;
-                    const uint32_t cx = cx0 + ((oct & 1) ? h : 0u);
-                    const uint32_t cy = cy0 + ((oct & 2) ? h : 0u);
-                    const uint32_t cz = cz0 + ((oct & 4) ? h : 0u);
-                    qout[at + j] = make_uint4(it.x, ch[j], cx | (cy << 10) | (cz << 20), (uint32_t)(s - 1));
-                }
-                scatter = false;
-            } else {
-                // queue full: this node stands for its children
-                for (uint32_t j = at; j < B.cap && j < at + kids; j++) qout[j] = make_uint4(kNullItem, 0u, 0u, 0u);
-            }
-        }
-        // scatter: into the finest level L of the bound pyramid (level 0: the
-        // tiles; level L: cells of 2^L x 2^L tiles) at which the rectangle
-        // spans at most 16 cells (or the coarsest); the pass ends with each
-        // tile taking the minimum over its cells
-        if (scatter) {
-            int L = 0;
-            int x0 = rc.x, y0 = rc.y, x1 = rc.z - 1, y1 = rc.w - 1;
-            while (L < kBeamPyr - 1 && (x1 - x0 + 1) * (y1 - y0 + 1) > 16) {
-                L++;
-                x0 >>= 1; y0 >>= 1; x1 >>= 1; y1 >>= 1;
-            }
-            int32_t* lv = L == 0 ? B.dn : B.pyr + B.poff[L];
-            const int wl = (B.tiles_x + (1 << L) - 1) >> L;
-            for (int y = y0; y <= y1; y++)
-                for (int x = x0; x <= x1; x++) atomicMin(&lv[(size_t)y * wl + x], D);
-        }
-        // level 0's count: the regions walked
-        if (level == 0) {
-            const unsigned walked = __ballot_sync(0xFFFFFFFFu, it.x != kNullItem);
-            if (lane == 0 && walked) atomicAdd(&B.cnt[0], (uint32_t)__popc(walked));
+        for (int a = 0; a < 3; a++) {
+            blo[a] = max(cell[a], (int32_t)ref.aabb[a]);
+            bhi[a] = min(cell[a] + (1 << s), (int32_t)ref.aabb[3 + a]);
         }
     }
+    // L-inf distance from the origin (exact, numerator units: |values| < 2^30)
+    int32_t wl[3], wh[3];
+    int32_t dmax = 0;
+    float e2 = 0.0f;
+    bool empty = false;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        empty = empty || blo[a] >= bhi[a];
+        wl[a] = (((u[a] << S.mlog) + blo[a]) << kFix) - K.O[a];
+        wh[a] = (((u[a] << S.mlog) + bhi[a]) << kFix) - K.O[a];
+        const int32_t da = wl[a] > 0 ? wl[a] : (wh[a] < 0 ? -wh[a] : 0);
+        dmax = max(dmax, da);
+        e2 += (float)da * (float)da;
+    }
+    D = dmax;
+    if (empty || (K.view_num > 0.0f && sqrtf(e2) > K.view_num)) return false;
+    if ((float)D < K.near_dn) {
+        rc = make_int4(0, 0, B.tiles_x, B.tiles_y);
+        return true;
+    }
+    const float sc = 1.0f / (1 << kFix);
+    const float lf[3] = {(float)wl[0] * sc, (float)wl[1] * sc, (float)wl[2] * sc};
+    const float hf[3] = {(float)wh[0] * sc, (float)wh[1] * sc, (float)wh[2] * sc};
+    return box_rect(K, B, lf, hf, rc);
 }
 
-// The whole pass in one cooperative launch (every block resident): bounds and
-// counters reset, then the levels of the walk with a grid-wide barrier after
-// each, ending at the first level that queued nothing.
+// Atomic minimum without a return value (a reduction the SM does not wait for).
+__device__ __forceinline__ void red_min_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.global.min.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// D into the finest level L of the bound pyramid (level 0: the tiles; level
+// L: cells of 2^L x 2^L tiles) at which the rectangle spans at most 16 cells
+// (or the coarsest); the casting kernel takes each tile's minimum over its
+// cells.
+__device__ __forceinline__ void scatter_bound(const BeamDev& B, const int4& rc, int32_t D) {
+    int L = 0;
+    int x0 = rc.x, y0 = rc.y, x1 = rc.z - 1, y1 = rc.w - 1;
+    while (L < kBeamPyr - 1 && (x1 - x0 + 1) * (y1 - y0 + 1) > 16) {
+        L++;
+        x0 >>= 1; y0 >>= 1; x1 >>= 1; y1 >>= 1;
+    }
+    unsigned long long* lv = L == 0 ? B.dn : B.pyr + B.poff[L];
+    const int wl = (B.tiles_x + (1 << L) - 1) >> L;
+    const unsigned long long v = ((unsigned long long)B.tag << 32) | (uint32_t)D;
+    for (int y = y0; y <= y1; y++)
+        for (int x = x0; x <= x1; x++) red_min_u64(&lv[(size_t)y * wl + x], v);
+}
+
+// Children of interior node `node` (side 2^s) at cell c: {pointer, packed cell}.
+__device__ __forceinline__ uint32_t node_children(const SceneDev& S, uint32_t node, uint32_t packed_cell, int s,
+                                                  uint32_t ch[8], uint32_t cc[8]) {
+    const uint32_t m0 = __ldg(S.nodes + node) & 0xFFu;
+    const uint32_t k = (uint32_t)__popc(m0);
+    const uint32_t h = 1u << (s - 1);
+    const uint32_t cx0 = packed_cell & 1023u, cy0 = (packed_cell >> 10) & 1023u, cz0 = (packed_cell >> 20) & 1023u;
+    uint32_t m = m0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        ch[j] = (uint32_t)j < k ? __ldg(S.nodes + node + 2 + 2 * j) : 0u;
+        const int oct = m ? __ffs(m) - 1 : 0;
+        m &= m - 1;
+        cc[j] = (cx0 + ((oct & 1) ? h : 0u)) | ((cy0 + ((oct & 2) ? h : 0u)) << 10) | ((cz0 + ((oct & 4) ? h : 0u)) << 20);
+    }
+    return k;
+}
+
+// The whole pass in one cooperative launch (every block resident): the
+// levels of the walk with a grid-wide barrier after each, ending at the first
+// level that queued nothing.  Level 0 takes the frame table's regions; every
+// lane of a warp runs the same iterations (the queue reservation is
+// warp-wide).  Bounds carry the pass's tag, so nothing has to be reset
+// before the walk or folded after it.
 __global__ void __launch_bounds__(kBeamThreads) beam_kernel(SceneDev S, BeamCam K, const ChunkRef* __restrict__ frame,
-                                                   BeamDev B, int levels, uint32_t n_regions, int32_t fill) {
+                                                            BeamDev B, uint32_t n_regions) {
     cg::grid_group g = cg::this_grid();
+    __shared__ uint32_t hist[kBeamLevels];
     const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-    const uint32_t tiles = (uint32_t)B.tiles_x * (uint32_t)B.tiles_y;
-    for (uint32_t i = gtid; i < tiles; i += stride) B.dn[i] = fill;
-    for (uint32_t i = gtid; i < (uint32_t)B.poff[kBeamPyr]; i += stride) B.pyr[i] = fill;
-    if (gtid < kBeamLevels) B.cnt[gtid] = 0;
-    g.sync();
-    for (int level = 0; level < levels; level++) {
+    const int lane = (int)(threadIdx.x & 31u);
+    if (threadIdx.x < kBeamLevels) hist[threadIdx.x] = 0;
+    __syncthreads();
+    for (int level = 0; level < kBeamLevels - 1; level++) {
         const uint32_t n = level == 0 ? n_regions : min(*(volatile uint32_t*)&B.cnt[level], B.cap);
         if (n == 0) break;  // the same value in every thread after the barrier
-        beam_level(S, K, frame, B, level, n, gtid, stride);
+        const uint4* __restrict__ qin = B.q[level & 1];
+        uint4* __restrict__ qout = B.q[(level + 1) & 1];
+        for (uint32_t base = gtid & ~31u; base < n; base += stride) {
+            const uint32_t i = base + (uint32_t)lane;
+            uint32_t kids = 0, ch[8], cc[8];
+            uint4 it = make_uint4(kNoItem, 0u, 0u, 0u);
+            ChunkRef ref;
+            if (i < n) {
+                if (level == 0) {
+                    ref = frame[i];
+                    if (ref.root != kNone) it = make_uint4(i, ref.root, 0u, (uint32_t)S.mlog);
+                } else {
+                    it = qin[i];
+                    if (it.x != kNoItem) ref = frame[it.x];
+                }
+            }
+            if (it.x != kNoItem) {
+                const int s = (int)it.w, lod = (int)ref.lod;
+                atomicAdd(&hist[min(S.mlog - s, kBeamLevels - 1)], 1u);
+                int4 rc;
+                int32_t D;
+                if (node_bound(S, K, B, ref, it.x, it.y, it.z, s, rc, D)) {
+                    const uint32_t area = (uint32_t)(rc.z - rc.x) * (uint32_t)(rc.w - rc.y);
+                    if (s > lod + 2 && area > K.expand && s > K.smin)
+                        kids = node_children(S, it.y, it.z, s, ch, cc);
+                    else
+                        scatter_bound(B, rc, D);
+                }
+            }
+            // queue the children: one reservation per warp
+            uint32_t pre = kids;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, pre, o);
+                if (lane >= o) pre += v;
+            }
+            const uint32_t total = __shfl_sync(0xFFFFFFFFu, pre, 31);
+            uint32_t wbase = 0;
+            if (total) {
+                if (lane == 31) wbase = atomicAdd(&B.cnt[level + 1], total);
+                wbase = __shfl_sync(0xFFFFFFFFu, wbase, 31);
+            }
+            if (kids) {
+                const uint32_t at = wbase + pre - kids;
+                if (at + kids <= B.cap) {
+#pragma unroll
+                    for (int q = 0; q < 8; q++)
+                        if ((uint32_t)q < kids) qout[at + q] = make_uint4(it.x, ch[q], cc[q], it.w - 1);
+                } else {
+                    // queue full: this node stands for its children; its slots
+                    // below the capacity are marked empty
+                    for (uint32_t q = at; q < B.cap && q < at + kids; q++) qout[q] = make_uint4(kNoItem, 0u, 0u, 0u);
+                    int4 rc;
+                    int32_t D;
+                    if (node_bound(S, K, B, ref, it.x, it.y, it.z, (int)it.w, rc, D)) scatter_bound(B, rc, D);
+                }
+            }
+        }
         g.sync();
     }
-    for (uint32_t i = gtid; i < tiles; i += stride) {
-        const uint32_t ty = i / (uint32_t)B.tiles_x, tx = i - ty * (uint32_t)B.tiles_x;
-        int32_t m = B.dn[i];
-        for (int L = 1; L < kBeamPyr; L++) {
-            const uint32_t wl = ((uint32_t)B.tiles_x + (1u << L) - 1) >> L;
-            m = min(m, B.pyr[B.poff[L] + (ty >> L) * wl + (tx >> L)]);
-        }
-        B.dn[i] = m;
-    }
+    __syncthreads();
+    if (threadIdx.x < kBeamLevels && hist[threadIdx.x]) atomicAdd(&B.hist[threadIdx.x], hist[threadIdx.x]);
 }
 
 }  // namespace
@@ -346,14 +354,7 @@ int aokk_beam(const SceneDev* S, const CamDev* C, const ChunkRef* frame, const B
                        A[2] * (A[3] * A[7] - A[4] * A[6]);
     double nrm = 0.0;
     for (int i = 0; i < 9; i++) nrm = fmax(nrm, fabs(A[i]));
-    const bool valid = std::isfinite(det) && fabs(det) > 1e-6 * nrm * nrm * nrm;
-    if (!valid) {
-        // an unusable camera matrix: bound 0 everywhere (nothing is skipped)
-        if (cudaMemsetAsync(B->dn, 0, (size_t)B->tiles_x * B->tiles_y * 4, st) != cudaSuccess ||
-            cudaMemsetAsync(B->cnt, 0, kBeamLevels * 4, st) != cudaSuccess)
-            return AOK_E_CUDA;
-        return AOK_OK;
-    }
+    if (!(std::isfinite(det) && fabs(det) > 1e-6 * nrm * nrm * nrm)) return AOK_E_INVALID;  // caller: bound 0
     const double id = 1.0 / det;
     double Ai[9];
     Ai[0] = (A[4] * A[8] - A[5] * A[7]) * id;
@@ -380,19 +381,19 @@ int aokk_beam(const SceneDev* S, const CamDev* C, const ChunkRef* frame, const B
     K.H = C->H;
     for (int a = 0; a < 3; a++) K.O[a] = C->O[a];
     uint32_t nch = (uint32_t)(S->grid[0] * S->grid[1] * S->grid[2]);
-    int levels = S->mlog - 1;  // root size 2^mlog down to LOD-0 leaves of size 4
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, beam_kernel, kBeamThreads, 0) != cudaSuccess ||
         per_sm < 1)
         return AOK_E_CUDA;
     const unsigned grid = (unsigned)(sms > 0 ? sms : 1) * (unsigned)(per_sm < kBeamBlocksPerSM ? per_sm : kBeamBlocksPerSM);
+    // queue counts and the walk histogram (cnt and hist are adjacent)
+    if (cudaMemsetAsync(B->cnt, 0, 2 * kBeamLevels * sizeof(uint32_t), st) != cudaSuccess) return AOK_E_CUDA;
     SceneDev s_ = *S;
     BeamDev b_ = *B;
-    int32_t fill = INT_MAX;
-    void* args[] = {&s_, &K, (void*)&frame, &b_, &levels, &nch, &fill};
+    void* args[] = {&s_, &K, (void*)&frame, &b_, &nch};
     if (cudaLaunchCooperativeKernel((const void*)beam_kernel, grid, kBeamThreads, args, 0, st) != cudaSuccess)
         return AOK_E_CUDA;
-    return cudaGetLastError() == cudaSuccess ? AOK_OK : AOK_E_CUDA;
+    return AOK_OK;
 }
 
 }  // extern "C"

@@ -87,12 +87,17 @@ constexpr int kBeamTileW = 8, kBeamTileH = 4;
 constexpr int kBeamLevels = 16;  // queue counters (node levels of a 512^3 chunk: 8)
 constexpr int kBeamPyr = 7;      // bound pyramid levels (level 0: the tiles)
 struct BeamDev {
-    int32_t* dn;             // [tiles] bound in origin numerator units (2^-kFix); INT32_MAX: nothing solid
-    int32_t* pyr;            // levels 1 .. kBeamPyr-1 of the bound pyramid: cells of 2^L x 2^L tiles, folded into dn
+    // bound entries: (pass tag << 32) | bound in origin numerator units (2^-kFix);
+    // an entry whose tag is not this pass's means "no solid voxel" (INT32_MAX)
+    unsigned long long* dn;  // [tiles] level 0 of the bound pyramid
+    unsigned long long* pyr; // levels 1 .. kBeamPyr-1: cells of 2^L x 2^L tiles
     int32_t poff[8];         // offset of level L in pyr (poff[kBeamPyr]: total)
     uint4* q[2];             // node queues of alternate levels: {chunk, node, cell x | y << 10 | z << 20, log2 size}
-    uint32_t* cnt;           // [kBeamLevels] items pushed per level
+    uint32_t* cnt;           // [kBeamLevels] items queued per level
+    uint32_t* hist;          // [kBeamLevels] nodes walked per depth below the region root
     uint32_t cap;            // queue capacity in items
+    uint32_t tag;            // this pass's tag: decreases from pass to pass
+    int32_t off;             // 1: bound 0 everywhere (no usable projection)
     int32_t tiles_x, tiles_y;
 };
 
@@ -147,8 +152,9 @@ extern "C" {
 int aokk_select(const aok::SceneDev* s, const aok::CamDev* c, aok::ChunkRef* frame, int8_t* lod_out,
                 uint8_t* vis_out, uint32_t* n_visible, void* stream);
 int aokk_cast(const aok::SceneDev* s, const aok::CamDev* c, const aok::ChunkRef* frame, uint4* hit, float* t,
-              uint32_t* counts, void* stream, const aok::CheckDev* ck, const int32_t* beam = nullptr);
-// Beam pass (aok_beam.cu): fills B->dn for the frame table `frame`.
+              uint32_t* counts, void* stream, const aok::CheckDev* ck, const aok::BeamDev* beam = nullptr);
+// Beam pass (aok_beam.cu): bounds tagged B->tag for the frame table `frame`;
+// AOK_E_INVALID if the camera matrix has no usable inverse (bounds unusable).
 int aokk_beam(const aok::SceneDev* S, const aok::CamDev* C, const aok::ChunkRef* frame, const aok::BeamDev* B,
               uint32_t expand_tiles, int min_log2, int sms, void* stream);
 int aokk_ray_dirs(const aok::CamDev* c, float* dirs, void* stream);

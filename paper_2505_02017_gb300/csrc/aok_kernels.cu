@@ -109,13 +109,25 @@ __global__ void select_batch_kernel(const __grid_constant__ BatchParams P) {
 template <bool COUNT, bool BEAM = false>
 __global__ void __launch_bounds__(128) cast_kernel(SceneDev S, CamDev C, const ChunkRef* __restrict__ frame,
                                                    uint4* __restrict__ out_hit, float* __restrict__ out_t,
-                                                   uint32_t* __restrict__ counts, const int32_t* __restrict__ beam) {
+                                                   uint32_t* __restrict__ counts, BeamDev beam) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int px = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
     const int py = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
     if (px >= C.W || py >= C.H) return;
     int32_t Dn = 0;
-    if (BEAM) Dn = __ldg(beam + (size_t)(py / kBeamTileH) * ((C.W + kBeamTileW - 1) / kBeamTileW) + px / kBeamTileW);
+    if (BEAM && !beam.off) {
+        // the tile's bound: the minimum over its cells of the bound pyramid
+        // (entries of earlier passes carry other tags: nothing there)
+        const uint32_t tx = (uint32_t)(px / kBeamTileW), ty = (uint32_t)(py / kBeamTileH);
+        const unsigned long long tag = (unsigned long long)beam.tag << 32;
+        unsigned long long v = __ldcg(beam.dn + (size_t)ty * beam.tiles_x + tx);
+#pragma unroll
+        for (int L = 1; L < kBeamPyr; L++) {
+            const uint32_t wl = ((uint32_t)beam.tiles_x + (1u << L) - 1) >> L;
+            v = min(v, __ldcg(beam.pyr + beam.poff[L] + (ty >> L) * wl + (tx >> L)));
+        }
+        Dn = (v & 0xFFFFFFFF00000000ull) == tag ? (int32_t)(uint32_t)v : INT_MAX;
+    }
     trace_pixel<COUNT, false, BEAM>(S, C, frame, px, py, out_hit, out_t, counts, (size_t)py * C.W + px, nullptr, Dn);
 }
 
@@ -233,19 +245,19 @@ int aokk_select(const SceneDev* s, const CamDev* c, ChunkRef* frame, int8_t* lod
 }
 
 int aokk_cast(const SceneDev* s, const CamDev* c, const ChunkRef* frame, uint4* hit, float* t, uint32_t* counts,
-              void* stream, const CheckDev* ck, const int32_t* beam) {
+              void* stream, const CheckDev* ck, const BeamDev* beam) {
     dim3 grid((c->W + 15) / 16, (c->H + 7) / 8);
     const cudaStream_t st = (cudaStream_t)stream;
     if (ck && !counts)
         cast_kernel_checked<<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, *ck);
     else if (counts && beam)
-        cast_kernel<true, true><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, counts, beam);
+        cast_kernel<true, true><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, counts, *beam);
     else if (counts)
-        cast_kernel<true><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, counts, nullptr);
+        cast_kernel<true><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, counts, BeamDev{});
     else if (beam)
-        cast_kernel<false, true><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, nullptr, beam);
+        cast_kernel<false, true><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, nullptr, *beam);
     else
-        cast_kernel<false><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, nullptr, nullptr);
+        cast_kernel<false><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, nullptr, BeamDev{});
     return status_of(cudaGetLastError());
 }
 
@@ -426,7 +438,7 @@ int aokk_render_noalloc(const SceneDev* s, const CamDev* c, uint4* hit, float* t
     const cudaStream_t st = (cudaStream_t)stream;
     select_kernel<<<(unsigned)((nch + 127) / 128), 128, 0, st>>>(*s, *c, frame, nullptr, nullptr, nullptr);
     dim3 grid((c->W + 15) / 16, (c->H + 7) / 8);
-    cast_kernel<false><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, nullptr, nullptr);
+    cast_kernel<false><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, nullptr, BeamDev{});
     return status_of(cudaGetLastError());
 }
 

@@ -816,21 +816,27 @@ static int ensure_beam(aok_ctx* ctx, int32_t W, int32_t H) {
     int32_t poff[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int L = 1; L < kBeamPyr; L++)
         poff[L + 1] = poff[L] + ((tx + (1 << L) - 1) >> L) * ((ty + (1 << L) - 1) >> L);
-    const size_t sd = al((size_t)tx * ty * 4), sdc = al((size_t)poff[kBeamPyr] * 4), sq = al((size_t)kBeamCap * 16),
-                 sc = al(kBeamLevels * 4);
+    const size_t sd = al((size_t)tx * ty * 8), sdc = al((size_t)poff[kBeamPyr] * 8), sq = al((size_t)kBeamCap * 16),
+                 sc = al(2 * kBeamLevels * 4);
     void* block = nullptr;
-    const int st = dev_alloc(ctx, &block, sd + sdc + 2 * sq + sc);
+    int st = dev_alloc(ctx, &block, sd + sdc + 2 * sq + sc);
     if (st) return st;
     char* p = (char*)block;
-    b.dev.dn = (int32_t*)p;
-    b.dev.pyr = (int32_t*)(p + sd);
+    b.dev.dn = (unsigned long long*)p;
+    b.dev.pyr = (unsigned long long*)(p + sd);
     for (int L = 0; L < 8; L++) b.dev.poff[L] = poff[L];
     b.dev.q[0] = (uint4*)(p + sd + sdc);
     b.dev.q[1] = (uint4*)(p + sd + sdc + sq);
     b.dev.cnt = (uint32_t*)(p + sd + sdc + 2 * sq);
+    b.dev.hist = b.dev.cnt + kBeamLevels;
     b.dev.cap = kBeamCap;
     b.dev.tiles_x = tx;
     b.dev.tiles_y = ty;
+    // no entry carries a pass tag yet (tags count down from 0xFFFFFFFE)
+    if (cudaMemset(p, 0xFF, sd + sdc) != cudaSuccess) {
+        dev_free(ctx, block, sd + sdc + 2 * sq + sc);
+        return cuda_status(ctx, cudaGetLastError());
+    }
     b.block = block;
     b.bytes = sd + sdc + 2 * sq + sc;
     b.W = W;
@@ -845,7 +851,21 @@ static int run_beam(aok_ctx* ctx, uint32_t scene, Scene* sc, const SceneDev& sd,
     if (st) return st;
     BeamState& b = ctx->beam;
     b.valid = false;
+    if (++b.passes >= 0xFFFFFFF0u) {
+        // tags are about to wrap: clear every entry first
+        const cudaStream_t s = (cudaStream_t)stream;
+        if (cudaMemsetAsync(b.dev.dn, 0xFF, (size_t)b.dev.tiles_x * b.dev.tiles_y * 8, s) != cudaSuccess ||
+            cudaMemsetAsync(b.dev.pyr, 0xFF, (size_t)b.dev.poff[kBeamPyr] * 8, s) != cudaSuccess)
+            return AOK_E_CUDA;
+        b.passes = 1;
+    }
+    b.dev.tag = 0xFFFFFFFFu - b.passes;
+    b.dev.off = 0;
     st = aokk_beam(&sd, &cd, sc->d_frame, &b.dev, ctx->beam_refine, ctx->beam_min_log2, ctx->sm_count, stream);
+    if (st == AOK_E_INVALID) {
+        b.dev.off = 1;  // no usable projection: bound 0 everywhere, nothing is skipped
+        st = AOK_OK;
+    }
     if (st) return st;
     b.valid = true;
     b.scene = scene;
@@ -871,13 +891,13 @@ static int cast_single(aok_ctx* ctx, uint32_t scene, Scene* sc, const SceneDev& 
                        const aok_frame* frame, uint32_t* counts, void* stream) {
     CheckDev ck;
     const CheckDev* ckp = check_dev(ctx, sc, &ck);
-    const int32_t* beam = nullptr;
+    const BeamDev* beam = nullptr;
     if (ctx->beam_on && !ckp && (uint64_t)cd.W * (uint64_t)cd.H >= ctx->beam_min_pixels) {
         if (!beam_fresh(ctx, scene, sc, cd)) {
             const int st = run_beam(ctx, scene, sc, sd, cd, stream);
             if (st) return st;
         }
-        beam = ctx->beam.dev.dn;
+        beam = &ctx->beam.dev;
     }
     return aokk_cast(&sd, &cd, sc->d_frame, (uint4*)frame->hit, frame->t, counts, stream, ckp, beam);
 }
@@ -1089,9 +1109,28 @@ int aok_beam_info(aok_ctx* ctx, int32_t* bounds, uint64_t n_bounds, uint32_t* le
     if (bounds && n_bounds < n) return AOK_E_INVALID;
     cudaSetDevice(ctx->device);
     if (cudaDeviceSynchronize() != cudaSuccess) return cuda_status(ctx, cudaGetLastError());
-    if (bounds && cudaMemcpy(bounds, b.dev.dn, n * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
-        return cuda_status(ctx, cudaGetLastError());
-    if (level_counts && cudaMemcpy(level_counts, b.dev.cnt, kBeamLevels * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    if (bounds) {
+        // the bounds the casting kernel uses: each tile's minimum over its
+        // cells of the pyramid among entries of the last pass's tag, or 0
+        // everywhere if that pass could not project
+        std::vector<unsigned long long> lv0(n), pyr((size_t)b.dev.poff[kBeamPyr]);
+        if (cudaMemcpy(lv0.data(), b.dev.dn, n * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            (!pyr.empty() && cudaMemcpy(pyr.data(), b.dev.pyr, pyr.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess))
+            return cuda_status(ctx, cudaGetLastError());
+        const unsigned long long tag = (unsigned long long)b.dev.tag << 32;
+        const int32_t tx = b.dev.tiles_x, ty = b.dev.tiles_y;
+        for (int32_t y = 0; y < ty; y++)
+            for (int32_t x = 0; x < tx; x++) {
+                unsigned long long v = lv0[(size_t)y * tx + x];
+                for (int L = 1; L < kBeamPyr; L++) {
+                    const int32_t wl = (tx + (1 << L) - 1) >> L;
+                    v = std::min(v, pyr[(size_t)b.dev.poff[L] + (size_t)(y >> L) * wl + (x >> L)]);
+                }
+                bounds[(size_t)y * tx + x] =
+                    b.dev.off ? 0 : ((v & 0xFFFFFFFF00000000ull) == tag ? (int32_t)(uint32_t)v : INT32_MAX);
+            }
+    }
+    if (level_counts && cudaMemcpy(level_counts, b.dev.hist, kBeamLevels * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
         return cuda_status(ctx, cudaGetLastError());
     if (tiles_xy) {
         tiles_xy[0] = b.dev.tiles_x;

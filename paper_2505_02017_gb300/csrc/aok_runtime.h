@@ -95,6 +95,7 @@ struct BeamState {
     int32_t W = 0, H = 0;
     // what the bounds in dev were computed for: a scene, its selection, a camera
     bool valid = false;
+    uint32_t passes = 0;  // passes run (their tags count down)
     uint32_t scene = 0xFFFFFFFFu;
     uint64_t gen = 0;
     CamDev cam{};
