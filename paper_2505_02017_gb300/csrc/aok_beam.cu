@@ -339,8 +339,16 @@ __global__ void __launch_bounds__(kBeamThreads) beam_kernel(SceneDev S, BeamCam 
 
 extern "C" {
 
+unsigned aokk_beam_grid(int sms) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, beam_kernel, kBeamThreads, 0) != cudaSuccess ||
+        per_sm < 1)
+        return 0;
+    return (unsigned)(sms > 0 ? sms : 1) * (unsigned)(per_sm < kBeamBlocksPerSM ? per_sm : kBeamBlocksPerSM);
+}
+
 int aokk_beam(const SceneDev* S, const CamDev* C, const ChunkRef* frame, const BeamDev* B, uint32_t expand_tiles,
-              int min_log2, int sms, void* stream) {
+              int min_log2, unsigned grid, void* stream) {
     const cudaStream_t st = (cudaStream_t)stream;
     BeamCam K;
     // A = [c0, c1, -c2] with d_i = R[3i] u + R[3i+1] v - R[3i+2]
@@ -381,11 +389,6 @@ int aokk_beam(const SceneDev* S, const CamDev* C, const ChunkRef* frame, const B
     K.H = C->H;
     for (int a = 0; a < 3; a++) K.O[a] = C->O[a];
     uint32_t nch = (uint32_t)(S->grid[0] * S->grid[1] * S->grid[2]);
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, beam_kernel, kBeamThreads, 0) != cudaSuccess ||
-        per_sm < 1)
-        return AOK_E_CUDA;
-    const unsigned grid = (unsigned)(sms > 0 ? sms : 1) * (unsigned)(per_sm < kBeamBlocksPerSM ? per_sm : kBeamBlocksPerSM);
     // queue counts and the walk histogram (cnt and hist are adjacent)
     if (cudaMemsetAsync(B->cnt, 0, 2 * kBeamLevels * sizeof(uint32_t), st) != cudaSuccess) return AOK_E_CUDA;
     SceneDev s_ = *S;

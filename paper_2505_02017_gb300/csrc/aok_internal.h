@@ -156,7 +156,9 @@ int aokk_cast(const aok::SceneDev* s, const aok::CamDev* c, const aok::ChunkRef*
 // Beam pass (aok_beam.cu): bounds tagged B->tag for the frame table `frame`;
 // AOK_E_INVALID if the camera matrix has no usable inverse (bounds unusable).
 int aokk_beam(const aok::SceneDev* S, const aok::CamDev* C, const aok::ChunkRef* frame, const aok::BeamDev* B,
-              uint32_t expand_tiles, int min_log2, int sms, void* stream);
+              uint32_t expand_tiles, int min_log2, unsigned grid, void* stream);
+// Blocks of the beam pass's cooperative launch on `sms` SMs (0 on error).
+unsigned aokk_beam_grid(int sms);
 int aokk_ray_dirs(const aok::CamDev* c, float* dirs, void* stream);
 int aokk_tiles_frame(const aok::SceneDev* S, const aok::CamDev* C, const aok::ChunkRef* frame, const aok::TileDev* T,
                      uint4* hit, float* t, int sms, void* stream);

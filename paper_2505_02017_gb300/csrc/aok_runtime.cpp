@@ -803,21 +803,36 @@ static const CheckDev* check_dev(aok_ctx* ctx, const Scene* sc, CheckDev* ck) {
 
 // Beam buffers for W x H (reallocated when the size changes).
 static constexpr uint32_t kBeamCap = 1u << 20;  // queued nodes per level
+// Beam buffers for W x H: the bound arrays grow to the largest frame seen
+// and keep their place for smaller ones (entries carry their pass's tag, so a
+// change of layout between passes needs no clearing).
 static int ensure_beam(aok_ctx* ctx, int32_t W, int32_t H) {
     BeamState& b = ctx->beam;
     if (b.block && b.W == W && b.H == H) return AOK_OK;
-    if (b.block) {
-        cudaDeviceSynchronize();
-        dev_free(ctx, b.block, b.bytes);
-        b = BeamState{};
-    }
     const int32_t tx = (W + kBeamTileW - 1) / kBeamTileW, ty = (H + kBeamTileH - 1) / kBeamTileH;
     auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
     int32_t poff[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int L = 1; L < kBeamPyr; L++)
         poff[L + 1] = poff[L] + ((tx + (1 << L) - 1) >> L) * ((ty + (1 << L) - 1) >> L);
-    const size_t sd = al((size_t)tx * ty * 8), sdc = al((size_t)poff[kBeamPyr] * 8), sq = al((size_t)kBeamCap * 16),
-                 sc = al(2 * kBeamLevels * 4);
+    const size_t need_dn = al((size_t)tx * ty * 8), need_pyr = al((size_t)poff[kBeamPyr] * 8);
+    if (b.block && need_dn <= b.cap_dn && need_pyr <= b.cap_pyr) {
+        for (int L = 0; L < 8; L++) b.dev.poff[L] = poff[L];
+        b.dev.tiles_x = tx;
+        b.dev.tiles_y = ty;
+        b.W = W;
+        b.H = H;
+        b.valid = false;
+        return AOK_OK;
+    }
+    const size_t sd = std::max(need_dn, b.cap_dn), sdc = std::max(need_pyr, b.cap_pyr);
+    const uint32_t passes = b.passes;
+    if (b.block) {
+        cudaDeviceSynchronize();
+        dev_free(ctx, b.block, b.bytes);
+        b = BeamState{};
+    }
+    b.passes = passes;
+    const size_t sq = al((size_t)kBeamCap * 16), sc = al(2 * kBeamLevels * 4);
     void* block = nullptr;
     int st = dev_alloc(ctx, &block, sd + sdc + 2 * sq + sc);
     if (st) return st;
@@ -839,6 +854,10 @@ static int ensure_beam(aok_ctx* ctx, int32_t W, int32_t H) {
     }
     b.block = block;
     b.bytes = sd + sdc + 2 * sq + sc;
+    b.cap_dn = sd;
+    b.cap_pyr = sdc;
+    b.grid = aokk_beam_grid(ctx->sm_count);
+    if (!b.grid) return AOK_E_CUDA;
     b.W = W;
     b.H = H;
     return AOK_OK;
@@ -854,14 +873,14 @@ static int run_beam(aok_ctx* ctx, uint32_t scene, Scene* sc, const SceneDev& sd,
     if (++b.passes >= 0xFFFFFFF0u) {
         // tags are about to wrap: clear every entry first
         const cudaStream_t s = (cudaStream_t)stream;
-        if (cudaMemsetAsync(b.dev.dn, 0xFF, (size_t)b.dev.tiles_x * b.dev.tiles_y * 8, s) != cudaSuccess ||
-            cudaMemsetAsync(b.dev.pyr, 0xFF, (size_t)b.dev.poff[kBeamPyr] * 8, s) != cudaSuccess)
+        if (cudaMemsetAsync(b.dev.dn, 0xFF, b.cap_dn, s) != cudaSuccess ||
+            cudaMemsetAsync(b.dev.pyr, 0xFF, b.cap_pyr, s) != cudaSuccess)
             return AOK_E_CUDA;
         b.passes = 1;
     }
     b.dev.tag = 0xFFFFFFFFu - b.passes;
     b.dev.off = 0;
-    st = aokk_beam(&sd, &cd, sc->d_frame, &b.dev, ctx->beam_refine, ctx->beam_min_log2, ctx->sm_count, stream);
+    st = aokk_beam(&sd, &cd, sc->d_frame, &b.dev, ctx->beam_refine, ctx->beam_min_log2, b.grid, stream);
     if (st == AOK_E_INVALID) {
         b.dev.off = 1;  // no usable projection: bound 0 everywhere, nothing is skipped
         st = AOK_OK;

@@ -92,6 +92,8 @@ struct BeamState {
     BeamDev dev{};
     void* block = nullptr;
     size_t bytes = 0;
+    size_t cap_dn = 0, cap_pyr = 0;  // bytes of the two bound arrays (grow-only)
+    unsigned grid = 0;               // blocks of the cooperative launch
     int32_t W = 0, H = 0;
     // what the bounds in dev were computed for: a scene, its selection, a camera
     bool valid = false;
