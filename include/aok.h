@@ -508,9 +508,12 @@ int aok_set_beam(aok_ctx* ctx, int on);
  * LOD-0 voxels (defaults 8 and 2: down to the 4^3 leaves); frames of fewer
  * than min_pixels pixels cast without the pass (default 1,500,000: below
  * that the pass's fixed cost, some tens of microseconds, outweighs what it
- * saves).  Any setting gives the same output records.  AOK_E_INVALID for
+ * saves); queue_nodes caps the nodes one level of the walk may queue
+ * (0: the allocated 2^20; past the cap a node stands for its children).
+ * Any setting gives the same output records.  AOK_E_INVALID for
  * min_node_log2 outside [2, 16]. */
-int aok_beam_tune(aok_ctx* ctx, uint32_t refine_tiles, int32_t min_node_log2, uint64_t min_pixels);
+int aok_beam_tune(aok_ctx* ctx, uint32_t refine_tiles, int32_t min_node_log2, uint64_t min_pixels,
+                  uint32_t queue_nodes);
 /* The beam pass alone, for the frame table the last aok_select_chunks (or
  * render) of this scene selected and this camera: the next
  * aok_cast_selected of the same scene and camera then casts with these

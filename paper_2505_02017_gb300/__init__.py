@@ -121,7 +121,7 @@ def lib() -> ctypes.CDLL:
             "aok_set_single_view_kernel": [vp, ctypes.c_int],
             "aok_set_checked": [vp, ctypes.c_int],
             "aok_set_beam": [vp, ctypes.c_int],
-            "aok_beam_tune": [vp, u32, ctypes.c_int32, u64],
+            "aok_beam_tune": [vp, u32, ctypes.c_int32, u64, u32],
             "aok_beam_info": [vp, P(ctypes.c_int32), u64, P(u32), P(ctypes.c_int32)],
             "aok_beam_selected": [vp, u32, P(Camera), vp],
             "aok_checked_errors": [vp, P(u32)],
@@ -431,9 +431,11 @@ def set_beam(ctx: Context, on: bool):
     return check(lib().aok_set_beam(ctx.h, 1 if on else 0), "aok_set_beam")
 
 
-def beam_tune(ctx: Context, refine_tiles: int = 8, min_node_log2: int = 2, min_pixels: int = 1500000):
-    """Refinement of the beam pass's walk and the smallest frame it runs for (aok_beam_tune)."""
-    return check(lib().aok_beam_tune(ctx.h, refine_tiles, min_node_log2, min_pixels), "aok_beam_tune")
+def beam_tune(ctx: Context, refine_tiles: int = 8, min_node_log2: int = 2, min_pixels: int = 1500000,
+              queue_nodes: int = 0):
+    """Refinement of the beam pass's walk, the smallest frame it runs for and
+    the queue capacity per level (aok_beam_tune)."""
+    return check(lib().aok_beam_tune(ctx.h, refine_tiles, min_node_log2, min_pixels, queue_nodes), "aok_beam_tune")
 
 
 def beam_selected(ctx: Context, scene: Scene, cam, stream=None):

@@ -880,6 +880,7 @@ static int run_beam(aok_ctx* ctx, uint32_t scene, Scene* sc, const SceneDev& sd,
     }
     b.dev.tag = 0xFFFFFFFFu - b.passes;
     b.dev.off = 0;
+    b.dev.cap = ctx->beam_queue && ctx->beam_queue < kBeamCap ? ctx->beam_queue : kBeamCap;
     st = aokk_beam(&sd, &cd, sc->d_frame, &b.dev, ctx->beam_refine, ctx->beam_min_log2, b.grid, stream);
     if (st == AOK_E_INVALID) {
         b.dev.off = 1;  // no usable projection: bound 0 everywhere, nothing is skipped
@@ -1098,11 +1099,13 @@ int aok_set_beam(aok_ctx* ctx, int on) {
     return AOK_OK;
 }
 
-int aok_beam_tune(aok_ctx* ctx, uint32_t refine_tiles, int32_t min_node_log2, uint64_t min_pixels) {
+int aok_beam_tune(aok_ctx* ctx, uint32_t refine_tiles, int32_t min_node_log2, uint64_t min_pixels,
+                  uint32_t queue_nodes) {
     if (!ctx || min_node_log2 < 2 || min_node_log2 > 16) return AOK_E_INVALID;
     ctx->beam_refine = refine_tiles;
     ctx->beam_min_log2 = min_node_log2;
     ctx->beam_min_pixels = min_pixels;
+    ctx->beam_queue = queue_nodes;
     return AOK_OK;
 }
 

@@ -139,6 +139,7 @@ struct aok_ctx {
     uint32_t beam_refine = 8;  // refine nodes spanning more tiles than this ...
     int beam_min_log2 = 2;     // ... whose side is above 2^this LOD-0 voxels
     uint64_t beam_min_pixels = 1500000;  // smaller frames cast without the pass
+    uint32_t beam_queue = 0;             // nodes a queue level may hold (0: the allocated 2^20)
     aok::HostPipe pipe;
     int checked = 0;  // single-view casts check every pool index (error word: d_counter[8])
     std::mutex upload_mu;  // the staging buffer and the copy stream: one upload at a time

@@ -29,7 +29,7 @@ INT32_MAX = 2**31 - 1
 @pytest.fixture(scope="module")
 def ctx():
     c = aok.Context(0)
-    aok.beam_tune(c, 8, 2, 0)  # the pass on every frame size
+    aok.beam_tune(c, 8, 2, 0, 0)  # the pass on every frame size
     yield c
     aok.set_beam(c, False)
     c.close()
@@ -233,6 +233,30 @@ def test_beam_selected_then_cast(ctx):
     assert same(ref_b, (hit, t))
 
 
+def test_queue_overflow_same_output(ctx):
+    """Queues far too small for the walk: parents stand in for the children
+    that do not fit, the bounds stay below every hit, the frame is unchanged."""
+    w, sc, _ = scene_for(ctx, MED64)
+    cam = sg.ground_camera(w, 9, 203, 117, z_lo=4, z_hi=40)
+    ref = render(ctx, sc, cam, 1.5, False)
+    try:
+        for cap in (1, 7, 40, 300):
+            aok.beam_tune(ctx, 0, 2, 0, cap)  # refine everything, tiny queues
+            out = render(ctx, sc, cam, 1.5, True)
+            assert same(ref, out), cap
+            b, _ = aok.beam_info(ctx)
+            g = decode(*out)
+            O = np.round(cam.origin.astype(np.float64) * 4096).astype(np.int64)
+            py, px = np.divmod(np.arange(cam.W * cam.H), cam.W)
+            h = g["hit"] == 1
+            lo = np.stack([g["x"], g["y"], g["z"]], 1).astype(np.int64) * 4096 - O
+            hi = lo + (np.int64(4096) << g["lod"].astype(np.int64))[:, None]
+            d = np.maximum(np.maximum(lo, -hi), 0).max(1)
+            assert (b[py // 4, px // 8].astype(np.int64)[h] <= d[h]).all(), cap
+    finally:
+        aok.beam_tune(ctx, 8, 2, 0, 0)
+
+
 def test_refinement_settings_same_output(ctx):
     """Any refinement setting gives the frame of the plain march."""
     w, sc, _ = scene_for(ctx, MED64)
@@ -240,7 +264,7 @@ def test_refinement_settings_same_output(ctx):
     ref = render(ctx, sc, cam, 1.5, False)
     try:
         for refine, lg in ((0, 2), (4, 2), (64, 3), (1 << 30, 9), (8, 16)):
-            aok.beam_tune(ctx, refine, lg, 0)
+            aok.beam_tune(ctx, refine, lg, 0, 0)
             out = render(ctx, sc, cam, 1.5, True)
             assert same(ref, out), (refine, lg)
             check_bounds(ctx, cam, out)
@@ -249,8 +273,8 @@ def test_refinement_settings_same_output(ctx):
         b0, _ = aok.beam_info(ctx)
         cam2 = sg.ground_camera(w, 4, 203, 117, z_lo=4, z_hi=40)
         ref2 = render(ctx, sc, cam2, 1.5, False)
-        aok.beam_tune(ctx, 8, 2, cam2.W * cam2.H + 1)
+        aok.beam_tune(ctx, 8, 2, cam2.W * cam2.H + 1, 0)
         assert same(ref2, render(ctx, sc, cam2, 1.5, True))
         assert (aok.beam_info(ctx)[0] == b0).all()
     finally:
-        aok.beam_tune(ctx, 8, 2, 0)
+        aok.beam_tune(ctx, 8, 2, 0, 0)
