@@ -45,6 +45,7 @@
 #include <climits>
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 
 #include <cooperative_groups.h>
 
@@ -60,18 +61,6 @@ constexpr int kBeamBlocksPerSM = 2;    // at most this many blocks per SM (fewer
 constexpr double kNearS = 1.0 / 16.0;  // camera-depth plane the projection clips at
 constexpr uint32_t kNoItem = 0xFFFFFFFFu;  // an empty queue slot
 
-// The camera as the beam pass projects with it (host-computed).
-struct BeamCam {
-    float Af[9];       // row-major inverse of A = [R col 0, R col 1, -R col 2] (d = A (u, v, 1)), rounded to FP32
-    float U, V;        // u and v at the screen edges: tan_half * W / H, tan_half
-    float near_dn;     // numerator units: boxes closer than this cover every tile
-    float view_num;    // > 0: boxes farther than this (Euclidean, numerator units) are dropped
-    uint32_t expand;   // refine nodes whose rectangle spans more tiles than this
-    int32_t smin;      // ... and whose side is above 2^smin LOD-0 voxels
-    int32_t W, H;
-    int32_t O[3];
-};
-
 // Screen rectangle [x, z) x [y, w) of tiles a box (relative to the origin)
 // can cover from its part at camera depth s >= kNearS; false if none.
 // q = Af p in FP32 errs by at most dl = 8 2^-24 max_i sum_j |Af_ij| |p_j|
@@ -80,7 +69,7 @@ struct BeamCam {
 // box's), widened by the error that dl and the division carry; a box that
 // straddles it by u = q_x / q_s over q_x in [X0, X1] and q_s in [kNearS, S1],
 // each widened by dl.  Then a 0.5 pixel margin for the FP32 pixel rays.
-__device__ bool box_rect(const BeamCam& K, const BeamDev& B, const float lo[3], const float hi[3], int4& rc) {
+__device__ bool box_rect(const BeamView& K, const float lo[3], const float hi[3], int4& rc) {
     float pm[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) pm[a] = fmaxf(fabsf(lo[a]), fabsf(hi[a]));
@@ -128,8 +117,8 @@ __device__ bool box_rect(const BeamCam& K, const BeamDev& B, const float lo[3], 
     if (!(x1 >= 0.0f) || !(y1 >= 0.0f) || !(x0 < (float)K.W) || !(y0 < (float)K.H)) return false;
     rc.x = (int)fmaxf(floorf(x0 * (1.0f / kBeamTileW)), 0.0f);
     rc.y = (int)fmaxf(floorf(y0 * (1.0f / kBeamTileH)), 0.0f);
-    rc.z = (int)fminf(floorf(x1 * (1.0f / kBeamTileW)) + 1.0f, (float)B.tiles_x);
-    rc.w = (int)fminf(floorf(y1 * (1.0f / kBeamTileH)) + 1.0f, (float)B.tiles_y);
+    rc.z = (int)fminf(floorf(x1 * (1.0f / kBeamTileW)) + 1.0f, (float)K.tiles_x);
+    rc.w = (int)fminf(floorf(y1 * (1.0f / kBeamTileH)) + 1.0f, (float)K.tiles_y);
     return rc.z > rc.x && rc.w > rc.y;
 }
 
@@ -160,9 +149,9 @@ __device__ __forceinline__ void leaf_extent(uint64_t m, int lo[3], int hi[3]) {
 // A node's box (chunk-local cell clipped to the region's AABB, or a leaf's
 // set voxels), its L-inf distance from the origin and screen rectangle.
 // Returns false if the node cannot meet any pixel ray.
-__device__ __forceinline__ bool node_bound(const SceneDev& S, const BeamCam& K, const BeamDev& B, const ChunkRef& ref,
-                                           uint32_t chunk, uint32_t node, uint32_t packed_cell, int s, int4& rc,
-                                           int32_t& D) {
+__device__ __forceinline__ bool node_bound(const BeamView& V, const ChunkRef& ref, uint32_t chunk, uint32_t node,
+                                           uint32_t packed_cell, int s, int4& rc, int32_t& D) {
+    const SceneDev& S = V.scene;
     const int lod = (int)ref.lod;
     const bool leaf = s == lod + 2;
     int32_t u[3];
@@ -195,22 +184,22 @@ __device__ __forceinline__ bool node_bound(const SceneDev& S, const BeamCam& K, 
 #pragma unroll
     for (int a = 0; a < 3; a++) {
         empty = empty || blo[a] >= bhi[a];
-        wl[a] = (((u[a] << S.mlog) + blo[a]) << kFix) - K.O[a];
-        wh[a] = (((u[a] << S.mlog) + bhi[a]) << kFix) - K.O[a];
+        wl[a] = (((u[a] << S.mlog) + blo[a]) << kFix) - V.O[a];
+        wh[a] = (((u[a] << S.mlog) + bhi[a]) << kFix) - V.O[a];
         const int32_t da = wl[a] > 0 ? wl[a] : (wh[a] < 0 ? -wh[a] : 0);
         dmax = max(dmax, da);
         e2 += (float)da * (float)da;
     }
     D = dmax;
-    if (empty || (K.view_num > 0.0f && sqrtf(e2) > K.view_num)) return false;
-    if ((float)D < K.near_dn) {
-        rc = make_int4(0, 0, B.tiles_x, B.tiles_y);
+    if (empty || (V.view_num > 0.0f && sqrtf(e2) > V.view_num)) return false;
+    if ((float)D < V.near_dn) {
+        rc = make_int4(0, 0, V.tiles_x, V.tiles_y);
         return true;
     }
     const float sc = 1.0f / (1 << kFix);
     const float lf[3] = {(float)wl[0] * sc, (float)wl[1] * sc, (float)wl[2] * sc};
     const float hf[3] = {(float)wh[0] * sc, (float)wh[1] * sc, (float)wh[2] * sc};
-    return box_rect(K, B, lf, hf, rc);
+    return box_rect(V, lf, hf, rc);
 }
 
 // Atomic minimum without a return value (a reduction the SM does not wait for).
@@ -218,20 +207,20 @@ __device__ __forceinline__ void red_min_u64(unsigned long long* p, unsigned long
     asm volatile("red.global.min.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// D into the finest level L of the bound pyramid (level 0: the tiles; level
-// L: cells of 2^L x 2^L tiles) at which the rectangle spans at most 16 cells
-// (or the coarsest); the casting kernel takes each tile's minimum over its
-// cells.
-__device__ __forceinline__ void scatter_bound(const BeamDev& B, const int4& rc, int32_t D) {
+// D into the finest level L of the view's bound pyramid (level 0: the tiles;
+// level L: cells of 2^L x 2^L tiles) at which the rectangle spans at most 16
+// cells (or the coarsest); the casting kernels take each tile's minimum over
+// its cells.
+__device__ __forceinline__ void scatter_bound(const BeamView& V, uint32_t tag, const int4& rc, int32_t D) {
     int L = 0;
     int x0 = rc.x, y0 = rc.y, x1 = rc.z - 1, y1 = rc.w - 1;
     while (L < kBeamPyr - 1 && (x1 - x0 + 1) * (y1 - y0 + 1) > 16) {
         L++;
         x0 >>= 1; y0 >>= 1; x1 >>= 1; y1 >>= 1;
     }
-    unsigned long long* lv = L == 0 ? B.dn : B.pyr + B.poff[L];
-    const int wl = (B.tiles_x + (1 << L) - 1) >> L;
-    const unsigned long long v = ((unsigned long long)B.tag << 32) | (uint32_t)D;
+    unsigned long long* lv = V.bounds + beam_level_offset((uint32_t)V.tiles_x, (uint32_t)V.tiles_y, L);
+    const int wl = (V.tiles_x + (1 << L) - 1) >> L;
+    const unsigned long long v = ((unsigned long long)tag << 32) | (uint32_t)D;
     for (int y = y0; y <= y1; y++)
         for (int x = x0; x <= x1; x++) red_min_u64(&lv[(size_t)y * wl + x], v);
 }
@@ -255,13 +244,12 @@ __device__ __forceinline__ uint32_t node_children(const SceneDev& S, uint32_t no
 }
 
 // The whole pass in one cooperative launch (every block resident): the
-// levels of the walk with a grid-wide barrier after each, ending at the first
-// level that queued nothing.  Level 0 takes the frame table's regions; every
-// lane of a warp runs the same iterations (the queue reservation is
-// warp-wide).  Bounds carry the pass's tag, so nothing has to be reset
-// before the walk or folded after it.
-__global__ void __launch_bounds__(kBeamThreads) beam_kernel(SceneDev S, BeamCam K, const ChunkRef* __restrict__ frame,
-                                                            BeamDev B, uint32_t n_regions) {
+// levels of the walk over all views with a grid-wide barrier after each,
+// ending at the first level that queued nothing.  Level 0 takes every view's
+// chunk regions; every lane of a warp runs the same iterations (the queue
+// reservation is warp-wide).  Bounds carry the pass's tag, so nothing has to
+// be reset before the walk or folded after it.
+__global__ void __launch_bounds__(kBeamThreads) beam_kernel(const __grid_constant__ BeamBatch P) {
     cg::grid_group g = cg::this_grid();
     __shared__ uint32_t hist[kBeamLevels];
     const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
@@ -269,35 +257,49 @@ __global__ void __launch_bounds__(kBeamThreads) beam_kernel(SceneDev S, BeamCam 
     if (threadIdx.x < kBeamLevels) hist[threadIdx.x] = 0;
     __syncthreads();
     for (int level = 0; level < kBeamLevels - 1; level++) {
-        const uint32_t n = level == 0 ? n_regions : min(*(volatile uint32_t*)&B.cnt[level], B.cap);
+        const uint32_t n = level == 0 ? P.n_regions : min(*(volatile uint32_t*)&P.cnt[level], P.cap);
         if (n == 0) break;  // the same value in every thread after the barrier
-        const uint4* __restrict__ qin = B.q[level & 1];
-        uint4* __restrict__ qout = B.q[(level + 1) & 1];
+        const uint4* __restrict__ qin = P.q[level & 1];
+        uint4* __restrict__ qout = P.q[(level + 1) & 1];
         for (uint32_t base = gtid & ~31u; base < n; base += stride) {
             const uint32_t i = base + (uint32_t)lane;
             uint32_t kids = 0, ch[8], cc[8];
             uint4 it = make_uint4(kNoItem, 0u, 0u, 0u);
+            uint32_t vi = 0;
             ChunkRef ref;
             if (i < n) {
                 if (level == 0) {
-                    ref = frame[i];
-                    if (ref.root != kNone) it = make_uint4(i, ref.root, 0u, (uint32_t)S.mlog);
+                    // the view holding region item i: the last with region_begin <= i
+                    uint32_t lo = 0, hi = P.n_views - 1;
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi + 1) >> 1;
+                        if (P.v[mid].region_begin <= i) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    vi = lo;
+                    const uint32_t r = i - P.v[vi].region_begin;
+                    ref = P.v[vi].frame[r];
+                    if (ref.root != kNone) it = make_uint4(r, ref.root, 0u, (uint32_t)P.v[vi].scene.mlog | (vi << 8));
                 } else {
                     it = qin[i];
-                    if (it.x != kNoItem) ref = frame[it.x];
+                    if (it.x != kNoItem) {
+                        vi = it.w >> 8;
+                        ref = P.v[vi].frame[it.x];
+                    }
                 }
             }
+            const BeamView& V = P.v[vi];
             if (it.x != kNoItem) {
-                const int s = (int)it.w, lod = (int)ref.lod;
-                atomicAdd(&hist[min(S.mlog - s, kBeamLevels - 1)], 1u);
+                const int s = (int)(it.w & 0xFFu), lod = (int)ref.lod;
+                atomicAdd(&hist[min(V.scene.mlog - s, kBeamLevels - 1)], 1u);
                 int4 rc;
                 int32_t D;
-                if (node_bound(S, K, B, ref, it.x, it.y, it.z, s, rc, D)) {
+                if (node_bound(V, ref, it.x, it.y, it.z, s, rc, D)) {
                     const uint32_t area = (uint32_t)(rc.z - rc.x) * (uint32_t)(rc.w - rc.y);
-                    if (s > lod + 2 && area > K.expand && s > K.smin)
-                        kids = node_children(S, it.y, it.z, s, ch, cc);
+                    if (s > lod + 2 && area > P.expand && s > P.smin)
+                        kids = node_children(V.scene, it.y, it.z, s, ch, cc);
                     else
-                        scatter_bound(B, rc, D);
+                        scatter_bound(V, P.tag, rc, D);
                 }
             }
             // queue the children: one reservation per warp
@@ -310,29 +312,29 @@ __global__ void __launch_bounds__(kBeamThreads) beam_kernel(SceneDev S, BeamCam 
             const uint32_t total = __shfl_sync(0xFFFFFFFFu, pre, 31);
             uint32_t wbase = 0;
             if (total) {
-                if (lane == 31) wbase = atomicAdd(&B.cnt[level + 1], total);
+                if (lane == 31) wbase = atomicAdd(&P.cnt[level + 1], total);
                 wbase = __shfl_sync(0xFFFFFFFFu, wbase, 31);
             }
             if (kids) {
                 const uint32_t at = wbase + pre - kids;
-                if (at + kids <= B.cap) {
+                if (at + kids <= P.cap) {
 #pragma unroll
                     for (int q = 0; q < 8; q++)
                         if ((uint32_t)q < kids) qout[at + q] = make_uint4(it.x, ch[q], cc[q], it.w - 1);
                 } else {
                     // queue full: this node stands for its children; its slots
                     // below the capacity are marked empty
-                    for (uint32_t q = at; q < B.cap && q < at + kids; q++) qout[q] = make_uint4(kNoItem, 0u, 0u, 0u);
+                    for (uint32_t q = at; q < P.cap && q < at + kids; q++) qout[q] = make_uint4(kNoItem, 0u, 0u, 0u);
                     int4 rc;
                     int32_t D;
-                    if (node_bound(S, K, B, ref, it.x, it.y, it.z, (int)it.w, rc, D)) scatter_bound(B, rc, D);
+                    if (node_bound(V, ref, it.x, it.y, it.z, (int)(it.w & 0xFFu), rc, D)) scatter_bound(V, P.tag, rc, D);
                 }
             }
         }
         g.sync();
     }
     __syncthreads();
-    if (threadIdx.x < kBeamLevels && hist[threadIdx.x]) atomicAdd(&B.hist[threadIdx.x], hist[threadIdx.x]);
+    if (threadIdx.x < kBeamLevels && hist[threadIdx.x]) atomicAdd(&P.hist[threadIdx.x], hist[threadIdx.x]);
 }
 
 }  // namespace
@@ -347,10 +349,8 @@ unsigned aokk_beam_grid(int sms) {
     return (unsigned)(sms > 0 ? sms : 1) * (unsigned)(per_sm < kBeamBlocksPerSM ? per_sm : kBeamBlocksPerSM);
 }
 
-int aokk_beam(const SceneDev* S, const CamDev* C, const ChunkRef* frame, const BeamDev* B, uint32_t expand_tiles,
-              int min_log2, unsigned grid, void* stream) {
-    const cudaStream_t st = (cudaStream_t)stream;
-    BeamCam K;
+bool aokk_beam_view(const SceneDev* S, const CamDev* C, const ChunkRef* frame, unsigned long long* bounds,
+                    BeamView* out) {
     // A = [c0, c1, -c2] with d_i = R[3i] u + R[3i+1] v - R[3i+2]
     double A[9];
     for (int i = 0; i < 3; i++) {
@@ -362,7 +362,7 @@ int aokk_beam(const SceneDev* S, const CamDev* C, const ChunkRef* frame, const B
                        A[2] * (A[3] * A[7] - A[4] * A[6]);
     double nrm = 0.0;
     for (int i = 0; i < 9; i++) nrm = fmax(nrm, fabs(A[i]));
-    if (!(std::isfinite(det) && fabs(det) > 1e-6 * nrm * nrm * nrm)) return AOK_E_INVALID;  // caller: bound 0
+    if (!(std::isfinite(det) && fabs(det) > 1e-6 * nrm * nrm * nrm)) return false;
     const double id = 1.0 / det;
     double Ai[9];
     Ai[0] = (A[4] * A[8] - A[5] * A[7]) * id;
@@ -374,12 +374,15 @@ int aokk_beam(const SceneDev* S, const CamDev* C, const ChunkRef* frame, const B
     Ai[6] = (A[3] * A[7] - A[4] * A[6]) * id;
     Ai[7] = (A[1] * A[6] - A[0] * A[7]) * id;
     Ai[8] = (A[0] * A[4] - A[1] * A[3]) * id;
+    BeamView& K = *out;
+    std::memset(&K, 0, sizeof(K));
+    K.scene = *S;
+    K.frame = frame;
+    K.bounds = bounds;
     for (int i = 0; i < 9; i++) K.Af[i] = (float)Ai[i];
     const double U = (double)C->tan_half * (double)C->W / (double)C->H, V = (double)C->tan_half;
     K.U = (float)U;
     K.V = (float)V;
-    K.expand = expand_tiles;
-    K.smin = min_log2;
     // largest |d| component over the screen, with slack for the FP32 ray arithmetic
     double dmax = 0.0;
     for (int i = 0; i < 3; i++) dmax = fmax(dmax, fabs(A[3 * i]) * U + fabs(A[3 * i + 1]) * V + fabs(A[3 * i + 2]));
@@ -387,13 +390,18 @@ int aokk_beam(const SceneDev* S, const CamDev* C, const ChunkRef* frame, const B
     K.view_num = S->view_dist > 0.0f ? (float)(((double)S->view_dist * 1.00001 + 1.0) * (double)(1 << kFix)) : 0.0f;
     K.W = C->W;
     K.H = C->H;
+    K.tiles_x = (C->W + kBeamTileW - 1) / kBeamTileW;
+    K.tiles_y = (C->H + kBeamTileH - 1) / kBeamTileH;
     for (int a = 0; a < 3; a++) K.O[a] = C->O[a];
-    uint32_t nch = (uint32_t)(S->grid[0] * S->grid[1] * S->grid[2]);
+    return true;
+}
+
+int aokk_beam_run(const BeamBatch* P, unsigned grid, void* stream) {
+    const cudaStream_t st = (cudaStream_t)stream;
+    if (P->n_views == 0) return AOK_OK;
     // queue counts and the walk histogram (cnt and hist are adjacent)
-    if (cudaMemsetAsync(B->cnt, 0, 2 * kBeamLevels * sizeof(uint32_t), st) != cudaSuccess) return AOK_E_CUDA;
-    SceneDev s_ = *S;
-    BeamDev b_ = *B;
-    void* args[] = {&s_, &K, (void*)&frame, &b_, &nch};
+    if (cudaMemsetAsync(P->cnt, 0, 2 * kBeamLevels * sizeof(uint32_t), st) != cudaSuccess) return AOK_E_CUDA;
+    void* args[] = {(void*)P};
     if (cudaLaunchCooperativeKernel((const void*)beam_kernel, grid, kBeamThreads, args, 0, st) != cudaSuccess)
         return AOK_E_CUDA;
     return AOK_OK;

@@ -78,27 +78,59 @@ struct TileDev {
     int32_t tiles_x, tiles_y;
 };
 
-// Device buffers of the beam pass (ESVO's beam optimisation, Sec. 2): per
-// 8 x 4 pixel tile (one casting warp) a lower bound on the L-infinity distance
-// from the camera origin of every solid voxel the tile's rays can meet,
-// found by a level-by-level walk of the selected DAGs that refines a node
-// while its screen rectangle spans more than a few tiles.
+// The beam pass (ESVO's beam optimisation, Sec. 2; aok_beam.cu): per 8 x 4
+// pixel tile (one casting warp) a lower bound on the L-infinity distance from
+// the camera origin of every solid voxel the tile's rays can meet, found by a
+// level-by-level walk of the selected DAGs.  A view's bounds form a pyramid
+// of 64-bit entries (pass tag << 32) | bound, level L (cells of 2^L x 2^L
+// tiles) at beam_level_offset(L) from the view's first entry; an entry whose
+// tag is not the pass's means "no solid voxel".
 constexpr int kBeamTileW = 8, kBeamTileH = 4;
 constexpr int kBeamLevels = 16;  // queue counters (node levels of a 512^3 chunk: 8)
 constexpr int kBeamPyr = 7;      // bound pyramid levels (level 0: the tiles)
-struct BeamDev {
-    // bound entries: (pass tag << 32) | bound in origin numerator units (2^-kFix);
-    // an entry whose tag is not this pass's means "no solid voxel" (INT32_MAX)
-    unsigned long long* dn;  // [tiles] level 0 of the bound pyramid
-    unsigned long long* pyr; // levels 1 .. kBeamPyr-1: cells of 2^L x 2^L tiles
-    int32_t poff[8];         // offset of level L in pyr (poff[kBeamPyr]: total)
-    uint4* q[2];             // node queues of alternate levels: {chunk, node, cell x | y << 10 | z << 20, log2 size}
-    uint32_t* cnt;           // [kBeamLevels] items queued per level
-    uint32_t* hist;          // [kBeamLevels] nodes walked per depth below the region root
-    uint32_t cap;            // queue capacity in items
-    uint32_t tag;            // this pass's tag: decreases from pass to pass
-    int32_t off;             // 1: bound 0 everywhere (no usable projection)
-    int32_t tiles_x, tiles_y;
+constexpr int kBeamViews = 128;  // views of one beam pass
+
+__host__ __device__ __forceinline__ uint32_t beam_level_offset(uint32_t tx, uint32_t ty, int L) {
+    uint32_t off = 0;
+    for (int l = 0; l < L; l++) off += ((tx + (1u << l) - 1) >> l) * ((ty + (1u << l) - 1) >> l);
+    return off;
+}
+__host__ __device__ __forceinline__ uint32_t beam_entries(uint32_t W, uint32_t H) {
+    return beam_level_offset((W + kBeamTileW - 1) / kBeamTileW, (H + kBeamTileH - 1) / kBeamTileH, kBeamPyr);
+}
+
+// One view of a beam pass.
+struct BeamView {
+    SceneDev scene;
+    const ChunkRef* frame;
+    unsigned long long* bounds;  // the view's pyramid (beam_entries(W, H) entries)
+    float Af[9];                 // row-major inverse of A = [R col 0, R col 1, -R col 2] (d = A (u, v, 1)), FP32
+    float U, V;                  // u and v at the screen edges: tan_half * W / H, tan_half
+    float near_dn;               // numerator units: boxes closer than this cover every tile
+    float view_num;              // > 0: boxes farther than this (Euclidean, numerator units) are dropped
+    int32_t W, H, tiles_x, tiles_y;
+    int32_t O[3];                // origin numerators
+    uint32_t region_begin;       // first item of this view among the pass's regions
+};
+
+// The parameter block of one beam pass over up to kBeamViews views.
+struct BeamBatch {
+    uint32_t n_views, n_regions;  // views; chunk regions of all views
+    uint32_t expand;              // refine nodes whose rectangle spans more tiles than this ...
+    int32_t smin;                 // ... and whose side is above 2^smin LOD-0 voxels
+    uint32_t tag;                 // the pass's tag: decreases from pass to pass
+    uint32_t cap;                 // queue capacity in items
+    uint4* q[2];                  // node queues of alternate levels: {chunk, node, cell x | y << 10 | z << 20, log2 size | view << 8}
+    uint32_t* cnt;                // [kBeamLevels] items queued per level
+    uint32_t* hist;               // [kBeamLevels] nodes walked per depth below the region roots
+    BeamView v[kBeamViews];
+};
+static_assert(sizeof(BeamBatch) < 32000, "a beam pass's parameters must fit the kernel parameter space");
+
+// What a casting kernel reads of a view's beam pass (bounds == nullptr: none).
+struct BeamRead {
+    const unsigned long long* bounds;
+    uint32_t tag;
 };
 
 // Descriptor updates applied by a kernel on the rendering stream, so that a
@@ -122,6 +154,7 @@ struct ViewDev {
     uint4* hit;
     float* t;
     uint64_t tile_begin;    // first global warp-tile index of this view in the batch
+    const unsigned long long* beam;  // the view's beam-pass bounds (BatchParams::beam_tag), or nullptr
 };
 
 // Parameter block of one batched launch (kernel parameters: up to 32 KB).
@@ -133,6 +166,8 @@ struct BatchParams {
     uint32_t max_chunks;       // largest chunk grid among the views
     uint64_t total_tiles;      // warp tiles of all views
     unsigned long long* queue; // [0] next warp tile, [1] finished CTAs; zero at launch, re-armed by the last CTA
+    uint32_t beam_tag;         // tag of the beam pass the views' bounds come from
+    uint32_t pad;
     ViewDev v[kBatchViews];
 };
 static_assert(sizeof(BatchParams) < 32000, "batched launch parameters must fit the kernel parameter space");
@@ -152,11 +187,13 @@ extern "C" {
 int aokk_select(const aok::SceneDev* s, const aok::CamDev* c, aok::ChunkRef* frame, int8_t* lod_out,
                 uint8_t* vis_out, uint32_t* n_visible, void* stream);
 int aokk_cast(const aok::SceneDev* s, const aok::CamDev* c, const aok::ChunkRef* frame, uint4* hit, float* t,
-              uint32_t* counts, void* stream, const aok::CheckDev* ck, const aok::BeamDev* beam = nullptr);
-// Beam pass (aok_beam.cu): bounds tagged B->tag for the frame table `frame`;
-// AOK_E_INVALID if the camera matrix has no usable inverse (bounds unusable).
-int aokk_beam(const aok::SceneDev* S, const aok::CamDev* C, const aok::ChunkRef* frame, const aok::BeamDev* B,
-              uint32_t expand_tiles, int min_log2, unsigned grid, void* stream);
+              uint32_t* counts, void* stream, const aok::CheckDev* ck, const aok::BeamRead* beam = nullptr);
+// Beam pass (aok_beam.cu).  aokk_beam_view fills a view's projection (false:
+// the camera matrix has no usable inverse; leave the view out, it casts
+// without bounds); aokk_beam_run zeroes P's counters and launches the pass.
+bool aokk_beam_view(const aok::SceneDev* S, const aok::CamDev* C, const aok::ChunkRef* frame,
+                    unsigned long long* bounds, aok::BeamView* out);
+int aokk_beam_run(const aok::BeamBatch* P, unsigned grid, void* stream);
 // Blocks of the beam pass's cooperative launch on `sms` SMs (0 on error).
 unsigned aokk_beam_grid(int sms);
 int aokk_ray_dirs(const aok::CamDev* c, float* dirs, void* stream);
@@ -169,6 +206,7 @@ int aokk_read_bw(const void* buf, size_t n16, int passes, uint32_t* sink, int sm
 int aokk_select_batch(const aok::BatchParams* p, void* stream);
 int aokk_cast_batch(const aok::BatchParams* p, uint32_t ctas, uint32_t threads, void* stream);
 int aokk_batch_run(const aok::BatchParams* groups, uint32_t n_groups, uint32_t ctas, uint32_t threads, void* stream,
+                   const aok::BeamBatch* beams, unsigned beam_grid,
                    aok::GraphCache* gc);
 void aokk_graph_destroy(aok::GraphCache* gc);
 int aokk_max_ctas_per_sm(uint32_t threads);

@@ -109,25 +109,12 @@ __global__ void select_batch_kernel(const __grid_constant__ BatchParams P) {
 template <bool COUNT, bool BEAM = false>
 __global__ void __launch_bounds__(128) cast_kernel(SceneDev S, CamDev C, const ChunkRef* __restrict__ frame,
                                                    uint4* __restrict__ out_hit, float* __restrict__ out_t,
-                                                   uint32_t* __restrict__ counts, BeamDev beam) {
+                                                   uint32_t* __restrict__ counts, BeamRead beam) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int px = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
     const int py = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
     if (px >= C.W || py >= C.H) return;
-    int32_t Dn = 0;
-    if (BEAM && !beam.off) {
-        // the tile's bound: the minimum over its cells of the bound pyramid
-        // (entries of earlier passes carry other tags: nothing there)
-        const uint32_t tx = (uint32_t)(px / kBeamTileW), ty = (uint32_t)(py / kBeamTileH);
-        const unsigned long long tag = (unsigned long long)beam.tag << 32;
-        unsigned long long v = __ldcg(beam.dn + (size_t)ty * beam.tiles_x + tx);
-#pragma unroll
-        for (int L = 1; L < kBeamPyr; L++) {
-            const uint32_t wl = ((uint32_t)beam.tiles_x + (1u << L) - 1) >> L;
-            v = min(v, __ldcg(beam.pyr + beam.poff[L] + (ty >> L) * wl + (tx >> L)));
-        }
-        Dn = (v & 0xFFFFFFFF00000000ull) == tag ? (int32_t)(uint32_t)v : INT_MAX;
-    }
+    const int32_t Dn = BEAM ? beam_bound(beam.bounds, beam.tag, C.W, C.H, px, py) : 0;
     trace_pixel<COUNT, false, BEAM>(S, C, frame, px, py, out_hit, out_t, counts, (size_t)py * C.W + px, nullptr, Dn);
 }
 
@@ -212,8 +199,12 @@ __global__ void __launch_bounds__(128, 7) cast_grid(const __grid_constant__ Batc
     const int32_t local = (int32_t)(blk - v.tile_begin);
     const int px = (local % bw) * 2 * tw + (warp & 1) * tw + (lane & (tw - 1));
     const int py = (local / bw) * 2 * th + (warp >> 1) * th + (lane >> twl);
-    if (px < v.cam.W && py < v.cam.H)
-        trace_pixel<false>(v.scene, v.cam, v.frame, px, py, v.hit, v.t, nullptr, (size_t)py * v.cam.W + px);
+    if (px < v.cam.W && py < v.cam.H) {
+        // with a bound of 0 (no beam pass for this view) the march is the plain one
+        const int32_t Dn = beam_bound(v.beam, P.beam_tag, v.cam.W, v.cam.H, px, py);
+        trace_pixel<false, false, true>(v.scene, v.cam, v.frame, px, py, v.hit, v.t, nullptr,
+                                        (size_t)py * v.cam.W + px, nullptr, Dn);
+    }
 }
 
 __global__ void patch_desc_kernel(ChunkRef* __restrict__ desc, const __grid_constant__ DescPatches P) {
@@ -245,7 +236,7 @@ int aokk_select(const SceneDev* s, const CamDev* c, ChunkRef* frame, int8_t* lod
 }
 
 int aokk_cast(const SceneDev* s, const CamDev* c, const ChunkRef* frame, uint4* hit, float* t, uint32_t* counts,
-              void* stream, const CheckDev* ck, const BeamDev* beam) {
+              void* stream, const CheckDev* ck, const BeamRead* beam) {
     dim3 grid((c->W + 15) / 16, (c->H + 7) / 8);
     const cudaStream_t st = (cudaStream_t)stream;
     if (ck && !counts)
@@ -253,11 +244,11 @@ int aokk_cast(const SceneDev* s, const CamDev* c, const ChunkRef* frame, uint4* 
     else if (counts && beam)
         cast_kernel<true, true><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, counts, *beam);
     else if (counts)
-        cast_kernel<true><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, counts, BeamDev{});
+        cast_kernel<true><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, counts, BeamRead{nullptr, 0});
     else if (beam)
         cast_kernel<false, true><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, nullptr, *beam);
     else
-        cast_kernel<false><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, nullptr, BeamDev{});
+        cast_kernel<false><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, nullptr, BeamRead{nullptr, 0});
     return status_of(cudaGetLastError());
 }
 
@@ -275,15 +266,18 @@ int aokk_cast_batch(const BatchParams* p, uint32_t ctas, uint32_t threads, void*
     return status_of(cudaGetLastError());
 }
 
-// Run n_groups (select, cast) launch pairs on `stream`.  With a cache, the pairs
-// form one CUDA graph built per shape (group sizes, launch dims) whose kernel
-// nodes are updated with the new parameters on every call.
+// Run n_groups (select, cast) launch pairs on `stream`; with beams, each
+// group's beam pass (beams[g], one cooperative launch) runs between its
+// selection and its cast.  With a cache and no beams, the pairs form one CUDA
+// graph built per shape (group sizes, launch dims) whose kernel nodes are
+// updated with the new parameters on every call.
 int aokk_batch_run(const BatchParams* groups, uint32_t n_groups, uint32_t ctas, uint32_t threads, void* stream,
-                   GraphCache* gc) {
+                   const BeamBatch* beams, unsigned beam_grid, GraphCache* gc) {
     const cudaStream_t st = (cudaStream_t)stream;
-    if (!gc) {
+    if (!gc || beams) {
         for (uint32_t g = 0; g < n_groups; g++) {
             int r = aokk_select_batch(&groups[g], stream);
+            if (!r && beams) r = aokk_beam_run(&beams[g], beam_grid, stream);
             if (!r) r = aokk_cast_batch(&groups[g], ctas, threads, stream);
             if (r) return r;
         }
@@ -438,7 +432,7 @@ int aokk_render_noalloc(const SceneDev* s, const CamDev* c, uint4* hit, float* t
     const cudaStream_t st = (cudaStream_t)stream;
     select_kernel<<<(unsigned)((nch + 127) / 128), 128, 0, st>>>(*s, *c, frame, nullptr, nullptr, nullptr);
     dim3 grid((c->W + 15) / 16, (c->H + 7) / 8);
-    cast_kernel<false><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, nullptr, BeamDev{});
+    cast_kernel<false><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, nullptr, BeamRead{nullptr, 0});
     return status_of(cudaGetLastError());
 }
 

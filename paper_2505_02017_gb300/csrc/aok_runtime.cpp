@@ -347,7 +347,8 @@ void aok_destroy(aok_ctx* ctx) {
     dev_free(ctx, ctx->d_counter, sizeof(uint32_t) * 16);
     dev_free(ctx, ctx->d_single_queue, 2 * sizeof(unsigned long long));
     dev_free(ctx, ctx->tiles.block, ctx->tiles.bytes);
-    dev_free(ctx, ctx->beam.block, ctx->beam.bytes);
+    dev_free(ctx, ctx->beam.qblock, ctx->beam.qbytes);
+    dev_free(ctx, ctx->beam.bounds, ctx->beam.bounds_cap * 8);
     pipe_release(ctx);
     if (ctx->pipe.render) cudaStreamDestroy(ctx->pipe.render);
     if (ctx->pipe.copy) cudaStreamDestroy(ctx->pipe.copy);
@@ -801,97 +802,151 @@ static const CheckDev* check_dev(aok_ctx* ctx, const Scene* sc, CheckDev* ck) {
     return ck;
 }
 
-// Beam buffers for W x H (reallocated when the size changes).
+// ---------------------------------------------------------------------------
+// beam pass
+// ---------------------------------------------------------------------------
 static constexpr uint32_t kBeamCap = 1u << 20;  // queued nodes per level
-// Beam buffers for W x H: the bound arrays grow to the largest frame seen
-// and keep their place for smaller ones (entries carry their pass's tag, so a
-// change of layout between passes needs no clearing).
-static int ensure_beam(aok_ctx* ctx, int32_t W, int32_t H) {
+
+// The walk's queues, counters and launch grid (shared by single-view and
+// batch passes, which run in stream order).
+static int ensure_beam_queues(aok_ctx* ctx) {
     BeamState& b = ctx->beam;
-    if (b.block && b.W == W && b.H == H) return AOK_OK;
-    const int32_t tx = (W + kBeamTileW - 1) / kBeamTileW, ty = (H + kBeamTileH - 1) / kBeamTileH;
-    auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
-    int32_t poff[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int L = 1; L < kBeamPyr; L++)
-        poff[L + 1] = poff[L] + ((tx + (1 << L) - 1) >> L) * ((ty + (1 << L) - 1) >> L);
-    const size_t need_dn = al((size_t)tx * ty * 8), need_pyr = al((size_t)poff[kBeamPyr] * 8);
-    if (b.block && need_dn <= b.cap_dn && need_pyr <= b.cap_pyr) {
-        for (int L = 0; L < 8; L++) b.dev.poff[L] = poff[L];
-        b.dev.tiles_x = tx;
-        b.dev.tiles_y = ty;
-        b.W = W;
-        b.H = H;
-        b.valid = false;
-        return AOK_OK;
-    }
-    const size_t sd = std::max(need_dn, b.cap_dn), sdc = std::max(need_pyr, b.cap_pyr);
-    const uint32_t passes = b.passes;
-    if (b.block) {
-        cudaDeviceSynchronize();
-        dev_free(ctx, b.block, b.bytes);
-        b = BeamState{};
-    }
-    b.passes = passes;
-    const size_t sq = al((size_t)kBeamCap * 16), sc = al(2 * kBeamLevels * 4);
+    if (b.qblock) return AOK_OK;
+    const size_t sq = (size_t)kBeamCap * 16, sc = 2 * kBeamLevels * 4;
     void* block = nullptr;
-    int st = dev_alloc(ctx, &block, sd + sdc + 2 * sq + sc);
+    int st = dev_alloc(ctx, &block, 2 * sq + sc);
     if (st) return st;
-    char* p = (char*)block;
-    b.dev.dn = (unsigned long long*)p;
-    b.dev.pyr = (unsigned long long*)(p + sd);
-    for (int L = 0; L < 8; L++) b.dev.poff[L] = poff[L];
-    b.dev.q[0] = (uint4*)(p + sd + sdc);
-    b.dev.q[1] = (uint4*)(p + sd + sdc + sq);
-    b.dev.cnt = (uint32_t*)(p + sd + sdc + 2 * sq);
-    b.dev.hist = b.dev.cnt + kBeamLevels;
-    b.dev.cap = kBeamCap;
-    b.dev.tiles_x = tx;
-    b.dev.tiles_y = ty;
-    // no entry carries a pass tag yet (tags count down from 0xFFFFFFFE)
-    if (cudaMemset(p, 0xFF, sd + sdc) != cudaSuccess) {
-        dev_free(ctx, block, sd + sdc + 2 * sq + sc);
-        return cuda_status(ctx, cudaGetLastError());
-    }
-    b.block = block;
-    b.bytes = sd + sdc + 2 * sq + sc;
-    b.cap_dn = sd;
-    b.cap_pyr = sdc;
+    b.q[0] = (uint4*)block;
+    b.q[1] = (uint4*)((char*)block + sq);
+    b.cnt = (uint32_t*)((char*)block + 2 * sq);
+    b.hist = b.cnt + kBeamLevels;
+    b.qblock = block;
+    b.qbytes = 2 * sq + sc;
     b.grid = aokk_beam_grid(ctx->sm_count);
     if (!b.grid) return AOK_E_CUDA;
-    b.W = W;
-    b.H = H;
+    if (!b.P) b.P.reset(new BeamBatch);
     return AOK_OK;
+}
+
+// A grow-only array of bound entries, all without a pass tag when allocated
+// (entries carry their pass's tag, so a change of layout needs no clearing).
+static int ensure_bounds(aok_ctx* ctx, unsigned long long** buf, size_t* cap, size_t need) {
+    if (need <= *cap) return AOK_OK;
+    if (*buf) {
+        cudaDeviceSynchronize();
+        dev_free(ctx, *buf, *cap * 8);
+        *buf = nullptr;
+        *cap = 0;
+    }
+    int st = dev_alloc(ctx, (void**)buf, need * 8);
+    if (st) return st;
+    if (cudaMemset(*buf, 0xFF, need * 8) != cudaSuccess) return cuda_status(ctx, cudaGetLastError());
+    *cap = need;
+    return AOK_OK;
+}
+
+// The next pass's tag (tags count down); before they wrap every bound array
+// is cleared.
+static int next_beam_tag(aok_ctx* ctx, void* stream, uint32_t* tag) {
+    BeamState& b = ctx->beam;
+    if (++b.passes >= 0xFFFFFFF0u) {
+        const cudaStream_t s = (cudaStream_t)stream;
+        if ((b.bounds && cudaMemsetAsync(b.bounds, 0xFF, b.bounds_cap * 8, s) != cudaSuccess) ||
+            (ctx->batch.beam_bounds &&
+             cudaMemsetAsync(ctx->batch.beam_bounds, 0xFF, ctx->batch.beam_cap * 8, s) != cudaSuccess))
+            return AOK_E_CUDA;
+        b.passes = 1;
+        b.valid = false;
+    }
+    *tag = 0xFFFFFFFFu - b.passes;
+    return AOK_OK;
+}
+
+// Fill the pass header of P (views and regions are filled by the caller).
+static void beam_header(aok_ctx* ctx, BeamBatch* P, uint32_t tag) {
+    P->expand = ctx->beam_refine;
+    P->smin = ctx->beam_min_log2;
+    P->tag = tag;
+    P->cap = ctx->beam_queue && ctx->beam_queue < kBeamCap ? ctx->beam_queue : kBeamCap;
+    P->q[0] = ctx->beam.q[0];
+    P->q[1] = ctx->beam.q[1];
+    P->cnt = ctx->beam.cnt;
+    P->hist = ctx->beam.hist;
 }
 
 // The beam pass over the scene's current frame table, remembered with what
 // it was computed for.
 static int run_beam(aok_ctx* ctx, uint32_t scene, Scene* sc, const SceneDev& sd, const CamDev& cd, void* stream) {
-    int st = ensure_beam(ctx, cd.W, cd.H);
+    int st = ensure_beam_queues(ctx);
     if (st) return st;
     BeamState& b = ctx->beam;
+    st = ensure_bounds(ctx, &b.bounds, &b.bounds_cap, beam_entries((uint32_t)cd.W, (uint32_t)cd.H));
+    if (st) return st;
     b.valid = false;
-    if (++b.passes >= 0xFFFFFFF0u) {
-        // tags are about to wrap: clear every entry first
-        const cudaStream_t s = (cudaStream_t)stream;
-        if (cudaMemsetAsync(b.dev.dn, 0xFF, b.cap_dn, s) != cudaSuccess ||
-            cudaMemsetAsync(b.dev.pyr, 0xFF, b.cap_pyr, s) != cudaSuccess)
-            return AOK_E_CUDA;
-        b.passes = 1;
+    uint32_t tag;
+    st = next_beam_tag(ctx, stream, &tag);
+    if (st) return st;
+    BeamBatch* P = b.P.get();
+    beam_header(ctx, P, tag);
+    P->n_views = 0;
+    P->n_regions = 0;
+    b.read.bounds = nullptr;  // no usable projection: no bounds, nothing is skipped
+    b.read.tag = tag;
+    if (aokk_beam_view(&sd, &cd, sc->d_frame, b.bounds, &P->v[0])) {
+        P->v[0].region_begin = 0;
+        P->n_views = 1;
+        P->n_regions = (uint32_t)sc->n_chunks;
+        b.read.bounds = b.bounds;
     }
-    b.dev.tag = 0xFFFFFFFFu - b.passes;
-    b.dev.off = 0;
-    b.dev.cap = ctx->beam_queue && ctx->beam_queue < kBeamCap ? ctx->beam_queue : kBeamCap;
-    st = aokk_beam(&sd, &cd, sc->d_frame, &b.dev, ctx->beam_refine, ctx->beam_min_log2, b.grid, stream);
-    if (st == AOK_E_INVALID) {
-        b.dev.off = 1;  // no usable projection: bound 0 everywhere, nothing is skipped
-        st = AOK_OK;
-    }
+    st = aokk_beam_run(P, b.grid, stream);
     if (st) return st;
     b.valid = true;
     b.scene = scene;
     b.gen = sc->select_gen;
     b.cam = cd;
     b.cam.sf = 0.0;  // the LOD threshold does not enter the bounds
+    b.W = cd.W;
+    b.H = cd.H;
+    return AOK_OK;
+}
+
+extern "C++" int aok::beam_for_batch(aok_ctx* ctx, BatchParams* groups, uint32_t ngroups,
+                                     std::vector<BeamBatch>& out, void* stream) {
+    out.clear();
+    if (!ctx->beam_on) return AOK_OK;
+    size_t need = 0;
+    for (uint32_t g = 0; g < ngroups; g++)
+        for (uint32_t i = 0; i < groups[g].n_views; i++) {
+            const CamDev& c = groups[g].v[i].cam;
+            if ((uint64_t)c.W * (uint64_t)c.H >= ctx->beam_min_pixels) need += beam_entries((uint32_t)c.W, (uint32_t)c.H);
+        }
+    if (!need) return AOK_OK;
+    int st = ensure_beam_queues(ctx);
+    if (!st) st = ensure_bounds(ctx, &ctx->batch.beam_bounds, &ctx->batch.beam_cap, need);
+    uint32_t tag = 0;
+    if (!st) st = next_beam_tag(ctx, stream, &tag);
+    if (st) return st;
+    out.resize(ngroups);
+    size_t off = 0;
+    for (uint32_t g = 0; g < ngroups; g++) {
+        BeamBatch& B = out[g];
+        beam_header(ctx, &B, tag);
+        B.n_views = 0;
+        B.n_regions = 0;
+        groups[g].beam_tag = tag;
+        for (uint32_t i = 0; i < groups[g].n_views; i++) {
+            ViewDev& d = groups[g].v[i];
+            d.beam = nullptr;
+            if ((uint64_t)d.cam.W * (uint64_t)d.cam.H < ctx->beam_min_pixels) continue;
+            unsigned long long* bnd = ctx->batch.beam_bounds + off;
+            off += beam_entries((uint32_t)d.cam.W, (uint32_t)d.cam.H);
+            if (!aokk_beam_view(&d.scene, &d.cam, d.frame, bnd, &B.v[B.n_views])) continue;  // casts without
+            B.v[B.n_views].region_begin = B.n_regions;
+            B.n_regions += (uint32_t)(d.scene.grid[0] * d.scene.grid[1] * d.scene.grid[2]);
+            B.n_views++;
+            d.beam = bnd;
+        }
+    }
     return AOK_OK;
 }
 
@@ -911,13 +966,13 @@ static int cast_single(aok_ctx* ctx, uint32_t scene, Scene* sc, const SceneDev& 
                        const aok_frame* frame, uint32_t* counts, void* stream) {
     CheckDev ck;
     const CheckDev* ckp = check_dev(ctx, sc, &ck);
-    const BeamDev* beam = nullptr;
+    const BeamRead* beam = nullptr;
     if (ctx->beam_on && !ckp && (uint64_t)cd.W * (uint64_t)cd.H >= ctx->beam_min_pixels) {
         if (!beam_fresh(ctx, scene, sc, cd)) {
             const int st = run_beam(ctx, scene, sc, sd, cd, stream);
             if (st) return st;
         }
-        beam = &ctx->beam.dev;
+        beam = &ctx->beam.read;
     }
     return aokk_cast(&sd, &cd, sc->d_frame, (uint4*)frame->hit, frame->t, counts, stream, ckp, beam);
 }
@@ -1126,8 +1181,9 @@ int aok_beam_selected(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, void*
 int aok_beam_info(aok_ctx* ctx, int32_t* bounds, uint64_t n_bounds, uint32_t* level_counts, int32_t* tiles_xy) {
     if (!ctx) return AOK_E_INVALID;
     const BeamState& b = ctx->beam;
-    if (!b.block) return AOK_E_INVALID;
-    const uint64_t n = (uint64_t)b.dev.tiles_x * b.dev.tiles_y;
+    if (!b.valid) return AOK_E_INVALID;
+    const uint32_t tx = (uint32_t)(b.W + kBeamTileW - 1) / kBeamTileW, ty = (uint32_t)(b.H + kBeamTileH - 1) / kBeamTileH;
+    const uint64_t n = (uint64_t)tx * ty;
     if (bounds && n_bounds < n) return AOK_E_INVALID;
     cudaSetDevice(ctx->device);
     if (cudaDeviceSynchronize() != cudaSuccess) return cuda_status(ctx, cudaGetLastError());
@@ -1135,28 +1191,27 @@ int aok_beam_info(aok_ctx* ctx, int32_t* bounds, uint64_t n_bounds, uint32_t* le
         // the bounds the casting kernel uses: each tile's minimum over its
         // cells of the pyramid among entries of the last pass's tag, or 0
         // everywhere if that pass could not project
-        std::vector<unsigned long long> lv0(n), pyr((size_t)b.dev.poff[kBeamPyr]);
-        if (cudaMemcpy(lv0.data(), b.dev.dn, n * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
-            (!pyr.empty() && cudaMemcpy(pyr.data(), b.dev.pyr, pyr.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess))
+        std::vector<unsigned long long> e(beam_entries((uint32_t)b.W, (uint32_t)b.H));
+        if (b.read.bounds &&
+            cudaMemcpy(e.data(), b.read.bounds, e.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
             return cuda_status(ctx, cudaGetLastError());
-        const unsigned long long tag = (unsigned long long)b.dev.tag << 32;
-        const int32_t tx = b.dev.tiles_x, ty = b.dev.tiles_y;
-        for (int32_t y = 0; y < ty; y++)
-            for (int32_t x = 0; x < tx; x++) {
-                unsigned long long v = lv0[(size_t)y * tx + x];
-                for (int L = 1; L < kBeamPyr; L++) {
-                    const int32_t wl = (tx + (1 << L) - 1) >> L;
-                    v = std::min(v, pyr[(size_t)b.dev.poff[L] + (size_t)(y >> L) * wl + (x >> L)]);
+        const unsigned long long tag = (unsigned long long)b.read.tag << 32;
+        for (uint32_t y = 0; y < ty; y++)
+            for (uint32_t x = 0; x < tx; x++) {
+                unsigned long long v = ~0ull;
+                for (int L = 0; L < kBeamPyr; L++) {
+                    const uint32_t wl = (tx + (1u << L) - 1) >> L;
+                    v = std::min(v, e[beam_level_offset(tx, ty, L) + (size_t)(y >> L) * wl + (x >> L)]);
                 }
                 bounds[(size_t)y * tx + x] =
-                    b.dev.off ? 0 : ((v & 0xFFFFFFFF00000000ull) == tag ? (int32_t)(uint32_t)v : INT32_MAX);
+                    !b.read.bounds ? 0 : ((v & 0xFFFFFFFF00000000ull) == tag ? (int32_t)(uint32_t)v : INT32_MAX);
             }
     }
-    if (level_counts && cudaMemcpy(level_counts, b.dev.hist, kBeamLevels * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    if (level_counts && cudaMemcpy(level_counts, b.hist, kBeamLevels * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
         return cuda_status(ctx, cudaGetLastError());
     if (tiles_xy) {
-        tiles_xy[0] = b.dev.tiles_x;
-        tiles_xy[1] = b.dev.tiles_y;
+        tiles_xy[0] = (int32_t)tx;
+        tiles_xy[1] = (int32_t)ty;
     }
     return AOK_OK;
 }

@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -52,6 +53,8 @@ struct Scene {
 struct BatchArena {
     ChunkRef* d_frames = nullptr;
     size_t frames_cap = 0;
+    unsigned long long* beam_bounds = nullptr;  // the views' bound pyramids (grow-only)
+    size_t beam_cap = 0;                        // entries
     unsigned long long* d_queue = nullptr;  // 2 per group, zero between launches
     size_t queue_cap = 0;
     GraphCache graph;
@@ -87,20 +90,27 @@ struct TileState {
     uint32_t scene = 0xFFFFFFFFu;
 };
 
-// Buffers of the beam pass for one resolution.
+// The beam pass: the walk's queues and launch grid (shared by all passes of
+// the context), the single-view bound pyramid and what its last pass was
+// computed for.
 struct BeamState {
-    BeamDev dev{};
-    void* block = nullptr;
-    size_t bytes = 0;
-    size_t cap_dn = 0, cap_pyr = 0;  // bytes of the two bound arrays (grow-only)
-    unsigned grid = 0;               // blocks of the cooperative launch
-    int32_t W = 0, H = 0;
-    // what the bounds in dev were computed for: a scene, its selection, a camera
+    void* qblock = nullptr;
+    size_t qbytes = 0;
+    uint4* q[2] = {nullptr, nullptr};
+    uint32_t* cnt = nullptr;   // [kBeamLevels] queue counts, then [kBeamLevels] walk histogram
+    uint32_t* hist = nullptr;
+    unsigned grid = 0;         // blocks of the cooperative launch
+    std::unique_ptr<BeamBatch> P;  // host parameter block (~26 KB)
+    unsigned long long* bounds = nullptr;  // single-view pyramid (grow-only)
+    size_t bounds_cap = 0;                 // entries
+    uint32_t passes = 0;                   // passes run (their tags count down)
+    // the last single-view pass: a scene, its selection, a camera
     bool valid = false;
-    uint32_t passes = 0;  // passes run (their tags count down)
     uint32_t scene = 0xFFFFFFFFu;
     uint64_t gen = 0;
     CamDev cam{};
+    BeamRead read{nullptr, 0};
+    int32_t W = 0, H = 0;
 };
 
 struct aok_ctx_impl;
@@ -156,6 +166,10 @@ int make_cam(aok_ctx* ctx, const Scene* sc, const aok_camera* cam, double tau, C
 SceneDev scene_dev(const Scene* sc);
 void batch_release(aok_ctx* ctx);
 void free_alloc(Scene* sc, ChunkAlloc& a);
+// The beam passes of a batch (one per group) for its views of at least the
+// context's beam frame size; sets the views' bounds.  Leaves `out` empty if
+// no view takes the pass.
+int beam_for_batch(aok_ctx* ctx, BatchParams* groups, uint32_t ngroups, std::vector<BeamBatch>& out, void* stream);
 // Pinned staging memory and the stream its copies go on.
 struct Staging {
     void* buf = nullptr;

@@ -131,6 +131,7 @@ void batch_release(aok_ctx* ctx) {
     aokk_graph_destroy(&A.graph);
     dev_free(ctx, A.d_frames, A.frames_cap * sizeof(ChunkRef));
     dev_free(ctx, A.d_queue, A.queue_cap * sizeof(unsigned long long));
+    dev_free(ctx, A.beam_bounds, A.beam_cap * 8);
     A = BatchArena();
 }
 
@@ -145,8 +146,14 @@ static int render_batch_impl(aok_ctx* ctx, const aok_view* views, uint32_t n, vo
     if (st) return st;
     st = prepare_batch(ctx, views, n, ctx->batch.d_frames, ctx->batch.frames_cap, ctx->batch.d_queue, L, prep);
     if (st) return st;
+    // the beam pass for the views large enough (grid launch only)
+    std::vector<BeamBatch> beams;
+    if (L.ctas == 0) {
+        st = beam_for_batch(ctx, prep.groups.data(), (uint32_t)prep.groups.size(), beams, stream);
+        if (st) return st;
+    }
     st = aokk_batch_run(prep.groups.data(), (uint32_t)prep.groups.size(), L.ctas, L.threads, stream,
-                        use_graph ? &ctx->batch.graph : nullptr);
+                        beams.empty() ? nullptr : beams.data(), ctx->beam.grid, use_graph ? &ctx->batch.graph : nullptr);
     return st == AOK_E_CUDA ? cuda_status(ctx, cudaGetLastError()) : st;
 }
 
@@ -387,7 +394,7 @@ static void serve_loop(aok_ctx* ctx) {
                 P.total_tiles = tiles;
             }
         }
-        if (rc == AOK_OK) rc = aokk_batch_run(S.params.data(), ngroups, L.ctas, L.threads, st, nullptr);
+        if (rc == AOK_OK) rc = aokk_batch_run(S.params.data(), ngroups, L.ctas, L.threads, st, nullptr, 0, nullptr);
         std::lock_guard<std::mutex> g(S.mu);
         if (rc != AOK_OK) {
             for (uint64_t id : batch) {

@@ -328,6 +328,25 @@ __device__ __forceinline__ float ray_norm(const RayState& r) {
     return sqrtf(__fadd_rn(__fadd_rn(__fmul_rn(r.d[0], r.d[0]), __fmul_rn(r.d[1], r.d[1])), __fmul_rn(r.d[2], r.d[2])));
 }
 
+// The beam-pass bound of pixel (px, py) of a W x H view: the minimum over
+// its 8 x 4 tile's cells of the bound pyramid among entries of pass `tag`
+// (INT32_MAX if there is none), 0 without bounds.
+__device__ __forceinline__ int32_t beam_bound(const unsigned long long* __restrict__ b, uint32_t tag, int W, int H,
+                                              int px, int py) {
+    if (!b) return 0;
+    const uint32_t tx = (uint32_t)(W + kBeamTileW - 1) / kBeamTileW, ty = (uint32_t)(H + kBeamTileH - 1) / kBeamTileH;
+    const uint32_t x = (uint32_t)px / kBeamTileW, y = (uint32_t)py / kBeamTileH;
+    unsigned long long v = ~0ull;
+    uint32_t off = 0;
+#pragma unroll
+    for (int L = 0; L < kBeamPyr; L++) {
+        const uint32_t wl = (tx + (1u << L) - 1) >> L, hl = (ty + (1u << L) - 1) >> L;
+        v = min(v, __ldcg(b + off + (y >> L) * wl + (x >> L)));
+        off += wl * hl;
+    }
+    return (uint32_t)(v >> 32) == tag ? (int32_t)(uint32_t)v : INT_MAX;
+}
+
 // Pixel ray in the mirrored frame.  Returns true for a FAST ray: the non-zero
 // |d| exponents span <= 6, mantissas shifted to a common exponent (E = 0),
 // zero components m = 0.

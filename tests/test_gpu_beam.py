@@ -278,3 +278,26 @@ def test_refinement_settings_same_output(ctx):
         assert (aok.beam_info(ctx)[0] == b0).all()
     finally:
         aok.beam_tune(ctx, 8, 2, 0, 0)
+
+
+def test_batch_with_beam_equals_plain(ctx):
+    """Batched rendering with the beam pass (one pass for all views of a
+    group): every view equals its plain single-view render; views of two
+    worlds, mixed sizes, one camera without a usable inverse."""
+    w1, sc1, _ = scene_for(ctx, MED64)
+    w2, sc2, _ = scene_for(ctx, MULTI32)
+    cams = [(sc1, sg.ground_camera(w1, s, W, H, z_lo=4, z_hi=40)) for s, W, H in
+            ((4, 160, 90), (9, 203, 117), (11, 64, 48), (12, 1, 1))]
+    cams += [(sc2, sg.ground_camera(w2, s, W, H, z_lo=4, z_hi=20)) for s, W, H in ((4, 64, 40), (5, 97, 33))]
+    bad = sg.ground_camera(w1, 13, 48, 32, z_lo=4, z_hi=40)
+    R = bad.R.copy()
+    R[:, 2] = R[:, 0]
+    cams.append((sc1, replace(bad, R=R)))
+    refs = [render(ctx, sc, cam, 1.0, False) for sc, cam in cams]
+    aok.set_beam(ctx, True)
+    outs = [aok.alloc_frame(cam.W, cam.H) for _, cam in cams]
+    views = [aok.make_view(sc, cam, 1.0, h, t) for (sc, cam), (h, t) in zip(cams, outs)]
+    aok.render_batch(ctx, views)
+    torch.cuda.synchronize()
+    for i, (ref, out) in enumerate(zip(refs, outs)):
+        assert same(ref, out), i
