@@ -485,23 +485,25 @@ int aok_render_noalloc(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, doub
 
 /* Beam pass (ESVO's beam optimisation, which the paper's traversal builds on,
  * Sec. 2; here exact): with on = 1, aok_render, aok_render_counted,
- * aok_render_host(_async) and aok_cast_selected of this context first compute,
- * for every 8 x 4 pixel tile, a lower bound on the L-infinity distance from
- * the camera origin of every solid voxel of the frame's LOD-cut scene that
- * the tile's rays can meet (a level-by-level walk of the selected DAGs,
- * refining a node while its screen rectangle spans more than R tiles and
- * its side is above 2^L voxels, each node scattering its distance to the
- * tiles of its rectangle with an atomic minimum; R and L: aok_beam_tune).  The casting kernel then
- * restarts each ray's march at the last integer plane of its dominant axis
- * that the ray crosses before that distance.  Output records are identical
- * with the pass on or off.  Buffers
- * (about 11 B per 8 x 4 pixel tile and two 16 MiB node queues) are charged to the budget at the
- * first render of each resolution.  Not used by checked casting, the
- * persistent single-view kernel, aok_render_noalloc, batches, serving or the
- * tile pipeline.  Default on (for frames of at least 1.5 M pixels,
- * aok_beam_tune).  The pass's buffers belong to the context:
- * with it on, renders of one context on different streams must be ordered
- * (an event or a synchronisation between them). */
+ * aok_render_host(_async), aok_cast_selected and aok_render_batch (grid
+ * launch) of this context first compute, for every 8 x 4 pixel tile of each
+ * frame of at least 1.5 M pixels (aok_beam_tune), a lower bound on the
+ * L-infinity distance from the camera origin of every solid voxel of the
+ * frame's LOD-cut scene that the tile's rays can meet: a level-by-level walk
+ * of the selected DAGs (all views of a batch in one launch), refining a node
+ * while its screen rectangle spans more than R tiles and its side is above
+ * 2^L voxels, each node scattering its distance over its rectangle with an
+ * atomic minimum.  The casting kernels then restart each ray's march at the
+ * last integer plane of its dominant axis that the ray crosses before that
+ * distance.  Output records are identical with the pass on or off.  Buffers
+ * (about 11 B per 8 x 4 pixel tile, grown to the largest frame or batch seen,
+ * and two 16 MiB node queues) are charged to the budget when first needed.
+ * Not used by checked casting, the persistent single-view and batch kernels,
+ * aok_render_noalloc, serving or the tile pipeline.  Default on.  The pass's
+ * buffers belong to the context: with it on, renders of one context on
+ * different streams must be ordered (an event or a synchronisation between
+ * them).  The passes of all contexts of a process run one after another on a
+ * device (each waits for the previous one's launch to finish). */
 int aok_set_beam(aok_ctx* ctx, int on);
 /* Refinement of the beam pass's walk: a node is refined while its rectangle
  * spans more than refine_tiles tiles and its side is above 2^min_node_log2

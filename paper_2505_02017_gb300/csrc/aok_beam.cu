@@ -46,6 +46,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 
 #include <cooperative_groups.h>
 
@@ -60,6 +61,7 @@ constexpr int kBeamThreads = 256;      // block size of the cooperative walk
 constexpr int kBeamBlocksPerSM = 2;    // at most this many blocks per SM (fewer blocks: cheaper barriers)
 constexpr double kNearS = 1.0 / 16.0;  // camera-depth plane the projection clips at
 constexpr uint32_t kNoItem = 0xFFFFFFFFu;  // an empty queue slot
+constexpr int kMaxBeamDevices = 128;
 
 // Screen rectangle [x, z) x [y, w) of tiles a box (relative to the origin)
 // can cover from its part at camera depth s >= kNearS; false if none.
@@ -396,14 +398,28 @@ bool aokk_beam_view(const SceneDev* S, const CamDev* C, const ChunkRef* frame, u
     return true;
 }
 
+// Beam passes of this process run one after another on each device: a pass
+// waits for the previous one, whatever stream either was launched on, so that
+// two cooperative launches that each fill the GPU never wait for each other's
+// blocks.
+static std::mutex g_beam_mu;
+static cudaEvent_t g_beam_done[kMaxBeamDevices];
+
 int aokk_beam_run(const BeamBatch* P, unsigned grid, void* stream) {
     const cudaStream_t st = (cudaStream_t)stream;
     if (P->n_views == 0) return AOK_OK;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxBeamDevices) return AOK_E_CUDA;
+    std::lock_guard<std::mutex> lk(g_beam_mu);
+    if (!g_beam_done[dev] && cudaEventCreateWithFlags(&g_beam_done[dev], cudaEventDisableTiming) != cudaSuccess)
+        return AOK_E_CUDA;
+    if (cudaStreamWaitEvent(st, g_beam_done[dev], 0) != cudaSuccess) return AOK_E_CUDA;
     // queue counts and the walk histogram (cnt and hist are adjacent)
     if (cudaMemsetAsync(P->cnt, 0, 2 * kBeamLevels * sizeof(uint32_t), st) != cudaSuccess) return AOK_E_CUDA;
     void* args[] = {(void*)P};
     if (cudaLaunchCooperativeKernel((const void*)beam_kernel, grid, kBeamThreads, args, 0, st) != cudaSuccess)
         return AOK_E_CUDA;
+    if (cudaEventRecord(g_beam_done[dev], st) != cudaSuccess) return AOK_E_CUDA;
     return AOK_OK;
 }
 
