@@ -485,8 +485,8 @@ int aok_render_noalloc(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, doub
 
 /* Beam pass (ESVO's beam optimisation, which the paper's traversal builds on,
  * Sec. 2; here exact): with on = 1, aok_render, aok_render_counted,
- * aok_render_host(_async), aok_cast_selected and aok_render_batch (grid
- * launch) of this context first compute, for every 8 x 4 pixel tile of each
+ * aok_render_host(_async), aok_cast_selected, aok_render_batch (grid
+ * launch) and the render server of this context first compute, for every 8 x 4 pixel tile of each
  * frame of at least 1.5 M pixels (aok_beam_tune), a lower bound on the
  * L-infinity distance from the camera origin of every solid voxel of the
  * frame's LOD-cut scene that the tile's rays can meet: a level-by-level walk
@@ -498,8 +498,9 @@ int aok_render_noalloc(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, doub
  * distance.  Output records are identical with the pass on or off.  Buffers
  * (about 11 B per 8 x 4 pixel tile, grown to the largest frame or batch seen,
  * and two 16 MiB node queues) are charged to the budget when first needed.
+ * The render server runs it for its batches too (per-request pyramids).
  * Not used by checked casting, the persistent single-view and batch kernels,
- * aok_render_noalloc, serving or the tile pipeline.  Default on.  The pass's
+ * aok_render_noalloc or the tile pipeline.  Default on.  The pass's
  * buffers belong to the context: with it on, renders of one context on
  * different streams must be ordered (an event or a synchronisation between
  * them).  The passes of all contexts of a process run one after another on a

@@ -811,6 +811,7 @@ static constexpr uint32_t kBeamCap = 1u << 20;  // queued nodes per level
 // batch passes, which run in stream order).
 static int ensure_beam_queues(aok_ctx* ctx) {
     BeamState& b = ctx->beam;
+    std::lock_guard<std::mutex> lk(b.mu);
     if (b.qblock) return AOK_OK;
     const size_t sq = (size_t)kBeamCap * 16, sc = 2 * kBeamLevels * 4;
     void* block = nullptr;
@@ -849,6 +850,7 @@ static int ensure_bounds(aok_ctx* ctx, unsigned long long** buf, size_t* cap, si
 // is cleared.
 static int next_beam_tag(aok_ctx* ctx, void* stream, uint32_t* tag) {
     BeamState& b = ctx->beam;
+    std::lock_guard<std::mutex> lk(b.mu);
     if (++b.passes >= 0xFFFFFFF0u) {
         const cudaStream_t s = (cudaStream_t)stream;
         if ((b.bounds && cudaMemsetAsync(b.bounds, 0xFF, b.bounds_cap * 8, s) != cudaSuccess) ||
@@ -910,36 +912,45 @@ static int run_beam(aok_ctx* ctx, uint32_t scene, Scene* sc, const SceneDev& sd,
     return AOK_OK;
 }
 
+extern "C++" bool aok::beam_wanted(const aok_ctx* ctx, int32_t W, int32_t H) {
+    return ctx->beam_on && (uint64_t)W * (uint64_t)H >= ctx->beam_min_pixels;
+}
+
 extern "C++" int aok::beam_for_batch(aok_ctx* ctx, BatchParams* groups, uint32_t ngroups,
-                                     std::vector<BeamBatch>& out, void* stream) {
+                                     std::vector<BeamBatch>& out, void* stream,
+                                     unsigned long long* const* view_bounds) {
     out.clear();
     if (!ctx->beam_on) return AOK_OK;
-    size_t need = 0;
+    size_t need = 0, n_big = 0;
     for (uint32_t g = 0; g < ngroups; g++)
         for (uint32_t i = 0; i < groups[g].n_views; i++) {
             const CamDev& c = groups[g].v[i].cam;
-            if ((uint64_t)c.W * (uint64_t)c.H >= ctx->beam_min_pixels) need += beam_entries((uint32_t)c.W, (uint32_t)c.H);
+            if (beam_wanted(ctx, c.W, c.H)) {
+                need += beam_entries((uint32_t)c.W, (uint32_t)c.H);
+                n_big++;
+            }
         }
-    if (!need) return AOK_OK;
+    if (!n_big) return AOK_OK;
     int st = ensure_beam_queues(ctx);
-    if (!st) st = ensure_bounds(ctx, &ctx->batch.beam_bounds, &ctx->batch.beam_cap, need);
+    if (!st && !view_bounds) st = ensure_bounds(ctx, &ctx->batch.beam_bounds, &ctx->batch.beam_cap, need);
     uint32_t tag = 0;
     if (!st) st = next_beam_tag(ctx, stream, &tag);
     if (st) return st;
     out.resize(ngroups);
-    size_t off = 0;
+    size_t off = 0, flat = 0;
     for (uint32_t g = 0; g < ngroups; g++) {
         BeamBatch& B = out[g];
         beam_header(ctx, &B, tag);
         B.n_views = 0;
         B.n_regions = 0;
         groups[g].beam_tag = tag;
-        for (uint32_t i = 0; i < groups[g].n_views; i++) {
+        for (uint32_t i = 0; i < groups[g].n_views; i++, flat++) {
             ViewDev& d = groups[g].v[i];
             d.beam = nullptr;
-            if ((uint64_t)d.cam.W * (uint64_t)d.cam.H < ctx->beam_min_pixels) continue;
-            unsigned long long* bnd = ctx->batch.beam_bounds + off;
+            if (!beam_wanted(ctx, d.cam.W, d.cam.H)) continue;
+            unsigned long long* bnd = view_bounds ? view_bounds[flat] : ctx->batch.beam_bounds + off;
             off += beam_entries((uint32_t)d.cam.W, (uint32_t)d.cam.H);
+            if (!bnd) continue;
             if (!aokk_beam_view(&d.scene, &d.cam, d.frame, bnd, &B.v[B.n_views])) continue;  // casts without
             B.v[B.n_views].region_begin = B.n_regions;
             B.n_regions += (uint32_t)(d.scene.grid[0] * d.scene.grid[1] * d.scene.grid[2]);

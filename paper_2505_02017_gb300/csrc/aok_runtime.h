@@ -94,6 +94,7 @@ struct TileState {
 // the context), the single-view bound pyramid and what its last pass was
 // computed for.
 struct BeamState {
+    std::mutex mu;  // the queues' allocation and the pass counter (the serving thread shares them)
     void* qblock = nullptr;
     size_t qbytes = 0;
     uint4* q[2] = {nullptr, nullptr};
@@ -167,9 +168,13 @@ SceneDev scene_dev(const Scene* sc);
 void batch_release(aok_ctx* ctx);
 void free_alloc(Scene* sc, ChunkAlloc& a);
 // The beam passes of a batch (one per group) for its views of at least the
-// context's beam frame size; sets the views' bounds.  Leaves `out` empty if
-// no view takes the pass.
-int beam_for_batch(aok_ctx* ctx, BatchParams* groups, uint32_t ngroups, std::vector<BeamBatch>& out, void* stream);
+// context's beam frame size; sets the views' bounds, in the batch arena or,
+// with view_bounds, in view_bounds[view] (nullptr: that view casts without).
+// Leaves `out` empty if no view takes the pass.
+int beam_for_batch(aok_ctx* ctx, BatchParams* groups, uint32_t ngroups, std::vector<BeamBatch>& out, void* stream,
+                   unsigned long long* const* view_bounds = nullptr);
+// Whether a frame of W x H pixels takes the beam pass in this context.
+bool beam_wanted(const aok_ctx* ctx, int32_t W, int32_t H);
 // Pinned staging memory and the stream its copies go on.
 struct Staging {
     void* buf = nullptr;

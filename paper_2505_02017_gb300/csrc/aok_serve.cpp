@@ -201,6 +201,7 @@ struct Ticket {
     void* hit = nullptr;
     float* t = nullptr;
     ChunkRef* frame = nullptr;
+    unsigned long long* bounds = nullptr;  // beam-pass pyramid (large frames with the pass on)
     size_t bytes = 0;
     int status = AOK_OK;
 };
@@ -263,9 +264,14 @@ static void CUDART_CB on_batch_done(void* p) {
     wake_loop(b->S);
 }
 
-static size_t request_bytes(const Scene* sc, const aok_camera& cam) {
+// A request's device memory: frame record, distances, chunk table and, for a
+// frame that takes the beam pass, its bound pyramid.
+static size_t request_bytes(const aok_ctx* ctx, const Scene* sc, const aok_camera& cam) {
     const size_t px = (size_t)cam.width * cam.height;
-    return ((px * 16 + 255) & ~(size_t)255) + ((px * 4 + 255) & ~(size_t)255) + (size_t)sc->n_chunks * sizeof(ChunkRef);
+    size_t b = ((px * 16 + 255) & ~(size_t)255) + ((px * 4 + 255) & ~(size_t)255) +
+               (((size_t)sc->n_chunks * sizeof(ChunkRef) + 255) & ~(size_t)255);
+    if (beam_wanted(ctx, cam.width, cam.height)) b += (size_t)beam_entries((uint32_t)cam.width, (uint32_t)cam.height) * 8;
+    return b;
 }
 
 static void free_ticket_memory(aok_ctx* ctx, Ticket& t, cudaStream_t s) {
@@ -276,6 +282,7 @@ static void free_ticket_memory(aok_ctx* ctx, Ticket& t, cudaStream_t s) {
     t.hit = nullptr;
     t.t = nullptr;
     t.frame = nullptr;
+    t.bounds = nullptr;
     t.bytes = 0;
 }
 
@@ -335,7 +342,7 @@ static void serve_loop(aok_ctx* ctx) {
                     S.pending.pop_front();
                     continue;
                 }
-                const size_t bytes = request_bytes(sc, t.req.cam);
+                const size_t bytes = request_bytes(ctx, sc, t.req.cam);
                 if (charge(ctx, bytes) != AOK_OK) break;  // wait for memory to free up
                 void* mem = nullptr;
                 if (cudaMallocFromPoolAsync(&mem, bytes, S.pool, S.streams[slot]) != cudaSuccess) {
@@ -347,6 +354,10 @@ static void serve_loop(aok_ctx* ctx) {
                 t.hit = mem;
                 t.t = (float*)((char*)mem + ((px * 16 + 255) & ~(size_t)255));
                 t.frame = (ChunkRef*)((char*)t.t + ((px * 4 + 255) & ~(size_t)255));
+                t.bounds = beam_wanted(ctx, t.req.cam.width, t.req.cam.height)
+                               ? (unsigned long long*)((char*)t.frame +
+                                                       (((size_t)sc->n_chunks * sizeof(ChunkRef) + 255) & ~(size_t)255))
+                               : nullptr;
                 t.bytes = bytes;
                 t.state = kRunning;
                 S.running++;
@@ -394,7 +405,27 @@ static void serve_loop(aok_ctx* ctx) {
                 P.total_tiles = tiles;
             }
         }
-        if (rc == AOK_OK) rc = aokk_batch_run(S.params.data(), ngroups, L.ctas, L.threads, st, nullptr, 0, nullptr);
+        // the beam pass for the large requests (grid launch): their pyramids
+        // are fresh pool memory, so every entry is first set to "no tag"
+        std::vector<BeamBatch> beams;
+        if (rc == AOK_OK && L.ctas == 0) {
+            std::vector<unsigned long long*> vb(batch.size(), nullptr);
+            {
+                std::lock_guard<std::mutex> g(S.mu);
+                for (size_t i = 0; i < batch.size(); i++) vb[i] = S.tickets[batch[i]].bounds;
+            }
+            for (size_t i = 0; i < batch.size() && rc == AOK_OK; i++) {
+                if (!vb[i]) continue;
+                const ViewDev& d = S.params[i / kBatchViews].v[i % kBatchViews];
+                if (cudaMemsetAsync(vb[i], 0xFF, (size_t)beam_entries((uint32_t)d.cam.W, (uint32_t)d.cam.H) * 8, st) !=
+                    cudaSuccess)
+                    rc = AOK_E_CUDA;
+            }
+            if (rc == AOK_OK) rc = beam_for_batch(ctx, S.params.data(), ngroups, beams, st, vb.data());
+        }
+        if (rc == AOK_OK)
+            rc = aokk_batch_run(S.params.data(), ngroups, L.ctas, L.threads, st, beams.empty() ? nullptr : beams.data(),
+                                ctx->beam.grid, nullptr);
         std::lock_guard<std::mutex> g(S.mu);
         if (rc != AOK_OK) {
             for (uint64_t id : batch) {
@@ -611,7 +642,7 @@ int aok_serve_submit(aok_ctx* ctx, const aok_request* req, uint64_t* ticket) {
     CamDev cd;
     int st = make_cam(ctx, sc, &req->cam, req->lod_threshold_px, &cd);
     if (st) return st;
-    if (request_bytes(sc, req->cam) > ctx->budget) return AOK_E_OOM;  // can never be admitted
+    if (request_bytes(ctx, sc, req->cam) > ctx->budget) return AOK_E_OOM;  // can never be admitted
     {
         std::lock_guard<std::mutex> g(S->mu);
         if (S->stop) return AOK_E_INVALID;

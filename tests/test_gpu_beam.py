@@ -301,3 +301,25 @@ def test_batch_with_beam_equals_plain(ctx):
     torch.cuda.synchronize()
     for i, (ref, out) in enumerate(zip(refs, outs)):
         assert same(ref, out), i
+
+
+def test_served_with_beam_equals_plain(ctx):
+    """The server runs the beam pass for its batches (per-request bound
+    pyramids, passes on several streams one after another): every served
+    frame equals the plain render."""
+    w1, sc1, _ = scene_for(ctx, MED64)
+    w2, sc2, _ = scene_for(ctx, MULTI32)
+    reqs = [(sc1, sg.ground_camera(w1, s, 96 + 8 * (s % 5), 64 + 4 * (s % 3), z_lo=4, z_hi=40)) for s in range(20, 32)]
+    reqs += [(sc2, sg.ground_camera(w2, s, 64, 40, z_lo=4, z_hi=20)) for s in range(4, 10)]
+    refs = [render(ctx, sc, cam, 1.0, False) for sc, cam in reqs]
+    aok.set_beam(ctx, True)
+    srv = aok.Server(ctx, max_slots=16, max_batch=4, n_streams=3)
+    try:
+        tickets = [srv.submit(sc, cam, 1.0) for sc, cam in reqs]
+        for i, tk in enumerate(tickets):
+            st, f = srv.wait(tk, 60000)
+            assert st == aok.AOK_OK, st
+            assert same(refs[i], srv.result(tk, f)), i
+            assert srv.release(tk) == aok.AOK_OK
+    finally:
+        srv.stop()
