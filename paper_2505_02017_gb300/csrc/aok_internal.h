@@ -205,8 +205,14 @@ int aokk_read_bw(const void* buf, size_t n16, int passes, uint32_t* sink, int sm
 // casting launch over all views' warp tiles.
 int aokk_select_batch(const aok::BatchParams* p, void* stream);
 int aokk_cast_batch(const aok::BatchParams* p, uint32_t ctas, uint32_t threads, void* stream);
+// A batch's beam passes on a stream of their own: the pass waits for the
+// group's selection (event sel), the cast for the pass (event beam).
+struct BeamHandoff {
+    void* stream;
+    cudaEvent_t sel, beam;
+};
 int aokk_batch_run(const aok::BatchParams* groups, uint32_t n_groups, uint32_t ctas, uint32_t threads, void* stream,
-                   const aok::BeamBatch* beams, unsigned beam_grid,
+                   const aok::BeamBatch* beams, unsigned beam_grid, const BeamHandoff* handoff,
                    aok::GraphCache* gc);
 void aokk_graph_destroy(aok::GraphCache* gc);
 int aokk_max_ctas_per_sm(uint32_t threads);

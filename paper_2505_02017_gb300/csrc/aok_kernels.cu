@@ -272,12 +272,24 @@ int aokk_cast_batch(const BatchParams* p, uint32_t ctas, uint32_t threads, void*
 // graph built per shape (group sizes, launch dims) whose kernel nodes are
 // updated with the new parameters on every call.
 int aokk_batch_run(const BatchParams* groups, uint32_t n_groups, uint32_t ctas, uint32_t threads, void* stream,
-                   const BeamBatch* beams, unsigned beam_grid, GraphCache* gc) {
+                   const BeamBatch* beams, unsigned beam_grid, const BeamHandoff* handoff, GraphCache* gc) {
     const cudaStream_t st = (cudaStream_t)stream;
     if (!gc || beams) {
         for (uint32_t g = 0; g < n_groups; g++) {
             int r = aokk_select_batch(&groups[g], stream);
-            if (!r && beams) r = aokk_beam_run(&beams[g], beam_grid, stream);
+            if (!r && beams && beams[g].n_views) {
+                if (handoff) {
+                    const cudaStream_t bs = (cudaStream_t)handoff->stream;
+                    if (cudaEventRecord(handoff->sel, st) != cudaSuccess || cudaStreamWaitEvent(bs, handoff->sel, 0) != cudaSuccess)
+                        return AOK_E_CUDA;
+                    r = aokk_beam_run(&beams[g], beam_grid, handoff->stream);
+                    if (!r && (cudaEventRecord(handoff->beam, bs) != cudaSuccess ||
+                               cudaStreamWaitEvent(st, handoff->beam, 0) != cudaSuccess))
+                        r = AOK_E_CUDA;
+                } else {
+                    r = aokk_beam_run(&beams[g], beam_grid, stream);
+                }
+            }
             if (!r) r = aokk_cast_batch(&groups[g], ctas, threads, stream);
             if (r) return r;
         }

@@ -153,7 +153,8 @@ static int render_batch_impl(aok_ctx* ctx, const aok_view* views, uint32_t n, vo
         if (st) return st;
     }
     st = aokk_batch_run(prep.groups.data(), (uint32_t)prep.groups.size(), L.ctas, L.threads, stream,
-                        beams.empty() ? nullptr : beams.data(), ctx->beam.grid, use_graph ? &ctx->batch.graph : nullptr);
+                        beams.empty() ? nullptr : beams.data(), ctx->beam.grid, nullptr,
+                        use_graph ? &ctx->batch.graph : nullptr);
     return st == AOK_E_CUDA ? cuda_status(ctx, cudaGetLastError()) : st;
 }
 
@@ -230,6 +231,8 @@ struct ServeState {
     std::condition_variable wake_cv;
     int wake = 0;
     std::vector<cudaStream_t> streams;
+    cudaStream_t beam_stream = nullptr;  // the batches' beam passes
+    std::vector<cudaEvent_t> beam_ev;    // per stream: selection done, beam pass done
     std::vector<unsigned long long*> counters;  // 2 * kBatchViews-group pairs per stream
     std::vector<uint32_t> stream_busy;
     std::mutex mu;
@@ -423,9 +426,13 @@ static void serve_loop(aok_ctx* ctx) {
             }
             if (rc == AOK_OK) rc = beam_for_batch(ctx, S.params.data(), ngroups, beams, st, vb.data());
         }
-        if (rc == AOK_OK)
+        if (rc == AOK_OK) {
+            // the server's passes share one stream: a pass waits only for its
+            // batch's selection and for the passes before it
+            const BeamHandoff ho{S.beam_stream, S.beam_ev[2 * slot], S.beam_ev[2 * slot + 1]};
             rc = aokk_batch_run(S.params.data(), ngroups, L.ctas, L.threads, st, beams.empty() ? nullptr : beams.data(),
-                                ctx->beam.grid, nullptr);
+                                ctx->beam.grid, &ho, nullptr);
+        }
         std::lock_guard<std::mutex> g(S.mu);
         if (rc != AOK_OK) {
             for (uint64_t id : batch) {
@@ -572,7 +579,13 @@ int aok_serve_start(aok_ctx* ctx, uint32_t max_slots, uint32_t max_batch, uint32
         cudaMemset(c, 0, 2 * ngroups * sizeof(unsigned long long));
         S->counters.push_back(c);
         S->stream_busy.push_back(0);
+        for (int k = 0; k < 2; k++) {
+            cudaEvent_t e;
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return AOK_E_CUDA;
+            S->beam_ev.push_back(e);
+        }
     }
+    if (cudaStreamCreateWithFlags(&S->beam_stream, cudaStreamNonBlocking) != cudaSuccess) return AOK_E_CUDA;
     cudaMemPoolProps props;
     std::memset(&props, 0, sizeof(props));
     props.allocType = cudaMemAllocationTypePinned;
@@ -611,6 +624,11 @@ int aok_serve_stop(aok_ctx* ctx) {
     cudaSetDevice(ctx->device);
     for (auto& kv : S->tickets) free_ticket_memory(ctx, kv.second, S->streams[0]);
     for (cudaStream_t s : S->streams) cudaStreamSynchronize(s);
+    if (S->beam_stream) {
+        cudaStreamSynchronize(S->beam_stream);
+        cudaStreamDestroy(S->beam_stream);
+    }
+    for (cudaEvent_t e : S->beam_ev) cudaEventDestroy(e);
     for (size_t i = 0; i < S->streams.size(); i++) {
         dev_free(ctx, S->counters[i], 0);
         cudaStreamDestroy(S->streams[i]);
