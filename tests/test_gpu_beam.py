@@ -323,3 +323,22 @@ def test_served_with_beam_equals_plain(ctx):
             assert srv.release(tk) == aok.AOK_OK
     finally:
         srv.stop()
+
+
+def test_random_cameras_equal(ctx):
+    """Seeded random poses inside and outside the worlds, looking anywhere
+    (axis-aligned and grazing directions included): beam on == beam off."""
+    rng = sg.Rng(2024)
+    for spec in (MULTI16, MED64):
+        w, sc, _ = scene_for(ctx, spec)
+        for k in range(24):
+            o = (rng.uniform(-0.3, 1.3) * spec.wx, rng.uniform(-0.3, 1.3) * spec.wy, rng.uniform(-0.2, 1.2) * spec.wz)
+            if k % 6 == 0:
+                fwd = [(1.0, 0.0, 0.0), (0.0, -1.0, 0.0), (0.0, 0.0, -1.0)][(k // 6) % 3]
+            else:
+                fwd = (rng.uniform(-1, 1), rng.uniform(-1, 1), rng.uniform(-1, 0.3))
+            cam = sg.make_camera(o, fwd, 24 + (k % 5) * 8, 16 + (k % 3) * 4, fovy_deg=30.0 + 20.0 * (k % 4))
+            off = render(ctx, sc, cam, 1.0, False)
+            on = render(ctx, sc, cam, 1.0, True)
+            assert same(off, on), (spec.name, k)
+            check_bounds(ctx, cam, on)
