@@ -350,6 +350,7 @@ void aok_destroy(aok_ctx* ctx) {
     dev_free(ctx, ctx->beam.qblock, ctx->beam.qbytes);
     dev_free(ctx, ctx->beam.bounds, ctx->beam.bounds_cap * 8);
     pipe_release(ctx);
+    if (ctx->pipe.prep) cudaStreamDestroy(ctx->pipe.prep);
     if (ctx->pipe.render) cudaStreamDestroy(ctx->pipe.render);
     if (ctx->pipe.copy) cudaStreamDestroy(ctx->pipe.copy);
     if (ctx->staging) cudaFreeHost(ctx->staging);
@@ -1289,6 +1290,9 @@ static void pipe_release(aok_ctx* ctx) {
         if (sl.copied) cudaEventSynchronize(sl.copied);
         dev_free(ctx, sl.hit, p.px * 16);
         dev_free(ctx, sl.t, p.px * 4);
+        dev_free(ctx, sl.frame, sl.frame_cap * sizeof(ChunkRef));
+        dev_free(ctx, sl.bounds, sl.bounds_cap * 8);
+        if (sl.prepped) cudaEventDestroy(sl.prepped);
         if (sl.rendered) cudaEventDestroy(sl.rendered);
         if (sl.copied) cudaEventDestroy(sl.copied);
         sl = HostSlot();
@@ -1299,16 +1303,21 @@ static void pipe_release(aok_ctx* ctx) {
 static int pipe_ensure(aok_ctx* ctx, size_t px) {
     HostPipe& p = ctx->pipe;
     if (!p.render) {
-        if (cudaStreamCreateWithFlags(&p.render, cudaStreamNonBlocking) != cudaSuccess ||
+        int least = 0, greatest = 0;
+        cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        if (cudaStreamCreateWithPriority(&p.prep, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&p.render, cudaStreamNonBlocking) != cudaSuccess ||
             cudaStreamCreateWithFlags(&p.copy, cudaStreamNonBlocking) != cudaSuccess)
             return cuda_status(ctx, cudaGetLastError());
+        p.P.reset(new BeamBatch);
     }
     if (px <= p.px) return AOK_OK;
     pipe_release(ctx);
     for (HostSlot& sl : p.slot) {
         int st = dev_alloc(ctx, &sl.hit, px * 16);
         if (!st) st = dev_alloc(ctx, (void**)&sl.t, px * 4);
-        if (!st && (cudaEventCreateWithFlags(&sl.rendered, cudaEventDisableTiming) != cudaSuccess ||
+        if (!st && (cudaEventCreateWithFlags(&sl.prepped, cudaEventDisableTiming) != cudaSuccess ||
+                    cudaEventCreateWithFlags(&sl.rendered, cudaEventDisableTiming) != cudaSuccess ||
                     cudaEventCreateWithFlags(&sl.copied, cudaEventDisableTiming) != cudaSuccess))
             st = cuda_status(ctx, cudaGetLastError());
         if (st) {
@@ -1319,6 +1328,58 @@ static int pipe_ensure(aok_ctx* ctx, size_t px) {
     }
     p.px = px;
     return AOK_OK;
+}
+
+// A slot's frame: selection into the slot's chunk table and the beam pass
+// into its pyramid on the prep stream, then the cast on the render stream.
+static int pipe_render(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double tau, HostSlot& sl) {
+    HostPipe& p = ctx->pipe;
+    Scene* sc = find_scene(ctx, scene);
+    if (!sc) return AOK_E_NOT_RESIDENT;
+    CamDev cd;
+    int st = make_cam(ctx, sc, cam, tau, &cd);
+    if (st) return st;
+    if ((size_t)sc->n_chunks > sl.frame_cap) {
+        dev_free(ctx, sl.frame, sl.frame_cap * sizeof(ChunkRef));
+        sl.frame = nullptr;
+        sl.frame_cap = 0;
+        st = dev_alloc(ctx, (void**)&sl.frame, (size_t)sc->n_chunks * sizeof(ChunkRef));
+        if (st) return st;
+        sl.frame_cap = (size_t)sc->n_chunks;
+    }
+    const bool beam = beam_wanted(ctx, cd.W, cd.H);
+    if (beam) {
+        st = ensure_beam_queues(ctx);
+        if (!st) st = ensure_bounds(ctx, &sl.bounds, &sl.bounds_cap, beam_entries((uint32_t)cd.W, (uint32_t)cd.H));
+        if (st) return st;
+    }
+    const SceneDev sd = scene_dev(sc);
+    st = aokk_select(&sd, &cd, sl.frame, nullptr, nullptr, nullptr, p.prep);
+    if (st) return cuda_status(ctx, cudaGetLastError());
+    BeamRead rd{nullptr, 0};
+    if (beam) {
+        uint32_t tag;
+        st = next_beam_tag(ctx, p.prep, &tag);
+        if (st) return st;
+        BeamBatch* P = p.P.get();
+        beam_header(ctx, P, tag);
+        P->n_views = 0;
+        P->n_regions = 0;
+        if (aokk_beam_view(&sd, &cd, sl.frame, sl.bounds, &P->v[0])) {
+            P->v[0].region_begin = 0;
+            P->n_views = 1;
+            P->n_regions = (uint32_t)sc->n_chunks;
+            rd.bounds = sl.bounds;
+            rd.tag = tag;
+        }
+        st = aokk_beam_run(P, ctx->beam.grid, p.prep);
+        if (st) return cuda_status(ctx, cudaGetLastError());
+    }
+    cudaError_t e = cudaEventRecord(sl.prepped, p.prep);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p.render, sl.prepped, 0);
+    if (e != cudaSuccess) return cuda_status(ctx, e);
+    st = aokk_cast(&sd, &cd, sl.frame, (uint4*)sl.hit, sl.t, nullptr, p.render, nullptr, rd.bounds ? &rd : nullptr);
+    return st ? cuda_status(ctx, cudaGetLastError()) : AOK_OK;
 }
 }  // extern "C++"
 
@@ -1333,8 +1394,13 @@ int aok_render_host_async(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, d
     HostSlot& sl = p.slot[p.next % kHostSlots];
     // the slot's previous frame must have left the device buffers
     if (sl.ticket && cudaEventSynchronize(sl.copied) != cudaSuccess) return cuda_status(ctx, cudaGetLastError());
-    aok_frame f{sl.hit, sl.t};
-    st = aok_render(ctx, scene, cam, tau, &f, p.render);
+    if (ctx->checked || ctx->single_persistent) {
+        // these modes render through the context's own path on the render stream
+        aok_frame f{sl.hit, sl.t};
+        st = aok_render(ctx, scene, cam, tau, &f, p.render);
+    } else {
+        st = pipe_render(ctx, scene, cam, tau, sl);
+    }
     if (st) return st;
     cudaError_t e = cudaEventRecord(sl.rendered, p.render);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(p.copy, sl.rendered, 0);

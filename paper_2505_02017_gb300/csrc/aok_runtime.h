@@ -62,20 +62,27 @@ struct BatchArena {
 
 struct ServeState;
 
-// Frames rendered into host memory through a pipeline: slot k's render (on
-// `render`) overlaps slot k-1's device-to-host copy (on `copy`).
+// Frames rendered into host memory through a pipeline: slot k's selection
+// and beam pass (on `prep`, the highest stream priority) overlap slot k-1's
+// cast (on `render`), which overlaps slot k-2's device-to-host copy (on
+// `copy`).  Each slot has its own chunk table and bound pyramid.
 constexpr int kHostSlots = 3;
 struct HostSlot {
     void* hit = nullptr;
     float* t = nullptr;
-    cudaEvent_t rendered = nullptr, copied = nullptr;
+    ChunkRef* frame = nullptr;  // the slot's chunk table
+    size_t frame_cap = 0;       // entries
+    unsigned long long* bounds = nullptr;  // the slot's bound pyramid
+    size_t bounds_cap = 0;                 // entries
+    cudaEvent_t prepped = nullptr, rendered = nullptr, copied = nullptr;
     uint64_t ticket = 0;  // frame in this slot (0: none yet)
 };
 struct HostPipe {
-    cudaStream_t render = nullptr, copy = nullptr;
+    cudaStream_t prep = nullptr, render = nullptr, copy = nullptr;
     HostSlot slot[kHostSlots];
     size_t px = 0;        // pixels each slot holds
     uint64_t next = 0;    // last ticket issued
+    std::unique_ptr<BeamBatch> P;  // beam pass parameter block
 };
 
 // Buffers of the tile-chunk pipeline for one resolution and grid size (one

@@ -342,3 +342,20 @@ def test_random_cameras_equal(ctx):
             on = render(ctx, sc, cam, 1.0, True)
             assert same(off, on), (spec.name, k)
             check_bounds(ctx, cam, on)
+
+
+def test_pipelined_host_frames_with_beam(ctx):
+    """aok_render_host_async: each slot's selection and beam pass run on the
+    prep stream while the previous slot casts; every frame equals the plain
+    render, for a sequence of poses longer than the pipeline."""
+    w, sc, _ = scene_for(ctx, MED64)
+    cams = sg.path_cameras(w, 31, 7, 150, 100, n_waypoints=3, span=150.0, z_lo=4.0, z_hi=40.0)
+    refs = [render(ctx, sc, cam, 1.0, False) for cam in cams]
+    aok.set_beam(ctx, True)
+    hh = [torch.empty((c.H, c.W, 4), dtype=torch.int32, pin_memory=True) for c in cams]
+    th = [torch.empty((c.H, c.W), dtype=torch.float32, pin_memory=True) for c in cams]
+    tickets = [aok.render_host_async(ctx, sc, c, 1.0, h, t) for c, h, t in zip(cams, hh, th)]
+    for tk in tickets:
+        aok.host_frame_wait(ctx, tk)
+    for i, (ref, h, t) in enumerate(zip(refs, hh, th)):
+        assert torch.equal(ref[0].cpu(), h) and torch.equal(ref[1].cpu().view(torch.int32), t.view(torch.int32)), i
