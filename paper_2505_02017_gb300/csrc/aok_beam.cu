@@ -58,7 +58,7 @@ using namespace aok;
 namespace {
 
 constexpr int kBeamThreads = 256;      // block size of the cooperative walk
-constexpr int kBeamBlocksPerSM = 2;    // at most this many blocks per SM (fewer blocks: cheaper barriers)
+constexpr int kBeamBlocksPerSM = 1;    // blocks per SM: one leaves room to start beside a running cast
 constexpr double kNearS = 1.0 / 16.0;  // camera-depth plane the projection clips at
 constexpr uint32_t kNoItem = 0xFFFFFFFFu;  // an empty queue slot
 constexpr int kMaxBeamDevices = 128;
