@@ -58,7 +58,9 @@ using namespace aok;
 namespace {
 
 constexpr int kBeamThreads = 256;      // block size of the cooperative walk
-constexpr int kBeamBlocksPerSM = 1;    // blocks per SM: one leaves room to start beside a running cast
+constexpr int kBeamBlocksPerSM = 2;    // blocks per SM of the full grid (walks over many regions)
+constexpr uint32_t kWideWalkRegions = 4096;  // above this many regions a pass takes the full grid; below,
+                                             // one block per SM, which can start beside a running cast
 constexpr double kNearS = 1.0 / 16.0;  // camera-depth plane the projection clips at
 constexpr uint32_t kNoItem = 0xFFFFFFFFu;  // an empty queue slot
 constexpr int kMaxBeamDevices = 128;
@@ -417,7 +419,8 @@ int aokk_beam_run(const BeamBatch* P, unsigned grid, void* stream) {
     // queue counts and the walk histogram (cnt and hist are adjacent)
     if (cudaMemsetAsync(P->cnt, 0, 2 * kBeamLevels * sizeof(uint32_t), st) != cudaSuccess) return AOK_E_CUDA;
     void* args[] = {(void*)P};
-    if (cudaLaunchCooperativeKernel((const void*)beam_kernel, grid, kBeamThreads, args, 0, st) != cudaSuccess)
+    const unsigned g = P->n_regions > kWideWalkRegions ? grid : (grid + kBeamBlocksPerSM - 1) / kBeamBlocksPerSM;
+    if (cudaLaunchCooperativeKernel((const void*)beam_kernel, g, kBeamThreads, args, 0, st) != cudaSuccess)
         return AOK_E_CUDA;
     if (cudaEventRecord(g_beam_done[dev], st) != cudaSuccess) return AOK_E_CUDA;
     return AOK_OK;
