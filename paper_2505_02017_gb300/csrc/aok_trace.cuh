@@ -249,10 +249,12 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
         } else {
             // leave cell (k, c) through its nearest exit face; while the
             // neighbour is an empty sibling in the same parent, keep going
+            // (the exit planes of the level, advanced one cell per step)
+            const int32_t side = 1 << (k + kFix);
+            int32_t N0 = ((c0 + 1) << (k + kFix)) - Oloc[0];
+            int32_t N1 = ((c1 + 1) << (k + kFix)) - Oloc[1];
+            int32_t N2 = ((c2 + 1) << (k + kFix)) - Oloc[2];
             for (;;) {
-                const int32_t N0 = ((c0 + 1) << (k + kFix)) - Oloc[0];
-                const int32_t N1 = ((c1 + 1) << (k + kFix)) - Oloc[1];
-                const int32_t N2 = ((c2 + 1) << (k + kFix)) - Oloc[2];
                 const bool xy = tltf<FAST>(N0, r.m[0], N1, r.m[1], r.E[1] - r.E[0]);
                 const int32_t Na = xy ? N0 : N1, ma = xy ? r.m[0] : r.m[1], Ea = xy ? r.E[0] : r.E[1];
                 const bool az = tltf<FAST>(Na, ma, N2, r.m[2], r.E[2] - Ea);
@@ -261,9 +263,9 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
                 else { ax = 2; Ne = N2; me = r.m[2]; Ee = r.E[2]; }
                 e = ax;
                 int32_t cax;
-                if (ax == 0) cax = ++c0;
-                else if (ax == 1) cax = ++c1;
-                else cax = ++c2;
+                if (ax == 0) { cax = ++c0; N0 += side; }
+                else if (ax == 1) { cax = ++c1; N1 += side; }
+                else { cax = ++c2; N2 += side; }
                 if ((cax << k) >= (1 << R)) return false;  // left the chunk
                 if ((cax & 1) == 0) {
                     do {
