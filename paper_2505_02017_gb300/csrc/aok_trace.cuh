@@ -254,8 +254,8 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
             int32_t N0 = ((c0 + 1) << (k + kFix)) - Oloc[0];
             int32_t N1 = ((c1 + 1) << (k + kFix)) - Oloc[1];
             int32_t N2 = ((c2 + 1) << (k + kFix)) - Oloc[2];
+            bool xy = tltf<FAST>(N0, r.m[0], N1, r.m[1], r.E[1] - r.E[0]);
             for (;;) {
-                const bool xy = tltf<FAST>(N0, r.m[0], N1, r.m[1], r.E[1] - r.E[0]);
                 const int32_t Na = xy ? N0 : N1, ma = xy ? r.m[0] : r.m[1], Ea = xy ? r.E[0] : r.E[1];
                 const bool az = tltf<FAST>(Na, ma, N2, r.m[2], r.E[2] - Ea);
                 int ax;
@@ -278,6 +278,7 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
                 }
                 if ((pm8 >> (((uint32_t)(c0 & 1) | ((uint32_t)(c1 & 1) << 1) | ((uint32_t)(c2 & 1) << 2)) ^ r.mir)) & 1u)
                     break;  // an occupied sibling
+                if (ax != 2) xy = tltf<FAST>(N0, r.m[0], N1, r.m[1], r.E[1] - r.E[0]);  // x against y changed
             }
         }
         // occupancy of cell (k, c) in its parent
