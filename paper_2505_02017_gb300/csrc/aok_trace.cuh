@@ -159,6 +159,84 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
     uint32_t pm8 = 0;   // parent's child mask, stored octant order (node mask / leaf groups / group voxels)
     uint32_t g8 = 0;    // group occupancy of the current leaf block
     bool occ = true;
+    // Child masks of the occupied cell (k, c) into pm8: its node's mask
+    // (interior levels, also pushed on the stack), its leaf block's group
+    // occupancy (leaf level) or its 2x2x2 group's voxel bits.  False when a
+    // checked build finds a pool index out of range.
+    uint32_t* const st_idx = sidx;
+    uint32_t* const st_mask = smask;
+    auto fetch = [&]() -> bool {
+        if (k >= n + 2) {
+            uint32_t idx;
+            if (k == R) {
+                idx = ref.root;
+            } else {
+                const uint32_t oct = ((uint32_t)(c0 & 1) | ((uint32_t)(c1 & 1) << 1) | ((uint32_t)(c2 & 1) << 2)) ^ r.mir;
+                const uint64_t at = (uint64_t)st_idx[k + 1] + 2 + 2 * __popc(st_mask[k + 1] & ((1u << oct) - 1u));
+                if (out_of<CHECK>(at, ck ? ck->n_nodes : 0, ck, 1u)) return false;
+                idx = nodes[at];
+            }
+            if (k >= n + 3) {
+                if (out_of<CHECK>((uint64_t)idx + 1, ck ? ck->n_nodes : 0, ck, 1u)) return false;
+                pm8 = nodes[idx] & 0xFFu;
+                st_idx[k] = idx;
+                st_mask[k] = pm8;
+                if (COUNT) cnt.v_int++;
+            } else {
+                if (out_of<CHECK>(idx, ck ? ck->n_leaves : 0, ck, 2u)) return false;
+                lmu = S.leaves[idx];
+                uint64_t t = lmu | (lmu >> 1);
+                t |= t >> 4;
+                t |= t >> 16;
+                g8 = (uint32_t)((t & 1) | ((t >> 1) & 2) | ((t >> 6) & 4) | ((t >> 7) & 8) | ((t >> 28) & 16) |
+                                ((t >> 29) & 32) | ((t >> 34) & 64) | ((t >> 35) & 128));
+                pm8 = g8;
+                if (COUNT) cnt.v_leaf++;
+            }
+        } else {
+            // entering a 2x2x2 group of the leaf: its 8 voxel bits in octant order
+            const uint64_t v = lmu >> (((c0 & 1) ^ f1) * 2 + ((c1 & 1) ^ f2) * 8 + ((c2 & 1) ^ f4) * 32);
+            pm8 = (uint32_t)((v & 3) | ((v >> 2) & 0xC) | ((v >> 12) & 0x30) | ((v >> 14) & 0xC0));
+        }
+        return true;
+    };
+    if (FAST) {
+        // First descent.  Until the first empty cell, every cell entered is
+        // the one holding the entry point, so its coordinates at level j are
+        // those of the entry point's voxel (level n) shifted right by j - n:
+        // the voxel coordinates F are found once (a float estimate, then the
+        // exact plane comparisons of the descent: a plane crossed no later
+        // than the entry is passed), and the descent needs no comparison per
+        // level.  F is clamped to the chunk as the per-level halving would.
+        const int sh = n + kFix;
+        const int32_t fmax = (1 << (R - n)) - 1;
+        const float te = e < 3 ? __fdividef((float)Ne, (float)me) : 0.0f;
+        int32_t F[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            int32_t f;
+            if (e == 3 || r.m[a] == 0) {
+                f = Oloc[a] >> sh;  // the origin's coordinate
+            } else if (a == e) {
+                f = (Ne + Oloc[a]) >> sh;  // on the entry plane
+            } else {
+                const float p = ((float)Oloc[a] + te * (float)r.m[a]) * (1.0f / (float)(1 << sh));
+                f = (int32_t)floorf(fminf(fmaxf(p, -1.0f), (float)fmax + 1.0f));
+                while (f < fmax && !tltf<FAST>(Ne, me, ((f + 1) << sh) - Oloc[a], r.m[a], 0)) f++;
+                while (f > 0 && tltf<FAST>(Ne, me, (f << sh) - Oloc[a], r.m[a], 0)) f--;
+            }
+            F[a] = max(0, min(f, fmax));
+        }
+        for (;;) {
+            if (!fetch()) return false;
+            k--;
+            c0 = F[0] >> (k - n);
+            c1 = F[1] >> (k - n);
+            c2 = F[2] >> (k - n);
+            occ = (pm8 >> (((uint32_t)(c0 & 1) | ((uint32_t)(c1 & 1) << 1) | ((uint32_t)(c2 & 1) << 2)) ^ r.mir)) & 1u;
+            if (!occ || k == n) break;
+        }
+    }
     for (;;) {
         if (occ) {
             if (k == n) {
@@ -202,38 +280,7 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
                 if (COUNT) cnt.rbytes += 1;
                 return true;
             }
-            if (k >= n + 2) {
-                uint32_t idx;
-                if (k == R) {
-                    idx = ref.root;
-                } else {
-                    const uint32_t oct = ((uint32_t)(c0 & 1) | ((uint32_t)(c1 & 1) << 1) | ((uint32_t)(c2 & 1) << 2)) ^ r.mir;
-                    const uint64_t at = (uint64_t)sidx[k + 1] + 2 + 2 * __popc(smask[k + 1] & ((1u << oct) - 1u));
-                    if (out_of<CHECK>(at, ck ? ck->n_nodes : 0, ck, 1u)) return false;
-                    idx = nodes[at];
-                }
-                if (k >= n + 3) {
-                    if (out_of<CHECK>((uint64_t)idx + 1, ck ? ck->n_nodes : 0, ck, 1u)) return false;
-                    pm8 = nodes[idx] & 0xFFu;
-                    sidx[k] = idx;
-                    smask[k] = pm8;
-                    if (COUNT) cnt.v_int++;
-                } else {
-                    if (out_of<CHECK>(idx, ck ? ck->n_leaves : 0, ck, 2u)) return false;
-                    lmu = S.leaves[idx];
-                    uint64_t t = lmu | (lmu >> 1);
-                    t |= t >> 4;
-                    t |= t >> 16;
-                    g8 = (uint32_t)((t & 1) | ((t >> 1) & 2) | ((t >> 6) & 4) | ((t >> 7) & 8) | ((t >> 28) & 16) |
-                                    ((t >> 29) & 32) | ((t >> 34) & 64) | ((t >> 35) & 128));
-                    pm8 = g8;
-                    if (COUNT) cnt.v_leaf++;
-                }
-            } else {
-                // entering a 2x2x2 group of the leaf: its 8 voxel bits in octant order
-                const uint64_t v = lmu >> (((c0 & 1) ^ f1) * 2 + ((c1 & 1) ^ f2) * 8 + ((c2 & 1) ^ f4) * 32);
-                pm8 = (uint32_t)((v & 3) | ((v >> 2) & 0xC) | ((v >> 12) & 0x30) | ((v >> 14) & 0xC0));
-            }
+            if (!fetch()) return false;
             // child of cell (k, c) holding the entry point: compare t_entry with the mid planes
             const int kk = k - 1;
             const int32_t mid0 = ((2 * c0 + 1) << (kk + kFix)) - Oloc[0];
