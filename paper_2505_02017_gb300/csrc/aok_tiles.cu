@@ -181,7 +181,8 @@ __device__ __forceinline__ int pair_pixel(const SceneDev& S, const CamDev& C, co
     if (cur != kNoKey && en.e < 3 && t_key(en.Ne, r.d[en.e]) > (uint32_t)(cur >> 32)) return 2;
     HitRec hit;
     Counters cnt = {0, 0, 0};
-    if (trace_chunk<FAST, false>(S, ref, r, en.Oloc, en.e, en.Ne, hit, cnt) && within_view(S, r, hit)) {
+    if (trace_chunk<FAST, false>(S, ref, r, en.Oloc, en.e, en.Ne, hit, cnt) &&
+        (lowest_entry_face<FAST>(r, en.Oloc, (int)ref.lod, hit), within_view(S, r, hit))) {
         const uint32_t tk = hit.e < 3 ? t_key(hit.Ne, r.d[hit.e]) : 0u;
         const int n = (int)ref.lod;
         const int32_t side = (1 << (S.mlog - n)) - 1;

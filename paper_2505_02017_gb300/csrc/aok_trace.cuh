@@ -333,6 +333,27 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
     }
 }
 
+// Entry face of a hit entered through an edge or a corner of its voxel (the
+// voxel's lower faces of several axes crossed at the entry instant): the
+// lowest of those axes, with its plane.  n: the hit's LOD; Oloc: the mirrored
+// chunk-local origin numerators trace_chunk was given.
+template <bool FAST>
+__device__ __noinline__ void lowest_entry_face(const RayState& r, const int32_t Oloc[3], int n, HitRec& hit) {
+    const int e = hit.e;
+    if (e == 0 || e == 3) return;
+    const int32_t Ne = hit.Ne, me = r.m[e], Ee = r.E[e];
+#pragma unroll
+    for (int b = 1; b >= 0; b--) {
+        if (b < e && r.d[b] != 0.0f) {
+            const int32_t Nb = (hit.c[b] << (n + kFix)) - Oloc[b];
+            if (!tltf<FAST>(Ne, me, Nb, r.m[b], r.E[b] - Ee) && !tltf<FAST>(Nb, r.m[b], Ne, me, Ee - r.E[b])) {
+                hit.e = b;
+                hit.Ne = Nb;
+            }
+        }
+    }
+}
+
 // With a view distance, a hit farther than it is a miss (FP64, fixed order).
 __device__ __forceinline__ bool within_view(const SceneDev& S, const RayState& r, const HitRec& hit) {
     if (S.view_dist <= 0.0f) return true;
@@ -547,6 +568,7 @@ __device__ __forceinline__ void trace_pixel_t(const SceneDev& S, const CamDev& C
 #pragma unroll
                 for (int a = 0; a < 3; a++) Oloc[a] = Ow[a] - (cc[a] << cs);
                 if (trace_chunk<FAST, COUNT, CHECK, BEAM>(S, ref, r, Oloc, e, Ne, hit, cnt, ck)) {
+                    lowest_entry_face<FAST>(r, Oloc, (int)ref.lod, hit);
                     found = emit_hit(S, r, ref, u, hit, dn, out_hit, out_t, pix);
                     break;
                 }

@@ -100,6 +100,25 @@ def test_small_worlds_equal_and_oracle(ctx, case):
     compare(decode(*on), S.cast(cam, S.select(cam, tau), view_dist=spec.view_dist), max_amb_frac=2e-3)
 
 
+def test_entry_points_on_planes(ctx):
+    """Origins on voxel and chunk planes, directions along two- and three-axis
+    diagonals: restart points and chunk entries on several planes at once."""
+    w, sc, S = scene_for(ctx, MULTI16)
+    origins = [(16.0, 16.0, 27.0), (32.0, 32.0, 29.0), (48.0, 16.0, 26.0), (16.0, 24.5, 28.0)]
+    dirs = [(1.0, 1.0, -1.0), (-1.0, -1.0, -1.0), (1.0, -1.0, -0.5), (1.0, 0.0, -1.0), (1.0, 1.0, -2.0),
+            (2.0, -1.0, -1.0)]
+    for o in origins:
+        for f in dirs:
+            for tau in (1.0, 6.0):
+                cam = sg.make_camera(o, f, 33, 17)
+                off = render(ctx, sc, cam, tau, False)
+                on = render(ctx, sc, cam, tau, True)
+                assert same(off, on), (o, f, tau)
+                check_bounds(ctx, cam, on)
+                compare(decode(*on), S.cast(cam, S.select(cam, tau), view_dist=MULTI16.view_dist), max_amb_frac=0.25,
+                        min_pixels_checked=0)
+
+
 def test_bounds_are_used(ctx):
     """On a walker view most tiles get a positive bound (geometry is not at the camera)."""
     w, sc, _ = scene_for(ctx, MED64)

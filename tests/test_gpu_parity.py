@@ -107,6 +107,31 @@ def test_degenerate_images_and_axis_aligned_rays(ctx):
     compare(g, ref)
 
 
+# Origins on voxel and chunk planes (exact on the 2^-12 grid) and directions
+# along diagonals of two or three axes or in an axis plane: entry points that
+# lie on several planes at once, including a chunk's upper faces, where the
+# traversal's exact ties (a plane crossed no later than the entry is passed)
+# and its clamp to the chunk decide the cell.
+PLANE_ORIGINS = [(16.0, 16.0, 27.0), (32.0, 32.0, 29.0), (48.0, 16.0, 26.0), (24.0, 40.0, 31.0), (16.0, 24.5, 28.0)]
+PLANE_DIRS = [(1.0, 1.0, -1.0), (-1.0, -1.0, -1.0), (1.0, -1.0, -0.5), (1.0, 0.0, -1.0), (0.0, 1.0, -1.0),
+              (1.0, 1.0, -2.0), (2.0, -1.0, -1.0), (1.0, 1.0, 0.0)]
+
+
+def test_entry_points_on_planes(ctx):
+    spec = MULTI16
+    checked = total = 0
+    for o in PLANE_ORIGINS:
+        for f in PLANE_DIRS:
+            for W, H in ((1, 1), (9, 7), (33, 17)):
+                for tau in (1.0, 6.0):  # LOD 0 and LOD 1 chunks
+                    cam = sg.make_camera(o, f, W, H)
+                    g, ref, _ = run(ctx, spec, cam, tau)
+                    c, _ = compare(g, ref, max_amb_frac=0.25, min_pixels_checked=0)
+                    checked += c
+                    total += W * H
+    assert checked > 0.95 * total
+
+
 def test_ray_directions_bitwise(ctx):
     w, _, _ = scene_for(ctx, MED64)
     cam = sg.ground_camera(w, 4, 97, 61, z_lo=4, z_hi=40)
