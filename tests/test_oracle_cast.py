@@ -62,6 +62,41 @@ def test_analytic_straight_down_hit():
     assert r3["hit"] == 0 and r3["lod"] == 255 and np.isinf(r3["dist"])
 
 
+def test_entry_through_an_edge_or_corner_takes_the_lowest_axis():
+    """A ray entering its voxel through an edge or a corner crosses the lower
+    faces of several axes at once; the entry face (normal) is the lowest of
+    those axes, the distance is the common entry distance."""
+    spec = sg.WorldSpec("box", seed=21, wx=32, wy=32, wz=32, chunk=32, n_lods=1, octaves=1, period0=8,
+                        h_min=0, h_max=0, crust=0, n_boxes=1, box_min=3, box_max=3, box_hollow=0)
+    w = sg.World(spec)
+    bx, by, bz, sx, sy, sz, _ = w.boxes()[0]
+    S = orc.OracleScene(w)
+    top = bz + sz
+    cases = [
+        # x-z edge of the top face: faces -x (normal 0) and +z (normal 5) at once
+        ((bx - 5.0, by + 1.5, top + 5.0), (1.0, 0.0, -1.0), (bx, by + 1, top - 1), 0),
+        # y-z edge: faces -y (normal 2) and +z
+        ((bx + 1.5, by - 4.0, top + 4.0), (0.0, 1.0, -1.0), (bx + 1, by, top - 1), 2),
+        # +x side and top: faces +x (normal 1) and +z
+        ((bx + sx + 3.0, by + 1.5, top + 3.0), (-1.0, 0.0, -1.0), (bx + sx - 1, by + 1, top - 1), 1),
+        # corner: -x, -y and +z at once
+        ((bx - 6.0, by - 6.0, top + 6.0), (1.0, 1.0, -1.0), (bx, by, top - 1), 0),
+    ]
+    for o, f, vox, normal in cases:
+        cam = sg.make_camera(o, f, 1, 1)
+        d = orc.ray_dir(cam, 0, 0).astype(np.float64)
+        nz = np.abs(d[d != 0])
+        assert (nz == nz[0]).all()  # equal |d| components: the faces are crossed at one instant
+        r = S.cast(cam, np.zeros(1, np.int8))[0]
+        assert r["hit"] == 1 and r["amb"] == 0
+        assert (r["x"], r["y"], r["z"]) == vox
+        assert r["normal"] == normal
+        t = (top - o[2]) / d[2]  # the common entry parameter, from the z face
+        assert abs(r["dist"] - t * np.linalg.norm(d)) <= 1e-12 * r["dist"]
+        b = orc.cast_brute(w, 32, 1, np.zeros(1, np.int8), cam)[0]
+        assert b["normal"] == normal and (b["x"], b["y"], b["z"]) == vox
+
+
 def test_single_chunk_matches_brute_force():
     w = sg.World(TINY32)
     S = orc.OracleScene(w)
