@@ -174,7 +174,9 @@ typedef struct aok_camera {
  *  hit  : 4 x uint32 per pixel, 16-byte aligned: x, y, z = min corner of the
  *         first-hit voxel (LOD-0 units, multiples of 2^lod) and meta =
  *         lod (bits 0..7) | material << 8 | normal << 16 (3 bits:
- *         2*axis + (d_axis < 0), 7 = origin inside a voxel) | 1 << 19 (hit).
+ *         2*axis + (d_axis < 0) for the voxel face the ray enters through,
+ *         the lowest such axis when it enters through an edge or a corner;
+ *         7 = origin inside a voxel) | 1 << 19 (hit).
  *         A miss writes x = y = z = 0, meta = 0xFF | 7 << 16.
  *  t    : float per pixel, 4-byte aligned: hit distance |t* d| in LOD-0
  *         units (+inf on a miss). */
