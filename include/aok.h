@@ -162,7 +162,8 @@ int aok_scene_usage(aok_ctx* ctx, uint32_t scene, uint64_t* usage);
  * The ray of pixel (px, py) is origin + t d with d computed in IEEE binary32,
  * one rounding per operation, no contraction:
  *   u = (((2px+1)/W) - 1) * tan_half_fovy * (W/H),  v = (1 - (2py+1)/H) * tan_half_fovy,
- *   d_i = ((R_i0 u) + (R_i1 v)) - R_i2. */
+ *   d_i = ((R_i0 u) + (R_i1 v)) - R_i2.
+ * width, height >= 1 with width * height <= 2^31 (AOK_E_INVALID otherwise). */
 typedef struct aok_camera {
     float origin[3];
     float R[9];
