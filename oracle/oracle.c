@@ -8,6 +8,7 @@
 #include "oracle.h"
 #include <math.h>
 #include <pthread.h>
+#include <sched.h>
 #include <stdatomic.h>
 #include <stdlib.h>
 #include <string.h>
@@ -378,7 +379,7 @@ struct or_scene {
     int32_t M, L, gx, gy, gz;
     double color_tol;   /* < 0: exact colour arrays */
     or_dag* dags;       /* [chunk * L + lod] */
-    uint8_t* built;
+    uint8_t* built;     /* 0: not built, 1: being built by a thread, 2: built */
     int32_t* aabb;      /* [chunk * L + lod][6] */
 };
 
@@ -430,7 +431,15 @@ void or_chunk_dense(const sg_scene* world, int32_t M, int32_t cx, int32_t cy, in
     size_t nv = (size_t)M * M * M;
     uint8_t* o0 = (uint8_t*)malloc(nv);
     uint8_t* m0 = (uint8_t*)malloc(nv);
-    sg_fill_bytes(world, cx * M, cy * M, cz * M, M, M, M, o0);
+    if (sg_fill_bytes(world, cx * M, cy * M, cz * M, M, M, M, o0) == 0) {
+        /* no solid voxel: empty at every LOD */
+        size_t r = (size_t)(M >> n);
+        memset(occ, 0, r * r * r);
+        memset(mat, 0, r * r * r);
+        free(o0);
+        free(m0);
+        return;
+    }
     for (int32_t z = 0; z < M; z++)
         for (int32_t y = 0; y < M; y++)
             for (int32_t x = 0; x < M; x++) {
@@ -490,7 +499,19 @@ static void build_one(or_scene* s, int64_t key) {
     }
     free(occ);
     free(mat);
-    s->built[key] = 1;
+    __atomic_store_n(&s->built[key], (uint8_t)2, __ATOMIC_RELEASE);
+}
+
+/* Build (chunk, LOD) `key` unless it is built; a thread that finds another
+ * building it waits until it is done.  Safe to call from several threads. */
+static void ensure_built(or_scene* s, int64_t key) {
+    if (__atomic_load_n(&s->built[key], __ATOMIC_ACQUIRE) == 2) return;
+    uint8_t expect = 0;
+    if (__atomic_compare_exchange_n(&s->built[key], &expect, (uint8_t)1, 0, __ATOMIC_ACQ_REL, __ATOMIC_ACQUIRE)) {
+        build_one(s, key);
+        return;
+    }
+    while (__atomic_load_n(&s->built[key], __ATOMIC_ACQUIRE) != 2) sched_yield();
 }
 
 static void* prep_worker(void* arg) {
@@ -498,7 +519,7 @@ static void* prep_worker(void* arg) {
     for (;;) {
         int64_t i = atomic_fetch_add(&c->next, 1);
         if (i >= c->n_jobs) break;
-        build_one(c->s, c->jobs[i]);
+        ensure_built(c->s, c->jobs[i]);
     }
     return NULL;
 }
@@ -511,7 +532,7 @@ int or_scene_prepare(or_scene* s, const int8_t* lod_sel, int n_threads) {
         int l = lod_sel[c];
         if (l < 0 || l >= s->L) continue;
         int64_t key = c * s->L + l;
-        if (!s->built[key]) jobs[nj++] = key;
+        if (__atomic_load_n(&s->built[key], __ATOMIC_ACQUIRE) != 2) jobs[nj++] = key;
     }
     if (n_threads < 1) n_threads = 1;
     prep_ctx ctx;
@@ -529,7 +550,7 @@ int or_scene_prepare(or_scene* s, const int8_t* lod_sel, int n_threads) {
 
 const or_dag* or_scene_dag(const or_scene* s, int32_t chunk, int32_t lod, int32_t aabb[6]) {
     int64_t key = (int64_t)chunk * s->L + lod;
-    if (!s->built[key]) return NULL;
+    if (__atomic_load_n(&s->built[key], __ATOMIC_ACQUIRE) != 2) return NULL;
     if (aabb) memcpy(aabb, &s->aabb[key * 6], 6 * sizeof(int32_t));
     return &s->dags[key];
 }
@@ -701,7 +722,7 @@ static void chunk_origin(const or_scene* s, int64_t c, int32_t org[3]) {
     org[2] = (int32_t)(c / ((int64_t)s->gx * s->gy)) * s->M;
 }
 
-static void cast_one(const or_scene* s, const int8_t* sel, const or_cam* cam, double view_dist,
+static void cast_one(or_scene* s, const int8_t* sel, const or_cam* cam, double view_dist,
                      int32_t px, int32_t py, ccand_t* cbuf, or_result* r) {
     cast_t ct;
     memset(&ct, 0, sizeof(ct));
@@ -712,13 +733,12 @@ static void cast_one(const or_scene* s, const int8_t* sel, const or_cam* cam, do
     for (int a = 0; a < 3; a++) { ct.o[a] = (double)cam->o[a]; ct.d[a] = (double)df[a]; }
     double dn = sqrt(ct.d[0] * ct.d[0] + ct.d[1] * ct.d[1] + ct.d[2] * ct.d[2]);
     double tlim = view_dist > 0.0 ? view_dist / dn : INFINITY;
-    /* chunks met by the ray, by entry parameter */
+    /* chunk cells met by the ray, by entry parameter (their DAGs are built
+     * when the ray reaches them; empty ones are skipped there) */
     int64_t nc = (int64_t)s->gx * s->gy * s->gz, k = 0;
     for (int64_t c = 0; c < nc; c++) {
         int l = sel[c];
         if (l < 0 || l >= s->L) continue;
-        const or_dag* g = &s->dags[c * s->L + l];
-        if (!s->built[c * s->L + l] || !g->n_words) continue;
         int32_t org[3];
         chunk_origin(s, c, org);
         double tn, tf;
@@ -735,7 +755,9 @@ static void cast_one(const or_scene* s, const int8_t* sel, const or_cam* cam, do
         if (cbuf[i].tn > tprune) break;
         int64_t c = cbuf[i].chunk;
         int l = sel[c];
+        ensure_built(s, c * s->L + l);
         const or_dag* g = &s->dags[c * s->L + l];
+        if (!g->n_words) continue;
         int32_t org[3];
         chunk_origin(s, c, org);
         first_hit_node(&ct, g, g->root, s->M, org, 1 << l, (int32_t)c, l);
@@ -749,13 +771,14 @@ static void cast_one(const or_scene* s, const int8_t* sel, const or_cam* cam, do
     for (int64_t c = 0; c < nc && !ct.amb; c++) {
         int l = sel[c];
         if (l < 0 || l >= s->L) continue;
-        const or_dag* g = &s->dags[c * s->L + l];
-        if (!s->built[c * s->L + l] || !g->n_words) continue;
         int32_t org[3];
         chunk_origin(s, c, org);
         double eps = 1e-5 * (double)(1 << l), tn, tf;
         int ax;
         if (!box_slab(ct.o, ct.d, org, s->M, eps, &tn, &tf, &ax) || tn > ct.tseg) continue;
+        ensure_built(s, c * s->L + l);
+        const or_dag* g = &s->dags[c * s->L + l];
+        if (!g->n_words) continue;
         amb_node(&ct, g, g->root, s->M, org, 1 << l, eps);
     }
     if (hit) {
@@ -775,7 +798,9 @@ static void cast_one(const or_scene* s, const int8_t* sel, const or_cam* cam, do
         int64_t c = cbuf[i].chunk;
         int l = sel[c];
         int64_t key = c * s->L + l;
+        ensure_built(s, key);
         const or_dag* g = &s->dags[key];
+        if (!g->n_words) continue;
         const int32_t* bb = &s->aabb[key * 6];
         double blo[3], bhi[3], tn, tf;
         int ax;
@@ -876,7 +901,6 @@ static void run_threads(cast_ctx* c, int n_threads) {
 
 int or_cast(or_scene* s, const int8_t* lod_sel, const or_cam* cam, double view_dist,
             const int32_t* pix, int64_t n, or_result* out, int n_threads) {
-    or_scene_prepare(s, lod_sel, n_threads);
     cast_ctx c;
     memset(&c, 0, sizeof(c));
     c.s = s;

@@ -146,7 +146,9 @@ typedef struct or_result {
 } or_result;
 
 /* Trace n pixels (pix = px0,py0,px1,py1,...).  view_dist <= 0 means unlimited.
- * Chunks whose lod_sel is negative are treated as empty. */
+ * Chunks whose lod_sel is negative are treated as empty.  A (chunk, LOD) DAG is
+ * built the first time a ray's segment reaches its chunk cell (or_scene_prepare
+ * builds them ahead instead); the results do not depend on which were built. */
 int or_cast(or_scene* s, const int8_t* lod_sel, const or_cam* cam, double view_dist,
             const int32_t* pix, int64_t n, or_result* out, int n_threads);
 /* Same first hit by testing every voxel of every chunk's dense LOD grid.  Tiny scenes only. */

@@ -65,6 +65,8 @@ def lib() -> ctypes.CDLL:
         vp, i32, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64
         L.sg_create.restype = vp
         L.sg_create.argtypes = [ctypes.POINTER(_Params)]
+        L.sg_create_with_boxes.restype = vp
+        L.sg_create_with_boxes.argtypes = [ctypes.POINTER(_Params), ctypes.POINTER(_Box)]
         L.sg_destroy.argtypes = [vp]
         L.sg_num_boxes.restype = i32
         L.sg_num_boxes.argtypes = [vp]
@@ -117,12 +119,21 @@ class WorldSpec:
 class World:
     """Handle on a generated world (C object); exposes dense fills and point queries."""
 
-    def __init__(self, spec: WorldSpec):
+    def __init__(self, spec: WorldSpec, boxes=None):
+        """boxes: optional list of (x0, y0, z0, sx, sy, sz, hollow) placed instead of the
+        seeded ones (hand-made test scenes; spec.n_boxes is then ignored)."""
+        if boxes is not None:
+            from dataclasses import replace
+            spec = replace(spec, n_boxes=len(boxes))
         self.spec = spec
         p = _Params(spec.seed, spec.wx, spec.wy, spec.wz, spec.octaves, spec.period0, spec.h_min,
                     spec.h_max, spec.crust, spec.n_boxes, spec.box_min, spec.box_max, spec.box_hollow,
                     spec.mat_mode)
-        self._h = lib().sg_create(ctypes.byref(p))
+        if boxes is None:
+            self._h = lib().sg_create(ctypes.byref(p))
+        else:
+            arr = (_Box * max(1, len(boxes)))(*[_Box(*b) for b in boxes])
+            self._h = lib().sg_create_with_boxes(ctypes.byref(p), arr)
         if not self._h:
             raise ValueError(f"bad world spec {spec}")
 

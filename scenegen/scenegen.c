@@ -127,18 +127,27 @@ const sg_params* sg_get_params(const sg_scene* s) { return &s->p; }
 int32_t sg_num_boxes(const sg_scene* s) { return s->p.n_boxes; }
 void sg_get_box(const sg_scene* s, int32_t i, sg_box* out) { *out = s->boxes[i]; }
 
-sg_scene* sg_create(const sg_params* p) {
+static sg_scene* create(const sg_params* p, const sg_box* given) {
     if (!p || p->wx <= 0 || p->wy <= 0 || p->wz <= 0 || p->octaves < 1 || p->octaves > 16 ||
         p->period0 < 1 || p->h_max < p->h_min || p->n_boxes < 0 || p->crust < 0 || p->mat_mode < 0 ||
         p->mat_mode > 1)
         return NULL;
+    if (given) {
+        for (int32_t b = 0; b < p->n_boxes; b++) {
+            const sg_box* g = &given[b];
+            if (g->sx < 1 || g->sy < 1 || g->sz < 1 || g->x0 < 0 || g->y0 < 0 || g->z0 < 0 ||
+                g->x0 + g->sx > p->wx || g->y0 + g->sy > p->wy || g->z0 + g->sz > p->wz)
+                return NULL;
+        }
+    }
     sg_scene* s = (sg_scene*)calloc(1, sizeof(sg_scene));
     s->p = *p;
     s->noise_seed = sg_mix64(p->seed ^ 0x6E6F697365ULL);
     s->mat_seed = sg_mix64(p->seed ^ 0x6D6174ULL);
     s->boxes = (sg_box*)calloc((size_t)(p->n_boxes > 0 ? p->n_boxes : 1), sizeof(sg_box));
     rng_t r = { sg_mix64(p->seed ^ 0x626F786573ULL) };
-    for (int32_t b = 0; b < p->n_boxes; b++) {
+    for (int32_t b = 0; b < p->n_boxes && given; b++) s->boxes[b] = given[b];
+    for (int32_t b = 0; b < p->n_boxes && !given; b++) {
         sg_box* bx = &s->boxes[b];
         bx->sx = rng_uniform(&r, p->box_min, p->box_max);
         bx->sy = rng_uniform(&r, p->box_min, p->box_max);
@@ -187,6 +196,10 @@ sg_scene* sg_create(const sg_params* p) {
     }
     return s;
 }
+
+sg_scene* sg_create(const sg_params* p) { return create(p, NULL); }
+
+sg_scene* sg_create_with_boxes(const sg_params* p, const sg_box* boxes) { return boxes ? create(p, boxes) : NULL; }
 
 void sg_destroy(sg_scene* s) {
     if (!s) return;

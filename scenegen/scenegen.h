@@ -62,6 +62,9 @@ typedef struct sg_scene sg_scene;
 
 /* Create a scene (draws the box list from the seed).  Returns NULL on bad params. */
 sg_scene* sg_create(const sg_params* p);
+/* The same with the box list given instead of drawn: p->n_boxes entries of
+ * `boxes`, each inside the world (NULL otherwise).  For hand-made test scenes. */
+sg_scene* sg_create_with_boxes(const sg_params* p, const sg_box* boxes);
 void sg_destroy(sg_scene* s);
 const sg_params* sg_get_params(const sg_scene* s);
 int32_t sg_num_boxes(const sg_scene* s);

@@ -21,3 +21,26 @@ MED64 = replace(sg.CITY_4096, name="med64", seed=14, wx=256, wy=256, wz=128, chu
 
 # MED64 with layered (coherent) materials: the colour-block workload
 MED64_LAYERED = replace(MED64, name="med64_layered", mat_mode=1)
+
+# one 32^3 chunk with no terrain, holding only cubes placed by hand (counter pins)
+HAND32 = sg.WorldSpec("hand32", seed=31, wx=32, wy=32, wz=32, chunk=32, n_lods=1, octaves=1, period0=8,
+                      h_min=0, h_max=0, crust=0, n_boxes=0, box_min=1, box_max=1, box_hollow=0)
+
+
+def hand_world(voxels, n_lods=1, size=1):
+    """HAND32 holding only the listed cubes (min corner, side `size`)."""
+    return sg.World(replace(HAND32, n_lods=n_lods), boxes=[(x, y, z, size, size, size, 0) for x, y, z in voxels])
+
+
+# Straight-down rays (origin (x, y, 40)) through hand-made scenes with their
+# visits counted by hand: (voxels, cube side, LODs of the world, LOD cast,
+# ray x, ray y, (interior visits, leaf-block visits, resolve bytes)).
+HAND_CASES = [
+    ([(9, 9, 9)], 2, 1, 0, 9.5, 10.5, (3, 1, 1)),
+    ([(2, 2, 2), (26, 26, 26)], 2, 1, 0, 20.5, 4.5, (1, 0, 0)),
+    ([(2, 2, 2), (26, 26, 26)], 2, 1, 0, 30.5, 4.5, (0, 0, 0)),
+    ([(1, 1, 1), (20, 1, 1), (20, 20, 1), (17, 17, 17), (28, 28, 20), (25, 25, 25), (28, 28, 28)], 1, 1, 0,
+     28.5, 28.5, (3, 1, 1 + 3 * 4 + 2 * 4 + 1 * 8)),
+    ([(5, 5, 10), (5, 6, 3)], 1, 1, 0, 5.5, 6.5, (4, 2, 1)),
+    ([(8, 8, 8)], 2, 2, 1, 8.5, 9.5, (2, 1, 1)),
+]
