@@ -210,8 +210,10 @@ def time_events(fn, reps, flush, stream):
 
 def bench_batched(aok, ctx, scene, world, flush, reps=5):
     """64 walker views of the city world at resolutions drawn from five sizes:
-    one aok_render_batch (autotuned persistent launch, CUDA graph) vs 64
-    separate aok_render launches on one stream.  Outputs must be identical."""
+    one aok_render_batch (the autotuner's launch kind; with the grid launch,
+    selection, one beam pass for the large views and the cast replayed as one
+    CUDA graph) vs 64 separate aok_render launches on one stream, and the same
+    batch with its launches issued one by one.  Outputs must be identical."""
     import torch
     cams = sg.batch_cameras(world, 104, 64)
     rays = sum(c.W * c.H for c in cams)
@@ -237,6 +239,14 @@ def bench_batched(aok, ctx, scene, world, flush, reps=5):
                 for a, b in zip(plain, batch))
     p_med, p_best = time_events(run_plain, reps, flush, stream)
     b_med, b_best = time_events(run_batch, reps, flush, stream)
+    aok.set_batch_graph(ctx, False)
+    e_med, e_best = time_events(run_batch, reps, flush, stream)
+    eager = [aok.alloc_frame(c.W, c.H) for c in cams]
+    aok.render_batch(ctx, [aok.make_view(scene, c, TAU, h, t) for c, (h, t) in zip(cams, eager)])
+    aok.set_batch_graph(ctx, True)
+    torch.cuda.synchronize()
+    equal = equal and all(torch.equal(a[0], b[0]) and torch.equal(a[1].view(torch.int32), b[1].view(torch.int32))
+                          for a, b in zip(plain, eager))
     ctas, threads, packet = aok.get_launch(ctx)
     # the beam pass runs for views of at least 1.5 M pixels: one launch per
     # such plain render, one for the batch (grid launch)
@@ -245,7 +255,8 @@ def bench_batched(aok, ctx, scene, world, flush, reps=5):
                         "{320x180, 640x360, 1280x720, 1920x1080, 2560x1440}, tau = 1 px",
             "rays": rays, "plain_rays_per_s": rays / (p_med / 1e3), "batched_rays_per_s": rays / (b_med / 1e3),
             "plain_ms": p_med, "batched_ms": b_med, "plain_best_ms": p_best, "batched_best_ms": b_best,
-            "speedup": p_med / b_med, "identical_outputs": bool(equal), "plain_launches": 128 + big,
+            "speedup": p_med / b_med, "identical_outputs": bool(equal),
+            "graph": True, "eager_batched_ms": e_med, "graph_vs_eager": e_med / b_med, "plain_launches": 128 + big,
             "batched_launches": 2 + (1 if big and ctas == 0 else 0), "views_with_beam_pass": big,
             "autotuned": {"ctas_per_sm": ctas, "threads": threads, "packet_rays": packet,
                           "best_ms": tune_ms, "tune_s": round(tune_s, 2)}}
@@ -763,11 +774,21 @@ def main():
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=f"cuda:{dev}")  # > 129 MB L2
 
     # ---- algorithmic bytes of this frame (counting kernel, untimed) ----
+    # The method's traversal (no beam restart) visits what the oracle counts;
+    # its bytes are the roofline's numerator.  With the restart the casting
+    # kernel reads fewer: reported beside it.
     counts = torch.zeros((H, W, 3), dtype=torch.int32, device=f"cuda:{dev}")
-    aok.render_counted(ctx, scene, cam, TAU, hit, t, counts)
-    torch.cuda.synchronize()
-    c = counts.view(-1, 3).to(torch.int64).sum(0).tolist()
-    algo_bytes = 8 * c[0] + 8 * c[1] + c[2] + 20 * W * H  # node visits, leaf visits, resolve, output
+
+    def frame_bytes(beam):
+        aok.set_beam(ctx, beam)
+        aok.render_counted(ctx, scene, cam, TAU, hit, t, counts)
+        torch.cuda.synchronize()
+        c = counts.view(-1, 3).to(torch.int64).sum(0).tolist()
+        return 8 * c[0] + 8 * c[1] + c[2] + 20 * W * H, c  # node visits, leaf visits, resolve, output
+
+    algo_bytes, algo_counts = frame_bytes(False)
+    restart_bytes, restart_counts = frame_bytes(True)
+    aok.set_beam(ctx, BEAM_DEFAULT)
     del counts
     n_visible = aok.select_chunks(ctx, scene, cam, TAU, count=True)
     meta = hit.view(-1, 4)[:, 3]
@@ -860,6 +881,12 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                      "traffic": profiled_traffic(), "kernel": "cast_kernel", "peak_kind": f"{peak_kind} hbm_gbs",
                      "algo_bytes_per_launch": algo_bytes, "algo_bytes_per_ray": algo_bytes / rays,
+                     "algo_bytes_def": "oracle traversal visits (no beam restart): 8 B per interior and per leaf "
+                                       "visit, 4 B per earlier-sibling count (8 B for leaf masks) + 1 B per hit, "
+                                       "20 B output; counting kernel equal to the oracle per pixel",
+                     "visits_per_ray": [algo_counts[0] / rays, algo_counts[1] / rays],
+                     "bytes_read_with_beam_restart": restart_bytes,
+                     "frac_on_restart_bytes": restart_bytes / (cast_avg / 1000.0) / 1e9 / hbm,
                      "cast_ms": cast_avg, "cast_ms_median": statistics.median(cast_ms),
                      "cast_ms_best": min(cast_ms),
                      "l2_read_gbs": l2_gbs, "frac_of_l2_read": achieved / l2_gbs,

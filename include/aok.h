@@ -163,7 +163,8 @@ int aok_scene_usage(aok_ctx* ctx, uint32_t scene, uint64_t* usage);
  * one rounding per operation, no contraction:
  *   u = (((2px+1)/W) - 1) * tan_half_fovy * (W/H),  v = (1 - (2py+1)/H) * tan_half_fovy,
  *   d_i = ((R_i0 u) + (R_i1 v)) - R_i2.
- * width, height >= 1 with width * height <= 2^31 (AOK_E_INVALID otherwise). */
+ * width, height >= 1, height <= 524280 (65535 rows of 8-pixel casting blocks)
+ * and width * height < 2^31 (AOK_E_INVALID otherwise). */
 typedef struct aok_camera {
     float origin[3];
     float R[9];
@@ -314,11 +315,17 @@ int aok_blobfile_close(aok_blobfile* f);
 int aok_plan_residency(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double lod_threshold_px,
                        uint8_t* lod_out, uint32_t* n_kept);
 
-/* Select (as aok_select_chunks) and cast every pixel's primary ray through
- * the chunk grid and the selected DAGs; writes `frame` on `stream`.  The
+/* One frame of the paper's per-frame work: the LOD selection of Eq. 1 and
+ * the chunk culling (Sec. 3.4, Sec. 3.5 chunk selection pass), then the ray
+ * marching pass (Sec. 3.5: every pixel's primary ray through the chunk grid
+ * and the selected DAGs to its first solid voxel) with the colour-resolve
+ * step (Sec. 3.3 depth-first index, Sec. 3.5) fused at the hit.  Selects as
+ * aok_select_chunks and writes `frame` (layout above) on `stream`.  The
  * scene's per-frame chunk table is shared: aok_render calls on one scene that
  * overlap on the GPU (different streams) race; use aok_render_batch for
- * concurrent views. */
+ * concurrent views.  AOK_E_INVALID for a bad camera, threshold or misaligned
+ * frame, AOK_E_NOT_RESIDENT for an unknown scene, AOK_E_CUDA when a launch
+ * fails (the context's last CUDA error then holds its code). */
 int aok_render(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double lod_threshold_px,
                const aok_frame* frame, void* stream);
 
@@ -398,15 +405,22 @@ typedef struct aok_view {
  * and one casting launch per group of up to 128 views: by default a grid
  * over the block tiles (2x2 warp tiles) of all views, scheduled by the
  * hardware; optionally (aok_set_batch_kernel) a persistent kernel whose warps
- * pull warp tiles from a global counter.  The launches of one list shape (n,
- * scenes, sizes) form a CUDA graph built on first use and updated in place.
- * Results equal n separate aok_render calls.  Calls on one context are
- * serialised by the caller (one stream).  AOK_E_INVALID if n is 0 or above
- * 4096. */
+ * pull warp tiles from a global counter.  With the grid launch and the beam
+ * pass on, one beam pass (a cooperative launch) per group serves all of the
+ * group's views large enough for it, between the selection and the cast.
+ * The launches of one list shape (n, scenes, sizes) -- selections, beam
+ * passes with their counter resets, casts -- form a CUDA graph built on first
+ * use and updated in place (aok_set_batch_graph(ctx, 0) launches them one by
+ * one instead).  Results equal n separate aok_render calls.  Calls on one
+ * context are serialised by the caller (one stream).  AOK_E_INVALID if n is 0
+ * or above 4096. */
 int aok_render_batch(aok_ctx* ctx, const aok_view* views, uint32_t n, void* stream);
 
 /* 0: batches use the grid launch (default); 1: the persistent kernel. */
 int aok_set_batch_kernel(aok_ctx* ctx, int persistent);
+/* 1 (default): aok_render_batch replays a CUDA graph of its launches; 0: it
+ * launches them one by one (same results). */
+int aok_set_batch_graph(aok_ctx* ctx, int on);
 /* Launch shape of the persistent casting kernel (0 = keep current):
  * CTAs per SM, threads per CTA (multiple of 32), rays per packet (multiple
  * of 32).  aok_autotune times grid launches (three warp tiles) and
@@ -477,7 +491,12 @@ int aok_serve_times(aok_ctx* ctx, uint64_t ticket, uint64_t* submit_ns, uint64_t
  *    with AOK_E_INVALID before any work is enqueued.
  *  - The first call on a device looks up the array's device address (with
  *    that device current) and caches it; make that first call before any
- *    CUDA stream capture.
+ *    CUDA stream capture.  The cached address belongs to the device's
+ *    current context: do not call this function again in a process that has
+ *    reset the device (cudaDeviceReset) after its first call there.
+ *  - With aok_set_checked(ctx, 1) it launches the checked casting kernel, as
+ *    aok_render does; the error word is context memory, so this allocates
+ *    nothing either.
  *  - All calls share the one array and each call overwrites the entries it
  *    uses, so calls whose GPU work overlaps (different streams, or no
  *    ordering between them) race and may return wrong pixels; order them on
@@ -548,8 +567,8 @@ int aok_beam_info(aok_ctx* ctx, int32_t* bounds, uint64_t n_bounds, uint32_t* le
 int aok_render_counted(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double lod_threshold_px,
                        const aok_frame* frame, uint32_t* counts, void* stream);
 /* Checked casting (no counterpart in the paper; the stand-in for a device
- * memory checker): with on = 1, aok_render / aok_cast_selected of this
- * context test every node, leaf and colour index against the scene's pool
+ * memory checker): with on = 1, aok_render / aok_cast_selected /
+ * aok_render_noalloc of this context test every node, leaf and colour index against the scene's pool
  * sizes before loading it; an index out of range ends that chunk's traversal
  * as a miss and ORs a code into the context's error word (1 node word, 2
  * leaf, 4 colour).  Slower; batches, serving and the tile pipeline are not

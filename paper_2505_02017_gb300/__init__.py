@@ -118,6 +118,7 @@ def lib() -> ctypes.CDLL:
             "aok_autotune": [vp, P(View), u32, vp, P(ctypes.c_float)],
             "aok_set_tile": [vp, u32],
             "aok_set_batch_kernel": [vp, ctypes.c_int],
+            "aok_set_batch_graph": [vp, ctypes.c_int],
             "aok_set_single_view_kernel": [vp, ctypes.c_int],
             "aok_set_checked": [vp, ctypes.c_int],
             "aok_set_beam": [vp, ctypes.c_int],
@@ -595,6 +596,11 @@ def set_tile(ctx: Context, tile_w: int):
 
 def set_batch_kernel(ctx: Context, persistent: bool):
     return check(lib().aok_set_batch_kernel(ctx.h, int(persistent)), "aok_set_batch_kernel")
+
+
+def set_batch_graph(ctx: Context, on: bool):
+    """aok_set_batch_graph: replay a batch's launches as one CUDA graph (default) or launch them one by one."""
+    return check(lib().aok_set_batch_graph(ctx.h, int(on)), "aok_set_batch_graph")
 
 
 def set_single_view_kernel(ctx: Context, persistent: bool):

@@ -407,23 +407,58 @@ bool aokk_beam_view(const SceneDev* S, const CamDev* C, const ChunkRef* frame, u
 static std::mutex g_beam_mu;
 static cudaEvent_t g_beam_done[kMaxBeamDevices];
 
+// The pass as a node of a CUDA graph (aokk_batch_run): its kernel with the
+// launch shape aokk_beam_run uses, and the memset of the counters that
+// aokk_beam_run zeroes before it.  argp: one slot, valid until the node is set.
+void aokk_beam_node(const BeamBatch* P, unsigned grid, void** argp, cudaKernelNodeParams* kp, cudaMemsetParams* zero) {
+    argp[0] = (void*)P;
+    kp->func = (void*)beam_kernel;
+    kp->gridDim = dim3(P->n_regions > kWideWalkRegions ? grid : (grid + kBeamBlocksPerSM - 1) / kBeamBlocksPerSM);
+    kp->blockDim = dim3(kBeamThreads);
+    kp->sharedMemBytes = 0;
+    kp->kernelParams = argp;
+    kp->extra = nullptr;
+    zero->dst = P->cnt;
+    zero->pitch = 0;
+    zero->value = 0;
+    zero->elementSize = sizeof(uint32_t);
+    zero->width = 2 * kBeamLevels;
+    zero->height = 1;
+}
+
+// The per-device order of beam passes for work that holds passes but is not
+// launched by aokk_beam_run (a graph): before (record = 0) the stream waits
+// for the previous pass; after (record = 1) the end of the stream's work so
+// far becomes the point the next pass waits for.
+int aokk_beam_order(void* stream, int record) {
+    const cudaStream_t st = (cudaStream_t)stream;
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return aokk_status(e);
+    if (dev < 0 || dev >= kMaxBeamDevices) return aokk_status(cudaErrorInvalidDevice);
+    std::lock_guard<std::mutex> lk(g_beam_mu);
+    if (!g_beam_done[dev]) e = cudaEventCreateWithFlags(&g_beam_done[dev], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = record ? cudaEventRecord(g_beam_done[dev], st) : cudaStreamWaitEvent(st, g_beam_done[dev], 0);
+    return aokk_status(e);
+}
+
 int aokk_beam_run(const BeamBatch* P, unsigned grid, void* stream) {
     const cudaStream_t st = (cudaStream_t)stream;
     if (P->n_views == 0) return AOK_OK;
     int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxBeamDevices) return AOK_E_CUDA;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return aokk_status(e);
+    if (dev < 0 || dev >= kMaxBeamDevices) return aokk_status(cudaErrorInvalidDevice);
     std::lock_guard<std::mutex> lk(g_beam_mu);
-    if (!g_beam_done[dev] && cudaEventCreateWithFlags(&g_beam_done[dev], cudaEventDisableTiming) != cudaSuccess)
-        return AOK_E_CUDA;
-    if (cudaStreamWaitEvent(st, g_beam_done[dev], 0) != cudaSuccess) return AOK_E_CUDA;
+    if (!g_beam_done[dev]) e = cudaEventCreateWithFlags(&g_beam_done[dev], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, g_beam_done[dev], 0);
     // queue counts and the walk histogram (cnt and hist are adjacent)
-    if (cudaMemsetAsync(P->cnt, 0, 2 * kBeamLevels * sizeof(uint32_t), st) != cudaSuccess) return AOK_E_CUDA;
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->cnt, 0, 2 * kBeamLevels * sizeof(uint32_t), st);
     void* args[] = {(void*)P};
     const unsigned g = P->n_regions > kWideWalkRegions ? grid : (grid + kBeamBlocksPerSM - 1) / kBeamBlocksPerSM;
-    if (cudaLaunchCooperativeKernel((const void*)beam_kernel, g, kBeamThreads, args, 0, st) != cudaSuccess)
-        return AOK_E_CUDA;
-    if (cudaEventRecord(g_beam_done[dev], st) != cudaSuccess) return AOK_E_CUDA;
-    return AOK_OK;
+    if (e == cudaSuccess) e = cudaLaunchCooperativeKernel((const void*)beam_kernel, g, kBeamThreads, args, 0, st);
+    if (e == cudaSuccess) e = cudaEventRecord(g_beam_done[dev], st);
+    return aokk_status(e);
 }
 
 }  // extern "C"

@@ -16,6 +16,7 @@ constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr uint32_t kResidentBit = 0x80000000u;
 constexpr int kFix = 12;            // camera origin fixed point: multiples of 2^-12
 constexpr int kMaxLevels = 10;      // log2(512) + 1
+constexpr int kMaxImageHeight = 65535 * 8;  // 8-row casting blocks, at most 65535 in grid y
 
 // One (chunk, LOD) as resident on the device, and (per frame) the selected
 // LOD of a chunk region.  32 bytes: one sector per lookup.
@@ -176,7 +177,7 @@ static_assert(sizeof(BatchParams) < 32000, "batched launch parameters must fit t
 struct GraphCache {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    std::vector<cudaGraphNode_t> nodes;  // select, cast per group
+    std::vector<cudaGraphNode_t> nodes;  // per group: select, [counter memset, beam pass], cast
     std::vector<uint64_t> key;
 };
 
@@ -184,6 +185,12 @@ struct GraphCache {
 
 // Kernel launchers (aok_kernels.cu), called by the runtime.
 extern "C" {
+// Launch errors.  Reading cudaGetLastError clears a non-sticky launch error
+// (an invalid grid, say), so a launcher that finds one keeps its code, per host
+// thread, and returns AOK_E_CUDA; aokk_take_launch_error hands the code to the
+// runtime (else the thread's last CUDA error, and never cudaSuccess).
+int aokk_status(cudaError_t e);
+cudaError_t aokk_take_launch_error();
 int aokk_select(const aok::SceneDev* s, const aok::CamDev* c, aok::ChunkRef* frame, int8_t* lod_out,
                 uint8_t* vis_out, uint32_t* n_visible, void* stream);
 int aokk_cast(const aok::SceneDev* s, const aok::CamDev* c, const aok::ChunkRef* frame, uint4* hit, float* t,
@@ -194,6 +201,12 @@ int aokk_cast(const aok::SceneDev* s, const aok::CamDev* c, const aok::ChunkRef*
 bool aokk_beam_view(const aok::SceneDev* S, const aok::CamDev* C, const aok::ChunkRef* frame,
                     unsigned long long* bounds, aok::BeamView* out);
 int aokk_beam_run(const aok::BeamBatch* P, unsigned grid, void* stream);
+// The pass as a graph node (kernel + counter memset) and the per-device pass
+// order around a graph launch (record = 0: wait for the previous pass before;
+// 1: mark the end of the launch as the point the next pass waits for).
+void aokk_beam_node(const aok::BeamBatch* P, unsigned grid, void** argp, cudaKernelNodeParams* kp,
+                    cudaMemsetParams* zero);
+int aokk_beam_order(void* stream, int record);
 // Blocks of the beam pass's cooperative launch on `sms` SMs (0 on error).
 unsigned aokk_beam_grid(int sms);
 int aokk_ray_dirs(const aok::CamDev* c, float* dirs, void* stream);
@@ -217,6 +230,8 @@ int aokk_batch_run(const aok::BatchParams* groups, uint32_t n_groups, uint32_t c
 void aokk_graph_destroy(aok::GraphCache* gc);
 int aokk_max_ctas_per_sm(uint32_t threads);
 int aokk_sm_count(int device);
-// aok_render_noalloc's launcher: chunk table in static device memory.
-int aokk_render_noalloc(const aok::SceneDev* s, const aok::CamDev* c, uint4* hit, float* t, void* stream);
+// aok_render_noalloc's launcher: chunk table in static device memory; with
+// ck, the checked casting kernel (its error word is context memory).
+int aokk_render_noalloc(const aok::SceneDev* s, const aok::CamDev* c, uint4* hit, float* t, void* stream,
+                        const aok::CheckDev* ck);
 }

@@ -6,6 +6,7 @@
 
 #include <atomic>
 #include <cstdint>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -213,20 +214,35 @@ __global__ void patch_desc_kernel(ChunkRef* __restrict__ desc, const __grid_cons
 }
 
 __global__ void ray_dirs_kernel(CamDev C, float* __restrict__ dirs) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= C.W * C.H) return;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)C.W * (size_t)C.H) return;
     float d[3];
-    ray_dir(C, i % C.W, i / C.W, d);
+    ray_dir(C, (int)(i % (size_t)C.W), (int)(i / (size_t)C.W), d);
     dirs[3 * i] = d[0];
     dirs[3 * i + 1] = d[1];
     dirs[3 * i + 2] = d[2];
 }
 
-int status_of(cudaError_t e) { return e == cudaSuccess ? AOK_OK : AOK_E_CUDA; }
+thread_local cudaError_t t_launch_error = cudaSuccess;
+
+int status_of(cudaError_t e) { return aokk_status(e); }
 
 }  // namespace
 
 extern "C" {
+
+int aokk_status(cudaError_t e) {
+    if (e == cudaSuccess) return AOK_OK;
+    t_launch_error = e;
+    return AOK_E_CUDA;
+}
+
+cudaError_t aokk_take_launch_error() {
+    cudaError_t e = t_launch_error;
+    t_launch_error = cudaSuccess;
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return e == cudaSuccess ? cudaErrorLaunchFailure : e;
+}
 
 int aokk_select(const SceneDev* s, const CamDev* c, ChunkRef* frame, int8_t* lod_out, uint8_t* vis_out,
                 uint32_t* n_visible, void* stream) {
@@ -268,24 +284,31 @@ int aokk_cast_batch(const BatchParams* p, uint32_t ctas, uint32_t threads, void*
 
 // Run n_groups (select, cast) launch pairs on `stream`; with beams, each
 // group's beam pass (beams[g], one cooperative launch) runs between its
-// selection and its cast.  With a cache and no beams, the pairs form one CUDA
-// graph built per shape (group sizes, launch dims) whose kernel nodes are
-// updated with the new parameters on every call.
+// selection and its cast.  With a cache and no hand-off stream, the whole
+// sequence is one CUDA graph built per shape (group sizes, launch dims, which
+// groups hold a beam pass) -- select, counter memset and cooperative beam
+// kernel, cast per group, chained -- whose nodes are updated with the new
+// parameters on every call; a graph holding beam passes keeps the per-device
+// order of passes around its launch.
 int aokk_batch_run(const BatchParams* groups, uint32_t n_groups, uint32_t ctas, uint32_t threads, void* stream,
                    const BeamBatch* beams, unsigned beam_grid, const BeamHandoff* handoff, GraphCache* gc) {
     const cudaStream_t st = (cudaStream_t)stream;
-    if (!gc || beams) {
+    auto has_beam = [&](uint32_t g) { return beams && beams[g].n_views > 0; };
+    if (!gc || handoff) {
         for (uint32_t g = 0; g < n_groups; g++) {
             int r = aokk_select_batch(&groups[g], stream);
-            if (!r && beams && beams[g].n_views) {
+            if (!r && has_beam(g)) {
                 if (handoff) {
                     const cudaStream_t bs = (cudaStream_t)handoff->stream;
-                    if (cudaEventRecord(handoff->sel, st) != cudaSuccess || cudaStreamWaitEvent(bs, handoff->sel, 0) != cudaSuccess)
-                        return AOK_E_CUDA;
-                    r = aokk_beam_run(&beams[g], beam_grid, handoff->stream);
-                    if (!r && (cudaEventRecord(handoff->beam, bs) != cudaSuccess ||
-                               cudaStreamWaitEvent(st, handoff->beam, 0) != cudaSuccess))
-                        r = AOK_E_CUDA;
+                    cudaError_t e = cudaEventRecord(handoff->sel, st);
+                    if (e == cudaSuccess) e = cudaStreamWaitEvent(bs, handoff->sel, 0);
+                    r = aokk_status(e);
+                    if (!r) r = aokk_beam_run(&beams[g], beam_grid, handoff->stream);
+                    if (!r) {
+                        e = cudaEventRecord(handoff->beam, bs);
+                        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, handoff->beam, 0);
+                        r = aokk_status(e);
+                    }
                 } else {
                     r = aokk_beam_run(&beams[g], beam_grid, stream);
                 }
@@ -295,11 +318,14 @@ int aokk_batch_run(const BatchParams* groups, uint32_t n_groups, uint32_t ctas, 
         }
         return AOK_OK;
     }
-    std::vector<uint64_t> key{n_groups, ctas, threads};
+    bool any_beam = false;
+    std::vector<uint64_t> key{n_groups, ctas, threads, beam_grid};
     for (uint32_t g = 0; g < n_groups; g++) {
         key.push_back(groups[g].n_views);
         key.push_back(groups[g].max_chunks);
         if (!ctas) key.push_back(groups[g].total_tiles);  // grid size of the casting node
+        key.push_back(has_beam(g) ? 1u + beams[g].n_regions : 0u);  // the pass's grid depends on its regions
+        any_beam |= has_beam(g);
     }
     auto params = [&](uint32_t g, bool sel, void** argp, cudaKernelNodeParams& kp) {
         argp[0] = (void*)&groups[g];
@@ -316,35 +342,68 @@ int aokk_batch_run(const BatchParams* groups, uint32_t n_groups, uint32_t ctas, 
         aokk_graph_destroy(gc);
         e = cudaGraphCreate(&gc->graph, 0);
         cudaGraphNode_t prev = nullptr;
+        auto add = [&](cudaGraphNode_t node) {
+            gc->nodes.push_back(node);
+            prev = node;
+        };
         for (uint32_t g = 0; g < n_groups && e == cudaSuccess; g++) {
-            for (int sel = 1; sel >= 0 && e == cudaSuccess; sel--) {
-                void* argp[1];
-                cudaKernelNodeParams kp;
-                params(g, sel != 0, argp, kp);
-                cudaGraphNode_t node;
-                e = cudaGraphAddKernelNode(&node, gc->graph, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
-                gc->nodes.push_back(node);
-                prev = node;
+            void* argp[1];
+            cudaKernelNodeParams kp;
+            cudaGraphNode_t node;
+            params(g, true, argp, kp);
+            e = cudaGraphAddKernelNode(&node, gc->graph, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
+            if (e != cudaSuccess) break;
+            add(node);
+            if (has_beam(g)) {
+                cudaMemsetParams zp;
+                aokk_beam_node(&beams[g], beam_grid, argp, &kp, &zp);
+                e = cudaGraphAddMemsetNode(&node, gc->graph, &prev, 1, &zp);
+                if (e != cudaSuccess) break;
+                add(node);
+                e = cudaGraphAddKernelNode(&node, gc->graph, &prev, 1, &kp);
+                if (e != cudaSuccess) break;
+                cudaLaunchAttributeValue coop;
+                std::memset(&coop, 0, sizeof(coop));
+                coop.cooperative = 1;
+                e = cudaGraphKernelNodeSetAttribute(node, cudaLaunchAttributeCooperative, &coop);
+                if (e != cudaSuccess) break;
+                add(node);
             }
+            params(g, false, argp, kp);
+            e = cudaGraphAddKernelNode(&node, gc->graph, &prev, 1, &kp);
+            if (e != cudaSuccess) break;
+            add(node);
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&gc->exec, gc->graph, 0);
         if (e != cudaSuccess) {
             aokk_graph_destroy(gc);
-            return AOK_E_CUDA;
+            return aokk_status(e);
         }
         gc->key = key;
     } else {
+        size_t i = 0;
         for (uint32_t g = 0; g < n_groups && e == cudaSuccess; g++) {
-            for (int sel = 1; sel >= 0 && e == cudaSuccess; sel--) {
-                void* argp[1];
-                cudaKernelNodeParams kp;
-                params(g, sel != 0, argp, kp);
-                e = cudaGraphExecKernelNodeSetParams(gc->exec, gc->nodes[2 * g + (sel ? 0 : 1)], &kp);
+            void* argp[1];
+            cudaKernelNodeParams kp;
+            params(g, true, argp, kp);
+            e = cudaGraphExecKernelNodeSetParams(gc->exec, gc->nodes[i++], &kp);
+            if (e == cudaSuccess && has_beam(g)) {
+                cudaMemsetParams zp;
+                aokk_beam_node(&beams[g], beam_grid, argp, &kp, &zp);
+                e = cudaGraphExecMemsetNodeSetParams(gc->exec, gc->nodes[i++], &zp);
+                if (e == cudaSuccess) e = cudaGraphExecKernelNodeSetParams(gc->exec, gc->nodes[i++], &kp);
+            }
+            if (e == cudaSuccess) {
+                params(g, false, argp, kp);
+                e = cudaGraphExecKernelNodeSetParams(gc->exec, gc->nodes[i++], &kp);
             }
         }
-        if (e != cudaSuccess) return AOK_E_CUDA;
+        if (e != cudaSuccess) return aokk_status(e);
     }
-    return status_of(cudaGraphLaunch(gc->exec, st));
+    int r = any_beam ? aokk_beam_order(stream, 0) : AOK_OK;
+    if (!r) r = status_of(cudaGraphLaunch(gc->exec, st));
+    if (!r && any_beam) r = aokk_beam_order(stream, 1);
+    return r;
 }
 
 void aokk_graph_destroy(GraphCache* gc) {
@@ -369,8 +428,8 @@ int aokk_patch_desc(ChunkRef* desc, const DescPatches* p, void* stream) {
 }
 
 int aokk_ray_dirs(const CamDev* c, float* dirs, void* stream) {
-    const int n = c->W * c->H;
-    ray_dirs_kernel<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(*c, dirs);
+    const size_t n = (size_t)c->W * (size_t)c->H;
+    ray_dirs_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(*c, dirs);
     return status_of(cudaGetLastError());
 }
 
@@ -423,7 +482,7 @@ static constexpr int kMaxNoallocDevices = 128;
 static std::atomic<ChunkRef*> g_noalloc_ptr[kMaxNoallocDevices];
 static std::mutex g_noalloc_mu;
 
-int aokk_render_noalloc(const SceneDev* s, const CamDev* c, uint4* hit, float* t, void* stream) {
+int aokk_render_noalloc(const SceneDev* s, const CamDev* c, uint4* hit, float* t, void* stream, const CheckDev* ck) {
     const long long nch = (long long)s->grid[0] * s->grid[1] * s->grid[2];
     if (nch > AOK_NOALLOC_MAX_CHUNKS) return AOK_E_INVALID;
     int dev = -1;
@@ -444,7 +503,10 @@ int aokk_render_noalloc(const SceneDev* s, const CamDev* c, uint4* hit, float* t
     const cudaStream_t st = (cudaStream_t)stream;
     select_kernel<<<(unsigned)((nch + 127) / 128), 128, 0, st>>>(*s, *c, frame, nullptr, nullptr, nullptr);
     dim3 grid((c->W + 15) / 16, (c->H + 7) / 8);
-    cast_kernel<false><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, nullptr, BeamRead{nullptr, 0});
+    if (ck)
+        cast_kernel_checked<<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, *ck);
+    else
+        cast_kernel<false><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, nullptr, BeamRead{nullptr, 0});
     return status_of(cudaGetLastError());
 }
 

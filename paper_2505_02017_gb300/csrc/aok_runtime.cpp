@@ -27,6 +27,8 @@ int cuda_status(aok_ctx* ctx, cudaError_t e) {
     return AOK_E_CUDA;
 }
 
+int launch_failure(aok_ctx* ctx) { return cuda_status(ctx, aokk_take_launch_error()); }
+
 int charge(aok_ctx* ctx, size_t bytes) {
     std::lock_guard<std::mutex> g(ctx->mem_mu);
     if (ctx->used + bytes > ctx->budget) return AOK_E_OOM;
@@ -112,7 +114,11 @@ void Pool::release(uint64_t off, uint64_t n) {
 
 int make_cam(aok_ctx* ctx, const Scene* sc, const aok_camera* cam, double tau, CamDev* out) {
     (void)ctx;
-    if (!cam || cam->width <= 0 || cam->height <= 0 || (int64_t)cam->width * cam->height > (1ll << 31)) return AOK_E_INVALID;
+    // the casting grid has (H + 7) / 8 rows of blocks (at most 65535), and pixel
+    // indices are computed in int32 by some launches
+    if (!cam || cam->width <= 0 || cam->height <= 0 || cam->height > kMaxImageHeight ||
+        (int64_t)cam->width * cam->height >= (1ll << 31))
+        return AOK_E_INVALID;
     if (!(tau > 0.0) || !std::isfinite(tau)) return AOK_E_INVALID;
     if (!(cam->tan_half_fovy > 0.0f) || !std::isfinite(cam->tan_half_fovy)) return AOK_E_INVALID;
     std::memset(out, 0, sizeof(*out));
@@ -732,7 +738,7 @@ int aok_select_chunks(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, doubl
     }
     sc->select_gen++;
     st = aokk_select(&sd, &cd, sc->d_frame, lod_out, vis_out, n_visible_out ? ctx->d_counter : nullptr, stream);
-    if (st) return cuda_status(ctx, cudaGetLastError());
+    if (st) return launch_failure(ctx);
     if (n_visible_out) {
         cudaError_t e = cudaMemcpyAsync(ctx->pinned_word, ctx->d_counter, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1007,9 +1013,8 @@ static int render_impl(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, doub
         st = aokk_select(&sd, &cd, sc->d_frame, nullptr, nullptr, nullptr, stream);
         if (!st) st = cast_single(ctx, scene, sc, sd, cd, frame, counts, stream);
     }
-    if (st == AOK_E_OOM) return st;
-    if (st) return cuda_status(ctx, cudaGetLastError());
-    return AOK_OK;
+    if (st == AOK_E_CUDA) return launch_failure(ctx);
+    return st;
 }
 
 int aok_render(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double tau, const aok_frame* frame, void* stream) {
@@ -1028,8 +1033,9 @@ int aok_render_noalloc(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, doub
     if (st) return st;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return cuda_status(ctx, cudaGetLastError());
     SceneDev sd = scene_dev(sc);
-    st = aokk_render_noalloc(&sd, &cd, (uint4*)frame->hit, frame->t, stream);
-    if (st == AOK_E_CUDA) return cuda_status(ctx, cudaGetLastError());
+    CheckDev ck;
+    st = aokk_render_noalloc(&sd, &cd, (uint4*)frame->hit, frame->t, stream, check_dev(ctx, sc, &ck));
+    if (st == AOK_E_CUDA) return launch_failure(ctx);
     return st;
 }
 
@@ -1051,8 +1057,7 @@ int aok_cast_selected(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, const
     SceneDev sd = scene_dev(sc);
     if (ctx->single_persistent) st = render_persistent(ctx, sc, cd, frame, stream, false);
     else st = cast_single(ctx, scene, sc, sd, cd, frame, nullptr, stream);
-    if (st == AOK_E_OOM) return st;
-    return st ? cuda_status(ctx, cudaGetLastError()) : AOK_OK;
+    return st == AOK_E_CUDA ? launch_failure(ctx) : st;
 }
 
 // ---------------------------------------------------------------------------
@@ -1140,7 +1145,7 @@ int aok_render_tiles(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double
     st = aokk_select(&sd, &cd, sc->d_frame, nullptr, nullptr, nullptr, stream);
     if (!st) st = aokk_tiles_frame(&sd, &cd, sc->d_frame, &ctx->tiles.dev, (uint4*)frame->hit, frame->t,
                                    ctx->sm_count, stream);
-    if (st) return cuda_status(ctx, cudaGetLastError());
+    if (st) return st == AOK_E_CUDA ? launch_failure(ctx) : st;
     std::swap(ctx->tiles.dev.hiz_prev, ctx->tiles.dev.hiz_next);  // this frame's depth culls the next one
     return AOK_OK;
 }
@@ -1186,7 +1191,7 @@ int aok_beam_selected(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, void*
     cudaSetDevice(ctx->device);
     SceneDev sd = scene_dev(sc);
     st = run_beam(ctx, scene, sc, sd, cd, stream);
-    if (st == AOK_E_CUDA) return cuda_status(ctx, cudaGetLastError());
+    if (st == AOK_E_CUDA) return launch_failure(ctx);
     return st;
 }
 
@@ -1355,7 +1360,7 @@ static int pipe_render(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, doub
     }
     const SceneDev sd = scene_dev(sc);
     st = aokk_select(&sd, &cd, sl.frame, nullptr, nullptr, nullptr, p.prep);
-    if (st) return cuda_status(ctx, cudaGetLastError());
+    if (st) return launch_failure(ctx);
     BeamRead rd{nullptr, 0};
     if (beam) {
         uint32_t tag;
@@ -1373,13 +1378,13 @@ static int pipe_render(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, doub
             rd.tag = tag;
         }
         st = aokk_beam_run(P, ctx->beam.grid, p.prep);
-        if (st) return cuda_status(ctx, cudaGetLastError());
+        if (st) return launch_failure(ctx);
     }
     cudaError_t e = cudaEventRecord(sl.prepped, p.prep);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(p.render, sl.prepped, 0);
     if (e != cudaSuccess) return cuda_status(ctx, e);
     st = aokk_cast(&sd, &cd, sl.frame, (uint4*)sl.hit, sl.t, nullptr, p.render, nullptr, rd.bounds ? &rd : nullptr);
-    return st ? cuda_status(ctx, cudaGetLastError()) : AOK_OK;
+    return st ? launch_failure(ctx) : AOK_OK;
 }
 }  // extern "C++"
 
@@ -1429,7 +1434,7 @@ int aok_ray_dirs(aok_ctx* ctx, const aok_camera* cam, float* dirs, void* stream)
     if (st) return st;
     cudaSetDevice(ctx->device);
     st = aokk_ray_dirs(&cd, dirs, stream);
-    return st ? cuda_status(ctx, cudaGetLastError()) : AOK_OK;
+    return st ? launch_failure(ctx) : AOK_OK;
 }
 
 int aok_read_bandwidth(aok_ctx* ctx, uint64_t bytes, int reps, double* gbs) {
@@ -1448,9 +1453,9 @@ int aok_read_bandwidth(aok_ctx* ctx, uint64_t bytes, int reps, double* gbs) {
     if (e == cudaSuccess) e = cudaMemsetAsync(buf, 0x5A, bytes + 16, s);
     const int sms = aokk_sm_count(ctx->device);
     // warm-up passes (below the L2 size they also make the buffer resident), then one timed launch
-    if (e == cudaSuccess && aokk_read_bw(buf, bytes / 16, 2, sink, sms, s)) e = cudaGetLastError();
+    if (e == cudaSuccess && aokk_read_bw(buf, bytes / 16, 2, sink, sms, s)) e = aokk_take_launch_error();
     if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-    if (e == cudaSuccess && aokk_read_bw(buf, bytes / 16, reps, sink, sms, s)) e = cudaGetLastError();
+    if (e == cudaSuccess && aokk_read_bw(buf, bytes / 16, reps, sink, sms, s)) e = aokk_take_launch_error();
     if (e == cudaSuccess) e = cudaEventRecord(e1, s);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float ms = 0.0f;

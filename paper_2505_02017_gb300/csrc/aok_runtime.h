@@ -143,6 +143,7 @@ struct aok_ctx {
     uint32_t ctas_per_sm = 0, threads_per_cta = 0, packet_rays = 0, tile_w_log = 0;
     int single_persistent = 0;
     int batch_persistent = 0;  // 0: batches cast with one grid launch over block tiles
+    int batch_graph = 1;       // 1: a batch's launches replay as one CUDA graph
     unsigned long long* d_single_queue = nullptr;  // counters of single-view persistent launches
     aok::BatchParams single_params;
     aok::BatchArena batch;
@@ -165,6 +166,8 @@ struct aok_ctx {
 
 namespace aok {
 int cuda_status(aok_ctx* ctx, cudaError_t e);
+// AOK_E_CUDA for a launcher that returned AOK_E_CUDA, with the error code it read.
+int launch_failure(aok_ctx* ctx);
 int charge(aok_ctx* ctx, size_t bytes);
 void uncharge(aok_ctx* ctx, size_t bytes);
 int dev_alloc(aok_ctx* ctx, void** p, size_t bytes);

@@ -470,7 +470,7 @@ static void serve_loop(aok_ctx* ctx) {
 extern "C" {
 
 int aok_render_batch(aok_ctx* ctx, const aok_view* views, uint32_t n, void* stream) {
-    return render_batch_impl(ctx, views, n, stream, true);
+    return render_batch_impl(ctx, views, n, stream, ctx && ctx->batch_graph);
 }
 
 int aok_set_launch(aok_ctx* ctx, uint32_t ctas_per_sm, uint32_t threads_per_cta, uint32_t packet_rays) {
@@ -503,6 +503,12 @@ int aok_set_tile(aok_ctx* ctx, uint32_t tile_w) {
 int aok_set_batch_kernel(aok_ctx* ctx, int persistent) {
     if (!ctx || persistent < 0 || persistent > 1) return AOK_E_INVALID;
     ctx->batch_persistent = persistent;
+    return AOK_OK;
+}
+
+int aok_set_batch_graph(aok_ctx* ctx, int on) {
+    if (!ctx || on < 0 || on > 1) return AOK_E_INVALID;
+    ctx->batch_graph = on;
     return AOK_OK;
 }
 

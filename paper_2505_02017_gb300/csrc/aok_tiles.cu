@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(128) tc_resolve_kernel(SceneDev S, CamDev C, c
         atomicMax((int*)&T.hiz_next[ty * T.tiles_x + tx], __float_as_int(dist_up));
 }
 
-int tiles_status(cudaError_t e) { return e == cudaSuccess ? AOK_OK : AOK_E_CUDA; }
+int tiles_status(cudaError_t e) { return aokk_status(e); }
 
 }  // namespace
 

@@ -354,6 +354,36 @@ __device__ __noinline__ void lowest_entry_face(const RayState& r, const int32_t 
     }
 }
 
+// Exact test that the ray (t >= 0) meets the closed box of the chunk's solid
+// voxels (ref.aabb), in the chunk's mirrored frame with origin numerators
+// Oloc.  The counting build enters a chunk only then, so that its visit counts
+// are the definition's (a chunk is entered iff the ray meets its AABB); the
+// casting builds use a cheaper FP32 test with a margin, which may enter a
+// chunk the ray passes within 1/16 voxel of without changing any hit.
+template <bool FAST>
+__device__ __noinline__ bool meets_aabb(const RayState& r, const int32_t Oloc[3], const ChunkRef& ref, int mlog) {
+    const int32_t M = 1 << mlog;
+    int32_t Nn = 0, mn = 1, En = 0;  // latest entry parameter so far: t = 0
+    int32_t Hi[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const bool mir = (r.mir >> a) & 1u;
+        const int32_t lo = mir ? M - (int32_t)ref.aabb[3 + a] : (int32_t)ref.aabb[a];
+        const int32_t hi = mir ? M - (int32_t)ref.aabb[a] : (int32_t)ref.aabb[3 + a];
+        const int32_t Lo = (lo << kFix) - Oloc[a];
+        Hi[a] = (hi << kFix) - Oloc[a];
+        if (r.d[a] == 0.0f) {
+            if (Lo > 0 || Hi[a] < 0) return false;
+        } else if (tltf<FAST>(Nn, mn, Lo, r.m[a], r.E[a] - En)) {
+            Nn = Lo; mn = r.m[a]; En = r.E[a];
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+        if (r.d[a] != 0.0f && tltf<FAST>(Hi[a], r.m[a], Nn, mn, En - r.E[a])) return false;
+    return true;
+}
+
 // With a view distance, a hit farther than it is a miss (FP64, fixed order).
 __device__ __forceinline__ bool within_view(const SceneDev& S, const RayState& r, const HitRec& hit) {
     if (S.view_dist <= 0.0f) return true;
@@ -563,10 +593,10 @@ __device__ __forceinline__ void trace_pixel_t(const SceneDev& S, const CamDev& C
                     tf = fminf(tf, fmaxf(t1, t2));
                 }
             }
-            if (pass && tn <= tf) {
-                int32_t Oloc[3];
+            int32_t Oloc[3];
 #pragma unroll
-                for (int a = 0; a < 3; a++) Oloc[a] = Ow[a] - (cc[a] << cs);
+            for (int a = 0; a < 3; a++) Oloc[a] = Ow[a] - (cc[a] << cs);
+            if (pass && tn <= tf && (!COUNT || meets_aabb<FAST>(r, Oloc, ref, S.mlog))) {
                 if (trace_chunk<FAST, COUNT, CHECK, BEAM>(S, ref, r, Oloc, e, Ne, hit, cnt, ck)) {
                     lowest_entry_face<FAST>(r, Oloc, (int)ref.lod, hit);
                     found = emit_hit(S, r, ref, u, hit, dn, out_hit, out_t, pix);

@@ -41,3 +41,16 @@ def compare(gpu, ref, idx=None, max_amb_frac=1e-4, min_pixels_checked=1):
     assert np.isinf(g["dist"][miss]).all()
     assert int(ok.sum()) >= min_pixels_checked
     return int(ok.sum()), n_amb
+
+
+def stratified(W, H, n, seed):
+    """Row-major pixel indices: one seeded pixel in each cell of a grid of at
+    least n cells over the W x H image."""
+    s = max(1, int((W * H / n) ** 0.5))
+    while ((W + s - 1) // s) * ((H + s - 1) // s) < n and s > 1:
+        s -= 1
+    rng = np.random.default_rng(seed)
+    ys, xs = np.mgrid[0:H:s, 0:W:s]
+    xs = np.minimum(xs + rng.integers(0, s, xs.shape), W - 1)
+    ys = np.minimum(ys + rng.integers(0, s, ys.shape), H - 1)
+    return np.unique((ys * W + xs).ravel())

@@ -72,6 +72,33 @@ def test_batch_equals_solo_and_graph_replay(env):
             assert same(r, o)
 
 
+def test_batch_graph_with_beam_passes(env):
+    """With the beam pass on for every view (its minimum frame size lowered),
+    a batch's selection, beam pass and cast replay as one CUDA graph: the
+    first call builds it, the second (same list shape, moved cameras) updates
+    its nodes in place; frames equal the eager launches and the solo renders."""
+    ctx, worlds, scenes = env
+    aok.beam_tune(ctx, min_pixels=1)
+    try:
+        ps1 = poses(worlds, 9, 303)
+        ps2 = [(n, replace(c, origin=c.origin + np.float32(0.25)), tau) for (n, c, tau) in ps1]
+        for ps in (ps1, ps2):
+            refs = [solo(ctx, scenes[n], c, tau) for (n, c, tau) in ps]
+            res = {}
+            for graph in (False, True):
+                aok.set_batch_graph(ctx, graph)
+                outs = [aok.alloc_frame(c.W, c.H) for (_, c, _) in ps]
+                views = [aok.make_view(scenes[n], c, tau, h, t) for (n, c, tau), (h, t) in zip(ps, outs)]
+                aok.render_batch(ctx, views)
+                torch.cuda.synchronize()
+                res[graph] = outs
+            for r, a, b in zip(refs, res[False], res[True]):
+                assert same(r, a) and same(r, b)
+    finally:
+        aok.set_batch_graph(ctx, True)
+        aok.beam_tune(ctx)
+
+
 def test_batch_over_128_views_and_every_tile_shape(env):
     ctx, worlds, scenes = env
     ps = poses(worlds, 133, 7)

@@ -70,17 +70,19 @@ def test_lossy_blocks_match_oracle(ctx, spec):
     raw = aok.Scene.from_world(ctx, w, built=bw)
     lossy = aok.Scene.from_world(ctx, w, built=bw, color_tol=0.05)
     S = orc.OracleScene(w, color_tol=0.05)
-    changed = 0
+    changed = amb = n = 0
     for camf in CAMS:
         cam = camf(w)
         g = decode(*render(ctx, lossy, cam, 2.0))
         ref = S.cast(cam, S.select(cam, 2.0))
-        compare(g, ref, max_amb_frac=2e-3)
+        amb += compare(g, ref, max_amb_frac=1.0)[1]  # the ambiguous share is bounded over the three frames
+        n += cam.W * cam.H
         g_raw = decode(*render(ctx, raw, cam, 2.0))
         for k in ("hit", "x", "y", "z", "lod", "normal", "dist"):
             assert (g[k] == g_raw[k]).all(), k
         changed += int((g["mat"] != g_raw["mat"]).sum())
         assert same(render(ctx, lossy, cam, 2.0), render(ctx, lossy, cam, 2.0, tiles=True))
+    assert amb <= 1e-4 * n, (amb, n)
     if spec.mat_mode == 1:
         assert changed > 0
     assert lossy.usage()["color_bytes"] <= raw.usage()["color_bytes"]

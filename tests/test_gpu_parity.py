@@ -10,7 +10,7 @@ import pytest
 import oracle as orc
 import scenegen as sg
 from gpu_util import compare, decode
-from worlds import MED64, MULTI16, MULTI32, TINY32
+from worlds import HAND_CASES, MED64, MULTI16, MULTI32, TINY32, hand_world
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -72,7 +72,7 @@ def test_small_worlds_every_pixel(ctx, case):
     w, _, _ = scene_for(ctx, spec)
     cam = camf(w)
     g, ref, _ = run(ctx, spec, cam, tau)
-    checked, amb = compare(g, ref, max_amb_frac=2e-3)
+    checked, amb = compare(g, ref)
     assert checked > 0.99 * cam.W * cam.H
 
 
@@ -90,7 +90,7 @@ def test_view_distance(ctx):
     w, _, _ = scene_for(ctx, spec)
     cam = sg.ground_camera(w, 4, 64, 40, z_lo=4, z_hi=20)
     g, ref, _ = run(ctx, spec, cam, 1.0)
-    compare(g, ref, max_amb_frac=2e-3)
+    compare(g, ref)
     assert (ref["hit"] == 0).sum() > 0
 
 
@@ -175,11 +175,27 @@ def test_traversal_counts_match_oracle(ctx):
     ref = S.cast(cam, sel)
     ok = ref["amb"] == 0
     for j, k in enumerate(("v_int", "v_leaf", "resolve_bytes")):
-        same = (c[ok, j] == ref[k][ok])
-        assert same.mean() > 0.995, (k, same.mean())
+        bad = np.nonzero(c[ok, j] != ref[k][ok])[0]
+        assert len(bad) == 0, (k, len(bad), c[ok, j][bad[:5]].tolist(), ref[k][ok][bad[:5]].tolist())
     # the counted frame equals the plain one
     g = decode(hit, t)
-    compare(g, ref, max_amb_frac=2e-3)
+    compare(g, ref)
+
+
+def test_counts_on_hand_counted_scenes(ctx):
+    """The counting kernel's visits and resolve bytes on the hand-counted scenes
+    (the oracle's counter pins): straight-down rays through a few placed voxels."""
+    for voxels, size, n_lods, lod, x, y, want in HAND_CASES:
+        w = hand_world(voxels, n_lods, size)
+        sc = aok.Scene.from_world(ctx, w, threads=2)
+        cam = sg.make_camera((x, y, 40.0), (0.0, 0.0, -1.0), 1, 1)
+        assert orc.OracleScene(w).select(cam, 1.0).tolist() == [lod]
+        hit, t = aok.alloc_frame(1, 1)
+        counts = torch.zeros((1, 1, 3), dtype=torch.int32, device="cuda")
+        aok.render_counted(ctx, sc, cam, 1.0, hit, t, counts)
+        torch.cuda.synchronize()
+        assert tuple(counts.view(-1).tolist()) == want, (voxels, x, y)
+        sc.destroy()
 
 
 def test_city4096_1080p_every_pixel(ctx):
@@ -223,6 +239,11 @@ def test_abi_errors(ctx):
     f2.hit = hit.data_ptr() + 4  # misaligned
     f2.t = t.data_ptr()
     assert L.aok_render(ctx.h, sc.id, ctypes.byref(c), 1.0, ctypes.byref(f2), s) == aok.AOK_E_INVALID
+    # image sizes whose casting grid could not launch (more than 65535 rows of
+    # 8-pixel blocks) or with 2^31 pixels are refused before any launch
+    for W, H in ((1, 600000), (4096, 524288)):
+        cb = aok.to_camera(sg.make_camera((10.0, 10.0, 10.0), (1.0, 0.5, -0.2), W, H))
+        assert L.aok_render(ctx.h, sc.id, ctypes.byref(cb), 1.0, ctypes.byref(f), s) == aok.AOK_E_INVALID
     # a corrupt blob is rejected by the upload and nothing changes
     aok.render(ctx, sc, cam, 1.0, hit, t)
     torch.cuda.synchronize()
@@ -295,15 +316,18 @@ def test_maximum_world_extent(ctx):
                         box_hollow=1)
     w, sc, S = scene_for(ctx, spec)
     x, y, z = 130990.25, 500.5, 900.0
+    amb = n = 0
     for fwd in [(-1.0, 0.05, -0.3), (1.0, -0.1, -0.4), (-1.0, 0.0, -0.035)]:
         cam = sg.make_camera((x, y, z), fwd, 160, 90)
         g, ref, sel = run(ctx, spec, cam, 1.0)
-        compare(g, ref, max_amb_frac=2e-3)
+        amb += compare(g, ref, max_amb_frac=1.0)[1]  # the ambiguous share is bounded over the three frames
+        n += cam.W * cam.H
         hit, t = aok.alloc_frame(cam.W, cam.H)
         aok.render_tiles(ctx, sc, cam, 1.0, hit, t)
         torch.cuda.synchronize()
         gt = decode(hit, t)
         assert all((gt[k] == g[k]).all() for k in ("hit", "x", "y", "z", "lod", "mat", "normal"))
+    assert amb <= 1e-4 * n, (amb, n)
     assert (g["hit"] == 1).sum() > 500 and (g["x"][g["hit"] == 1] < 131072 - 16 * 512).any()
 
 

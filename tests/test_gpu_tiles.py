@@ -85,7 +85,7 @@ def test_small_worlds_equal_march_and_oracle(ctx, case):
     assert same(ref, again)
     assert st2["items_marched_1"] + st2["items_marched_2"] <= st1["items_marched_1"]
     orc_ref = S.cast(cam, S.select(cam, tau), view_dist=spec.view_dist)
-    compare(decode(*first), orc_ref, max_amb_frac=2e-3)
+    compare(decode(*first), orc_ref)
 
 
 def test_moving_camera_with_history(ctx):
@@ -113,7 +113,7 @@ def test_view_distance(ctx):
         out, _ = tiles(ctx, sc, cam, 1.0)
         assert same(ref, out)
     orc_ref = S.cast(cam, S.select(cam, 1.0), view_dist=spec.view_dist)
-    compare(decode(*out), orc_ref, max_amb_frac=2e-3)
+    compare(decode(*out), orc_ref)
     assert (orc_ref["hit"] == 0).sum() > 0
 
 

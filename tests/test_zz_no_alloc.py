@@ -51,6 +51,29 @@ def test_noalloc_matches_render_on_two_calls_in_a_row():
         rel = np.abs(a["dist"][h] - b["dist"][h]) / b["dist"][h]
         assert (rel <= DIST_RTOL).all()
         assert np.isinf(a["dist"][~h]).all()
+
+    # with checked casting on it takes the checked kernel: the same frame and no
+    # pool index out of range (its error word is context memory: still no allocation)
+    cam = cams[0]
+    ref_hit, ref_t = aok.alloc_frame(cam.W, cam.H)
+    aok.render(ctx, scene, cam, 4.0, ref_hit, ref_t)
+    aok.set_checked(ctx, True)
+    hit, t = aok.alloc_frame(cam.W, cam.H)
+    c = aok.to_camera(cam)
+    f = aok.frame_of(hit, t)
+    assert L.aok_render_noalloc(ctx.h, scene.id, ctypes.byref(c), 4.0, ctypes.byref(f), stream) == aok.AOK_OK
+    torch.cuda.synchronize()
+    assert aok.checked_errors(ctx) == 0
+    aok.set_checked(ctx, False)
+    assert torch.equal(hit, ref_hit) and torch.equal(t.view(torch.int32), ref_t.view(torch.int32))
+
+    # a camera whose casting grid could not launch (more than 65535 rows of
+    # 8-pixel blocks) and one of 2^31 pixels are refused before any launch
+    for W, H in ((1, 600000), (4096, 524288)):
+        c = aok.to_camera(sg.make_camera((10.0, 10.0, 10.0), (1.0, 0.5, -0.2), W, H))
+        f = aok.frame_of(hit, t)
+        assert L.aok_render_noalloc(ctx.h, scene.id, ctypes.byref(c), 1.0, ctypes.byref(f), stream) == \
+            aok.AOK_E_INVALID
     scene.destroy()
 
     # a grid larger than the static table is refused before any work is enqueued
