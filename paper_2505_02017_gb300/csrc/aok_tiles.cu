@@ -192,7 +192,8 @@ __device__ __forceinline__ int pair_pixel(const SceneDev& S, const CamDev& C, co
             const int32_t uv = ((r.mir >> a) & 1u) ? side - hit.c[a] : hit.c[a];
             pay |= (unsigned long long)(uint32_t)((u[a] << S.mlog) + (uv << n)) << (17 * a);
         }
-        pay |= (unsigned long long)n << 51 | (unsigned long long)hit.e << 54 | (unsigned long long)hit.mat << 56;
+        const uint32_t mat = hit_material(S, ref, hit.idx);
+        pay |= (unsigned long long)n << 51 | (unsigned long long)hit.e << 54 | (unsigned long long)mat << 56;
         const ulonglong2 mine = make_ulonglong2(
             ((unsigned long long)tk << 32) | ((unsigned long long)(en.order & 0xFFFFu) << 16) | chunk, pay);
         // install the record if its key is the smallest so far

@@ -117,8 +117,14 @@ struct HitRec {
     int32_t c[3];       // voxel index (mirrored, chunk-local, voxel units of the LOD)
     int e;              // entry axis (3 = origin inside)
     int32_t Ne;         // entry plane numerator
-    uint32_t mat;
+    uint32_t idx;       // depth-first index of the voxel in its DAG (Sec. 3.3)
 };
+
+// Material of a hit: the entry of its DFS index in the (chunk, LOD)'s colour
+// array or colour blocks (the colour resolve of Sec. 3.5).
+__device__ __forceinline__ uint32_t hit_material(const SceneDev& S, const ChunkRef& ref, uint32_t idx) {
+    return ref.nblocks == 0 ? S.mats[ref.mat_base + idx] : block_colour(S.mats + ref.mat_base, ref.nblocks, idx);
+}
 
 struct Counters {
     uint32_t v_int, v_leaf, rbytes;
@@ -141,6 +147,9 @@ __device__ __forceinline__ bool out_of(uint64_t i, uint64_t n, const CheckDev* c
     return false;
 }
 
+// (the per-level stack is written on entering a level, before any read: the
+// compiler cannot see that through the level index)
+#pragma nv_diag_suppress 549
 template <bool FAST, bool COUNT, bool CHECK = false, bool BEAM = false>
 __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& ref, const RayState& r,
                                             const int32_t Oloc[3], int e, int32_t Ne, HitRec& hit, Counters& cnt,
@@ -148,8 +157,12 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
     const uint32_t* __restrict__ nodes = S.nodes;
     const int R = S.mlog;
     const int n = (int)ref.lod;
-    uint32_t sidx[kMaxLevels];
+    // per interior level on the path: {node word index, DFS index of the
+    // node's first voxel}, and the node's child mask (a level is written when
+    // the path enters it, before any read)
+    uint2 sia[kMaxLevels];
     uint32_t smask[kMaxLevels];
+    uint32_t lacc = 0;  // DFS index of the current leaf block's first voxel
     int k = R;
     int32_t c0 = 0, c1 = 0, c2 = 0;
     int32_t me = 1, Ee = 0;
@@ -163,27 +176,33 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
     // (interior levels, also pushed on the stack), its leaf block's group
     // occupancy (leaf level) or its 2x2x2 group's voxel bits.  False when a
     // checked build finds a pool index out of range.
-    uint32_t* const st_idx = sidx;
-    uint32_t* const st_mask = smask;
+    // The node's device layout [hdr, count, (child, prefix) x k] gives the
+    // child pointer and the summed counts of the earlier children in one
+    // 8-byte load, so each level's DFS index is accumulated on the way down.
     auto fetch = [&]() -> bool {
         if (k >= n + 2) {
-            uint32_t idx;
+            uint32_t idx, acc;
             if (k == R) {
                 idx = ref.root;
+                acc = 0;
             } else {
                 const uint32_t oct = ((uint32_t)(c0 & 1) | ((uint32_t)(c1 & 1) << 1) | ((uint32_t)(c2 & 1) << 2)) ^ r.mir;
-                const uint64_t at = (uint64_t)st_idx[k + 1] + 2 + 2 * __popc(st_mask[k + 1] & ((1u << oct) - 1u));
-                if (out_of<CHECK>(at, ck ? ck->n_nodes : 0, ck, 1u)) return false;
-                idx = nodes[at];
+                const uint2 par = sia[k + 1];
+                const uint64_t at = (uint64_t)par.x + 2 + 2 * __popc(smask[k + 1] & ((1u << oct) - 1u));
+                if (out_of<CHECK>(at + 1, ck ? ck->n_nodes : 0, ck, 1u)) return false;
+                const uint2 cp = *reinterpret_cast<const uint2*>(nodes + at);  // even word index: 8-byte aligned
+                idx = cp.x;
+                acc = par.y + cp.y;
             }
             if (k >= n + 3) {
                 if (out_of<CHECK>((uint64_t)idx + 1, ck ? ck->n_nodes : 0, ck, 1u)) return false;
                 pm8 = nodes[idx] & 0xFFu;
-                st_idx[k] = idx;
-                st_mask[k] = pm8;
+                sia[k] = make_uint2(idx, acc);
+                smask[k] = pm8;
                 if (COUNT) cnt.v_int++;
             } else {
                 if (out_of<CHECK>(idx, ck ? ck->n_leaves : 0, ck, 2u)) return false;
+                lacc = acc;
                 lmu = S.leaves[idx];
                 uint64_t t = lmu | (lmu >> 1);
                 t |= t >> 4;
@@ -243,26 +262,28 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
                 hit.c[0] = c0; hit.c[1] = c1; hit.c[2] = c2;
                 hit.e = e;
                 hit.Ne = Ne;
-                // material through the depth-first index (Sec. 3.3)
+                // depth-first index (Sec. 3.3): the leaf block's first voxel
+                // plus the solid voxels before the hit bit
                 const uint32_t mirv = r.mir;
                 const int32_t side = (1 << (R - n)) - 1;
                 const int32_t u0 = (mirv & 1u) ? side - c0 : c0;
                 const int32_t u1 = (mirv & 2u) ? side - c1 : c1;
                 const int32_t u2 = (mirv & 4u) ? side - c2 : c2;
-                // node = [hdr, count, (child, earlier siblings' count) x k]: one word per level
-                uint32_t idx = 0;
-                for (int j = R; j >= n + 3; j--) {
-                    const int sh = j - 1 - n;
-                    const int oct = ((u0 >> sh) & 1) | (((u1 >> sh) & 1) << 1) | (((u2 >> sh) & 1) << 2);
-                    const int rk = __popc(smask[j] & ((1u << oct) - 1u));
-                    if (out_of<CHECK>((uint64_t)sidx[j] + 3 + 2 * rk, ck ? ck->n_nodes : 0, ck, 1u)) return false;
-                    idx += nodes[sidx[j] + 3 + 2 * rk];
-                    if (COUNT) cnt.rbytes += rk * ((j - 1 == n + 2) ? 8u : 4u);
-                }
                 const int bit = (u0 & 3) + 4 * (u1 & 3) + 16 * (u2 & 3);
-                idx += (uint32_t)__popcll(lmu & ((1ull << bit) - 1ull));
+                hit.idx = lacc + (uint32_t)__popcll(lmu & ((1ull << bit) - 1ull));
+                if (COUNT) {
+                    // the paper-format resolve: the counts of the earlier siblings on the path
+                    for (int j = R; j >= n + 3; j--) {
+                        const int sh = j - 1 - n;
+                        const int oct = ((u0 >> sh) & 1) | (((u1 >> sh) & 1) << 1) | (((u2 >> sh) & 1) << 2);
+                        const int rk = __popc(smask[j] & ((1u << oct) - 1u));
+                        cnt.rbytes += rk * ((j - 1 == n + 2) ? 8u : 4u);
+                    }
+                    cnt.rbytes += 1;
+                }
                 if (CHECK) {
                     // raw array: the entry; blocks: the whole block structure
+                    const uint32_t idx = hit.idx;
                     const uint64_t end = ref.nblocks == 0
                                              ? ref.mat_base + idx
                                              : ref.mat_base + 4ull * (1 + ((uint64_t)idx >> 7) + 1) - 1;
@@ -275,9 +296,6 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
                             return false;
                     }
                 }
-                hit.mat = ref.nblocks == 0 ? S.mats[ref.mat_base + idx]
-                                           : block_colour(S.mats + ref.mat_base, ref.nblocks, idx);
-                if (COUNT) cnt.rbytes += 1;
                 return true;
             }
             if (!fetch()) return false;
@@ -315,11 +333,11 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
                 else { cax = ++c2; N2 += side; }
                 if ((cax << k) >= (1 << R)) return false;  // left the chunk
                 if ((cax & 1) == 0) {
-                    do {
-                        c0 >>= 1; c1 >>= 1; c2 >>= 1;
-                        cax >>= 1;
-                        k++;
-                    } while (k < R && (cax & 1) == 0);
+                    // left the parent: up as many levels as cax has trailing
+                    // zero bits (fewer than R - k, as the chunk was not left)
+                    const int p = __ffs(cax) - 1;
+                    c0 >>= p; c1 >>= p; c2 >>= p;
+                    k += p;
                     pm8 = k >= n + 2 ? smask[k + 1] : g8;  // popped into a new parent (a node or the leaf)
                     break;
                 }
@@ -333,12 +351,14 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
     }
 }
 
+#pragma nv_diag_default 549
+
 // Entry face of a hit entered through an edge or a corner of its voxel (the
 // voxel's lower faces of several axes crossed at the entry instant): the
 // lowest of those axes, with its plane.  n: the hit's LOD; Oloc: the mirrored
 // chunk-local origin numerators trace_chunk was given.
 template <bool FAST>
-__device__ __noinline__ void lowest_entry_face(const RayState& r, const int32_t Oloc[3], int n, HitRec& hit) {
+__device__ __forceinline__ void lowest_entry_face(const RayState& r, const int32_t Oloc[3], int n, HitRec& hit) {
     const int e = hit.e;
     if (e == 0 || e == 3) return;
     const int32_t Ne = hit.Ne, me = r.m[e], Ee = r.E[e];
@@ -396,12 +416,14 @@ __device__ __forceinline__ bool within_view(const SceneDev& S, const RayState& r
 }
 
 // Write the output record of a hit that trace_chunk found in the chunk region
-// u (unmirrored chunk coordinates); dn = |d| in FP32.  Returns false (writes
-// nothing) when the view distance turns the hit into a miss.
+// u (unmirrored chunk coordinates) of the (chunk, LOD) ref; dn = |d| in FP32.
+// Returns false (writes nothing) when the view distance turns the hit into a
+// miss.
 __device__ __forceinline__ bool emit_hit(const SceneDev& S, const RayState& r, const ChunkRef& ref, const int32_t u[3],
                                          const HitRec& hit, float dn, uint4* __restrict__ out_hit,
                                          float* __restrict__ out_t, size_t pix) {
     if (!within_view(S, r, hit)) return false;
+    const uint32_t mat = hit_material(S, ref, hit.idx);
     // un-mirror the voxel index to world LOD-0 units
     const int n = (int)ref.lod;
     const int32_t side = (1 << (S.mlog - n)) - 1;
@@ -415,7 +437,7 @@ __device__ __forceinline__ bool emit_hit(const SceneDev& S, const RayState& r, c
     if (hit.e < 3) dist = __fdiv_rn((float)hit.Ne * (1.0f / 4096.0f), fabsf(r.d[hit.e])) * dn;
     const uint32_t normal = hit.e == 3 ? 7u : (uint32_t)(2 * hit.e) + ((r.mir >> hit.e) & 1u);
     out_hit[pix] = make_uint4((uint32_t)wxyz[0], (uint32_t)wxyz[1], (uint32_t)wxyz[2],
-                              (uint32_t)n | (hit.mat << 8) | (normal << 16) | (1u << 19));
+                              (uint32_t)n | (mat << 8) | (normal << 16) | (1u << 19));
     out_t[pix] = dist;
     return true;
 }
@@ -564,18 +586,22 @@ __device__ __forceinline__ void trace_pixel_t(const SceneDev& S, const CamDev& C
             }
         }
     }
-    const float dn = ray_norm(r);
     float inv[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) inv[a] = 1.0f / r.d[a];
+    // The march stops at the first hit and keeps what the output needs; the
+    // per-hit work (entry-face rule, material, distance, stores) runs after
+    // the loop, where the warp's lanes are together again.
+    int32_t u[3];
+    ChunkRef ref;
+    int32_t Oloc[3];
     while (alive) {
-        int32_t u[3];
 #pragma unroll
         for (int a = 0; a < 3; a++) u[a] = ((r.mir >> a) & 1u) ? S.grid[a] - 1 - cc[a] : cc[a];
-        const ChunkRef ref = frame[(size_t)u[0] + (size_t)S.grid[0] * ((size_t)u[1] + (size_t)S.grid[1] * u[2])];
+        ref = frame[(size_t)u[0] + (size_t)S.grid[0] * ((size_t)u[1] + (size_t)S.grid[1] * u[2])];
         if (S.view_dist > 0.0f && e < 3) {
             const float tent = (float)Ne / (4096.0f * fabsf(r.d[e]));
-            if (tent * dn > S.view_dist * 1.00001f + 1.0f) break;
+            if (tent * ray_norm(r) > S.view_dist * 1.00001f + 1.0f) break;
         }
         if (ref.root != kNone) {
             // skip chunks whose solid-voxel AABB (grown by 1/16 voxel) the ray misses
@@ -593,13 +619,11 @@ __device__ __forceinline__ void trace_pixel_t(const SceneDev& S, const CamDev& C
                     tf = fminf(tf, fmaxf(t1, t2));
                 }
             }
-            int32_t Oloc[3];
 #pragma unroll
             for (int a = 0; a < 3; a++) Oloc[a] = Ow[a] - (cc[a] << cs);
             if (pass && tn <= tf && (!COUNT || meets_aabb<FAST>(r, Oloc, ref, S.mlog))) {
                 if (trace_chunk<FAST, COUNT, CHECK, BEAM>(S, ref, r, Oloc, e, Ne, hit, cnt, ck)) {
-                    lowest_entry_face<FAST>(r, Oloc, (int)ref.lod, hit);
-                    found = emit_hit(S, r, ref, u, hit, dn, out_hit, out_t, pix);
+                    found = true;
                     break;
                 }
             }
@@ -616,6 +640,10 @@ __device__ __forceinline__ void trace_pixel_t(const SceneDev& S, const CamDev& C
         else { ax = 2; Ne = N2; me = r.m[2]; Ee = r.E[2]; }
         e = ax;
         if (++cc[ax] >= S.grid[ax]) break;
+    }
+    if (found) {
+        lowest_entry_face<FAST>(r, Oloc, (int)ref.lod, hit);
+        found = emit_hit(S, r, ref, u, hit, ray_norm(r), out_hit, out_t, pix);
     }
     if (!found) emit_miss(out_hit, out_t, pix);
     if (COUNT) {
