@@ -60,6 +60,8 @@ struct CamDev {
     float of[3];            // origin as float
     float planes[4][4];     // view-pyramid side planes: n . (p - o) <= 0 inside (n, unused)
     double sf;              // StreamingFactor for Eq. 1
+    float aspect;           // (float)W / (float)H, one IEEE rounding
+    float pad;
 };
 
 // Device buffers of the tile-chunk pipeline (Sec. 3.5) for one resolution.

@@ -6,6 +6,7 @@
 
 #include <atomic>
 #include <cstdint>
+#include <climits>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -104,18 +105,52 @@ __global__ void select_batch_kernel(const __grid_constant__ BatchParams P) {
     if (chunk < nch) select_one(v.scene, v.cam, v.frame, nullptr, nullptr, nullptr, chunk);
 }
 
+// The beam pass's bound pyramid of one W x H view as a casting kernel reads
+// it: per level, the offset of its first entry and its row width (computed
+// once on the host instead of per pixel).
+struct BeamLookup {
+    const unsigned long long* bounds;  // nullptr: no bounds
+    uint32_t tag;
+    uint32_t off[kBeamPyr], wl[kBeamPyr];
+};
+
+BeamLookup beam_lookup(const BeamRead* b, int W, int H) {
+    BeamLookup L;
+    std::memset(&L, 0, sizeof(L));
+    if (!b) return L;
+    L.bounds = b->bounds;
+    L.tag = b->tag;
+    const uint32_t tx = (uint32_t)(W + kBeamTileW - 1) / kBeamTileW, ty = (uint32_t)(H + kBeamTileH - 1) / kBeamTileH;
+    for (int l = 0; l < kBeamPyr; l++) {
+        L.off[l] = beam_level_offset(tx, ty, l);
+        L.wl[l] = (tx + (1u << l) - 1) >> l;
+    }
+    return L;
+}
+
+// beam_bound (aok_trace.cuh) with the pyramid's level table; 0 (no restart)
+// without bounds (a pass that found no usable projection for the view)
+__device__ __forceinline__ int32_t beam_bound_lut(const BeamLookup& b, int px, int py) {
+    if (!b.bounds) return 0;
+    const uint32_t x = (uint32_t)px / kBeamTileW, y = (uint32_t)py / kBeamTileH;
+    unsigned long long v = ~0ull;
+#pragma unroll
+    for (int L = 0; L < kBeamPyr; L++) v = min(v, __ldcg(b.bounds + b.off[L] + (y >> L) * b.wl[L] + (x >> L)));
+    return (uint32_t)(v >> 32) == b.tag ? (int32_t)(uint32_t)v : INT_MAX;
+}
+
 // 16 x 8 pixel tiles, warps of 8 x 4 pixels.  BEAM: the warp's 8 x 4 tile
 // bound from the beam pass (aok_beam.cu) restarts its rays' march past the
 // space in front of the nearest voxel they can meet.
 template <bool COUNT, bool BEAM = false>
 __global__ void __launch_bounds__(128) cast_kernel(SceneDev S, CamDev C, const ChunkRef* __restrict__ frame,
                                                    uint4* __restrict__ out_hit, float* __restrict__ out_t,
-                                                   uint32_t* __restrict__ counts, BeamRead beam) {
+                                                   uint32_t* __restrict__ counts, const BeamLookup beam) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int px = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
     const int py = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
     if (px >= C.W || py >= C.H) return;
-    const int32_t Dn = BEAM ? beam_bound(beam.bounds, beam.tag, C.W, C.H, px, py) : 0;
+    const int32_t Dn = BEAM ? beam_bound_lut(beam, px, py) : 0;
     trace_pixel<COUNT, false, BEAM>(S, C, frame, px, py, out_hit, out_t, counts, (size_t)py * C.W + px, nullptr, Dn);
 }
 
@@ -255,16 +290,17 @@ int aokk_cast(const SceneDev* s, const CamDev* c, const ChunkRef* frame, uint4* 
               void* stream, const CheckDev* ck, const BeamRead* beam) {
     dim3 grid((c->W + 15) / 16, (c->H + 7) / 8);
     const cudaStream_t st = (cudaStream_t)stream;
+    const BeamLookup bl = beam_lookup(beam, c->W, c->H);
     if (ck && !counts)
         cast_kernel_checked<<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, *ck);
     else if (counts && beam)
-        cast_kernel<true, true><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, counts, *beam);
+        cast_kernel<true, true><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, counts, bl);
     else if (counts)
-        cast_kernel<true><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, counts, BeamRead{nullptr, 0});
+        cast_kernel<true><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, counts, bl);
     else if (beam)
-        cast_kernel<false, true><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, nullptr, *beam);
+        cast_kernel<false, true><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, nullptr, bl);
     else
-        cast_kernel<false><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, nullptr, BeamRead{nullptr, 0});
+        cast_kernel<false><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, nullptr, bl);
     return status_of(cudaGetLastError());
 }
 
@@ -506,7 +542,7 @@ int aokk_render_noalloc(const SceneDev* s, const CamDev* c, uint4* hit, float* t
     if (ck)
         cast_kernel_checked<<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, *ck);
     else
-        cast_kernel<false><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, nullptr, BeamRead{nullptr, 0});
+        cast_kernel<false><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, nullptr, beam_lookup(nullptr, 0, 0));
     return status_of(cudaGetLastError());
 }
 

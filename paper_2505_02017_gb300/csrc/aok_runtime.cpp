@@ -129,6 +129,7 @@ int make_cam(aok_ctx* ctx, const Scene* sc, const aok_camera* cam, double tau, C
     out->tan_half = cam->tan_half_fovy;
     out->W = cam->width;
     out->H = cam->height;
+    out->aspect = (float)cam->width / (float)cam->height;  // the ray's W / H: one IEEE binary32 division
     for (int a = 0; a < 3; a++) {
         const double o = cam->origin[a];
         if (!std::isfinite(o) || std::fabs(o) >= 131072.0) return AOK_E_INVALID;

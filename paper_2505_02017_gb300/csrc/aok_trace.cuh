@@ -46,6 +46,17 @@ __device__ __forceinline__ void decompose(float d, int32_t& m, int32_t& E) {
     else { m = (int32_t)(man | 0x800000u); E = (int32_t)ex - 150; }
 }
 
+// floor(x) of a real x from an FP32 estimate p with |p - x| <= err: when no
+// integer lies within err of p, floor(p) == floor(x) (p - floor(p) and
+// floor(p) + 1 - p are exact for the magnitudes used here).  False when an
+// integer is that close: the caller then decides with exact comparisons.
+__device__ __forceinline__ bool floor_if_clear(float p, float err, int32_t& f) {
+    const float fl = floorf(p);
+    if (!(p - fl > err && fl + 1.0f - p > err)) return false;
+    f = (int32_t)fl;
+    return true;
+}
+
 // Ray direction of pixel (px, py): IEEE binary32, one rounding per operation.
 __device__ __forceinline__ void ray_dir(const CamDev& c, int px, int py, float d[3]) {
     const float fW = __int2float_rn(c.W), fH = __int2float_rn(c.H);
@@ -53,7 +64,7 @@ __device__ __forceinline__ void ray_dir(const CamDev& c, int px, int py, float d
     const float b = __fdiv_rn(a, fW);
     const float cc = __fsub_rn(b, 1.0f);
     const float e = __fmul_rn(cc, c.tan_half);
-    const float aspect = __fdiv_rn(fW, fH);
+    const float aspect = c.aspect;  // fW / fH, rounded once (on the host)
     const float u = __fmul_rn(e, aspect);
     const float a2 = __int2float_rn(2 * py + 1);
     const float b2 = __fdiv_rn(a2, fH);
@@ -158,10 +169,11 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
     const int R = S.mlog;
     const int n = (int)ref.lod;
     // per interior level on the path: {node word index, DFS index of the
-    // node's first voxel}, and the node's child mask (a level is written when
-    // the path enters it, before any read)
-    uint2 sia[kMaxLevels];
-    uint32_t smask[kMaxLevels];
+    // node's first voxel, child mask} (a level is written when the path
+    // enters it, before any read); the parent of the current level's cells
+    // is also kept in registers (pidx, pacc and its mask pm8)
+    uint4 st[kMaxLevels];
+    uint32_t pidx = 0, pacc = 0;
     uint32_t lacc = 0;  // DFS index of the current leaf block's first voxel
     int k = R;
     int32_t c0 = 0, c1 = 0, c2 = 0;
@@ -187,18 +199,18 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
                 acc = 0;
             } else {
                 const uint32_t oct = ((uint32_t)(c0 & 1) | ((uint32_t)(c1 & 1) << 1) | ((uint32_t)(c2 & 1) << 2)) ^ r.mir;
-                const uint2 par = sia[k + 1];
-                const uint64_t at = (uint64_t)par.x + 2 + 2 * __popc(smask[k + 1] & ((1u << oct) - 1u));
+                const uint64_t at = (uint64_t)pidx + 2 + 2 * __popc(pm8 & ((1u << oct) - 1u));
                 if (out_of<CHECK>(at + 1, ck ? ck->n_nodes : 0, ck, 1u)) return false;
                 const uint2 cp = *reinterpret_cast<const uint2*>(nodes + at);  // even word index: 8-byte aligned
                 idx = cp.x;
-                acc = par.y + cp.y;
+                acc = pacc + cp.y;
             }
             if (k >= n + 3) {
                 if (out_of<CHECK>((uint64_t)idx + 1, ck ? ck->n_nodes : 0, ck, 1u)) return false;
                 pm8 = nodes[idx] & 0xFFu;
-                sia[k] = make_uint2(idx, acc);
-                smask[k] = pm8;
+                st[k] = make_uint4(idx, acc, pm8, 0u);
+                pidx = idx;
+                pacc = acc;
                 if (COUNT) cnt.v_int++;
             } else {
                 if (out_of<CHECK>(idx, ck ? ck->n_leaves : 0, ck, 2u)) return false;
@@ -239,10 +251,19 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
             } else if (a == e) {
                 f = (Ne + Oloc[a]) >> sh;  // on the entry plane
             } else {
-                const float p = ((float)Oloc[a] + te * (float)r.m[a]) * (1.0f / (float)(1 << sh));
-                f = (int32_t)floorf(fminf(fmaxf(p, -1.0f), (float)fmax + 1.0f));
-                while (f < fmax && !tltf<FAST>(Ne, me, ((f + 1) << sh) - Oloc[a], r.m[a], 0)) f++;
-                while (f > 0 && tltf<FAST>(Ne, me, (f << sh) - Oloc[a], r.m[a], 0)) f--;
+                // p: the entry point's coordinate in voxels of the LOD.  Its
+                // error is below 2^-21 of |Oloc| + |te m| (six roundings, the
+                // quotient within 2 ulp): with a margin of 2, the floor of p
+                // is exact unless p lies that close to an integer.
+                const float fo = (float)Oloc[a], pr = te * (float)r.m[a];
+                const float p = (fo + pr) * (1.0f / (float)(1 << sh));
+                const float err = (fabsf(fo) + fabsf(pr)) * (1.0f / (float)(1 << sh)) * 0x1p-20f;
+                const float pc = fminf(fmaxf(p, -1.0f), (float)fmax + 1.0f);
+                if (!floor_if_clear(pc, err, f)) {
+                    f = (int32_t)floorf(pc);
+                    while (f < fmax && !tltf<FAST>(Ne, me, ((f + 1) << sh) - Oloc[a], r.m[a], 0)) f++;
+                    while (f > 0 && tltf<FAST>(Ne, me, (f << sh) - Oloc[a], r.m[a], 0)) f--;
+                }
             }
             F[a] = max(0, min(f, fmax));
         }
@@ -276,7 +297,7 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
                     for (int j = R; j >= n + 3; j--) {
                         const int sh = j - 1 - n;
                         const int oct = ((u0 >> sh) & 1) | (((u1 >> sh) & 1) << 1) | (((u2 >> sh) & 1) << 2);
-                        const int rk = __popc(smask[j] & ((1u << oct) - 1u));
+                        const int rk = __popc(st[j].z & ((1u << oct) - 1u));
                         cnt.rbytes += rk * ((j - 1 == n + 2) ? 8u : 4u);
                     }
                     cnt.rbytes += 1;
@@ -338,7 +359,14 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
                     const int p = __ffs(cax) - 1;
                     c0 >>= p; c1 >>= p; c2 >>= p;
                     k += p;
-                    pm8 = k >= n + 2 ? smask[k + 1] : g8;  // popped into a new parent (a node or the leaf)
+                    if (k >= n + 2) {  // popped into a new parent: a node ...
+                        const uint4 par = st[k + 1];
+                        pidx = par.x;
+                        pacc = par.y;
+                        pm8 = par.z;
+                    } else {
+                        pm8 = g8;  // ... or the leaf block
+                    }
                     break;
                 }
                 if ((pm8 >> (((uint32_t)(c0 & 1) | ((uint32_t)(c1 & 1) << 1) | ((uint32_t)(c2 & 1) << 2)) ^ r.mir)) & 1u)
@@ -489,6 +517,27 @@ __device__ __forceinline__ bool make_ray(const CamDev& C, int px, int py, RaySta
     return true;
 }
 
+// Chunk cell along axis a of the point where the ray crosses the plane (e, Ne)
+// (me, Ee: |d_e| as mantissa and exponent), exactly: cell M <= x_a < (cell+1) M,
+// clamped to the grid.  Ow: mirrored world origin numerators; t_num: Ne / |d_e|
+// in FP32.  The FP32 estimate's error is below 2^-22 of |Ow| + |t_num d_a|
+// (five roundings); with a margin of 4 its floor is used unless it lies that
+// close to a chunk plane, where the plane comparisons decide.
+template <bool FAST>
+__device__ __forceinline__ int32_t chunk_cell(const SceneDev& S, const RayState& r, const int32_t Ow[3], int a,
+                                              float t_num, int32_t Ne, int32_t me, int32_t Ee, int cs) {
+    const float fo = (float)Ow[a], pr = t_num * fabsf(r.d[a]);
+    const float q = (fo + pr) * (1.0f / (float)(1 << cs));
+    const float err = (fabsf(fo) + fabsf(pr)) * (1.0f / (float)(1 << cs)) * 0x1p-20f;
+    const float qc = fminf(fmaxf(q, -1.0f), (float)S.grid[a]);
+    int32_t cell;
+    if (floor_if_clear(qc, err, cell)) return max(0, min(cell, S.grid[a] - 1));
+    cell = max(0, min((int32_t)floorf(qc), S.grid[a] - 1));
+    while (cell + 1 < S.grid[a] && !tltf<FAST>(Ne, me, ((cell + 1) << cs) - Ow[a], r.m[a], r.E[a] - Ee)) cell++;
+    while (cell > 0 && tltf<FAST>(Ne, me, (cell << cs) - Ow[a], r.m[a], r.E[a] - Ee)) cell--;
+    return cell;
+}
+
 // ---------------------------------------------------------------------------
 // one pixel: world-grid chunk march + per-chunk DAG traversal
 // ---------------------------------------------------------------------------
@@ -536,13 +585,7 @@ __device__ __forceinline__ void trace_pixel_t(const SceneDev& S, const CamDev& C
 #pragma unroll
             for (int a = 0; a < 3; a++) {
                 if (a == e) { cc[a] = 0; continue; }
-                const float pa = (float)Ow[a] + te_num * fabsf(r.d[a]);
-                int32_t cell = (int32_t)floorf(pa * (1.0f / (float)(1 << cs)));
-                cell = max(0, min(cell, S.grid[a] - 1));
-                // exact correction: cell*M <= x_a(t_entry) < (cell+1)*M
-                while (cell + 1 < S.grid[a] && !tltf<FAST>(Ne, me, ((cell + 1) << cs) - Ow[a], r.m[a], r.E[a] - Ee)) cell++;
-                while (cell > 0 && tltf<FAST>(Ne, me, (cell << cs) - Ow[a], r.m[a], r.E[a] - Ee)) cell--;
-                cc[a] = cell;
+                cc[a] = chunk_cell<FAST>(S, r, Ow, a, te_num, Ne, me, Ee, cs);
             }
         } else {
             alive = false;
@@ -575,13 +618,7 @@ __device__ __forceinline__ void trace_pixel_t(const SceneDev& S, const CamDev& C
 #pragma unroll
                 for (int a = 0; a < 3; a++) {
                     if (a == as) continue;
-                    const float pa = (float)Ow[a] + ts_num * fabsf(r.d[a]);
-                    int32_t cell = (int32_t)floorf(pa * (1.0f / (float)(1 << cs)));
-                    cell = max(0, min(cell, S.grid[a] - 1));
-                    // exact: cell*M <= x_a(t_s) < (cell+1)*M
-                    while (cell + 1 < S.grid[a] && !tltf<FAST>(Ne, me, ((cell + 1) << cs) - Ow[a], r.m[a], r.E[a] - Ee)) cell++;
-                    while (cell > 0 && tltf<FAST>(Ne, me, (cell << cs) - Ow[a], r.m[a], r.E[a] - Ee)) cell--;
-                    cc[a] = cell;
+                    cc[a] = chunk_cell<FAST>(S, r, Ow, a, ts_num, Ne, me, Ee, cs);
                 }
             }
         }
