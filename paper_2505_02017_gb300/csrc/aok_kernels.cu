@@ -141,9 +141,10 @@ __device__ __forceinline__ int32_t beam_bound_lut(const BeamLookup& b, int px, i
 
 // 16 x 8 pixel tiles, warps of 8 x 4 pixels.  BEAM: the warp's 8 x 4 tile
 // bound from the beam pass (aok_beam.cu) restarts its rays' march past the
-// space in front of the nearest voxel they can meet.
+// space in front of the nearest voxel they can meet.  At most 72 registers:
+// 7 blocks per SM (the loop needs no more; no spills).
 template <bool COUNT, bool BEAM = false>
-__global__ void __launch_bounds__(128) cast_kernel(SceneDev S, CamDev C, const ChunkRef* __restrict__ frame,
+__global__ void __launch_bounds__(128, 7) cast_kernel(SceneDev S, CamDev C, const ChunkRef* __restrict__ frame,
                                                    uint4* __restrict__ out_hit, float* __restrict__ out_t,
                                                    uint32_t* __restrict__ counts, const BeamLookup beam) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

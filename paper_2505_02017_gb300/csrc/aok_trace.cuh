@@ -168,13 +168,12 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
     const uint32_t* __restrict__ nodes = S.nodes;
     const int R = S.mlog;
     const int n = (int)ref.lod;
-    // per interior level on the path: {node word index, DFS index of the
-    // node's first voxel, child mask} (a level is written when the path
-    // enters it, before any read); the parent of the current level's cells
-    // is also kept in registers (pidx, pacc and its mask pm8)
-    uint4 st[kMaxLevels];
-    uint32_t pidx = 0, pacc = 0;
-    uint32_t lacc = 0;  // DFS index of the current leaf block's first voxel
+    // per interior level j (3 <= j <= R) on the path: {node word index, child
+    // mask} in st[j - 3] (a level is written when the path enters it, before
+    // any read); the parent of the current level's cells is also kept in
+    // registers (pidx and its mask pm8)
+    uint2 st[kMaxLevels - 3];
+    uint32_t pidx = 0;
     int k = R;
     int32_t c0 = 0, c1 = 0, c2 = 0;
     int32_t me = 1, Ee = 0;
@@ -188,33 +187,25 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
     // (interior levels, also pushed on the stack), its leaf block's group
     // occupancy (leaf level) or its 2x2x2 group's voxel bits.  False when a
     // checked build finds a pool index out of range.
-    // The node's device layout [hdr, count, (child, prefix) x k] gives the
-    // child pointer and the summed counts of the earlier children in one
-    // 8-byte load, so each level's DFS index is accumulated on the way down.
     auto fetch = [&]() -> bool {
         if (k >= n + 2) {
-            uint32_t idx, acc;
+            uint32_t idx;
             if (k == R) {
                 idx = ref.root;
-                acc = 0;
             } else {
                 const uint32_t oct = ((uint32_t)(c0 & 1) | ((uint32_t)(c1 & 1) << 1) | ((uint32_t)(c2 & 1) << 2)) ^ r.mir;
                 const uint64_t at = (uint64_t)pidx + 2 + 2 * __popc(pm8 & ((1u << oct) - 1u));
-                if (out_of<CHECK>(at + 1, ck ? ck->n_nodes : 0, ck, 1u)) return false;
-                const uint2 cp = *reinterpret_cast<const uint2*>(nodes + at);  // even word index: 8-byte aligned
-                idx = cp.x;
-                acc = pacc + cp.y;
+                if (out_of<CHECK>(at, ck ? ck->n_nodes : 0, ck, 1u)) return false;
+                idx = nodes[at];
             }
             if (k >= n + 3) {
                 if (out_of<CHECK>((uint64_t)idx + 1, ck ? ck->n_nodes : 0, ck, 1u)) return false;
                 pm8 = nodes[idx] & 0xFFu;
-                st[k] = make_uint4(idx, acc, pm8, 0u);
+                st[k - 3] = make_uint2(idx, pm8);
                 pidx = idx;
-                pacc = acc;
                 if (COUNT) cnt.v_int++;
             } else {
                 if (out_of<CHECK>(idx, ck ? ck->n_leaves : 0, ck, 2u)) return false;
-                lacc = acc;
                 lmu = S.leaves[idx];
                 uint64_t t = lmu | (lmu >> 1);
                 t |= t >> 4;
@@ -279,46 +270,7 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
     }
     for (;;) {
         if (occ) {
-            if (k == n) {
-                hit.c[0] = c0; hit.c[1] = c1; hit.c[2] = c2;
-                hit.e = e;
-                hit.Ne = Ne;
-                // depth-first index (Sec. 3.3): the leaf block's first voxel
-                // plus the solid voxels before the hit bit
-                const uint32_t mirv = r.mir;
-                const int32_t side = (1 << (R - n)) - 1;
-                const int32_t u0 = (mirv & 1u) ? side - c0 : c0;
-                const int32_t u1 = (mirv & 2u) ? side - c1 : c1;
-                const int32_t u2 = (mirv & 4u) ? side - c2 : c2;
-                const int bit = (u0 & 3) + 4 * (u1 & 3) + 16 * (u2 & 3);
-                hit.idx = lacc + (uint32_t)__popcll(lmu & ((1ull << bit) - 1ull));
-                if (COUNT) {
-                    // the paper-format resolve: the counts of the earlier siblings on the path
-                    for (int j = R; j >= n + 3; j--) {
-                        const int sh = j - 1 - n;
-                        const int oct = ((u0 >> sh) & 1) | (((u1 >> sh) & 1) << 1) | (((u2 >> sh) & 1) << 2);
-                        const int rk = __popc(st[j].z & ((1u << oct) - 1u));
-                        cnt.rbytes += rk * ((j - 1 == n + 2) ? 8u : 4u);
-                    }
-                    cnt.rbytes += 1;
-                }
-                if (CHECK) {
-                    // raw array: the entry; blocks: the whole block structure
-                    const uint32_t idx = hit.idx;
-                    const uint64_t end = ref.nblocks == 0
-                                             ? ref.mat_base + idx
-                                             : ref.mat_base + 4ull * (1 + ((uint64_t)idx >> 7) + 1) - 1;
-                    if (out_of<CHECK>(end, ck->n_mats, ck, 4u)) return false;
-                    if (ref.nblocks) {
-                        const uint32_t nt = *reinterpret_cast<const uint32_t*>(S.mats + ref.mat_base);
-                        if (out_of<CHECK>(ref.mat_base + 4ull * (1 + nt + ref.nblocks) + ref.nblocks - 1, ck->n_mats,
-                                          ck, 4u) ||
-                            out_of<CHECK>(idx >> 7, nt, ck, 4u))
-                            return false;
-                    }
-                }
-                return true;
-            }
+            if (k == n) break;  // the hit: its index is resolved after the loop
             if (!fetch()) return false;
             // child of cell (k, c) holding the entry point: compare t_entry with the mid planes
             const int kk = k - 1;
@@ -360,10 +312,9 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
                     c0 >>= p; c1 >>= p; c2 >>= p;
                     k += p;
                     if (k >= n + 2) {  // popped into a new parent: a node ...
-                        const uint4 par = st[k + 1];
+                        const uint2 par = st[k - 2];
                         pidx = par.x;
-                        pacc = par.y;
-                        pm8 = par.z;
+                        pm8 = par.y;
                     } else {
                         pm8 = g8;  // ... or the leaf block
                     }
@@ -377,6 +328,45 @@ __device__ __forceinline__ bool trace_chunk(const SceneDev& S, const ChunkRef& r
         // occupancy of cell (k, c) in its parent
         occ = (pm8 >> (((uint32_t)(c0 & 1) | ((uint32_t)(c1 & 1) << 1) | ((uint32_t)(c2 & 1) << 2)) ^ r.mir)) & 1u;
     }
+    // The hit (k == n): the lanes that hit in this chunk resolve together.
+    hit.c[0] = c0; hit.c[1] = c1; hit.c[2] = c2;
+    hit.e = e;
+    hit.Ne = Ne;
+    // depth-first index (Sec. 3.3): per level of the path the summed counts
+    // of the earlier children (the prefix word beside the child pointer in the
+    // device layout), then the solid voxels before the hit bit in its leaf
+    const int32_t side = (1 << (R - n)) - 1;
+    const int32_t u0 = (r.mir & 1u) ? side - c0 : c0;
+    const int32_t u1 = (r.mir & 2u) ? side - c1 : c1;
+    const int32_t u2 = (r.mir & 4u) ? side - c2 : c2;
+    uint32_t idx = 0;
+    for (int j = R; j >= n + 3; j--) {
+        const int sh = j - 1 - n;
+        const int oct = ((u0 >> sh) & 1) | (((u1 >> sh) & 1) << 1) | (((u2 >> sh) & 1) << 2);
+        const uint2 sj = st[j - 3];
+        const int rk = __popc(sj.y & ((1u << oct) - 1u));
+        const uint64_t at = (uint64_t)sj.x + 3 + 2 * rk;
+        if (out_of<CHECK>(at, ck ? ck->n_nodes : 0, ck, 1u)) return false;
+        idx += nodes[at];
+        if (COUNT) cnt.rbytes += rk * ((j - 1 == n + 2) ? 8u : 4u);  // the paper-format resolve
+    }
+    const int bit = (u0 & 3) + 4 * (u1 & 3) + 16 * (u2 & 3);
+    idx += (uint32_t)__popcll(lmu & ((1ull << bit) - 1ull));
+    if (COUNT) cnt.rbytes += 1;
+    hit.idx = idx;
+    if (CHECK) {
+        // raw array: the entry; blocks: the whole block structure
+        const uint64_t end =
+            ref.nblocks == 0 ? ref.mat_base + idx : ref.mat_base + 4ull * (1 + ((uint64_t)idx >> 7) + 1) - 1;
+        if (out_of<CHECK>(end, ck->n_mats, ck, 4u)) return false;
+        if (ref.nblocks) {
+            const uint32_t nt = *reinterpret_cast<const uint32_t*>(S.mats + ref.mat_base);
+            if (out_of<CHECK>(ref.mat_base + 4ull * (1 + nt + ref.nblocks) + ref.nblocks - 1, ck->n_mats, ck, 4u) ||
+                out_of<CHECK>(idx >> 7, nt, ck, 4u))
+                return false;
+        }
+    }
+    return true;
 }
 
 #pragma nv_diag_default 549
@@ -623,6 +613,7 @@ __device__ __forceinline__ void trace_pixel_t(const SceneDev& S, const CamDev& C
             }
         }
     }
+    const float dn = ray_norm(r);
     float inv[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) inv[a] = 1.0f / r.d[a];
@@ -638,7 +629,7 @@ __device__ __forceinline__ void trace_pixel_t(const SceneDev& S, const CamDev& C
         ref = frame[(size_t)u[0] + (size_t)S.grid[0] * ((size_t)u[1] + (size_t)S.grid[1] * u[2])];
         if (S.view_dist > 0.0f && e < 3) {
             const float tent = (float)Ne / (4096.0f * fabsf(r.d[e]));
-            if (tent * ray_norm(r) > S.view_dist * 1.00001f + 1.0f) break;
+            if (tent * dn > S.view_dist * 1.00001f + 1.0f) break;
         }
         if (ref.root != kNone) {
             // skip chunks whose solid-voxel AABB (grown by 1/16 voxel) the ray misses
@@ -680,7 +671,7 @@ __device__ __forceinline__ void trace_pixel_t(const SceneDev& S, const CamDev& C
     }
     if (found) {
         lowest_entry_face<FAST>(r, Oloc, (int)ref.lod, hit);
-        found = emit_hit(S, r, ref, u, hit, ray_norm(r), out_hit, out_t, pix);
+        found = emit_hit(S, r, ref, u, hit, dn, out_hit, out_t, pix);
     }
     if (!found) emit_miss(out_hit, out_t, pix);
     if (COUNT) {
