@@ -262,6 +262,53 @@ def bench_batched(aok, ctx, scene, world, flush, reps=5):
                           "best_ms": tune_ms, "tune_s": round(tune_s, 2)}}
 
 
+def bench_walk(aok, ctx, scene, world, flush, n_poses=120):
+    """The benchmark frame's metric along a moving camera: a path of poses at
+    walker height through the city (1920x1080, tau = 1 px).  Device time: per
+    pose the selection, beam pass and cast on one stream, L2 flushed before
+    each pose.  End to end: the same poses through aok_render_host_async, every
+    frame copied to pinned host memory."""
+    import torch
+    cams = sg.path_cameras(world, 106, n_poses, W, H, n_waypoints=6, span=2500.0, z_lo=64.0, z_hi=400.0,
+                           pitch=(-30.0, 5.0))
+    stream = torch.cuda.current_stream()
+    hit, t = aok.alloc_frame(W, H)
+    for cam in cams[:3]:
+        aok.render(ctx, scene, cam, TAU, hit, t)
+    torch.cuda.synchronize()
+    ms = []
+    for cam in cams:
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        aok.select_chunks(ctx, scene, cam, TAU, stream=stream)
+        if BEAM_DEFAULT:
+            aok.beam_selected(ctx, scene, cam, stream=stream)
+        aok.cast_selected(ctx, scene, cam, hit, t, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    nbuf = 3
+    hh = [torch.empty((H, W, 4), dtype=torch.int32, pin_memory=True) for _ in range(nbuf)]
+    th = [torch.empty((H, W), dtype=torch.float32, pin_memory=True) for _ in range(nbuf)]
+    t0 = time.perf_counter()
+    tickets = []
+    for k, cam in enumerate(cams):
+        if len(tickets) >= nbuf:
+            aok.host_frame_wait(ctx, tickets[-nbuf])
+        tickets.append(aok.render_host_async(ctx, scene, cam, TAU, hh[k % nbuf], th[k % nbuf]))
+    for tk in tickets[-nbuf:]:
+        aok.host_frame_wait(ctx, tk)
+    e2e_s = time.perf_counter() - t0
+    srt = sorted(ms)
+    return {"workload": f"city4096, {n_poses}-pose walker path (seed 106, 6 waypoints over 2500 voxels, "
+                        "64-400 voxels above the terrain at the waypoints), 1920x1080, tau = 1 px",
+            "rays_per_s": W * H * len(ms) / (sum(ms) / 1e3), "frame_ms_median": srt[len(srt) // 2],
+            "frame_ms_p99": srt[int(len(srt) * 0.99) - 1], "e2e_rays_per_s": W * H * len(cams) / e2e_s,
+            "e2e_api": "aok_render_host_async (3 frames in flight)"}
+
+
 def bench_served(aok, ctx, base_scene, threads, rates=(200, 500, 1000, 2000, 4000), n_req=1000, n_warm=100):
     """Poisson arrivals over 4 resident worlds (two 4096^3 cities, two 2048^3),
     each request a random walker pose, a resolution from the five sizes and a
@@ -736,6 +783,7 @@ def main():
     ap.add_argument("--no-tiles", action="store_true")
     ap.add_argument("--no-color", action="store_true")
     ap.add_argument("--no-beam-ab", action="store_true")
+    ap.add_argument("--no-walk", action="store_true")
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--cpu-scaling", action="store_true",
                     help="print the oracle's 1-thread / all-thread rays/s for three workloads and exit")
@@ -903,6 +951,8 @@ def main():
     }
     if not args.no_beam_ab:
         out["beam_pass"]["on_off"] = bench_beam(aok, ctx, scene, world, flush)
+    if not args.no_walk:
+        out["walk"] = bench_walk(aok, ctx, scene, world, flush)
     if not args.no_tiles:
         out["tile_pipeline"] = bench_tiles(aok, ctx, scene, world, flush)
     if not args.no_color:
@@ -922,6 +972,30 @@ def main():
             out["cpu_baseline"] = cpu_oracle_sample(world, cam, gpu_frame=(hit.cpu().numpy(), t.cpu().numpy()))
         except Exception as ex:  # pragma: no cover
             out["cpu_baseline"] = {"error": str(ex)}
+    # the records a reader of the line's tail needs, last
+    summ = {"device_rays_per_s": out["value"], "e2e_rays_per_s": out["e2e"]["value"],
+            "cast_ms": out["roofline"]["cast_ms"], "roofline_frac": out["roofline"]["frac"]}
+    if "walk" in out:
+        summ["walk_rays_per_s"] = out["walk"]["rays_per_s"]
+        summ["walk_e2e_rays_per_s"] = out["walk"]["e2e_rays_per_s"]
+    if "batched" in out:
+        b = out["batched"]
+        summ["batched"] = {"rays_per_s": b["batched_rays_per_s"], "plain_rays_per_s": b["plain_rays_per_s"],
+                           "speedup": b["speedup"], "graph": b["graph"], "identical": b["identical_outputs"]}
+    if "served" in out:
+        summ["served"] = {str(r["arrival_req_per_s"]): {"req_per_s": round(r["served"]["req_per_s"], 1),
+                                                        "p50_ms": round(r["served"]["p50_ms"], 3),
+                                                        "p99_ms": round(r["served"]["p99_ms"], 3),
+                                                        "serial_p99_ms": round(r["serial_plain"]["p99_ms"], 3)}
+                          for r in out["served"]["rates"]}
+    if "open_world" in out:
+        summ["open_world_frame_ms_median"] = out["open_world"]["frame_ms_median"]
+        summ["open_world_async_installed_median"] = out["open_world_async"]["planned_lods_installed_frac_median"]
+        summ["open_world_async_file_installed_median"] = \
+            out["open_world_async_file"]["planned_lods_installed_frac_median"]
+    if "cpu_baseline" in out and "value" in out["cpu_baseline"]:
+        summ["cpu_oracle_rays_per_s"] = out["cpu_baseline"]["value"]
+    out["summary"] = summ
     if rank == 0:
         print(json.dumps(out), flush=True)
     scene.destroy()
