@@ -150,14 +150,27 @@ void build_dag(const BitGrid& g, MatFn mat, Blob& out) {
     // 4x4x4 leaf masks, bit x + 4y + 16z, block index bx + nb*(by + nb*bz)
     std::vector<uint64_t> lm(nblk, 0);
     size_t nonempty = 0;
+    // per row of blocks (by, bz) and 64-bit word of x: the 16 words of its 4 x 4
+    // voxel rows; all zero = 16 (or r / 4) empty blocks at once
+    const int bpw = std::min(16, nb);  // blocks per word
     for (int bz = 0; bz < nb; bz++)
         for (int by = 0; by < nb; by++)
-            for (int bx = 0; bx < nb; bx++) {
-                uint64_t m = 0;
+            for (int wx = 0; wx < g.w64; wx++) {
+                uint64_t rw[16], any = 0;
                 for (int z = 0; z < 4; z++)
-                    for (int y = 0; y < 4; y++) m |= g.row_bits(4 * bx, 4 * by + y, 4 * bz + z, 4) << (4 * y + 16 * z);
-                lm[(size_t)bx + (size_t)nb * ((size_t)by + (size_t)nb * bz)] = m;
-                nonempty += m != 0;
+                    for (int y = 0; y < 4; y++) {
+                        rw[4 * z + y] = g.w[(size_t)wx + (size_t)g.w64 * ((size_t)(4 * by + y) + (size_t)r * (4 * bz + z))];
+                        any |= rw[4 * z + y];
+                    }
+                if (!any) continue;
+                for (int j = 0; j < bpw; j++) {
+                    uint64_t m = 0;
+                    for (int q = 0; q < 16; q++) m |= ((rw[q] >> (4 * j)) & 0xFull) << (4 * q);
+                    if (!m) continue;
+                    const int bx = wx * 16 + j;
+                    lm[(size_t)bx + (size_t)nb * ((size_t)by + (size_t)nb * bz)] = m;
+                    nonempty++;
+                }
             }
     if (!nonempty) {  // empty chunk
         out = Blob();
