@@ -85,6 +85,9 @@ def lib() -> ctypes.CDLL:
         L.sg_fill_bits.restype = u64
         L.sg_fill_bits.argtypes = [vp, i32, i32, i32, i32, i32, i32, vp]
         L.sg_materials.argtypes = [vp, vp, ctypes.c_size_t, vp]
+        L.sg_materials_block4.argtypes = [vp, i32, i32, i32, u64, vp]
+        L.sg_fill_bits_z.argtypes = [vp, i32, i32, i32, i32, i32, i32, vp, vp]
+        L.sg_fill_bits_z.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -185,6 +188,24 @@ class World:
         out = np.empty(len(xyz), dtype=np.uint8)
         lib().sg_materials(self._h, xyz.ctypes.data, len(xyz), out.ctypes.data)
         return out
+
+    def materials_block4(self, x0, y0, z0, mask: int, out: np.ndarray) -> np.ndarray:
+        """Materials of the set bits of a 4x4x4 block mask written into out[64]."""
+        assert out.dtype == np.uint8 and out.size == 64 and out.flags.c_contiguous
+        lib().sg_materials_block4(self._h, x0, y0, z0, mask, out.ctypes.data)
+        return out
+
+    def fill_bits_z(self, x0, y0, z0, nx, ny, nz, out: np.ndarray):
+        """Bit-packed occupancy into a zeroed uint64 buffer; returns (any, (z_lo, z_hi))."""
+        assert out.dtype == np.uint64 and out.flags.c_contiguous
+        zr = np.zeros(2, np.int32)
+        r = lib().sg_fill_bits_z(self._h, x0, y0, z0, nx, ny, nz, out.ctypes.data, zr.ctypes.data)
+        return int(r), (int(zr[0]), int(zr[1]))
+
+    def fill_bits(self, x0, y0, z0, nx, ny, nz) -> tuple[int, np.ndarray]:
+        out = np.empty(nx // 64 * ny * nz, np.uint64)
+        n = lib().sg_fill_bits(self._h, x0, y0, z0, nx, ny, nz, out.ctypes.data)
+        return int(n), out
 
 
 # ---------------------------------------------------------------------------

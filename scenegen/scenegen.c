@@ -76,7 +76,8 @@ void sg_heights(const sg_scene* s, int32_t x0, int32_t y0, int32_t nx, int32_t n
     int32_t* iy = (int32_t*)malloc((size_t)ny * sizeof(int32_t));
     int64_t* sx = (int64_t*)malloc((size_t)nx * sizeof(int64_t));
     int64_t* sy = (int64_t*)malloc((size_t)ny * sizeof(int64_t));
-    int64_t wsum = 0;
+    int64_t* ta = (int64_t*)malloc((size_t)nx * sizeof(int64_t));
+    int64_t* tb = (int64_t*)malloc((size_t)nx * sizeof(int64_t));
     for (int32_t o = 0; o < p->octaves; o++) {
         int32_t P = p->period0 >> o;
         if (P < 1) P = 1;
@@ -96,27 +97,52 @@ void sg_heights(const sg_scene* s, int32_t x0, int32_t y0, int32_t nx, int32_t n
         for (int32_t j = 0; j < cj; j++)
             for (int32_t i = 0; i < ci; i++) lat[(size_t)j * ci + i] = lattice(s, i0 + i, j0 + j, o);
         for (int32_t y = 0; y < ny; y++) {
-            const int64_t* r0 = lat + (size_t)(iy[y] - j0) * ci;
-            const int64_t* r1 = r0 + ci;
+            if (y == 0 || iy[y] != iy[y - 1]) {
+                /* the x interpolation of this lattice row pair, shared by the rows up to the next pair */
+                const int64_t* r0 = lat + (size_t)(iy[y] - j0) * ci;
+                const int64_t* r1 = r0 + ci;
+                for (int32_t x = 0; x < nx; x++) {
+                    const int32_t c = ix[x] - i0;
+                    const int64_t wx = sx[x];
+                    ta[x] = (r0[c] * (65536 - wx) + r0[c + 1] * wx) >> 16;
+                    tb[x] = (r1[c] * (65536 - wx) + r1[c + 1] * wx) >> 16;
+                }
+            }
             const int64_t wy = sy[y];
             int64_t* a = acc + (size_t)y * nx;
-            for (int32_t x = 0; x < nx; x++) {
-                const int32_t c = ix[x] - i0;
-                const int64_t wx = sx[x];
-                const int64_t ta = (r0[c] * (65536 - wx) + r0[c + 1] * wx) >> 16;
-                const int64_t tb = (r1[c] * (65536 - wx) + r1[c + 1] * wx) >> 16;
-                const int64_t n = (ta * (65536 - wy) + tb * wy) >> 16;
-                a[x] += n << (K - o);
-            }
+            for (int32_t x = 0; x < nx; x++) a[x] += ((ta[x] * (65536 - wy) + tb[x] * wy) >> 16) << (K - o);
         }
         free(lat);
-        wsum += (int64_t)1 << (K - o);
     }
-    for (size_t k = 0; k < (size_t)nx * ny; k++) {
-        const int64_t nq = acc[k] / wsum;
-        out[k] = p->h_min + (int32_t)(((int64_t)(p->h_max - p->h_min) * nq) >> 16);
+    /* the weight sum is 2^octaves - 1; a literal divisor per case lets the
+     * compiler divide by multiplication (the same quotients) */
+    const size_t n = (size_t)nx * ny;
+    const int64_t span = (int64_t)(p->h_max - p->h_min);
+#define SG_HEIGHTS_OUT(d) \
+    for (size_t k = 0; k < n; k++) out[k] = p->h_min + (int32_t)((span * (acc[k] / (d))) >> 16); \
+    break;
+    switch (p->octaves) {
+    case 1: SG_HEIGHTS_OUT(1)
+    case 2: SG_HEIGHTS_OUT(3)
+    case 3: SG_HEIGHTS_OUT(7)
+    case 4: SG_HEIGHTS_OUT(15)
+    case 5: SG_HEIGHTS_OUT(31)
+    case 6: SG_HEIGHTS_OUT(63)
+    case 7: SG_HEIGHTS_OUT(127)
+    case 8: SG_HEIGHTS_OUT(255)
+    case 9: SG_HEIGHTS_OUT(511)
+    case 10: SG_HEIGHTS_OUT(1023)
+    case 11: SG_HEIGHTS_OUT(2047)
+    case 12: SG_HEIGHTS_OUT(4095)
+    case 13: SG_HEIGHTS_OUT(8191)
+    case 14: SG_HEIGHTS_OUT(16383)
+    case 15: SG_HEIGHTS_OUT(32767)
+    default: SG_HEIGHTS_OUT(65535)
     }
+#undef SG_HEIGHTS_OUT
     free(acc);
+    free(ta);
+    free(tb);
     free(ix);
     free(iy);
     free(sx);
@@ -241,7 +267,7 @@ int sg_solid(const sg_scene* s, int32_t x, int32_t y, int32_t z) {
     return 0;
 }
 
-uint8_t sg_material(const sg_scene* s, int32_t x, int32_t y, int32_t z) {
+static inline uint8_t material_at(const sg_scene* s, int32_t x, int32_t y, int32_t z) {
     uint64_t key = ((uint64_t)(uint32_t)x & 0x1FFFFFULL) | (((uint64_t)(uint32_t)y & 0x1FFFFFULL) << 21) |
                    (((uint64_t)(uint32_t)z & 0x1FFFFFULL) << 42);
     const uint64_t h = sg_mix64(key ^ s->mat_seed);
@@ -250,6 +276,16 @@ uint8_t sg_material(const sg_scene* s, int32_t x, int32_t y, int32_t z) {
     const uint32_t stratum = (uint32_t)z >> 3;
     const uint32_t cell = (((uint32_t)x >> 6) * 7u + ((uint32_t)y >> 6) * 13u) & 31u;
     return (uint8_t)((stratum * 5u + cell * 3u + (uint32_t)(s->mat_seed & 63u)) & 0xFFu);
+}
+
+uint8_t sg_material(const sg_scene* s, int32_t x, int32_t y, int32_t z) { return material_at(s, x, y, z); }
+
+void sg_materials_block4(const sg_scene* s, int32_t x0, int32_t y0, int32_t z0, uint64_t mask, uint8_t* out) {
+    while (mask) {
+        const int b = __builtin_ctzll(mask);
+        mask &= mask - 1;
+        out[b] = material_at(s, x0 + (b & 3), y0 + ((b >> 2) & 3), z0 + (b >> 4));
+    }
 }
 
 void sg_materials(const sg_scene* s, const int32_t* xyz, size_t n, uint8_t* out) {
@@ -261,7 +297,14 @@ void sg_materials(const sg_scene* s, const int32_t* xyz, size_t n, uint8_t* out)
 typedef struct {
     uint8_t* bytes; uint64_t* bits;
     int32_t x0, y0, z0, nx, ny, nz;
+    int32_t zlo, zhi;  /* world z range of the rows written (zlo >= zhi: none) */
 } region_t;
+
+static inline void touch_z(region_t* r, int32_t z0, int32_t z1) {
+    if (z0 >= z1) return;
+    if (z0 < r->zlo) r->zlo = z0;
+    if (z1 > r->zhi) r->zhi = z1;
+}
 
 static inline void set_voxel(region_t* r, int32_t x, int32_t y, int32_t z) {
     /* region-local coordinates, already clipped */
@@ -283,24 +326,58 @@ static void fill_region(const sg_scene* s, region_t* r) {
     int32_t hx = ax1 - ax0 + 2, hy = ay1 - ay0 + 2;
     int32_t* h = (int32_t*)malloc((size_t)hx * hy * sizeof(int32_t));
     sg_heights(s, ax0 - 1, ay0 - 1, hx, hy, h);
+    /* per row y and 64-column word of the bit layout: each column's first and
+     * one-past-last solid z are marked in ev[] and a running XOR over z gives
+     * the word of every row (bytes: one voxel at a time) */
+    uint64_t* ev = r->bits ? (uint64_t*)calloc((size_t)(az1 - az0 + 1), sizeof(uint64_t)) : NULL;
+    const int32_t w64 = r->nx >> 6;
     for (int32_t y = ay0; y < ay1; y++) {
-        for (int32_t x = ax0; x < ax1; x++) {
-            size_t c = (size_t)(y - ay0 + 1) * hx + (size_t)(x - ax0 + 1);
-            int32_t top = h[c];
-            int32_t lo = 0;
-            if (p->crust > 0) {
-                int32_t m = top;
-                if (h[c - 1] < m) m = h[c - 1];
-                if (h[c + 1] < m) m = h[c + 1];
-                if (h[c - hx] < m) m = h[c - hx];
-                if (h[c + hx] < m) m = h[c + hx];
-                lo = m - p->crust;
-                if (lo < 0) lo = 0;
+        int32_t x = ax0;
+        while (x < ax1) {
+            /* columns [x, xe): one word of the bit layout */
+            const int32_t xe0 = r->x0 + (((x - r->x0) >> 6) + 1) * 64;
+            const int32_t xe = r->bits && xe0 < ax1 ? xe0 : ax1;
+            int32_t zmn = az1, zmx = az0;
+            for (; x < xe; x++) {
+                size_t c = (size_t)(y - ay0 + 1) * hx + (size_t)(x - ax0 + 1);
+                int32_t top = h[c];
+                int32_t lo = 0;
+                if (p->crust > 0) {
+                    int32_t m = top;
+                    if (h[c - 1] < m) m = h[c - 1];
+                    if (h[c + 1] < m) m = h[c + 1];
+                    if (h[c - hx] < m) m = h[c - hx];
+                    if (h[c + hx] < m) m = h[c + hx];
+                    lo = m - p->crust;
+                    if (lo < 0) lo = 0;
+                }
+                int32_t z0 = lo > az0 ? lo : az0, z1 = top < az1 ? top : az1;
+                if (z0 >= z1) continue;
+                touch_z(r, z0, z1);
+                if (!r->bits) {
+                    for (int32_t z = z0; z < z1; z++) set_voxel(r, x - r->x0, y - r->y0, z - r->z0);
+                    continue;
+                }
+                const uint64_t bit = 1ULL << ((x - r->x0) & 63);
+                ev[z0 - az0] ^= bit;
+                ev[z1 - az0] ^= bit;
+                if (z0 < zmn) zmn = z0;
+                if (z1 > zmx) zmx = z1;
             }
-            int32_t z0 = lo > az0 ? lo : az0, z1 = top < az1 ? top : az1;
-            for (int32_t z = z0; z < z1; z++) set_voxel(r, x - r->x0, y - r->y0, z - r->z0);
+            if (zmn >= zmx) continue;
+            /* x - 1 is the word's last column */
+            uint64_t* col = r->bits + (size_t)((x - 1 - r->x0) >> 6) + (size_t)w64 * (size_t)(y - r->y0);
+            const size_t zstride = (size_t)w64 * (size_t)r->ny;
+            uint64_t cur = 0;
+            for (int32_t z = zmn; z < zmx; z++) {
+                cur ^= ev[z - az0];
+                ev[z - az0] = 0;
+                col[zstride * (size_t)(z - r->z0)] |= cur;
+            }
+            ev[zmx - az0] = 0;
         }
     }
+    free(ev);
     free(h);
     /* boxes: visit each box overlapping the region once */
     int32_t bi0 = ax0 / BIN, bi1 = (ax1 - 1) / BIN, bj0 = ay0 / BIN, bj1 = (ay1 - 1) / BIN;
@@ -322,11 +399,18 @@ static void fill_region(const sg_scene* s, region_t* r) {
                         int shell_row = !b->hollow || z == b->z0 || z == b->z0 + b->sz - 1 ||
                                         y == b->y0 || y == b->y0 + b->sy - 1;
                         if (shell_row) {
+                            if (x0 < x1) touch_z(r, z, z + 1);
                             for (int32_t x = x0; x < x1; x++) set_voxel(r, x - r->x0, y - r->y0, z - r->z0);
                         } else {
-                            if (b->x0 >= x0 && b->x0 < x1) set_voxel(r, b->x0 - r->x0, y - r->y0, z - r->z0);
                             int32_t xe = b->x0 + b->sx - 1;
-                            if (xe >= x0 && xe < x1) set_voxel(r, xe - r->x0, y - r->y0, z - r->z0);
+                            if (b->x0 >= x0 && b->x0 < x1) {
+                                touch_z(r, z, z + 1);
+                                set_voxel(r, b->x0 - r->x0, y - r->y0, z - r->z0);
+                            }
+                            if (xe >= x0 && xe < x1) {
+                                touch_z(r, z, z + 1);
+                                set_voxel(r, xe - r->x0, y - r->y0, z - r->z0);
+                            }
                         }
                     }
             }
@@ -337,7 +421,7 @@ uint64_t sg_fill_bytes(const sg_scene* s, int32_t x0, int32_t y0, int32_t z0,
                        int32_t nx, int32_t ny, int32_t nz, uint8_t* out) {
     size_t n = (size_t)nx * ny * nz;
     memset(out, 0, n);
-    region_t r = { out, NULL, x0, y0, z0, nx, ny, nz };
+    region_t r = { out, NULL, x0, y0, z0, nx, ny, nz, 0, 0 };
     fill_region(s, &r);
     uint64_t cnt = 0;
     for (size_t i = 0; i < n; i++) cnt += out[i];
@@ -349,9 +433,21 @@ uint64_t sg_fill_bits(const sg_scene* s, int32_t x0, int32_t y0, int32_t z0,
     if (nx % 64) return 0;
     size_t nw = (size_t)(nx / 64) * ny * nz;
     memset(out, 0, nw * sizeof(uint64_t));
-    region_t r = { NULL, out, x0, y0, z0, nx, ny, nz };
+    region_t r = { NULL, out, x0, y0, z0, nx, ny, nz, 0, 0 };
     fill_region(s, &r);
     uint64_t cnt = 0;
     for (size_t i = 0; i < nw; i++) cnt += (uint64_t)__builtin_popcountll(out[i]);
     return cnt;
+}
+
+int sg_fill_bits_z(const sg_scene* s, int32_t x0, int32_t y0, int32_t z0,
+                   int32_t nx, int32_t ny, int32_t nz, uint64_t* out, int32_t* zr) {
+    zr[0] = zr[1] = 0;
+    if (nx % 64) return -1;
+    region_t r = { NULL, out, x0, y0, z0, nx, ny, nz, 0x7FFFFFFF, -0x7FFFFFFF };
+    fill_region(s, &r);
+    if (r.zlo >= r.zhi) return 0;
+    zr[0] = r.zlo - z0;
+    zr[1] = r.zhi - z0;
+    return 1;
 }

@@ -94,6 +94,19 @@ uint64_t sg_fill_bits(const sg_scene* s, int32_t x0, int32_t y0, int32_t z0,
 
 /* Materials of the listed voxels: out[i] = material(xyz[3i], xyz[3i+1], xyz[3i+2]). */
 void sg_materials(const sg_scene* s, const int32_t* xyz, size_t n, uint8_t* out);
+/* Materials of the solid voxels of one 4x4x4 block with corner (x0, y0, z0):
+ * out[b] = material(x0 + (b & 3), y0 + ((b >> 2) & 3), z0 + (b >> 4)) for every
+ * set bit b of `mask`; the other entries of out[64] are left as they are. */
+void sg_materials_block4(const sg_scene* s, int32_t x0, int32_t y0, int32_t z0, uint64_t mask, uint8_t* out);
+
+/* sg_fill_bits into a buffer the caller has zeroed (nothing is cleared here),
+ * without the count: returns 1 if any voxel of the region is solid, else 0.
+ * zr[0], zr[1] (region-local z) are the lowest z holding a solid voxel and one
+ * past the highest, so every row outside [zr[0], zr[1]) is left untouched
+ * (zr = {0, 0} when nothing is solid).  Returns -1 (nothing written) unless nx
+ * is a multiple of 64. */
+int sg_fill_bits_z(const sg_scene* s, int32_t x0, int32_t y0, int32_t z0,
+                   int32_t nx, int32_t ny, int32_t nz, uint64_t* out, int32_t* zr);
 
 #ifdef __cplusplus
 }
