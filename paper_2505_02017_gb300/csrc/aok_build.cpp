@@ -3,39 +3,28 @@
 // subtree leaf counts and a depth-first material array, in the blob format
 // of aok.h.  Input voxels come from scenegen; chunks are built in parallel.
 //
-// Layout choices (not fixed by the paper): occupancy is bit-packed (x
-// fastest); identical subtrees are merged by hash-consing per level; the
-// final node pool is laid out breadth-first from the root, so a chunk's
-// upper levels are contiguous, and leaves follow in first-reference order.
+// Layout choices (not fixed by the paper): each LOD is held as 64-bit masks
+// of 4x4x4 blocks over the z slab that holds solid voxels (the generator's
+// bit rows are regrouped once); identical subtrees are merged by hash-consing
+// per level; the final node pool is laid out breadth-first from the root, so
+// a chunk's upper levels are contiguous, and leaves follow in first-reference
+// order.
 #include <algorithm>
 #include <atomic>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <list>
+#include <memory>
+#include <mutex>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/aok.h"
 #include "../../scenegen/scenegen.h"
 
 namespace {
-
-// ---- bit grid: side r, rows of w64 = ceil(r/64) words, row index y + r*z ----
-struct BitGrid {
-    int r = 0, w64 = 0;
-    std::vector<uint64_t> w;
-    void init(int side) {
-        r = side;
-        w64 = (side + 63) / 64;
-        w.assign((size_t)w64 * side * side, 0);
-    }
-    inline bool get(int x, int y, int z) const {
-        return (w[(size_t)(x >> 6) + (size_t)w64 * ((size_t)y + (size_t)r * z)] >> (x & 63)) & 1;
-    }
-    inline uint64_t row_bits(int x, int y, int z, int n) const {  // n <= 4 bits from x (x aligned to n)
-        return (w[(size_t)(x >> 6) + (size_t)w64 * ((size_t)y + (size_t)r * z)] >> (x & 63)) & ((1ull << n) - 1);
-    }
-};
 
 inline uint64_t mix64(uint64_t z) {
     z = (z ^ (z >> 33)) * 0xff51afd7ed558ccdull;
@@ -141,74 +130,150 @@ struct Blob {
 
 constexpr uint32_t NONE = 0xFFFFFFFFu;
 
-// Build the DAG of one dense LOD grid (bits, side r); mat(x, y, z) gives the
-// material of a solid voxel (LOD-local coordinates).
-template <class MatFn>
-void build_dag(const BitGrid& g, MatFn mat, Blob& out) {
-    const int r = g.r, nb = r / 4;
-    const size_t nblk = (size_t)nb * nb * nb;
-    // 4x4x4 leaf masks, bit x + 4y + 16z, block index bx + nb*(by + nb*bz)
-    std::vector<uint64_t> lm(nblk, 0);
-    size_t nonempty = 0;
-    // per row of blocks (by, bz) and 64-bit word of x: the 16 words of its 4 x 4
-    // voxel rows; all zero = 16 (or r / 4) empty blocks at once
-    const int bpw = std::min(16, nb);  // blocks per word
-    for (int bz = 0; bz < nb; bz++)
+// ---- one LOD of a chunk region as 4x4x4 blocks ----
+// Occupancy per block (bit x + 4y + 16z); only the slab of block layers
+// [bz0, bz1) that holds solid voxels is stored, block (bx, by, bz) at
+// index bx + nb*(by + nb*(bz - bz0)).  Aggregated LODs keep the materials of
+// each non-empty block in a 64-byte slot (entry = bit); LOD 0 materials come
+// from the generator.
+struct Blocks {
+    int r = 0, nb = 0, bz0 = 0, bz1 = 0;
+    std::vector<uint64_t> m;
+    std::vector<uint32_t> slot;  // material slot per block (NONE: empty), LOD >= 1 only
+    std::vector<uint8_t> mat;    // 64 bytes per slot
+    size_t index(int bx, int by, int bz) const {
+        return (size_t)bx + (size_t)nb * ((size_t)by + (size_t)nb * (size_t)(bz - bz0));
+    }
+    uint64_t mask(int bx, int by, int bz) const { return bz < bz0 || bz >= bz1 ? 0 : m[index(bx, by, bz)]; }
+    void init(int side, int z0, int z1, bool slots) {
+        r = side;
+        nb = side / 4;
+        bz0 = z0;
+        bz1 = std::max(z0, z1);
+        const size_t n = (size_t)nb * nb * (size_t)(bz1 - bz0);
+        m.assign(n, 0);
+        if (slots) slot.assign(n, NONE);
+        else slot.clear();
+        mat.clear();
+    }
+};
+
+// x, y, z extents of the solid voxels of one block mask (bit sets 0..15 per axis)
+inline void block_extent(uint64_t m, uint32_t e[3]) {
+    uint64_t t = m | (m >> 32);
+    t |= t >> 16;
+    const uint32_t xy = (uint32_t)t & 0xFFFFu;
+    e[0] = (xy | xy >> 4 | xy >> 8 | xy >> 12) & 0xFu;
+    e[1] = (uint32_t)((xy & 0xFu) != 0) | (uint32_t)((xy & 0xF0u) != 0) << 1 | (uint32_t)((xy & 0xF00u) != 0) << 2 |
+           (uint32_t)((xy & 0xF000u) != 0) << 3;
+    e[2] = (uint32_t)((m & 0xFFFFull) != 0) | (uint32_t)(((m >> 16) & 0xFFFFull) != 0) << 1 |
+           (uint32_t)(((m >> 32) & 0xFFFFull) != 0) << 2 | (uint32_t)((m >> 48) != 0) << 3;
+}
+
+// Per-thread LOD-0 bit grid (side M, rows of w64 = ceil(M/64) words, row y + M*z),
+// reused across chunks: only the rows the last fill wrote are cleared.
+struct FillScratch {
+    int r = 0, w64 = 0, dz0 = 0, dz1 = 0;  // rows of z in [dz0, dz1) may hold bits
+    std::vector<uint64_t> w;
+    uint64_t* prepare(int side) {
+        if (side != r) {
+            r = side;
+            w64 = (side + 63) / 64;
+            w.assign((size_t)w64 * side * side, 0);
+            dz0 = dz1 = 0;
+        } else if (dz1 > dz0) {
+            std::memset(w.data() + (size_t)w64 * r * dz0, 0, sizeof(uint64_t) * (size_t)w64 * r * (dz1 - dz0));
+        }
+        dz0 = dz1 = 0;
+        return w.data();
+    }
+};
+
+// Block masks of the rows [z0, z1) of a bit grid; per row of blocks (by, bz)
+// and 64-bit word of x, the 16 words of its 4 x 4 voxel rows: all zero = up to
+// 16 empty blocks at once.
+void blocks_from_bits(const FillScratch& g, int z0, int z1, Blocks& B) {
+    B.init(g.r, z0 / 4, (z1 + 3) / 4, false);
+    const int nb = B.nb, bpw = std::min(16, nb);
+    for (int bz = B.bz0; bz < B.bz1; bz++)
         for (int by = 0; by < nb; by++)
             for (int wx = 0; wx < g.w64; wx++) {
                 uint64_t rw[16], any = 0;
                 for (int z = 0; z < 4; z++)
                     for (int y = 0; y < 4; y++) {
-                        rw[4 * z + y] = g.w[(size_t)wx + (size_t)g.w64 * ((size_t)(4 * by + y) + (size_t)r * (4 * bz + z))];
+                        rw[4 * z + y] =
+                            g.w[(size_t)wx + (size_t)g.w64 * ((size_t)(4 * by + y) + (size_t)g.r * (size_t)(4 * bz + z))];
                         any |= rw[4 * z + y];
                     }
                 if (!any) continue;
                 for (int j = 0; j < bpw; j++) {
                     uint64_t m = 0;
                     for (int q = 0; q < 16; q++) m |= ((rw[q] >> (4 * j)) & 0xFull) << (4 * q);
-                    if (!m) continue;
-                    const int bx = wx * 16 + j;
-                    lm[(size_t)bx + (size_t)nb * ((size_t)by + (size_t)nb * bz)] = m;
-                    nonempty++;
+                    B.m[B.index(wx * 16 + j, by, bz)] = m;
                 }
             }
+}
+
+// Node ids of one DAG level (side n, cells x + n*(y + n*(z - z0)) for z in [z0, z1))
+struct Level {
+    int n = 0, z0 = 0, z1 = 0;
+    std::vector<uint32_t> id;
+    void init(int side, int lo, int hi) {
+        n = side;
+        z0 = lo;
+        z1 = std::max(lo, hi);
+        id.assign((size_t)n * n * (size_t)(z1 - z0), NONE);
+    }
+    uint32_t& at(int x, int y, int z) { return id[(size_t)x + (size_t)n * ((size_t)y + (size_t)n * (size_t)(z - z0))]; }
+    uint32_t get(int x, int y, int z) const {
+        return z < z0 || z >= z1 ? NONE : id[(size_t)x + (size_t)n * ((size_t)y + (size_t)n * (size_t)(z - z0))];
+    }
+};
+
+// Build the DAG of one LOD (blocks B, side r); matb(B, bx, by, bz, mask, tmp)
+// returns the materials of a block's solid voxels (entry = bit).
+template <class MatBlock>
+void build_dag(const Blocks& B, MatBlock matb, Blob& out) {
+    const int r = B.r, nb = B.nb;
+    // leaves: hash-consed ids per block
+    size_t nonempty = 0;
+    for (uint64_t m : B.m) nonempty += m != 0;
     if (!nonempty) {  // empty chunk
         out = Blob();
         return;
     }
-    // leaves: hash-consed ids per block
     LeafTable lt;
     lt.reset(nonempty);
-    std::vector<uint32_t> ids(nblk, NONE);
-    for (size_t i = 0; i < nblk; i++)
-        if (lm[i]) ids[i] = lt.intern(lm[i]);
-    // interior levels bottom-up; per level keep the id grid (for DFS emission)
     int levels = 0;
     for (int s = r; s > 4; s >>= 1) levels++;  // interior levels: node sides r .. 8
     std::vector<NodeTable> tabs(levels);
-    std::vector<std::vector<uint32_t>> grids(levels + 1);  // grids[levels] = leaf ids
-    grids[levels] = std::move(ids);
+    std::vector<Level> grids(levels + 1);  // grids[levels] = leaf ids
+    {
+        Level& lv = grids[levels];
+        lv.init(nb, B.bz0, B.bz1);
+        for (size_t i = 0; i < B.m.size(); i++)
+            if (B.m[i]) lv.id[i] = lt.intern(B.m[i]);
+    }
+    // interior levels bottom-up
     std::vector<uint64_t> cnt_leaf(lt.masks.size());
     for (size_t i = 0; i < lt.masks.size(); i++) cnt_leaf[i] = (uint64_t)__builtin_popcountll(lt.masks[i]);
-    int n = nb;
     for (int lev = levels - 1; lev >= 0; lev--) {
-        const int p = n / 2;
-        const std::vector<uint32_t>& cg = grids[lev + 1];
-        std::vector<uint32_t> pg((size_t)p * p * p, NONE);
+        const Level& cg = grids[lev + 1];
+        const int p = cg.n / 2;
+        Level& pg = grids[lev];
+        pg.init(p, cg.z0 / 2, (cg.z1 + 1) / 2);
         NodeTable& t = tabs[lev];
-        t.reset(std::max<size_t>(16, (size_t)p * p * p / 8));
+        t.reset(std::max<size_t>(16, pg.id.size() / 8));
         const bool leaf_children = lev == levels - 1;
         uint32_t key[10];
-        for (int z = 0; z < p; z++)
+        for (int z = pg.z0; z < pg.z1; z++)
             for (int y = 0; y < p; y++)
                 for (int x = 0; x < p; x++) {
                     uint32_t mask = 0;
                     int k = 2;
                     uint64_t c = 0;
                     for (int o = 0; o < 8; o++) {
-                        size_t ci = (size_t)(2 * x + (o & 1)) +
-                                    (size_t)n * ((size_t)(2 * y + ((o >> 1) & 1)) + (size_t)n * (size_t)(2 * z + (o >> 2)));
-                        uint32_t ch = cg[ci];
+                        const uint32_t ch = cg.get(2 * x + (o & 1), 2 * y + ((o >> 1) & 1), 2 * z + (o >> 2));
                         if (ch == NONE) continue;
                         mask |= 1u << o;
                         key[k++] = ch;
@@ -217,23 +282,22 @@ void build_dag(const BitGrid& g, MatFn mat, Blob& out) {
                     if (!mask) continue;
                     key[0] = mask;
                     key[1] = (uint32_t)c;
-                    pg[(size_t)x + (size_t)p * ((size_t)y + (size_t)p * z)] = t.intern(key, k);
+                    pg.at(x, y, z) = t.intern(key, k);
                 }
-        grids[lev] = std::move(pg);
-        n = p;
     }
+    const uint32_t root = grids[0].get(0, 0, 0);
     // breadth-first relayout: level by level from the root
     std::vector<std::vector<uint32_t>> newoff(levels);
     std::vector<uint32_t> leafnew(lt.masks.size(), NONE);
     out.nodes.clear();
     out.leaves.clear();
-    std::vector<uint32_t> frontier{grids[0][0]}, next;
+    std::vector<uint32_t> next;
     newoff[0].assign(tabs[0].words.size(), NONE);
-    newoff[0][grids[0][0]] = 0;
+    newoff[0][root] = 0;
     // first pass assigns offsets level by level, second pass writes words
     std::vector<std::vector<uint32_t>> order(levels);
-    order[0] = frontier;
-    uint32_t woff = 2 + __builtin_popcount(tabs[0].words[grids[0][0]]);
+    order[0] = {root};
+    uint32_t woff = 2 + __builtin_popcount(tabs[0].words[root]);
     for (int lev = 0; lev < levels; lev++) {
         next.clear();
         if (lev + 1 < levels) newoff[lev + 1].assign(tabs[lev + 1].words.size(), NONE);
@@ -270,30 +334,35 @@ void build_dag(const BitGrid& g, MatFn mat, Blob& out) {
     out.root = 0;
     // depth-first materials and AABB, walking tree positions (ascending octant, then leaf bit)
     out.mats.clear();
-    out.mats.reserve(tabs[0].words[grids[0][0] + 1]);
+    out.mats.reserve(tabs[0].words[root + 1]);
     int lo[3] = {r, r, r}, hi[3] = {-1, -1, -1};
     struct Frame { int lev, x, y, z, oct; };
     std::vector<Frame> st;
     st.push_back({0, 0, 0, 0, 0});
+    uint8_t tmp[64];
     while (!st.empty()) {
         Frame& f = st.back();
         if (f.oct == 8) { st.pop_back(); continue; }
         int o = f.oct++;
         int cx = 2 * f.x + (o & 1), cy = 2 * f.y + ((o >> 1) & 1), cz = 2 * f.z + (o >> 2);
-        int side = 1 << (f.lev + 1);  // cells per axis at level lev + 1
-        uint32_t ch = grids[f.lev + 1][(size_t)cx + (size_t)side * ((size_t)cy + (size_t)side * cz)];
+        uint32_t ch = grids[f.lev + 1].get(cx, cy, cz);
         if (ch == NONE) continue;
         if (f.lev + 1 < levels) {
             st.push_back({f.lev + 1, cx, cy, cz, 0});
         } else {
             uint64_t m = lt.masks[ch];
+            const uint8_t* mt = matb(B, cx, cy, cz, m, tmp);
+            uint32_t e[3];
+            block_extent(m, e);
+            const int c4[3] = {4 * cx, 4 * cy, 4 * cz};
+            for (int a = 0; a < 3; a++) {
+                lo[a] = std::min(lo[a], c4[a] + __builtin_ctz(e[a]));
+                hi[a] = std::max(hi[a], c4[a] + 31 - __builtin_clz(e[a]));
+            }
             while (m) {
-                int bit = __builtin_ctzll(m);
+                const int bit = __builtin_ctzll(m);
                 m &= m - 1;
-                int vx = 4 * cx + (bit & 3), vy = 4 * cy + ((bit >> 2) & 3), vz = 4 * cz + (bit >> 4);
-                out.mats.push_back(mat(vx, vy, vz));
-                lo[0] = std::min(lo[0], vx); lo[1] = std::min(lo[1], vy); lo[2] = std::min(lo[2], vz);
-                hi[0] = std::max(hi[0], vx); hi[1] = std::max(hi[1], vy); hi[2] = std::max(hi[2], vz);
+                out.mats.push_back(mt[bit]);
             }
         }
     }
@@ -301,93 +370,103 @@ void build_dag(const BitGrid& g, MatFn mat, Blob& out) {
 }
 
 // One LOD step (Sec. 3.4): a voxel exists iff >= 2 of its 8 children exist; its
-// material is the rounded mean of the existing children's (mat(x, y, z) of
-// the finer grid).
-template <class MatFn>
-void aggregate(const BitGrid& g, MatFn mat, BitGrid& g2, std::vector<uint8_t>& mat2) {
-    const int r = g.r, h = r / 2;
-    g2.init(h);
-    mat2.resize((size_t)h * h * h);
-    for (int z = 0; z < h; z++)
-        for (int y = 0; y < h; y++)
-            for (int x0 = 0; x0 < h; x0 += 32) {
-                const int xn = std::min(32, h - x0);
-                uint64_t rows[4];
-                for (int k = 0; k < 4; k++) {
-                    int yy = 2 * y + (k & 1), zz = 2 * z + (k >> 1);
-                    int xb = 2 * x0;  // 64 source bits
-                    rows[k] = g.w[(size_t)(xb >> 6) + (size_t)g.w64 * ((size_t)yy + (size_t)r * zz)] >> (xb & 63);
+// material is the rounded mean of the existing children's.  Coarse block
+// (X, Y, Z) takes its 2x2x2 voxel octants from the 8 fine blocks
+// (2X + i, 2Y + j, 2Z + k).
+template <class MatBlock>
+void aggregate(const Blocks& F, MatBlock matb, Blocks& C) {
+    C.init(F.r / 2, F.bz0 / 2, (F.bz1 + 1) / 2, true);
+    const int nc = C.nb;
+    uint8_t tmp[64], cm8[64];
+    for (int Z = C.bz0; Z < C.bz1; Z++)
+        for (int Y = 0; Y < nc; Y++)
+            for (int X = 0; X < nc; X++) {
+                uint64_t fm[8], any = 0;
+                for (int o = 0; o < 8; o++) {
+                    fm[o] = F.mask(2 * X + (o & 1), 2 * Y + ((o >> 1) & 1), 2 * Z + (o >> 2));
+                    any |= fm[o];
                 }
-                if ((rows[0] | rows[1] | rows[2] | rows[3]) == 0) continue;  // nothing below these 32 voxels
-                for (int i = 0; i < xn; i++) {
-                    int c = 0;
-                    for (int k = 0; k < 4; k++) c += __builtin_popcountll((rows[k] >> (2 * i)) & 3);
-                    if (c < 2) continue;
-                    int x = x0 + i;
-                    int sum = 0;
-                    for (int k = 0; k < 4; k++) {
-                        int yy = 2 * y + (k & 1), zz = 2 * z + (k >> 1);
-                        for (int dx = 0; dx < 2; dx++)
-                            if ((rows[k] >> (2 * i + dx)) & 1) sum += mat(2 * x + dx, yy, zz);
+                if (!any) continue;
+                uint64_t cm = 0;
+                for (int o = 0; o < 8; o++) {
+                    if (!fm[o]) continue;
+                    const uint8_t* fmat = matb(F, 2 * X + (o & 1), 2 * Y + ((o >> 1) & 1), 2 * Z + (o >> 2), fm[o], tmp);
+                    for (int s = 0; s < 8; s++) {
+                        const int a = s & 1, b = (s >> 1) & 1, c = s >> 2;
+                        uint64_t sub = fm[o] & (0x330033ull << (2 * a + 8 * b + 32 * c));
+                        const int cnt = __builtin_popcountll(sub);
+                        if (cnt < 2) continue;
+                        int sum = 0;
+                        while (sub) {
+                            sum += fmat[__builtin_ctzll(sub)];
+                            sub &= sub - 1;
+                        }
+                        const int q = (2 * (o & 1) + a) + 4 * (2 * ((o >> 1) & 1) + b) + 16 * (2 * (o >> 2) + c);
+                        cm |= 1ull << q;
+                        cm8[q] = (uint8_t)((sum + cnt / 2) / cnt);
                     }
-                    g2.w[(size_t)(x >> 6) + (size_t)g2.w64 * ((size_t)y + (size_t)h * z)] |= 1ull << (x & 63);
-                    mat2[(size_t)x + (size_t)h * ((size_t)y + (size_t)h * z)] = (uint8_t)((sum + c / 2) / c);
                 }
+                if (!cm) continue;
+                const size_t i = C.index(X, Y, Z);
+                C.m[i] = cm;
+                C.slot[i] = (uint32_t)(C.mat.size() / 64);
+                C.mat.insert(C.mat.end(), cm8, cm8 + 64);
             }
 }
 
 void build_chunk(const sg_scene* w, int M, int L, int cx, int cy, int cz, Blob* out /* [L] */,
                  uint32_t lod_mask = 0xFFFFFFFFu) {
-    BitGrid g;
-    g.init(M);
-    uint64_t solid;
-    if (M % 64 == 0) {
-        solid = sg_fill_bits(w, cx * M, cy * M, cz * M, M, M, M, g.w.data());
-    } else {
-        std::vector<uint8_t> b((size_t)M * M * M);
-        solid = sg_fill_bytes(w, cx * M, cy * M, cz * M, M, M, M, b.data());
-        for (int z = 0; z < M; z++)
-            for (int y = 0; y < M; y++)
-                for (int x = 0; x < M; x++)
-                    if (b[(size_t)x + (size_t)M * ((size_t)y + (size_t)M * z)])
-                        g.w[(size_t)(x >> 6) + (size_t)g.w64 * ((size_t)y + (size_t)M * z)] |= 1ull << (x & 63);
-    }
-    if (!solid) {
-        for (int l = 0; l < L; l++) out[l] = Blob();
-        return;
-    }
-    // LOD 0 materials straight from the generator; coarser LODs in dense grids
-    const int ox = cx * M, oy = cy * M, oz = cz * M;
-    auto mat0 = [&](int x, int y, int z) -> uint8_t { return sg_material(w, ox + x, oy + y, oz + z); };
-    std::vector<uint8_t> mat;
+    static thread_local FillScratch g;
     int last = -1;
     for (int l = 0; l < L; l++)
         if ((lod_mask >> l) & 1u) last = l;
+    for (int l = 0; l < L; l++) out[l] = Blob();
+    if (last < 0) return;
+    uint64_t* bits = g.prepare(M);
+    int zr[2] = {0, 0};
+    const int ox = cx * M, oy = cy * M, oz = cz * M;
+    if (M % 64 == 0) {
+        if (sg_fill_bits_z(w, ox, oy, oz, M, M, M, bits, zr) <= 0) return;
+    } else {
+        std::vector<uint8_t> b((size_t)M * M * M);
+        if (!sg_fill_bytes(w, ox, oy, oz, M, M, M, b.data())) return;
+        zr[0] = M;
+        for (int z = 0; z < M; z++)
+            for (int y = 0; y < M; y++)
+                for (int x = 0; x < M; x++)
+                    if (b[(size_t)x + (size_t)M * ((size_t)y + (size_t)M * z)]) {
+                        bits[(size_t)(x >> 6) + (size_t)g.w64 * ((size_t)y + (size_t)M * z)] |= 1ull << (x & 63);
+                        zr[0] = std::min(zr[0], z);
+                        zr[1] = z + 1;
+                    }
+    }
+    g.dz0 = zr[0];
+    g.dz1 = zr[1];
+    // LOD 0 materials straight from the generator; coarser LODs from their blocks' slots
+    auto mat0 = [&](const Blocks&, int bx, int by, int bz, uint64_t m, uint8_t* tmp) -> const uint8_t* {
+        sg_materials_block4(w, ox + 4 * bx, oy + 4 * by, oz + 4 * bz, m, tmp);
+        return tmp;
+    };
+    auto matl = [](const Blocks& B, int bx, int by, int bz, uint64_t, uint8_t*) -> const uint8_t* {
+        return &B.mat[(size_t)64 * B.slot[B.index(bx, by, bz)]];
+    };
+    Blocks cur, next;
+    blocks_from_bits(g, zr[0], zr[1], cur);
     for (int l = 0; l <= last; l++) {
-        const int rl = g.r;
-        auto matl = [&](int x, int y, int z) -> uint8_t {
-            return mat[(size_t)x + (size_t)rl * ((size_t)y + (size_t)rl * z)];
-        };
         if ((lod_mask >> l) & 1u) {
-            if (l == 0) build_dag(g, mat0, out[l]);
-            else build_dag(g, matl, out[l]);
+            if (l == 0) build_dag(cur, mat0, out[l]);
+            else build_dag(cur, matl, out[l]);
             for (int a = 0; a < 3; a++) {  // AABB to chunk-local LOD-0 units
                 out[l].lo[a] <<= l;
                 out[l].hi[a] <<= l;
             }
-        } else {
-            out[l] = Blob();
         }
         if (l + 1 <= last) {
-            BitGrid g2;
-            std::vector<uint8_t> m2;
-            if (l == 0) aggregate(g, mat0, g2, m2);
-            else aggregate(g, matl, g2, m2);
-            g = std::move(g2);
-            mat = std::move(m2);
+            if (l == 0) aggregate(cur, mat0, next);
+            else aggregate(cur, matl, next);
+            std::swap(cur, next);
         }
     }
-    for (int l = last + 1; l < L; l++) out[l] = Blob();
 }
 
 }  // namespace
@@ -460,30 +539,41 @@ int aokb_get(const aokb_world* b, int64_t i, int32_t lod, int64_t* chunk, aok_ch
 // Chunk source for aok_stream (the callback types of include/aok.h): builds
 // one (chunk, LOD) of a world on the calling thread.  The blob points into a
 // builder-owned allocation returned through *handle and freed by
-// aokb_source_release.
-typedef struct aokb_source {
+// aokb_source_release.  With a cache (aokb_source_set_cache) a build also
+// makes the region's coarser LODs (their aggregation is a small part of the
+// work), and recently built blobs are kept in host memory up to a byte
+// budget, least recently used out first: a (chunk, LOD) asked for again --
+// a region leaving and re-entering the view, or its LOD switching back --
+// costs no second build.
+struct aokb_source {
     const sg_scene* w;
     int M, L;
     int64_t gx, gy, gz;
-} aokb_source;
+    std::mutex mu;
+    size_t cap = 0, bytes = 0;
+    uint64_t hits = 0, misses = 0;
+    std::list<int64_t> lru;  // most recently used first
+    struct Entry {
+        std::shared_ptr<const Blob> blob;
+        size_t bytes;
+        std::list<int64_t>::iterator pos;
+    };
+    std::unordered_map<int64_t, Entry> cache;  // key chunk * L + lod
 
-aokb_source* aokb_source_create(const sg_scene* w, int32_t M, int32_t L) {
-    const sg_params* p = sg_get_params(w);
-    if (M < 8 || (M & (M - 1)) || L < 1 || (M >> (L - 1)) < 8 || p->wx % M || p->wy % M || p->wz % M) return nullptr;
-    return new aokb_source{w, M, L, p->wx / M, p->wy / M, p->wz / M};
-}
+    void evict_to(size_t limit) {
+        while (bytes > limit && !lru.empty()) {
+            auto it = cache.find(lru.back());
+            bytes -= it->second.bytes;
+            cache.erase(it);
+            lru.pop_back();
+        }
+    }
+};
 
-void aokb_source_destroy(aokb_source* s) { delete s; }
+namespace {
+size_t blob_bytes(const Blob& b) { return b.nodes.size() * 4 + b.leaves.size() * 8 + b.mats.size() + sizeof(Blob); }
 
-int aokb_source_build(void* user, int32_t cx, int32_t cy, int32_t cz, uint32_t lod, aok_chunk_blob* out,
-                      void** handle) {
-    const aokb_source* s = (const aokb_source*)user;
-    if (!s || !out || !handle || cx < 0 || cy < 0 || cz < 0 || cx >= s->gx || cy >= s->gy || cz >= s->gz ||
-        (int)lod >= s->L)
-        return -1;
-    std::vector<Blob>* blobs = new std::vector<Blob>(s->L);
-    build_chunk(s->w, s->M, s->L, cx, cy, cz, blobs->data(), 1u << lod);
-    const Blob& b = (*blobs)[lod];
+void fill_blob(const Blob& b, aok_chunk_blob* out) {
     out->nodes = b.nodes.data();
     out->n_node_words = b.nodes.size();
     out->leaves = b.leaves.data();
@@ -492,13 +582,93 @@ int aokb_source_build(void* user, int32_t cx, int32_t cy, int32_t cz, uint32_t l
     out->n_mats = b.mats.size();
     out->root = b.root;
     for (int a = 0; a < 3; a++) { out->aabb_lo[a] = b.lo[a]; out->aabb_hi[a] = b.hi[a]; }
-    *handle = blobs;
+}
+}  // namespace
+
+aokb_source* aokb_source_create(const sg_scene* w, int32_t M, int32_t L) {
+    const sg_params* p = sg_get_params(w);
+    if (M < 8 || (M & (M - 1)) || L < 1 || L > 8 || (M >> (L - 1)) < 8 || p->wx % M || p->wy % M || p->wz % M)
+        return nullptr;
+    aokb_source* s = new aokb_source();
+    s->w = w;
+    s->M = M;
+    s->L = L;
+    s->gx = p->wx / M;
+    s->gy = p->wy / M;
+    s->gz = p->wz / M;
+    return s;
+}
+
+void aokb_source_destroy(aokb_source* s) { delete s; }
+
+// Host-memory budget of the blob cache in bytes (0, the default: no cache;
+// blobs still held by a handle outlive their eviction).
+void aokb_source_set_cache(aokb_source* s, uint64_t bytes) {
+    if (!s) return;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->cap = (size_t)bytes;
+    s->evict_to(s->cap);
+}
+
+// [0] cache hits, [1] builds, [2] cached bytes, [3] cached blobs
+void aokb_source_stats(aokb_source* s, uint64_t out[4]) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    out[0] = s->hits;
+    out[1] = s->misses;
+    out[2] = s->bytes;
+    out[3] = s->cache.size();
+}
+
+int aokb_source_build(void* user, int32_t cx, int32_t cy, int32_t cz, uint32_t lod, aok_chunk_blob* out,
+                      void** handle) {
+    aokb_source* s = (aokb_source*)user;
+    if (!s || !out || !handle || cx < 0 || cy < 0 || cz < 0 || cx >= s->gx || cy >= s->gy || cz >= s->gz ||
+        (int)lod >= s->L)
+        return -1;
+    const int64_t chunk = (int64_t)cx + s->gx * ((int64_t)cy + s->gy * (int64_t)cz);
+    const int64_t key = chunk * s->L + lod;
+    bool cached;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        cached = s->cap > 0;
+        auto it = s->cache.find(key);
+        if (it != s->cache.end()) {
+            s->lru.splice(s->lru.begin(), s->lru, it->second.pos);
+            s->hits++;
+            auto* h = new std::shared_ptr<const Blob>(it->second.blob);
+            fill_blob(**h, out);
+            *handle = h;
+            return 0;
+        }
+        s->misses++;
+    }
+    // without a cache only the asked LOD; with one, it and every coarser LOD
+    const uint32_t mask = cached ? (0xFFu << lod) & ((1u << s->L) - 1u) : 1u << lod;
+    std::vector<Blob> blobs(s->L);
+    build_chunk(s->w, s->M, s->L, cx, cy, cz, blobs.data(), mask);
+    auto* h = new std::shared_ptr<const Blob>(std::make_shared<const Blob>(std::move(blobs[lod])));
+    if (cached) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (int l = (int)lod; l < s->L; l++) {
+            const int64_t k = chunk * s->L + l;
+            if (s->cache.count(k)) continue;  // another thread built it meanwhile
+            std::shared_ptr<const Blob> b = l == (int)lod ? *h : std::make_shared<const Blob>(std::move(blobs[l]));
+            const size_t nb = blob_bytes(*b);
+            if (nb > s->cap) continue;
+            s->lru.push_front(k);
+            s->cache.emplace(k, aokb_source::Entry{std::move(b), nb, s->lru.begin()});
+            s->bytes += nb;
+        }
+        s->evict_to(s->cap);
+    }
+    fill_blob(**h, out);
+    *handle = h;
     return 0;
 }
 
 void aokb_source_release(void* user, void* handle) {
     (void)user;
-    delete (std::vector<Blob>*)handle;
+    delete (std::shared_ptr<const Blob>*)handle;
 }
 
 // Totals over all entries: [0] node words, [1] leaves, [2] material bytes, [3] non-empty blobs.

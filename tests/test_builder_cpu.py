@@ -164,3 +164,60 @@ def test_abi_exports_every_declared_symbol():
     L = aok.lib()
     for n in sorted(names):
         assert hasattr(L, n), n
+
+
+def test_chunk_source_blob_cache():
+    """The procedural chunk source's blob cache: a (chunk, LOD) asked again is
+    served without a build, a build also caches the coarser LODs, every blob
+    equals the uncached build, the budget is kept by evicting the least
+    recently used, and a blob still held outlives its eviction."""
+    B = aok.blib()
+    vp = ctypes.c_void_p
+    B.aokb_source_build.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32,
+                                    ctypes.POINTER(aok.ChunkBlob), ctypes.POINTER(vp)]
+    B.aokb_source_release.argtypes = [vp, vp]
+    spec = MED64
+    w = sg.World(spec)
+    plain = B.aokb_source_create(w.handle, spec.chunk, spec.n_lods)
+    cached = B.aokb_source_create(w.handle, spec.chunk, spec.n_lods)
+    B.aokb_source_set_cache(cached, 64 << 20)
+
+    def stats(s):
+        a = (ctypes.c_uint64 * 4)()
+        B.aokb_source_stats(s, ctypes.byref(a))
+        return list(a)
+
+    def get(s, c, lod):
+        b, h = aok.ChunkBlob(), vp()
+        assert B.aokb_source_build(s, *c, lod, ctypes.byref(b), ctypes.byref(h)) == 0
+        return b, h
+
+    def same(a, b):
+        return all(np.array_equal(x, y) for x, y in zip(blob_arrays(a), blob_arrays(b))) and a.root == b.root \
+            and list(a.aabb_lo) == list(b.aabb_lo) and list(a.aabb_hi) == list(b.aabb_hi)
+
+    gx, gy, gz = spec.grid
+    c = (gx // 2, gy // 2, 0)
+    refs = [get(plain, c, lod) for lod in range(spec.n_lods)]
+    assert refs[0][0].n_node_words > 0
+    b1, h1 = get(cached, c, 1)
+    assert stats(cached)[:2] == [0, 1] and stats(cached)[3] == spec.n_lods - 1
+    assert same(b1, refs[1][0])
+    for lod in range(1, spec.n_lods):  # served from the cache, equal to the plain builds
+        b, h = get(cached, c, lod)
+        assert same(b, refs[lod][0])
+        B.aokb_source_release(cached, h)
+    assert stats(cached)[:2] == [spec.n_lods - 1, 1]
+    b0, h0 = get(cached, c, 0)  # a finer LOD: a build
+    assert same(b0, refs[0][0]) and stats(cached)[1] == 2
+    # a budget below the region's LOD-0 blob: evicted, while the handle keeps it alive
+    B.aokb_source_set_cache(cached, 1)
+    st = stats(cached)
+    assert st[2] == 0 and st[3] == 0
+    assert same(b0, refs[0][0]) and same(b1, refs[1][0])
+    for b, h in refs:
+        B.aokb_source_release(plain, h)
+    B.aokb_source_release(cached, h0)
+    B.aokb_source_release(cached, h1)
+    B.aokb_source_destroy(plain)
+    B.aokb_source_destroy(cached)
