@@ -643,7 +643,8 @@ def scene_grid(spec):
     return (spec.wx // spec.chunk, spec.wy // spec.chunk, spec.wz // spec.chunk)
 
 
-def bench_open_async(aok, ctx, threads, n_poses=300, fps=60.0, from_file=False):
+def bench_open_async(aok, ctx, threads, n_poses=300, fps=60.0, from_file=False, prefetch=(8, 2),
+                     build_cache_mb=4096):
     """The open-world path with asynchronous residency (aok_stream): frames
     are paced at `fps`; each frame installs what the background workers
     loaded since the previous one (coarser LODs first, then nearest), renders
@@ -651,7 +652,12 @@ def bench_open_async(aok, ctx, threads, n_poses=300, fps=60.0, from_file=False):
     load.  The first pose is loaded completely before the path starts.  The
     loaders build chunks from the procedural world, or (from_file) read them
     from a chunk-blob file holding every (chunk, LOD) the path plans, as the
-    paper streams preprocessed chunks from disk."""
+    paper streams preprocessed chunks from disk.  prefetch = (frames,
+    samples) also loads the plans of the camera extrapolated up to `frames`
+    frames ahead along its last displacement (aok_stream_set_prefetch);
+    None plans the current camera only, as the paper does.  The procedural
+    source keeps up to build_cache_mb of built blobs in host memory
+    (aokb_source_set_cache; 0: none)."""
     import torch
     from paper_2505_02017_gb300.stream import AsyncStreamer, Streamer
     spec = sg.OPEN_65536
@@ -682,7 +688,9 @@ def bench_open_async(aok, ctx, threads, n_poses=300, fps=60.0, from_file=False):
                      "file_build_s": round(t1 - t0, 2), "file_write_s": round(t2 - t1, 2)}
         blobs = aok.BlobFile(path)
     scene = aok.Scene(ctx, spec, node_words=512 << 20, leaves=256 << 20, mat_bytes=16 << 30)
-    st = AsyncStreamer(ctx, world, scene, threads, blobs=blobs)
+    st = AsyncStreamer(ctx, world, scene, threads, blobs=blobs, build_cache_mb=0 if from_file else build_cache_mb)
+    if prefetch:
+        st.set_prefetch(*prefetch)
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
     st.update(cams[0], TAU, stream=stream)
@@ -711,6 +719,7 @@ def bench_open_async(aok, ctx, threads, n_poses=300, fps=60.0, from_file=False):
         if rest > 0:
             time.sleep(rest)
     s = st.stats()
+    cache = st.source_stats()
     st.close()
     scene.destroy()
     if blobs is not None:
@@ -719,7 +728,10 @@ def bench_open_async(aok, ctx, threads, n_poses=300, fps=60.0, from_file=False):
     rs, us = sorted(render_ms), sorted(update_ms)
     return {"workload": f"open65536 path (seed 103), {n_poses} poses at 2560x1440 paced at {fps:g} frames/s, "
                         f"tau = 1 px; {threads} loader threads "
-                        + ("reading a chunk-blob file" if from_file else "building chunks procedurally"),
+                        + ("reading a chunk-blob file" if from_file else "building chunks procedurally")
+                        + (f"; prefetch {prefetch[0]} frames ahead ({prefetch[1]} extrapolated plans)" if prefetch
+                           else "; no prefetch")
+                        + (f"; {build_cache_mb} MB host blob cache" if build_cache_mb and not from_file else ""),
             **file_info,
             "first_pose_load_s": round(warm_s, 2),
             "render_ms_median": rs[len(rs) // 2], "render_ms_p99": rs[int(len(rs) * 0.99) - 1],
@@ -730,7 +742,9 @@ def bench_open_async(aok, ctx, threads, n_poses=300, fps=60.0, from_file=False):
             "regions_missing_median": sorted(missing)[len(missing) // 2], "max_regions_missing": max(missing), "max_resident_chunks": s["max_resident"],
             "max_resident_mb": round(s["max_resident_bytes"] / 1e6, 1), "installed_total": s["installed_total"],
             "evicted_total": s["evicted_total"], "cancelled_total": s["cancelled_total"],
-            "failed_total": s["failed_total"], "deferred_total": s["deferred_total"]}
+            "failed_total": s["failed_total"], "deferred_total": s["deferred_total"],
+            "ahead_installed_total": s["ahead_installed_total"],
+            **({"builder_cache": cache} if cache else {})}
 
 
 def run_reference(args):
@@ -964,6 +978,11 @@ def main():
     if not args.no_open:
         out["open_world"] = bench_open(aok, ctx, threads)
         out["open_world_async"] = bench_open_async(aok, ctx, threads)
+        plain = bench_open_async(aok, ctx, threads, prefetch=None, build_cache_mb=0)
+        out["open_world_async"]["without_prefetch_or_cache"] = {
+            k: plain[k] for k in ("frames_with_every_planned_lod", "planned_lods_installed_frac_median",
+                                  "planned_lods_installed_frac_min", "regions_missing_median", "installed_total",
+                                  "max_resident_mb")}
         out["open_world_async_file"] = bench_open_async(aok, ctx, threads, from_file=True)
     if rank == 0 and world_size == 1 and not args.no_cpu_baseline:
         try:
@@ -990,9 +1009,9 @@ def main():
                           for r in out["served"]["rates"]}
     if "open_world" in out:
         summ["open_world_frame_ms_median"] = out["open_world"]["frame_ms_median"]
-        summ["open_world_async_installed_median"] = out["open_world_async"]["planned_lods_installed_frac_median"]
-        summ["open_world_async_file_installed_median"] = \
-            out["open_world_async_file"]["planned_lods_installed_frac_median"]
+        for k in ("open_world_async", "open_world_async_file"):
+            summ[k] = {"installed_median": out[k]["planned_lods_installed_frac_median"],
+                       "frames_with_every_planned_lod": out[k]["frames_with_every_planned_lod"]}
     if "cpu_baseline" in out and "value" in out["cpu_baseline"]:
         summ["cpu_oracle_rays_per_s"] = out["cpu_baseline"]["value"]
     out["summary"] = summ

@@ -243,8 +243,11 @@ typedef struct aok_stream aok_stream;
  * (coarser first; see aok_select_chunks' lod output).  The scene's pools
  * (aok_scene_desc capacities) are the HBM budget: a load that does not fit
  * waits for evictions and is retried.  The streamer owns the residency of
- * its scene: do not upload or evict its chunks by other calls meanwhile, and
- * destroy it before the scene. */
+ * its scene: do not upload or evict its chunks by other calls meanwhile.
+ * Destroy it before the scene; destroying the scene (or its context) first
+ * stops it -- its workers are joined, its loads freed -- after which
+ * aok_stream_update, _wait and _set_prefetch return AOK_E_NOT_RESIDENT and
+ * aok_stream_destroy only frees the object. */
 int aok_stream_create(aok_ctx* ctx, uint32_t scene, aok_chunk_source_fn source, aok_chunk_release_fn release,
                       void* user, int32_t n_threads, aok_stream** out);
 /* Between frames, on the rendering thread: plan the camera's residency (as
@@ -259,13 +262,27 @@ int aok_stream_update(aok_stream* s, const aok_camera* cam, double lod_threshold
  * < 0 waits without limit).  The finished loads are installed by the next
  * aok_stream_update. */
 int aok_stream_wait(aok_stream* s, int32_t timeout_ms);
+/* Load ahead of need along the camera's motion (not in the paper, which
+ * plans for the current camera only).  From its second update on, each
+ * aok_stream_update also plans `samples` cameras moved on from the current
+ * one by frames * k / samples (k = 1 .. samples) times the displacement
+ * since the previous update (same orientation and projection).  LODs those
+ * plans want are queued after the current plan's (the nearest in time
+ * first) and are not evicted while an extrapolated plan still wants them;
+ * the current plan's loads, evictions and stand-ins are as without
+ * prefetch.  frames = 0 (the default) turns it off.  frames in [0, 1000],
+ * samples in [1, 16] when frames > 0, else AOK_E_INVALID.  Takes effect at
+ * the next update; costs `samples` more residency plans per update. */
+int aok_stream_set_prefetch(aok_stream* s, int32_t frames, int32_t samples);
 /* stats[0] installed (chunk, LOD)s, [1] their device bytes, [2] / [3] the
  * maxima of both so far, [4] queued requests, [5] loads running, [6] loads
  * finished but not installed, [7] installed in total, [8] evicted in total,
  * [9] requests cancelled, [10] loads that failed (source or validation),
  * [11] loads deferred for lack of pool space, [12] planned regions whose
  * planned LOD was not installed at the last update (0: the frame after it
- * renders exactly the Eq. 1 selection), [13] regions that update planned. */
+ * renders exactly the Eq. 1 selection), [13] regions that update planned,
+ * [14] installs of LODs that only an extrapolated plan wanted (prefetch).
+ * stats holds 15 entries. */
 int aok_stream_stats(aok_stream* s, uint64_t* stats);
 /* Per chunk region (x fastest) the bitmask of installed LODs (bit l = LOD l). */
 int aok_stream_resident(aok_stream* s, uint8_t* lod_masks);

@@ -85,6 +85,7 @@ def lib() -> ctypes.CDLL:
             "aok_stream_update": [vp, P(Camera), dbl, vp],
             "aok_stream_wait": [vp, i32],
             "aok_stream_stats": [vp, P(u64)],
+            "aok_stream_set_prefetch": [vp, i32, i32],
             "aok_stream_resident": [vp, vp],
             "aok_stream_destroy": [vp],
             "aok_blobfile_create": [ctypes.c_char_p, i32, i32, P(i32), P(vp)],
@@ -167,6 +168,8 @@ def blib() -> ctypes.CDLL:
         L.aokb_source_create.restype = vp
         L.aokb_source_create.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
         L.aokb_source_destroy.argtypes = [vp]
+        L.aokb_source_set_cache.argtypes = [vp, ctypes.c_uint64]
+        L.aokb_source_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64 * 4)]
         _blib = L
     return _blib
 

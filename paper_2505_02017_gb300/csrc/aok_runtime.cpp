@@ -433,6 +433,12 @@ int aok_scene_destroy(aok_ctx* ctx, uint32_t id) {
         ctx->scenes.erase(it);
     }
     cudaSetDevice(ctx->device);
+    std::vector<aok_stream*> streams;
+    {
+        std::lock_guard<std::mutex> g(sc->mu);
+        streams.swap(sc->streams);
+    }
+    for (aok_stream* s : streams) stream_detach(s);  // their workers write into this scene's pools
     cudaDeviceSynchronize();
     const size_t ndesc = (size_t)sc->n_chunks * sc->desc.n_lods;
     dev_free(ctx, sc->d_nodes, sc->nodes.cap * 4);

@@ -46,7 +46,12 @@ struct Scene {
     std::vector<ChunkRef> h_desc;
     std::vector<ChunkAlloc> alloc;
     std::mutex mu;
+    std::vector<aok_stream*> streams;  // streamers of this scene (guarded by mu)
 };
+
+// Stop a streamer of a scene that is being destroyed: join its workers, free
+// its loads and quarantined space; the object stays for aok_stream_destroy.
+void stream_detach(aok_stream* s);
 
 // Device arena of aok_render_batch: per-view frame tables, work counters and
 // the CUDA graph of the last list shape.

@@ -2,11 +2,13 @@
 // (chunk, LOD)s a camera needs while frames render; loads and evictions are
 // installed in the descriptor table at frame boundaries, by a kernel on the
 // rendering stream; evicted pool space is reused only after the frames that
-// could still read it have finished.
+// could still read it have finished.  Optionally the plans of the camera
+// extrapolated along its last displacement are loaded ahead of need.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -21,16 +23,19 @@ using namespace aok;
 namespace {
 
 struct Request {
+    uint32_t rank;  // 0: the current plan; k > 0: the k-th extrapolated plan (loaded ahead of need)
     uint32_t lod;
-    double dist2;  // squared distance from the camera to the region's centre
+    double dist2;   // squared distance from the camera to the region's centre
     int64_t chunk;
 };
 
-// Heap order: the paper loads coarser LODs first, then the regions nearest
-// the camera.  std::push_heap keeps the "largest" on top, so "less" means
-// "loaded later".
+// Heap order: the current plan before the extrapolated ones (nearest in time
+// first); within a plan the paper's order, coarser LODs first, then the
+// regions nearest the camera.  std::push_heap keeps the "largest" on top, so
+// "less" means "loaded later".
 struct LoadsLater {
     bool operator()(const Request& a, const Request& b) const {
+        if (a.rank != b.rank) return a.rank > b.rank;
         if (a.lod != b.lod) return a.lod < b.lod;
         if (a.dist2 != b.dist2) return a.dist2 > b.dist2;
         return a.chunk > b.chunk;
@@ -67,7 +72,9 @@ struct aok_stream {
     std::mutex mu;
     std::condition_variable work_cv, idle_cv;
     bool stop = false;
+    bool detached = false;  // its scene was destroyed: workers joined, calls refused
     std::vector<uint8_t> want;      // planned LOD per region (0xFF: none)
+    std::vector<uint8_t> ahead;     // LODs of the extrapolated plans per region (bitmask)
     std::vector<uint8_t> resident;  // installed LODs per region (bitmask)
     std::vector<uint8_t> pending;   // LODs queued, loading or loaded-not-installed (bitmask)
     std::vector<Request> heap;
@@ -81,7 +88,15 @@ struct aok_stream {
     uint64_t n_installed = 0, n_evicted = 0, n_cancelled = 0, n_failed = 0, n_deferred = 0;
     uint64_t n_missing = 0;  // planned regions whose planned LOD was not installed at the last update
     uint64_t n_planned = 0;  // regions the last update planned
+    uint64_t n_ahead_installed = 0;  // installs of LODs only the extrapolated plans wanted
 
+    // prefetch along the camera's motion (aok_stream_set_prefetch)
+    int ahead_frames = 0, ahead_samples = 0;
+    bool have_prev = false;
+    double prev_origin[3] = {0, 0, 0};
+
+    // the LODs region c needs: its planned one and those of the extrapolated plans
+    uint8_t needed(int64_t c) const { return (uint8_t)((want[c] != 0xFF ? 1u << want[c] : 0u) | ahead[c]); }
     void worker();
 };
 
@@ -103,7 +118,7 @@ void aok_stream::worker() {
             std::pop_heap(heap.begin(), heap.end(), LoadsLater());
             r = heap.back();
             heap.pop_back();
-            if (want[r.chunk] != r.lod) {  // the plan moved on: cancel
+            if (!((needed(r.chunk) >> r.lod) & 1u)) {  // the plan moved on: cancel
                 pending[r.chunk] &= (uint8_t)~(1u << r.lod);
                 n_cancelled++;
                 if (heap.empty() && running == 0) idle_cv.notify_all();
@@ -141,6 +156,36 @@ void aok_stream::worker() {
     if (sg.stream) cudaStreamDestroy(sg.stream);
 }
 
+namespace aok {
+
+void stream_detach(aok_stream* s) {
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->work_cv.notify_all();
+    for (std::thread& t : s->workers) t.join();
+    s->workers.clear();
+    cudaSetDevice(s->ctx->device);
+    {
+        std::lock_guard<std::mutex> g(s->sc->mu);
+        for (Loaded& ld : s->loaded) free_alloc(s->sc, ld.alloc);
+        for (Quarantined& q : s->quarantine) {
+            cudaEventSynchronize(q.done);
+            for (ChunkAlloc& a : q.allocs) free_alloc(s->sc, a);
+            cudaEventDestroy(q.done);
+        }
+    }
+    s->loaded.clear();
+    s->quarantine.clear();
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->detached = true;
+    s->ctx = nullptr;
+    s->sc = nullptr;
+}
+
+}  // namespace aok
+
 extern "C" {
 
 int aok_stream_create(aok_ctx* ctx, uint32_t scene, aok_chunk_source_fn source, aok_chunk_release_fn release,
@@ -161,6 +206,7 @@ int aok_stream_create(aok_ctx* ctx, uint32_t scene, aok_chunk_source_fn source, 
     s->gx = sc->desc.grid[0];
     s->gy = sc->desc.grid[1];
     s->want.assign((size_t)s->n, 0xFF);
+    s->ahead.assign((size_t)s->n, 0);
     s->resident.assign((size_t)s->n, 0);
     s->pending.assign((size_t)s->n, 0);
     {
@@ -179,6 +225,10 @@ int aok_stream_create(aok_ctx* ctx, uint32_t scene, aok_chunk_source_fn source, 
         s->max_count = s->res_count;
         s->max_bytes = s->res_bytes;
     }
+    {
+        std::lock_guard<std::mutex> g(sc->mu);
+        sc->streams.push_back(s);
+    }
     for (int i = 0; i < n_threads; i++) s->workers.emplace_back([s] { s->worker(); });
     *out = s;
     return AOK_OK;
@@ -186,11 +236,43 @@ int aok_stream_create(aok_ctx* ctx, uint32_t scene, aok_chunk_source_fn source, 
 
 int aok_stream_update(aok_stream* s, const aok_camera* cam, double tau, void* stream) {
     if (!s || !cam) return AOK_E_INVALID;
+    if (s->detached) return AOK_E_NOT_RESIDENT;
     aok_ctx* ctx = s->ctx;
     Scene* sc = s->sc;
     std::vector<uint8_t> plan((size_t)s->n);
     int st = aok_plan_residency(ctx, s->scene_id, cam, tau, plan.data(), nullptr);
     if (st) return st;
+    // extrapolated plans: the camera moved on by its last displacement for
+    // frames * k / samples more updates (k = 1 .. samples)
+    std::vector<uint8_t> ahead((size_t)s->n, 0), ahead_rank;
+    int ahead_frames, ahead_samples;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        ahead_frames = s->ahead_frames;
+        ahead_samples = s->ahead_samples;
+    }
+    if (ahead_frames > 0 && s->have_prev) {
+        ahead_rank.assign((size_t)s->n * s->L, 0);
+        std::vector<uint8_t> pk((size_t)s->n);
+        for (int k = 1; k <= ahead_samples; k++) {
+            aok_camera ck = *cam;
+            const double f = (double)ahead_frames * k / ahead_samples;
+            for (int a = 0; a < 3; a++) {
+                // on the 2^-12 grid camera origins take (exact in binary32 after rounding)
+                const double o = cam->origin[a] + f * ((double)cam->origin[a] - s->prev_origin[a]);
+                ck.origin[a] = (float)(std::nearbyint(std::min(std::max(o, -131000.0), 131000.0) * 4096.0) / 4096.0);
+            }
+            if (aok_plan_residency(ctx, s->scene_id, &ck, tau, pk.data(), nullptr) != AOK_OK) continue;
+            for (int64_t c = 0; c < s->n; c++) {
+                const uint8_t l = pk[c];
+                if (l == 0xFF || l == plan[c] || ((ahead[c] >> l) & 1u)) continue;
+                ahead[c] |= (uint8_t)(1u << l);
+                ahead_rank[(size_t)(c * s->L + l)] = (uint8_t)k;
+            }
+        }
+    }
+    for (int a = 0; a < 3; a++) s->prev_origin[a] = cam->origin[a];
+    s->have_prev = true;
     CamDev cd;
     st = make_cam(ctx, sc, cam, tau, &cd);
     if (st) return st;
@@ -202,6 +284,7 @@ int aok_stream_update(aok_stream* s, const aok_camera* cam, double tau, void* st
         std::lock_guard<std::mutex> lk(s->mu);
         std::lock_guard<std::mutex> g(sc->mu);
         s->want.swap(plan);
+        s->ahead.swap(ahead);
         auto none_ref = [](uint32_t lod) {
             ChunkRef r;
             std::memset(&r, 0, sizeof(r));
@@ -209,15 +292,16 @@ int aok_stream_update(aok_stream* s, const aok_camera* cam, double tau, void* st
             r.lod = lod;
             return r;
         };
-        // 1. install finished loads (a region no longer planned frees its load at once: never visible)
+        // 1. install finished loads (one no plan wants any more frees its space at once: never visible)
         for (Loaded& ld : s->loaded) {
             const size_t di = (size_t)(ld.chunk * s->L + ld.lod);
             s->pending[ld.chunk] &= (uint8_t)~(1u << ld.lod);
-            if (s->want[ld.chunk] == 0xFF) {
+            if (!((s->needed(ld.chunk) >> ld.lod) & 1u) && s->want[ld.chunk] == 0xFF) {
                 free_alloc(sc, ld.alloc);
                 s->n_cancelled++;
                 continue;
             }
+            if (s->want[ld.chunk] != ld.lod && ((s->ahead[ld.chunk] >> ld.lod) & 1u)) s->n_ahead_installed++;
             patches.push_back({(uint64_t)di, ld.ref});
             sc->alloc[di] = ld.alloc;
             sc->h_desc[di] = ld.ref;
@@ -228,7 +312,7 @@ int aok_stream_update(aok_stream* s, const aok_camera* cam, double tau, void* st
         }
         s->loaded.clear();
         // 2. evictions: a region's other LODs go once its planned LOD is installed,
-        //    all of them once it is no longer planned
+        //    all of them once it is no longer planned; LODs an extrapolated plan wants stay
         for (int64_t c = 0; c < s->n; c++) {
             const uint8_t res = s->resident[c];
             if (!res) continue;
@@ -236,7 +320,7 @@ int aok_stream_update(aok_stream* s, const aok_camera* cam, double tau, void* st
             const bool settled = w == 0xFF || (res >> w) & 1u;
             if (!settled) continue;
             for (int l = 0; l < s->L; l++) {
-                if (!((res >> l) & 1u) || l == (int)w) continue;
+                if (!((res >> l) & 1u) || l == (int)w || ((s->ahead[c] >> l) & 1u)) continue;
                 const size_t di = (size_t)(c * s->L + l);
                 patches.push_back({(uint64_t)di, none_ref((uint32_t)l)});
                 s->res_bytes -= std::min(s->res_bytes, alloc_bytes(sc->alloc[di]));
@@ -250,16 +334,18 @@ int aok_stream_update(aok_stream* s, const aok_camera* cam, double tau, void* st
         }
         s->max_count = std::max(s->max_count, s->res_count);
         s->max_bytes = std::max(s->max_bytes, s->res_bytes);
-        // 3. requests for planned LODs neither installed nor on their way; deferred loads retry
-        for (Request& r : s->deferred) {
-            if (s->want[r.chunk] == r.lod) {
-                s->heap.push_back(r);
-                std::push_heap(s->heap.begin(), s->heap.end(), LoadsLater());
-            } else {
-                s->pending[r.chunk] &= (uint8_t)~(1u << r.lod);
-                s->n_cancelled++;
-            }
+        // 3. the load queue, rebuilt from the plans: queued and deferred requests
+        //    no plan wants are dropped, the others re-ranked; then the needed LODs
+        //    neither installed nor on their way are queued
+        for (const Request& r : s->heap) {
+            s->pending[r.chunk] &= (uint8_t)~(1u << r.lod);
+            if (!((s->needed(r.chunk) >> r.lod) & 1u)) s->n_cancelled++;
         }
+        for (const Request& r : s->deferred) {
+            s->pending[r.chunk] &= (uint8_t)~(1u << r.lod);
+            if (!((s->needed(r.chunk) >> r.lod) & 1u)) s->n_cancelled++;
+        }
+        s->heap.clear();
         s->deferred.clear();
         s->n_missing = 0;
         s->n_planned = 0;
@@ -267,13 +353,19 @@ int aok_stream_update(aok_stream* s, const aok_camera* cam, double tau, void* st
             const uint8_t w = s->want[c];
             if (w != 0xFF) s->n_planned++;
             if (w != 0xFF && !((s->resident[c] >> w) & 1u)) s->n_missing++;
-            if (w == 0xFF || ((s->resident[c] | s->pending[c]) >> w) & 1u) continue;
+            uint8_t need = (uint8_t)(s->needed(c) & ~(s->resident[c] | s->pending[c]));
+            if (!need) continue;
             const int cx = (int)(c % s->gx), cy = (int)((c / s->gx) % s->gy), cz = (int)(c / ((int64_t)s->gx * s->gy));
             const double q[3] = {(cx + 0.5) * M - cd.of[0], (cy + 0.5) * M - cd.of[1], (cz + 0.5) * M - cd.of[2]};
-            s->heap.push_back({(uint32_t)w, q[0] * q[0] + q[1] * q[1] + q[2] * q[2], c});
-            std::push_heap(s->heap.begin(), s->heap.end(), LoadsLater());
-            s->pending[c] |= (uint8_t)(1u << w);
+            const double d2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+            for (int l = 0; l < s->L; l++) {
+                if (!((need >> l) & 1u)) continue;
+                const uint32_t rank = l == (int)w ? 0u : (uint32_t)ahead_rank[(size_t)(c * s->L + l)];
+                s->heap.push_back({rank, (uint32_t)l, d2, c});
+                s->pending[c] |= (uint8_t)(1u << l);
+            }
         }
+        std::make_heap(s->heap.begin(), s->heap.end(), LoadsLater());
     }
     s->work_cv.notify_all();
     // 4. the descriptor changes, ordered before every later frame on `stream`
@@ -310,6 +402,11 @@ int aok_stream_update(aok_stream* s, const aok_camera* cam, double tau, void* st
         cudaGetLastError();  // cudaErrorNotReady from the query is not an error
         if (freed && !s->deferred.empty()) {
             for (Request& r : s->deferred) {
+                if (!((s->needed(r.chunk) >> r.lod) & 1u)) {
+                    s->pending[r.chunk] &= (uint8_t)~(1u << r.lod);
+                    s->n_cancelled++;
+                    continue;
+                }
                 s->heap.push_back(r);
                 std::push_heap(s->heap.begin(), s->heap.end(), LoadsLater());
             }
@@ -322,6 +419,7 @@ int aok_stream_update(aok_stream* s, const aok_camera* cam, double tau, void* st
 
 int aok_stream_wait(aok_stream* s, int32_t timeout_ms) {
     if (!s) return AOK_E_INVALID;
+    if (s->detached) return AOK_E_NOT_RESIDENT;
     std::unique_lock<std::mutex> lk(s->mu);
     auto idle = [&] { return s->heap.empty() && s->running == 0; };
     if (timeout_ms < 0) {
@@ -334,10 +432,20 @@ int aok_stream_wait(aok_stream* s, int32_t timeout_ms) {
 int aok_stream_stats(aok_stream* s, uint64_t* st) {
     if (!s || !st) return AOK_E_INVALID;
     std::lock_guard<std::mutex> lk(s->mu);
-    const uint64_t v[14] = {s->res_count, s->res_bytes, s->max_count, s->max_bytes, (uint64_t)s->heap.size(),
+    const uint64_t v[15] = {s->res_count, s->res_bytes, s->max_count, s->max_bytes, (uint64_t)s->heap.size(),
                             (uint64_t)s->running, (uint64_t)s->loaded.size(), s->n_installed, s->n_evicted,
-                            s->n_cancelled, s->n_failed, s->n_deferred, s->n_missing, s->n_planned};
+                            s->n_cancelled, s->n_failed, s->n_deferred, s->n_missing, s->n_planned,
+                            s->n_ahead_installed};
     std::memcpy(st, v, sizeof(v));
+    return AOK_OK;
+}
+
+int aok_stream_set_prefetch(aok_stream* s, int32_t frames, int32_t samples) {
+    if (!s || frames < 0 || frames > 1000 || (frames > 0 && (samples < 1 || samples > 16))) return AOK_E_INVALID;
+    if (s->detached) return AOK_E_NOT_RESIDENT;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->ahead_frames = frames;
+    s->ahead_samples = frames > 0 ? samples : 0;
     return AOK_OK;
 }
 
@@ -350,19 +458,13 @@ int aok_stream_resident(aok_stream* s, uint8_t* masks) {
 
 int aok_stream_destroy(aok_stream* s) {
     if (!s) return AOK_E_INVALID;
-    {
-        std::lock_guard<std::mutex> lk(s->mu);
-        s->stop = true;
-    }
-    s->work_cv.notify_all();
-    for (std::thread& t : s->workers) t.join();
-    cudaSetDevice(s->ctx->device);
-    std::lock_guard<std::mutex> g(s->sc->mu);
-    for (Loaded& ld : s->loaded) free_alloc(s->sc, ld.alloc);
-    for (Quarantined& q : s->quarantine) {
-        cudaEventSynchronize(q.done);
-        for (ChunkAlloc& a : q.allocs) free_alloc(s->sc, a);
-        cudaEventDestroy(q.done);
+    if (!s->detached) {
+        {
+            std::lock_guard<std::mutex> g(s->sc->mu);
+            auto& v = s->sc->streams;
+            v.erase(std::remove(v.begin(), v.end(), s), v.end());
+        }
+        stream_detach(s);
     }
     delete s;
     return AOK_OK;

@@ -15,13 +15,28 @@ Every step runs in the native libraries; this module only moves lists.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import os
 import time
+import weakref
 
 import numpy as np
 
 from . import BuiltWorld, Scene, _stream_handle, blib, check, lib, to_camera
+
+# streamers still open: their worker threads are joined before the interpreter
+# (and the CUDA runtime) shuts down
+_open_streamers: "weakref.WeakSet[AsyncStreamer]" = weakref.WeakSet()
+
+
+@atexit.register
+def _close_open_streamers():
+    for st in list(_open_streamers):
+        try:
+            st.close()
+        except Exception:
+            pass
 
 
 class Streamer:
@@ -82,15 +97,17 @@ class Streamer:
 
 STREAM_STATS = ("resident", "resident_bytes", "max_resident", "max_resident_bytes", "queued", "running",
                 "loaded_not_installed", "installed_total", "evicted_total", "cancelled_total", "failed_total",
-                "deferred_total", "missing", "planned")
+                "deferred_total", "missing", "planned", "ahead_installed_total")
 
 
 class AsyncStreamer:
     """Background residency for `scene` (aok_stream_*), loading from the
     native builder over `world`, or from a chunk-blob file (`blobs`, an open
-    BlobFile) -- the paper's disk-resident chunks."""
+    BlobFile) -- the paper's disk-resident chunks.  build_cache_mb > 0 gives
+    the native builder a host-memory blob cache of that size
+    (aokb_source_set_cache)."""
 
-    def __init__(self, ctx, world, scene: Scene, threads: int | None = None, blobs=None):
+    def __init__(self, ctx, world, scene: Scene, threads: int | None = None, blobs=None, build_cache_mb: int = 0):
         self.ctx, self.world, self.scene = ctx, world, scene
         self._src = None
         self._blobs = blobs
@@ -103,6 +120,7 @@ class AsyncStreamer:
             self._src = blib().aokb_source_create(world.handle, spec.chunk, spec.n_lods)
             if not self._src:
                 raise ValueError("bad chunking for the builder")
+            blib().aokb_source_set_cache(self._src, int(build_cache_mb) << 20)
             build = ctypes.cast(blib().aokb_source_build, ctypes.c_void_p)
             release = ctypes.cast(blib().aokb_source_release, ctypes.c_void_p)
             user = self._src
@@ -110,6 +128,7 @@ class AsyncStreamer:
         check(lib().aok_stream_create(ctx.h, scene.id, build, release, user, int(threads or os.cpu_count() or 1),
                                       ctypes.byref(h)), "aok_stream_create")
         self.h = h
+        _open_streamers.add(self)
         gx, gy, gz = scene.grid
         self.n = gx * gy * gz
 
@@ -118,13 +137,26 @@ class AsyncStreamer:
         return check(lib().aok_stream_update(self.h, ctypes.byref(c), float(tau), _stream_handle(stream)),
                      "aok_stream_update")
 
+    def set_prefetch(self, frames: int, samples: int = 2):
+        """Load the plans of the camera extrapolated `frames` updates ahead
+        (aok_stream_set_prefetch); 0 turns it off."""
+        return check(lib().aok_stream_set_prefetch(self.h, int(frames), int(samples)), "aok_stream_set_prefetch")
+
     def wait(self, timeout_ms: int = -1) -> int:
         return int(lib().aok_stream_wait(self.h, int(timeout_ms)))
 
     def stats(self) -> dict:
-        a = (ctypes.c_uint64 * 14)()
+        a = (ctypes.c_uint64 * len(STREAM_STATS))()
         check(lib().aok_stream_stats(self.h, a), "aok_stream_stats")
         return dict(zip(STREAM_STATS, (int(v) for v in a)))
+
+    def source_stats(self) -> dict:
+        """The native builder's blob cache: hits, builds, cached bytes and blobs."""
+        if not self._src:
+            return {}
+        a = (ctypes.c_uint64 * 4)()
+        blib().aokb_source_stats(self._src, ctypes.byref(a))
+        return dict(zip(("cache_hits", "builds", "cached_bytes", "cached_blobs"), (int(v) for v in a)))
 
     def resident(self) -> np.ndarray:
         out = np.zeros(self.n, np.uint8)

@@ -231,3 +231,105 @@ def test_async_streaming_from_blob_file(tmp_path):
     sc_f.destroy()
     sc_s.destroy()
     ctx.close()
+
+
+def test_async_prefetch_along_motion():
+    """Prefetch along the camera's motion (aok_stream_set_prefetch): with
+    every load finished between poses, the streamer that plans the camera
+    extrapolated ahead already holds nearly every LOD the next pose plans when
+    that pose's update runs, where the one without prefetch holds none of the
+    new ones; frames equal the oracle for the LODs they used; once settled,
+    frames equal the synchronous streamer's; bad arguments are refused."""
+    from paper_2505_02017_gb300.stream import AsyncStreamer
+    spec = sg.OPEN_8192
+    w = sg.World(spec)
+    ctx = aok.Context(0)
+    scs = [aok.Scene(ctx, spec, node_words=64 << 20, leaves=16 << 20, mat_bytes=1 << 30) for _ in range(3)]
+    pre = AsyncStreamer(ctx, w, scs[0], threads=8)
+    plain = AsyncStreamer(ctx, w, scs[1], threads=8)
+    try:
+        sst = Streamer(ctx, w, scs[2], threads=8)
+        for bad in ((-1, 2), (1001, 2), (4, 0), (4, 17)):
+            with pytest.raises(aok.AokError):
+                pre.set_prefetch(*bad)
+        pre.set_prefetch(3, 3)
+        S = orc.OracleScene(w)
+        # one straight leg: poses equally spaced along it (the ground clamp aside)
+        W, H = 320, 180
+        cams = sg.path_cameras(w, 77, 12, W, H, n_waypoints=2, span=3000.0)
+        tau = 1.0 / 3.0
+        n = scs[0].grid[0] * scs[0].grid[1] * scs[0].grid[2]
+        miss_pre = miss_plain = new_pairs = checked = amb = 0
+        prev_plan = None
+        for i, cam in enumerate(cams):
+            pre.update(cam, tau)
+            plain.update(cam, tau)
+            plan = sst.plan(cam, tau)
+            if i >= 2:  # the first update has no motion, the second extrapolates from one step
+                new_pairs += int(((plan != 0xFF) & (plan != prev_plan)).sum())
+                miss_pre += pre.stats()["missing"]
+                miss_plain += plain.stats()["missing"]
+            prev_plan = plan
+            if i % 4 == 3:
+                lod = torch.empty(n, dtype=torch.int8, device="cuda")
+                hit, t = aok.alloc_frame(W, H)
+                aok.select_chunks(ctx, scs[0], cam, tau, lod_out=lod)
+                aok.cast_selected(ctx, scs[0], cam, hit, t)
+                torch.cuda.synchronize()
+                used = lod.cpu().numpy().astype(np.int64)
+                res = pre.resident().astype(np.int64)
+                sel = np.where((res >> used) & 1, used, -1).astype(np.int8)
+                c, a = compare(decode(hit, t), S.cast(cam, sel, view_dist=spec.view_dist), max_amb_frac=1.0,
+                               min_pixels_checked=0)
+                checked += c
+                amb += a
+            assert pre.wait(120000) == aok.AOK_OK and plain.wait(120000) == aok.AOK_OK
+        assert amb <= 1e-4 * (checked + amb), (amb, checked)
+        st = pre.stats()
+        assert new_pairs > 0 and miss_plain >= new_pairs // 2
+        assert miss_pre <= 0.1 * miss_plain, (miss_pre, miss_plain, new_pairs)
+        assert st["ahead_installed_total"] > 0 and st["failed_total"] == 0
+        # settled on the last pose: the frame equals the synchronous streamer's
+        pre.update(cams[-1], tau)
+        assert pre.stats()["missing"] == 0
+        sst.update(cams[-1], tau)
+        fa, fs = aok.alloc_frame(W, H), aok.alloc_frame(W, H)
+        aok.render(ctx, scs[0], cams[-1], tau, *fa)
+        aok.render(ctx, scs[2], cams[-1], tau, *fs)
+        torch.cuda.synchronize()
+        assert torch.equal(fa[0], fs[0]) and torch.equal(fa[1].view(torch.int32), fs[1].view(torch.int32))
+        pre.set_prefetch(0, 0)  # off again
+    finally:
+        pre.close()
+        plain.close()
+        for sc in scs:
+            sc.destroy()
+        ctx.close()
+
+
+def test_scene_destroyed_under_a_running_streamer():
+    """Destroying a scene (or its context) while its streamer still loads
+    stops the streamer first: its workers are joined, later calls are
+    refused with AOK_E_NOT_RESIDENT, and closing it afterwards is safe."""
+    from paper_2505_02017_gb300.stream import AsyncStreamer
+    spec = sg.OPEN_8192
+    w = sg.World(spec)
+    ctx = aok.Context(0)
+    sc = aok.Scene(ctx, spec, node_words=64 << 20, leaves=16 << 20, mat_bytes=1 << 30)
+    st = AsyncStreamer(ctx, w, sc, threads=4)
+    cam = sg.path_cameras(w, 77, 2, 160, 90, n_waypoints=2, span=3000.0)[0]
+    st.update(cam, 1.0 / 3.0)  # loads start in the background
+    sc.destroy()
+    with pytest.raises(aok.AokError) as e:
+        st.update(cam, 1.0 / 3.0)
+    assert e.value.status == aok.AOK_E_NOT_RESIDENT
+    assert st.wait(0) == aok.AOK_E_NOT_RESIDENT
+    st.stats()
+    st.close()
+    # the same through the context: its scenes go, and with them the streamer's
+    sc2 = aok.Scene(ctx, spec, node_words=64 << 20, leaves=16 << 20, mat_bytes=1 << 30)
+    st2 = AsyncStreamer(ctx, w, sc2, threads=4)
+    st2.update(cam, 1.0 / 3.0)
+    ctx.close()
+    assert st2.wait(0) == aok.AOK_E_NOT_RESIDENT
+    st2.close()
