@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 #include <vector>
 
 #include "../../include/aok.h"
@@ -74,6 +75,8 @@ struct TileDev {
     float* hiz_next;           // [tiles] this frame's final per-tile max distance
     int4* rect;                // [chunks] tile rectangle [x0, x1) x [y0, y1) of the chunk's AABB
     float* dmin;               // [chunks] lower bound of the distance from the camera to the AABB
+    int32_t* dfar;             // [chunks] largest L-inf distance (2^-12 units) from the camera origin to a
+                               // point of the AABB
     uint32_t* area;            // [chunks] tiles in the rectangle (0: no pairs)
     uint32_t* list;            // [chunks] chunks with pairs, ascending
     unsigned long long* offs;  // [chunks + 1] exclusive prefix of their areas; offs[n_list] = pairs
@@ -90,7 +93,8 @@ struct TileDev {
 // tag is not the pass's means "no solid voxel".
 constexpr int kBeamTileW = 8, kBeamTileH = 4;
 constexpr int kBeamLevels = 16;  // queue counters (node levels of a 512^3 chunk: 8)
-constexpr int kBeamPyr = 7;      // bound pyramid levels (level 0: the tiles)
+constexpr int kBeamPyr = 7;      // bound pyramid levels (level 0: the tiles), at most 8
+static_assert(kBeamPyr <= 8, "a warp reads the pyramid levels with one lane each, reduced over 8 lanes");
 constexpr int kBeamViews = 128;  // views of one beam pass
 
 __host__ __device__ __forceinline__ uint32_t beam_level_offset(uint32_t tx, uint32_t ty, int L) {
@@ -135,6 +139,29 @@ struct BeamRead {
     const unsigned long long* bounds;
     uint32_t tag;
 };
+
+// The beam pass's bound pyramid of one W x H view as a casting kernel reads
+// it: per level, the offset of its first entry and its row width (computed
+// once on the host instead of per pixel).
+struct BeamLookup {
+    const unsigned long long* bounds;  // nullptr: no bounds
+    uint32_t tag;
+    uint32_t off[kBeamPyr], wl[kBeamPyr];
+};
+
+inline BeamLookup beam_lookup(const BeamRead* b, int W, int H) {
+    BeamLookup L;
+    std::memset(&L, 0, sizeof(L));
+    if (!b) return L;
+    L.bounds = b->bounds;
+    L.tag = b->tag;
+    const uint32_t tx = (uint32_t)(W + kBeamTileW - 1) / kBeamTileW, ty = (uint32_t)(H + kBeamTileH - 1) / kBeamTileH;
+    for (int l = 0; l < kBeamPyr; l++) {
+        L.off[l] = beam_level_offset(tx, ty, l);
+        L.wl[l] = (tx + (1u << l) - 1) >> l;
+    }
+    return L;
+}
 
 // Descriptor updates applied by a kernel on the rendering stream, so that a
 // frame sees every (chunk, LOD) change published before it and none after.
@@ -213,7 +240,7 @@ int aokk_beam_order(void* stream, int record);
 unsigned aokk_beam_grid(int sms);
 int aokk_ray_dirs(const aok::CamDev* c, float* dirs, void* stream);
 int aokk_tiles_frame(const aok::SceneDev* S, const aok::CamDev* C, const aok::ChunkRef* frame, const aok::TileDev* T,
-                     uint4* hit, float* t, int sms, void* stream);
+                     uint4* hit, float* t, int sms, void* stream, const aok::BeamRead* beam = nullptr);
 int aokk_patch_desc(aok::ChunkRef* desc, const aok::DescPatches* p, void* stream);
 int aokk_read_bw(const void* buf, size_t n16, int passes, uint32_t* sink, int sms, void* stream);
 // Batched: one selection launch over (view, chunk), then one persistent

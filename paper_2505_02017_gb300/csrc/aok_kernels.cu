@@ -105,29 +105,6 @@ __global__ void select_batch_kernel(const __grid_constant__ BatchParams P) {
     if (chunk < nch) select_one(v.scene, v.cam, v.frame, nullptr, nullptr, nullptr, chunk);
 }
 
-// The beam pass's bound pyramid of one W x H view as a casting kernel reads
-// it: per level, the offset of its first entry and its row width (computed
-// once on the host instead of per pixel).
-struct BeamLookup {
-    const unsigned long long* bounds;  // nullptr: no bounds
-    uint32_t tag;
-    uint32_t off[kBeamPyr], wl[kBeamPyr];
-};
-
-BeamLookup beam_lookup(const BeamRead* b, int W, int H) {
-    BeamLookup L;
-    std::memset(&L, 0, sizeof(L));
-    if (!b) return L;
-    L.bounds = b->bounds;
-    L.tag = b->tag;
-    const uint32_t tx = (uint32_t)(W + kBeamTileW - 1) / kBeamTileW, ty = (uint32_t)(H + kBeamTileH - 1) / kBeamTileH;
-    for (int l = 0; l < kBeamPyr; l++) {
-        L.off[l] = beam_level_offset(tx, ty, l);
-        L.wl[l] = (tx + (1u << l) - 1) >> l;
-    }
-    return L;
-}
-
 // beam_bound (aok_trace.cuh) with the pyramid's level table; 0 (no restart)
 // without bounds (a pass that found no usable projection for the view)
 __device__ __forceinline__ int32_t beam_bound_lut(const BeamLookup& b, int px, int py) {

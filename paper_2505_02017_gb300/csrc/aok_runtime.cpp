@@ -1094,15 +1094,16 @@ static int ensure_tiles(aok_ctx* ctx, uint32_t scene, int32_t W, int32_t H, int6
     const size_t tiles = (size_t)tx * ty, px = (size_t)W * H, n = (size_t)nch;
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t sz[] = {px * 16, tiles * 4, tiles * 4, tiles * 4, n * 16, n * 4, n * 4, n * 4, (n + 1) * 8,
-                         kTileStats * 8};
+                         kTileStats * 8, n * 4};
+    constexpr int kParts = (int)(sizeof(sz) / sizeof(sz[0]));
     size_t total = 0;
     for (size_t b : sz) total += al(b);
     void* block = nullptr;
     int st = dev_alloc(ctx, &block, total);
     if (st) return st;
     char* p = (char*)block;
-    char* q[10];
-    for (int i = 0; i < 10; i++) { q[i] = p; p += al(sz[i]); }
+    char* q[kParts];
+    for (int i = 0; i < kParts; i++) { q[i] = p; p += al(sz[i]); }
     TileDev& d = ts.dev;
     d.vis = (unsigned long long*)q[0];
     d.hiz_prev = (float*)q[1];
@@ -1114,6 +1115,7 @@ static int ensure_tiles(aok_ctx* ctx, uint32_t scene, int32_t W, int32_t H, int6
     d.list = (uint32_t*)q[7];
     d.offs = (unsigned long long*)q[8];
     d.stats = (unsigned long long*)q[9];
+    d.dfar = (int32_t*)q[10];
     d.tiles_x = tx;
     d.tiles_y = ty;
     cudaError_t e = cudaMemsetAsync(d.vis, 0xFF, px * 16, s);
@@ -1150,8 +1152,15 @@ int aok_render_tiles(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double
     SceneDev sd = scene_dev(sc);
     sc->select_gen++;
     st = aokk_select(&sd, &cd, sc->d_frame, nullptr, nullptr, nullptr, stream);
+    // the beam pass's bounds cull the pairs in front of every voxel a tile's
+    // rays can meet and restart the rays of the others (as in the march)
+    const BeamRead* beam = nullptr;
+    if (!st && beam_wanted(ctx, cd.W, cd.H)) {
+        st = run_beam(ctx, scene, sc, sd, cd, stream);
+        beam = &ctx->beam.read;
+    }
     if (!st) st = aokk_tiles_frame(&sd, &cd, sc->d_frame, &ctx->tiles.dev, (uint4*)frame->hit, frame->t,
-                                   ctx->sm_count, stream);
+                                   ctx->sm_count, stream, beam);
     if (st) return st == AOK_E_CUDA ? launch_failure(ctx) : st;
     std::swap(ctx->tiles.dev.hiz_prev, ctx->tiles.dev.hiz_next);  // this frame's depth culls the next one
     return AOK_OK;

@@ -22,7 +22,10 @@
 //
 // Pass 2 makes the result independent of the previous frame: a pair it culls
 // lies beyond every pixel's current hit in that tile, so it cannot hold a
-// nearer one.  Differences from the paper: the pair list is implicit (a
+// nearer one.  With the beam pass (aok_beam.cu) a half tile (8 x 4 pixels,
+// one beam tile) also skips the pairs whose chunk AABB lies wholly nearer
+// than its bound -- no voxel there can be met -- and its rays start each
+// remaining pair at the bound's restart plane, as in the march.  Differences from the paper: the pair list is implicit (a
 // prefix sum over the chunks' rectangle areas, searched by the marching warps)
 // instead of an appended TileInfo buffer with indirect dispatch; the key is
 // widened; each marching warp takes half a tile (32 pixels).
@@ -98,6 +101,7 @@ struct Entry {
     int e;
     int32_t Ne;
     int32_t Oloc[3];
+    int32_t Hi[3];  // exit plane numerators of the region
     uint32_t order;
 };
 
@@ -117,6 +121,7 @@ __device__ __forceinline__ bool enter_region(const SceneDev& S, const CamDev& C,
         Lo[a] = (cc << cs) - Ow;
         Hi[a] = ((cc + 1) << cs) - Ow;
         en.Oloc[a] = -Lo[a];
+        en.Hi[a] = Hi[a];
     }
 #pragma unroll
     for (int a = 0; a < 3; a++) {
@@ -168,10 +173,14 @@ __device__ __forceinline__ bool aabb_pass(const SceneDev& S, const CamDev& C, co
 }
 
 // One pixel of a pair: 0 = region not entered, 1 = traced, 2 = skipped (the
-// pixel already holds a hit nearer than the region's entry).
-template <bool FAST>
+// pixel already holds a hit nearer than the region's entry, or the beam
+// bound Dn puts every voxel the ray can meet past the region).  Dn > 0: the
+// ray starts at the bound's restart plane when that lies later than the
+// region's entry (trace_pixel_t's beam restart, within one region).
+template <bool FAST, bool BEAM>
 __device__ __forceinline__ int pair_pixel(const SceneDev& S, const CamDev& C, const ChunkRef& ref, uint32_t chunk,
-                                          const RayState& r, size_t pix, unsigned long long* __restrict__ vis) {
+                                          const RayState& r, size_t pix, unsigned long long* __restrict__ vis,
+                                          int32_t Dn) {
     int32_t u[3];
     region_coords(S, chunk, u);
     Entry en;
@@ -179,9 +188,32 @@ __device__ __forceinline__ int pair_pixel(const SceneDev& S, const CamDev& C, co
     unsigned long long* rec = vis + 2 * pix;
     const unsigned long long cur = __ldcg(rec);
     if (cur != kNoKey && en.e < 3 && t_key(en.Ne, r.d[en.e]) > (uint32_t)(cur >> 32)) return 2;
+    int e = en.e;
+    int32_t Ne = en.Ne;
+    if (BEAM && Dn > 0) {
+        // the last integer plane of the dominant axis crossed before the ray's
+        // L-inf distance reaches Dn; at or past the region's exit: no hit here
+        int as = 0;
+        if (fabsf(r.d[1]) > fabsf(r.d[as])) as = 1;
+        if (fabsf(r.d[2]) > fabsf(r.d[as])) as = 2;
+        const int32_t Wf = S.grid[as] << (S.mlog + kFix);
+        const int32_t Ow = ((r.mir >> as) & 1u) ? Wf - C.O[as] : C.O[as];
+        const long long kp = ((long long)Dn - 1 + Ow) >> kFix;
+        const long long Nl = (kp << kFix) - Ow;
+        if (Nl >= (long long)en.Hi[as]) return 2;
+        const int32_t me = e < 3 ? r.m[e] : 1, Ee = e < 3 ? r.E[e] : 0;
+        if (Nl > 0 && (e == 3 || tltf<FAST>(Ne, me, (int32_t)Nl, r.m[as], r.E[as] - Ee))) {
+#pragma unroll
+            for (int a = 0; a < 3; a++)
+                if (a != as && r.d[a] != 0.0f && !tltf<FAST>((int32_t)Nl, r.m[as], en.Hi[a], r.m[a], r.E[a] - r.E[as]))
+                    return 2;  // the ray leaves the region no later than the restart point
+            e = as;
+            Ne = (int32_t)Nl;
+        }
+    }
     HitRec hit;
     Counters cnt = {0, 0, 0};
-    if (trace_chunk<FAST, false>(S, ref, r, en.Oloc, en.e, en.Ne, hit, cnt) &&
+    if (trace_chunk<FAST, false, false, BEAM>(S, ref, r, en.Oloc, e, Ne, hit, cnt) &&
         (lowest_entry_face<FAST>(r, en.Oloc, (int)ref.lod, hit), within_view(S, r, hit))) {
         const uint32_t tk = hit.e < 3 ? t_key(hit.Ne, r.d[hit.e]) : 0u;
         const int n = (int)ref.lod;
@@ -220,9 +252,16 @@ __global__ void tc_rect_kernel(SceneDev S, CamDev C, const ChunkRef* __restrict_
     uint32_t area = 0;
     int4 rc = make_int4(0, 0, 0, 0);
     float dm = 0.0f;
+    int32_t far = 0;
     if (ref.root != kNone) {
         int32_t u[3];
         region_coords(S, (uint32_t)chunk, u);
+#pragma unroll
+        for (int a = 0; a < 3; a++) {  // exact: |values| < 2^30
+            const int32_t l = (((u[a] << S.mlog) + (int32_t)ref.aabb[a]) << kFix) - C.O[a];
+            const int32_t h = (((u[a] << S.mlog) + (int32_t)ref.aabb[3 + a]) << kFix) - C.O[a];
+            far = max(far, max(abs(l), abs(h)));
+        }
         double lo[3], hi[3], d2 = 0.0;
 #pragma unroll
         for (int a = 0; a < 3; a++) {
@@ -263,6 +302,7 @@ __global__ void tc_rect_kernel(SceneDev S, CamDev C, const ChunkRef* __restrict_
     }
     T.rect[chunk] = rc;
     T.dmin[chunk] = dm;
+    T.dfar[chunk] = far;
     T.area[chunk] = area;
 }
 
@@ -316,9 +356,9 @@ __global__ void __launch_bounds__(1024) tc_scan_kernel(int nch, TileDev T) {
 // pairs the previous frame's Hi-Z keeps, PASS 2 those it culled and this
 // frame's keeps.
 // ---------------------------------------------------------------------------
-template <int PASS>
+template <int PASS, bool BEAM>
 __global__ void __launch_bounds__(128, 7) tc_cast_kernel(SceneDev S, CamDev C, const ChunkRef* __restrict__ frame,
-                                                      TileDev T) {
+                                                      TileDev T, const BeamLookup beam) {
     const uint32_t n_list = (uint32_t)T.stats[kStList];
     if (n_list == 0) return;
     const unsigned long long n_items = 2ull * T.offs[n_list];
@@ -347,14 +387,21 @@ __global__ void __launch_bounds__(128, 7) tc_cast_kernel(SceneDev S, CamDev C, c
             if (dm <= T.hiz_prev[tile]) continue;  // marched in pass 1
             if (dm > T.hiz[tile]) { culled++; continue; }
         }
+        const int by = ty * 2 + (int)(item & 1);  // the half tile: one beam tile
+        if (by * 4 >= C.H) continue;              // below the last row
+        int32_t Dn = 0;
+        if (BEAM) {
+            Dn = warp_beam_bound(beam, (uint32_t)tx, (uint32_t)by, lane);
+            if (Dn > T.dfar[chunk]) { culled++; continue; }  // wholly nearer than every voxel its rays meet
+        }
         traced++;
-        const int px = tx * 8 + (lane & 7), py = ty * 8 + (int)(item & 1) * 4 + (lane >> 3);
+        const int px = tx * 8 + (lane & 7), py = by * 4 + (lane >> 3);
         if (px < C.W && py < C.H) {
             const ChunkRef ref = frame[chunk];
             RayState r;
             const size_t pix = (size_t)py * C.W + px;
-            const int res = make_ray(C, px, py, r) ? pair_pixel<true>(S, C, ref, chunk, r, pix, T.vis)
-                                                   : pair_pixel<false>(S, C, ref, chunk, r, pix, T.vis);
+            const int res = make_ray(C, px, py, r) ? pair_pixel<true, BEAM>(S, C, ref, chunk, r, pix, T.vis, Dn)
+                                                   : pair_pixel<false, BEAM>(S, C, ref, chunk, r, pix, T.vis, Dn);
             pix_traced += res == 1;
             pix_skipped += res == 2;
             if (res == 3) atomicAdd(&T.stats[kStCasExhausted], 1ull);
@@ -390,9 +437,11 @@ __global__ void __launch_bounds__(256) tc_hiz_kernel(CamDev C, TileDev T) {
             if (key != kNoKey) {
                 float d[3];
                 ray_dir(C, px, py, d);
-                const double dn = sqrt((double)d[0] * d[0] + (double)d[1] * d[1] + (double)d[2] * d[2]);
-                const double t_up = __longlong_as_double((long long)(((key >> 32) + 1ull) << 32));
-                dist = __double2float_ru(t_up * dn * (1.0 + 1e-12));
+                // upper bounds in FP32 with upward rounding: |d| and t (the key's next value)
+                const float dn = __fsqrt_ru(__fadd_ru(__fadd_ru(__fmul_ru(d[0], d[0]), __fmul_ru(d[1], d[1])),
+                                                      __fmul_ru(d[2], d[2])));
+                const float t_up = __double2float_ru(__longlong_as_double((long long)(((key >> 32) + 1ull) << 32)));
+                dist = __fmul_ru(t_up, dn);
             }
             m = fmaxf(m, dist);
         }
@@ -416,14 +465,14 @@ __global__ void __launch_bounds__(128) tc_resolve_kernel(SceneDev S, CamDev C, c
     if (px < C.W && py < C.H) {
         const size_t pix = (size_t)py * C.W + px;
         const ulonglong2 rec = __ldcg(reinterpret_cast<const ulonglong2*>(T.vis) + pix);
-        reinterpret_cast<ulonglong2*>(T.vis)[pix] = make_ulonglong2(kNoKey, kNoKey);  // re-armed for the next frame
         if (rec.x == kNoKey) {
             emit_miss(out_hit, out_t, pix);
             dist_up = __int_as_float(0x7F800000);
         } else {
             // the output record of emit_hit, rebuilt from the payload and the ray
             RayState r;
-            make_ray(C, px, py, r);
+            ray_dir(C, px, py, r.d);
+            r.mir = (r.d[0] < 0.0f ? 1u : 0u) | (r.d[1] < 0.0f ? 2u : 0u) | (r.d[2] < 0.0f ? 4u : 0u);
             const unsigned long long pay = rec.y;
             const uint32_t x = (uint32_t)(pay & 0x1FFFFu), y = (uint32_t)((pay >> 17) & 0x1FFFFu),
                            z = (uint32_t)((pay >> 34) & 0x1FFFFu);
@@ -459,26 +508,31 @@ int tiles_status(cudaError_t e) { return aokk_status(e); }
 extern "C" {
 
 int aokk_tiles_frame(const SceneDev* S, const CamDev* C, const ChunkRef* frame, const TileDev* T, uint4* hit, float* t,
-                     int sms, void* stream) {
+                     int sms, void* stream, const BeamRead* beam) {
     const cudaStream_t s = (cudaStream_t)stream;
     const int nch = S->grid[0] * S->grid[1] * S->grid[2];
     const int tiles = T->tiles_x * T->tiles_y;
     static int per_sm[2] = {0, 0};
     if (!per_sm[0]) {
         int a = 0, b = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, tc_cast_kernel<1>, 128, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, tc_cast_kernel<2>, 128, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, tc_cast_kernel<1, true>, 128, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, tc_cast_kernel<2, true>, 128, 0);
         per_sm[1] = b > 0 ? b : 1;
         per_sm[0] = a > 0 ? a : 1;
     }
+    const BeamLookup bl = beam_lookup(beam && beam->bounds ? beam : nullptr, C->W, C->H);
     cudaError_t e = cudaMemsetAsync(T->hiz_next, 0, (size_t)tiles * sizeof(float), s);
     if (e != cudaSuccess) return AOK_E_CUDA;
     tc_rect_kernel<<<(nch + 255) / 256, 256, 0, s>>>(*S, *C, frame, *T);
     tc_scan_kernel<<<1, 1024, 0, s>>>(nch, *T);
-    tc_cast_kernel<1><<<sms * per_sm[0], 128, 0, s>>>(*S, *C, frame, *T);
+    if (bl.bounds) tc_cast_kernel<1, true><<<sms * per_sm[0], 128, 0, s>>>(*S, *C, frame, *T, bl);
+    else tc_cast_kernel<1, false><<<sms * per_sm[0], 128, 0, s>>>(*S, *C, frame, *T, bl);
     tc_hiz_kernel<<<(tiles + 7) / 8, 256, 0, s>>>(*C, *T);
-    tc_cast_kernel<2><<<sms * per_sm[1], 128, 0, s>>>(*S, *C, frame, *T);
+    if (bl.bounds) tc_cast_kernel<2, true><<<sms * per_sm[1], 128, 0, s>>>(*S, *C, frame, *T, bl);
+    else tc_cast_kernel<2, false><<<sms * per_sm[1], 128, 0, s>>>(*S, *C, frame, *T, bl);
     tc_resolve_kernel<<<dim3((C->W + 15) / 16, (C->H + 7) / 8), 128, 0, s>>>(*S, *C, frame, *T, hit, t);
+    e = cudaMemsetAsync(T->vis, 0xFF, (size_t)C->W * C->H * 16, s);  // re-armed for the next frame
+    if (e != cudaSuccess) return AOK_E_CUDA;
     return tiles_status(cudaGetLastError());
 }
 

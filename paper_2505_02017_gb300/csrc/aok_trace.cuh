@@ -488,6 +488,21 @@ __device__ __forceinline__ int32_t beam_bound(const unsigned long long* __restri
     return (uint32_t)(v >> 32) == tag ? (int32_t)(uint32_t)v : INT_MAX;
 }
 
+// The same bound for the 8 x 4 tile (x, y) of a warp, called by all 32 lanes
+// with the same tile: lane L reads level L of the pyramid through the level
+// table and a butterfly takes the minimum.  The tile must lie in the view.
+__device__ __forceinline__ int32_t warp_beam_bound(const BeamLookup& b, uint32_t x, uint32_t y, int lane) {
+    uint32_t off = 0, wl = 0;
+#pragma unroll
+    for (int L = 0; L < kBeamPyr; L++)
+        if (lane == L) { off = b.off[L]; wl = b.wl[L]; }
+    unsigned long long v = lane < kBeamPyr ? __ldcg(b.bounds + off + (y >> lane) * wl + (x >> lane)) : ~0ull;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) v = min(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+    v = __shfl_sync(0xFFFFFFFFu, v, 0);  // lanes 0..7 hold the minimum
+    return (uint32_t)(v >> 32) == b.tag ? (int32_t)(uint32_t)v : INT_MAX;
+}
+
 // Pixel ray in the mirrored frame.  Returns true for a FAST ray: the non-zero
 // |d| exponents span <= 6, mantissas shifted to a common exponent (E = 0),
 // zero components m = 0.

@@ -88,6 +88,27 @@ def test_small_worlds_equal_march_and_oracle(ctx, case):
     compare(decode(*first), orc_ref)
 
 
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_small_worlds_with_beam_bounds(ctx, case):
+    """The beam pass on for every frame size: its bounds cull pairs wholly
+    nearer than every voxel a half tile's rays can meet and restart the rays
+    of the others; the frames still equal the march's (which restarts too)
+    and the oracle's."""
+    spec, camf, tau = CASES[case]
+    w, sc, S = scene_for(ctx, spec)
+    cam = camf(w)
+    aok.beam_tune(ctx, min_pixels=0)
+    try:
+        ref = march(ctx, sc, cam, tau)
+        aok.tiles_forget(ctx)
+        first, _ = tiles(ctx, sc, cam, tau)
+        again, _ = tiles(ctx, sc, cam, tau)
+    finally:
+        aok.beam_tune(ctx)
+    assert same(ref, first) and same(ref, again)
+    compare(decode(*first), S.cast(cam, S.select(cam, tau), view_dist=spec.view_dist))
+
+
 def test_moving_camera_with_history(ctx):
     """Hi-Z of the previous pose culls in pass 1; pass 2 repairs what it culled wrongly."""
     spec = MED64
@@ -150,6 +171,14 @@ def test_city4096_1080p_equals_march(ctx):
     out2, st2 = tiles(ctx, sc, cam, 1.0)
     assert same(ref, out2)
     assert st2["items_culled_1"] > 0
+    aok.set_beam(ctx, False)  # the pipeline without the beam pass's bounds
+    try:
+        aok.tiles_forget(ctx)
+        out3, st3 = tiles(ctx, sc, cam, 1.0)
+    finally:
+        aok.set_beam(ctx, True)
+    assert same(ref, out3)
+    assert st3["items_marched_1"] > st1["items_marched_1"]  # the bounds culled pairs
     # a far view with LOD 1-3 surfaces
     cam = sg.ground_camera(w, 8, 640, 360, z_lo=600, z_hi=900, pitch=(-20.0, -8.0))
     assert same(march(ctx, sc, cam, 1.0 / 3.0), tiles(ctx, sc, cam, 1.0 / 3.0)[0])
