@@ -244,66 +244,84 @@ __device__ __forceinline__ int pair_pixel(const SceneDev& S, const CamDev& C, co
 // ---------------------------------------------------------------------------
 // 1. tile selection: per chunk region, its tile rectangle and depth
 // ---------------------------------------------------------------------------
-__global__ void tc_rect_kernel(SceneDev S, CamDev C, const ChunkRef* __restrict__ frame, TileDev T) {
+// Eight lanes per region (lane k projects corner k of its AABB; FP64 is a
+// slow pipe on this GPU, so the corners are spread over more SMs).
+__global__ void __launch_bounds__(128) tc_rect_kernel(SceneDev S, CamDev C, const ChunkRef* __restrict__ frame,
+                                                      TileDev T) {
     const int nch = S.grid[0] * S.grid[1] * S.grid[2];
-    const int chunk = blockIdx.x * blockDim.x + threadIdx.x;
-    if (chunk >= nch) return;
-    const ChunkRef ref = frame[chunk];
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int chunk = tid >> 3, k = tid & 7;
+    const bool valid = chunk < nch;
+    const ChunkRef ref = valid ? frame[chunk] : ChunkRef{kNone, 0, 0, {0, 0, 0, 0, 0, 0}, 0};
     uint32_t area = 0;
     int4 rc = make_int4(0, 0, 0, 0);
     float dm = 0.0f;
     int32_t far = 0;
-    if (ref.root != kNone) {
+    // the group's lanes agree on every branch below (same region)
+    const bool live = valid && ref.root != kNone;
+    double lo[3] = {0.0, 0.0, 0.0}, hi[3] = {0.0, 0.0, 0.0};
+    if (live) {
         int32_t u[3];
         region_coords(S, (uint32_t)chunk, u);
+        double d2 = 0.0;
 #pragma unroll
         for (int a = 0; a < 3; a++) {  // exact: |values| < 2^30
             const int32_t l = (((u[a] << S.mlog) + (int32_t)ref.aabb[a]) << kFix) - C.O[a];
             const int32_t h = (((u[a] << S.mlog) + (int32_t)ref.aabb[3 + a]) << kFix) - C.O[a];
             far = max(far, max(abs(l), abs(h)));
-        }
-        double lo[3], hi[3], d2 = 0.0;
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
             lo[a] = (double)((u[a] << S.mlog) + ref.aabb[a]) - (double)C.of[a];
             hi[a] = (double)((u[a] << S.mlog) + ref.aabb[3 + a]) - (double)C.of[a];
             const double q = fmax(fmax(lo[a], -hi[a]), 0.0);
             d2 += q * q;
         }
         // every hit point of the region lies in the AABB: its distance is >= this
-        dm = __double2float_rd(sqrt(d2) * (1.0 - 1e-12));
-        if (!(S.view_dist > 0.0f && dm > S.view_dist)) {
-            // screen rectangle of the 8 corners (pixel-centre coordinates), 2 px margin;
-            // a corner near or behind the camera plane makes it the whole screen
-            const double th = C.tan_half, asp = (double)C.W / (double)C.H;
-            double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
-            bool full = false;
-            for (int k = 0; k < 8 && !full; k++) {
-                const double p0 = (k & 1) ? hi[0] : lo[0], p1 = (k & 2) ? hi[1] : lo[1], p2 = (k & 4) ? hi[2] : lo[2];
-                const double xc = C.R[0] * p0 + C.R[3] * p1 + C.R[6] * p2;
-                const double yc = C.R[1] * p0 + C.R[4] * p1 + C.R[7] * p2;
-                const double zc = -(C.R[2] * p0 + C.R[5] * p1 + C.R[8] * p2);
-                if (zc < 1e-3 * (fabs(p0) + fabs(p1) + fabs(p2) + 1.0)) { full = true; break; }
-                const double px = (xc / zc / (th * asp) + 1.0) * 0.5 * C.W - 0.5;
-                const double py = (1.0 - yc / zc / th) * 0.5 * C.H - 0.5;
-                x0 = fmin(x0, px); x1 = fmax(x1, px);
-                y0 = fmin(y0, py); y1 = fmax(y1, py);
-            }
-            if (full) {
-                rc = make_int4(0, 0, T.tiles_x, T.tiles_y);
-            } else {
-                rc.x = (int)fmax(floor((x0 - 2.0) / 8.0), 0.0);
-                rc.y = (int)fmax(floor((y0 - 2.0) / 8.0), 0.0);
-                rc.z = (int)fmin(floor((x1 + 2.0) / 8.0) + 1.0, (double)T.tiles_x);
-                rc.w = (int)fmin(floor((y1 + 2.0) / 8.0) + 1.0, (double)T.tiles_y);
-            }
-            if (rc.z > rc.x && rc.w > rc.y) area = (uint32_t)(rc.z - rc.x) * (uint32_t)(rc.w - rc.y);
+        if (k == 0) dm = __double2float_rd(sqrt(d2) * (1.0 - 1e-12));
+    }
+    dm = __shfl_sync(0xFFFFFFFFu, dm, 0, 8);
+    const bool project = live && !(S.view_dist > 0.0f && dm > S.view_dist);
+    // screen position of corner k (pixel-centre coordinates); a corner near or
+    // behind the camera plane makes the rectangle the whole screen
+    double px = 0.0, py = 0.0;
+    bool full = false;
+    if (project) {
+        const double th = C.tan_half, asp = (double)C.W / (double)C.H;
+        const double p0 = (k & 1) ? hi[0] : lo[0], p1 = (k & 2) ? hi[1] : lo[1], p2 = (k & 4) ? hi[2] : lo[2];
+        const double xc = C.R[0] * p0 + C.R[3] * p1 + C.R[6] * p2;
+        const double yc = C.R[1] * p0 + C.R[4] * p1 + C.R[7] * p2;
+        const double zc = -(C.R[2] * p0 + C.R[5] * p1 + C.R[8] * p2);
+        if (zc < 1e-3 * (fabs(p0) + fabs(p1) + fabs(p2) + 1.0)) {
+            full = true;
+        } else {
+            px = (xc / zc / (th * asp) + 1.0) * 0.5 * C.W - 0.5;
+            py = (1.0 - yc / zc / th) * 0.5 * C.H - 0.5;
         }
     }
-    T.rect[chunk] = rc;
-    T.dmin[chunk] = dm;
-    T.dfar[chunk] = far;
-    T.area[chunk] = area;
+    double x0 = full ? 1e300 : px, x1 = full ? -1e300 : px, y0 = full ? 1e300 : py, y1 = full ? -1e300 : py;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        x0 = fmin(x0, __shfl_xor_sync(0xFFFFFFFFu, x0, o, 8));
+        x1 = fmax(x1, __shfl_xor_sync(0xFFFFFFFFu, x1, o, 8));
+        y0 = fmin(y0, __shfl_xor_sync(0xFFFFFFFFu, y0, o, 8));
+        y1 = fmax(y1, __shfl_xor_sync(0xFFFFFFFFu, y1, o, 8));
+        full = full || __shfl_xor_sync(0xFFFFFFFFu, (int)full, o, 8);
+    }
+    if (project) {
+        if (full) {
+            rc = make_int4(0, 0, T.tiles_x, T.tiles_y);
+        } else {  // 2 px margin
+            rc.x = (int)fmax(floor((x0 - 2.0) / 8.0), 0.0);
+            rc.y = (int)fmax(floor((y0 - 2.0) / 8.0), 0.0);
+            rc.z = (int)fmin(floor((x1 + 2.0) / 8.0) + 1.0, (double)T.tiles_x);
+            rc.w = (int)fmin(floor((y1 + 2.0) / 8.0) + 1.0, (double)T.tiles_y);
+        }
+        if (rc.z > rc.x && rc.w > rc.y) area = (uint32_t)(rc.z - rc.x) * (uint32_t)(rc.w - rc.y);
+    }
+    if (valid && k == 0) {
+        T.rect[chunk] = rc;
+        T.dmin[chunk] = dm;
+        T.dfar[chunk] = far;
+        T.area[chunk] = area;
+    }
 }
 
 // Compacts the regions with pairs (ascending) and their exclusive area prefix
@@ -523,7 +541,7 @@ int aokk_tiles_frame(const SceneDev* S, const CamDev* C, const ChunkRef* frame, 
     const BeamLookup bl = beam_lookup(beam && beam->bounds ? beam : nullptr, C->W, C->H);
     cudaError_t e = cudaMemsetAsync(T->hiz_next, 0, (size_t)tiles * sizeof(float), s);
     if (e != cudaSuccess) return AOK_E_CUDA;
-    tc_rect_kernel<<<(nch + 255) / 256, 256, 0, s>>>(*S, *C, frame, *T);
+    tc_rect_kernel<<<(8 * nch + 127) / 128, 128, 0, s>>>(*S, *C, frame, *T);
     tc_scan_kernel<<<1, 1024, 0, s>>>(nch, *T);
     if (bl.bounds) tc_cast_kernel<1, true><<<sms * per_sm[0], 128, 0, s>>>(*S, *C, frame, *T, bl);
     else tc_cast_kernel<1, false><<<sms * per_sm[0], 128, 0, s>>>(*S, *C, frame, *T, bl);
