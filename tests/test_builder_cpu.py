@@ -221,3 +221,61 @@ def test_chunk_source_blob_cache():
     B.aokb_source_release(cached, h1)
     B.aokb_source_destroy(plain)
     B.aokb_source_destroy(cached)
+
+
+def test_chunk_source_cache_under_concurrent_loaders():
+    """Eight threads asking the cached source for overlapping (chunk, LOD)s at
+    once, as the streamer's loaders do, with a budget small enough to evict
+    while blobs are held: every blob equals the uncached build."""
+    import threading
+    B = aok.blib()
+    vp = ctypes.c_void_p
+    B.aokb_source_build.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32,
+                                    ctypes.POINTER(aok.ChunkBlob), ctypes.POINTER(vp)]
+    B.aokb_source_release.argtypes = [vp, vp]
+    spec = MED64
+    w = sg.World(spec)
+    gx, gy, gz = spec.grid
+    keys = [((x, y, z), lod) for x in range(gx) for y in range(gy) for z in range(gz) for lod in range(spec.n_lods)]
+    plain = B.aokb_source_create(w.handle, spec.chunk, spec.n_lods)
+    ref = {}
+    for c, lod in keys:
+        b, h = aok.ChunkBlob(), vp()
+        assert B.aokb_source_build(plain, *c, lod, ctypes.byref(b), ctypes.byref(h)) == 0
+        ref[(c, lod)] = (blob_arrays(b), b.root, tuple(b.aabb_lo), tuple(b.aabb_hi))
+        B.aokb_source_release(plain, h)
+    B.aokb_source_destroy(plain)
+    cached = B.aokb_source_create(w.handle, spec.chunk, spec.n_lods)
+    B.aokb_source_set_cache(cached, 256 << 10)  # a few blobs: evictions while others are held
+    errors = []
+
+    def loader(seed):
+        rng = np.random.default_rng(seed)
+        held = []
+        for _ in range(60):
+            c, lod = keys[int(rng.integers(len(keys)))]
+            b, h = aok.ChunkBlob(), vp()
+            if B.aokb_source_build(cached, *c, lod, ctypes.byref(b), ctypes.byref(h)) != 0:
+                errors.append(("build", c, lod))
+                continue
+            held.append((c, lod, b, h))
+            if len(held) > 3:  # keep a few blobs alive across later calls
+                c0, l0, b0, h0 = held.pop(0)
+                r = ref[(c0, l0)]
+                got = (blob_arrays(b0), b0.root, tuple(b0.aabb_lo), tuple(b0.aabb_hi))
+                if not (all(np.array_equal(x, y) for x, y in zip(got[0], r[0])) and got[1:] == r[1:]):
+                    errors.append(("mismatch", c0, l0))
+                B.aokb_source_release(cached, h0)
+        for c0, l0, b0, h0 in held:
+            B.aokb_source_release(cached, h0)
+
+    th = [threading.Thread(target=loader, args=(s,)) for s in range(8)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    a = (ctypes.c_uint64 * 4)()
+    B.aokb_source_stats(cached, ctypes.byref(a))
+    B.aokb_source_destroy(cached)
+    assert not errors, errors[:5]
+    assert a[0] > 0 and a[1] > 0 and a[2] <= 256 << 10  # hits, builds, the budget kept
