@@ -58,6 +58,7 @@ using namespace aok;
 namespace {
 
 constexpr int kBeamThreads = 256;      // block size of the cooperative walk
+constexpr int kBeamNarrowThreads = 128;  // block size of the walk that shares SMs with a cast
 constexpr int kBeamBlocksPerSM = 2;    // blocks per SM of the full grid (walks over many regions)
 constexpr uint32_t kWideWalkRegions = 4096;  // above this many regions a pass takes the full grid; below,
                                              // one block per SM, which can start beside a running cast
@@ -253,7 +254,7 @@ __device__ __forceinline__ uint32_t node_children(const SceneDev& S, uint32_t no
 // chunk regions; every lane of a warp runs the same iterations (the queue
 // reservation is warp-wide).  Bounds carry the pass's tag, so nothing has to
 // be reset before the walk or folded after it.
-__global__ void __launch_bounds__(kBeamThreads) beam_kernel(const __grid_constant__ BeamBatch P) {
+__device__ __forceinline__ void beam_walk(const BeamBatch& P) {
     cg::grid_group g = cg::this_grid();
     __shared__ uint32_t hist[kBeamLevels];
     const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
@@ -340,6 +341,15 @@ __global__ void __launch_bounds__(kBeamThreads) beam_kernel(const __grid_constan
     __syncthreads();
     if (threadIdx.x < kBeamLevels && hist[threadIdx.x]) atomicAdd(&P.hist[threadIdx.x], hist[threadIdx.x]);
 }
+
+__global__ void __launch_bounds__(kBeamThreads) beam_kernel(const __grid_constant__ BeamBatch P) { beam_walk(P); }
+
+// The same walk as one block of kBeamNarrowThreads per SM with at most 80
+// registers: it fits beside six blocks of a running cast (7 x 128 threads x
+// 72 registers per SM), so a pipelined frame's pass can start on an SM as
+// soon as one casting block of the frame before retires there instead of
+// after the cast.  Alone it is slower (half the threads).
+__global__ void __maxnreg__(80) beam_kernel_narrow(const __grid_constant__ BeamBatch P) { beam_walk(P); }
 
 }  // namespace
 
@@ -442,7 +452,7 @@ int aokk_beam_order(void* stream, int record) {
     return aokk_status(e);
 }
 
-int aokk_beam_run(const BeamBatch* P, unsigned grid, void* stream) {
+int aokk_beam_run(const BeamBatch* P, unsigned grid, void* stream, int narrow) {
     const cudaStream_t st = (cudaStream_t)stream;
     if (P->n_views == 0) return AOK_OK;
     int dev = -1;
@@ -455,8 +465,14 @@ int aokk_beam_run(const BeamBatch* P, unsigned grid, void* stream) {
     // queue counts and the walk histogram (cnt and hist are adjacent)
     if (e == cudaSuccess) e = cudaMemsetAsync(P->cnt, 0, 2 * kBeamLevels * sizeof(uint32_t), st);
     void* args[] = {(void*)P};
-    const unsigned g = P->n_regions > kWideWalkRegions ? grid : (grid + kBeamBlocksPerSM - 1) / kBeamBlocksPerSM;
-    if (e == cudaSuccess) e = cudaLaunchCooperativeKernel((const void*)beam_kernel, g, kBeamThreads, args, 0, st);
+    const bool wide = P->n_regions > kWideWalkRegions;
+    const unsigned g = wide ? grid : (grid + kBeamBlocksPerSM - 1) / kBeamBlocksPerSM;
+    if (e == cudaSuccess) {
+        if (narrow && !wide)  // one narrow block per SM
+            e = cudaLaunchCooperativeKernel((const void*)beam_kernel_narrow, g, kBeamNarrowThreads, args, 0, st);
+        else
+            e = cudaLaunchCooperativeKernel((const void*)beam_kernel, g, kBeamThreads, args, 0, st);
+    }
     if (e == cudaSuccess) e = cudaEventRecord(g_beam_done[dev], st);
     return aokk_status(e);
 }

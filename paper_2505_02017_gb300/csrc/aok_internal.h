@@ -226,10 +226,12 @@ int aokk_cast(const aok::SceneDev* s, const aok::CamDev* c, const aok::ChunkRef*
               uint32_t* counts, void* stream, const aok::CheckDev* ck, const aok::BeamRead* beam = nullptr);
 // Beam pass (aok_beam.cu).  aokk_beam_view fills a view's projection (false:
 // the camera matrix has no usable inverse; leave the view out, it casts
-// without bounds); aokk_beam_run zeroes P's counters and launches the pass.
+// without bounds); aokk_beam_run zeroes P's counters and launches the pass
+// (narrow: as one 128-thread block per SM that fits beside a running cast,
+// for walks over at most 4096 regions; the pipelined host frames use it).
 bool aokk_beam_view(const aok::SceneDev* S, const aok::CamDev* C, const aok::ChunkRef* frame,
                     unsigned long long* bounds, aok::BeamView* out);
-int aokk_beam_run(const aok::BeamBatch* P, unsigned grid, void* stream);
+int aokk_beam_run(const aok::BeamBatch* P, unsigned grid, void* stream, int narrow = 0);
 // The pass as a graph node (kernel + counter memset) and the per-device pass
 // order around a graph launch (record = 0: wait for the previous pass before;
 // 1: mark the end of the launch as the point the next pass waits for).

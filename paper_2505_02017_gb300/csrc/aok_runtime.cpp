@@ -1393,7 +1393,7 @@ static int pipe_render(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, doub
             rd.bounds = sl.bounds;
             rd.tag = tag;
         }
-        st = aokk_beam_run(P, ctx->beam.grid, p.prep);
+        st = aokk_beam_run(P, ctx->beam.grid, p.prep, 1);  // beside the previous frame's cast
         if (st) return launch_failure(ctx);
     }
     cudaError_t e = cudaEventRecord(sl.prepped, p.prep);
