@@ -1,7 +1,9 @@
 #!/usr/bin/env python3
 """Benchmark: primary rays/s of the single-view 1920x1080 render of the
 4096^3 city world (8^3 chunks of 512^3, 4 LODs, LOD threshold 1 px), one
-step = Eq. 1 selection + visibility + per-pixel first-hit cast of one frame.
+step = Eq. 1 selection + visibility + per-pixel first-hit cast of one frame
+(with the beam pass on, the selection is the first step of the pass's walk,
+one launch; then the casting launch).
 
 Prints one JSON line.  `value` is device time (CUDA events on the launch
 stream, L2 flushed between steps, scene resident in HBM); `e2e` is the same
@@ -265,8 +267,8 @@ def bench_batched(aok, ctx, scene, world, flush, reps=5):
 def bench_walk(aok, ctx, scene, world, flush, n_poses=120):
     """The benchmark frame's metric along a moving camera: a path of poses at
     walker height through the city (1920x1080, tau = 1 px).  Device time: per
-    pose the selection, beam pass and cast on one stream, L2 flushed before
-    each pose.  End to end: the same poses through aok_render_host_async, every
+    pose the beam pass that selects first (aok_select_beam) and the cast on
+    one stream, L2 flushed before each pose.  End to end: the same poses through aok_render_host_async, every
     frame copied to pinned host memory."""
     import torch
     cams = sg.path_cameras(world, 106, n_poses, W, H, n_waypoints=6, span=2500.0, z_lo=64.0, z_hi=400.0,
@@ -282,9 +284,7 @@ def bench_walk(aok, ctx, scene, world, flush, n_poses=120):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        aok.select_chunks(ctx, scene, cam, TAU, stream=stream)
-        if BEAM_DEFAULT:
-            aok.beam_selected(ctx, scene, cam, stream=stream)
+        aok.select_beam(ctx, scene, cam, TAU, stream=stream)
         aok.cast_selected(ctx, scene, cam, hit, t, stream=stream)
         e1.record(stream)
         e1.synchronize()
@@ -863,8 +863,10 @@ def main():
         aok.render(ctx, scene, cam, TAU, hit, t)
     torch.cuda.synchronize()
 
-    # ---- timed: K steps, L2 flushed between steps, events around select, beam pass and cast ----
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    # ---- timed: K steps, L2 flushed between steps; a step is the beam pass that
+    # selects the frame table as its first step (aok_select_beam; the selection
+    # kernel alone when the pass is off), then the cast, events around each ----
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     clocks = Clocks(dev)
     if dist:
         dist.barrier()
@@ -875,20 +877,31 @@ def main():
     for k in range(args.steps):
         flush.zero_()
         ev[k][0].record(stream)
-        aok.select_chunks(ctx, scene, cam, TAU, stream=stream)
+        aok.select_beam(ctx, scene, cam, TAU, stream=stream)
         ev[k][1].record(stream)
-        if BEAM_DEFAULT:
-            aok.beam_selected(ctx, scene, cam, stream=stream)
-        ev[k][2].record(stream)
         aok.cast_selected(ctx, scene, cam, hit, t, stream=stream)
-        ev[k][3].record(stream)
+        ev[k][2].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     time.sleep(0.3)
     clk = clocks.stop()
-    step_ms = [e[0].elapsed_time(e[3]) for e in ev]
-    beam_ms = [e[1].elapsed_time(e[2]) for e in ev]
-    cast_ms = [e[2].elapsed_time(e[3]) for e in ev]
+    step_ms = [e[0].elapsed_time(e[2]) for e in ev]
+    beam_ms = [e[0].elapsed_time(e[1]) for e in ev]  # selection inside the pass
+    cast_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    # the same frame with the selection kernel before the pass (untimed for the value)
+    split = []
+    for _ in range(20):
+        flush.zero_()
+        es = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        es[0].record(stream)
+        aok.select_chunks(ctx, scene, cam, TAU, stream=stream)
+        es[1].record(stream)
+        aok.beam_selected(ctx, scene, cam, stream=stream)
+        es[2].record(stream)
+        split.append(es)
+    torch.cuda.synchronize()
+    split_select_ms = statistics.median([e[0].elapsed_time(e[1]) for e in split])
+    split_pass_ms = statistics.median([e[1].elapsed_time(e[2]) for e in split])
     total_ms = sum(step_ms)
     if dist:
         total_ms = max_over_ranks(total_ms, dist, f"cuda:{dev}")
@@ -957,11 +970,11 @@ def main():
                 "api": "aok_render_host_async (3 frames in flight) + aok_host_frame_wait",
                 "ms_per_step": 1e3 * e2e_s, "synchronous_value": e2e_sync,
                 "synchronous_api": "aok_render_host"},
-        "gpu_launches": (3 if BEAM_DEFAULT else 2) * args.steps,
+        "gpu_launches": 2 * args.steps,
         "clocks": clk,
         "wall_s_timed": wall,
-        "beam_pass": {"on": BEAM_DEFAULT, "pass_ms_median": statistics.median(beam_ms) if BEAM_DEFAULT else 0.0,
-                      "select_ms_median": statistics.median([e[0].elapsed_time(e[1]) for e in ev])},
+        "beam_pass": {"on": BEAM_DEFAULT, "select_and_pass_ms_median": statistics.median(beam_ms),
+                      "split": {"select_ms_median": split_select_ms, "pass_ms_median": split_pass_ms}},
     }
     if not args.no_beam_ab:
         out["beam_pass"]["on_off"] = bench_beam(aok, ctx, scene, world, flush)

@@ -563,6 +563,15 @@ int aok_beam_tune(aok_ctx* ctx, uint32_t refine_tiles, int32_t min_node_log2, ui
  * be timed apart).  Runs whether or not aok_set_beam is on.  Stream rules as
  * for aok_cast_selected. */
 int aok_beam_selected(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, void* stream);
+/* Selection and beam pass in one launch (Eq. 1 and visibility, Sec. 3.4-3.5,
+ * then the bounds): the beam pass selects this camera's frame table as the
+ * first step of its walk, as aok_render does when the pass runs.  Without
+ * the pass for this frame (aok_set_beam off, checked casting, a frame below
+ * the beam_tune pixel floor, or a camera without a usable projection) it is
+ * aok_select_chunks without outputs.  The next aok_cast_selected of the same
+ * scene and camera casts the selection with these bounds.  Arguments and
+ * stream rules as for aok_select_chunks and aok_cast_selected. */
+int aok_select_beam(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double lod_threshold_px, void* stream);
 /* The last beam pass of this context (synchronises the device): bounds
  * (nullable, n_bounds >= tiles_x * tiles_y entries, row-major, numerator
  * units of 2^-12 LOD-0 voxels, INT32_MAX = no solid voxel reachable; 0

@@ -126,6 +126,7 @@ def lib() -> ctypes.CDLL:
             "aok_beam_tune": [vp, u32, ctypes.c_int32, u64, u32],
             "aok_beam_info": [vp, P(ctypes.c_int32), u64, P(u32), P(ctypes.c_int32)],
             "aok_beam_selected": [vp, u32, P(Camera), vp],
+            "aok_select_beam": [vp, u32, P(Camera), dbl, vp],
             "aok_checked_errors": [vp, P(u32)],
             "aok_serve_start": [vp, u32, u32, u32],
             "aok_serve_stop": [vp],
@@ -447,6 +448,13 @@ def beam_selected(ctx: Context, scene: Scene, cam, stream=None):
     c = to_camera(cam)
     return check(lib().aok_beam_selected(ctx.h, scene.id, ctypes.byref(c), _stream_handle(stream)),
                  "aok_beam_selected")
+
+
+def select_beam(ctx: Context, scene: Scene, cam, tau: float, stream=None):
+    """Selection and beam pass in one launch (aok_select_beam); then cast_selected."""
+    c = to_camera(cam)
+    return check(lib().aok_select_beam(ctx.h, scene.id, ctypes.byref(c), float(tau), _stream_handle(stream)),
+                 "aok_select_beam")
 
 
 def beam_info(ctx: Context):

@@ -44,7 +44,8 @@ def build(force: bool = False, verbose: bool = False) -> None:
     """Compile libaok.so (nvcc, -gencode arch=compute_103a,code=sm_103a) and
     libaokbuild.so (g++/gcc).  Translation units compile in parallel."""
     hdrs = [os.path.join(_ROOT, "include", "aok.h"), os.path.join(_CSRC, "aok_internal.h"),
-            os.path.join(_CSRC, "aok_runtime.h"), os.path.join(_CSRC, "aok_trace.cuh")]
+            os.path.join(_CSRC, "aok_runtime.h"), os.path.join(_CSRC, "aok_trace.cuh"),
+            os.path.join(_CSRC, "aok_select.cuh")]
     srcs_cu = [os.path.join(_CSRC, f) for f in ("aok_kernels.cu", "aok_tiles.cu", "aok_beam.cu")]
     srcs_cpp = [os.path.join(_CSRC, f) for f in ("aok_runtime.cpp", "aok_serve.cpp", "aok_stream.cpp", "aok_file.cpp")]
     bsrc = os.path.join(_CSRC, "aok_build.cpp")

@@ -51,6 +51,7 @@
 #include <cooperative_groups.h>
 
 #include "aok_internal.h"
+#include "aok_select.cuh"
 
 namespace cg = cooperative_groups;
 using namespace aok;
@@ -207,6 +208,17 @@ __device__ __forceinline__ bool node_bound(const BeamView& V, const ChunkRef& re
     return box_rect(V, lf, hf, rc);
 }
 
+// A frame entry read through L2 (not the L1 of this SM, which may hold a line
+// read before another SM's selection wrote it in the same launch).
+__device__ __forceinline__ ChunkRef load_ref_l2(const ChunkRef* p) {
+    const uint4* q = reinterpret_cast<const uint4*>(p);
+    const uint4 a = __ldcg(q), b = __ldcg(q + 1);
+    ChunkRef r;
+    std::memcpy(&r, &a, 16);
+    std::memcpy(reinterpret_cast<char*>(&r) + 16, &b, 16);
+    return r;
+}
+
 // Atomic minimum without a return value (a reduction the SM does not wait for).
 __device__ __forceinline__ void red_min_u64(unsigned long long* p, unsigned long long v) {
     asm volatile("red.global.min.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
@@ -266,7 +278,10 @@ __device__ __forceinline__ void beam_walk(const BeamBatch& P) {
         if (n == 0) break;  // the same value in every thread after the barrier
         const uint4* __restrict__ qin = P.q[level & 1];
         uint4* __restrict__ qout = P.q[(level + 1) & 1];
-        for (uint32_t base = gtid & ~31u; base < n; base += stride) {
+        // level 0 (the regions, few): one warp per block first, so that its
+        // selection and root projections spread over the SMs
+        const uint32_t first = level == 0 ? (((threadIdx.x >> 5) * gridDim.x + blockIdx.x) << 5) : (gtid & ~31u);
+        for (uint32_t base = first; base < n; base += stride) {
             const uint32_t i = base + (uint32_t)lane;
             uint32_t kids = 0, ch[8], cc[8];
             uint4 it = make_uint4(kNoItem, 0u, 0u, 0u);
@@ -283,13 +298,17 @@ __device__ __forceinline__ void beam_walk(const BeamBatch& P) {
                     }
                     vi = lo;
                     const uint32_t r = i - P.v[vi].region_begin;
-                    ref = P.v[vi].frame[r];
+                    // a pass that selects first writes the region's frame entry here;
+                    // later levels read entries through L2 only (written by other SMs)
+                    ref = P.select ? select_one(P.v[vi].scene, P.cam, const_cast<ChunkRef*>(P.v[vi].frame), nullptr,
+                                                nullptr, nullptr, (int)r)
+                                   : P.v[vi].frame[r];
                     if (ref.root != kNone) it = make_uint4(r, ref.root, 0u, (uint32_t)P.v[vi].scene.mlog | (vi << 8));
                 } else {
                     it = qin[i];
                     if (it.x != kNoItem) {
                         vi = it.w >> 8;
-                        ref = P.v[vi].frame[it.x];
+                        ref = load_ref_l2(P.v[vi].frame + it.x);
                     }
                 }
             }

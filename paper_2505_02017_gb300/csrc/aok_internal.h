@@ -130,6 +130,8 @@ struct BeamBatch {
     uint4* q[2];                  // node queues of alternate levels: {chunk, node, cell x | y << 10 | z << 20, log2 size | view << 8}
     uint32_t* cnt;                // [kBeamLevels] items queued per level
     uint32_t* hist;               // [kBeamLevels] nodes walked per depth below the region roots
+    uint32_t select;              // 1: one view whose frame table the pass selects first (cam)
+    CamDev cam;                   // that view's camera (select == 1)
     BeamView v[kBeamViews];
 };
 static_assert(sizeof(BeamBatch) < 32000, "a beam pass's parameters must fit the kernel parameter space");

@@ -888,11 +888,15 @@ static void beam_header(aok_ctx* ctx, BeamBatch* P, uint32_t tag) {
     P->q[1] = ctx->beam.q[1];
     P->cnt = ctx->beam.cnt;
     P->hist = ctx->beam.hist;
+    P->select = 0;
 }
 
 // The beam pass over the scene's current frame table, remembered with what
-// it was computed for.
-static int run_beam(aok_ctx* ctx, uint32_t scene, Scene* sc, const SceneDev& sd, const CamDev& cd, void* stream) {
+// it was computed for.  select: the frame table is not selected yet; the
+// pass selects it as its first step (one launch fewer), or, for a view
+// without a usable projection, the selection kernel does.
+static int run_beam(aok_ctx* ctx, uint32_t scene, Scene* sc, const SceneDev& sd, const CamDev& cd, void* stream,
+                    bool select = false) {
     int st = ensure_beam_queues(ctx);
     if (st) return st;
     BeamState& b = ctx->beam;
@@ -913,6 +917,13 @@ static int run_beam(aok_ctx* ctx, uint32_t scene, Scene* sc, const SceneDev& sd,
         P->n_views = 1;
         P->n_regions = (uint32_t)sc->n_chunks;
         b.read.bounds = b.bounds;
+        if (select) {
+            P->select = 1;
+            P->cam = cd;
+        }
+    } else if (select) {
+        st = aokk_select(&sd, &cd, sc->d_frame, nullptr, nullptr, nullptr, stream);
+        if (st) return st;
     }
     st = aokk_beam_run(P, b.grid, stream);
     if (st) return st;
@@ -983,22 +994,27 @@ static bool beam_fresh(const aok_ctx* ctx, uint32_t scene, const Scene* sc, cons
     return std::memcmp(&k, &b.cam, sizeof(CamDev)) == 0;
 }
 
-// The casting launch of a single view, after the frame table is selected:
-// with the beam pass on (and no checked casting) the casting kernel takes the
-// pass's per-tile bounds, computed first unless aok_beam_selected already did
-// for this selection and camera.
+// The casting launch of a single view: with the beam pass on (and no checked
+// casting) the casting kernel takes the pass's per-tile bounds, computed
+// first unless aok_beam_selected already did for this selection and camera.
+// selected: the frame table is already selected; else the beam pass selects
+// it (or, without the pass, the selection kernel).
 static int cast_single(aok_ctx* ctx, uint32_t scene, Scene* sc, const SceneDev& sd, const CamDev& cd,
-                       const aok_frame* frame, uint32_t* counts, void* stream) {
+                       const aok_frame* frame, uint32_t* counts, void* stream, bool selected = true) {
     CheckDev ck;
     const CheckDev* ckp = check_dev(ctx, sc, &ck);
     const BeamRead* beam = nullptr;
+    int st = AOK_OK;
     if (ctx->beam_on && !ckp && (uint64_t)cd.W * (uint64_t)cd.H >= ctx->beam_min_pixels) {
-        if (!beam_fresh(ctx, scene, sc, cd)) {
-            const int st = run_beam(ctx, scene, sc, sd, cd, stream);
+        if (!selected || !beam_fresh(ctx, scene, sc, cd)) {
+            st = run_beam(ctx, scene, sc, sd, cd, stream, !selected);
             if (st) return st;
+            selected = true;
         }
         beam = &ctx->beam.read;
     }
+    if (!selected) st = aokk_select(&sd, &cd, sc->d_frame, nullptr, nullptr, nullptr, stream);
+    if (st) return st;
     return aokk_cast(&sd, &cd, sc->d_frame, (uint4*)frame->hit, frame->t, counts, stream, ckp, beam);
 }
 
@@ -1017,8 +1033,7 @@ static int render_impl(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, doub
     if (ctx->single_persistent && !counts) {
         st = render_persistent(ctx, sc, cd, frame, stream, true);
     } else {
-        st = aokk_select(&sd, &cd, sc->d_frame, nullptr, nullptr, nullptr, stream);
-        if (!st) st = cast_single(ctx, scene, sc, sd, cd, frame, counts, stream);
+        st = cast_single(ctx, scene, sc, sd, cd, frame, counts, stream, false);
     }
     if (st == AOK_E_CUDA) return launch_failure(ctx);
     return st;
@@ -1211,6 +1226,25 @@ int aok_beam_selected(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, void*
     return st;
 }
 
+int aok_select_beam(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double tau, void* stream) {
+    if (!ctx) return AOK_E_INVALID;
+    Scene* sc = find_scene(ctx, scene);
+    if (!sc) return AOK_E_NOT_RESIDENT;
+    CamDev cd;
+    int st = make_cam(ctx, sc, cam, tau, &cd);
+    if (st) return st;
+    cudaSetDevice(ctx->device);
+    SceneDev sd = scene_dev(sc);
+    sc->select_gen++;
+    CheckDev ck;
+    if (ctx->beam_on && !check_dev(ctx, sc, &ck) && (uint64_t)cd.W * (uint64_t)cd.H >= ctx->beam_min_pixels)
+        st = run_beam(ctx, scene, sc, sd, cd, stream, true);
+    else
+        st = aokk_select(&sd, &cd, sc->d_frame, nullptr, nullptr, nullptr, stream);
+    if (st == AOK_E_CUDA) return launch_failure(ctx);
+    return st;
+}
+
 int aok_beam_info(aok_ctx* ctx, int32_t* bounds, uint64_t n_bounds, uint32_t* level_counts, int32_t* tiles_xy) {
     if (!ctx) return AOK_E_INVALID;
     const BeamState& b = ctx->beam;
@@ -1375,6 +1409,8 @@ static int pipe_render(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, doub
         if (st) return st;
     }
     const SceneDev sd = scene_dev(sc);
+    // the selection kernel, then the pass (measured faster here than the pass
+    // that selects first: the pass runs beside the previous frame's cast)
     st = aokk_select(&sd, &cd, sl.frame, nullptr, nullptr, nullptr, p.prep);
     if (st) return launch_failure(ctx);
     BeamRead rd{nullptr, 0};

@@ -378,3 +378,33 @@ def test_pipelined_host_frames_with_beam(ctx):
         aok.host_frame_wait(ctx, tk)
     for i, (ref, h, t) in enumerate(zip(refs, hh, th)):
         assert torch.equal(ref[0].cpu(), h) and torch.equal(ref[1].cpu().view(torch.int32), t.view(torch.int32)), i
+
+
+@pytest.mark.parametrize("spec", [MULTI16, MED64, replace(MULTI32, name="multi32vd_fused", view_dist=45.0)],
+                         ids=lambda s: s.name)
+def test_selection_inside_the_pass(ctx, spec):
+    """The beam pass that selects the frame table as the first step of its
+    walk (aok_render with the pass on, aok_select_beam) gives the frame of
+    the selection kernel followed by the pass and the cast, bit for bit."""
+    w, sc, _ = scene_for(ctx, spec)
+    aok.set_beam(ctx, True)
+    for seed in (3, 4, 9):
+        cam = sg.ground_camera(w, seed, 203, 117, z_lo=3, z_hi=20)
+        tau = 1.5
+        ref = aok.alloc_frame(cam.W, cam.H)
+        aok.select_chunks(ctx, sc, cam, tau)  # the selection kernel, then the pass, then the cast
+        aok.beam_selected(ctx, sc, cam)
+        aok.cast_selected(ctx, sc, cam, *ref)
+        fused = aok.alloc_frame(cam.W, cam.H)
+        aok.select_beam(ctx, sc, cam, tau)
+        aok.cast_selected(ctx, sc, cam, *fused)
+        rendered = aok.alloc_frame(cam.W, cam.H)
+        aok.render(ctx, sc, cam, tau, *rendered)
+        torch.cuda.synchronize()
+        assert same(ref, fused) and same(ref, rendered), seed
+    aok.set_beam(ctx, False)
+    plain = aok.alloc_frame(cam.W, cam.H)  # without the pass: the selection kernel alone
+    aok.select_beam(ctx, sc, cam, tau)
+    aok.cast_selected(ctx, sc, cam, *plain)
+    torch.cuda.synchronize()
+    assert same(ref, plain)
