@@ -303,7 +303,8 @@ __global__ void __launch_bounds__(128) tc_rect_kernel(SceneDev S, CamDev C, cons
         x1 = fmax(x1, __shfl_xor_sync(0xFFFFFFFFu, x1, o, 8));
         y0 = fmin(y0, __shfl_xor_sync(0xFFFFFFFFu, y0, o, 8));
         y1 = fmax(y1, __shfl_xor_sync(0xFFFFFFFFu, y1, o, 8));
-        full = full || __shfl_xor_sync(0xFFFFFFFFu, (int)full, o, 8);
+        const int fo = __shfl_xor_sync(0xFFFFFFFFu, (int)full, o, 8);  // every lane shuffles
+        full = full || fo;
     }
     if (project) {
         if (full) {

@@ -199,6 +199,31 @@ def test_streamed_open_world_path(ctx):
     sc.destroy()
 
 
+def test_open_world_path_poses_equal_march(ctx):
+    """Poses of the open-world benchmark path at its full resolution whose
+    near chunk regions straddle the camera plane (some AABB corners behind
+    it: whole-screen rectangles next to projected ones in one warp): every
+    pose equals the march, with and without the previous pose's Hi-Z."""
+    from paper_2505_02017_gb300.stream import Streamer
+    spec = sg.OPEN_65536
+    w = sg.World(spec)
+    sc = aok.Scene(ctx, spec, node_words=512 << 20, leaves=256 << 20, mat_bytes=16 << 30)
+    st = Streamer(ctx, w, sc, threads=16)
+    cams = sg.path_cameras(w, 103, 300, 2560, 1440)
+    try:
+        aok.tiles_forget(ctx)
+        for pose in (34, 35, 68, 72, 79):
+            st.update(cams[pose], 1.0)
+            ref = march(ctx, sc, cams[pose], 1.0)
+            out, _ = tiles(ctx, sc, cams[pose], 1.0)
+            assert same(ref, out), pose
+        aok.tiles_forget(ctx)
+        out, _ = tiles(ctx, sc, cams[79], 1.0)
+        assert same(ref, out)
+    finally:
+        sc.destroy()
+
+
 def test_limits_and_errors():
     c = aok.Context(0)
     L = aok.lib()
