@@ -152,11 +152,13 @@ __device__ __forceinline__ void leaf_extent(uint64_t m, int lo[3], int hi[3]) {
     }
 }
 
-// A node's box (chunk-local cell clipped to the region's AABB, or a leaf's
-// set voxels), its L-inf distance from the origin and screen rectangle.
-// Returns false if the node cannot meet any pixel ray.
+// A node's box (the box of its solid voxels the device header carries, in
+// 16ths of the cell, clipped to the region's AABB, or a leaf's set voxels),
+// its L-inf distance from the origin and screen rectangle.  hdr: the interior
+// node's header word, loaded here.  Returns false if the node cannot meet any
+// pixel ray.
 __device__ __forceinline__ bool node_bound(const BeamView& V, const ChunkRef& ref, uint32_t chunk, uint32_t node,
-                                           uint32_t packed_cell, int s, int4& rc, int32_t& D) {
+                                           uint32_t packed_cell, int s, int4& rc, int32_t& D, uint32_t& hdr) {
     const SceneDev& S = V.scene;
     const int lod = (int)ref.lod;
     const bool leaf = s == lod + 2;
@@ -176,10 +178,13 @@ __device__ __forceinline__ bool node_bound(const BeamView& V, const ChunkRef& re
             bhi[a] = cell[a] + (h[a] << lod);
         }
     } else {
+        hdr = __ldg(S.nodes + node);
+        const uint32_t q = hdr >> 8;
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            blo[a] = max(cell[a], (int32_t)ref.aabb[a]);
-            bhi[a] = min(cell[a] + (1 << s), (int32_t)ref.aabb[3 + a]);
+            const int32_t ql = (int32_t)((q >> (8 * a)) & 15u), qh = (int32_t)((q >> (8 * a + 4)) & 15u) + 1;
+            blo[a] = max(cell[a] + ((ql << s) >> 4), (int32_t)ref.aabb[a]);
+            bhi[a] = min(cell[a] + (((qh << s) + 15) >> 4), (int32_t)ref.aabb[3 + a]);
         }
     }
     // L-inf distance from the origin (exact, numerator units: |values| < 2^30)
@@ -244,8 +249,8 @@ __device__ __forceinline__ void scatter_bound(const BeamView& V, uint32_t tag, c
 
 // Children of interior node `node` (side 2^s) at cell c: {pointer, packed cell}.
 __device__ __forceinline__ uint32_t node_children(const SceneDev& S, uint32_t node, uint32_t packed_cell, int s,
-                                                  uint32_t ch[8], uint32_t cc[8]) {
-    const uint32_t m0 = __ldg(S.nodes + node) & 0xFFu;
+                                                  uint32_t ch[8], uint32_t cc[8], uint32_t hdr) {
+    const uint32_t m0 = hdr & 0xFFu;
     const uint32_t k = (uint32_t)__popc(m0);
     const uint32_t h = 1u << (s - 1);
     const uint32_t cx0 = packed_cell & 1023u, cy0 = (packed_cell >> 10) & 1023u, cz0 = (packed_cell >> 20) & 1023u;
@@ -318,10 +323,11 @@ __device__ __forceinline__ void beam_walk(const BeamBatch& P) {
                 atomicAdd(&hist[min(V.scene.mlog - s, kBeamLevels - 1)], 1u);
                 int4 rc;
                 int32_t D;
-                if (node_bound(V, ref, it.x, it.y, it.z, s, rc, D)) {
+                uint32_t hdr = 0;
+                if (node_bound(V, ref, it.x, it.y, it.z, s, rc, D, hdr)) {
                     const uint32_t area = (uint32_t)(rc.z - rc.x) * (uint32_t)(rc.w - rc.y);
                     if (s > lod + 2 && area > P.expand && s > P.smin)
-                        kids = node_children(V.scene, it.y, it.z, s, ch, cc);
+                        kids = node_children(V.scene, it.y, it.z, s, ch, cc, hdr);
                     else
                         scatter_bound(V, P.tag, rc, D);
                 }
@@ -351,7 +357,9 @@ __device__ __forceinline__ void beam_walk(const BeamBatch& P) {
                     for (uint32_t q = at; q < P.cap && q < at + kids; q++) qout[q] = make_uint4(kNoItem, 0u, 0u, 0u);
                     int4 rc;
                     int32_t D;
-                    if (node_bound(V, ref, it.x, it.y, it.z, (int)(it.w & 0xFFu), rc, D)) scatter_bound(V, P.tag, rc, D);
+                    uint32_t hdr;
+                    if (node_bound(V, ref, it.x, it.y, it.z, (int)(it.w & 0xFFu), rc, D, hdr))
+                        scatter_bound(V, P.tag, rc, D);
                 }
             }
         }

@@ -236,8 +236,12 @@ static int validate_blob(const aok_chunk_blob* b, int res, int M) {
 // prefix = summed counts of the earlier children, so that the depth-first
 // index of a voxel needs one word per level instead of every earlier
 // sibling's count.  Child pointers are rebased (node_base: device word
-// offset of this chunk's nodes, leaf_base: of its leaves).  Returns the
-// word count; with out == nullptr only sizes are computed.
+// offset of this chunk's nodes, leaf_base: of its leaves).  The header keeps
+// the child mask in bits 0-7; bits 8-31 hold the box of the node's solid
+// voxels within its cell, per axis (x, y, z from bit 8) a 4-bit lower bound
+// and a 4-bit upper bound - 1 in 16ths of the cell's side (rounded outward),
+// which the beam pass projects instead of the whole cell.  Returns the word
+// count; with out == nullptr only sizes are computed.
 static uint64_t layout_blob(const aok_chunk_blob* b, int res, uint32_t node_base, uint32_t leaf_base, uint32_t* out,
                             uint32_t* root_out) {
     const uint64_t nw = b->n_node_words;
@@ -267,12 +271,67 @@ static uint64_t layout_blob(const aok_chunk_blob* b, int res, uint32_t node_base
         w += 2 + 2 * (uint64_t)__builtin_popcount(b->nodes[i]);
     }
     if (!out) return w;
+    // solid-voxel box of every node in its own cell (LOD voxels), deepest first
+    std::vector<uint32_t> order;
+    for (uint64_t i = 0; i < nw; i++)
+        if (depth[i] >= 0) order.push_back((uint32_t)i);
+    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t c) { return depth[a] > depth[c]; });
+    std::vector<uint16_t> box(6 * nw, 0);  // lo x, y, z, hi x, y, z
+    for (uint32_t i : order) {
+        const int side = res >> depth[i], half = side >> 1;
+        const bool leafkids = depth[i] == n_int - 1;
+        int lo[3] = {side, side, side}, hi[3] = {0, 0, 0};
+        uint32_t m = b->nodes[i] & 0xFFu;
+        for (int c = 0; m; c++) {
+            const int oc = __builtin_ctz(m);
+            m &= m - 1;
+            const uint32_t ch = b->nodes[i + 2 + c];
+            int clo[3], chi[3];
+            if (leafkids) {  // a 4^3 leaf mask, bit x + 4y + 16z: the rows present per axis
+                const uint64_t lm = b->leaves[ch];
+                uint64_t t = lm | (lm >> 32);
+                t |= t >> 16;  // bit x + 4y: any z
+                const uint32_t xy = (uint32_t)t & 0xFFFFu;
+                const uint32_t bits[3] = {
+                    (xy | xy >> 4 | xy >> 8 | xy >> 12) & 0xFu,
+                    (uint32_t)((xy & 0xFu) != 0) | (uint32_t)((xy & 0xF0u) != 0) << 1 |
+                        (uint32_t)((xy & 0xF00u) != 0) << 2 | (uint32_t)((xy & 0xF000u) != 0) << 3,
+                    (uint32_t)((lm & 0xFFFFull) != 0) | (uint32_t)(((lm >> 16) & 0xFFFFull) != 0) << 1 |
+                        (uint32_t)(((lm >> 32) & 0xFFFFull) != 0) << 2 | (uint32_t)((lm >> 48) != 0) << 3};
+                for (int a = 0; a < 3; a++) {
+                    clo[a] = __builtin_ctz(bits[a]);
+                    chi[a] = 32 - __builtin_clz(bits[a]);
+                }
+            } else {
+                for (int a = 0; a < 3; a++) {
+                    clo[a] = box[6 * (size_t)ch + a];
+                    chi[a] = box[6 * (size_t)ch + 3 + a];
+                }
+            }
+            for (int a = 0; a < 3; a++) {
+                const int at = ((oc >> a) & 1) * half;
+                lo[a] = std::min(lo[a], at + clo[a]);
+                hi[a] = std::max(hi[a], at + chi[a]);
+            }
+        }
+        for (int a = 0; a < 3; a++) {
+            box[6 * (size_t)i + a] = (uint16_t)lo[a];
+            box[6 * (size_t)i + 3 + a] = (uint16_t)hi[a];
+        }
+    }
     for (uint64_t i = 0; i < nw; i++) {
         if (depth[i] < 0) continue;
         const uint32_t hdr = b->nodes[i], o = off[i];
-        const int k = __builtin_popcount(hdr);
+        const int k = __builtin_popcount(hdr & 0xFFu);
         const bool leafkids = depth[i] == n_int - 1;
-        out[o] = hdr;
+        const int side = res >> depth[i];
+        uint32_t q = 0;
+        for (int a = 0; a < 3; a++) {
+            const uint32_t ql = (uint32_t)(box[6 * i + a] * 16 / side);                  // rounded down
+            const uint32_t qh = (uint32_t)((box[6 * i + 3 + a] * 16 + side - 1) / side);  // rounded up, >= 1
+            q |= (ql | (qh - 1) << 4) << (8 * a);
+        }
+        out[o] = (hdr & 0xFFu) | q << 8;
         out[o + 1] = b->nodes[i + 1];
         uint32_t pre = 0;
         for (int c = 0; c < k; c++) {
