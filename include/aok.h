@@ -538,8 +538,9 @@ int aok_render_noalloc(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, doub
  * (about 11 B per 8 x 4 pixel tile, grown to the largest frame or batch seen,
  * and two 16 MiB node queues) are charged to the budget when first needed.
  * The render server runs it for its batches too (per-request pyramids).
- * Not used by checked casting, the persistent single-view and batch kernels,
- * aok_render_noalloc or the tile pipeline.  Default on.  The pass's
+ * Not used by the persistent single-view and batch kernels,
+ * aok_render_noalloc or the tile pipeline; with checked casting it runs with
+ * its node and leaf indices checked.  Default on.  The pass's
  * buffers belong to the context: with it on, renders of one context on
  * different streams must be ordered (an event or a synchronisation between
  * them).  The passes of all contexts of a process run one after another on a
@@ -566,8 +567,8 @@ int aok_beam_selected(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, void*
 /* Selection and beam pass in one launch (Eq. 1 and visibility, Sec. 3.4-3.5,
  * then the bounds): the beam pass selects this camera's frame table as the
  * first step of its walk, as aok_render does when the pass runs.  Without
- * the pass for this frame (aok_set_beam off, checked casting, a frame below
- * the beam_tune pixel floor, or a camera without a usable projection) it is
+ * the pass for this frame (aok_set_beam off, a frame below the beam_tune
+ * pixel floor, or a camera without a usable projection) it is
  * aok_select_chunks without outputs.  The next aok_cast_selected of the same
  * scene and camera casts the selection with these bounds.  Arguments and
  * stream rules as for aok_select_chunks and aok_cast_selected. */
@@ -597,7 +598,10 @@ int aok_render_counted(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, doub
  * aok_render_noalloc of this context test every node, leaf and colour index against the scene's pool
  * sizes before loading it; an index out of range ends that chunk's traversal
  * as a miss and ORs a code into the context's error word (1 node word, 2
- * leaf, 4 colour).  Slower; batches, serving and the tile pipeline are not
+ * leaf, 4 colour).  The beam pass of aok_render and aok_select_beam keeps
+ * running and tests its node and leaf indices too: one out of range ORs its
+ * code and bounds the whole view by 0 (no ray skips anything).  Slower;
+ * batches, serving, the pipelined host frames and the tile pipeline are not
  * checked. */
 int aok_set_checked(aok_ctx* ctx, int on);
 /* Read and clear the error word (synchronises the device); 0 = no index was

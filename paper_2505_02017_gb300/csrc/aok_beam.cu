@@ -153,14 +153,17 @@ __device__ __forceinline__ void leaf_extent(uint64_t m, int lo[3], int hi[3]) {
 }
 
 // A node's box (the box of its solid voxels the device header carries, in
-// 16ths of the cell, clipped to the region's AABB, or a leaf's set voxels),
-// its L-inf distance from the origin and screen rectangle.  hdr: the interior
-// node's header word, loaded here.  Returns false if the node cannot meet any
-// pixel ray.
-__device__ __forceinline__ bool node_bound(const BeamView& V, const ChunkRef& ref, uint32_t chunk, uint32_t node,
-                                           uint32_t packed_cell, int s, int4& rc, int32_t& D, uint32_t& hdr) {
+// 16ths of the cell, or a leaf's set voxels), its L-inf distance from the
+// origin and screen rectangle.  A region root's box is also clipped to the
+// region's AABB (clip, ref: the region's entry; below the roots a node's
+// solid voxels lie in that AABB already, so the clip would only trim the
+// rounding to 16ths).  hdr: the
+// interior node's header word, loaded here.  Returns false if the node cannot
+// meet any pixel ray.
+__device__ __forceinline__ bool node_bound(const BeamView& V, int lod, bool clip, const ChunkRef& ref, uint32_t chunk,
+                                           uint32_t node, uint32_t packed_cell, int s, int4& rc, int32_t& D,
+                                           uint32_t& hdr) {
     const SceneDev& S = V.scene;
-    const int lod = (int)ref.lod;
     const bool leaf = s == lod + 2;
     int32_t u[3];
     u[0] = (int32_t)(chunk % (uint32_t)S.grid[0]);
@@ -183,8 +186,12 @@ __device__ __forceinline__ bool node_bound(const BeamView& V, const ChunkRef& re
 #pragma unroll
         for (int a = 0; a < 3; a++) {
             const int32_t ql = (int32_t)((q >> (8 * a)) & 15u), qh = (int32_t)((q >> (8 * a + 4)) & 15u) + 1;
-            blo[a] = max(cell[a] + ((ql << s) >> 4), (int32_t)ref.aabb[a]);
-            bhi[a] = min(cell[a] + (((qh << s) + 15) >> 4), (int32_t)ref.aabb[3 + a]);
+            blo[a] = cell[a] + ((ql << s) >> 4);
+            bhi[a] = cell[a] + (((qh << s) + 15) >> 4);
+            if (clip) {
+                blo[a] = max(blo[a], (int32_t)ref.aabb[a]);
+                bhi[a] = min(bhi[a], (int32_t)ref.aabb[3 + a]);
+            }
         }
     }
     // L-inf distance from the origin (exact, numerator units: |values| < 2^30)
@@ -213,17 +220,6 @@ __device__ __forceinline__ bool node_bound(const BeamView& V, const ChunkRef& re
     return box_rect(V, lf, hf, rc);
 }
 
-// A frame entry read through L2 (not the L1 of this SM, which may hold a line
-// read before another SM's selection wrote it in the same launch).
-__device__ __forceinline__ ChunkRef load_ref_l2(const ChunkRef* p) {
-    const uint4* q = reinterpret_cast<const uint4*>(p);
-    const uint4 a = __ldcg(q), b = __ldcg(q + 1);
-    ChunkRef r;
-    std::memcpy(&r, &a, 16);
-    std::memcpy(reinterpret_cast<char*>(&r) + 16, &b, 16);
-    return r;
-}
-
 // Atomic minimum without a return value (a reduction the SM does not wait for).
 __device__ __forceinline__ void red_min_u64(unsigned long long* p, unsigned long long v) {
     asm volatile("red.global.min.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
@@ -245,6 +241,14 @@ __device__ __forceinline__ void scatter_bound(const BeamView& V, uint32_t tag, c
     const unsigned long long v = ((unsigned long long)tag << 32) | (uint32_t)D;
     for (int y = y0; y <= y1; y++)
         for (int x = x0; x <= x1; x++) red_min_u64(&lv[(size_t)y * wl + x], v);
+}
+
+// A checked pass (P.ck.err set) that meets a node or leaf index outside its
+// pool: the error code goes into the error word and the view is bounded by 0
+// (no ray of it skips anything), in place of the loads.
+__device__ __noinline__ void bad_index(const BeamBatch& P, const BeamView& V, uint32_t code) {
+    atomicOr(P.ck.err, code);
+    scatter_bound(V, P.tag, make_int4(0, 0, V.tiles_x, V.tiles_y), 0);
 }
 
 // Children of interior node `node` (side 2^s) at cell c: {pointer, packed cell}.
@@ -269,8 +273,13 @@ __device__ __forceinline__ uint32_t node_children(const SceneDev& S, uint32_t no
 // levels of the walk over all views with a grid-wide barrier after each,
 // ending at the first level that queued nothing.  Level 0 takes every view's
 // chunk regions; every lane of a warp runs the same iterations (the queue
-// reservation is warp-wide).  Bounds carry the pass's tag, so nothing has to
-// be reset before the walk or folded after it.
+// reservation is warp-wide).  A queued item carries what its node's bound
+// needs (region, node, cell, side, view, LOD), so a level's chain of
+// dependent loads starts at the item itself; each thread loads its first
+// item beside the level's count and the next one while it works on the
+// current one.  Queues are read through L2 (written by other SMs before the
+// barrier).  Bounds carry the pass's tag, so nothing has to be reset before
+// the walk or folded after it.
 __device__ __forceinline__ void beam_walk(const BeamBatch& P) {
     cg::grid_group g = cg::this_grid();
     __shared__ uint32_t hist[kBeamLevels];
@@ -279,18 +288,20 @@ __device__ __forceinline__ void beam_walk(const BeamBatch& P) {
     if (threadIdx.x < kBeamLevels) hist[threadIdx.x] = 0;
     __syncthreads();
     for (int level = 0; level < kBeamLevels - 1; level++) {
-        const uint32_t n = level == 0 ? P.n_regions : min(*(volatile uint32_t*)&P.cnt[level], P.cap);
-        if (n == 0) break;  // the same value in every thread after the barrier
-        const uint4* __restrict__ qin = P.q[level & 1];
-        uint4* __restrict__ qout = P.q[(level + 1) & 1];
+        const uint4* qin = P.q[level & 1];
+        uint4* qout = P.q[(level + 1) & 1];
         // level 0 (the regions, few): one warp per block first, so that its
         // selection and root projections spread over the SMs
         const uint32_t first = level == 0 ? (((threadIdx.x >> 5) * gridDim.x + blockIdx.x) << 5) : (gtid & ~31u);
+        uint4 nxt = make_uint4(kNoItem, 0u, 0u, 0u);
+        if (level > 0 && first + (uint32_t)lane < P.cap) nxt = __ldcg(qin + first + lane);
+        const uint32_t n = level == 0 ? P.n_regions : min(*(volatile uint32_t*)&P.cnt[level], P.cap);
+        if (n == 0) break;  // the same value in every thread after the barrier
         for (uint32_t base = first; base < n; base += stride) {
             const uint32_t i = base + (uint32_t)lane;
             uint32_t kids = 0, ch[8], cc[8];
             uint4 it = make_uint4(kNoItem, 0u, 0u, 0u);
-            uint32_t vi = 0;
+            bool clip = false;
             ChunkRef ref;
             if (i < n) {
                 if (level == 0) {
@@ -301,35 +312,44 @@ __device__ __forceinline__ void beam_walk(const BeamBatch& P) {
                         if (P.v[mid].region_begin <= i) lo = mid;
                         else hi = mid - 1;
                     }
-                    vi = lo;
-                    const uint32_t r = i - P.v[vi].region_begin;
-                    // a pass that selects first writes the region's frame entry here;
-                    // later levels read entries through L2 only (written by other SMs)
-                    ref = P.select ? select_one(P.v[vi].scene, P.cam, const_cast<ChunkRef*>(P.v[vi].frame), nullptr,
+                    const uint32_t r = i - P.v[lo].region_begin;
+                    // a pass that selects first writes the region's frame entry here
+                    ref = P.select ? select_one(P.v[lo].scene, P.cam, const_cast<ChunkRef*>(P.v[lo].frame), nullptr,
                                                 nullptr, nullptr, (int)r)
-                                   : P.v[vi].frame[r];
-                    if (ref.root != kNone) it = make_uint4(r, ref.root, 0u, (uint32_t)P.v[vi].scene.mlog | (vi << 8));
+                                   : P.v[lo].frame[r];
+                    if (ref.root != kNone)
+                        it = make_uint4(r, ref.root, 0u,
+                                        (uint32_t)P.v[lo].scene.mlog | (lo << 8) | ((uint32_t)ref.lod << 16));
+                    clip = true;
                 } else {
-                    it = qin[i];
-                    if (it.x != kNoItem) {
-                        vi = it.w >> 8;
-                        ref = load_ref_l2(P.v[vi].frame + it.x);
-                    }
+                    it = nxt;
                 }
             }
-            const BeamView& V = P.v[vi];
+            if (level > 0) {
+                const uint32_t j = i + stride;
+                nxt = make_uint4(kNoItem, 0u, 0u, 0u);
+                if (j < n) nxt = __ldcg(qin + j);
+            }
+            const uint32_t vi = (it.w >> 8) & 0xFFu;
+            const int s = (int)(it.w & 0xFFu), lod = (int)((it.w >> 16) & 0xFFu);
+            const BeamView& V = P.v[it.x != kNoItem ? vi : 0u];
             if (it.x != kNoItem) {
-                const int s = (int)(it.w & 0xFFu), lod = (int)ref.lod;
                 atomicAdd(&hist[min(V.scene.mlog - s, kBeamLevels - 1)], 1u);
                 int4 rc;
                 int32_t D;
                 uint32_t hdr = 0;
-                if (node_bound(V, ref, it.x, it.y, it.z, s, rc, D, hdr)) {
+                if (P.ck.err && (s == lod + 2 ? it.y >= P.ck.n_leaves : (uint64_t)it.y + 2 > P.ck.n_nodes)) {
+                    bad_index(P, V, s == lod + 2 ? 2u : 1u);
+                } else if (node_bound(V, lod, clip, ref, it.x, it.y, it.z, s, rc, D, hdr)) {
                     const uint32_t area = (uint32_t)(rc.z - rc.x) * (uint32_t)(rc.w - rc.y);
-                    if (s > lod + 2 && area > P.expand && s > P.smin)
-                        kids = node_children(V.scene, it.y, it.z, s, ch, cc, hdr);
-                    else
+                    if (s > lod + 2 && area > P.expand && s > P.smin) {
+                        if (P.ck.err && (uint64_t)it.y + 2 + 2 * __popc(hdr & 0xFFu) > P.ck.n_nodes)
+                            bad_index(P, V, 1u);
+                        else
+                            kids = node_children(V.scene, it.y, it.z, s, ch, cc, hdr);
+                    } else {
                         scatter_bound(V, P.tag, rc, D);
+                    }
                 }
             }
             // queue the children: one reservation per warp
@@ -358,8 +378,7 @@ __device__ __forceinline__ void beam_walk(const BeamBatch& P) {
                     int4 rc;
                     int32_t D;
                     uint32_t hdr;
-                    if (node_bound(V, ref, it.x, it.y, it.z, (int)(it.w & 0xFFu), rc, D, hdr))
-                        scatter_bound(V, P.tag, rc, D);
+                    if (node_bound(V, lod, clip, ref, it.x, it.y, it.z, s, rc, D, hdr)) scatter_bound(V, P.tag, rc, D);
                 }
             }
         }

@@ -127,11 +127,12 @@ struct BeamBatch {
     int32_t smin;                 // ... and whose side is above 2^smin LOD-0 voxels
     uint32_t tag;                 // the pass's tag: decreases from pass to pass
     uint32_t cap;                 // queue capacity in items
-    uint4* q[2];                  // node queues of alternate levels: {chunk, node, cell x | y << 10 | z << 20, log2 size | view << 8}
+    uint4* q[2];                  // node queues of alternate levels: {chunk, node, cell x | y << 10 | z << 20, log2 size | view << 8 | LOD << 16}
     uint32_t* cnt;                // [kBeamLevels] items queued per level
     uint32_t* hist;               // [kBeamLevels] nodes walked per depth below the region roots
     uint32_t select;              // 1: one view whose frame table the pass selects first (cam)
     CamDev cam;                   // that view's camera (select == 1)
+    CheckDev ck;                  // ck.err != nullptr: node and leaf indices tested before their loads
     BeamView v[kBeamViews];
 };
 static_assert(sizeof(BeamBatch) < 32000, "a beam pass's parameters must fit the kernel parameter space");

@@ -61,15 +61,18 @@ __global__ void __launch_bounds__(128, 7) cast_kernel(SceneDev S, CamDev C, cons
     trace_pixel<COUNT, false, BEAM>(S, C, frame, px, py, out_hit, out_t, counts, (size_t)py * C.W + px, nullptr, Dn);
 }
 
-// The same casting with every pool index checked (CheckDev).
+// The same casting with every pool index checked (CheckDev); BEAM: with the
+// beam pass's bounds.
+template <bool BEAM>
 __global__ void __launch_bounds__(128) cast_kernel_checked(SceneDev S, CamDev C, const ChunkRef* __restrict__ frame,
                                                            uint4* __restrict__ out_hit, float* __restrict__ out_t,
-                                                           CheckDev ck) {
+                                                           CheckDev ck, const BeamLookup beam) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int px = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
     const int py = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
     if (px >= C.W || py >= C.H) return;
-    trace_pixel<false, true>(S, C, frame, px, py, out_hit, out_t, nullptr, (size_t)py * C.W + px, &ck);
+    const int32_t Dn = BEAM ? beam_bound_lut(beam, px, py) : 0;
+    trace_pixel<false, true, BEAM>(S, C, frame, px, py, out_hit, out_t, nullptr, (size_t)py * C.W + px, &ck, Dn);
 }
 
 // Persistent casting over a list of views (P.queue[0] = next tile, P.queue[1]
@@ -150,9 +153,11 @@ __global__ void __launch_bounds__(128, 7) cast_grid(const __grid_constant__ Batc
     }
 }
 
+// Descriptor patches in the order the host queued them (one thread: a later
+// patch of the same descriptor must win, and there are at most kPatchMax).
 __global__ void patch_desc_kernel(ChunkRef* __restrict__ desc, const __grid_constant__ DescPatches P) {
-    const uint32_t i = threadIdx.x;
-    if (i < P.n) desc[P.p[i].index] = P.p[i].ref;
+    if (threadIdx.x != 0) return;
+    for (uint32_t i = 0; i < P.n; i++) desc[P.p[i].index] = P.p[i].ref;
 }
 
 __global__ void ray_dirs_kernel(CamDev C, float* __restrict__ dirs) {
@@ -198,8 +203,10 @@ int aokk_cast(const SceneDev* s, const CamDev* c, const ChunkRef* frame, uint4* 
     dim3 grid((c->W + 15) / 16, (c->H + 7) / 8);
     const cudaStream_t st = (cudaStream_t)stream;
     const BeamLookup bl = beam_lookup(beam, c->W, c->H);
-    if (ck && !counts)
-        cast_kernel_checked<<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, *ck);
+    if (ck && !counts && beam)
+        cast_kernel_checked<true><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, *ck, bl);
+    else if (ck && !counts)
+        cast_kernel_checked<false><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, *ck, bl);
     else if (counts && beam)
         cast_kernel<true, true><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, counts, bl);
     else if (counts)
@@ -366,7 +373,7 @@ int aokk_max_ctas_per_sm(uint32_t threads) {
 
 int aokk_patch_desc(ChunkRef* desc, const DescPatches* p, void* stream) {
     if (p->n == 0) return AOK_OK;
-    patch_desc_kernel<<<1, kPatchMax, 0, (cudaStream_t)stream>>>(desc, *p);
+    patch_desc_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(desc, *p);
     return status_of(cudaGetLastError());
 }
 
@@ -447,7 +454,7 @@ int aokk_render_noalloc(const SceneDev* s, const CamDev* c, uint4* hit, float* t
     select_kernel<<<(unsigned)((nch + 127) / 128), 128, 0, st>>>(*s, *c, frame, nullptr, nullptr, nullptr);
     dim3 grid((c->W + 15) / 16, (c->H + 7) / 8);
     if (ck)
-        cast_kernel_checked<<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, *ck);
+        cast_kernel_checked<false><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, *ck, beam_lookup(nullptr, 0, 0));
     else
         cast_kernel<false><<<grid, 128, 0, st>>>(*s, *c, frame, hit, t, nullptr, beam_lookup(nullptr, 0, 0));
     return status_of(cudaGetLastError());

@@ -948,14 +948,17 @@ static void beam_header(aok_ctx* ctx, BeamBatch* P, uint32_t tag) {
     P->cnt = ctx->beam.cnt;
     P->hist = ctx->beam.hist;
     P->select = 0;
+    std::memset(&P->ck, 0, sizeof(P->ck));  // unchecked
 }
 
 // The beam pass over the scene's current frame table, remembered with what
 // it was computed for.  select: the frame table is not selected yet; the
 // pass selects it as its first step (one launch fewer), or, for a view
-// without a usable projection, the selection kernel does.
+// without a usable projection, the selection kernel does.  ck: checked
+// casting's pool sizes and error word (the pass tests its node and leaf
+// indices too), or null.
 static int run_beam(aok_ctx* ctx, uint32_t scene, Scene* sc, const SceneDev& sd, const CamDev& cd, void* stream,
-                    bool select = false) {
+                    bool select = false, const CheckDev* ck = nullptr) {
     int st = ensure_beam_queues(ctx);
     if (st) return st;
     BeamState& b = ctx->beam;
@@ -967,6 +970,7 @@ static int run_beam(aok_ctx* ctx, uint32_t scene, Scene* sc, const SceneDev& sd,
     if (st) return st;
     BeamBatch* P = b.P.get();
     beam_header(ctx, P, tag);
+    if (ck) P->ck = *ck;
     P->n_views = 0;
     P->n_regions = 0;
     b.read.bounds = nullptr;  // no usable projection: no bounds, nothing is skipped
@@ -1053,9 +1057,10 @@ static bool beam_fresh(const aok_ctx* ctx, uint32_t scene, const Scene* sc, cons
     return std::memcmp(&k, &b.cam, sizeof(CamDev)) == 0;
 }
 
-// The casting launch of a single view: with the beam pass on (and no checked
-// casting) the casting kernel takes the pass's per-tile bounds, computed
-// first unless aok_beam_selected already did for this selection and camera.
+// The casting launch of a single view: with the beam pass on the casting
+// kernel takes the pass's per-tile bounds, computed first unless
+// aok_beam_selected already did for this selection and camera (with checked
+// casting the pass tests its node and leaf indices as well).
 // selected: the frame table is already selected; else the beam pass selects
 // it (or, without the pass, the selection kernel).
 static int cast_single(aok_ctx* ctx, uint32_t scene, Scene* sc, const SceneDev& sd, const CamDev& cd,
@@ -1064,9 +1069,9 @@ static int cast_single(aok_ctx* ctx, uint32_t scene, Scene* sc, const SceneDev& 
     const CheckDev* ckp = check_dev(ctx, sc, &ck);
     const BeamRead* beam = nullptr;
     int st = AOK_OK;
-    if (ctx->beam_on && !ckp && (uint64_t)cd.W * (uint64_t)cd.H >= ctx->beam_min_pixels) {
+    if (ctx->beam_on && (uint64_t)cd.W * (uint64_t)cd.H >= ctx->beam_min_pixels) {
         if (!selected || !beam_fresh(ctx, scene, sc, cd)) {
-            st = run_beam(ctx, scene, sc, sd, cd, stream, !selected);
+            st = run_beam(ctx, scene, sc, sd, cd, stream, !selected, ckp);
             if (st) return st;
             selected = true;
         }
@@ -1296,8 +1301,8 @@ int aok_select_beam(aok_ctx* ctx, uint32_t scene, const aok_camera* cam, double 
     SceneDev sd = scene_dev(sc);
     sc->select_gen++;
     CheckDev ck;
-    if (ctx->beam_on && !check_dev(ctx, sc, &ck) && (uint64_t)cd.W * (uint64_t)cd.H >= ctx->beam_min_pixels)
-        st = run_beam(ctx, scene, sc, sd, cd, stream, true);
+    if (ctx->beam_on && (uint64_t)cd.W * (uint64_t)cd.H >= ctx->beam_min_pixels)
+        st = run_beam(ctx, scene, sc, sd, cd, stream, true, check_dev(ctx, sc, &ck));
     else
         st = aokk_select(&sd, &cd, sc->d_frame, nullptr, nullptr, nullptr, stream);
     if (st == AOK_E_CUDA) return launch_failure(ctx);

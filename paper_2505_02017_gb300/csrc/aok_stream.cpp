@@ -14,6 +14,7 @@
 #include <deque>
 #include <mutex>
 #include <thread>
+#include <unordered_set>
 #include <vector>
 
 #include "aok_runtime.h"
@@ -368,7 +369,18 @@ int aok_stream_update(aok_stream* s, const aok_camera* cam, double tau, void* st
         std::make_heap(s->heap.begin(), s->heap.end(), LoadsLater());
     }
     s->work_cv.notify_all();
-    // 4. the descriptor changes, ordered before every later frame on `stream`
+    // 4. the descriptor changes, ordered before every later frame on `stream`;
+    //    a descriptor changed twice (a load installed above and evicted at
+    //    once because its region settled on another LOD) keeps only its last
+    //    change, the eviction: its space is quarantined and must never be
+    //    published
+    {
+        std::unordered_set<uint64_t> seen;
+        size_t keep = patches.size();
+        for (size_t i = patches.size(); i-- > 0;)
+            if (seen.insert(patches[i].index).second) patches[--keep] = patches[i];
+        patches.erase(patches.begin(), patches.begin() + (ptrdiff_t)keep);
+    }
     for (size_t i = 0; i < patches.size(); i += kPatchMax) {
         DescPatches P;
         P.n = (uint32_t)std::min<size_t>(kPatchMax, patches.size() - i);

@@ -276,6 +276,42 @@ def test_queue_overflow_same_output(ctx):
         aok.beam_tune(ctx, 8, 2, 0, 0)
 
 
+def test_checked_casting_with_the_pass(ctx):
+    """Checked casting keeps the beam pass and tests the pass's node and leaf
+    indices as well as the cast's: on several worlds, with ample and with
+    overflowing queues, no index is out of range, the bounds stay below
+    every hit and the frame equals the plain march's."""
+    assert aok.checked_errors(ctx) == 0
+    try:
+        for spec, camf, tau in (CASES[2], CASES[4], CASES[6]):
+            w, sc, _ = scene_for(ctx, spec)
+            cam = camf(w)
+            ref = render(ctx, sc, cam, tau, False)
+            for cap in (0, 40):
+                aok.beam_tune(ctx, 8, 2, 0, cap)
+                aok.set_checked(ctx, True)
+                try:
+                    out = render(ctx, sc, cam, tau, True)
+                finally:
+                    aok.set_checked(ctx, False)
+                assert aok.checked_errors(ctx) == 0, (spec.name, cap)
+                assert same(ref, out), (spec.name, cap)
+                b, _ = aok.beam_info(ctx)
+                g = decode(*out)
+                O = np.round(cam.origin.astype(np.float64) * 4096).astype(np.int64)
+                py, px = np.divmod(np.arange(cam.W * cam.H), cam.W)
+                h = g["hit"] == 1
+                lo = np.stack([g["x"], g["y"], g["z"]], 1).astype(np.int64) * 4096 - O
+                hi = lo + (np.int64(4096) << g["lod"].astype(np.int64))[:, None]
+                d = np.maximum(np.maximum(lo, -hi), 0).max(1)
+                assert (b[py // 4, px // 8].astype(np.int64)[h] <= d[h]).all(), (spec.name, cap)
+                if cap == 0 and spec is MED64:
+                    assert (b > 0).mean() > 0.5  # the checked pass bounds the walker view's tiles
+    finally:
+        aok.beam_tune(ctx, 8, 2, 0, 0)
+        aok.set_beam(ctx, False)
+
+
 def test_refinement_settings_same_output(ctx):
     """Any refinement setting gives the frame of the plain march."""
     w, sc, _ = scene_for(ctx, MED64)

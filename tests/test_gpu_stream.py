@@ -307,6 +307,70 @@ def test_async_prefetch_along_motion():
         ctx.close()
 
 
+def test_async_load_installed_and_evicted_in_one_update():
+    """A load that lands after its region has settled on another resident
+    LOD is installed and evicted by the same update (its space goes to
+    quarantine): the region's descriptor must end evicted, so that no frame
+    selects that LOD while its space can be reused.  Checked on every region
+    two path poses plan at different LODs, with selection at the pose that
+    asked for the load and a checked render there."""
+    from paper_2505_02017_gb300.stream import AsyncStreamer
+    spec = sg.OPEN_8192
+    w = sg.World(spec)
+    ctx = aok.Context(0)
+    sc = aok.Scene(ctx, spec, node_words=64 << 20, leaves=16 << 20, mat_bytes=1 << 30)
+    planner_scene = aok.Scene(ctx, spec, node_words=1 << 16, leaves=1 << 16, mat_bytes=1 << 16)
+    ast = AsyncStreamer(ctx, w, sc, threads=8)
+    try:
+        tau = 1.0 / 3.0
+        cams = sg.path_cameras(w, 77, 6, 160, 90, n_waypoints=3, span=3000.0)
+        planner = Streamer(ctx, w, planner_scene, threads=1)
+        plans = [planner.plan(c, tau) for c in cams]
+        best = None
+        for i in range(len(cams)):
+            for j in range(len(cams)):
+                both = (plans[i] != 0xFF) & (plans[j] != 0xFF) & (plans[i] != plans[j])
+                if i != j and (best is None or both.sum() > best[2]):
+                    best = (i, j, int(both.sum()))
+        ia, ib, n_diff = best
+        assert n_diff > 0
+        A, B = cams[ia], cams[ib]
+        ast.update(A, tau)
+        assert ast.wait(120000) == aok.AOK_OK
+        ast.update(A, tau)  # A's plan installed
+        assert ast.stats()["missing"] == 0
+        ast.update(B, tau)  # B's LODs load; the regions both plan keep A's LOD meanwhile
+        assert ast.wait(120000) == aok.AOK_OK
+        ast.update(A, tau)  # B's loads land: installed, and evicted at once where A's LOD is resident
+        torch.cuda.synchronize()
+        res = ast.resident().astype(np.int64)
+        n = sc.grid[0] * sc.grid[1] * sc.grid[2]
+        both = (plans[ia] != 0xFF) & (plans[ib] != 0xFF) & (plans[ia] != plans[ib])
+        assert not ((res[both] >> plans[ib][both].astype(np.int64)) & 1).any()  # evicted on the host
+        lod = torch.empty(n, dtype=torch.int8, device="cuda")
+        vis = torch.empty(n, dtype=torch.uint8, device="cuda")
+        aok.select_chunks(ctx, sc, B, tau, lod_out=lod, vis_out=vis)
+        torch.cuda.synchronize()
+        used = lod.cpu().numpy().astype(np.int64)
+        shown = vis.cpu().numpy() == 1
+        assert shown.any()
+        assert ((res[shown] >> used[shown]) & 1).all()  # every LOD a frame uses is resident
+        assert aok.checked_errors(ctx) == 0
+        aok.set_checked(ctx, True)
+        try:
+            hit, t = aok.alloc_frame(B.W, B.H)
+            aok.render(ctx, sc, B, tau, hit, t)
+            torch.cuda.synchronize()
+        finally:
+            aok.set_checked(ctx, False)
+        assert aok.checked_errors(ctx) == 0
+    finally:
+        ast.close()
+        sc.destroy()
+        planner_scene.destroy()
+        ctx.close()
+
+
 def test_scene_destroyed_under_a_running_streamer():
     """Destroying a scene (or its context) while its streamer still loads
     stops the streamer first: its workers are joined, later calls are
