@@ -323,7 +323,8 @@ def test_async_load_installed_and_evicted_in_one_update():
     ast = AsyncStreamer(ctx, w, sc, threads=8)
     try:
         tau = 1.0 / 3.0
-        cams = sg.path_cameras(w, 77, 6, 160, 90, n_waypoints=3, span=3000.0)
+        # at 320 x 180 and tau = 1/3 the path's poses plan LODs 0-3 (Eq. 1 depends on the image height)
+        cams = sg.path_cameras(w, 77, 6, 320, 180, n_waypoints=3, span=3000.0)
         planner = Streamer(ctx, w, planner_scene, threads=1)
         plans = [planner.plan(c, tau) for c in cams]
         best = None
