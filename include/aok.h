@@ -260,7 +260,8 @@ int aok_stream_create(aok_ctx* ctx, uint32_t scene, aok_chunk_source_fn source, 
 int aok_stream_update(aok_stream* s, const aok_camera* cam, double lod_threshold_px, void* stream);
 /* Block until no load is queued or running (AOK_E_TIMEOUT after timeout_ms;
  * < 0 waits without limit).  The finished loads are installed by the next
- * aok_stream_update. */
+ * aok_stream_update.  A wait under way when the scene is destroyed returns
+ * AOK_E_NOT_RESIDENT. */
 int aok_stream_wait(aok_stream* s, int32_t timeout_ms);
 /* Load ahead of need along the camera's motion (not in the paper, which
  * plans for the current camera only).  From its second update on, each

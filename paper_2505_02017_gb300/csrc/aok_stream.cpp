@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -73,7 +74,7 @@ struct aok_stream {
     std::mutex mu;
     std::condition_variable work_cv, idle_cv;
     bool stop = false;
-    bool detached = false;  // its scene was destroyed: workers joined, calls refused
+    std::atomic<bool> detached{false};  // its scene was destroyed: workers joined, calls refused
     std::vector<uint8_t> want;      // planned LOD per region (0xFF: none)
     std::vector<uint8_t> ahead;     // LODs of the extrapolated plans per region (bitmask)
     std::vector<uint8_t> resident;  // installed LODs per region (bitmask)
@@ -179,10 +180,16 @@ void stream_detach(aok_stream* s) {
     }
     s->loaded.clear();
     s->quarantine.clear();
-    std::lock_guard<std::mutex> lk(s->mu);
-    s->detached = true;
-    s->ctx = nullptr;
-    s->sc = nullptr;
+    {
+        // queued requests are dropped; a thread blocked in aok_stream_wait returns
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->heap.clear();
+        s->deferred.clear();
+        s->detached = true;
+        s->ctx = nullptr;
+        s->sc = nullptr;
+    }
+    s->idle_cv.notify_all();
 }
 
 }  // namespace aok
@@ -433,12 +440,10 @@ int aok_stream_wait(aok_stream* s, int32_t timeout_ms) {
     if (!s) return AOK_E_INVALID;
     if (s->detached) return AOK_E_NOT_RESIDENT;
     std::unique_lock<std::mutex> lk(s->mu);
-    auto idle = [&] { return s->heap.empty() && s->running == 0; };
-    if (timeout_ms < 0) {
-        s->idle_cv.wait(lk, idle);
-        return AOK_OK;
-    }
-    return s->idle_cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), idle) ? AOK_OK : AOK_E_TIMEOUT;
+    auto idle = [&] { return s->detached || (s->heap.empty() && s->running == 0); };
+    if (timeout_ms < 0) s->idle_cv.wait(lk, idle);
+    else if (!s->idle_cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), idle)) return AOK_E_TIMEOUT;
+    return s->detached ? AOK_E_NOT_RESIDENT : AOK_OK;
 }
 
 int aok_stream_stats(aok_stream* s, uint64_t* st) {

@@ -2,6 +2,8 @@
 within the view distance are resident; moving along a path evicts and builds
 chunks between frames, and every frame still equals the oracle on every
 non-ambiguous pixel."""
+import time
+
 import numpy as np
 import pytest
 
@@ -391,6 +393,20 @@ def test_scene_destroyed_under_a_running_streamer():
     assert st.wait(0) == aok.AOK_E_NOT_RESIDENT
     st.stats()
     st.close()
+    # a wait under way when the scene goes returns (AOK_E_NOT_RESIDENT, or AOK_OK
+    # if the loads finished first) instead of waiting for loads that never come
+    import threading
+    sc3 = aok.Scene(ctx, spec, node_words=64 << 20, leaves=16 << 20, mat_bytes=1 << 30)
+    st3 = AsyncStreamer(ctx, w, sc3, threads=2)
+    st3.update(cam, 1.0 / 3.0)
+    res = []
+    th = threading.Thread(target=lambda: res.append(st3.wait(60000)))
+    th.start()
+    time.sleep(0.05)
+    sc3.destroy()
+    th.join(90)
+    assert not th.is_alive() and res and res[0] in (aok.AOK_OK, aok.AOK_E_NOT_RESIDENT), res
+    st3.close()
     # the same through the context: its scenes go, and with them the streamer's
     sc2 = aok.Scene(ctx, spec, node_words=64 << 20, leaves=16 << 20, mat_bytes=1 << 30)
     st2 = AsyncStreamer(ctx, w, sc2, threads=4)
